@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark: HDG linearize + condense throughput on GB300.
+
+One step is one pass of the whole hot path over the workload: per-element
+quadrature-point fluxes and Jacobians, contraction into the element blocks,
+bordered elimination (interior LU, solves, Schur complement), assembly of the
+block-sparse trace system, one trace matvec and the interior recovery.
+
+Default workload: 16^3 = 4096 affine hexahedra of degree 2 on the periodic
+cube [0, 2 pi]^3 (Taylor-Green state at M = 0.1, Re = 1600, constant
+viscosity, seeded noise 1e-4), FP64.  Inputs are resident in HBM for ``value``;
+``e2e`` repeats the step through the C-ABI from pinned host buffers.
+
+``--impl reference`` times the FP64 CPU oracle on the host cores instead (the
+only other place this file runs ``oracle/``), on a bounded element sample.
+Under torchrun each rank runs an independent replica (elements are
+independent; no data-path collective) and rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "HDG linearize+condense elements/s & % of FP64/TC peak; mixed vs FP64 at tol"
+L2_BYTES = 129 * 1024 * 1024
+
+WORKLOADS = {
+    "hex-p2-16^3-tgv": dict(fn="config2", kw={}),
+    "hex-p3-24^3-tgv-av": dict(fn="config3", kw={}),
+    "quad-p2-8x8": dict(fn="config1", kw={}),
+}
+DEFAULT_WORKLOAD = "hex-p2-16^3-tgv"
+
+
+def make_problem(name):
+    import synth
+    w = WORKLOADS[name]
+    return getattr(synth, w["fn"])(**w["kw"])
+
+
+# ----------------------------------------------------------------------------
+# algorithmic FLOP counts per element (the executed reduced-structure counts)
+# ----------------------------------------------------------------------------
+def flop_counts(d, p):
+    m, n1, q1 = d + 2, p + 1, p + 2
+    Np, Nq, nf, Nfp, Nfq = n1 ** d, q1 ** d, 2 * d, n1 ** (d - 1), q1 ** (d - 1)
+    NU, NT = m * Np, nf * m * Nfp
+    NR, NC = NU + NT, NU + NT + 1
+    elim = sum(2 * (NR - k - 1) * (NC - k - 1) + (NR - k - 1) for k in range(NU))
+    NCB = Np + nf * Nfp
+    K = d * Nq
+    blocks = m * m * (2 * Np * NCB * K                 # contraction GEMM
+                      + K * (2 * (1 + d) * Np + nf * Nfp)  # generated operand
+                      + nf * (2 * Nfq * NCB * (d + 1) + 2 * Nfp * NCB * Nfq))  # face terms
+    return {"elim": elim, "blocks": blocks, "total": elim + blocks}
+
+
+# ----------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------
+# CPU oracle leg (spawned workers, one single-threaded process per core)
+# ----------------------------------------------------------------------------
+_W = {}
+
+
+def _worker_init(name):
+    sys.path.insert(0, ROOT)
+    from oracle.hdg import Problem
+    _W["pb"] = Problem(make_problem(name))
+
+
+def _worker_condense(e):
+    _W["pb"].condense(int(e))
+    return 1
+
+
+def oracle_pool(name, cores):
+    import multiprocessing as mp
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    ctx = mp.get_context("spawn")
+    pool = ctx.Pool(cores, initializer=_worker_init, initargs=(name,))
+    for k, v in saved.items():
+        if v is None:
+            del os.environ[k]
+        else:
+            os.environ[k] = v
+    pool.map(_worker_condense, [0] * cores)  # warm every worker
+    return pool
+
+
+def oracle_rate(pool, cores, n_elem, seconds, seed):
+    """Elements/s of the oracle's per-element linearize + condense on a seeded sample."""
+    import synth
+    done, t0 = 0, time.perf_counter()
+    batch = 0
+    while True:   # at least one batch of one element per core
+        ids = [int(x) for x in synth.splitmix64(seed + batch, cores) % n_elem]
+        done += sum(pool.map(_worker_condense, ids))
+        batch += 1
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt
+
+
+# ----------------------------------------------------------------------------
+# GPU leg
+# ----------------------------------------------------------------------------
+def fp64_peak_tflops(torch):
+    """cuBLAS DGEMM throughput measured in this run (the FP64 roofline denominator)."""
+    n = 4096
+    a = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    b = torch.randn(n, n, dtype=torch.float64, device="cuda")
+    c = a @ b
+    torch.cuda.synchronize()
+    best = 1e30
+    for _ in range(3):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        c = a @ b
+        e.record()
+        torch.cuda.synchronize()
+        best = min(best, s.elapsed_time(e))
+    del a, b, c
+    return 2 * n ** 3 / best / 1e9
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2608_27863_gb300 import build as B
+    from paper_2608_27863_gb300 import hdg as H
+
+    cpu = None
+    pool = None
+    ncores = os.cpu_count() or 1
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = oracle_pool(args.workload, ncores)      # before the first GPU call
+
+    torch.cuda.set_device(local_rank)
+    B.build()
+    P = make_problem(args.workload)
+    m = P.mesh
+    h = H.hdg_create(m.dim, m.vert_xyz, m.elem_vert, m.periodic_map, None, P.p, P.gamma, P.re, P.pr, P.mach)
+    H.hdg_set_params(h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s)
+    stream = torch.cuda.current_stream()
+    H.hdg_set_stream(h, stream.cuda_stream)
+    dev = torch.device("cuda", local_rank)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    U, Q, UH, Us = t(P.U), t(P.Q), t(P.UH), t(P.Ustar)
+    nu = None if P.nu is None else t(P.nu)
+    x = t(np.random.default_rng(rank).normal(size=P.UH.shape))
+    y = torch.empty_like(UH)
+    dQ, dU = torch.empty_like(Q), torch.empty_like(U)
+    flush = torch.empty(2 * L2_BYTES // 8, dtype=torch.float64, device=dev)
+
+    def step():
+        H.hdg_linearize_condense(h, U, Q, UH, Us, nu, P.dt, P.a_ii)
+        H.hdg_trace_matvec(h, x, y)
+        H.hdg_recover_interior(h, y, dQ, dU)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if H.hdg_status(h) != 0:
+        raise RuntimeError("device status: " + H.hdg_last_error(h))
+    peak = fp64_peak_tflops(torch)
+    H.hdg_profile_read(h)
+    H.hdg_profile(h, True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    times = []
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)       # L2 flush between timed steps (not timed)
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            step()
+            e.record(stream)
+            e.synchronize()
+            times.append(s.elapsed_time(e))
+    torch.cuda.synchronize()
+    prof = H.hdg_profile_read(h)
+    H.hdg_profile(h, False)
+    t_ms = sum(times)
+    if world > 1:
+        tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_ms = float(tt.item())
+        dist.barrier()
+
+    # end to end through the C-ABI from pinned host memory
+    hU, hQ, hUH, hUs = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (P.U, P.Q, P.UH, P.Ustar))
+    hdQ = torch.empty(dQ.shape, dtype=torch.float64).pin_memory()
+    hdU = torch.empty(dU.shape, dtype=torch.float64).pin_memory()
+    h2d = sum(a.numel() * 8 for a in (hU, hQ, hUH, hUs))
+    d2h = (hdQ.numel() + hdU.numel()) * 8
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        U.copy_(hU, non_blocking=True)
+        Q.copy_(hQ, non_blocking=True)
+        UH.copy_(hUH, non_blocking=True)
+        Us.copy_(hUs, non_blocking=True)
+        step()
+        hdQ.copy_(dQ, non_blocking=True)
+        hdU.copy_(dU, non_blocking=True)
+        e.record(stream)
+        e.synchronize()
+        e2e_ms += s.elapsed_time(e)
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_ms = float(tt.item())
+
+    if pool is not None:
+        rate, n_done, secs = oracle_rate(pool, ncores, m.n_elem, args.cpu_seconds, 100)
+        pool.close()
+        cpu = {"value": rate, "unit": "elements/s", "cores": ncores, "kind": "oracle",
+               "sample": "%d seeded elements of the same workload in %.1f s: per-element residual, complex-step "
+                         "Jacobian, dense FP64 LU of the (q,u) block and Schur complement (assembly, matvec "
+                         "and recovery not included)" % (n_done, secs)}
+
+    E = m.n_elem
+    fl = flop_counts(m.dim, P.p)
+    kern = {}
+    for k, (ms, n) in prof.items():
+        kern[k] = {"ms_per_step": ms / args.steps, "launches_per_step": n / args.steps}
+    kern["elim"]["gflops"] = fl["elim"] * E / (prof["elim"][0] / args.steps) / 1e6 if prof["elim"][0] else None
+    kern["blocks"]["gflops"] = fl["blocks"] * E / (prof["blocks"][0] / args.steps) / 1e6 if prof["blocks"][0] else None
+    dom = max(("elim", "blocks"), key=lambda k: prof[k][0])
+    avg_launch_ms = prof[dom][0] / max(prof[dom][1], 1)
+    per_launch_elems = E / max(prof[dom][1] / args.steps, 1)
+    achieved = fl[dom] * per_launch_elems / (avg_launch_ms * 1e-3) / 1e12
+    launches = sum(n for _, n in prof.values()) / args.steps
+    value = world * E * args.steps / (t_ms * 1e-3)
+    out = {
+        "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "elements_per_gpu": E, "degree": P.p, "dim": m.dim,
+                   "faces": H.hdg_query_sizes(h)["n_faces"], "parallelism": "replicas" if world > 1 else "single",
+                   "precision": "fp64", "l2": "flushed between timed steps (256 MiB write)"},
+        "roofline": {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (FP64 pipe)",
+                     "flops_per_element": fl[dom]},
+        "gflops_total": fl["total"] * E * args.steps / (t_ms * 1e-3) / 1e9,
+        "kernels": kern,
+        "e2e": {"value": world * E * args.steps / (e2e_ms * 1e-3), "unit": "elements/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches,
+        "clocks": clk.summary(),
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    H.hdg_destroy(h)
+    return out
+
+
+def run_reference(args, rank, world):
+    """The FP64 CPU oracle as it stands, on the host cores, same workload and metric."""
+    if rank != 0:
+        return None
+    ncores = os.cpu_count() or 1
+    P = make_problem(args.workload)
+    pool = oracle_pool(args.workload, ncores)
+    for w in range(args.warmup):
+        oracle_rate(pool, ncores, P.mesh.n_elem, 0.0, 500 + w)
+    tot_e, tot_s = 0, 0.0
+    for k in range(args.steps):
+        _, n, s = oracle_rate(pool, ncores, P.mesh.n_elem, 0.0, 900 + k)
+        tot_e += n
+        tot_s += s
+    pool.close()
+    rate = tot_e / tot_s
+    return {
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": "elements/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "elements_per_gpu": P.mesh.n_elem, "degree": P.p},
+        "cpu_baseline": {"value": rate, "unit": "elements/s", "cores": ncores, "kind": "oracle",
+                         "sample": "each step condenses %d seeded elements (one per core) of the workload" % ncores},
+        "e2e": {"value": rate, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl")
+        out = run_ours(args, rank, world, local_rank)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if rank == 0 and out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

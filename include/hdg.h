@@ -1,0 +1,173 @@
+/*
+ * hdg.h -- C-ABI of the GB300 HDG linearize + condense library (libhdg.so).
+ *
+ * The library implements the data-parallel hot path of an implicit HDG
+ * discretization of the compressible Navier-Stokes equations (Welter, Collin,
+ * Nguyen, Peraire): at one Newton step of one DIRK stage it evaluates the
+ * element residuals and their Jacobians at quadrature points (Sec. 2.1, 2.2,
+ * eqs. hdg-weak, num-flux-hdg, fully-discrete-local), contracts them into the
+ * element blocks, eliminates the interior unknowns (Q, U) by static
+ * condensation (Sec. 2.5, eqs. newton-local-block, local-elimination,
+ * schur-trace), scatters the condensed face blocks into a block-sparse trace
+ * matrix, and provides the trace matvec and the interior recovery that GMRES
+ * consumes (Sec. 3.2).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  d = 2 (quadrilaterals) or 3 (hexahedra), m = d + 2 conserved variables
+ *  u = [rho, rho v_1..rho v_d, rho E]; degree p (1..3); element nodes are the
+ *  tensor Gauss-Lobatto points, Np = (p+1)^d, node j = j1 + (p+1) j2 +
+ *  (p+1)^2 j3; local face f = 2 r + s is the face xi_r = -1 (s = 0) or +1
+ *  (s = 1); Nfp = (p+1)^(d-1) trace nodes per face, ordered in the face's
+ *  canonical frame (origin at the corner with the smallest master vertex id,
+ *  first axis towards the adjacent corner with the smaller id).
+ *  Faces are numbered by first encounter scanning elements and local faces.
+ *
+ *  Device arrays (caller-owned, FP64, contiguous, row-major as written):
+ *    U     [E][m][Np]          conserved state
+ *    Q     [E][d][m][Np]       gradient, Q[e][k][a] = d u_a / d x_k
+ *    UH    [F][m][Nfp]         single-valued trace
+ *    Ustar [E][m][Np]          known DIRK stage data: the stage residual is
+ *                              (1/a_ii) M (U - Ustar) + dt N(W)
+ *    nu    [E][Np]             nodal artificial viscosity (frozen), or NULL
+ *  Trace vectors x, y, g, dUH are [F][m][Nfp].
+ *
+ * Errors: every call returns HDG_OK (0) or a negative code; the handle keeps a
+ * message (hdg_last_error).  Nothing aborts, exits or traps on the device.
+ * Device work is asynchronous on the stream set with hdg_set_stream (default:
+ * the legacy default stream); the caller synchronises.  Numerical failures
+ * found on the device (zero pivot, non-finite values) are latched in a status
+ * word that hdg_status() reads back.
+ */
+#ifndef HDG_H
+#define HDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HDG_OK 0
+#define HDG_EINVAL (-1)       /* bad argument */
+#define HDG_ENOMEM (-2)       /* device or host allocation failed */
+#define HDG_ECUDA (-3)        /* a CUDA runtime call failed */
+#define HDG_ESINGULAR (-4)    /* zero pivot in an element interior block */
+#define HDG_ENONFINITE (-5)   /* NaN / Inf in an element block */
+#define HDG_ENOCONV (-6)      /* iterative solve did not converge */
+#define HDG_EUNSUPPORTED (-7) /* mesh / degree / mode not supported */
+
+#define HDG_QUAD 1
+#define HDG_HEX 2
+
+/* Arithmetic of the condensation path. */
+#define HDG_PREC_FP64 0       /* everything in FP64 */
+
+typedef struct hdg_ctx* hdg_handle;
+
+/* Mesh description, host memory, copied at create; the caller keeps ownership.
+ * Elements are affine (parallelograms / parallelepipeds); vertices in tensor
+ * order, vertex c = c1 + 2 c2 + 4 c3 at reference corner xi_r = 2 c_r - 1. */
+typedef struct {
+    int32_t dim;                  /* 2 or 3 */
+    int32_t elem_type;            /* HDG_QUAD (dim 2) or HDG_HEX (dim 3) */
+    int64_t n_elem;
+    int64_t n_vert;
+    const double* vert_xyz;       /* [n_vert][dim] */
+    const int64_t* elem_vert;     /* [n_elem][2^dim] */
+    const int64_t* periodic_map;  /* [n_vert] master vertex of each vertex, or NULL */
+    const int32_t* bnd_tag;       /* [n_elem][2 dim] 0 = interior / periodic, or NULL */
+} hdg_mesh;
+
+/* Solver parameters (hdg_set_params).  tau: constant scalar stabilization of
+ * eq. num-flux-hdg; visc_law 0: mu = 1/Re, 1: mu = C1 T^1.5 / (T + S) / Re
+ * with T = gamma (gamma-1) M^2 e (eq. sutherland, eq. tgv-sutherland). */
+typedef struct {
+    double tau;
+    int32_t visc_law;
+    double suth_c1;
+    double suth_s;
+    int32_t precision;            /* HDG_PREC_* */
+} hdg_params;
+
+typedef struct {
+    int32_t dim, p, m, Np, Nq, nf, Nfp, Nfq;
+    int32_t n_u;                  /* m Np: interior U unknowns per element */
+    int32_t n_q;                  /* d m Np */
+    int32_t t;                    /* nf m Nfp: trace unknowns per element */
+    int32_t block;                /* m Nfp: BSR block size */
+    int64_t n_elem, n_faces, nnzb;
+    int64_t device_bytes;         /* device memory held by the handle */
+} hdg_sizes;
+
+/* Build tables, connectivity, the BSR pattern and device storage (Sec. 2.2
+ * spaces, Sec. 3.5 face partition).  Fails with HDG_EUNSUPPORTED for
+ * non-affine elements or p outside 1..3, HDG_EINVAL for inconsistent meshes
+ * (a face shared by more than two elements, a degenerate periodic face). */
+int hdg_create(hdg_handle* out, const hdg_mesh* mesh, int p, double gamma, double Re,
+               double Pr, double Mach);
+/* Same as hdg_create without touching the GPU: connectivity and tables only;
+ * device calls on such a handle return HDG_EINVAL. */
+int hdg_create_host(hdg_handle* out, const hdg_mesh* mesh, int p, double gamma, double Re,
+                    double Pr, double Mach);
+int hdg_destroy(hdg_handle h);
+const char* hdg_last_error(hdg_handle h);
+
+int hdg_set_params(hdg_handle h, const hdg_params* prm);
+int hdg_set_stream(hdg_handle h, void* cuda_stream);
+int hdg_query_sizes(hdg_handle h, hdg_sizes* out);
+
+/* Host copies of the integer skeleton data (any pointer may be NULL):
+ * f2e [F][2] elements of each face (-1 on the boundary), f2lf [F][2] local
+ * faces, e2f [E][nf], perm [E][nf][Nfp] canonical index of each local face
+ * node, bsr_rowptr [F+1], bsr_col [nnzb] (ascending within a row). */
+int hdg_get_connectivity(hdg_handle h, int32_t* f2e, int32_t* f2lf, int32_t* e2f,
+                         int32_t* perm, int32_t* bsr_rowptr, int32_t* bsr_col);
+
+/* One Newton linearization of one DIRK stage at W = (Q, U, UH), followed by
+ * static condensation of every element and assembly of the trace system
+ * S dUH = g (eqs. newton-linearization, local-elimination, schur-trace).
+ * Inputs are device pointers (layouts above); dt and a_ii enter the stage
+ * residual of eq. fully-discrete-local.  The library keeps S (BSR), g and the
+ * per-element factors needed by hdg_recover_interior.  res_norm must be NULL
+ * (the FP64 residual norm is hdg_residual_norm). */
+int hdg_linearize_condense(hdg_handle h, const double* U, const double* Q, const double* UH,
+                           const double* Ustar, const double* nu, double dt, double a_ii,
+                           double* res_norm);
+
+/* y = S x on the assembled trace operator (device pointers, [F][m][Nfp]). */
+int hdg_trace_matvec(hdg_handle h, const double* x, double* y);
+/* Copy the condensed right-hand side g = sum_K (-R_uhat^K + C^K y^K) to g. */
+int hdg_trace_rhs(hdg_handle h, double* g);
+/* Interior recovery dW_K = -y_K - X_K dUH_K (eq. local-elimination) for every
+ * element: dQ [E][d][m][Np], dU [E][m][Np] (device, caller-owned). */
+int hdg_recover_interior(hdg_handle h, const double* dUH, double* dQ, double* dU);
+/* Copy the BSR values: [nnzb][block][block], block column-major, i.e.
+ * value (r, c) of block b at vals[(b * block + c) * block + r], r = a Nfp + k. */
+int hdg_get_blocks(hdg_handle h, double* vals);
+/* Read back the latched device status: HDG_OK, HDG_ESINGULAR or
+ * HDG_ENONFINITE (synchronises the stream). */
+int hdg_status(hdg_handle h);
+
+/* Per-kernel timing with CUDA events recorded on the handle's stream around
+ * every kernel launch (not from the paper: instrumentation for rooflines).
+ * Kernel classes: HDG_K_POINT (A0/A1 quadrature-point fluxes and Jacobians),
+ * HDG_K_BLOCKS (A2 contraction), HDG_K_ELIM (A3/A4 bordered elimination),
+ * HDG_K_ASSEMBLE (A5), HDG_K_MATVEC (A6), HDG_K_RECOVER (A7).
+ * hdg_profile_read synchronises the stream, writes the accumulated
+ * milliseconds [HDG_NK] and launch counts [HDG_NK] since the last read, and
+ * clears them. */
+#define HDG_K_POINT 0
+#define HDG_K_BLOCKS 1
+#define HDG_K_ELIM 2
+#define HDG_K_ASSEMBLE 3
+#define HDG_K_MATVEC 4
+#define HDG_K_RECOVER 5
+#define HDG_NK 6
+int hdg_profile(hdg_handle h, int enable);
+int hdg_profile_read(hdg_handle h, double* ms, int64_t* launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HDG_H */

@@ -69,7 +69,7 @@ class Geometry:
             J = jac(ref.xq[g])
             Jinv = np.linalg.inv(J)  # Jinv[r, k] = d xi_r / d x_k
             self.W[g] = ref.wq[g] * np.linalg.det(J)
-            self.dphi[g] = np.einsum("ri,rk->ik", ref.dphi[:, g, :], Jinv)
+            self.dphi[g] = np.einsum("ri,rk->ik", ref.dphi[:, g, :], Jinv, optimize=True)
         self.omega = np.zeros((ref.nf, ref.Nfq))
         self.n = np.zeros((ref.nf, ref.Nfq, d))
         for f in range(ref.nf):
@@ -79,7 +79,7 @@ class Geometry:
                 nw = ref.wf[s] * np.linalg.det(J) * (Jinv.T @ ref.nref[f])
                 self.omega[f, s] = np.linalg.norm(nw)
                 self.n[f, s] = nw / self.omega[f, s]
-        self.M = np.einsum("g,gi,gj->ij", self.W, ref.phi, ref.phi)
+        self.M = np.einsum("g,gi,gj->ij", self.W, ref.phi, ref.phi, optimize=True)
 
 
 class Problem:
@@ -137,9 +137,9 @@ class Problem:
         nu_g = None if nu_nodes is None else r.phi @ nu_nodes
         F = convective_flux(u_g, ph) - viscous_flux(u_g, q_g, nu_g, ph)
         Ru = (1.0 / self.a_ii) * (Ue - self.Ustar[e]) @ G.M.T
-        Ru = Ru - self.dt * np.einsum("g,...gak,gik->...ai", G.W, F, G.dphi)
-        Rq = np.einsum("g,...gak,gi->...kai", G.W, q_g, r.phi)
-        Rq = Rq + np.einsum("g,...ga,gik->...kai", G.W, u_g, G.dphi)
+        Ru = Ru - self.dt * np.einsum("g,...gak,gik->...ai", G.W, F, G.dphi, optimize=True)
+        Rq = np.einsum("g,...gak,gi->...kai", G.W, q_g, r.phi, optimize=True)
+        Rq = Rq + np.einsum("g,...ga,gik->...kai", G.W, u_g, G.dphi, optimize=True)
         Rh = np.zeros(Ue.shape[:-2] + (r.nf, r.m, r.Nfp), dtype=np.result_type(Qe, Ue, UHe, 1.0))
         for f in range(r.nf):
             u_s = np.swapaxes(Ue @ r.phif[f].T, -1, -2)              # [..., s, a]
@@ -147,14 +147,14 @@ class Problem:
             uh_s = np.swapaxes(UHe[..., f, :, :] @ r.mu.T, -1, -2)   # [..., s, a]
             nu_s = None if nu_nodes is None else r.phif[f] @ nu_nodes
             fhat = numerical_flux(u_s, uh_s, q_s, nu_s, G.n[f], self.tau, ph)
-            Ru = Ru + self.dt * np.einsum("s,...sa,sj->...aj", G.omega[f], fhat, r.phif[f])
-            Rq = Rq - np.einsum("s,...sa,sk,sj->...kaj", G.omega[f], uh_s, G.n[f], r.phif[f])
+            Ru = Ru + self.dt * np.einsum("s,...sa,sj->...aj", G.omega[f], fhat, r.phif[f], optimize=True)
+            Rq = Rq - np.einsum("s,...sa,sk,sj->...kaj", G.omega[f], uh_s, G.n[f], r.phif[f], optimize=True)
             tag = int(self.bnd[e, f])
             if tag == 0:
-                Rh[..., f, :, :] = np.einsum("s,...sa,sl->...al", G.omega[f], fhat, r.mu)
+                Rh[..., f, :, :] = np.einsum("s,...sa,sl->...al", G.omega[f], fhat, r.mu, optimize=True)
             elif tag == 1:
                 bh = uh_s - self.ubc
-                Rh[..., f, :, :] = np.einsum("s,...sa,sl->...al", G.omega[f], bh, r.mu)
+                Rh[..., f, :, :] = np.einsum("s,...sa,sl->...al", G.omega[f], bh, r.mu, optimize=True)
             else:
                 raise ValueError("boundary tag %d not in the oracle" % tag)
         return Rq, Ru, Rh

@@ -1,0 +1,363 @@
+// C-ABI entry points of libhdg: handle life cycle, host set-up (tables,
+// skeleton, affine geometry), device storage and dispatch to the kernels of
+// the (d, p) configuration.
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "common.h"
+
+using namespace hdg;
+
+namespace hdg {
+void prof_begin(hdg_ctx* h, int kind) {
+    h->launches[kind] += 1;
+    if (!h->prof) return;
+    while (h->ev_pool.size() < h->ev_used + 2) {
+        cudaEvent_t ev;
+        if (cudaEventCreate(&ev) != cudaSuccess) { h->prof = false; return; }
+        h->ev_pool.push_back(ev);
+    }
+    cudaEventRecord(h->ev_pool[h->ev_used], h->stream);
+    h->ev_kind.push_back(kind);
+}
+void prof_end(hdg_ctx* h) {
+    if (!h->prof || h->ev_kind.size() * 2 != h->ev_used + 2) return;
+    cudaEventRecord(h->ev_pool[h->ev_used + 1], h->stream);
+    h->ev_used += 2;
+}
+}  // namespace hdg
+
+namespace {
+
+int fail(hdg_ctx* h, int code, const std::string& msg) {
+    if (h) h->err = msg;
+    return code;
+}
+
+#define CKH(call)                                                                   \
+    do {                                                                            \
+        cudaError_t e_ = (call);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            return fail(h, e_ == cudaErrorMemoryAllocation ? HDG_ENOMEM : HDG_ECUDA, \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));        \
+    } while (0)
+
+// Affine element geometry: x = X0 + J (xi + 1), J[:, r] = (X_{2^r} - X_0) / 2.
+int build_geometry(hdg_ctx* h, const hdg_mesh& m) {
+    const int d = h->d, nv = 1 << d, nf = 2 * d;
+    h->detJ.assign(h->E, 0.0);
+    h->Jinv.assign((size_t)h->E * d * d, 0.0);
+    h->NW.assign((size_t)h->E * nf * d, 0.0);
+    for (int64_t e = 0; e < h->E; ++e) {
+        double X[8][3] = {};
+        for (int c = 0; c < nv; ++c)
+            for (int k = 0; k < d; ++k) X[c][k] = m.vert_xyz[(size_t)m.elem_vert[(size_t)e * nv + c] * d + k];
+        double J[3][3] = {};  // J[k][r] = d x_k / d xi_r
+        for (int r = 0; r < d; ++r)
+            for (int k = 0; k < d; ++k) J[k][r] = 0.5 * (X[1 << r][k] - X[0][k]);
+        double diam = 0.0;
+        for (int r = 0; r < d; ++r)
+            for (int k = 0; k < d; ++k) diam = std::max(diam, std::fabs(J[k][r]));
+        for (int c = 0; c < nv; ++c)
+            for (int k = 0; k < d; ++k) {
+                double x = X[0][k];
+                for (int r = 0; r < d; ++r) if ((c >> r) & 1) x += 2.0 * J[k][r];
+                if (std::fabs(x - X[c][k]) > 1e-10 * diam)
+                    return fail(h, HDG_EUNSUPPORTED, "element " + std::to_string(e) + " is not affine");
+            }
+        double det, inv[3][3];
+        if (d == 2) {
+            det = J[0][0] * J[1][1] - J[0][1] * J[1][0];
+            inv[0][0] = J[1][1] / det; inv[0][1] = -J[0][1] / det;
+            inv[1][0] = -J[1][0] / det; inv[1][1] = J[0][0] / det;
+        } else {
+            det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) - J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                  J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j) {
+                    int i1 = (j + 1) % 3, i2 = (j + 2) % 3, j1 = (i + 1) % 3, j2 = (i + 2) % 3;
+                    inv[i][j] = (J[i1][j1] * J[i2][j2] - J[i1][j2] * J[i2][j1]) / det;
+                }
+        }
+        if (!(det > 0.0)) return fail(h, HDG_EINVAL, "element " + std::to_string(e) + " has non-positive volume");
+        // inv[r][k] = d xi_r / d x_k
+        h->detJ[e] = det;
+        for (int r = 0; r < d; ++r)
+            for (int k = 0; k < d; ++k) h->Jinv[((size_t)e * d + r) * d + k] = inv[r][k];
+        for (int f = 0; f < nf; ++f) {
+            int r = f / 2;
+            double sg = (f % 2) ? 1.0 : -1.0;
+            for (int k = 0; k < d; ++k) h->NW[((size_t)e * nf + f) * d + k] = det * sg * inv[r][k];
+        }
+    }
+    return HDG_OK;
+}
+
+int create_host(hdg_ctx* h, const hdg_mesh* mesh, int p, double gamma, double Re, double Pr, double Mach) {
+    if (!mesh) return fail(h, HDG_EINVAL, "mesh is NULL");
+    if (!(mesh->dim == 2 && mesh->elem_type == HDG_QUAD) && !(mesh->dim == 3 && mesh->elem_type == HDG_HEX))
+        return fail(h, HDG_EUNSUPPORTED, "supported elements: HDG_QUAD (dim 2), HDG_HEX (dim 3)");
+    if (p < 1 || p > 3) return fail(h, HDG_EUNSUPPORTED, "degree p must be 1, 2 or 3");
+    if (mesh->n_elem <= 0 || mesh->n_vert <= 0 || !mesh->vert_xyz || !mesh->elem_vert)
+        return fail(h, HDG_EINVAL, "empty mesh or NULL arrays");
+    if (!(gamma > 1.0) || !(Re > 0.0) || !(Pr > 0.0) || !(Mach > 0.0))
+        return fail(h, HDG_EINVAL, "gamma > 1, Re > 0, Pr > 0, Mach > 0 required");
+    const int d = mesh->dim;
+    h->d = d; h->p = p; h->m = d + 2;
+    h->Np = ipow(p + 1, d); h->Nq = ipow(p + 2, d); h->nf = 2 * d;
+    h->Nfp = ipow(p + 1, d - 1); h->Nfq = ipow(p + 2, d - 1);
+    h->NU = h->m * h->Np; h->NQV = d * h->m * h->Np; h->NT = h->nf * h->m * h->Nfp;
+    h->NR = h->NU + h->NT; h->NC = h->NR + 1; h->LD = (h->NC + 3) & ~3;
+    h->BS = h->m * h->Nfp; h->NCOEF = 1 + d + h->nf;
+    h->E = mesh->n_elem;
+    h->phys = Phys{gamma, Re, Pr, Mach, 5.0, 0, 1.4042, 0.40417};
+    try {
+        build_ref_tables(d, p, h->ref);
+    } catch (const std::exception& ex) {
+        return fail(h, HDG_EINVAL, ex.what());
+    }
+    int rc = build_skeleton(*mesh, p, h->sk, h->err);
+    if (rc) return rc;
+    h->F = h->sk.n_faces;
+    h->nnzb = h->sk.rowptr[h->F];
+    if (mesh->bnd_tag)
+        for (int64_t i = 0; i < h->E * h->nf; ++i)
+            if (mesh->bnd_tag[i] != 0)
+                return fail(h, HDG_EUNSUPPORTED, "boundary faces are not supported yet (periodic meshes only)");
+    for (int64_t F = 0; F < h->F; ++F)
+        if (h->sk.f2e[2 * F + 1] < 0)
+            return fail(h, HDG_EUNSUPPORTED, "boundary faces are not supported yet (periodic meshes only)");
+    return build_geometry(h, *mesh);
+}
+
+template <class T>
+int dev_alloc(hdg_ctx* h, T** out, size_t count) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, HDG_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    h->allocs.push_back(p);
+    h->device_bytes += (int64_t)(count * sizeof(T));
+    *out = (T*)p;
+    return HDG_OK;
+}
+
+template <class T>
+int dev_upload(hdg_ctx* h, T** out, const std::vector<T>& v) {
+    int rc = dev_alloc(h, out, v.size());
+    if (rc) return rc;
+    CKH(cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return HDG_OK;
+}
+
+int create_device(hdg_ctx* h) {
+    const RefTables& t = h->ref;
+    int rc;
+#define UP(dst, src) if ((rc = dev_upload(h, &(dst), (src)))) return rc
+    UP(h->tab.phi, t.phi); UP(h->tab.dphi, t.dphi); UP(h->tab.wq, t.wq);
+    UP(h->tab.mu, t.mu); UP(h->tab.wf, t.wf); UP(h->tab.fnode, t.fnode); UP(h->tab.node_face, t.node_face);
+    UP(h->tab.mhat, t.mhat); UP(h->tab.mf, t.mf); UP(h->tab.minv_c, t.minv_c); UP(h->tab.minv_e, t.minv_e);
+    UP(h->tab.psi, t.psi); UP(h->tab.theta, t.theta); UP(h->tab.psi_f, t.psi_f); UP(h->tab.theta_f, t.theta_f);
+    const int d = h->d, G = 1 + d * d + h->nf * d;
+    std::vector<double> geo((size_t)h->E * G);
+    for (int64_t e = 0; e < h->E; ++e) {
+        double* g = &geo[(size_t)e * G];
+        g[0] = h->detJ[e];
+        for (int i = 0; i < d * d; ++i) g[1 + i] = h->Jinv[(size_t)e * d * d + i];
+        for (int i = 0; i < h->nf * d; ++i) g[1 + d * d + i] = h->NW[(size_t)e * h->nf * d + i];
+    }
+    UP(h->d_geo, geo);
+    UP(h->d_e2f, h->sk.e2f); UP(h->d_perm, h->sk.perm); UP(h->d_iperm, h->sk.iperm);
+    UP(h->d_rowptr, h->sk.rowptr); UP(h->d_col, h->sk.col);
+    UP(h->d_blk, h->sk.blk); UP(h->d_rank, h->sk.rank); UP(h->d_frank, h->sk.frank);
+#undef UP
+    if ((rc = dev_alloc(h, &h->d_vals, (size_t)h->nnzb * h->BS * h->BS))) return rc;
+    if ((rc = dev_alloc(h, &h->d_g, (size_t)h->F * h->BS))) return rc;
+    if ((rc = dev_alloc(h, &h->d_top, (size_t)h->E * h->NU * h->LD))) return rc;
+    if ((rc = dev_alloc(h, &h->d_dq0, (size_t)h->E * h->NQV))) return rc;
+    if ((rc = dev_alloc(h, &h->d_status, 1))) return rc;
+    CKH(cudaMemset(h->d_status, 0, sizeof(int32_t)));
+    // per-chunk scratch: trace rows of the bordered matrix and the point coefficients
+    const size_t per = sizeof(double) * ((size_t)h->NT * h->LD + (size_t)h->m * h->m * d * h->NCOEF * h->Nq +
+                                         (size_t)h->nf * h->m * h->m * h->NCOEF * h->Nfq);
+    size_t budget = (size_t)8 << 30;
+    if (const char* s = std::getenv("HDG_SCRATCH_BYTES")) budget = std::strtoull(s, nullptr, 10);
+    h->chunk = std::max<int64_t>(1, std::min<int64_t>(h->E, (int64_t)(budget / per)));
+    if ((rc = dev_alloc(h, &h->d_bot, (size_t)h->chunk * h->NT * h->LD))) return rc;
+    if ((rc = dev_alloc(h, &h->d_vcoef, (size_t)h->chunk * h->m * h->m * d * h->NCOEF * h->Nq))) return rc;
+    if ((rc = dev_alloc(h, &h->d_fcoef, (size_t)h->chunk * h->nf * h->m * h->m * h->NCOEF * h->Nfq))) return rc;
+    h->device = true;
+    return HDG_OK;
+}
+
+#define DISPATCH(FN, ...)                                                       \
+    switch (h->d * 10 + h->p) {                                                  \
+        case 21: return FN<2, 1>(__VA_ARGS__);                                   \
+        case 22: return FN<2, 2>(__VA_ARGS__);                                   \
+        case 23: return FN<2, 3>(__VA_ARGS__);                                   \
+        case 31: return FN<3, 1>(__VA_ARGS__);                                   \
+        case 32: return FN<3, 2>(__VA_ARGS__);                                   \
+        case 33: return FN<3, 3>(__VA_ARGS__);                                   \
+        default: return fail(h, HDG_EUNSUPPORTED, "unsupported (d, p)");        \
+    }
+
+}  // namespace
+
+extern "C" {
+
+int hdg_create_host(hdg_handle* out, const hdg_mesh* mesh, int p, double gamma, double Re, double Pr, double Mach) {
+    if (!out) return HDG_EINVAL;
+    *out = nullptr;
+    hdg_ctx* h = new (std::nothrow) hdg_ctx();
+    if (!h) return HDG_ENOMEM;
+    int rc = create_host(h, mesh, p, gamma, Re, Pr, Mach);
+    *out = h;  // the handle is returned even on failure so that hdg_last_error works
+    return rc;
+}
+
+int hdg_create(hdg_handle* out, const hdg_mesh* mesh, int p, double gamma, double Re, double Pr, double Mach) {
+    int rc = hdg_create_host(out, mesh, p, gamma, Re, Pr, Mach);
+    if (rc) return rc;
+    hdg_ctx* h = *out;
+    rc = create_device(h);
+    return rc;
+}
+
+int hdg_destroy(hdg_handle h) {
+    if (!h) return HDG_OK;
+    for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
+    for (void* p : h->allocs) cudaFree(p);
+    delete h;
+    return HDG_OK;
+}
+
+const char* hdg_last_error(hdg_handle h) { return h ? h->err.c_str() : "NULL handle"; }
+
+int hdg_set_params(hdg_handle h, const hdg_params* prm) {
+    if (!h || !prm) return fail(h, HDG_EINVAL, "NULL argument");
+    if (!(prm->tau > 0.0)) return fail(h, HDG_EINVAL, "tau must be positive");
+    if (prm->visc_law != 0 && prm->visc_law != 1) return fail(h, HDG_EINVAL, "visc_law must be 0 or 1");
+    if (prm->visc_law == 1 && !(prm->suth_c1 > 0.0 && prm->suth_s > 0.0))
+        return fail(h, HDG_EINVAL, "Sutherland constants must be positive");
+    if (prm->precision != HDG_PREC_FP64) return fail(h, HDG_EUNSUPPORTED, "precision mode not available");
+    h->phys.tau = prm->tau;
+    h->phys.visc_law = prm->visc_law;
+    h->phys.c1 = prm->suth_c1;
+    h->phys.s = prm->suth_s;
+    h->precision = prm->precision;
+    return HDG_OK;
+}
+
+int hdg_set_stream(hdg_handle h, void* stream) {
+    if (!h) return HDG_EINVAL;
+    h->stream = (cudaStream_t)stream;
+    return HDG_OK;
+}
+
+int hdg_query_sizes(hdg_handle h, hdg_sizes* o) {
+    if (!h || !o) return fail(h, HDG_EINVAL, "NULL argument");
+    o->dim = h->d; o->p = h->p; o->m = h->m; o->Np = h->Np; o->Nq = h->Nq; o->nf = h->nf;
+    o->Nfp = h->Nfp; o->Nfq = h->Nfq; o->n_u = h->NU; o->n_q = h->NQV; o->t = h->NT; o->block = h->BS;
+    o->n_elem = h->E; o->n_faces = h->F; o->nnzb = h->nnzb; o->device_bytes = h->device_bytes;
+    return HDG_OK;
+}
+
+int hdg_get_connectivity(hdg_handle h, int32_t* f2e, int32_t* f2lf, int32_t* e2f, int32_t* perm,
+                         int32_t* rowptr, int32_t* col) {
+    if (!h) return HDG_EINVAL;
+    const Skeleton& s = h->sk;
+    if (f2e) std::memcpy(f2e, s.f2e.data(), s.f2e.size() * sizeof(int32_t));
+    if (f2lf) std::memcpy(f2lf, s.f2lf.data(), s.f2lf.size() * sizeof(int32_t));
+    if (e2f) std::memcpy(e2f, s.e2f.data(), s.e2f.size() * sizeof(int32_t));
+    if (perm) std::memcpy(perm, s.perm.data(), s.perm.size() * sizeof(int32_t));
+    if (rowptr) std::memcpy(rowptr, s.rowptr.data(), s.rowptr.size() * sizeof(int32_t));
+    if (col) std::memcpy(col, s.col.data(), s.col.size() * sizeof(int32_t));
+    return HDG_OK;
+}
+
+int hdg_linearize_condense(hdg_handle h, const double* U, const double* Q, const double* UH, const double* Ustar,
+                           const double* nu, double dt, double a_ii, double* res_norm) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage (created with hdg_create_host)");
+    if (!U || !Q || !UH || !Ustar) return fail(h, HDG_EINVAL, "U, Q, UH and Ustar are required");
+    if (res_norm) return fail(h, HDG_EINVAL, "res_norm must be NULL");
+    if (!(dt > 0.0) || !(a_ii > 0.0)) return fail(h, HDG_EINVAL, "dt and a_ii must be positive");
+    CKH(cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), h->stream));
+    LinArgs a{U, Q, UH, Ustar, nu, dt, a_ii};
+    DISPATCH(run_linearize, h, a);
+}
+
+int hdg_trace_matvec(hdg_handle h, const double* x, double* y) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
+    if (!x || !y || x == y) return fail(h, HDG_EINVAL, "x and y must be distinct device arrays");
+    DISPATCH(run_matvec, h, x, y);
+}
+
+int hdg_trace_rhs(hdg_handle h, double* g) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
+    if (!g) return fail(h, HDG_EINVAL, "g is NULL");
+    CKH(cudaMemcpyAsync(g, h->d_g, sizeof(double) * h->F * h->BS, cudaMemcpyDeviceToDevice, h->stream));
+    return HDG_OK;
+}
+
+int hdg_recover_interior(hdg_handle h, const double* dUH, double* dQ, double* dU) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no linearization to recover from");
+    if (!dUH || !dQ || !dU) return fail(h, HDG_EINVAL, "NULL argument");
+    DISPATCH(run_recover, h, dUH, dQ, dU);
+}
+
+int hdg_get_blocks(hdg_handle h, double* vals) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
+    if (!vals) return fail(h, HDG_EINVAL, "vals is NULL");
+    CKH(cudaMemcpyAsync(vals, h->d_vals, sizeof(double) * h->nnzb * h->BS * h->BS, cudaMemcpyDeviceToDevice, h->stream));
+    return HDG_OK;
+}
+
+int hdg_status(hdg_handle h) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
+    int32_t st = 0;
+    CKH(cudaMemcpyAsync(&st, h->d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, h->stream));
+    CKH(cudaStreamSynchronize(h->stream));
+    if (st & 2) return fail(h, HDG_ENONFINITE, "non-finite pivot in an element interior block");
+    if (st & 1) return fail(h, HDG_ESINGULAR, "zero pivot in an element interior block");
+    return HDG_OK;
+}
+
+int hdg_profile(hdg_handle h, int enable) {
+    if (!h) return HDG_EINVAL;
+    h->prof = enable != 0;
+    return HDG_OK;
+}
+
+int hdg_profile_read(hdg_handle h, double* ms, int64_t* launches) {
+    if (!h) return HDG_EINVAL;
+    if (h->device && h->ev_used) {
+        CKH(cudaStreamSynchronize(h->stream));
+        for (size_t i = 0; i < h->ev_kind.size(); ++i) {
+            float t = 0.f;
+            CKH(cudaEventElapsedTime(&t, h->ev_pool[2 * i], h->ev_pool[2 * i + 1]));
+            h->ms_acc[h->ev_kind[i]] += t;
+        }
+    }
+    for (int k = 0; k < HDG_NK; ++k) {
+        if (ms) ms[k] = h->ms_acc[k];
+        if (launches) launches[k] = h->launches[k];
+        h->ms_acc[k] = 0.0;
+        h->launches[k] = 0;
+    }
+    h->ev_kind.clear();
+    h->ev_used = 0;
+    return HDG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,142 @@
+// Internal declarations of libhdg: the handle, reference-element tables,
+// skeleton connectivity and the per-configuration kernel launchers.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/hdg.h"
+
+namespace hdg {
+
+constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// Compile-time sizes of one (dimension, degree) configuration.
+template <int D_, int P_>
+struct Cfg {
+    static constexpr int D = D_, P = P_;
+    static constexpr int M = D + 2;
+    static constexpr int N1 = P + 1, Q1 = P + 2;
+    static constexpr int NP = ipow(N1, D), NQ = ipow(Q1, D);
+    static constexpr int NF = 2 * D;
+    static constexpr int NFP = ipow(N1, D - 1), NFQ = ipow(Q1, D - 1);
+    static constexpr int NU = M * NP;            // interior u unknowns
+    static constexpr int NQV = D * M * NP;       // interior q unknowns
+    static constexpr int NT = NF * M * NFP;      // element trace unknowns
+    static constexpr int NR = NU + NT;           // rows of the bordered matrix
+    static constexpr int NC = NU + NT + 1;       // columns (+ right-hand side)
+    static constexpr int LD = (NC + 3) & ~3;     // padded row stride
+    static constexpr int BS = M * NFP;           // BSR block size
+    static constexpr int NCOEF = 1 + D + NF;     // coefficients per (a, b, r, point)
+};
+
+// Reference-element tables of one configuration (host, FP64).
+struct RefTables {
+    int d = 0, p = 0, Np = 0, Nq = 0, nf = 0, Nfp = 0, Nfq = 0;
+    std::vector<double> nodes1, gq1, gw1;           // 1-D GLL nodes, Gauss points / weights
+    std::vector<double> phi, dphi, wq;              // [Nq][Np], [d][Nq][Np], [Nq]
+    std::vector<double> mu, wf;                     // [Nfq][Nfp], [Nfq]
+    std::vector<int32_t> fnode;                     // [nf][Nfp]
+    std::vector<int32_t> node_face;                 // [Np][d]: f*Nfp + l, or -1
+    std::vector<double> mhat, mf;                   // [Np][Np], [Nfp][Nfp]
+    std::vector<double> minv_c, minv_e;             // [d][Np][Np], [nf][Np][Nfp]
+    std::vector<double> psi, theta;                 // [d][Nq][Np], [nf][Nq][Nfp]
+    std::vector<double> psi_f, theta_f;             // [nf][d][Nfq][Np], [nf][nf][Nfq][Nfp]
+};
+void build_ref_tables(int d, int p, RefTables& t);
+
+// Skeleton connectivity (host).
+struct Skeleton {
+    int64_t n_faces = 0;
+    std::vector<int32_t> f2e, f2lf;                 // [F][2]
+    std::vector<int32_t> e2f;                       // [E][nf]
+    std::vector<int32_t> perm, iperm;               // [E][nf][Nfp] local->canonical, inverse
+    std::vector<int32_t> rowptr, col;               // BSR pattern
+    std::vector<int32_t> blk, rank;                 // [E][nf][nf]: BSR block, contribution rank
+    std::vector<int32_t> frank;                     // [E][nf]: rank of the element on the face
+};
+int build_skeleton(const hdg_mesh& mesh, int p, Skeleton& s, std::string& err);
+
+// Physical and numerical parameters seen by the kernels.
+struct Phys {
+    double gamma, re, pr, mach, tau;
+    int visc_law;
+    double c1, s;
+};
+
+struct DeviceTables {
+    double* phi;  double* dphi; double* wq;
+    double* mu;   double* wf;
+    int32_t* fnode; int32_t* node_face;
+    double* mhat; double* mf;
+    double* minv_c; double* minv_e;
+    double* psi; double* theta; double* psi_f; double* theta_f;
+};
+
+}  // namespace hdg
+
+struct hdg_ctx {
+    int d = 0, p = 0;
+    int m = 0, Np = 0, Nq = 0, nf = 0, Nfp = 0, Nfq = 0;
+    int NU = 0, NQV = 0, NT = 0, NR = 0, NC = 0, LD = 0, BS = 0, NCOEF = 0;
+    int64_t E = 0, F = 0, nnzb = 0;
+    bool device = false;
+    hdg::Phys phys{};
+    int precision = HDG_PREC_FP64;
+    cudaStream_t stream = nullptr;
+    std::string err;
+
+    hdg::RefTables ref;
+    hdg::Skeleton sk;
+    std::vector<double> detJ, Jinv, NW;    // [E], [E][d][d], [E][nf][d]
+
+    // device memory
+    std::vector<void*> allocs;
+    int64_t device_bytes = 0;
+    hdg::DeviceTables tab{};
+    double* d_geo = nullptr;               // [E][1 + d*d + nf*d]
+    int32_t* d_e2f = nullptr;
+    int32_t* d_perm = nullptr;
+    int32_t* d_iperm = nullptr;
+    int32_t* d_rowptr = nullptr;
+    int32_t* d_col = nullptr;
+    int32_t* d_blk = nullptr;
+    int32_t* d_rank = nullptr;
+    int32_t* d_frank = nullptr;
+    double* d_vals = nullptr;              // [nnzb][BS][BS]
+    double* d_g = nullptr;                 // [F][m][Nfp]
+    double* d_top = nullptr;               // [E][NU][LD] bordered matrix, interior rows
+    double* d_bot = nullptr;               // [chunk][NT][LD] bordered matrix, trace rows
+    double* d_vcoef = nullptr;             // [chunk][m][m][d][NCOEF][Nq]
+    double* d_fcoef = nullptr;             // [chunk][nf][m][m][NCOEF][Nfq]
+    double* d_dq0 = nullptr;               // [E][d][m][Np]
+    int32_t* d_status = nullptr;           // [1]
+    int64_t chunk = 0;
+    bool have_system = false;
+
+    // instrumentation: event pairs around kernel launches
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_kind;        // kernel class of each recorded pair
+    size_t ev_used = 0;              // events in use (2 per pair)
+    int64_t launches[HDG_NK] = {};
+    double ms_acc[HDG_NK] = {};
+};
+
+namespace hdg {
+// Records a CUDA event on the handle's stream before (begin) / after (end) a
+// launch of kernel class `kind` when profiling is on; counts launches always.
+void prof_begin(hdg_ctx* h, int kind);
+void prof_end(hdg_ctx* h);
+// Launchers, one instantiation per (d, p), defined in kern_*.cu.
+struct LinArgs {
+    const double* U; const double* Q; const double* UH; const double* Ustar; const double* nu;
+    double dt, a_ii;
+};
+template <int D, int P> int run_linearize(hdg_ctx* h, const LinArgs& a);
+template <int D, int P> int run_matvec(hdg_ctx* h, const double* x, double* y);
+template <int D, int P> int run_recover(hdg_ctx* h, const double* dUH, double* dQ, double* dU);
+}  // namespace hdg

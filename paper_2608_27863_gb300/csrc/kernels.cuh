@@ -1,0 +1,872 @@
+// FP64 kernels of the HDG linearize + condense path, templated on (d, p).
+//
+// Per element K the path forms the bordered matrix
+//
+//     [ At  Bt  Rt ]     At = A_uu - A_uq A_qq^{-1} A_qu      (n_u x n_u)
+//     [ Ct  Dt  Rh ]     Bt = B_u  - A_uq A_qq^{-1} B_q       (n_u x t)
+//                        Ct = C_u  - C_q  A_qq^{-1} A_qu      (t x n_u)
+//                        Dt = D    - C_q  A_qq^{-1} B_q       (t x t)
+//
+// i.e. the element system of eq. newton-local-block with the gradient block
+// eliminated exactly (A_qq = I (x) M_K is the mass matrix and R_q is linear,
+// eq. hdg-grad), and eliminates its first n_u columns by Gaussian elimination
+// with partial pivoting restricted to the first n_u rows.  The trailing block
+// is then S^K = Dt - Ct At^{-1} Bt = D - C A^{-1} B and the last column
+// -g^K (eq. schur-trace); the first n_u rows keep [U | L^{-1} P Bt | L^{-1} P Rt]
+// for the recovery of eq. local-elimination.
+//
+// The right-hand-side column uses the fluxes at the lifted gradient
+// Q_lift(U, Uhat) = Q - A_qq^{-1} R_q: R_u and R_uhat are affine in Q, so
+// R_u(Q_lift) = R_u - A_uq A_qq^{-1} R_q exactly.
+#pragma once
+
+#include <climits>
+
+#include "common.h"
+#include "physics.cuh"
+
+namespace hdg {
+
+// per-element geometry record: detJ, Jinv[d][d] (d xi_r / d x_k), NW[nf][d]
+template <int D> struct Geo { static constexpr int N = 1 + D * D + 2 * D * D; };
+
+// ----------------------------------------------------------------------------
+// A0 + A1: gather, interpolation, fluxes and their Jacobians at quadrature points
+// ----------------------------------------------------------------------------
+struct PointArgs {
+    const double* U; const double* Q; const double* UH; const double* Ustar; const double* nu;
+    double dt, a_ii;
+    Phys ph;
+    DeviceTables tab;
+    const double* geo;
+    const int32_t* e2f; const int32_t* perm;
+    double* top; double* bot; double* vcoef; double* fcoef; double* dq0;
+    int64_t e0;
+};
+
+template <class C>
+constexpr int point_smem_doubles() {
+    return C::NU + 2 * C::NQV + C::NP + 2 * C::NT + C::D * C::M * C::NQ + C::NF * C::M * C::NFQ;
+}
+
+template <class C, int NTH>
+__global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
+    constexpr int D = C::D, M = C::M, NP = C::NP, NQ = C::NQ, NF = C::NF, NFP = C::NFP, NFQ = C::NFQ;
+    constexpr int NU = C::NU, NQV = C::NQV, NT = C::NT, LD = C::LD, NC = C::NC, NCOEF = C::NCOEF;
+    constexpr int GEO = Geo<D>::N;
+    const int tid = threadIdx.x;
+    const int64_t el = blockIdx.x, e = A.e0 + el;
+    extern __shared__ double sm[];
+    double* sU = sm;                     // [m][Np]
+    double* sQ = sU + NU;                // [d][m][Np]
+    double* sQL = sQ + NQV;              // lifted gradient [d][m][Np]
+    double* sNu = sQL + NQV;             // [Np]
+    double* sUH = sNu + NP;              // [nf][m][Nfp] element-local face order
+    double* sFres = sUH + NT;            // [d][m][Nq]
+    double* sFH = sFres + D * M * NQ;    // [nf][m][Nfq]
+    double* sRh = sFH + NF * M * NFQ;    // [nf][m][Nfp]
+    __shared__ double geo[GEO];
+    const DeviceTables& T = A.tab;
+
+    for (int i = tid; i < NU; i += NTH) sU[i] = A.U[e * NU + i];
+    for (int i = tid; i < NQV; i += NTH) sQ[i] = A.Q[e * NQV + i];
+    for (int i = tid; i < NP; i += NTH) sNu[i] = A.nu ? A.nu[e * NP + i] : 0.0;
+    for (int i = tid; i < NT; i += NTH) {
+        int f = i / (M * NFP), rem = i - f * M * NFP, a = rem / NFP, l = rem - a * NFP;
+        int64_t F = A.e2f[e * NF + f];
+        int k = A.perm[(e * NF + f) * NFP + l];
+        sUH[i] = A.UH[(F * M + a) * NFP + k];
+    }
+    for (int i = tid; i < GEO; i += NTH) geo[i] = A.geo[e * GEO + i];
+    __syncthreads();
+    const double detJ = geo[0];
+    const double* Jinv = geo + 1;
+    const double* NW = geo + 1 + D * D;
+
+    // lifted gradient at the nodes: Q_lift = -L U + Lambda Uhat (A_qq^{-1} applied)
+    for (int idx = tid; idx < M * NP; idx += NTH) {
+        int a = idx / NP, i = idx - a * NP;
+        double t[D], ef[NF];
+        for (int r = 0; r < D; ++r) {
+            double s = 0.0;
+            const double* mc = T.minv_c + ((size_t)r * NP + i) * NP;
+            for (int j = 0; j < NP; ++j) s += mc[j] * sU[a * NP + j];
+            t[r] = s;
+        }
+        for (int f = 0; f < NF; ++f) {
+            double s = 0.0;
+            const double* me = T.minv_e + ((size_t)f * NP + i) * NFP;
+            for (int l = 0; l < NFP; ++l) s += me[l] * sUH[(f * M + a) * NFP + l];
+            ef[f] = s;
+        }
+        for (int l = 0; l < D; ++l) {
+            double ql = 0.0;
+            for (int r = 0; r < D; ++r) ql -= Jinv[r * D + l] * t[r];
+            for (int f = 0; f < NF; ++f) ql += NW[f * D + l] / detJ * ef[f];
+            int o = (l * M + a) * NP + i;
+            sQL[o] = ql;
+            A.dq0[e * NQV + o] = ql - sQ[o];
+        }
+    }
+    __syncthreads();
+
+    const Phys ph = A.ph;
+    double* vc = A.vcoef + el * (size_t)(M * M * D * NCOEF * NQ);
+    // volume points
+    for (int g = tid; g < NQ; g += NTH) {
+        double u[M], q[M][D], ql[M][D], nuv = 0.0;
+        for (int a = 0; a < M; ++a) { u[a] = 0.0; for (int l = 0; l < D; ++l) { q[a][l] = 0.0; ql[a][l] = 0.0; } }
+        for (int j = 0; j < NP; ++j) {
+            double w = T.phi[g * NP + j];
+            nuv += w * sNu[j];
+            for (int a = 0; a < M; ++a) {
+                u[a] += w * sU[a * NP + j];
+                for (int l = 0; l < D; ++l) {
+                    q[a][l] += w * sQ[(l * M + a) * NP + j];
+                    ql[a][l] += w * sQL[(l * M + a) * NP + j];
+                }
+            }
+        }
+        const double wJ = -A.dt * T.wq[g] * detJ;
+        {
+            double Fc[M][D], Fv[M][D];
+            conv_flux<D, double>(u, ph, Fc);
+            visc_flux<D, double>(u, ql, nuv, ph, Fv);
+            for (int r = 0; r < D; ++r)
+                for (int a = 0; a < M; ++a) {
+                    double s = 0.0;
+                    for (int k = 0; k < D; ++k) s += Jinv[r * D + k] * (Fc[a][k] - Fv[a][k]);
+                    sFres[(r * M + a) * NQ + g] = wJ * s;
+                }
+        }
+        for (int b = 0; b < M; ++b) {
+            Dir ud[M];
+            for (int a = 0; a < M; ++a) ud[a] = {u[a], a == b ? 1.0 : 0.0};
+            Dir Fc[M][D], Fv[M][D];
+            conv_flux<D, Dir>(ud, ph, Fc);
+            visc_flux<D, Dir>(ud, q, nuv, ph, Fv);
+            for (int a = 0; a < M; ++a)
+                for (int r = 0; r < D; ++r) {
+                    double s = 0.0;
+                    for (int k = 0; k < D; ++k) s += Jinv[r * D + k] * (Fc[a][k].t - Fv[a][k].t);
+                    vc[((((size_t)a * M + b) * D + r) * NCOEF + 0) * NQ + g] = wJ * s;
+                }
+        }
+        for (int b = 0; b < M; ++b) {
+            double cq[D][M][D];
+            for (int l = 0; l < D; ++l) {
+                double qe[M][D];
+                for (int a = 0; a < M; ++a) for (int k = 0; k < D; ++k) qe[a][k] = (a == b && k == l) ? 1.0 : 0.0;
+                double Fv[M][D];
+                visc_flux<D, double>(u, qe, nuv, ph, Fv);
+                for (int r = 0; r < D; ++r)
+                    for (int a = 0; a < M; ++a) {
+                        double s = 0.0;
+                        for (int k = 0; k < D; ++k) s += Jinv[r * D + k] * Fv[a][k];
+                        cq[r][a][l] = -wJ * s;
+                    }
+            }
+            for (int a = 0; a < M; ++a)
+                for (int r = 0; r < D; ++r) {
+                    double* o = vc + ((((size_t)a * M + b) * D + r) * NCOEF) * NQ + g;
+                    for (int r2 = 0; r2 < D; ++r2) {
+                        double s = 0.0;
+                        for (int l = 0; l < D; ++l) s += cq[r][a][l] * Jinv[r2 * D + l];
+                        o[(1 + r2) * NQ] = s;
+                    }
+                    for (int f = 0; f < NF; ++f) {
+                        double s = 0.0;
+                        for (int l = 0; l < D; ++l) s += cq[r][a][l] * NW[f * D + l];
+                        o[(1 + D + f) * NQ] = s / detJ;
+                    }
+                }
+        }
+    }
+    // face points
+    double* fc = A.fcoef + el * (size_t)(NF * M * M * NCOEF * NFQ);
+    for (int fs = tid; fs < NF * NFQ; fs += NTH) {
+        const int f = fs / NFQ, s = fs - f * NFQ;
+        double u[M], uh[M], q[M][D], ql[M][D], nuv = 0.0;
+        for (int a = 0; a < M; ++a) { u[a] = 0.0; uh[a] = 0.0; for (int l = 0; l < D; ++l) { q[a][l] = 0.0; ql[a][l] = 0.0; } }
+        for (int lam = 0; lam < NFP; ++lam) {
+            double w = T.mu[s * NFP + lam];
+            int j = T.fnode[f * NFP + lam];
+            nuv += w * sNu[j];
+            for (int a = 0; a < M; ++a) {
+                u[a] += w * sU[a * NP + j];
+                uh[a] += w * sUH[(f * M + a) * NFP + lam];
+                for (int l = 0; l < D; ++l) {
+                    q[a][l] += w * sQ[(l * M + a) * NP + j];
+                    ql[a][l] += w * sQL[(l * M + a) * NP + j];
+                }
+            }
+        }
+        const double* nw = NW + f * D;
+        double nrm = 0.0;
+        for (int k = 0; k < D; ++k) nrm += nw[k] * nw[k];
+        nrm = sqrt(nrm);
+        const double ws = T.wf[s];
+        {
+            double Fc[M][D], Fv[M][D];
+            conv_flux<D, double>(uh, ph, Fc);
+            visc_flux<D, double>(uh, ql, nuv, ph, Fv);
+            for (int a = 0; a < M; ++a) {
+                double fn = 0.0;
+                for (int k = 0; k < D; ++k) fn += (Fc[a][k] - Fv[a][k]) * nw[k];
+                sFH[(f * M + a) * NFQ + s] = ws * (fn + nrm * ph.tau * (u[a] - uh[a]));
+            }
+        }
+        for (int b = 0; b < M; ++b) {
+            Dir ud[M];
+            for (int a = 0; a < M; ++a) ud[a] = {uh[a], a == b ? 1.0 : 0.0};
+            Dir Fc[M][D], Fv[M][D];
+            conv_flux<D, Dir>(ud, ph, Fc);
+            visc_flux<D, Dir>(ud, q, nuv, ph, Fv);
+            for (int a = 0; a < M; ++a) {
+                double fn = 0.0;
+                for (int k = 0; k < D; ++k) fn += (Fc[a][k].t - Fv[a][k].t) * nw[k];
+                if (a == b) fn -= nrm * ph.tau;
+                fc[((((size_t)f * M + a) * M + b) * NCOEF + 0) * NFQ + s] = ws * fn;
+            }
+        }
+        for (int b = 0; b < M; ++b) {
+            double qh[M][D];
+            for (int l = 0; l < D; ++l) {
+                double qe[M][D];
+                for (int a = 0; a < M; ++a) for (int k = 0; k < D; ++k) qe[a][k] = (a == b && k == l) ? 1.0 : 0.0;
+                double Fv[M][D];
+                visc_flux<D, double>(uh, qe, nuv, ph, Fv);
+                for (int a = 0; a < M; ++a) {
+                    double fn = 0.0;
+                    for (int k = 0; k < D; ++k) fn += Fv[a][k] * nw[k];
+                    qh[a][l] = -ws * fn;
+                }
+            }
+            for (int a = 0; a < M; ++a) {
+                double* o = fc + ((((size_t)f * M + a) * M + b) * NCOEF) * NFQ + s;
+                for (int r2 = 0; r2 < D; ++r2) {
+                    double t = 0.0;
+                    for (int l = 0; l < D; ++l) t += qh[a][l] * Jinv[r2 * D + l];
+                    o[(1 + r2) * NFQ] = t;
+                }
+                for (int f2 = 0; f2 < NF; ++f2) {
+                    double t = 0.0;
+                    for (int l = 0; l < D; ++l) t += qh[a][l] * NW[f2 * D + l];
+                    o[(1 + D + f2) * NFQ] = t / detJ;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // right-hand-side column: Rh (trace rows) then Rt (interior rows)
+    double* Bm = A.bot + el * (size_t)NT * LD;
+    for (int idx = tid; idx < NT; idx += NTH) {
+        int f = idx / (M * NFP), rem = idx - f * M * NFP, a = rem / NFP, l = rem - a * NFP;
+        double s = 0.0;
+        for (int q = 0; q < NFQ; ++q) s += T.mu[q * NFP + l] * sFH[(f * M + a) * NFQ + q];
+        sRh[idx] = s;
+        Bm[(size_t)idx * LD + NC - 1] = s;
+    }
+    __syncthreads();
+    double* Tm = A.top + e * (size_t)NU * LD;
+    for (int idx = tid; idx < NU; idx += NTH) {
+        int a = idx / NP, i = idx - a * NP;
+        double mass = 0.0;
+        for (int j = 0; j < NP; ++j) mass += T.mhat[i * NP + j] * (sU[a * NP + j] - A.Ustar[e * NU + a * NP + j]);
+        double s = mass * detJ / A.a_ii;
+        for (int r = 0; r < D; ++r)
+            for (int g = 0; g < NQ; ++g) s += T.dphi[((size_t)r * NQ + g) * NP + i] * sFres[(r * M + a) * NQ + g];
+        for (int k = 0; k < D; ++k) {
+            int nfc = T.node_face[i * D + k];
+            if (nfc < 0) continue;
+            int f = nfc / NFP, l = nfc - f * NFP;
+            s += A.dt * sRh[(f * M + a) * NFP + l];
+        }
+        Tm[(size_t)idx * LD + NC - 1] = s;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// A2: contraction of the coefficients with the basis tables into the blocks
+// ----------------------------------------------------------------------------
+struct BlkArgs {
+    const double* vcoef; const double* fcoef; const double* geo;
+    DeviceTables tab;
+    double* top; double* bot;
+    double dt, a_ii, tau;
+    int64_t e0;
+};
+
+template <class C, int TY, int TX, int KC>
+struct BlkShape {
+    static constexpr int NCB = C::NP + C::NF * C::NFP;
+    static constexpr int TM = (C::NP + TY - 1) / TY, TN = (NCB + TX - 1) / TX;
+    static constexpr int NPP = TM * TY, NCBP = TN * TX;
+    static constexpr int main_smem = KC * (NPP + NCBP + C::NCOEF);
+    static constexpr int face_smem = C::NCOEF * C::NFQ + C::NFQ * NCB;
+    static constexpr int smem = main_smem > face_smem ? main_smem : face_smem;
+};
+
+template <class C, int TY, int TX, int KC>
+__global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs A) {
+    constexpr int D = C::D, M = C::M, NP = C::NP, NQ = C::NQ, NF = C::NF, NFP = C::NFP, NFQ = C::NFQ;
+    constexpr int NU = C::NU, NT = C::NT, LD = C::LD, NCOEF = C::NCOEF;
+    using S = BlkShape<C, TY, TX, KC>;
+    constexpr int NCB = S::NCB, TM = S::TM, TN = S::TN, NPP = S::NPP, NCBP = S::NCBP;
+    constexpr int K = D * NQ, NTH = TY * TX;
+    constexpr int GEO = Geo<D>::N;
+    const int tid = threadIdx.x, ty = tid / TX, tx = tid - ty * TX;
+    const int64_t bid = blockIdx.x;
+    const int b = (int)(bid % M), a = (int)((bid / M) % M);
+    const int64_t el = bid / (M * M), e = A.e0 + el;
+    const DeviceTables& T = A.tab;
+    extern __shared__ double sm[];
+    double* As = sm;
+    double* Bs = As + KC * NPP;
+    double* Cs = Bs + KC * NCBP;
+    const double* cf = A.vcoef + (((size_t)el * M + a) * M + b) * (size_t)(D * NCOEF * NQ);
+
+    double acc[TM][TN];
+#pragma unroll
+    for (int ii = 0; ii < TM; ++ii)
+#pragma unroll
+        for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = 0.0;
+
+    for (int k0 = 0; k0 < K; k0 += KC) {
+        const int kc = min(KC, K - k0);
+        for (int idx = tid; idx < kc * NCOEF; idx += NTH) {
+            int kk = idx / NCOEF, c = idx - kk * NCOEF, k = k0 + kk, r = k / NQ, g = k - r * NQ;
+            Cs[idx] = cf[(r * NCOEF + c) * NQ + g];
+        }
+        for (int idx = tid; idx < KC * NPP; idx += NTH) {
+            int kk = idx / NPP, i = idx - kk * NPP;
+            As[idx] = (kk < kc && i < NP) ? T.dphi[(size_t)(k0 + kk) * NP + i] : 0.0;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < KC * NCBP; idx += NTH) {
+            int kk = idx / NCBP, c = idx - kk * NCBP;
+            double v = 0.0;
+            if (kk < kc && c < NCB) {
+                int k = k0 + kk, r = k / NQ, g = k - r * NQ;
+                const double* cc = Cs + kk * NCOEF;
+                if (c < NP) {
+                    v = cc[0] * T.phi[g * NP + c];
+                    for (int r2 = 0; r2 < D; ++r2) v -= cc[1 + r2] * T.psi[((size_t)r2 * NQ + g) * NP + c];
+                } else {
+                    int c2 = c - NP, f = c2 / NFP, l = c2 - f * NFP;
+                    v = cc[1 + D + f] * T.theta[((size_t)f * NQ + g) * NFP + l];
+                }
+            }
+            Bs[idx] = v;
+        }
+        __syncthreads();
+        for (int kk = 0; kk < kc; ++kk) {
+            double av[TM], bv[TN];
+#pragma unroll
+            for (int ii = 0; ii < TM; ++ii) av[ii] = As[kk * NPP + ty + TY * ii];
+#pragma unroll
+            for (int jj = 0; jj < TN; ++jj) bv[jj] = Bs[kk * NCBP + tx + TX * jj];
+#pragma unroll
+            for (int ii = 0; ii < TM; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = fma(av[ii], bv[jj], acc[ii][jj]);
+        }
+        __syncthreads();
+    }
+
+    const double* G = A.geo + e * GEO;
+    const double detJ = G[0];
+    double* Tm = A.top + e * (size_t)NU * LD;
+#pragma unroll
+    for (int ii = 0; ii < TM; ++ii) {
+        int i = ty + TY * ii;
+        if (i >= NP) continue;
+#pragma unroll
+        for (int jj = 0; jj < TN; ++jj) {
+            int c = tx + TX * jj;
+            if (c >= NCB) continue;
+            int col;
+            double v = acc[ii][jj];
+            if (c < NP) {
+                col = b * NP + c;
+                if (a == b) v += detJ / A.a_ii * T.mhat[i * NP + c];
+            } else {
+                int c2 = c - NP, f = c2 / NFP, l = c2 - f * NFP;
+                col = NU + (f * M + b) * NFP + l;
+            }
+            Tm[(size_t)(a * NP + i) * LD + col] = v;
+        }
+    }
+    __syncthreads();
+
+    // face terms: rows of Ct / Dt, and dt x the same rows added to At / Bt at the face nodes
+    double* Bm = A.bot + el * (size_t)NT * LD;
+    double* Fc = sm;                       // [NCOEF][Nfq]
+    double* Tt = Fc + NCOEF * NFQ;         // [Nfq][NCB]
+    const double* NW = G + 1 + D * D;
+    const double* Jg = G + 1;
+    (void)Jg;
+    for (int f = 0; f < NF; ++f) {
+        const double* fsrc = A.fcoef + ((((size_t)el * NF + f) * M + a) * M + b) * (size_t)(NCOEF * NFQ);
+        for (int idx = tid; idx < NCOEF * NFQ; idx += NTH) Fc[idx] = fsrc[idx];
+        __syncthreads();
+        for (int idx = tid; idx < NFQ * NCB; idx += NTH) {
+            int s = idx / NCB, c = idx - s * NCB;
+            double v = 0.0;
+            if (c < NP) {
+                for (int r2 = 0; r2 < D; ++r2)
+                    v -= Fc[(1 + r2) * NFQ + s] * T.psi_f[(((size_t)f * D + r2) * NFQ + s) * NP + c];
+            } else {
+                int c2 = c - NP, f2 = c2 / NFP, l2 = c2 - f2 * NFP;
+                v = Fc[(1 + D + f2) * NFQ + s] * T.theta_f[(((size_t)f * NF + f2) * NFQ + s) * NFP + l2];
+                if (f2 == f) v += Fc[s] * T.mu[s * NFP + l2];
+            }
+            Tt[idx] = v;
+        }
+        __syncthreads();
+        double nrm = 0.0;
+        for (int k = 0; k < D; ++k) nrm += NW[f * D + k] * NW[f * D + k];
+        nrm = sqrt(nrm);
+        for (int idx = tid; idx < NFP * NCB; idx += NTH) {
+            int lam = idx / NCB, c = idx - lam * NCB;
+            double v = 0.0;
+            for (int s = 0; s < NFQ; ++s) v += T.mu[s * NFP + lam] * Tt[s * NCB + c];
+            int col;
+            if (c < NP) {
+                col = b * NP + c;
+                if (a == b) {
+                    for (int k = 0; k < D; ++k) {
+                        int nfc = T.node_face[c * D + k];
+                        if (nfc >= 0 && nfc / NFP == f) v += A.tau * nrm * T.mf[lam * NFP + (nfc - f * NFP)];
+                    }
+                }
+            } else {
+                int c2 = c - NP, f2 = c2 / NFP, l2 = c2 - f2 * NFP;
+                col = NU + (f2 * M + b) * NFP + l2;
+            }
+            Bm[(size_t)((f * M + a) * NFP + lam) * LD + col] = v;
+            double* t = Tm + (size_t)(a * NP + T.fnode[f * NFP + lam]) * LD + col;
+            *t += A.dt * v;
+        }
+        __syncthreads();
+    }
+}
+
+// ----------------------------------------------------------------------------
+// A3 + A4: bordered Gaussian elimination (interior LU, solves and Schur complement)
+// ----------------------------------------------------------------------------
+template <class C, int NB>
+constexpr int elim_smem_doubles() { return C::NR * NB + NB * 64; }
+
+template <class C, int NB, int NTH>
+__global__ void __launch_bounds__(NTH) k_elim(double* top, double* bot, int64_t e0, int32_t* status) {
+    constexpr int NU = C::NU, NR = C::NR, NC = C::NC, LD = C::LD;
+    constexpr int TCW = 64;                 // column tile of the trailing update
+    static_assert(NTH == 256, "trailing-update layout assumes 256 threads");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t el = blockIdx.x, e = e0 + el;
+    double* Tm = top + e * (size_t)NU * LD;
+    double* Bm = bot + el * (size_t)(NR - NU) * LD;
+    auto rowp = [&](int r) -> double* { return r < NU ? Tm + (size_t)r * LD : Bm + (size_t)(r - NU) * LD; };
+    extern __shared__ double sm[];
+    double* pan = sm;                       // [NR][NB], row index relative to k0
+    double* ust = pan + NR * NB;            // [NB][TCW]
+    __shared__ int piv[NB];
+    __shared__ double rv[NTH / 32];
+    __shared__ int ri[NTH / 32];
+    __shared__ int sflag;
+    if (tid == 0) sflag = 0;
+
+    for (int k0 = 0; k0 < NU; k0 += NB) {
+        const int kb = min(NB, NU - k0), nrows = NR - k0, ntop = NU - k0;
+        for (int idx = tid; idx < nrows * kb; idx += NTH) {
+            int rr = idx / kb, c = idx - rr * kb;
+            pan[rr * NB + c] = rowp(k0 + rr)[k0 + c];
+        }
+        __syncthreads();
+        for (int j = 0; j < kb; ++j) {
+            double bv = -1.0;
+            int bi = INT_MAX;
+            for (int rr = j + tid; rr < ntop; rr += NTH) {
+                double v = fabs(pan[rr * NB + j]);
+                if (v > bv) { bv = v; bi = rr; }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                double ov = __shfl_down_sync(0xffffffffu, bv, off);
+                int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            }
+            if (lane == 0) { rv[warp] = bv; ri[warp] = bi; }
+            __syncthreads();
+            if (tid == 0) {
+                double b2 = rv[0];
+                int i2 = ri[0];
+                for (int w = 1; w < NTH / 32; ++w)
+                    if (rv[w] > b2 || (rv[w] == b2 && ri[w] < i2)) { b2 = rv[w]; i2 = ri[w]; }
+                if (i2 == INT_MAX) { i2 = j; sflag |= 2; }
+                piv[j] = i2;
+            }
+            __syncthreads();
+            const int pr = piv[j];
+            if (pr != j)
+                for (int c = tid; c < kb; c += NTH) {
+                    double t = pan[j * NB + c];
+                    pan[j * NB + c] = pan[pr * NB + c];
+                    pan[pr * NB + c] = t;
+                }
+            __syncthreads();
+            double pv = pan[j * NB + j];
+            if (pv == 0.0 || !isfinite(pv)) {
+                if (tid == 0) sflag |= (pv == 0.0) ? 1 : 2;
+                pv = 1.0;
+            }
+            const double inv = 1.0 / pv;
+            for (int rr = j + 1 + tid; rr < nrows; rr += NTH) {
+                double l = pan[rr * NB + j] * inv;
+                pan[rr * NB + j] = l;
+                for (int c = j + 1; c < kb; ++c) pan[rr * NB + c] = fma(-l, pan[j * NB + c], pan[rr * NB + c]);
+            }
+            __syncthreads();
+        }
+        for (int idx = tid; idx < nrows * kb; idx += NTH) {
+            int rr = idx / kb, c = idx - rr * kb;
+            rowp(k0 + rr)[k0 + c] = pan[rr * NB + c];
+        }
+        // trailing columns: row swaps and U12 = L11^{-1} A12 (each thread owns columns)
+        const int c0 = k0 + kb;
+        for (int c = c0 + tid; c < NC; c += NTH) {
+            for (int j = 0; j < kb; ++j) {
+                int pr = piv[j];
+                if (pr != j) {
+                    double* x = rowp(k0 + j) + c;
+                    double* y = rowp(k0 + pr) + c;
+                    double t = *x; *x = *y; *y = t;
+                }
+            }
+            double xv[NB];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                if (j < kb) {
+                    double s = rowp(k0 + j)[c];
+#pragma unroll
+                    for (int i = 0; i < NB; ++i)
+                        if (i < j) s = fma(-pan[j * NB + i], xv[i], s);
+                    xv[j] = s;
+                    rowp(k0 + j)[c] = s;
+                }
+            }
+        }
+        __syncthreads();
+        // trailing update A22 -= L21 U12 on rows [c0, NR) x cols [c0, NC)
+        const int tx = tid & 15, ty = tid >> 4;
+        for (int ct = c0; ct < NC; ct += TCW) {
+            for (int idx = tid; idx < kb * TCW; idx += NTH) {
+                int j = idx / TCW, cc = idx - j * TCW;
+                ust[j * TCW + cc] = (ct + cc < NC) ? rowp(k0 + j)[ct + cc] : 0.0;
+            }
+            __syncthreads();
+            for (int rb = c0; rb < NR; rb += 64) {
+                double acc[4][4];
+                double* rp[4];
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii) {
+                    int r = rb + ty + 16 * ii;
+                    rp[ii] = (r < NR) ? rowp(r) : nullptr;
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        int c = ct + tx + 16 * jj;
+                        acc[ii][jj] = (rp[ii] && c < NC) ? rp[ii][c] : 0.0;
+                    }
+                }
+                for (int j = 0; j < kb; ++j) {
+                    double lv[4], uv[4];
+#pragma unroll
+                    for (int ii = 0; ii < 4; ++ii) {
+                        int r = rb + ty + 16 * ii;
+                        lv[ii] = (r < NR) ? pan[(r - k0) * NB + j] : 0.0;
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) uv[jj] = ust[j * TCW + tx + 16 * jj];
+#pragma unroll
+                    for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fma(-lv[ii], uv[jj], acc[ii][jj]);
+                }
+#pragma unroll
+                for (int ii = 0; ii < 4; ++ii) {
+                    if (!rp[ii]) continue;
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) {
+                        int c = ct + tx + 16 * jj;
+                        if (c < NC) rp[ii][c] = acc[ii][jj];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    if (tid == 0 && sflag) atomicOr(status, sflag);
+}
+
+// ----------------------------------------------------------------------------
+// A5: deterministic assembly of S^K and g^K into the block-sparse trace system
+// ----------------------------------------------------------------------------
+template <class C>
+__global__ void k_assemble(const double* bot, int64_t e0, const int32_t* blk, const int32_t* rank,
+                           const int32_t* iperm, double* vals, int pass) {
+    constexpr int M = C::M, NF = C::NF, NFP = C::NFP, NU = C::NU, NT = C::NT, LD = C::LD, BS = C::BS;
+    const int64_t bid = blockIdx.x;
+    const int gl = (int)(bid % NF), fl = (int)((bid / NF) % NF);
+    const int64_t el = bid / (NF * NF), e = e0 + el;
+    const size_t item = ((size_t)e * NF + fl) * NF + gl;
+    if (rank[item] != pass) return;
+    double* out = vals + (size_t)blk[item] * BS * BS;
+    const double* Bm = bot + el * (size_t)NT * LD;
+    const int32_t* ipf = iperm + ((size_t)e * NF + fl) * NFP;
+    const int32_t* ipg = iperm + ((size_t)e * NF + gl) * NFP;
+    for (int idx = threadIdx.x; idx < BS * BS; idx += blockDim.x) {
+        int c = idx / BS, r = idx - c * BS;
+        int a = r / NFP, k = r - a * NFP, b2 = c / NFP, k2 = c - b2 * NFP;
+        int row = (fl * M + a) * NFP + ipf[k];
+        int col = NU + (gl * M + b2) * NFP + ipg[k2];
+        out[idx] += Bm[(size_t)row * LD + col];
+    }
+}
+
+template <class C>
+__global__ void k_assemble_g(const double* bot, int64_t e0, const int32_t* e2f, const int32_t* frank,
+                             const int32_t* iperm, double* g, int pass) {
+    constexpr int M = C::M, NF = C::NF, NFP = C::NFP, NT = C::NT, LD = C::LD, NC = C::NC, BS = C::BS;
+    const int64_t bid = blockIdx.x;
+    const int fl = (int)(bid % NF);
+    const int64_t el = bid / NF, e = e0 + el;
+    if (frank[e * NF + fl] != pass) return;
+    const int64_t F = e2f[e * NF + fl];
+    const double* Bm = bot + el * (size_t)NT * LD;
+    const int32_t* ipf = iperm + ((size_t)e * NF + fl) * NFP;
+    for (int idx = threadIdx.x; idx < BS; idx += blockDim.x) {
+        int a = idx / NFP, k = idx - a * NFP;
+        int row = (fl * M + a) * NFP + ipf[k];
+        g[F * BS + idx] -= Bm[(size_t)row * LD + NC - 1];
+    }
+}
+
+// ----------------------------------------------------------------------------
+// A6: trace matvec y = S x (block rows, column-major blocks)
+// ----------------------------------------------------------------------------
+template <class C>
+struct MvShape {
+    static constexpr int RB = ((C::BS + 31) / 32) * 32;
+    static constexpr int GROUPS = (RB <= 64) ? 4 : 2;
+    static constexpr int NTH = RB * GROUPS;
+};
+
+template <class C>
+__global__ void __launch_bounds__(MvShape<C>::NTH) k_matvec(const int32_t* rowptr, const int32_t* col,
+                                                            const double* vals, const double* x, double* y) {
+    constexpr int BS = C::BS, RB = MvShape<C>::RB, GROUPS = MvShape<C>::GROUPS;
+    __shared__ double part[GROUPS][RB];
+    const int64_t F = blockIdx.x;
+    const int grp = threadIdx.x / RB, r = threadIdx.x - grp * RB;
+    double acc0 = 0.0, acc1 = 0.0;
+    if (r < BS) {
+        for (int b = rowptr[F] + grp; b < rowptr[F + 1]; b += GROUPS) {
+            const double* xs = x + (size_t)col[b] * BS;
+            const double* v = vals + (size_t)b * BS * BS + r;
+            int c = 0;
+#pragma unroll 4
+            for (; c + 1 < BS; c += 2) {
+                acc0 = fma(v[(size_t)c * BS], xs[c], acc0);
+                acc1 = fma(v[(size_t)(c + 1) * BS], xs[c + 1], acc1);
+            }
+            if (c < BS) acc0 = fma(v[(size_t)c * BS], xs[c], acc0);
+        }
+    }
+    part[grp][r] = acc0 + acc1;
+    __syncthreads();
+    if (grp == 0 && r < BS) {
+        double s = part[0][r];
+        for (int g2 = 1; g2 < GROUPS; ++g2) s += part[g2][r];
+        y[F * BS + r] = s;
+    }
+}
+
+// ----------------------------------------------------------------------------
+// A7: interior recovery dU = -U^{-1}(z + Z dUhat_K), dQ = dq0 - L dU + Lambda dUhat_K
+// ----------------------------------------------------------------------------
+struct RecArgs {
+    const double* top; const double* dq0; const double* geo;
+    DeviceTables tab;
+    const int32_t* e2f; const int32_t* perm;
+    const double* dUH; double* dQ; double* dU;
+};
+
+template <class C, int NTH>
+__global__ void __launch_bounds__(NTH) k_recover(RecArgs A) {
+    constexpr int D = C::D, M = C::M, NP = C::NP, NF = C::NF, NFP = C::NFP;
+    constexpr int NU = C::NU, NQV = C::NQV, NT = C::NT, LD = C::LD, NC = C::NC;
+    constexpr int GEO = Geo<D>::N;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t e = blockIdx.x;
+    __shared__ double duh[NT];
+    __shared__ double w[NU];
+    __shared__ double x[NU];
+    __shared__ double geo[GEO];
+    for (int i = tid; i < NT; i += NTH) {
+        int f = i / (M * NFP), rem = i - f * M * NFP, a = rem / NFP, l = rem - a * NFP;
+        int64_t F = A.e2f[e * NF + f];
+        int k = A.perm[(e * NF + f) * NFP + l];
+        duh[i] = A.dUH[(F * M + a) * NFP + k];
+    }
+    for (int i = tid; i < GEO; i += NTH) geo[i] = A.geo[e * GEO + i];
+    __syncthreads();
+    const double* Tm = A.top + e * (size_t)NU * LD;
+    for (int i = warp; i < NU; i += NTH / 32) {
+        const double* row = Tm + (size_t)i * LD;
+        double s = 0.0;
+        for (int c = lane; c < NT; c += 32) s = fma(row[NU + c], duh[c], s);
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) w[i] = s + row[NC - 1];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int i = NU - 1; i >= 0; --i) {
+            const double* row = Tm + (size_t)i * LD;
+            double s = 0.0;
+            for (int j = i + 1 + lane; j < NU; j += 32) s = fma(row[j], x[j], s);
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+            if (lane == 0) x[i] = (w[i] - s) / row[i];
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < NU; i += NTH) A.dU[e * NU + i] = -x[i];
+    const double detJ = geo[0];
+    const double* Jinv = geo + 1;
+    const double* NW = geo + 1 + D * D;
+    const DeviceTables& T = A.tab;
+    for (int idx = tid; idx < M * NP; idx += NTH) {
+        int b = idx / NP, i = idx - b * NP;
+        double t[D], ef[NF];
+        for (int r = 0; r < D; ++r) {
+            double s = 0.0;
+            const double* mc = T.minv_c + ((size_t)r * NP + i) * NP;
+            for (int j = 0; j < NP; ++j) s -= mc[j] * x[b * NP + j];   // dU = -x
+            t[r] = s;
+        }
+        for (int f = 0; f < NF; ++f) {
+            double s = 0.0;
+            const double* me = T.minv_e + ((size_t)f * NP + i) * NFP;
+            for (int l = 0; l < NFP; ++l) s += me[l] * duh[(f * M + b) * NFP + l];
+            ef[f] = s;
+        }
+        for (int l = 0; l < D; ++l) {
+            double v = 0.0;
+            for (int r = 0; r < D; ++r) v -= Jinv[r * D + l] * t[r];
+            for (int f = 0; f < NF; ++f) v += NW[f * D + l] / detJ * ef[f];
+            int o = (l * M + b) * NP + i;
+            A.dQ[e * NQV + o] = A.dq0[e * NQV + o] + v;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// launchers
+// ----------------------------------------------------------------------------
+template <class C> struct BlkCfg;
+template <> struct BlkCfg<Cfg<2, 1>> { static constexpr int TY = 4, TX = 8, KC = 16; };
+template <> struct BlkCfg<Cfg<2, 2>> { static constexpr int TY = 4, TX = 8, KC = 16; };
+template <> struct BlkCfg<Cfg<2, 3>> { static constexpr int TY = 8, TX = 8, KC = 16; };
+template <> struct BlkCfg<Cfg<3, 1>> { static constexpr int TY = 8, TX = 8, KC = 16; };
+template <> struct BlkCfg<Cfg<3, 2>> { static constexpr int TY = 8, TX = 16, KC = 16; };
+template <> struct BlkCfg<Cfg<3, 3>> { static constexpr int TY = 16, TX = 16, KC = 16; };
+
+#define HDG_CK(call)                                                                   \
+    do {                                                                               \
+        cudaError_t err_ = (call);                                                     \
+        if (err_ != cudaSuccess) {                                                     \
+            h->err = std::string(#call) + ": " + cudaGetErrorString(err_);             \
+            return HDG_ECUDA;                                                          \
+        }                                                                              \
+    } while (0)
+
+template <int D, int P>
+int run_linearize(hdg_ctx* h, const LinArgs& la) {
+    using C = Cfg<D, P>;
+    using BC = BlkCfg<C>;
+    using BS_ = BlkShape<C, BC::TY, BC::TX, BC::KC>;
+    constexpr int PT = 128, NB = 16;
+    const size_t sm_point = sizeof(double) * point_smem_doubles<C>();
+    const size_t sm_blk = sizeof(double) * BS_::smem;
+    const size_t sm_elim = sizeof(double) * elim_smem_doubles<C, NB>();
+    HDG_CK(cudaFuncSetAttribute(k_point<C, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_point));
+    HDG_CK(cudaFuncSetAttribute(k_blocks<C, BC::TY, BC::TX, BC::KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
+    HDG_CK(cudaFuncSetAttribute(k_elim<C, NB, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
+    cudaStream_t st = h->stream;
+    HDG_CK(cudaMemsetAsync(h->d_vals, 0, sizeof(double) * h->nnzb * C::BS * C::BS, st));
+    HDG_CK(cudaMemsetAsync(h->d_g, 0, sizeof(double) * h->F * C::BS, st));
+    PointArgs pa;
+    pa.U = la.U; pa.Q = la.Q; pa.UH = la.UH; pa.Ustar = la.Ustar; pa.nu = la.nu;
+    pa.dt = la.dt; pa.a_ii = la.a_ii; pa.ph = h->phys; pa.tab = h->tab; pa.geo = h->d_geo;
+    pa.e2f = h->d_e2f; pa.perm = h->d_perm; pa.top = h->d_top; pa.bot = h->d_bot;
+    pa.vcoef = h->d_vcoef; pa.fcoef = h->d_fcoef; pa.dq0 = h->d_dq0;
+    BlkArgs ba;
+    ba.vcoef = h->d_vcoef; ba.fcoef = h->d_fcoef; ba.geo = h->d_geo; ba.tab = h->tab;
+    ba.top = h->d_top; ba.bot = h->d_bot; ba.dt = la.dt; ba.a_ii = la.a_ii; ba.tau = h->phys.tau;
+    for (int64_t e0 = 0; e0 < h->E; e0 += h->chunk) {
+        const int64_t ne = std::min<int64_t>(h->chunk, h->E - e0);
+        pa.e0 = e0; ba.e0 = e0;
+        prof_begin(h, HDG_K_POINT);
+        k_point<C, PT><<<(unsigned)ne, PT, sm_point, st>>>(pa);
+        prof_end(h);
+        prof_begin(h, HDG_K_BLOCKS);
+        k_blocks<C, BC::TY, BC::TX, BC::KC><<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
+        prof_end(h);
+        prof_begin(h, HDG_K_ELIM);
+        k_elim<C, NB, 256><<<(unsigned)ne, 256, sm_elim, st>>>(h->d_top, h->d_bot, e0, h->d_status);
+        prof_end(h);
+        for (int pass = 0; pass < 2; ++pass) {
+            prof_begin(h, HDG_K_ASSEMBLE);
+            k_assemble<C><<<(unsigned)(ne * C::NF * C::NF), 256, 0, st>>>(h->d_bot, e0, h->d_blk, h->d_rank,
+                                                                          h->d_iperm, h->d_vals, pass);
+            prof_end(h);
+            prof_begin(h, HDG_K_ASSEMBLE);
+            k_assemble_g<C><<<(unsigned)(ne * C::NF), 128, 0, st>>>(h->d_bot, e0, h->d_e2f, h->d_frank,
+                                                                   h->d_iperm, h->d_g, pass);
+            prof_end(h);
+        }
+        HDG_CK(cudaGetLastError());
+    }
+    h->have_system = true;
+    return HDG_OK;
+}
+
+template <int D, int P>
+int run_matvec(hdg_ctx* h, const double* x, double* y) {
+    using C = Cfg<D, P>;
+    prof_begin(h, HDG_K_MATVEC);
+    k_matvec<C><<<(unsigned)h->F, MvShape<C>::NTH, 0, h->stream>>>(h->d_rowptr, h->d_col, h->d_vals, x, y);
+    prof_end(h);
+    HDG_CK(cudaGetLastError());
+    return HDG_OK;
+}
+
+template <int D, int P>
+int run_recover(hdg_ctx* h, const double* dUH, double* dQ, double* dU) {
+    using C = Cfg<D, P>;
+    RecArgs ra;
+    ra.top = h->d_top; ra.dq0 = h->d_dq0; ra.geo = h->d_geo; ra.tab = h->tab;
+    ra.e2f = h->d_e2f; ra.perm = h->d_perm; ra.dUH = dUH; ra.dQ = dQ; ra.dU = dU;
+    prof_begin(h, HDG_K_RECOVER);
+    k_recover<C, 256><<<(unsigned)h->E, 256, 0, h->stream>>>(ra);
+    prof_end(h);
+    HDG_CK(cudaGetLastError());
+    return HDG_OK;
+}
+
+#define HDG_INSTANTIATE(D, P)                                                             \
+    template int run_linearize<D, P>(hdg_ctx*, const LinArgs&);                           \
+    template int run_matvec<D, P>(hdg_ctx*, const double*, double*);                      \
+    template int run_recover<D, P>(hdg_ctx*, const double*, double*, double*);
+
+}  // namespace hdg

@@ -1,0 +1,216 @@
+"""ctypes binding of libhdg.so: the C-ABI of ``include/hdg.h`` under the same names.
+
+Argument marshalling only: device arrays are torch CUDA tensors (float64,
+contiguous) passed by ``data_ptr()``; every step of the computation runs in the
+library's kernels.  A missing library raises ``HDGError`` -- there is no
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhdg.so")
+
+HDG_OK = 0
+HDG_EINVAL = -1
+HDG_ENOMEM = -2
+HDG_ECUDA = -3
+HDG_ESINGULAR = -4
+HDG_ENONFINITE = -5
+HDG_ENOCONV = -6
+HDG_EUNSUPPORTED = -7
+HDG_QUAD = 1
+HDG_HEX = 2
+HDG_PREC_FP64 = 0
+
+EXPORTS = [
+    "hdg_create", "hdg_create_host", "hdg_destroy", "hdg_last_error", "hdg_set_params", "hdg_set_stream",
+    "hdg_query_sizes", "hdg_get_connectivity", "hdg_linearize_condense", "hdg_trace_matvec",
+    "hdg_trace_rhs", "hdg_recover_interior", "hdg_get_blocks", "hdg_status", "hdg_profile",
+    "hdg_profile_read",
+]
+KERNEL_CLASSES = ["point", "blocks", "elim", "assemble", "matvec", "recover"]
+
+
+class HDGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libhdg error %d: %s" % (code, msg))
+        self.code = code
+
+
+class hdg_mesh(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("elem_type", ctypes.c_int32), ("n_elem", ctypes.c_int64),
+                ("n_vert", ctypes.c_int64), ("vert_xyz", ctypes.c_void_p), ("elem_vert", ctypes.c_void_p),
+                ("periodic_map", ctypes.c_void_p), ("bnd_tag", ctypes.c_void_p)]
+
+
+class hdg_params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("visc_law", ctypes.c_int32), ("suth_c1", ctypes.c_double),
+                ("suth_s", ctypes.c_double), ("precision", ctypes.c_int32)]
+
+
+class hdg_sizes(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int32) for n in ("dim", "p", "m", "Np", "Nq", "nf", "Nfp", "Nfq", "n_u", "n_q", "t",
+                                               "block")] + \
+               [(n, ctypes.c_int64) for n in ("n_elem", "n_faces", "nnzb", "device_bytes")]
+
+
+_lib = None
+
+
+def lib():
+    """Load libhdg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise HDGError(HDG_EINVAL, "libhdg.so not found at %s; build it with "
+                                   "paper_2608_27863_gb300.build.build()" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i32, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "hdg_create": [ctypes.POINTER(vp), ctypes.POINTER(hdg_mesh), i32, dbl, dbl, dbl, dbl],
+        "hdg_create_host": [ctypes.POINTER(vp), ctypes.POINTER(hdg_mesh), i32, dbl, dbl, dbl, dbl],
+        "hdg_destroy": [vp],
+        "hdg_set_params": [vp, ctypes.POINTER(hdg_params)],
+        "hdg_set_stream": [vp, vp],
+        "hdg_query_sizes": [vp, ctypes.POINTER(hdg_sizes)],
+        "hdg_get_connectivity": [vp] * 7,
+        "hdg_linearize_condense": [vp, vp, vp, vp, vp, vp, dbl, dbl, vp],
+        "hdg_trace_matvec": [vp, vp, vp],
+        "hdg_trace_rhs": [vp, vp],
+        "hdg_recover_interior": [vp, vp, vp, vp],
+        "hdg_get_blocks": [vp, vp],
+        "hdg_status": [vp],
+        "hdg_profile": [vp, i32],
+        "hdg_profile_read": [vp, vp, vp],
+    }
+    for name, args in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    L.hdg_last_error.argtypes = [vp]
+    L.hdg_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(h, rc):
+    if rc != HDG_OK:
+        msg = lib().hdg_last_error(h).decode() if h else "error"
+        raise HDGError(rc, msg)
+
+
+def _ptr(t):
+    """Device pointer of a torch CUDA float64 tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise HDGError(HDG_EINVAL, "arguments must be contiguous CUDA tensors")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class _MeshArgs:
+    """Keeps the host arrays of an hdg_mesh alive for the duration of a call."""
+
+    def __init__(self, dim, vert_xyz, elem_vert, periodic_map=None, bnd_tag=None):
+        self.vert = np.ascontiguousarray(vert_xyz, dtype=np.float64)
+        self.ev = np.ascontiguousarray(elem_vert, dtype=np.int64)
+        self.pm = None if periodic_map is None else np.ascontiguousarray(periodic_map, dtype=np.int64)
+        self.bt = None if bnd_tag is None else np.ascontiguousarray(bnd_tag, dtype=np.int32)
+        self.s = hdg_mesh(dim, HDG_QUAD if dim == 2 else HDG_HEX, self.ev.shape[0], self.vert.shape[0],
+                          self.vert.ctypes.data, self.ev.ctypes.data,
+                          None if self.pm is None else self.pm.ctypes.data,
+                          None if self.bt is None else self.bt.ctypes.data)
+
+
+def hdg_create(dim, vert_xyz, elem_vert, periodic_map, bnd_tag, p, gamma, Re, Pr, Mach, host_only=False):
+    """Create a handle; returns it as a ctypes void pointer."""
+    m = _MeshArgs(dim, vert_xyz, elem_vert, periodic_map, bnd_tag)
+    h = ctypes.c_void_p()
+    fn = lib().hdg_create_host if host_only else lib().hdg_create
+    rc = fn(ctypes.byref(h), ctypes.byref(m.s), p, gamma, Re, Pr, Mach)
+    if rc != HDG_OK:
+        msg = lib().hdg_last_error(h).decode() if h else "error"
+        lib().hdg_destroy(h)
+        raise HDGError(rc, msg)
+    return h
+
+
+def hdg_create_host(dim, vert_xyz, elem_vert, periodic_map, bnd_tag, p, gamma, Re, Pr, Mach):
+    return hdg_create(dim, vert_xyz, elem_vert, periodic_map, bnd_tag, p, gamma, Re, Pr, Mach, host_only=True)
+
+
+def hdg_destroy(h):
+    lib().hdg_destroy(h)
+
+
+def hdg_last_error(h):
+    return lib().hdg_last_error(h).decode()
+
+
+def hdg_set_params(h, tau=5.0, visc_law=0, suth_c1=1.4042, suth_s=0.40417, precision=HDG_PREC_FP64):
+    prm = hdg_params(tau, visc_law, suth_c1, suth_s, precision)
+    _check(h, lib().hdg_set_params(h, ctypes.byref(prm)))
+
+
+def hdg_set_stream(h, stream_handle):
+    _check(h, lib().hdg_set_stream(h, ctypes.c_void_p(stream_handle)))
+
+
+def hdg_query_sizes(h):
+    s = hdg_sizes()
+    _check(h, lib().hdg_query_sizes(h, ctypes.byref(s)))
+    return {n: getattr(s, n) for n, _ in hdg_sizes._fields_}
+
+
+def hdg_get_connectivity(h):
+    s = hdg_query_sizes(h)
+    E, F, nf, Nfp, nnzb = s["n_elem"], s["n_faces"], s["nf"], s["Nfp"], s["nnzb"]
+    out = {"f2e": np.zeros((F, 2), np.int32), "f2lf": np.zeros((F, 2), np.int32),
+           "e2f": np.zeros((E, nf), np.int32), "perm": np.zeros((E, nf, Nfp), np.int32),
+           "rowptr": np.zeros(F + 1, np.int32), "col": np.zeros(nnzb, np.int32)}
+    _check(h, lib().hdg_get_connectivity(h, *[out[k].ctypes.data for k in
+                                              ("f2e", "f2lf", "e2f", "perm", "rowptr", "col")]))
+    return out
+
+
+def hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii):
+    _check(h, lib().hdg_linearize_condense(h, _ptr(U), _ptr(Q), _ptr(UH), _ptr(Ustar), _ptr(nu),
+                                           float(dt), float(a_ii), None))
+
+
+def hdg_trace_matvec(h, x, y):
+    _check(h, lib().hdg_trace_matvec(h, _ptr(x), _ptr(y)))
+
+
+def hdg_trace_rhs(h, g):
+    _check(h, lib().hdg_trace_rhs(h, _ptr(g)))
+
+
+def hdg_recover_interior(h, dUH, dQ, dU):
+    _check(h, lib().hdg_recover_interior(h, _ptr(dUH), _ptr(dQ), _ptr(dU)))
+
+
+def hdg_get_blocks(h, vals):
+    _check(h, lib().hdg_get_blocks(h, _ptr(vals)))
+
+
+def hdg_status(h):
+    return lib().hdg_status(h)
+
+
+def hdg_profile(h, enable=True):
+    _check(h, lib().hdg_profile(h, 1 if enable else 0))
+
+
+def hdg_profile_read(h):
+    """{kernel class: (milliseconds, launches)} accumulated since the last read."""
+    ms = np.zeros(len(KERNEL_CLASSES), np.float64)
+    n = np.zeros(len(KERNEL_CLASSES), np.int64)
+    _check(h, lib().hdg_profile_read(h, ms.ctypes.data, n.ctypes.data))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}

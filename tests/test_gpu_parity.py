@@ -1,0 +1,163 @@
+"""GPU FP64 path vs the FP64 oracle, element by element and block by block.
+
+Bar: every compared block of the assembled trace matrix within 1e-11 relative
+Frobenius norm, the condensed right-hand side and the recovered interior
+corrections within 1e-11 relative to their norm; integer data bit-exact
+(tested on the host in test_lib_host.py).  Small meshes are compared in full;
+the full-size workloads on sampled block rows (the two elements of each
+sampled face provide every contribution to the row).
+"""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle.hdg import Problem
+from tests.helpers import GpuRun, block_rel_errors, create
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2608_27863_gb300 import build
+    build.build()
+
+
+def compare(P, rows=None, check_matvec=False, seed=0):
+    run = GpuRun(P).linearize()
+    from paper_2608_27863_gb300 import hdg as H
+    assert H.hdg_status(run.h) == 0
+    vals = run.blocks()
+    g = run.rhs()
+    pb = Problem(P)
+    cn = pb.conn
+    rows = range(cn.n_faces) if rows is None else rows
+    blocks = [b for F in rows for b in range(cn.rowptr[F], cn.rowptr[F + 1])]
+    orc, cache = pb.assemble(blocks=blocks)
+    errs = block_rel_errors(vals, orc)
+    worst = max(errs.values())
+    assert worst < TOL, worst
+    og = pb.assemble_g(cache, rows)
+    for F in rows:
+        assert np.linalg.norm(g[F] - og[F]) <= TOL * max(np.linalg.norm(og[F]), 1e-300), F
+    rng = np.random.default_rng(seed)
+    dUH = rng.normal(size=P.UH.shape) * np.abs(P.UH).mean(axis=(0, 2))[None, :, None] * 1e-3
+    dQ, dU = run.recover(dUH)
+    for e in sorted(cache):
+        oq, ou = pb.recover(e, cache[e], dUH)
+        assert np.linalg.norm(dU[e] - ou) <= TOL * np.linalg.norm(ou), e
+        assert np.linalg.norm(dQ[e] - oq) <= TOL * np.linalg.norm(oq), e
+    if check_matvec:
+        x = rng.normal(size=P.UH.shape)
+        y = run.matvec(x)
+        # kernel alone: against a dense product with the GPU's own blocks
+        bs = vals.shape[1]
+        xv = x.reshape(cn.n_faces, bs)
+        yref = np.zeros_like(xv)
+        for F in range(cn.n_faces):
+            for b in range(cn.rowptr[F], cn.rowptr[F + 1]):
+                yref[F] += vals[b] @ xv[cn.col[b]]
+        assert np.abs(y.reshape(yref.shape) - yref).max() <= 1e-13 * np.abs(yref).max()
+        # whole path: against the oracle's assembled operator
+        yo = pb.matvec(orc, x)
+        assert np.linalg.norm(y - yo) <= TOL * np.linalg.norm(yo)
+    run.close()
+    return worst
+
+
+def test_config1_quad_p2_full():
+    """8 x 8 periodic unit square, quads p = 2 (the small workload), everything compared."""
+    compare(synth.config1(), check_matvec=True)
+
+
+@pytest.mark.parametrize("dim,p,law,av", [(2, 1, 0, 0.0), (2, 3, 1, 2e-3), (3, 1, 1, 1e-3)])
+def test_tiny_meshes_full(dim, p, law, av):
+    compare(synth.tiny(dim, p, visc_law=law, av=av), check_matvec=True)
+
+
+def test_hex_p2_small_full():
+    """3 x 3 x 3 TGV hexes p = 2: several tiles of every kernel, ragged tails."""
+    compare(synth.config2(n=3), check_matvec=True)
+
+
+def test_hex_p3_small_sampled():
+    P = synth.config3(n=3)
+    compare(P, rows=[0, 17, 40])
+
+
+def test_skewed_scrambled_nonuniform_mesh():
+    """Parallelepiped elements, a 3 x 4 x 3 box and randomly relabelled vertices
+    (rotated / reflected face frames)."""
+    P = synth.config_tgv(3, 2, 0.5, 5, True, 1e-3)
+    mesh = synth.box_mesh(3, (3, 4, 3), (0,) * 3, (2 * np.pi,) * 3, (True,) * 3)
+    rng = np.random.default_rng(4)
+    perm = rng.permutation(mesh.n_vert)
+    inv = np.argsort(perm)
+    xyz = mesh.vert_xyz[inv].copy()
+    xyz[:, 0] += 0.2 * xyz[:, 1] + 0.1 * xyz[:, 2]
+    xyz[:, 2] += 0.15 * xyz[:, 1]
+    mesh.vert_xyz = xyz
+    mesh.elem_vert = perm[mesh.elem_vert]
+    mesh.periodic_map = perm[mesh.periodic_map[inv]]
+    x = synth.node_xyz(mesh, 2)
+    fun = lambda y: synth.tgv_state(y, 1.4, 0.5)
+    P.mesh = mesh
+    P.U = np.ascontiguousarray(fun(x).transpose(0, 2, 1))
+    P.Q = np.ascontiguousarray(synth.nodal_gradient(fun, x).transpose(0, 2, 3, 1))
+    P.Ustar = P.U + 1e-3 * synth.normal(9, P.U.size).reshape(P.U.shape)
+    P.UH = P.UH[:mesh.n_faces()] if P.UH.shape[0] >= mesh.n_faces() else np.resize(P.UH, (mesh.n_faces(),) + P.UH.shape[1:])
+    P.nu = synth.synthetic_nu(mesh, 2, 3, 1e-3)
+    compare(P, rows=[0, 5, 33, 70, 107])
+
+
+def test_chunking_is_bitwise_invisible():
+    P = synth.config2(n=3)
+    a = GpuRun(P).linearize()
+    va, ga = a.blocks(), a.rhs()
+    a.close()
+    os.environ["HDG_SCRATCH_BYTES"] = str(5 * 1024 * 1024)   # a few elements per chunk, ragged last chunk
+    try:
+        b = GpuRun(P).linearize()
+    finally:
+        del os.environ["HDG_SCRATCH_BYTES"]
+    vb, gb = b.blocks(), b.rhs()
+    b.linearize()
+    vc = b.blocks()
+    b.close()
+    assert np.array_equal(va, vb) and np.array_equal(ga, gb)
+    assert np.array_equal(vb, vc)   # run-to-run determinism
+
+
+def test_config2_full_size_sampled():
+    """16^3 = 4096 hexes p = 2 (the timed workload), sampled block rows."""
+    P = synth.config2()
+    rows = list(synth.splitmix64(21, 6) % np.uint64(P.mesh.n_faces()))
+    compare(P, rows=[int(r) for r in rows])
+
+
+def test_config3_full_size_sampled():
+    """24^3 = 13824 hexes p = 3, Sutherland + artificial viscosity, sampled rows."""
+    P = synth.config3()
+    rows = list(synth.splitmix64(22, 2) % np.uint64(P.mesh.n_faces()))
+    compare(P, rows=[int(r) for r in rows])
+
+
+def test_nonfinite_input_is_reported():
+    import torch
+    from paper_2608_27863_gb300 import hdg as H
+    P = synth.tiny(2, 2)
+    P.U = P.U.copy()
+    P.U[4, 0, 3] = np.nan
+    run = GpuRun(P).linearize()
+    assert H.hdg_status(run.h) == H.HDG_ENONFINITE
+    # the handle stays usable
+    run.U.copy_(torch.from_numpy(synth.tiny(2, 2).U).cuda())
+    run.linearize()
+    assert H.hdg_status(run.h) == 0
+    run.close()
