@@ -167,6 +167,25 @@ int hdg_status(hdg_handle h);
 int hdg_profile(hdg_handle h, int enable);
 int hdg_profile_read(hdg_handle h, double* ms, int64_t* launches);
 
+/* Allocation-free variant of hdg_linearize_condense (the paper has no
+ * counterpart).  It is for callers that must not allocate device memory once
+ * the handle exists: a host whose memory pool has taken the remaining HBM
+ * after set-up, or a step loop that cannot afford the implicit device
+ * synchronisation of cudaMalloc / cudaFree.  Same arguments and results as
+ * hdg_linearize_condense (res_norm omitted); the per-chunk scratch comes from
+ * a 64 MiB file-scope device array of the library instead of the handle's
+ * scratch, so elements are condensed in chunks of at most 64 MiB / (scratch
+ * of one element) (45 hex p=2, 15 hex p=3 elements).  The call issues no
+ * cudaMalloc, cudaFree or other allocating routine.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current, so make it before any stream capture.  Every call, from any
+ * handle, shares the one array: calls whose GPU work overlaps (for example on
+ * two streams) race and corrupt each other's results; serialise them.
+ * Returns HDG_EINVAL if one element's scratch exceeded the array (no
+ * supported (d, p) does). */
+int hdg_linearize_condense_static(hdg_handle h, const double* U, const double* Q, const double* UH,
+                                  const double* Ustar, const double* nu, double dt, double a_ii);
+
 #ifdef __cplusplus
 }
 #endif

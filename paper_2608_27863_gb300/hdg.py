@@ -31,7 +31,7 @@ EXPORTS = [
     "hdg_create", "hdg_create_host", "hdg_destroy", "hdg_last_error", "hdg_set_params", "hdg_set_stream",
     "hdg_query_sizes", "hdg_get_connectivity", "hdg_linearize_condense", "hdg_trace_matvec",
     "hdg_trace_rhs", "hdg_recover_interior", "hdg_get_blocks", "hdg_status", "hdg_profile",
-    "hdg_profile_read",
+    "hdg_profile_read", "hdg_linearize_condense_static",
 ]
 KERNEL_CLASSES = ["point", "blocks", "elim", "assemble", "matvec", "recover"]
 
@@ -88,6 +88,7 @@ def lib():
         "hdg_status": [vp],
         "hdg_profile": [vp, i32],
         "hdg_profile_read": [vp, vp, vp],
+        "hdg_linearize_condense_static": [vp, vp, vp, vp, vp, vp, dbl, dbl],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -182,6 +183,12 @@ def hdg_get_connectivity(h):
 def hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii):
     _check(h, lib().hdg_linearize_condense(h, _ptr(U), _ptr(Q), _ptr(UH), _ptr(Ustar), _ptr(nu),
                                            float(dt), float(a_ii), None))
+
+
+def hdg_linearize_condense_static(h, U, Q, UH, Ustar, nu, dt, a_ii):
+    """Allocation-free variant: scratch from the library's static device array."""
+    _check(h, lib().hdg_linearize_condense_static(h, _ptr(U), _ptr(Q), _ptr(UH), _ptr(Ustar), _ptr(nu),
+                                                  float(dt), float(a_ii)))
 
 
 def hdg_trace_matvec(h, x, y):
