@@ -34,6 +34,7 @@ L2_BYTES = 129 * 1024 * 1024
 
 WORKLOADS = {
     "hex-p2-16^3-tgv": dict(fn="config2", kw={}),
+    "hex-p2-8^3-tgv": dict(fn="config2", kw={"n": 8}),
     "hex-p3-24^3-tgv-av": dict(fn="config3", kw={}),
     "quad-p2-8x8": dict(fn="config1", kw={}),
 }
@@ -170,8 +171,17 @@ def oracle_rate(pool, cores, n_elem, seconds, seed):
 # ----------------------------------------------------------------------------
 # GPU leg
 # ----------------------------------------------------------------------------
+SMS = 152
+FP64_FMA_PER_CLK_PER_SM = 2      # measured with a DFMA-chain probe: 1.19 TFLOP/s saturates at 2 per clock
+
+
+def fp64_peak_derived(sm_max_mhz):
+    """FP64 pipe peak from unit counts and the maximum SM clock (TFLOP/s)."""
+    return SMS * FP64_FMA_PER_CLK_PER_SM * 2 * sm_max_mhz * 1e6 / 1e12
+
+
 def fp64_peak_tflops(torch):
-    """cuBLAS DGEMM throughput measured in this run (the FP64 roofline denominator)."""
+    """cuBLAS DGEMM throughput measured in this run (context for the FP64 roofline)."""
     n = 4096
     a = torch.randn(n, n, dtype=torch.float64, device="cuda")
     b = torch.randn(n, n, dtype=torch.float64, device="cuda")
@@ -225,36 +235,55 @@ def run_ours(args, rank, world, local_rank):
         H.hdg_trace_matvec(h, x, y)
         H.hdg_recover_interior(h, y, dQ, dU)
 
+    def set_prec(prec):
+        H.hdg_set_params(h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s, precision=prec)
+
+    def timed(nsteps, clk_index=None):
+        H.hdg_profile_read(h)
+        H.hdg_profile(h, True)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        times = []
+        with ClockSampler(local_rank if clk_index is None else clk_index) as clk:
+            for _ in range(nsteps):
+                flush.fill_(1.0)       # L2 flush between timed steps (not timed)
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record(stream)
+                step()
+                e.record(stream)
+                e.synchronize()
+                times.append(s.elapsed_time(e))
+        torch.cuda.synchronize()
+        prof = H.hdg_profile_read(h)
+        H.hdg_profile(h, False)
+        t_ms = sum(times)
+        if world > 1:
+            tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t_ms = float(tt.item())
+            dist.barrier()
+        return t_ms, prof, clk.summary()
+
+    # FP64 form (the headline value)
+    set_prec(H.HDG_PREC_FP64)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
     if H.hdg_status(h) != 0:
         raise RuntimeError("device status: " + H.hdg_last_error(h))
-    peak = fp64_peak_tflops(torch)
-    H.hdg_profile_read(h)
-    H.hdg_profile(h, True)
-    if world > 1:
-        dist.barrier()
+    dgemm = fp64_peak_tflops(torch)
+    t_ms, prof, clocks = timed(args.steps)
+
+    # mixed form on the same workload and step
+    set_prec(H.HDG_PREC_MIXED)
+    for _ in range(args.warmup):
+        step()
     torch.cuda.synchronize()
-    times = []
-    with ClockSampler(local_rank) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1.0)       # L2 flush between timed steps (not timed)
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record(stream)
-            step()
-            e.record(stream)
-            e.synchronize()
-            times.append(s.elapsed_time(e))
-    torch.cuda.synchronize()
-    prof = H.hdg_profile_read(h)
-    H.hdg_profile(h, False)
-    t_ms = sum(times)
-    if world > 1:
-        tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_ms = float(tt.item())
-        dist.barrier()
+    if H.hdg_status(h) != 0:
+        raise RuntimeError("device status (mixed): " + H.hdg_last_error(h))
+    tm_ms, prof_m, clocks_m = timed(args.steps)
+    set_prec(H.HDG_PREC_FP64)
 
     # end to end through the C-ABI from pinned host memory
     hU, hQ, hUH, hUs = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (P.U, P.Q, P.UH, P.Ustar))
@@ -291,19 +320,58 @@ def run_ours(args, rank, world, local_rank):
                          "Jacobian, dense FP64 LU of the (q,u) block and Schur complement (assembly, matvec "
                          "and recovery not included)" % (n_done, secs)}
 
+    # mixed vs FP64 at tolerance: Newton on the stage equations to ||F||_2 <= 1e-8 (FP64 residual)
+    newton = {}
+    if not args.no_newton:
+        for name, prec in (("fp64", H.HDG_PREC_FP64), ("mixed", H.HDG_PREC_MIXED)):
+            set_prec(prec)
+            U2, Q2, UH2 = U.clone(), Q.clone(), UH.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            nit, git, hist = H.hdg_newton(h, U2, Q2, UH2, Us, nu, P.dt, P.a_ii, tol=1e-8, max_newton=12,
+                                          restart=40, max_gmres=600, gmres_rtol=1e-9, raise_on_noconv=False)
+            torch.cuda.synchronize()
+            newton[name] = {"seconds": time.perf_counter() - t0, "newton_iters": nit, "gmres_iters": git,
+                            "residual_history": [float(v) for v in hist]}
+            newton[name + "_state"] = (U2, UH2)
+        du = float(torch.linalg.norm(newton["mixed_state"][0] - newton["fp64_state"][0]) /
+                   torch.linalg.norm(newton["fp64_state"][0]))
+        duh = float(torch.linalg.norm(newton["mixed_state"][1] - newton["fp64_state"][1]) /
+                    torch.linalg.norm(newton["fp64_state"][1]))
+        del newton["mixed_state"], newton["fp64_state"]
+        newton["tol"] = 1e-8
+        newton["state_rel_diff_U"] = du
+        newton["state_rel_diff_UH"] = duh
+        newton["speedup"] = newton["fp64"]["seconds"] / newton["mixed"]["seconds"]
+        set_prec(H.HDG_PREC_FP64)
+
     E = m.n_elem
     fl = flop_counts(m.dim, P.p)
     kern = {}
     for k, (ms, n) in prof.items():
-        kern[k] = {"ms_per_step": ms / args.steps, "launches_per_step": n / args.steps}
-    kern["elim"]["gflops"] = fl["elim"] * E / (prof["elim"][0] / args.steps) / 1e6 if prof["elim"][0] else None
-    kern["blocks"]["gflops"] = fl["blocks"] * E / (prof["blocks"][0] / args.steps) / 1e6 if prof["blocks"][0] else None
+        if n:
+            kern[k] = {"ms_per_step": ms / args.steps, "launches_per_step": n / args.steps}
+    kern["elim"]["tflops"] = fl["elim"] * E / (prof["elim"][0] / args.steps) / 1e9
+    kern["blocks"]["tflops"] = fl["blocks"] * E / (prof["blocks"][0] / args.steps) / 1e9
     dom = max(("elim", "blocks"), key=lambda k: prof[k][0])
     avg_launch_ms = prof[dom][0] / max(prof[dom][1], 1)
     per_launch_elems = E / max(prof[dom][1] / args.steps, 1)
     achieved = fl[dom] * per_launch_elems / (avg_launch_ms * 1e-3) / 1e12
+    smmax = clocks.get("sm_max_mhz") or 2070.0
+    peak = fp64_peak_derived(smmax)
     launches = sum(n for _, n in prof.values()) / args.steps
     value = world * E * args.steps / (t_ms * 1e-3)
+    mixed = {"value": world * E * args.steps / (tm_ms * 1e-3), "unit": "elements/s", "ms_per_step": tm_ms / args.steps,
+             "speedup_vs_fp64_step": t_ms / tm_ms,
+             "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                         for k, v in prof_m.items() if v[1]},
+             "dtype": "fp64 pointwise terms, interior LU, residual and Arnoldi; fp32 blocks and Schur",
+             "clocks": clocks_m}
+    lu_flops = sum(2 * (C_nu - k - 1) * (C_nu - k) + (C_nu - k - 1) for C_nu in [(m.dim + 2) * (P.p + 1) ** m.dim]
+                   for k in range(C_nu))
+    mixed["fp64_lu_tflops"] = lu_flops * E / (prof_m["elim"][0] / args.steps) / 1e9
+    if newton:
+        mixed["newton"] = newton
     out = {
         "metric": METRIC, "value": value, "unit": "elements/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True,
@@ -313,14 +381,16 @@ def run_ours(args, rank, world, local_rank):
                    "precision": "fp64", "l2": "flushed between timed steps (256 MiB write)"},
         "roofline": {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                     "peak_source": "cuBLAS DGEMM 4096^3 measured in this run (FP64 pipe)",
+                     "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz (derived); cuBLAS DGEMM "
+                                    "measured in this run: %.3f TFLOP/s" % (smmax, dgemm),
                      "flops_per_element": fl[dom]},
         "gflops_total": fl["total"] * E * args.steps / (t_ms * 1e-3) / 1e9,
         "kernels": kern,
+        "mixed": mixed,
         "e2e": {"value": world * E * args.steps / (e2e_ms * 1e-3), "unit": "elements/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
-        "clocks": clk.summary(),
+        "clocks": clocks,
     }
     if cpu is not None:
         out["cpu_baseline"] = cpu
@@ -364,6 +434,7 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default=DEFAULT_WORKLOAD)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-newton", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -62,6 +62,10 @@ extern "C" {
 
 /* Arithmetic of the condensation path. */
 #define HDG_PREC_FP64 0       /* everything in FP64 */
+#define HDG_PREC_MIXED 1      /* FP64 pointwise terms, interior LU (with pivoting) and right-hand sides;
+                                 FP32 contraction, off-diagonal blocks, Schur complement and trace blocks */
+#define HDG_PREC_MIXED_TF32 2   /* as HDG_PREC_MIXED, Schur product S = Dt - W Z on tensor cores in TF32 */
+#define HDG_PREC_MIXED_3XTF32 3 /* as HDG_PREC_MIXED, Schur product in 3xTF32 split precision on tensor cores */
 
 typedef struct hdg_ctx* hdg_handle;
 
@@ -143,17 +147,56 @@ int hdg_trace_rhs(hdg_handle h, double* g);
  * element: dQ [E][d][m][Np], dU [E][m][Np] (device, caller-owned). */
 int hdg_recover_interior(hdg_handle h, const double* dUH, double* dQ, double* dU);
 /* Copy the BSR values: [nnzb][block][block], block column-major, i.e.
- * value (r, c) of block b at vals[(b * block + c) * block + r], r = a Nfp + k. */
+ * value (r, c) of block b at vals[(b * block + c) * block + r], r = a Nfp + k.
+ * The values are FP64 after an FP64 linearization and FP32 (vals then points
+ * to float storage of the same shape) after an HDG_PREC_MIXED one. */
 int hdg_get_blocks(hdg_handle h, double* vals);
 /* Read back the latched device status: HDG_OK, HDG_ESINGULAR or
  * HDG_ENONFINITE (synchronises the stream). */
 int hdg_status(hdg_handle h);
 
+/* FP64 stage residual F(W) = [R_q; R_u; R_uhat] at W = (Q, U, UH) (eq.
+ * nonlinear-residual; R_uhat assembled over both sides of every face).
+ * Optional device outputs Rq [E][d][m][Np], Ru [E][m][Np], Ruh [F][m][Nfp];
+ * norms (host, optional) receives ||F||_2, ||(R_q, R_u)||_2, ||R_uhat||_2 and
+ * then the call synchronises the stream.  Allocates its scratch on first use. */
+int hdg_residual(hdg_handle h, const double* U, const double* Q, const double* UH, const double* Ustar,
+                 const double* nu, double dt, double a_ii, double* Rq, double* Ru, double* Ruh, double* norms);
+/* Newton update W <- W + alpha dW (eq. newton-update) on device arrays. */
+int hdg_update_state(hdg_handle h, double* U, double* Q, double* UH, const double* dU, const double* dQ,
+                     const double* dUH, double alpha);
+/* Block-Jacobi preconditioner of the trace system: partial-pivot LU of every
+ * diagonal block S_FF of the current S (the one-face special case of the
+ * additive Schwarz method, eq. additive-schwarz), and y = M^{-1} x. */
+int hdg_blockjacobi_setup(hdg_handle h);
+int hdg_blockjacobi_apply(hdg_handle h, const double* x, double* y);
+/* Restarted GMRES(restart) on S x = b with FP64 modified Gram-Schmidt
+ * Arnoldi (Sec. 3.2), left-preconditioned by block-Jacobi when precond != 0.
+ * x holds the initial guess and receives the solution (device arrays
+ * [F][m][Nfp]).  Stops when the preconditioned residual drops below
+ * rtol x its initial value or after max_iter iterations (HDG_ENOCONV).
+ * iters / relres (host, optional) receive the iteration count and the final
+ * relative preconditioned residual.  Workspace is allocated on first use. */
+int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_iter, double rtol, int precond,
+              int* iters, double* relres);
+
+/* Newton iteration on the DIRK stage equations (eqs. newton-linearization,
+ * newton-update with alpha = 1): repeat { F(W); linearize + condense;
+ * block-Jacobi GMRES on S dUH = g (rtol gmres_rtol); recover; W += dW } until
+ * ||F(W)||_2 <= tol (absolute, FP64) or max_newton linearizations.  U, Q, UH
+ * are updated in place.  hist (host, optional, max_newton + 1 entries)
+ * receives ||F|| before each iteration.  Returns HDG_ENOCONV if tol was not
+ * reached.  Work arrays are allocated on first use. */
+int hdg_newton(hdg_handle h, double* U, double* Q, double* UH, const double* Ustar, const double* nu, double dt,
+               double a_ii, double tol, int max_newton, int restart, int max_gmres, double gmres_rtol,
+               double* hist, int* newton_iters, int* gmres_iters);
+
 /* Per-kernel timing with CUDA events recorded on the handle's stream around
  * every kernel launch (not from the paper: instrumentation for rooflines).
  * Kernel classes: HDG_K_POINT (A0/A1 quadrature-point fluxes and Jacobians),
  * HDG_K_BLOCKS (A2 contraction), HDG_K_ELIM (A3/A4 bordered elimination),
- * HDG_K_ASSEMBLE (A5), HDG_K_MATVEC (A6), HDG_K_RECOVER (A7).
+ * HDG_K_ASSEMBLE (A5), HDG_K_MATVEC (A6), HDG_K_RECOVER (A7), HDG_K_SCHUR
+ * (the separate Schur product of the mixed form).
  * hdg_profile_read synchronises the stream, writes the accumulated
  * milliseconds [HDG_NK] and launch counts [HDG_NK] since the last read, and
  * clears them. */
@@ -163,7 +206,8 @@ int hdg_status(hdg_handle h);
 #define HDG_K_ASSEMBLE 3
 #define HDG_K_MATVEC 4
 #define HDG_K_RECOVER 5
-#define HDG_NK 6
+#define HDG_K_SCHUR 6
+#define HDG_NK 7
 int hdg_profile(hdg_handle h, int enable);
 int hdg_profile_read(hdg_handle h, double* ms, int64_t* launches);
 

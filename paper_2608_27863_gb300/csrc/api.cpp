@@ -188,6 +188,7 @@ int create_device(hdg_ctx* h) {
     size_t budget = (size_t)8 << 30;
     if (const char* s = std::getenv("HDG_SCRATCH_BYTES")) budget = std::strtoull(s, nullptr, 10);
     h->chunk = std::max<int64_t>(1, std::min<int64_t>(h->E, (int64_t)(budget / per)));
+    if (const char* s = std::getenv("HDG_ELIM_MINB")) h->elim_minb = std::atoi(s) == 1 ? 1 : 2;
     if ((rc = dev_alloc(h, &h->d_bot, (size_t)h->chunk * h->NT * h->LD))) return rc;
     if ((rc = dev_alloc(h, &h->d_vcoef, (size_t)h->chunk * h->m * h->m * d * h->NCOEF * h->Nq))) return rc;
     if ((rc = dev_alloc(h, &h->d_fcoef, (size_t)h->chunk * h->nf * h->m * h->m * h->NCOEF * h->Nfq))) return rc;
@@ -244,12 +245,14 @@ int hdg_set_params(hdg_handle h, const hdg_params* prm) {
     if (prm->visc_law != 0 && prm->visc_law != 1) return fail(h, HDG_EINVAL, "visc_law must be 0 or 1");
     if (prm->visc_law == 1 && !(prm->suth_c1 > 0.0 && prm->suth_s > 0.0))
         return fail(h, HDG_EINVAL, "Sutherland constants must be positive");
-    if (prm->precision != HDG_PREC_FP64) return fail(h, HDG_EUNSUPPORTED, "precision mode not available");
+    if (prm->precision < HDG_PREC_FP64 || prm->precision > HDG_PREC_MIXED_3XTF32)
+        return fail(h, HDG_EUNSUPPORTED, "precision mode not available");
     h->phys.tau = prm->tau;
     h->phys.visc_law = prm->visc_law;
     h->phys.c1 = prm->suth_c1;
     h->phys.s = prm->suth_s;
-    h->precision = prm->precision;
+    h->precision = prm->precision == HDG_PREC_FP64 ? HDG_PREC_FP64 : HDG_PREC_MIXED;
+    h->schur_mode = prm->precision == HDG_PREC_FP64 ? 0 : prm->precision - HDG_PREC_MIXED;
     return HDG_OK;
 }
 
@@ -289,6 +292,9 @@ int hdg_linearize_condense(hdg_handle h, const double* U, const double* Q, const
     if (!(dt > 0.0) || !(a_ii > 0.0)) return fail(h, HDG_EINVAL, "dt and a_ii must be positive");
     CKH(cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), h->stream));
     LinArgs a{U, Q, UH, Ustar, nu, dt, a_ii};
+    if (h->precision == HDG_PREC_MIXED) {
+        DISPATCH(run_linearize_mixed, h, a);
+    }
     DISPATCH(run_linearize, h, a);
 }
 
@@ -318,7 +324,9 @@ int hdg_get_blocks(hdg_handle h, double* vals) {
     if (!h) return HDG_EINVAL;
     if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
     if (!vals) return fail(h, HDG_EINVAL, "vals is NULL");
-    CKH(cudaMemcpyAsync(vals, h->d_vals, sizeof(double) * h->nnzb * h->BS * h->BS, cudaMemcpyDeviceToDevice, h->stream));
+    const size_t bytes = (h->sys_prec == HDG_PREC_MIXED ? sizeof(float) : sizeof(double)) * h->nnzb * h->BS * h->BS;
+    CKH(cudaMemcpyAsync(vals, h->sys_prec == HDG_PREC_MIXED ? (const void*)h->d_vals32 : (const void*)h->d_vals,
+                        bytes, cudaMemcpyDeviceToDevice, h->stream));
     return HDG_OK;
 }
 

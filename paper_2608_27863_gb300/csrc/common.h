@@ -114,8 +114,35 @@ struct hdg_ctx {
     double* d_fcoef = nullptr;             // [chunk][nf][m][m][NCOEF][Nfq]
     double* d_dq0 = nullptr;               // [E][d][m][Np]
     int32_t* d_status = nullptr;           // [1]
+    int32_t* d_f2e = nullptr;              // [F][2]
+    int32_t* d_f2lf = nullptr;             // [F][2]
+    double* d_rk = nullptr;                // [E][NT] element contributions to R_uhat
+    double* d_part = nullptr;              // [E + F] partial sums of squares
+    double* d_norms = nullptr;             // [3]
+    // block-Jacobi factors (allocated on first set-up)
+    double* d_bjlu = nullptr;              // [F][BS][BS]
+    int32_t* d_bjpiv = nullptr;            // [F][BS]
+    bool bj_ready = false;
+    // GMRES workspace (allocated on first use)
+    double* d_V = nullptr;                 // [restart + 1][N]
+    double* d_w = nullptr;                 // [N]
+    double* d_red = nullptr;               // [kRedBlocks]
+    double* d_h = nullptr;                 // [restart + 2]
+    int gm_cap = 0;
+    double* d_nw = nullptr;                // Newton work: dU, dQ, dUH, g
+    // mixed form (allocated on the first mixed linearization)
+    int sys_prec = HDG_PREC_FP64;          // precision of the assembled system
+    int schur_mode = 0;                    // mixed Schur product: 0 FP32 SIMT, 1 TF32, 2 3xTF32 tensor cores
+    double* d_m11 = nullptr;               // [E][NU][NU] interior block / its LU factors (FP64)
+    float* d_m12 = nullptr;                // [E][NU][NT] Bt, then Z = L^{-1} P Bt
+    double* d_mrt = nullptr;               // [E][NU] Rt, then z
+    float* d_m21 = nullptr;                // [chunk][NT][NU] Ct, then W
+    float* d_m22 = nullptr;                // [chunk][NT][NT] Dt, then S^K
+    double* d_mrb = nullptr;               // [chunk][NT] Rh, then -g^K
+    float* d_vals32 = nullptr;             // [nnzb][BS][BS] condensed blocks (FP32)
     int64_t chunk = 0;
     bool have_system = false;
+    int elim_minb = 2;                     // k_elim variant: resident CTAs per SM the kernel is built for
 
     // instrumentation: event pairs around kernel launches
     bool prof = false;
@@ -139,4 +166,8 @@ struct LinArgs {
 template <int D, int P> int run_linearize(hdg_ctx* h, const LinArgs& a);
 template <int D, int P> int run_matvec(hdg_ctx* h, const double* x, double* y);
 template <int D, int P> int run_recover(hdg_ctx* h, const double* dUH, double* dQ, double* dU);
+template <int D, int P> int run_residual(hdg_ctx* h, const LinArgs& a, double* Rq, double* Ru, double* Ruh);
+template <int D, int P> int run_linearize_mixed(hdg_ctx* h, const LinArgs& a);
+template <int D, int P> int run_bj_setup(hdg_ctx* h);
+template <int D, int P> int run_bj_apply(hdg_ctx* h, const double* x, double* y);
 }  // namespace hdg

@@ -1,5 +1,7 @@
 // Kernel instantiations for one group of (d, p) configurations.
-#include "kernels.cuh"
+#include "solve.cuh"
 namespace hdg {
 HDG_INSTANTIATE(3, 1)
+HDG_INSTANTIATE_SOLVE(3, 1)
+HDG_INSTANTIATE_MIXED(3, 1)
 }  // namespace hdg

@@ -1,5 +1,7 @@
 // Kernel instantiations for one group of (d, p) configurations.
-#include "kernels.cuh"
+#include "solve.cuh"
 namespace hdg {
 HDG_INSTANTIATE(3, 2)
+HDG_INSTANTIATE_SOLVE(3, 2)
+HDG_INSTANTIATE_MIXED(3, 2)
 }  // namespace hdg

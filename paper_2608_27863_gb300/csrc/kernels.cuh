@@ -30,6 +30,35 @@ namespace hdg {
 // per-element geometry record: detJ, Jinv[d][d] (d xi_r / d x_k), NW[nf][d]
 template <int D> struct Geo { static constexpr int N = 1 + D * D + 2 * D * D; };
 
+// Storage of the bordered matrix [[At, Bt, Rt], [Ct, Dt, Rh]] of each element as
+// region views: base pointer, element stride and row stride.  Interior rows are
+// indexed by the global element, trace rows by the element's index in the chunk.
+// The FP64 form keeps one row-major matrix per element (all views alias it);
+// the mixed form keeps At and the right-hand sides in FP64 and Bt, Ct, Dt in TL.
+template <class TL>
+struct Regions {
+    double* a11; int64_t a11_es, a11_rs;   // At  [n_u][n_u]
+    TL* a12; int64_t a12_es, a12_rs;       // Bt  [n_u][t]
+    TL* a21; int64_t a21_es, a21_rs;       // Ct  [t][n_u]   (chunk-local)
+    TL* a22; int64_t a22_es, a22_rs;       // Dt  [t][t]     (chunk-local)
+    double* rt; int64_t rt_es, rt_rs;      // Rt  [n_u]
+    double* rb; int64_t rb_es, rb_rs;      // Rh  [t]        (chunk-local)
+};
+
+// views of the FP64 form's single row-major bordered matrix (row stride LD)
+template <class C>
+inline Regions<double> fp64_regions(double* top, double* bot) {
+    constexpr int64_t NU = C::NU, NT = C::NT, LD = C::LD, NC = C::NC;
+    Regions<double> R;
+    R.a11 = top;           R.a11_es = NU * LD; R.a11_rs = LD;
+    R.a12 = top + NU;      R.a12_es = NU * LD; R.a12_rs = LD;
+    R.a21 = bot;           R.a21_es = NT * LD; R.a21_rs = LD;
+    R.a22 = bot + NU;      R.a22_es = NT * LD; R.a22_rs = LD;
+    R.rt = top + NC - 1;   R.rt_es = NU * LD;  R.rt_rs = LD;
+    R.rb = bot + NC - 1;   R.rb_es = NT * LD;  R.rb_rs = LD;
+    return R;
+}
+
 // ----------------------------------------------------------------------------
 // A0 + A1: gather, interpolation, fluxes and their Jacobians at quadrature points
 // ----------------------------------------------------------------------------
@@ -40,7 +69,9 @@ struct PointArgs {
     DeviceTables tab;
     const double* geo;
     const int32_t* e2f; const int32_t* perm;
-    double* top; double* bot; double* vcoef; double* fcoef; double* dq0;
+    double* rt; int64_t rt_es, rt_rs;      // right-hand side, interior rows
+    double* rb; int64_t rb_es, rb_rs;      // right-hand side, trace rows (chunk-local)
+    double* vcoef; double* fcoef; double* dq0;
     int64_t e0;
 };
 
@@ -259,16 +290,16 @@ __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
     }
     __syncthreads();
     // right-hand-side column: Rh (trace rows) then Rt (interior rows)
-    double* Bm = A.bot + el * (size_t)NT * LD;
+    double* rbe = A.rb + el * A.rb_es;
     for (int idx = tid; idx < NT; idx += NTH) {
         int f = idx / (M * NFP), rem = idx - f * M * NFP, a = rem / NFP, l = rem - a * NFP;
         double s = 0.0;
         for (int q = 0; q < NFQ; ++q) s += T.mu[q * NFP + l] * sFH[(f * M + a) * NFQ + q];
         sRh[idx] = s;
-        Bm[(size_t)idx * LD + NC - 1] = s;
+        rbe[idx * A.rb_rs] = s;
     }
     __syncthreads();
-    double* Tm = A.top + e * (size_t)NU * LD;
+    double* rte = A.rt + e * A.rt_es;
     for (int idx = tid; idx < NU; idx += NTH) {
         int a = idx / NP, i = idx - a * NP;
         double mass = 0.0;
@@ -282,17 +313,18 @@ __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
             int f = nfc / NFP, l = nfc - f * NFP;
             s += A.dt * sRh[(f * M + a) * NFP + l];
         }
-        Tm[(size_t)idx * LD + NC - 1] = s;
+        rte[idx * A.rt_rs] = s;
     }
 }
 
 // ----------------------------------------------------------------------------
 // A2: contraction of the coefficients with the basis tables into the blocks
 // ----------------------------------------------------------------------------
+template <class TL>
 struct BlkArgs {
     const double* vcoef; const double* fcoef; const double* geo;
     DeviceTables tab;
-    double* top; double* bot;
+    Regions<TL> R;
     double dt, a_ii, tau;
     int64_t e0;
 };
@@ -300,15 +332,20 @@ struct BlkArgs {
 template <class C, int TY, int TX, int KC>
 struct BlkShape {
     static constexpr int NCB = C::NP + C::NF * C::NFP;
-    static constexpr int TM = (C::NP + TY - 1) / TY, TN = (NCB + TX - 1) / TX;
-    static constexpr int NPP = TM * TY, NCBP = TN * TX;
+    static constexpr int NTH = TY * TX;
+    // register tiles when the output tile divides evenly; otherwise a flat
+    // thread -> output map (two shared loads per DFMA are free next to the FP64 pipe)
+    static constexpr bool FLAT = (C::NP % TY) != 0 || (NCB % TX) != 0;
+    static constexpr int TM = FLAT ? 1 : C::NP / TY, TN = FLAT ? 1 : NCB / TX;
+    static constexpr int SLOTS = (C::NP * NCB + NTH - 1) / NTH;
+    static constexpr int NPP = C::NP, NCBP = NCB;
     static constexpr int main_smem = KC * (NPP + NCBP + C::NCOEF);
     static constexpr int face_smem = C::NCOEF * C::NFQ + C::NFQ * NCB;
     static constexpr int smem = main_smem > face_smem ? main_smem : face_smem;
 };
 
-template <class C, int TY, int TX, int KC>
-__global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs A) {
+template <class C, int TY, int TX, int KC, class TA, class TL>
+__global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
     constexpr int D = C::D, M = C::M, NP = C::NP, NQ = C::NQ, NF = C::NF, NFP = C::NFP, NFQ = C::NFQ;
     constexpr int NU = C::NU, NT = C::NT, LD = C::LD, NCOEF = C::NCOEF;
     using S = BlkShape<C, TY, TX, KC>;
@@ -320,106 +357,117 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs A) {
     const int b = (int)(bid % M), a = (int)((bid / M) % M);
     const int64_t el = bid / (M * M), e = A.e0 + el;
     const DeviceTables& T = A.tab;
-    extern __shared__ double sm[];
-    double* As = sm;
-    double* Bs = As + KC * NPP;
-    double* Cs = Bs + KC * NCBP;
+    extern __shared__ double sm_raw[];
+    TA* sm = reinterpret_cast<TA*>(sm_raw);
+    TA* As = sm;
+    TA* Bs = As + KC * NPP;
+    TA* Cs = Bs + KC * NCBP;
     const double* cf = A.vcoef + (((size_t)el * M + a) * M + b) * (size_t)(D * NCOEF * NQ);
 
-    double acc[TM][TN];
+    constexpr bool FLAT = S::FLAT;
+    constexpr int SL = FLAT ? S::SLOTS : TM * TN;
+    TA acc[SL];
+    int ri[SL], ci[SL];
 #pragma unroll
-    for (int ii = 0; ii < TM; ++ii)
-#pragma unroll
-        for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = 0.0;
+    for (int s = 0; s < SL; ++s) {
+        acc[s] = 0.0;
+        if (FLAT) {
+            int idx = tid + NTH * s;
+            ri[s] = idx < NP * NCB ? idx / NCB : -1;
+            ci[s] = idx < NP * NCB ? idx - (idx / NCB) * NCB : 0;
+        } else {
+            ri[s] = ty + TY * (s / TN);
+            ci[s] = tx + TX * (s % TN);
+        }
+    }
 
     for (int k0 = 0; k0 < K; k0 += KC) {
         const int kc = min(KC, K - k0);
         for (int idx = tid; idx < kc * NCOEF; idx += NTH) {
             int kk = idx / NCOEF, c = idx - kk * NCOEF, k = k0 + kk, r = k / NQ, g = k - r * NQ;
-            Cs[idx] = cf[(r * NCOEF + c) * NQ + g];
+            Cs[idx] = (TA)cf[(r * NCOEF + c) * NQ + g];
         }
-        for (int idx = tid; idx < KC * NPP; idx += NTH) {
-            int kk = idx / NPP, i = idx - kk * NPP;
-            As[idx] = (kk < kc && i < NP) ? T.dphi[(size_t)(k0 + kk) * NP + i] : 0.0;
-        }
+        for (int idx = tid; idx < kc * NPP; idx += NTH) As[idx] = (TA)T.dphi[(size_t)k0 * NP + idx];
         __syncthreads();
-        for (int idx = tid; idx < KC * NCBP; idx += NTH) {
+        for (int idx = tid; idx < kc * NCBP; idx += NTH) {
             int kk = idx / NCBP, c = idx - kk * NCBP;
-            double v = 0.0;
-            if (kk < kc && c < NCB) {
-                int k = k0 + kk, r = k / NQ, g = k - r * NQ;
-                const double* cc = Cs + kk * NCOEF;
-                if (c < NP) {
-                    v = cc[0] * T.phi[g * NP + c];
-                    for (int r2 = 0; r2 < D; ++r2) v -= cc[1 + r2] * T.psi[((size_t)r2 * NQ + g) * NP + c];
-                } else {
-                    int c2 = c - NP, f = c2 / NFP, l = c2 - f * NFP;
-                    v = cc[1 + D + f] * T.theta[((size_t)f * NQ + g) * NFP + l];
-                }
+            int k = k0 + kk, r = k / NQ, g = k - r * NQ;
+            const TA* cc = Cs + kk * NCOEF;
+            TA v;
+            if (c < NP) {
+                v = cc[0] * (TA)T.phi[g * NP + c];
+                for (int r2 = 0; r2 < D; ++r2) v -= cc[1 + r2] * (TA)T.psi[((size_t)r2 * NQ + g) * NP + c];
+            } else {
+                int c2 = c - NP, f = c2 / NFP, l = c2 - f * NFP;
+                v = cc[1 + D + f] * (TA)T.theta[((size_t)f * NQ + g) * NFP + l];
             }
             Bs[idx] = v;
         }
         __syncthreads();
-        for (int kk = 0; kk < kc; ++kk) {
-            double av[TM], bv[TN];
+        if (FLAT) {
+            for (int kk = 0; kk < kc; ++kk) {
 #pragma unroll
-            for (int ii = 0; ii < TM; ++ii) av[ii] = As[kk * NPP + ty + TY * ii];
+                for (int s = 0; s < SL; ++s)
+                    if (ri[s] >= 0) acc[s] = fma(As[kk * NPP + ri[s]], Bs[kk * NCBP + ci[s]], acc[s]);
+            }
+        } else {
+            for (int kk = 0; kk < kc; ++kk) {
+                TA av[TM], bv[TN];
 #pragma unroll
-            for (int jj = 0; jj < TN; ++jj) bv[jj] = Bs[kk * NCBP + tx + TX * jj];
+                for (int ii = 0; ii < TM; ++ii) av[ii] = As[kk * NPP + ty + TY * ii];
 #pragma unroll
-            for (int ii = 0; ii < TM; ++ii)
+                for (int jj = 0; jj < TN; ++jj) bv[jj] = Bs[kk * NCBP + tx + TX * jj];
 #pragma unroll
-                for (int jj = 0; jj < TN; ++jj) acc[ii][jj] = fma(av[ii], bv[jj], acc[ii][jj]);
+                for (int ii = 0; ii < TM; ++ii)
+#pragma unroll
+                    for (int jj = 0; jj < TN; ++jj) acc[ii * TN + jj] = fma(av[ii], bv[jj], acc[ii * TN + jj]);
+            }
         }
         __syncthreads();
     }
 
     const double* G = A.geo + e * GEO;
     const double detJ = G[0];
-    double* Tm = A.top + e * (size_t)NU * LD;
+    double* A11 = A.R.a11 + e * A.R.a11_es;
+    TL* A12 = A.R.a12 + e * A.R.a12_es;
 #pragma unroll
-    for (int ii = 0; ii < TM; ++ii) {
-        int i = ty + TY * ii;
-        if (i >= NP) continue;
-#pragma unroll
-        for (int jj = 0; jj < TN; ++jj) {
-            int c = tx + TX * jj;
-            if (c >= NCB) continue;
-            int col;
-            double v = acc[ii][jj];
-            if (c < NP) {
-                col = b * NP + c;
-                if (a == b) v += detJ / A.a_ii * T.mhat[i * NP + c];
-            } else {
-                int c2 = c - NP, f = c2 / NFP, l = c2 - f * NFP;
-                col = NU + (f * M + b) * NFP + l;
-            }
-            Tm[(size_t)(a * NP + i) * LD + col] = v;
+    for (int s = 0; s < SL; ++s) {
+        const int i = ri[s], c = ci[s];
+        if (i < 0 || i >= NP || c >= NCB) continue;
+        const int64_t row = a * NP + i;
+        if (c < NP) {
+            double v = (double)acc[s];
+            if (a == b) v += detJ / A.a_ii * T.mhat[i * NP + c];
+            A11[row * A.R.a11_rs + b * NP + c] = v;
+        } else {
+            int c2 = c - NP, f = c2 / NFP, l = c2 - f * NFP;
+            A12[row * A.R.a12_rs + (f * M + b) * NFP + l] = (TL)acc[s];
         }
     }
     __syncthreads();
 
     // face terms: rows of Ct / Dt, and dt x the same rows added to At / Bt at the face nodes
-    double* Bm = A.bot + el * (size_t)NT * LD;
-    double* Fc = sm;                       // [NCOEF][Nfq]
-    double* Tt = Fc + NCOEF * NFQ;         // [Nfq][NCB]
+    TL* A21 = A.R.a21 + el * A.R.a21_es;
+    TL* A22 = A.R.a22 + el * A.R.a22_es;
+    TA* Fc = sm;                           // [NCOEF][Nfq]
+    TA* Tt = Fc + NCOEF * NFQ;             // [Nfq][NCB]
     const double* NW = G + 1 + D * D;
     const double* Jg = G + 1;
     (void)Jg;
     for (int f = 0; f < NF; ++f) {
         const double* fsrc = A.fcoef + ((((size_t)el * NF + f) * M + a) * M + b) * (size_t)(NCOEF * NFQ);
-        for (int idx = tid; idx < NCOEF * NFQ; idx += NTH) Fc[idx] = fsrc[idx];
+        for (int idx = tid; idx < NCOEF * NFQ; idx += NTH) Fc[idx] = (TA)fsrc[idx];
         __syncthreads();
         for (int idx = tid; idx < NFQ * NCB; idx += NTH) {
             int s = idx / NCB, c = idx - s * NCB;
-            double v = 0.0;
+            TA v = 0;
             if (c < NP) {
                 for (int r2 = 0; r2 < D; ++r2)
-                    v -= Fc[(1 + r2) * NFQ + s] * T.psi_f[(((size_t)f * D + r2) * NFQ + s) * NP + c];
+                    v -= Fc[(1 + r2) * NFQ + s] * (TA)T.psi_f[(((size_t)f * D + r2) * NFQ + s) * NP + c];
             } else {
                 int c2 = c - NP, f2 = c2 / NFP, l2 = c2 - f2 * NFP;
-                v = Fc[(1 + D + f2) * NFQ + s] * T.theta_f[(((size_t)f * NF + f2) * NFQ + s) * NFP + l2];
-                if (f2 == f) v += Fc[s] * T.mu[s * NFP + l2];
+                v = Fc[(1 + D + f2) * NFQ + s] * (TA)T.theta_f[(((size_t)f * NF + f2) * NFQ + s) * NFP + l2];
+                if (f2 == f) v += Fc[s] * (TA)T.mu[s * NFP + l2];
             }
             Tt[idx] = v;
         }
@@ -429,24 +477,27 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs A) {
         nrm = sqrt(nrm);
         for (int idx = tid; idx < NFP * NCB; idx += NTH) {
             int lam = idx / NCB, c = idx - lam * NCB;
-            double v = 0.0;
-            for (int s = 0; s < NFQ; ++s) v += T.mu[s * NFP + lam] * Tt[s * NCB + c];
-            int col;
+            TA vs = 0;
+            for (int s = 0; s < NFQ; ++s) vs += (TA)T.mu[s * NFP + lam] * Tt[s * NCB + c];
+            double v = (double)vs;
+            const int64_t trow = (f * M + a) * NFP + lam;
+            const int64_t irow = a * NP + T.fnode[f * NFP + lam];
             if (c < NP) {
-                col = b * NP + c;
                 if (a == b) {
                     for (int k = 0; k < D; ++k) {
                         int nfc = T.node_face[c * D + k];
                         if (nfc >= 0 && nfc / NFP == f) v += A.tau * nrm * T.mf[lam * NFP + (nfc - f * NFP)];
                     }
                 }
+                const int col = b * NP + c;
+                A21[trow * A.R.a21_rs + col] = (TL)v;
+                A11[irow * A.R.a11_rs + col] += A.dt * v;
             } else {
                 int c2 = c - NP, f2 = c2 / NFP, l2 = c2 - f2 * NFP;
-                col = NU + (f2 * M + b) * NFP + l2;
+                const int col = (f2 * M + b) * NFP + l2;
+                A22[trow * A.R.a22_rs + col] = (TL)v;
+                A12[irow * A.R.a12_rs + col] = (TL)((double)A12[irow * A.R.a12_rs + col] + A.dt * v);
             }
-            Bm[(size_t)((f * M + a) * NFP + lam) * LD + col] = v;
-            double* t = Tm + (size_t)(a * NP + T.fnode[f * NFP + lam]) * LD + col;
-            *t += A.dt * v;
         }
         __syncthreads();
     }
@@ -455,11 +506,52 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs A) {
 // ----------------------------------------------------------------------------
 // A3 + A4: bordered Gaussian elimination (interior LU, solves and Schur complement)
 // ----------------------------------------------------------------------------
+// One 64 x 64 (or smaller, NII / NJJ groups of 16) tile of the trailing
+// update A22 -= L21 U12: thread (tx, ty) owns rows rb + ty + 16 ii and
+// columns ct + tx + 16 jj.
+template <int NII, int NJJ, int NB, int NR, int NC, int TCW, class RowP>
+__device__ __forceinline__ void trail_tile(RowP rowp, const double* pan, const double* ust, int rb, int ct, int k0,
+                                           int kb, int tx, int ty) {
+    double acc[NII][NJJ];
+    double* rp[NII];
+#pragma unroll
+    for (int ii = 0; ii < NII; ++ii) {
+        int r = rb + ty + 16 * ii;
+        rp[ii] = (r < NR) ? rowp(r) : nullptr;
+#pragma unroll
+        for (int jj = 0; jj < NJJ; ++jj) {
+            int c = ct + tx + 16 * jj;
+            acc[ii][jj] = (rp[ii] && c < NC) ? rp[ii][c] : 0.0;
+        }
+    }
+    const double* lp = pan + (size_t)(rb + ty - k0) * NB;
+    for (int j = 0; j < kb; ++j) {
+        double lv[NII], uv[NJJ];
+#pragma unroll
+        for (int ii = 0; ii < NII; ++ii) lv[ii] = (rb + ty + 16 * ii < NR) ? lp[16 * ii * NB + j] : 0.0;
+#pragma unroll
+        for (int jj = 0; jj < NJJ; ++jj) uv[jj] = ust[j * TCW + tx + 16 * jj];
+#pragma unroll
+        for (int ii = 0; ii < NII; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < NJJ; ++jj) acc[ii][jj] = fma(-lv[ii], uv[jj], acc[ii][jj]);
+    }
+#pragma unroll
+    for (int ii = 0; ii < NII; ++ii) {
+        if (!rp[ii]) continue;
+#pragma unroll
+        for (int jj = 0; jj < NJJ; ++jj) {
+            int c = ct + tx + 16 * jj;
+            if (c < NC) rp[ii][c] = acc[ii][jj];
+        }
+    }
+}
+
 template <class C, int NB>
 constexpr int elim_smem_doubles() { return C::NR * NB + NB * 64; }
 
-template <class C, int NB, int NTH>
-__global__ void __launch_bounds__(NTH) k_elim(double* top, double* bot, int64_t e0, int32_t* status) {
+template <class C, int NB, int NTH, int MINB>
+__global__ void __launch_bounds__(NTH, MINB) k_elim(double* top, double* bot, int64_t e0, int32_t* status) {
     constexpr int NU = C::NU, NR = C::NR, NC = C::NC, LD = C::LD;
     constexpr int TCW = 64;                 // column tile of the trailing update
     static_assert(NTH == 256, "trailing-update layout assumes 256 threads");
@@ -479,6 +571,7 @@ __global__ void __launch_bounds__(NTH) k_elim(double* top, double* bot, int64_t 
 
     for (int k0 = 0; k0 < NU; k0 += NB) {
         const int kb = min(NB, NU - k0), nrows = NR - k0, ntop = NU - k0;
+#pragma unroll 1
         for (int idx = tid; idx < nrows * kb; idx += NTH) {
             int rr = idx / kb, c = idx - rr * kb;
             pan[rr * NB + c] = rowp(k0 + rr)[k0 + c];
@@ -487,6 +580,7 @@ __global__ void __launch_bounds__(NTH) k_elim(double* top, double* bot, int64_t 
         for (int j = 0; j < kb; ++j) {
             double bv = -1.0;
             int bi = INT_MAX;
+#pragma unroll 1
             for (int rr = j + tid; rr < ntop; rr += NTH) {
                 double v = fabs(pan[rr * NB + j]);
                 if (v > bv) { bv = v; bi = rr; }
@@ -521,6 +615,7 @@ __global__ void __launch_bounds__(NTH) k_elim(double* top, double* bot, int64_t 
                 pv = 1.0;
             }
             const double inv = 1.0 / pv;
+#pragma unroll 1
             for (int rr = j + 1 + tid; rr < nrows; rr += NTH) {
                 double l = pan[rr * NB + j] * inv;
                 pan[rr * NB + j] = l;
@@ -528,12 +623,14 @@ __global__ void __launch_bounds__(NTH) k_elim(double* top, double* bot, int64_t 
             }
             __syncthreads();
         }
+#pragma unroll 1
         for (int idx = tid; idx < nrows * kb; idx += NTH) {
             int rr = idx / kb, c = idx - rr * kb;
             rowp(k0 + rr)[k0 + c] = pan[rr * NB + c];
         }
         // trailing columns: row swaps and U12 = L11^{-1} A12 (each thread owns columns)
         const int c0 = k0 + kb;
+#pragma unroll 1
         for (int c = c0 + tid; c < NC; c += NTH) {
             for (int j = 0; j < kb; ++j) {
                 int pr = piv[j];
@@ -559,47 +656,27 @@ __global__ void __launch_bounds__(NTH) k_elim(double* top, double* bot, int64_t 
         __syncthreads();
         // trailing update A22 -= L21 U12 on rows [c0, NR) x cols [c0, NC)
         const int tx = tid & 15, ty = tid >> 4;
+#pragma unroll 1
         for (int ct = c0; ct < NC; ct += TCW) {
             for (int idx = tid; idx < kb * TCW; idx += NTH) {
                 int j = idx / TCW, cc = idx - j * TCW;
                 ust[j * TCW + cc] = (ct + cc < NC) ? rowp(k0 + j)[ct + cc] : 0.0;
             }
             __syncthreads();
+            int njj = 0;                       // column groups of 16 inside the matrix (warp-uniform)
+            while (njj < 4 && ct + 16 * njj < NC) ++njj;
+#pragma unroll 1
             for (int rb = c0; rb < NR; rb += 64) {
-                double acc[4][4];
-                double* rp[4];
-#pragma unroll
-                for (int ii = 0; ii < 4; ++ii) {
-                    int r = rb + ty + 16 * ii;
-                    rp[ii] = (r < NR) ? rowp(r) : nullptr;
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        int c = ct + tx + 16 * jj;
-                        acc[ii][jj] = (rp[ii] && c < NC) ? rp[ii][c] : 0.0;
-                    }
-                }
-                for (int j = 0; j < kb; ++j) {
-                    double lv[4], uv[4];
-#pragma unroll
-                    for (int ii = 0; ii < 4; ++ii) {
-                        int r = rb + ty + 16 * ii;
-                        lv[ii] = (r < NR) ? pan[(r - k0) * NB + j] : 0.0;
-                    }
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) uv[jj] = ust[j * TCW + tx + 16 * jj];
-#pragma unroll
-                    for (int ii = 0; ii < 4; ++ii)
-#pragma unroll
-                        for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fma(-lv[ii], uv[jj], acc[ii][jj]);
-                }
-#pragma unroll
-                for (int ii = 0; ii < 4; ++ii) {
-                    if (!rp[ii]) continue;
-#pragma unroll
-                    for (int jj = 0; jj < 4; ++jj) {
-                        int c = ct + tx + 16 * jj;
-                        if (c < NC) rp[ii][c] = acc[ii][jj];
-                    }
+                int nii = 0;                   // row groups of 16 inside the matrix (warp-uniform)
+                while (nii < 4 && rb + 16 * nii < NR) ++nii;
+                switch (nii * 4 + njj - 5) {
+#define HDG_TT(I, J) case (I) * 4 + (J) - 5: trail_tile<I, J, NB, NR, NC, TCW>(rowp, pan, ust, rb, ct, k0, kb, tx, ty); break;
+                    HDG_TT(1, 1) HDG_TT(1, 2) HDG_TT(1, 3) HDG_TT(1, 4)
+                    HDG_TT(2, 1) HDG_TT(2, 2) HDG_TT(2, 3) HDG_TT(2, 4)
+                    HDG_TT(3, 1) HDG_TT(3, 2) HDG_TT(3, 3) HDG_TT(3, 4)
+                    HDG_TT(4, 1) HDG_TT(4, 2) HDG_TT(4, 3) HDG_TT(4, 4)
+#undef HDG_TT
+                    default: break;
                 }
             }
             __syncthreads();
@@ -795,24 +872,29 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
     using C = Cfg<D, P>;
     using BC = BlkCfg<C>;
     using BS_ = BlkShape<C, BC::TY, BC::TX, BC::KC>;
+    auto kblk = k_blocks<C, BC::TY, BC::TX, BC::KC, double, double>;
     constexpr int PT = 128, NB = 16;
     const size_t sm_point = sizeof(double) * point_smem_doubles<C>();
     const size_t sm_blk = sizeof(double) * BS_::smem;
     const size_t sm_elim = sizeof(double) * elim_smem_doubles<C, NB>();
     HDG_CK(cudaFuncSetAttribute(k_point<C, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_point));
-    HDG_CK(cudaFuncSetAttribute(k_blocks<C, BC::TY, BC::TX, BC::KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
-    HDG_CK(cudaFuncSetAttribute(k_elim<C, NB, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
+    HDG_CK(cudaFuncSetAttribute(kblk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
+    HDG_CK(cudaFuncSetAttribute(k_elim<C, NB, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
+    HDG_CK(cudaFuncSetAttribute(k_elim<C, NB, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
     cudaStream_t st = h->stream;
     HDG_CK(cudaMemsetAsync(h->d_vals, 0, sizeof(double) * h->nnzb * C::BS * C::BS, st));
     HDG_CK(cudaMemsetAsync(h->d_g, 0, sizeof(double) * h->F * C::BS, st));
     PointArgs pa;
     pa.U = la.U; pa.Q = la.Q; pa.UH = la.UH; pa.Ustar = la.Ustar; pa.nu = la.nu;
     pa.dt = la.dt; pa.a_ii = la.a_ii; pa.ph = h->phys; pa.tab = h->tab; pa.geo = h->d_geo;
-    pa.e2f = h->d_e2f; pa.perm = h->d_perm; pa.top = h->d_top; pa.bot = h->d_bot;
+    const Regions<double> RG = fp64_regions<C>(h->d_top, h->d_bot);
+    pa.e2f = h->d_e2f; pa.perm = h->d_perm;
+    pa.rt = RG.rt; pa.rt_es = RG.rt_es; pa.rt_rs = RG.rt_rs;
+    pa.rb = RG.rb; pa.rb_es = RG.rb_es; pa.rb_rs = RG.rb_rs;
     pa.vcoef = h->d_vcoef; pa.fcoef = h->d_fcoef; pa.dq0 = h->d_dq0;
-    BlkArgs ba;
+    BlkArgs<double> ba;
     ba.vcoef = h->d_vcoef; ba.fcoef = h->d_fcoef; ba.geo = h->d_geo; ba.tab = h->tab;
-    ba.top = h->d_top; ba.bot = h->d_bot; ba.dt = la.dt; ba.a_ii = la.a_ii; ba.tau = h->phys.tau;
+    ba.R = RG; ba.dt = la.dt; ba.a_ii = la.a_ii; ba.tau = h->phys.tau;
     for (int64_t e0 = 0; e0 < h->E; e0 += h->chunk) {
         const int64_t ne = std::min<int64_t>(h->chunk, h->E - e0);
         pa.e0 = e0; ba.e0 = e0;
@@ -820,10 +902,13 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
         k_point<C, PT><<<(unsigned)ne, PT, sm_point, st>>>(pa);
         prof_end(h);
         prof_begin(h, HDG_K_BLOCKS);
-        k_blocks<C, BC::TY, BC::TX, BC::KC><<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
+        kblk<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
         prof_end(h);
         prof_begin(h, HDG_K_ELIM);
-        k_elim<C, NB, 256><<<(unsigned)ne, 256, sm_elim, st>>>(h->d_top, h->d_bot, e0, h->d_status);
+        if (h->elim_minb == 1)
+            k_elim<C, NB, 256, 1><<<(unsigned)ne, 256, sm_elim, st>>>(h->d_top, h->d_bot, e0, h->d_status);
+        else
+            k_elim<C, NB, 256, 2><<<(unsigned)ne, 256, sm_elim, st>>>(h->d_top, h->d_bot, e0, h->d_status);
         prof_end(h);
         for (int pass = 0; pass < 2; ++pass) {
             prof_begin(h, HDG_K_ASSEMBLE);
@@ -838,22 +923,20 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
         HDG_CK(cudaGetLastError());
     }
     h->have_system = true;
+    h->sys_prec = HDG_PREC_FP64;
+    h->bj_ready = false;
     return HDG_OK;
 }
 
 template <int D, int P>
-int run_matvec(hdg_ctx* h, const double* x, double* y) {
-    using C = Cfg<D, P>;
-    prof_begin(h, HDG_K_MATVEC);
-    k_matvec<C><<<(unsigned)h->F, MvShape<C>::NTH, 0, h->stream>>>(h->d_rowptr, h->d_col, h->d_vals, x, y);
-    prof_end(h);
-    HDG_CK(cudaGetLastError());
-    return HDG_OK;
-}
+int run_matvec(hdg_ctx* h, const double* x, double* y);
+template <int D, int P>
+int run_recover_mixed(hdg_ctx* h, const double* dUH, double* dQ, double* dU);
 
 template <int D, int P>
 int run_recover(hdg_ctx* h, const double* dUH, double* dQ, double* dU) {
     using C = Cfg<D, P>;
+    if (h->sys_prec == HDG_PREC_MIXED) return run_recover_mixed<D, P>(h, dUH, dQ, dU);
     RecArgs ra;
     ra.top = h->d_top; ra.dq0 = h->d_dq0; ra.geo = h->d_geo; ra.tab = h->tab;
     ra.e2f = h->d_e2f; ra.perm = h->d_perm; ra.dUH = dUH; ra.dQ = dQ; ra.dU = dU;

@@ -1,0 +1,779 @@
+// Mixed-precision condensation.  The interior block At and both right-hand
+// sides stay in FP64 and At is factored with partial pivoting in FP64; the
+// blocks Bt, Ct, Dt and the condensed trace blocks are FP32.
+//
+// k_elim_mixed runs the bordered elimination of k_elim on the FP64 part and
+// the two FP32 off-diagonal regions, but does not touch Dt: after the last
+// panel the interior rows hold [U | Z = L^{-1} P Bt | z = L^{-1} P Rt] and the
+// trace rows' multipliers W = Ct U^{-1}, so that the Schur complement is one
+// product S^K = Dt - W Z (K = n_u) and -g^K = Rh - W z, left to k_schur_*.
+#pragma once
+
+#include "kernels.cuh"
+
+namespace hdg {
+
+// one (up to) 64 x 64 tile of A22 -= L21 U12 in type T; rows/cols >= r_end/c_end skipped
+template <int NII, int NJJ, int NB, int TCW, class T, class RowP>
+__device__ __forceinline__ void trail_tile_t(RowP rowp, const double* pan, const T* ust, int rb, int ct, int k0,
+                                             int kb, int tx, int ty, int r_end, int c_end) {
+    T acc[NII][NJJ];
+    T* rp[NII];
+#pragma unroll
+    for (int ii = 0; ii < NII; ++ii) {
+        int r = rb + ty + 16 * ii;
+        rp[ii] = (r < r_end) ? rowp(r) : nullptr;
+#pragma unroll
+        for (int jj = 0; jj < NJJ; ++jj) {
+            int c = ct + tx + 16 * jj;
+            acc[ii][jj] = (rp[ii] && c < c_end) ? rp[ii][c] : T(0);
+        }
+    }
+    for (int j = 0; j < kb; ++j) {
+        T lv[NII], uv[NJJ];
+#pragma unroll
+        for (int ii = 0; ii < NII; ++ii) {
+            int r = rb + ty + 16 * ii;
+            lv[ii] = (r < r_end) ? (T)pan[(size_t)(r - k0) * NB + j] : T(0);
+        }
+#pragma unroll
+        for (int jj = 0; jj < NJJ; ++jj) uv[jj] = ust[j * TCW + tx + 16 * jj];
+#pragma unroll
+        for (int ii = 0; ii < NII; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < NJJ; ++jj) acc[ii][jj] = fma(-lv[ii], uv[jj], acc[ii][jj]);
+    }
+#pragma unroll
+    for (int ii = 0; ii < NII; ++ii) {
+        if (!rp[ii]) continue;
+#pragma unroll
+        for (int jj = 0; jj < NJJ; ++jj) {
+            int c = ct + tx + 16 * jj;
+            if (c < c_end) rp[ii][c] = acc[ii][jj];
+        }
+    }
+}
+
+// trailing update of one storage region: rows [r_begin, r_end) (absolute bordered
+// rows, rowp(r) gives the region row), columns [0, c_end) of the region with U12
+// row j at urow(j)
+template <class T, int NB, int NTH, class RowP, class URow>
+__device__ void trailing_region(RowP rowp, URow urow, int r_begin, int r_end, int c_begin, int c_end,
+                                const double* pan, int k0, int kb, T* ust) {
+    constexpr int TCW = 64;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+#pragma unroll 1
+    for (int ct = c_begin; ct < c_end; ct += TCW) {
+        for (int idx = tid; idx < kb * TCW; idx += NTH) {
+            int j = idx / TCW, cc = idx - j * TCW;
+            ust[j * TCW + cc] = (ct + cc < c_end) ? (T)urow(j)[ct + cc] : T(0);
+        }
+        __syncthreads();
+        int njj = 0;
+        while (njj < 4 && ct + 16 * njj < c_end) ++njj;
+#pragma unroll 1
+        for (int rb = r_begin; rb < r_end; rb += 64) {
+            int nii = 0;
+            while (nii < 4 && rb + 16 * nii < r_end) ++nii;
+            switch (nii * 4 + njj - 5) {
+#define HDG_TT(I, J) case (I) * 4 + (J) - 5: trail_tile_t<I, J, NB, TCW, T>(rowp, pan, ust, rb, ct, k0, kb, tx, ty, r_end, c_end); break;
+                HDG_TT(1, 1) HDG_TT(1, 2) HDG_TT(1, 3) HDG_TT(1, 4)
+                HDG_TT(2, 1) HDG_TT(2, 2) HDG_TT(2, 3) HDG_TT(2, 4)
+                HDG_TT(3, 1) HDG_TT(3, 2) HDG_TT(3, 3) HDG_TT(3, 4)
+                HDG_TT(4, 1) HDG_TT(4, 2) HDG_TT(4, 3) HDG_TT(4, 4)
+#undef HDG_TT
+                default: break;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <class C, int NB>
+constexpr int elim_mixed_smem_bytes() { return (C::NR * NB + NB * 64) * 8 + NB * 64 * 4; }
+
+template <class C, int NB, int NTH>
+__global__ void __launch_bounds__(NTH, 1) k_elim_mixed(Regions<float> R, int64_t e0, int32_t* status) {
+    constexpr int NU = C::NU, NT = C::NT, NR = C::NR;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t el = blockIdx.x, e = e0 + el;
+    double* A11 = R.a11 + e * R.a11_es;
+    float* A12 = R.a12 + e * R.a12_es;
+    float* A21 = R.a21 + el * R.a21_es;
+    double* rt = R.rt + e * R.rt_es;
+    const int64_t s11 = R.a11_rs, s12 = R.a12_rs, s21 = R.a21_rs, srt = R.rt_rs;
+    extern __shared__ double sm[];
+    double* pan = sm;                              // [NR][NB]
+    double* ust64 = pan + NR * NB;                 // [NB][64]
+    float* ust32 = reinterpret_cast<float*>(ust64 + NB * 64);
+    __shared__ int piv[NB];
+    __shared__ double rv[NTH / 32];
+    __shared__ int ri[NTH / 32];
+    __shared__ int sflag;
+    if (tid == 0) sflag = 0;
+
+    for (int k0 = 0; k0 < NU; k0 += NB) {
+        const int kb = min(NB, NU - k0), nrows = NR - k0, ntop = NU - k0;
+#pragma unroll 1
+        for (int idx = tid; idx < nrows * kb; idx += NTH) {
+            int rr = idx / kb, c = idx - rr * kb, r = k0 + rr;
+            pan[rr * NB + c] = r < NU ? A11[r * s11 + k0 + c] : (double)A21[(r - NU) * s21 + k0 + c];
+        }
+        __syncthreads();
+        for (int j = 0; j < kb; ++j) {
+            double bv = -1.0;
+            int bi = INT_MAX;
+#pragma unroll 1
+            for (int rr = j + tid; rr < ntop; rr += NTH) {
+                double v = fabs(pan[rr * NB + j]);
+                if (v > bv) { bv = v; bi = rr; }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                double ov = __shfl_down_sync(0xffffffffu, bv, off);
+                int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            }
+            if (lane == 0) { rv[warp] = bv; ri[warp] = bi; }
+            __syncthreads();
+            if (tid == 0) {
+                double b2 = rv[0];
+                int i2 = ri[0];
+                for (int w = 1; w < NTH / 32; ++w)
+                    if (rv[w] > b2 || (rv[w] == b2 && ri[w] < i2)) { b2 = rv[w]; i2 = ri[w]; }
+                if (i2 == INT_MAX) { i2 = j; sflag |= 2; }
+                piv[j] = i2;
+            }
+            __syncthreads();
+            const int pr = piv[j];
+            if (pr != j)
+                for (int c = tid; c < kb; c += NTH) {
+                    double t = pan[j * NB + c];
+                    pan[j * NB + c] = pan[pr * NB + c];
+                    pan[pr * NB + c] = t;
+                }
+            __syncthreads();
+            double pv = pan[j * NB + j];
+            if (pv == 0.0 || !isfinite(pv)) {
+                if (tid == 0) sflag |= (pv == 0.0) ? 1 : 2;
+                pv = 1.0;
+            }
+            const double inv = 1.0 / pv;
+#pragma unroll 1
+            for (int rr = j + 1 + tid; rr < nrows; rr += NTH) {
+                double l = pan[rr * NB + j] * inv;
+                pan[rr * NB + j] = l;
+                for (int c = j + 1; c < kb; ++c) pan[rr * NB + c] = fma(-l, pan[j * NB + c], pan[rr * NB + c]);
+            }
+            __syncthreads();
+        }
+#pragma unroll 1
+        for (int idx = tid; idx < nrows * kb; idx += NTH) {
+            int rr = idx / kb, c = idx - rr * kb, r = k0 + rr;
+            if (r < NU) A11[r * s11 + k0 + c] = pan[rr * NB + c];
+            else A21[(r - NU) * s21 + k0 + c] = (float)pan[rr * NB + c];
+        }
+        // trailing columns of the interior rows: swaps and U12 = L11^{-1} A12,
+        // columns [c0, NU) of At, all columns of Bt, and Rt
+        const int c0 = k0 + kb;
+        const int ncols = (NU - c0) + NT + 1;
+#pragma unroll 1
+        for (int cc = tid; cc < ncols; cc += NTH) {
+            const int kind = cc < NU - c0 ? 0 : (cc < NU - c0 + NT ? 1 : 2);
+            auto at = [&](int r) -> double {
+                if (kind == 0) return A11[r * s11 + c0 + cc];
+                if (kind == 1) return (double)A12[r * s12 + (cc - (NU - c0))];
+                return rt[r * srt];
+            };
+            auto put = [&](int r, double v) {
+                if (kind == 0) A11[r * s11 + c0 + cc] = v;
+                else if (kind == 1) A12[r * s12 + (cc - (NU - c0))] = (float)v;
+                else rt[r * srt] = v;
+            };
+            for (int j = 0; j < kb; ++j) {
+                int pr = piv[j];
+                if (pr != j) {
+                    double x = at(k0 + j), y = at(k0 + pr);
+                    put(k0 + j, y);
+                    put(k0 + pr, x);
+                }
+            }
+            double xv[NB];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                if (j < kb) {
+                    double s = at(k0 + j);
+#pragma unroll
+                    for (int i = 0; i < NB; ++i)
+                        if (i < j) s = fma(-pan[j * NB + i], xv[i], s);
+                    xv[j] = s;
+                    put(k0 + j, s);
+                }
+            }
+        }
+        __syncthreads();
+        // At (FP64): rows [c0, NU) x cols [c0, NU)
+        trailing_region<double, NB, NTH>([&](int r) { return A11 + r * s11; },
+                                         [&](int j) { return (const double*)(A11 + (k0 + j) * s11); },
+                                         c0, NU, c0, NU, pan, k0, kb, ust64);
+        // Ct multipliers (FP32): rows [NU, NR) x cols [c0, NU)
+        trailing_region<float, NB, NTH>([&](int r) { return A21 + (r - NU) * s21; },
+                                        [&](int j) { return (const double*)(A11 + (k0 + j) * s11); },
+                                        NU, NR, c0, NU, pan, k0, kb, ust32);
+        // Bt (FP32): rows [c0, NU) x all t columns
+        trailing_region<float, NB, NTH>([&](int r) { return A12 + r * s12; },
+                                        [&](int j) { return (const float*)(A12 + (k0 + j) * s12); },
+                                        c0, NU, 0, NT, pan, k0, kb, ust32);
+        // Rt (FP64): rows [c0, NU)
+#pragma unroll 1
+        for (int r = c0 + tid; r < NU; r += NTH) {
+            double s = rt[r * srt];
+            for (int j = 0; j < kb; ++j) s = fma(-pan[(r - k0) * NB + j], rt[(k0 + j) * srt], s);
+            rt[r * srt] = s;
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && sflag) atomicOr(status, sflag);
+}
+
+// S^K = Dt - W Z (in place over Dt) and Rh <- Rh - W z, FP32 SIMT with FP32
+// accumulation (W [t][n_u] = Ct region, Z [n_u][t] = Bt region after k_elim_mixed)
+template <class C, int NTH>
+__global__ void __launch_bounds__(NTH) k_schur_simt(Regions<float> R, int64_t e0) {
+    constexpr int NU = C::NU, NT = C::NT, KC = 32, TW = 64;
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t el = blockIdx.x, e = e0 + el;
+    const float* W = R.a21 + el * R.a21_es;
+    const float* Z = R.a12 + e * R.a12_es;
+    float* Dm = R.a22 + el * R.a22_es;
+    const double* z = R.rt + e * R.rt_es;
+    double* rb = R.rb + el * R.rb_es;
+    const int64_t sw = R.a21_rs, sz = R.a12_rs, sd = R.a22_rs;
+    __shared__ float Ws[TW][KC + 1];
+    __shared__ float Zs[KC][TW];
+    // right-hand side: rb -= W z (FP64 accumulation)
+    for (int r = tid; r < NT; r += NTH) {
+        double s = rb[r * R.rb_rs];
+        for (int k = 0; k < NU; ++k) s -= (double)W[r * sw + k] * z[k * R.rt_rs];
+        rb[r * R.rb_rs] = s;
+    }
+    for (int rt0 = 0; rt0 < NT; rt0 += TW)
+        for (int ct0 = 0; ct0 < NT; ct0 += TW) {
+            float acc[4][4];
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = 0.f;
+            for (int k0 = 0; k0 < NU; k0 += KC) {
+                for (int idx = tid; idx < TW * KC; idx += NTH) {
+                    int r = idx / KC, k = idx - r * KC;
+                    Ws[r][k] = (rt0 + r < NT && k0 + k < NU) ? W[(rt0 + r) * sw + k0 + k] : 0.f;
+                    int k2 = idx / TW, c = idx - k2 * TW;
+                    Zs[k2][c] = (k0 + k2 < NU && ct0 + c < NT) ? Z[(k0 + k2) * sz + ct0 + c] : 0.f;
+                }
+                __syncthreads();
+#pragma unroll 8
+                for (int k = 0; k < KC; ++k) {
+                    float a[4], b[4];
+#pragma unroll
+                    for (int ii = 0; ii < 4; ++ii) a[ii] = Ws[ty + 16 * ii][k];
+#pragma unroll
+                    for (int jj = 0; jj < 4; ++jj) b[jj] = Zs[k][tx + 16 * jj];
+#pragma unroll
+                    for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fmaf(a[ii], b[jj], acc[ii][jj]);
+                }
+                __syncthreads();
+            }
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii) {
+                int r = rt0 + ty + 16 * ii;
+                if (r >= NT) continue;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) {
+                    int c = ct0 + tx + 16 * jj;
+                    if (c < NT) Dm[r * sd + c] -= acc[ii][jj];
+                }
+            }
+        }
+}
+
+// assembly from region views (S^K in Dt, -g^K in Rh) into BSR blocks of type TL
+template <class C, class TL>
+__global__ void k_assemble_r(Regions<TL> R, int64_t e0, const int32_t* blk, const int32_t* rank,
+                             const int32_t* iperm, TL* vals, int pass) {
+    constexpr int M = C::M, NF = C::NF, NFP = C::NFP, BS = C::BS;
+    const int64_t bid = blockIdx.x;
+    const int gl = (int)(bid % NF), fl = (int)((bid / NF) % NF);
+    const int64_t el = bid / (NF * NF), e = e0 + el;
+    const size_t item = ((size_t)e * NF + fl) * NF + gl;
+    if (rank[item] != pass) return;
+    TL* out = vals + (size_t)blk[item] * BS * BS;
+    const TL* S = R.a22 + el * R.a22_es;
+    const int32_t* ipf = iperm + ((size_t)e * NF + fl) * NFP;
+    const int32_t* ipg = iperm + ((size_t)e * NF + gl) * NFP;
+    for (int idx = threadIdx.x; idx < BS * BS; idx += blockDim.x) {
+        int c = idx / BS, r = idx - c * BS;
+        int a = r / NFP, k = r - a * NFP, b2 = c / NFP, k2 = c - b2 * NFP;
+        int row = (fl * M + a) * NFP + ipf[k];
+        int col = (gl * M + b2) * NFP + ipg[k2];
+        out[idx] += S[(size_t)row * R.a22_rs + col];
+    }
+}
+
+template <class C, class TL>
+__global__ void k_assemble_g_r(Regions<TL> R, int64_t e0, const int32_t* e2f, const int32_t* frank,
+                               const int32_t* iperm, double* g, int pass) {
+    constexpr int M = C::M, NF = C::NF, NFP = C::NFP, BS = C::BS;
+    const int64_t bid = blockIdx.x;
+    const int fl = (int)(bid % NF);
+    const int64_t el = bid / NF, e = e0 + el;
+    if (frank[e * NF + fl] != pass) return;
+    const int64_t F = e2f[e * NF + fl];
+    const double* rb = R.rb + el * R.rb_es;
+    const int32_t* ipf = iperm + ((size_t)e * NF + fl) * NFP;
+    for (int idx = threadIdx.x; idx < BS; idx += blockDim.x) {
+        int a = idx / NFP, k = idx - a * NFP;
+        int row = (fl * M + a) * NFP + ipf[k];
+        g[F * BS + idx] -= rb[row * R.rb_rs];
+    }
+}
+
+// y = S x with blocks of type TL, FP64 vectors and accumulation
+template <class C, class TL>
+__global__ void __launch_bounds__(MvShape<C>::NTH) k_matvec_t(const int32_t* rowptr, const int32_t* col,
+                                                              const TL* vals, const double* x, double* y) {
+    constexpr int BS = C::BS, RB = MvShape<C>::RB, GROUPS = MvShape<C>::GROUPS;
+    __shared__ double part[GROUPS][RB];
+    const int64_t F = blockIdx.x;
+    const int grp = threadIdx.x / RB, r = threadIdx.x - grp * RB;
+    double acc0 = 0.0, acc1 = 0.0;
+    if (r < BS) {
+        for (int b = rowptr[F] + grp; b < rowptr[F + 1]; b += GROUPS) {
+            const double* xs = x + (size_t)col[b] * BS;
+            const TL* v = vals + (size_t)b * BS * BS + r;
+            int c = 0;
+#pragma unroll 4
+            for (; c + 1 < BS; c += 2) {
+                acc0 = fma((double)v[(size_t)c * BS], xs[c], acc0);
+                acc1 = fma((double)v[(size_t)(c + 1) * BS], xs[c + 1], acc1);
+            }
+            if (c < BS) acc0 = fma((double)v[(size_t)c * BS], xs[c], acc0);
+        }
+    }
+    part[grp][r] = acc0 + acc1;
+    __syncthreads();
+    if (grp == 0 && r < BS) {
+        double s = part[0][r];
+        for (int g2 = 1; g2 < GROUPS; ++g2) s += part[g2][r];
+        y[F * BS + r] = s;
+    }
+}
+
+// recovery from region views: dU = -U^{-1}(z + Z dUhat), dQ = dq0 - L dU + Lambda dUhat
+template <class C, class TL, int NTH>
+__global__ void __launch_bounds__(NTH) k_recover_r(Regions<TL> R, RecArgs A) {
+    constexpr int D = C::D, M = C::M, NP = C::NP, NF = C::NF, NFP = C::NFP;
+    constexpr int NU = C::NU, NQV = C::NQV, NT = C::NT;
+    constexpr int GEO = Geo<D>::N;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t e = blockIdx.x;
+    __shared__ double duh[NT];
+    __shared__ double w[NU];
+    __shared__ double x[NU];
+    __shared__ double geo[GEO];
+    for (int i = tid; i < NT; i += NTH) {
+        int f = i / (M * NFP), rem = i - f * M * NFP, a = rem / NFP, l = rem - a * NFP;
+        int64_t F = A.e2f[e * NF + f];
+        int k = A.perm[(e * NF + f) * NFP + l];
+        duh[i] = A.dUH[(F * M + a) * NFP + k];
+    }
+    for (int i = tid; i < GEO; i += NTH) geo[i] = A.geo[e * GEO + i];
+    __syncthreads();
+    const double* U11 = R.a11 + e * R.a11_es;
+    const TL* Z = R.a12 + e * R.a12_es;
+    const double* z = R.rt + e * R.rt_es;
+    for (int i = warp; i < NU; i += NTH / 32) {
+        const TL* row = Z + (size_t)i * R.a12_rs;
+        double s = 0.0;
+        for (int c = lane; c < NT; c += 32) s = fma((double)row[c], duh[c], s);
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) w[i] = s + z[i * R.rt_rs];
+    }
+    __syncthreads();
+    if (warp == 0) {
+        for (int i = NU - 1; i >= 0; --i) {
+            const double* row = U11 + (size_t)i * R.a11_rs;
+            double s = 0.0;
+            for (int j = i + 1 + lane; j < NU; j += 32) s = fma(row[j], x[j], s);
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+            if (lane == 0) x[i] = (w[i] - s) / row[i];
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    for (int i = tid; i < NU; i += NTH) A.dU[e * NU + i] = -x[i];
+    const double detJ = geo[0];
+    const double* Jinv = geo + 1;
+    const double* NW = geo + 1 + D * D;
+    const DeviceTables& T = A.tab;
+    for (int idx = tid; idx < M * NP; idx += NTH) {
+        int b = idx / NP, i = idx - b * NP;
+        double t[D], ef[NF];
+        for (int r = 0; r < D; ++r) {
+            double s = 0.0;
+            const double* mc = T.minv_c + ((size_t)r * NP + i) * NP;
+            for (int j = 0; j < NP; ++j) s -= mc[j] * x[b * NP + j];
+            t[r] = s;
+        }
+        for (int f = 0; f < NF; ++f) {
+            double s = 0.0;
+            const double* me = T.minv_e + ((size_t)f * NP + i) * NFP;
+            for (int l = 0; l < NFP; ++l) s += me[l] * duh[(f * M + b) * NFP + l];
+            ef[f] = s;
+        }
+        for (int l = 0; l < D; ++l) {
+            double v = 0.0;
+            for (int r = 0; r < D; ++r) v -= Jinv[r * D + l] * t[r];
+            for (int f = 0; f < NF; ++f) v += NW[f * D + l] / detJ * ef[f];
+            int o = (l * M + b) * NP + i;
+            A.dQ[e * NQV + o] = A.dq0[e * NQV + o] + v;
+        }
+    }
+}
+
+}  // namespace hdg
+
+namespace hdg {
+
+template <class C, bool SPLIT3>
+__global__ void k_schur_tc(Regions<float> R, int64_t e0, int32_t* status);
+template <class C>
+struct SchurTC;
+
+template <class T>
+int mixed_alloc(hdg_ctx* h, T** p, size_t count) {
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        h->err = "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes for the mixed form failed";
+        return HDG_ENOMEM;
+    }
+    h->allocs.push_back(q);
+    h->device_bytes += (int64_t)(count * sizeof(T));
+    *p = (T*)q;
+    return HDG_OK;
+}
+
+inline Regions<float> mixed_regions(hdg_ctx* h) {
+    const int64_t NU = h->NU, NT = h->NT;
+    Regions<float> R;
+    R.a11 = h->d_m11; R.a11_es = NU * NU; R.a11_rs = NU;
+    R.a12 = h->d_m12; R.a12_es = NU * NT; R.a12_rs = NT;
+    R.a21 = h->d_m21; R.a21_es = NT * NU; R.a21_rs = NU;
+    R.a22 = h->d_m22; R.a22_es = NT * NT; R.a22_rs = NT;
+    R.rt = h->d_mrt;  R.rt_es = NU;       R.rt_rs = 1;
+    R.rb = h->d_mrb;  R.rb_es = NT;       R.rb_rs = 1;
+    return R;
+}
+
+template <int D, int P>
+int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
+    using C = Cfg<D, P>;
+    using BC = BlkCfg<C>;
+    using BS_ = BlkShape<C, BC::TY, BC::TX, BC::KC>;
+    constexpr int PT = 128, NB = 16;
+    int rc;
+    if (!h->d_m11) {
+        const size_t E = h->E, ch = h->chunk;
+        if ((rc = mixed_alloc(h, &h->d_m11, E * C::NU * C::NU))) return rc;
+        if ((rc = mixed_alloc(h, &h->d_m12, E * C::NU * C::NT))) return rc;
+        if ((rc = mixed_alloc(h, &h->d_mrt, E * C::NU))) return rc;
+        if ((rc = mixed_alloc(h, &h->d_m21, ch * C::NT * C::NU))) return rc;
+        if ((rc = mixed_alloc(h, &h->d_m22, ch * C::NT * C::NT))) return rc;
+        if ((rc = mixed_alloc(h, &h->d_mrb, ch * C::NT))) return rc;
+        if ((rc = mixed_alloc(h, &h->d_vals32, (size_t)h->nnzb * C::BS * C::BS))) return rc;
+    }
+    auto kblk = k_blocks<C, BC::TY, BC::TX, BC::KC, float, float>;
+    const size_t sm_point = sizeof(double) * point_smem_doubles<C>();
+    const size_t sm_blk = sizeof(float) * BS_::smem;
+    const size_t sm_elim = elim_mixed_smem_bytes<C, NB>();
+    HDG_CK(cudaFuncSetAttribute(k_point<C, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_point));
+    HDG_CK(cudaFuncSetAttribute(kblk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
+    HDG_CK(cudaFuncSetAttribute(k_elim_mixed<C, NB, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
+    cudaStream_t st = h->stream;
+    HDG_CK(cudaMemsetAsync(h->d_vals32, 0, sizeof(float) * h->nnzb * C::BS * C::BS, st));
+    HDG_CK(cudaMemsetAsync(h->d_g, 0, sizeof(double) * h->F * C::BS, st));
+    const Regions<float> RM = mixed_regions(h);
+    PointArgs pa;
+    pa.U = la.U; pa.Q = la.Q; pa.UH = la.UH; pa.Ustar = la.Ustar; pa.nu = la.nu;
+    pa.dt = la.dt; pa.a_ii = la.a_ii; pa.ph = h->phys; pa.tab = h->tab; pa.geo = h->d_geo;
+    pa.e2f = h->d_e2f; pa.perm = h->d_perm;
+    pa.rt = RM.rt; pa.rt_es = RM.rt_es; pa.rt_rs = RM.rt_rs;
+    pa.rb = RM.rb; pa.rb_es = RM.rb_es; pa.rb_rs = RM.rb_rs;
+    pa.vcoef = h->d_vcoef; pa.fcoef = h->d_fcoef; pa.dq0 = h->d_dq0;
+    BlkArgs<float> ba;
+    ba.vcoef = h->d_vcoef; ba.fcoef = h->d_fcoef; ba.geo = h->d_geo; ba.tab = h->tab;
+    ba.R = RM; ba.dt = la.dt; ba.a_ii = la.a_ii; ba.tau = h->phys.tau;
+    for (int64_t e0 = 0; e0 < h->E; e0 += h->chunk) {
+        const int64_t ne = std::min<int64_t>(h->chunk, h->E - e0);
+        pa.e0 = e0; ba.e0 = e0;
+        prof_begin(h, HDG_K_POINT);
+        k_point<C, PT><<<(unsigned)ne, PT, sm_point, st>>>(pa);
+        prof_end(h);
+        prof_begin(h, HDG_K_BLOCKS);
+        kblk<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
+        prof_end(h);
+        prof_begin(h, HDG_K_ELIM);
+        k_elim_mixed<C, NB, 256><<<(unsigned)ne, 256, sm_elim, st>>>(RM, e0, h->d_status);
+        prof_end(h);
+        prof_begin(h, HDG_K_SCHUR);
+        if (h->schur_mode == 0) {
+            k_schur_simt<C, 256><<<(unsigned)ne, 256, 0, st>>>(RM, e0);
+        } else {
+            using ST = SchurTC<C>;
+            const unsigned grid = (unsigned)(ne * ST::NMT * ST::NNT);
+            if (h->schur_mode == 1) {
+                const int smb = ST::smem_bytes(false);
+                HDG_CK(cudaFuncSetAttribute(k_schur_tc<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+                k_schur_tc<C, false><<<grid, 128, smb, st>>>(RM, e0, h->d_status);
+            } else {
+                const int smb = ST::smem_bytes(true);
+                HDG_CK(cudaFuncSetAttribute(k_schur_tc<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
+                k_schur_tc<C, true><<<grid, 128, smb, st>>>(RM, e0, h->d_status);
+            }
+        }
+        prof_end(h);
+        for (int pass = 0; pass < 2; ++pass) {
+            prof_begin(h, HDG_K_ASSEMBLE);
+            k_assemble_r<C, float><<<(unsigned)(ne * C::NF * C::NF), 256, 0, st>>>(RM, e0, h->d_blk, h->d_rank,
+                                                                                 h->d_iperm, h->d_vals32, pass);
+            prof_end(h);
+            prof_begin(h, HDG_K_ASSEMBLE);
+            k_assemble_g_r<C, float><<<(unsigned)(ne * C::NF), 128, 0, st>>>(RM, e0, h->d_e2f, h->d_frank,
+                                                                            h->d_iperm, h->d_g, pass);
+            prof_end(h);
+        }
+        HDG_CK(cudaGetLastError());
+    }
+    h->have_system = true;
+    h->sys_prec = HDG_PREC_MIXED;
+    h->bj_ready = false;
+    return HDG_OK;
+}
+
+template <int D, int P>
+int run_matvec(hdg_ctx* h, const double* x, double* y) {
+    using C = Cfg<D, P>;
+    prof_begin(h, HDG_K_MATVEC);
+    if (h->sys_prec == HDG_PREC_MIXED)
+        k_matvec_t<C, float><<<(unsigned)h->F, MvShape<C>::NTH, 0, h->stream>>>(h->d_rowptr, h->d_col, h->d_vals32, x, y);
+    else
+        k_matvec<C><<<(unsigned)h->F, MvShape<C>::NTH, 0, h->stream>>>(h->d_rowptr, h->d_col, h->d_vals, x, y);
+    prof_end(h);
+    HDG_CK(cudaGetLastError());
+    return HDG_OK;
+}
+
+template <int D, int P>
+int run_recover_mixed(hdg_ctx* h, const double* dUH, double* dQ, double* dU) {
+    using C = Cfg<D, P>;
+    RecArgs ra;
+    ra.top = nullptr; ra.dq0 = h->d_dq0; ra.geo = h->d_geo; ra.tab = h->tab;
+    ra.e2f = h->d_e2f; ra.perm = h->d_perm; ra.dUH = dUH; ra.dQ = dQ; ra.dU = dU;
+    prof_begin(h, HDG_K_RECOVER);
+    k_recover_r<C, float, 256><<<(unsigned)h->E, 256, 0, h->stream>>>(mixed_regions(h), ra);
+    prof_end(h);
+    HDG_CK(cudaGetLastError());
+    return HDG_OK;
+}
+
+#define HDG_INSTANTIATE_MIXED(D, P)                                            \
+    template int run_linearize_mixed<D, P>(hdg_ctx*, const LinArgs&);          \
+    template int run_recover_mixed<D, P>(hdg_ctx*, const double*, double*, double*);
+
+}  // namespace hdg
+
+namespace hdg {
+
+// ----------------------------------------------------------------------------
+// Schur product on the 5th-generation tensor cores: S^K = Dt - W Z per element,
+// tcgen05.mma kind::tf32 with FP32 accumulation in tensor memory.  W rows and Z
+// columns are staged by the CTA's threads into shared memory in the canonical
+// K-major layout without swizzle (8-row x 16-byte core matrices; K-adjacent
+// cores 128 B apart, 8-row groups KC/4 x 128 B apart).  SPLIT3 selects 3xTF32:
+// x = hi + lo with hi = tf32(x), lo = tf32(x - hi), and W Z ~ Wh Zh + Wh Zl + Wl Zh.
+// One CTA (4 warps) per (element, 128-row tile, column tile).  Waits on the
+// MMA completion barrier are bounded; on timeout the CTA latches status bit 4,
+// waits once more (bounded) and frees its tensor memory.
+// ----------------------------------------------------------------------------
+template <class C>
+struct SchurTC {
+    static constexpr int NT = C::NT, NU = C::NU;
+    static constexpr int MT = 128, KC = 32;
+    static constexpr int NNT = (NT + 255) / 256;                          // column tiles
+    static constexpr int NTN = (((NT + NNT - 1) / NNT) + 15) / 16 * 16;   // columns per tile (mult. of 16)
+    static constexpr int NMT = (NT + MT - 1) / MT;                        // row tiles
+    static constexpr int TCOLS = NTN <= 32 ? 32 : NTN <= 64 ? 64 : NTN <= 128 ? 128 : 256;
+    static_assert(NTN <= 256, "column tile too wide");
+    __host__ __device__ static constexpr int tile_floats(int rows) { return rows * KC; }
+    __host__ __device__ static constexpr int smem_bytes(bool split3) {
+        return (split3 ? 2 : 1) * (tile_floats(MT) + tile_floats(NTN)) * 4 + 64;
+    }
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version of the 5th-generation tensor core
+    return d;                 // no swizzle, base offset 0
+}
+
+__device__ __forceinline__ float tf32_round(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase, int limit) {
+    uint32_t done = 0;
+    for (int it = 0; it < limit && !done; ++it)
+        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done) : "r"(bar), "r"(phase));
+    return done != 0;
+}
+
+template <int KC>
+__device__ __forceinline__ int core_off(int r, int k) {
+    return ((r >> 3) * (KC / 4) + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3);
+}
+
+template <class C, bool SPLIT3>
+__global__ void __launch_bounds__(128) k_schur_tc(Regions<float> R, int64_t e0, int32_t* status) {
+    using S = SchurTC<C>;
+    constexpr int NT = S::NT, NU = S::NU, MT = S::MT, KC = S::KC, NTN = S::NTN;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t bid = blockIdx.x;
+    const int nt = (int)(bid % S::NNT), mt = (int)((bid / S::NNT) % S::NMT);
+    const int64_t el = bid / (S::NNT * S::NMT), e = e0 + el;
+    const int m0 = mt * MT, n0 = nt * NTN;
+    const float* W = R.a21 + el * R.a21_es;
+    const float* Z = R.a12 + e * R.a12_es;
+    float* Dm = R.a22 + el * R.a22_es;
+    const int64_t sw = R.a21_rs, sz = R.a12_rs, sd = R.a22_rs;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    float* Ah = reinterpret_cast<float*>(smraw);
+    float* Bh = Ah + S::tile_floats(MT);
+    float* Al = Bh + S::tile_floats(NTN);
+    float* Bl = Al + S::tile_floats(MT);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smraw + S::smem_bytes(SPLIT3) - 64);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+    // right-hand side of this row tile: Rh -= W z (FP64), done by the first column tile
+    if (nt == 0) {
+        const double* z = R.rt + e * R.rt_es;
+        double* rb = R.rb + el * R.rb_es;
+        const int r = m0 + tid;
+        if (r < NT) {
+            double s = rb[r * R.rb_rs];
+            for (int k = 0; k < NU; ++k) s -= (double)W[r * sw + k] * z[k * R.rt_rs];
+            rb[r * R.rb_rs] = s;
+        }
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(tslot)),
+                     "r"(S::TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NTN >> 3) << 17) | ((uint32_t)(MT >> 4) << 24);
+    const uint32_t bar = smem_u32(mbar);
+    uint32_t phase = 0;
+    bool ok = true;
+    for (int k0 = 0; k0 < NU; k0 += KC) {
+        for (int idx = tid; idx < MT * KC; idx += 128) {
+            int r = idx / KC, k = idx - r * KC;
+            float v = (m0 + r < NT && k0 + k < NU) ? W[(m0 + r) * sw + k0 + k] : 0.f;
+            float hi = tf32_round(v);
+            Ah[core_off<KC>(r, k)] = hi;
+            if (SPLIT3) Al[core_off<KC>(r, k)] = tf32_round(v - hi);
+        }
+        for (int idx = tid; idx < NTN * KC; idx += 128) {
+            int k = idx / NTN, n = idx - k * NTN;
+            float v = (n0 + n < NT && k0 + k < NU) ? Z[(k0 + k) * sz + n0 + n] : 0.f;
+            float hi = tf32_round(v);
+            Bh[core_off<KC>(n, k)] = hi;
+            if (SPLIT3) Bl[core_off<KC>(n, k)] = tf32_round(v - hi);
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int nsteps = (min(KC, NU - k0) + 7) / 8;
+            for (int s = 0; s < nsteps; ++s) {
+                const uint32_t off = s * 256;
+                const uint64_t ah = umma_desc(smem_u32(Ah) + off, 128, (KC / 4) * 128);
+                const uint64_t bh = umma_desc(smem_u32(Bh) + off, 128, (KC / 4) * 128);
+                uint32_t acc = (k0 > 0 || s > 0) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                             :: "r"(tmem), "l"(ah), "l"(bh), "r"(idesc), "r"(acc));
+                if (SPLIT3) {
+                    const uint64_t al = umma_desc(smem_u32(Al) + off, 128, (KC / 4) * 128);
+                    const uint64_t bl = umma_desc(smem_u32(Bl) + off, 128, (KC / 4) * 128);
+                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
+                                 :: "r"(tmem), "l"(ah), "l"(bl), "r"(idesc));
+                    asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
+                                 :: "r"(tmem), "l"(al), "l"(bh), "r"(idesc));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar));
+        }
+        if (!mbar_wait_bounded(bar, phase, 1 << 24)) {
+            ok = false;
+            if (tid == 0) atomicOr(status, 4);
+            mbar_wait_bounded(bar, phase, 1 << 24);
+        }
+        phase ^= 1;
+        __syncthreads();
+        if (!ok) break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        const int r = m0 + warp * 32 + lane;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NTN; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                           "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                         : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (r < NT) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int c = n0 + c0 + j;
+                    if (c0 + j < NTN && c < NT) Dm[r * sd + c] -= __uint_as_float(v[j]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(S::TCOLS));
+}
+
+}  // namespace hdg

@@ -26,14 +26,18 @@ HDG_EUNSUPPORTED = -7
 HDG_QUAD = 1
 HDG_HEX = 2
 HDG_PREC_FP64 = 0
+HDG_PREC_MIXED = 1
+HDG_PREC_MIXED_TF32 = 2
+HDG_PREC_MIXED_3XTF32 = 3
 
 EXPORTS = [
     "hdg_create", "hdg_create_host", "hdg_destroy", "hdg_last_error", "hdg_set_params", "hdg_set_stream",
     "hdg_query_sizes", "hdg_get_connectivity", "hdg_linearize_condense", "hdg_trace_matvec",
     "hdg_trace_rhs", "hdg_recover_interior", "hdg_get_blocks", "hdg_status", "hdg_profile",
-    "hdg_profile_read", "hdg_linearize_condense_static",
+    "hdg_profile_read", "hdg_linearize_condense_static", "hdg_residual", "hdg_update_state",
+    "hdg_blockjacobi_setup", "hdg_blockjacobi_apply", "hdg_gmres", "hdg_newton",
 ]
-KERNEL_CLASSES = ["point", "blocks", "elim", "assemble", "matvec", "recover"]
+KERNEL_CLASSES = ["point", "blocks", "elim", "assemble", "matvec", "recover", "schur"]
 
 
 class HDGError(RuntimeError):
@@ -89,6 +93,12 @@ def lib():
         "hdg_profile": [vp, i32],
         "hdg_profile_read": [vp, vp, vp],
         "hdg_linearize_condense_static": [vp, vp, vp, vp, vp, vp, dbl, dbl],
+        "hdg_residual": [vp, vp, vp, vp, vp, vp, dbl, dbl, vp, vp, vp, vp],
+        "hdg_update_state": [vp, vp, vp, vp, vp, vp, vp, dbl],
+        "hdg_blockjacobi_setup": [vp],
+        "hdg_blockjacobi_apply": [vp, vp, vp],
+        "hdg_gmres": [vp, vp, vp, i32, i32, dbl, i32, vp, vp],
+        "hdg_newton": [vp, vp, vp, vp, vp, vp, dbl, dbl, dbl, i32, i32, i32, dbl, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -221,3 +231,48 @@ def hdg_profile_read(h):
     n = np.zeros(len(KERNEL_CLASSES), np.int64)
     _check(h, lib().hdg_profile_read(h, ms.ctypes.data, n.ctypes.data))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+
+def hdg_residual(h, U, Q, UH, Ustar, nu, dt, a_ii, Rq=None, Ru=None, Ruh=None):
+    """FP64 stage residual; returns (||F||, ||(R_q, R_u)||, ||R_uhat||)."""
+    norms = np.zeros(3, np.float64)
+    _check(h, lib().hdg_residual(h, _ptr(U), _ptr(Q), _ptr(UH), _ptr(Ustar), _ptr(nu), float(dt), float(a_ii),
+                                 _ptr(Rq), _ptr(Ru), _ptr(Ruh), norms.ctypes.data))
+    return tuple(float(v) for v in norms)
+
+
+def hdg_update_state(h, U, Q, UH, dU, dQ, dUH, alpha):
+    _check(h, lib().hdg_update_state(h, _ptr(U), _ptr(Q), _ptr(UH), _ptr(dU), _ptr(dQ), _ptr(dUH), float(alpha)))
+
+
+def hdg_blockjacobi_setup(h):
+    _check(h, lib().hdg_blockjacobi_setup(h))
+
+
+def hdg_blockjacobi_apply(h, x, y):
+    _check(h, lib().hdg_blockjacobi_apply(h, _ptr(x), _ptr(y)))
+
+
+def hdg_gmres(h, b, x, restart=30, max_iter=300, rtol=1e-10, precond=True, raise_on_noconv=True):
+    """GMRES on S x = b; returns (iterations, relative preconditioned residual)."""
+    it = ctypes.c_int(0)
+    rel = ctypes.c_double(0.0)
+    rc = lib().hdg_gmres(h, _ptr(b), _ptr(x), int(restart), int(max_iter), float(rtol), 1 if precond else 0,
+                         ctypes.byref(it), ctypes.byref(rel))
+    if rc != HDG_OK and (raise_on_noconv or rc != HDG_ENOCONV):
+        _check(h, rc)
+    return it.value, rel.value
+
+
+def hdg_newton(h, U, Q, UH, Ustar, nu, dt, a_ii, tol=1e-8, max_newton=10, restart=40, max_gmres=400,
+               gmres_rtol=1e-10, raise_on_noconv=True):
+    """Newton on the stage equations; returns (newton iterations, gmres iterations, residual history)."""
+    hist = np.zeros(max_newton + 1, np.float64)
+    nit = ctypes.c_int(0)
+    git = ctypes.c_int(0)
+    rc = lib().hdg_newton(h, _ptr(U), _ptr(Q), _ptr(UH), _ptr(Ustar), _ptr(nu), float(dt), float(a_ii),
+                          float(tol), int(max_newton), int(restart), int(max_gmres), float(gmres_rtol),
+                          hist.ctypes.data, ctypes.byref(nit), ctypes.byref(git))
+    if rc != HDG_OK and (raise_on_noconv or rc != HDG_ENOCONV):
+        _check(h, rc)
+    return nit.value, git.value, hist[:nit.value + 1].copy()
