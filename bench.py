@@ -276,7 +276,9 @@ def run_ours(args, rank, world, local_rank):
     t_ms, prof, clocks = timed(args.steps)
 
     # mixed form on the same workload and step
-    set_prec(H.HDG_PREC_MIXED)
+    mixed_prec = {"fp32": H.HDG_PREC_MIXED, "tf32": H.HDG_PREC_MIXED_TF32,
+                  "3xtf32": H.HDG_PREC_MIXED_3XTF32}[args.mixed_prec]
+    set_prec(mixed_prec)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -323,7 +325,7 @@ def run_ours(args, rank, world, local_rank):
     # mixed vs FP64 at tolerance: Newton on the stage equations to ||F||_2 <= 1e-8 (FP64 residual)
     newton = {}
     if not args.no_newton:
-        for name, prec in (("fp64", H.HDG_PREC_FP64), ("mixed", H.HDG_PREC_MIXED)):
+        for name, prec in (("fp64", H.HDG_PREC_FP64), ("mixed", mixed_prec)):
             set_prec(prec)
             U2, Q2, UH2 = U.clone(), Q.clone(), UH.clone()
             torch.cuda.synchronize()
@@ -365,7 +367,9 @@ def run_ours(args, rank, world, local_rank):
              "speedup_vs_fp64_step": t_ms / tm_ms,
              "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                          for k, v in prof_m.items() if v[1]},
-             "dtype": "fp64 pointwise terms, interior LU, residual and Arnoldi; fp32 blocks and Schur",
+             "dtype": "fp64 residual, interior LU (pivoting) and Arnoldi; fp32 Jacobian terms and blocks; Schur "
+                      "product %s" % {"fp32": "fp32 SIMT", "tf32": "TF32 tensor cores (tcgen05)",
+                                      "3xtf32": "3xTF32 tensor cores (tcgen05)"}[args.mixed_prec],
              "clocks": clocks_m}
     lu_flops = sum(2 * (C_nu - k - 1) * (C_nu - k) + (C_nu - k - 1) for C_nu in [(m.dim + 2) * (P.p + 1) ** m.dim]
                    for k in range(C_nu))
@@ -435,6 +439,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-newton", action="store_true")
+    ap.add_argument("--mixed-prec", choices=["fp32", "tf32", "3xtf32"], default="3xtf32")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -80,7 +80,8 @@ typedef struct {
     const double* vert_xyz;       /* [n_vert][dim] */
     const int64_t* elem_vert;     /* [n_elem][2^dim] */
     const int64_t* periodic_map;  /* [n_vert] master vertex of each vertex, or NULL */
-    const int32_t* bnd_tag;       /* [n_elem][2 dim] 0 = interior / periodic, or NULL */
+    const int32_t* bnd_tag;       /* [n_elem][2 dim] 0 = interior / periodic, 1 = Dirichlet / far-field
+                                     (bhat = uhat - u_b, state set by hdg_set_bc_state), or NULL */
 } hdg_mesh;
 
 /* Solver parameters (hdg_set_params).  tau: constant scalar stabilization of
@@ -106,8 +107,10 @@ typedef struct {
 
 /* Build tables, connectivity, the BSR pattern and device storage (Sec. 2.2
  * spaces, Sec. 3.5 face partition).  Fails with HDG_EUNSUPPORTED for
- * non-affine elements or p outside 1..3, HDG_EINVAL for inconsistent meshes
- * (a face shared by more than two elements, a degenerate periodic face). */
+ * non-affine elements, p outside 1..3 or boundary tags other than 0 / 1, and
+ * HDG_EINVAL for inconsistent meshes (a face shared by more than two
+ * elements, a degenerate periodic face, tag 1 not marking exactly the faces
+ * with a single element). */
 int hdg_create(hdg_handle* out, const hdg_mesh* mesh, int p, double gamma, double Re,
                double Pr, double Mach);
 /* Same as hdg_create without touching the GPU: connectivity and tables only;
@@ -119,6 +122,10 @@ const char* hdg_last_error(hdg_handle h);
 
 int hdg_set_params(hdg_handle h, const hdg_params* prm);
 int hdg_set_stream(hdg_handle h, void* cuda_stream);
+/* State u_b [m] (host) of the tag-1 boundary faces: their trace equation is
+ * <uhat - u_b, mu> = 0 (the prescribed-state boundary of Sec. 2.1, the bhat of
+ * eq. hdg-trace); required before linearizing a mesh with tag-1 faces. */
+int hdg_set_bc_state(hdg_handle h, int tag, const double* ub);
 int hdg_query_sizes(hdg_handle h, hdg_sizes* out);
 
 /* Host copies of the integer skeleton data (any pointer may be NULL):
@@ -162,9 +169,33 @@ int hdg_status(hdg_handle h);
  * then the call synchronises the stream.  Allocates its scratch on first use. */
 int hdg_residual(hdg_handle h, const double* U, const double* Q, const double* UH, const double* Ustar,
                  const double* nu, double dt, double a_ii, double* Rq, double* Ru, double* Ruh, double* norms);
+/* Q = Q_lift(U, Uhat): per element, the gradient for which the gradient
+ * equations hold exactly (eq. hdg-grad with R_q = 0; R_q is linear in Q, so
+ * Q_lift = M_K^{-1} (-(u, grad phi)_K + <uhat, phi n>_dK) component by
+ * component).  U [E][m][Np], UH [F][m][Nfp] and Q [E][d][m][Np] are device
+ * arrays; Q is written.  Asynchronous on the handle's stream. */
+int hdg_lift_gradient(hdg_handle h, const double* U, const double* UH, double* Q);
+
 /* Newton update W <- W + alpha dW (eq. newton-update) on device arrays. */
 int hdg_update_state(hdg_handle h, double* U, double* Q, double* UH, const double* dU, const double* dQ,
                      const double* dUH, double alpha);
+/* Preconditioner used by hdg_gmres (precond != 0), hdg_newton,
+ * hdg_newton_fixed and hdg_dirk_step: HDG_PC_BLOCKJACOBI (default) or
+ * HDG_PC_SCHWARZ. */
+#define HDG_PC_BLOCKJACOBI 1
+#define HDG_PC_SCHWARZ 2
+int hdg_set_preconditioner(hdg_handle h, int kind);
+/* One-level additive Schwarz on element-centred face patches (Sec. 3.3,
+ * eq. additive-schwarz): M^{-1} = sum_r R_r^T S_r^{-1} R_r, R_r the
+ * restriction to the nf faces of element r, S_r = R_r S R_r^T (t x t, no
+ * coarse space).  Setup factors every S_r (partial pivoting; FP64 for the
+ * FP64 system, FP32 for the mixed one), on the stream; apply computes
+ * y = M^{-1} x for device vectors x, y [F][m][Nfp] (distinct), summing the
+ * patch corrections of a face in a fixed order (bitwise reproducible).
+ * A zero or non-finite pivot sets the status read by hdg_status. */
+int hdg_schwarz_setup(hdg_handle h);
+int hdg_schwarz_apply(hdg_handle h, const double* x, double* y);
+
 /* Block-Jacobi preconditioner of the trace system: partial-pivot LU of every
  * diagonal block S_FF of the current S (the one-face special case of the
  * additive Schwarz method, eq. additive-schwarz), and y = M^{-1} x. */
@@ -190,6 +221,28 @@ int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_ite
 int hdg_newton(hdg_handle h, double* U, double* Q, double* UH, const double* Ustar, const double* nu, double dt,
                double a_ii, double tol, int max_newton, int restart, int max_gmres, double gmres_rtol,
                double* hist, int* newton_iters, int* gmres_iters);
+
+/* Newton iterations with a fixed-length GMRES(m) (m iterations from zero,
+ * block-Jacobi, Givens rotations and the triangular solve on the device): no
+ * host synchronisation inside an iteration, so with use_graph != 0 one
+ * iteration is captured once into a CUDA graph (on an internal stream) and
+ * replayed n_newton times on the handle's stream; the graph is rebuilt when
+ * the arguments change.  hist (host, optional, n_newton + 1 entries) receives
+ * ||F|| before each iteration and after the last.  Synchronises at the end. */
+int hdg_newton_fixed(hdg_handle h, double* U, double* Q, double* UH, const double* Ustar, const double* nu,
+                     double dt, double a_ii, int n_newton, int m, int use_graph, double* hist);
+/* One step of an s-stage DIRK method (Sec. 2.3, eqs. dirk-stage, dirk-update)
+ * with Butcher matrix A [s][s] (row-major, lower triangular) and weights b [s];
+ * the tableau must be stiffly accurate (b = last row of A), so that W^{n+1} is
+ * the last stage.  Stage i solves the stage equations with
+ * U* = U^n - a_ii sum_{j<i} d_ij (U^{n,j} - U^n), d = A^{-1}, by n_newton
+ * fixed Newton iterations (as hdg_newton_fixed), starting from the previous
+ * stage.  With use_graph != 0 the whole step (s stages x n_newton iterations)
+ * is captured once as one CUDA graph and replayed.  U, Q, UH hold W^n on entry
+ * and W^{n+1} on return; hist (host, optional, s (n_newton + 1) entries)
+ * receives the residual norms.  Synchronises at the end. */
+int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* nu, double dt, int s,
+                  const double* A, const double* b, int n_newton, int m, int use_graph, double* hist);
 
 /* Per-kernel timing with CUDA events recorded on the handle's stream around
  * every kernel launch (not from the paper: instrumentation for rooflines).

@@ -259,6 +259,22 @@ class Problem:
         dU = dW[self.nq_dofs:].reshape(r.m, r.Np)
         return dQ, dU
 
+    def lift_gradient(self, U, UH):
+        """Q for which R_q = 0 on every element (eq. hdg-grad).
+
+        R_q is affine in Q with dR_q/dQ = I (x) M_K, so
+        Q_K = -M_K^{-1} R_q(0, U_K, Uhat_K), one solve per (k, a).
+        """
+        r = self.ref
+        E = U.shape[0]
+        Q = np.zeros((E, self.d, r.m, r.Np))
+        zero = np.zeros((self.d, r.m, r.Np))
+        for e in range(E):
+            Rq0 = self.element_residual(e, zero, U[e], self.local_trace(UH, e))[0]
+            rhs = -Rq0.reshape(self.d * r.m, r.Np).T
+            Q[e] = np.linalg.solve(self.geom(e).M, rhs).T.reshape(self.d, r.m, r.Np)
+        return Q
+
     # -------------------------------------------------------- global system
     def global_residual(self, Q, U, UH):
         """[R_q; R_u; R_uhat] over the whole mesh (eq. nonlinear-residual)."""

@@ -123,13 +123,25 @@ int create_host(hdg_ctx* h, const hdg_mesh* mesh, int p, double gamma, double Re
     if (rc) return rc;
     h->F = h->sk.n_faces;
     h->nnzb = h->sk.rowptr[h->F];
+    // boundary tags: 0 on interior / periodic faces, 1 (Dirichlet / far-field, bhat = uhat - u_b) on
+    // faces with a single element
+    h->ftag.assign((size_t)h->E * h->nf, 0);
     if (mesh->bnd_tag)
-        for (int64_t i = 0; i < h->E * h->nf; ++i)
-            if (mesh->bnd_tag[i] != 0)
-                return fail(h, HDG_EUNSUPPORTED, "boundary faces are not supported yet (periodic meshes only)");
-    for (int64_t F = 0; F < h->F; ++F)
-        if (h->sk.f2e[2 * F + 1] < 0)
-            return fail(h, HDG_EUNSUPPORTED, "boundary faces are not supported yet (periodic meshes only)");
+        for (int64_t i = 0; i < h->E * h->nf; ++i) {
+            if (mesh->bnd_tag[i] != 0 && mesh->bnd_tag[i] != 1)
+                return fail(h, HDG_EUNSUPPORTED, "boundary tag " + std::to_string(mesh->bnd_tag[i]) + " not supported (0, 1)");
+            h->ftag[i] = mesh->bnd_tag[i];
+        }
+    for (int64_t F = 0; F < h->F; ++F) {
+        const int32_t e0 = h->sk.f2e[2 * F], f0 = h->sk.f2lf[2 * F];
+        const bool single = h->sk.f2e[2 * F + 1] < 0;
+        if (single != (h->ftag[(size_t)e0 * h->nf + f0] == 1))
+            return fail(h, HDG_EINVAL, "face " + std::to_string(F) + ": tag 1 must mark exactly the faces with one element");
+        if (!single && h->ftag[(size_t)h->sk.f2e[2 * F + 1] * h->nf + h->sk.f2lf[2 * F + 1]] != 0)
+            return fail(h, HDG_EINVAL, "face " + std::to_string(F) + ": interior face tagged as boundary");
+    }
+    h->has_bnd = false;
+    for (int32_t t : h->ftag) h->has_bnd |= (t != 0);
     return build_geometry(h, *mesh);
 }
 
@@ -163,6 +175,10 @@ int create_device(hdg_ctx* h) {
     UP(h->tab.mu, t.mu); UP(h->tab.wf, t.wf); UP(h->tab.fnode, t.fnode); UP(h->tab.node_face, t.node_face);
     UP(h->tab.mhat, t.mhat); UP(h->tab.mf, t.mf); UP(h->tab.minv_c, t.minv_c); UP(h->tab.minv_e, t.minv_e);
     UP(h->tab.psi, t.psi); UP(h->tab.theta, t.theta); UP(h->tab.psi_f, t.psi_f); UP(h->tab.theta_f, t.theta_f);
+    auto f32 = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
+    UP(h->tab.fphi, f32(t.phi)); UP(h->tab.fdphi, f32(t.dphi)); UP(h->tab.fpsi, f32(t.psi));
+    UP(h->tab.ftheta, f32(t.theta)); UP(h->tab.fpsi_f, f32(t.psi_f)); UP(h->tab.ftheta_f, f32(t.theta_f));
+    UP(h->tab.fmu, f32(t.mu)); UP(h->tab.fmf, f32(t.mf));
     const int d = h->d, G = 1 + d * d + h->nf * d;
     std::vector<double> geo((size_t)h->E * G);
     for (int64_t e = 0; e < h->E; ++e) {
@@ -181,6 +197,11 @@ int create_device(hdg_ctx* h) {
     if ((rc = dev_alloc(h, &h->d_top, (size_t)h->E * h->NU * h->LD))) return rc;
     if ((rc = dev_alloc(h, &h->d_dq0, (size_t)h->E * h->NQV))) return rc;
     if ((rc = dev_alloc(h, &h->d_status, 1))) return rc;
+    if (h->has_bnd) {
+        if ((rc = dev_upload(h, &h->d_ftag, h->ftag))) return rc;
+        if ((rc = dev_alloc(h, &h->d_ub, (size_t)h->m))) return rc;
+        CKH(cudaMemset(h->d_ub, 0, sizeof(double) * h->m));
+    }
     CKH(cudaMemset(h->d_status, 0, sizeof(int32_t)));
     // per-chunk scratch: trace rows of the bordered matrix and the point coefficients
     const size_t per = sizeof(double) * ((size_t)h->NT * h->LD + (size_t)h->m * h->m * d * h->NCOEF * h->Nq +
@@ -232,6 +253,8 @@ int hdg_create(hdg_handle* out, const hdg_mesh* mesh, int p, double gamma, doubl
 int hdg_destroy(hdg_handle h) {
     if (!h) return HDG_OK;
     for (cudaEvent_t ev : h->ev_pool) cudaEventDestroy(ev);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
     for (void* p : h->allocs) cudaFree(p);
     delete h;
     return HDG_OK;
@@ -253,6 +276,16 @@ int hdg_set_params(hdg_handle h, const hdg_params* prm) {
     h->phys.s = prm->suth_s;
     h->precision = prm->precision == HDG_PREC_FP64 ? HDG_PREC_FP64 : HDG_PREC_MIXED;
     h->schur_mode = prm->precision == HDG_PREC_FP64 ? 0 : prm->precision - HDG_PREC_MIXED;
+    return HDG_OK;
+}
+
+int hdg_set_bc_state(hdg_handle h, int tag, const double* ub) {
+    if (!h || !ub) return fail(h, HDG_EINVAL, "NULL argument");
+    if (tag != 1) return fail(h, HDG_EUNSUPPORTED, "only tag 1 (Dirichlet / far-field) carries a state");
+    if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
+    if (!h->has_bnd) return fail(h, HDG_EINVAL, "the mesh has no tag-1 faces");
+    CKH(cudaMemcpy(h->d_ub, ub, sizeof(double) * h->m, cudaMemcpyHostToDevice));
+    h->ub_set = true;
     return HDG_OK;
 }
 
@@ -290,6 +323,7 @@ int hdg_linearize_condense(hdg_handle h, const double* U, const double* Q, const
     if (!U || !Q || !UH || !Ustar) return fail(h, HDG_EINVAL, "U, Q, UH and Ustar are required");
     if (res_norm) return fail(h, HDG_EINVAL, "res_norm must be NULL");
     if (!(dt > 0.0) || !(a_ii > 0.0)) return fail(h, HDG_EINVAL, "dt and a_ii must be positive");
+    if (h->has_bnd && !h->ub_set) return fail(h, HDG_EINVAL, "boundary state of tag 1 not set (hdg_set_bc_state)");
     CKH(cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), h->stream));
     LinArgs a{U, Q, UH, Ustar, nu, dt, a_ii};
     if (h->precision == HDG_PREC_MIXED) {

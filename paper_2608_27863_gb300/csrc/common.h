@@ -74,6 +74,8 @@ struct DeviceTables {
     double* mhat; double* mf;
     double* minv_c; double* minv_e;
     double* psi; double* theta; double* psi_f; double* theta_f;
+    // float copies for the mixed form's FP32 contraction
+    float* fphi; float* fdphi; float* fpsi; float* ftheta; float* fpsi_f; float* ftheta_f; float* fmu; float* fmf;
 };
 
 }  // namespace hdg
@@ -114,6 +116,11 @@ struct hdg_ctx {
     double* d_fcoef = nullptr;             // [chunk][nf][m][m][NCOEF][Nfq]
     double* d_dq0 = nullptr;               // [E][d][m][Np]
     int32_t* d_status = nullptr;           // [1]
+    int32_t* d_ftag = nullptr;             // [E][nf] boundary tags, NULL for fully periodic meshes
+    double* d_ub = nullptr;                // [m] state of tag-1 boundary faces
+    std::vector<int32_t> ftag;             // host copy of the tags
+    bool ub_set = false;
+    bool has_bnd = false;
     int32_t* d_f2e = nullptr;              // [F][2]
     int32_t* d_f2lf = nullptr;             // [F][2]
     double* d_rk = nullptr;                // [E][NT] element contributions to R_uhat
@@ -123,6 +130,14 @@ struct hdg_ctx {
     double* d_bjlu = nullptr;              // [F][BS][BS]
     int32_t* d_bjpiv = nullptr;            // [F][BS]
     bool bj_ready = false;
+    // additive Schwarz factors on element face patches (allocated on first set-up)
+    void* d_asmlu = nullptr;               // [E][NT][LDA] LU factors of S_r (FP64, or FP32 for the mixed form)
+    int32_t* d_asmpiv = nullptr;           // [E][NT]
+    double* d_asmz = nullptr;              // [E][NT] patch corrections
+    size_t asm_bytes = 0;
+    int asm_prec = -1;                     // precision of the stored factors
+    bool asm_ready = false;
+    int pc_kind = HDG_PC_BLOCKJACOBI;      // preconditioner of GMRES and Newton
     // GMRES workspace (allocated on first use)
     double* d_V = nullptr;                 // [restart + 1][N]
     double* d_w = nullptr;                 // [N]
@@ -130,6 +145,16 @@ struct hdg_ctx {
     double* d_h = nullptr;                 // [restart + 2]
     int gm_cap = 0;
     double* d_nw = nullptr;                // Newton work: dU, dQ, dUH, g
+    // synchronisation-free Newton / DIRK driver and its CUDA graph
+    double* d_fx = nullptr;                // device GMRES scalars: beta, R, cs, sn, y, g
+    int fx_cap = 0;
+    double* d_hist = nullptr;              // [4096] residual history
+    int* d_hcount = nullptr;
+    double* d_dirk = nullptr;              // U^n, U*, stage states
+    int dirk_cap = 0;
+    cudaStream_t gstream = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    uint64_t gkey = 0;
     // mixed form (allocated on the first mixed linearization)
     int sys_prec = HDG_PREC_FP64;          // precision of the assembled system
     int schur_mode = 0;                    // mixed Schur product: 0 FP32 SIMT, 1 TF32, 2 3xTF32 tensor cores
@@ -140,6 +165,7 @@ struct hdg_ctx {
     float* d_m22 = nullptr;                // [chunk][NT][NT] Dt, then S^K
     double* d_mrb = nullptr;               // [chunk][NT] Rh, then -g^K
     float* d_vals32 = nullptr;             // [nnzb][BS][BS] condensed blocks (FP32)
+    float* d_x32 = nullptr;                // [F][BS] FP32 copy of a matvec operand
     int64_t chunk = 0;
     bool have_system = false;
     int elim_minb = 2;                     // k_elim variant: resident CTAs per SM the kernel is built for
@@ -167,6 +193,9 @@ template <int D, int P> int run_linearize(hdg_ctx* h, const LinArgs& a);
 template <int D, int P> int run_matvec(hdg_ctx* h, const double* x, double* y);
 template <int D, int P> int run_recover(hdg_ctx* h, const double* dUH, double* dQ, double* dU);
 template <int D, int P> int run_residual(hdg_ctx* h, const LinArgs& a, double* Rq, double* Ru, double* Ruh);
+template <int D, int P> int run_asm_setup(hdg_ctx* h);
+template <int D, int P> int run_asm_apply(hdg_ctx* h, const double* x, double* y);
+template <int D, int P> int run_lift(hdg_ctx* h, const double* U, const double* UH, double* Q);
 template <int D, int P> int run_linearize_mixed(hdg_ctx* h, const LinArgs& a);
 template <int D, int P> int run_bj_setup(hdg_ctx* h);
 template <int D, int P> int run_bj_apply(hdg_ctx* h, const double* x, double* y);

@@ -65,22 +65,31 @@ inline Regions<double> fp64_regions(double* top, double* bot) {
 struct PointArgs {
     const double* U; const double* Q; const double* UH; const double* Ustar; const double* nu;
     double dt, a_ii;
-    Phys ph;
+    PhysT<double> ph;        // residual terms (FP64)
+    PhysT<float> phf;        // Jacobian terms of the mixed form
+    double tau;
     DeviceTables tab;
     const double* geo;
     const int32_t* e2f; const int32_t* perm;
     double* rt; int64_t rt_es, rt_rs;      // right-hand side, interior rows
     double* rb; int64_t rb_es, rb_rs;      // right-hand side, trace rows (chunk-local)
-    double* vcoef; double* fcoef; double* dq0;
+    void* vcoef; void* fcoef;   // Jacobian coefficients, in the form's Jacobian type
+    double* dq0;
+    const int32_t* ftag;        // [E][nf] boundary tag of each element face (0 interior / periodic)
+    const double* ub;           // [m] boundary state of tag-1 faces
     int64_t e0;
 };
 
+template <class S> __device__ __forceinline__ const PhysT<S>& jac_phys(const PointArgs& A);
+template <> __device__ __forceinline__ const PhysT<double>& jac_phys<double>(const PointArgs& A) { return A.ph; }
+template <> __device__ __forceinline__ const PhysT<float>& jac_phys<float>(const PointArgs& A) { return A.phf; }
+
 template <class C>
 constexpr int point_smem_doubles() {
-    return C::NU + 2 * C::NQV + C::NP + 2 * C::NT + C::D * C::M * C::NQ + C::NF * C::M * C::NFQ;
+    return C::NU + 2 * C::NQV + C::NP + 2 * C::NT + C::D * C::M * C::NQ + 2 * C::NF * C::M * C::NFQ;
 }
 
-template <class C, int NTH>
+template <class C, int NTH, class TJ>
 __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
     constexpr int D = C::D, M = C::M, NP = C::NP, NQ = C::NQ, NF = C::NF, NFP = C::NFP, NFQ = C::NFQ;
     constexpr int NU = C::NU, NQV = C::NQV, NT = C::NT, LD = C::LD, NC = C::NC, NCOEF = C::NCOEF;
@@ -96,6 +105,7 @@ __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
     double* sFres = sUH + NT;            // [d][m][Nq]
     double* sFH = sFres + D * M * NQ;    // [nf][m][Nfq]
     double* sRh = sFH + NF * M * NFQ;    // [nf][m][Nfp]
+    double* sFB = sRh + NT;              // [nf][m][Nfq] boundary form bhat on tag-1 faces
     __shared__ double geo[GEO];
     const DeviceTables& T = A.tab;
 
@@ -141,8 +151,12 @@ __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
     }
     __syncthreads();
 
-    const Phys ph = A.ph;
-    double* vc = A.vcoef + el * (size_t)(M * M * D * NCOEF * NQ);
+    const PhysT<double>& ph = A.ph;
+    const PhysT<TJ>& pj = jac_phys<TJ>(A);
+    TJ* vc = reinterpret_cast<TJ*>(A.vcoef) + el * (size_t)(M * M * D * NCOEF * NQ);
+    TJ Jj[D * D], NWj[NF * D];
+    for (int i = 0; i < D * D; ++i) Jj[i] = (TJ)Jinv[i];
+    for (int i = 0; i < NF * D; ++i) NWj[i] = (TJ)(NW[i] / detJ);
     // volume points
     for (int g = tid; g < NQ; g += NTH) {
         double u[M], q[M][D], ql[M][D], nuv = 0.0;
@@ -161,8 +175,8 @@ __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
         const double wJ = -A.dt * T.wq[g] * detJ;
         {
             double Fc[M][D], Fv[M][D];
-            conv_flux<D, double>(u, ph, Fc);
-            visc_flux<D, double>(u, ql, nuv, ph, Fv);
+            conv_flux<D, double, double>(u, ph, Fc);
+            visc_flux<D, double, double>(u, ql, nuv, ph, Fv);
             for (int r = 0; r < D; ++r)
                 for (int a = 0; a < M; ++a) {
                     double s = 0.0;
@@ -170,51 +184,55 @@ __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
                     sFres[(r * M + a) * NQ + g] = wJ * s;
                 }
         }
+        // Jacobian coefficients in TJ
+        TJ uj[M], qj[M][D];
+        for (int a = 0; a < M; ++a) { uj[a] = (TJ)u[a]; for (int l = 0; l < D; ++l) qj[a][l] = (TJ)q[a][l]; }
+        const TJ nuj = (TJ)nuv, wJj = (TJ)wJ;
         for (int b = 0; b < M; ++b) {
-            Dir ud[M];
-            for (int a = 0; a < M; ++a) ud[a] = {u[a], a == b ? 1.0 : 0.0};
-            Dir Fc[M][D], Fv[M][D];
-            conv_flux<D, Dir>(ud, ph, Fc);
-            visc_flux<D, Dir>(ud, q, nuv, ph, Fv);
+            DirT<TJ> ud[M];
+            for (int a = 0; a < M; ++a) ud[a] = {uj[a], a == b ? TJ(1) : TJ(0)};
+            DirT<TJ> Fc[M][D], Fv[M][D];
+            conv_flux<D, DirT<TJ>, TJ>(ud, pj, Fc);
+            visc_flux<D, DirT<TJ>, TJ>(ud, qj, nuj, pj, Fv);
             for (int a = 0; a < M; ++a)
                 for (int r = 0; r < D; ++r) {
-                    double s = 0.0;
-                    for (int k = 0; k < D; ++k) s += Jinv[r * D + k] * (Fc[a][k].t - Fv[a][k].t);
-                    vc[((((size_t)a * M + b) * D + r) * NCOEF + 0) * NQ + g] = wJ * s;
+                    TJ s = 0;
+                    for (int k = 0; k < D; ++k) s += Jj[r * D + k] * (Fc[a][k].t - Fv[a][k].t);
+                    vc[((((size_t)a * M + b) * D + r) * NCOEF + 0) * NQ + g] = wJj * s;
                 }
         }
         for (int b = 0; b < M; ++b) {
-            double cq[D][M][D];
+            TJ cq[D][M][D];
             for (int l = 0; l < D; ++l) {
-                double qe[M][D];
-                for (int a = 0; a < M; ++a) for (int k = 0; k < D; ++k) qe[a][k] = (a == b && k == l) ? 1.0 : 0.0;
-                double Fv[M][D];
-                visc_flux<D, double>(u, qe, nuv, ph, Fv);
+                TJ qe[M][D];
+                for (int a = 0; a < M; ++a) for (int k = 0; k < D; ++k) qe[a][k] = (a == b && k == l) ? TJ(1) : TJ(0);
+                TJ Fv[M][D];
+                visc_flux<D, TJ, TJ>(uj, qe, nuj, pj, Fv);
                 for (int r = 0; r < D; ++r)
                     for (int a = 0; a < M; ++a) {
-                        double s = 0.0;
-                        for (int k = 0; k < D; ++k) s += Jinv[r * D + k] * Fv[a][k];
-                        cq[r][a][l] = -wJ * s;
+                        TJ s = 0;
+                        for (int k = 0; k < D; ++k) s += Jj[r * D + k] * Fv[a][k];
+                        cq[r][a][l] = -wJj * s;
                     }
             }
             for (int a = 0; a < M; ++a)
                 for (int r = 0; r < D; ++r) {
-                    double* o = vc + ((((size_t)a * M + b) * D + r) * NCOEF) * NQ + g;
+                    TJ* o = vc + ((((size_t)a * M + b) * D + r) * NCOEF) * NQ + g;
                     for (int r2 = 0; r2 < D; ++r2) {
-                        double s = 0.0;
-                        for (int l = 0; l < D; ++l) s += cq[r][a][l] * Jinv[r2 * D + l];
+                        TJ s = 0;
+                        for (int l = 0; l < D; ++l) s += cq[r][a][l] * Jj[r2 * D + l];
                         o[(1 + r2) * NQ] = s;
                     }
                     for (int f = 0; f < NF; ++f) {
-                        double s = 0.0;
-                        for (int l = 0; l < D; ++l) s += cq[r][a][l] * NW[f * D + l];
-                        o[(1 + D + f) * NQ] = s / detJ;
+                        TJ s = 0;
+                        for (int l = 0; l < D; ++l) s += cq[r][a][l] * NWj[f * D + l];
+                        o[(1 + D + f) * NQ] = s;
                     }
                 }
         }
     }
     // face points
-    double* fc = A.fcoef + el * (size_t)(NF * M * M * NCOEF * NFQ);
+    TJ* fc = reinterpret_cast<TJ*>(A.fcoef) + el * (size_t)(NF * M * M * NCOEF * NFQ);
     for (int fs = tid; fs < NF * NFQ; fs += NTH) {
         const int f = fs / NFQ, s = fs - f * NFQ;
         double u[M], uh[M], q[M][D], ql[M][D], nuv = 0.0;
@@ -239,51 +257,57 @@ __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
         const double ws = T.wf[s];
         {
             double Fc[M][D], Fv[M][D];
-            conv_flux<D, double>(uh, ph, Fc);
-            visc_flux<D, double>(uh, ql, nuv, ph, Fv);
+            conv_flux<D, double, double>(uh, ph, Fc);
+            visc_flux<D, double, double>(uh, ql, nuv, ph, Fv);
             for (int a = 0; a < M; ++a) {
                 double fn = 0.0;
                 for (int k = 0; k < D; ++k) fn += (Fc[a][k] - Fv[a][k]) * nw[k];
-                sFH[(f * M + a) * NFQ + s] = ws * (fn + nrm * ph.tau * (u[a] - uh[a]));
+                sFH[(f * M + a) * NFQ + s] = ws * (fn + nrm * A.tau * (u[a] - uh[a]));
+                // tag-1 (Dirichlet / far-field) faces: bhat = uhat - u_b
+                sFB[(f * M + a) * NFQ + s] = (A.ftag && A.ftag[e * NF + f] == 1) ? ws * nrm * (uh[a] - A.ub[a]) : 0.0;
             }
         }
+        TJ uhj[M], qj[M][D], nwj[D];
+        for (int a = 0; a < M; ++a) { uhj[a] = (TJ)uh[a]; for (int l = 0; l < D; ++l) qj[a][l] = (TJ)q[a][l]; }
+        for (int k = 0; k < D; ++k) nwj[k] = (TJ)nw[k];
+        const TJ nuj = (TJ)nuv, wsj = (TJ)ws, taun = (TJ)(nrm * A.tau);
         for (int b = 0; b < M; ++b) {
-            Dir ud[M];
-            for (int a = 0; a < M; ++a) ud[a] = {uh[a], a == b ? 1.0 : 0.0};
-            Dir Fc[M][D], Fv[M][D];
-            conv_flux<D, Dir>(ud, ph, Fc);
-            visc_flux<D, Dir>(ud, q, nuv, ph, Fv);
+            DirT<TJ> ud[M];
+            for (int a = 0; a < M; ++a) ud[a] = {uhj[a], a == b ? TJ(1) : TJ(0)};
+            DirT<TJ> Fc[M][D], Fv[M][D];
+            conv_flux<D, DirT<TJ>, TJ>(ud, pj, Fc);
+            visc_flux<D, DirT<TJ>, TJ>(ud, qj, nuj, pj, Fv);
             for (int a = 0; a < M; ++a) {
-                double fn = 0.0;
-                for (int k = 0; k < D; ++k) fn += (Fc[a][k].t - Fv[a][k].t) * nw[k];
-                if (a == b) fn -= nrm * ph.tau;
-                fc[((((size_t)f * M + a) * M + b) * NCOEF + 0) * NFQ + s] = ws * fn;
+                TJ fn = 0;
+                for (int k = 0; k < D; ++k) fn += (Fc[a][k].t - Fv[a][k].t) * nwj[k];
+                if (a == b) fn -= taun;
+                fc[((((size_t)f * M + a) * M + b) * NCOEF + 0) * NFQ + s] = wsj * fn;
             }
         }
         for (int b = 0; b < M; ++b) {
-            double qh[M][D];
+            TJ qh[M][D];
             for (int l = 0; l < D; ++l) {
-                double qe[M][D];
-                for (int a = 0; a < M; ++a) for (int k = 0; k < D; ++k) qe[a][k] = (a == b && k == l) ? 1.0 : 0.0;
-                double Fv[M][D];
-                visc_flux<D, double>(uh, qe, nuv, ph, Fv);
+                TJ qe[M][D];
+                for (int a = 0; a < M; ++a) for (int k = 0; k < D; ++k) qe[a][k] = (a == b && k == l) ? TJ(1) : TJ(0);
+                TJ Fv[M][D];
+                visc_flux<D, TJ, TJ>(uhj, qe, nuj, pj, Fv);
                 for (int a = 0; a < M; ++a) {
-                    double fn = 0.0;
-                    for (int k = 0; k < D; ++k) fn += Fv[a][k] * nw[k];
-                    qh[a][l] = -ws * fn;
+                    TJ fn = 0;
+                    for (int k = 0; k < D; ++k) fn += Fv[a][k] * nwj[k];
+                    qh[a][l] = -wsj * fn;
                 }
             }
             for (int a = 0; a < M; ++a) {
-                double* o = fc + ((((size_t)f * M + a) * M + b) * NCOEF) * NFQ + s;
+                TJ* o = fc + ((((size_t)f * M + a) * M + b) * NCOEF) * NFQ + s;
                 for (int r2 = 0; r2 < D; ++r2) {
-                    double t = 0.0;
-                    for (int l = 0; l < D; ++l) t += qh[a][l] * Jinv[r2 * D + l];
+                    TJ t = 0;
+                    for (int l = 0; l < D; ++l) t += qh[a][l] * Jj[r2 * D + l];
                     o[(1 + r2) * NFQ] = t;
                 }
                 for (int f2 = 0; f2 < NF; ++f2) {
-                    double t = 0.0;
-                    for (int l = 0; l < D; ++l) t += qh[a][l] * NW[f2 * D + l];
-                    o[(1 + D + f2) * NFQ] = t / detJ;
+                    TJ t = 0;
+                    for (int l = 0; l < D; ++l) t += qh[a][l] * NWj[f2 * D + l];
+                    o[(1 + D + f2) * NFQ] = t;
                 }
             }
         }
@@ -293,10 +317,14 @@ __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
     double* rbe = A.rb + el * A.rb_es;
     for (int idx = tid; idx < NT; idx += NTH) {
         int f = idx / (M * NFP), rem = idx - f * M * NFP, a = rem / NFP, l = rem - a * NFP;
-        double s = 0.0;
-        for (int q = 0; q < NFQ; ++q) s += T.mu[q * NFP + l] * sFH[(f * M + a) * NFQ + q];
+        double s = 0.0, sb = 0.0;
+        for (int q = 0; q < NFQ; ++q) {
+            s += T.mu[q * NFP + l] * sFH[(f * M + a) * NFQ + q];
+            sb += T.mu[q * NFP + l] * sFB[(f * M + a) * NFQ + q];
+        }
         sRh[idx] = s;
-        rbe[idx * A.rb_rs] = s;
+        const bool bnd = A.ftag && A.ftag[e * NF + f] != 0;
+        rbe[idx * A.rb_rs] = bnd ? sb : s;
     }
     __syncthreads();
     double* rte = A.rt + e * A.rt_es;
@@ -322,7 +350,9 @@ __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
 // ----------------------------------------------------------------------------
 template <class TL>
 struct BlkArgs {
-    const double* vcoef; const double* fcoef; const double* geo;
+    const void* vcoef; const void* fcoef;   // Jacobian coefficients in the accumulation type
+    const int32_t* ftag;                    // [E][nf] or NULL
+    const double* geo;
     DeviceTables tab;
     Regions<TL> R;
     double dt, a_ii, tau;
@@ -362,7 +392,17 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
     TA* As = sm;
     TA* Bs = As + KC * NPP;
     TA* Cs = Bs + KC * NCBP;
-    const double* cf = A.vcoef + (((size_t)el * M + a) * M + b) * (size_t)(D * NCOEF * NQ);
+    const TA* cf = reinterpret_cast<const TA*>(A.vcoef) + (((size_t)el * M + a) * M + b) * (size_t)(D * NCOEF * NQ);
+    // reference tables in the accumulation type
+    constexpr bool F32 = sizeof(TA) == 4;
+    const TA* tphi = F32 ? (const TA*)T.fphi : (const TA*)T.phi;
+    const TA* tdphi = F32 ? (const TA*)T.fdphi : (const TA*)T.dphi;
+    const TA* tpsi = F32 ? (const TA*)T.fpsi : (const TA*)T.psi;
+    const TA* ttheta = F32 ? (const TA*)T.ftheta : (const TA*)T.theta;
+    const TA* tpsif = F32 ? (const TA*)T.fpsi_f : (const TA*)T.psi_f;
+    const TA* tthetaf = F32 ? (const TA*)T.ftheta_f : (const TA*)T.theta_f;
+    const TA* tmu = F32 ? (const TA*)T.fmu : (const TA*)T.mu;
+    const TA* tmf = F32 ? (const TA*)T.fmf : (const TA*)T.mf;
 
     constexpr bool FLAT = S::FLAT;
     constexpr int SL = FLAT ? S::SLOTS : TM * TN;
@@ -385,9 +425,9 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
         const int kc = min(KC, K - k0);
         for (int idx = tid; idx < kc * NCOEF; idx += NTH) {
             int kk = idx / NCOEF, c = idx - kk * NCOEF, k = k0 + kk, r = k / NQ, g = k - r * NQ;
-            Cs[idx] = (TA)cf[(r * NCOEF + c) * NQ + g];
+            Cs[idx] = cf[(r * NCOEF + c) * NQ + g];
         }
-        for (int idx = tid; idx < kc * NPP; idx += NTH) As[idx] = (TA)T.dphi[(size_t)k0 * NP + idx];
+        for (int idx = tid; idx < kc * NPP; idx += NTH) As[idx] = tdphi[(size_t)k0 * NP + idx];
         __syncthreads();
         for (int idx = tid; idx < kc * NCBP; idx += NTH) {
             int kk = idx / NCBP, c = idx - kk * NCBP;
@@ -395,11 +435,11 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
             const TA* cc = Cs + kk * NCOEF;
             TA v;
             if (c < NP) {
-                v = cc[0] * (TA)T.phi[g * NP + c];
-                for (int r2 = 0; r2 < D; ++r2) v -= cc[1 + r2] * (TA)T.psi[((size_t)r2 * NQ + g) * NP + c];
+                v = cc[0] * tphi[g * NP + c];
+                for (int r2 = 0; r2 < D; ++r2) v -= cc[1 + r2] * tpsi[((size_t)r2 * NQ + g) * NP + c];
             } else {
                 int c2 = c - NP, f = c2 / NFP, l = c2 - f * NFP;
-                v = cc[1 + D + f] * (TA)T.theta[((size_t)f * NQ + g) * NFP + l];
+                v = cc[1 + D + f] * ttheta[((size_t)f * NQ + g) * NFP + l];
             }
             Bs[idx] = v;
         }
@@ -455,19 +495,19 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
     const double* Jg = G + 1;
     (void)Jg;
     for (int f = 0; f < NF; ++f) {
-        const double* fsrc = A.fcoef + ((((size_t)el * NF + f) * M + a) * M + b) * (size_t)(NCOEF * NFQ);
-        for (int idx = tid; idx < NCOEF * NFQ; idx += NTH) Fc[idx] = (TA)fsrc[idx];
+        const TA* fsrc = reinterpret_cast<const TA*>(A.fcoef) + ((((size_t)el * NF + f) * M + a) * M + b) * (size_t)(NCOEF * NFQ);
+        for (int idx = tid; idx < NCOEF * NFQ; idx += NTH) Fc[idx] = fsrc[idx];
         __syncthreads();
         for (int idx = tid; idx < NFQ * NCB; idx += NTH) {
             int s = idx / NCB, c = idx - s * NCB;
             TA v = 0;
             if (c < NP) {
                 for (int r2 = 0; r2 < D; ++r2)
-                    v -= Fc[(1 + r2) * NFQ + s] * (TA)T.psi_f[(((size_t)f * D + r2) * NFQ + s) * NP + c];
+                    v -= Fc[(1 + r2) * NFQ + s] * tpsif[(((size_t)f * D + r2) * NFQ + s) * NP + c];
             } else {
                 int c2 = c - NP, f2 = c2 / NFP, l2 = c2 - f2 * NFP;
-                v = Fc[(1 + D + f2) * NFQ + s] * (TA)T.theta_f[(((size_t)f * NF + f2) * NFQ + s) * NFP + l2];
-                if (f2 == f) v += Fc[s] * (TA)T.mu[s * NFP + l2];
+                v = Fc[(1 + D + f2) * NFQ + s] * tthetaf[(((size_t)f * NF + f2) * NFQ + s) * NFP + l2];
+                if (f2 == f) v += Fc[s] * tmu[s * NFP + l2];
             }
             Tt[idx] = v;
         }
@@ -475,28 +515,33 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
         double nrm = 0.0;
         for (int k = 0; k < D; ++k) nrm += NW[f * D + k] * NW[f * D + k];
         nrm = sqrt(nrm);
+        const TA taun = (TA)(A.tau * nrm), dtt = (TA)A.dt;
+        const bool bnd = A.ftag && A.ftag[e * NF + f] != 0;
+        const TA nrmt = (TA)nrm;
         for (int idx = tid; idx < NFP * NCB; idx += NTH) {
             int lam = idx / NCB, c = idx - lam * NCB;
-            TA vs = 0;
-            for (int s = 0; s < NFQ; ++s) vs += (TA)T.mu[s * NFP + lam] * Tt[s * NCB + c];
-            double v = (double)vs;
+            TA v = 0;
+            for (int s = 0; s < NFQ; ++s) v += tmu[s * NFP + lam] * Tt[s * NCB + c];
             const int64_t trow = (f * M + a) * NFP + lam;
             const int64_t irow = a * NP + T.fnode[f * NFP + lam];
             if (c < NP) {
                 if (a == b) {
                     for (int k = 0; k < D; ++k) {
                         int nfc = T.node_face[c * D + k];
-                        if (nfc >= 0 && nfc / NFP == f) v += A.tau * nrm * T.mf[lam * NFP + (nfc - f * NFP)];
+                        if (nfc >= 0 && nfc / NFP == f) v += taun * tmf[lam * NFP + (nfc - f * NFP)];
                     }
                 }
                 const int col = b * NP + c;
-                A21[trow * A.R.a21_rs + col] = (TL)v;
-                A11[irow * A.R.a11_rs + col] += A.dt * v;
+                // trace rows of a boundary face do not depend on the interior state
+                A21[trow * A.R.a21_rs + col] = bnd ? (TL)0 : (TL)v;
+                A11[irow * A.R.a11_rs + col] += A.dt * (double)v;
             } else {
                 int c2 = c - NP, f2 = c2 / NFP, l2 = c2 - f2 * NFP;
                 const int col = (f2 * M + b) * NFP + l2;
-                A22[trow * A.R.a22_rs + col] = (TL)v;
-                A12[irow * A.R.a12_rs + col] = (TL)((double)A12[irow * A.R.a12_rs + col] + A.dt * v);
+                // boundary face: d bhat / d uhat = face mass matrix, diagonal in components
+                const TA vb = (f2 == f && a == b) ? nrmt * tmf[lam * NFP + l2] : (TA)0;
+                A22[trow * A.R.a22_rs + col] = bnd ? (TL)vb : (TL)v;
+                A12[irow * A.R.a12_rs + col] = (TL)(A12[irow * A.R.a12_rs + col] + dtt * v);
             }
         }
         __syncthreads();
@@ -877,7 +922,7 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
     const size_t sm_point = sizeof(double) * point_smem_doubles<C>();
     const size_t sm_blk = sizeof(double) * BS_::smem;
     const size_t sm_elim = sizeof(double) * elim_smem_doubles<C, NB>();
-    HDG_CK(cudaFuncSetAttribute(k_point<C, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_point));
+    HDG_CK(cudaFuncSetAttribute(k_point<C, PT, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_point));
     HDG_CK(cudaFuncSetAttribute(kblk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
     HDG_CK(cudaFuncSetAttribute(k_elim<C, NB, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
     HDG_CK(cudaFuncSetAttribute(k_elim<C, NB, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
@@ -886,20 +931,22 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
     HDG_CK(cudaMemsetAsync(h->d_g, 0, sizeof(double) * h->F * C::BS, st));
     PointArgs pa;
     pa.U = la.U; pa.Q = la.Q; pa.UH = la.UH; pa.Ustar = la.Ustar; pa.nu = la.nu;
-    pa.dt = la.dt; pa.a_ii = la.a_ii; pa.ph = h->phys; pa.tab = h->tab; pa.geo = h->d_geo;
+    pa.dt = la.dt; pa.a_ii = la.a_ii; pa.ph = phys_t<double>(h->phys); pa.phf = phys_t<float>(h->phys);
+    pa.tau = h->phys.tau; pa.tab = h->tab; pa.geo = h->d_geo;
     const Regions<double> RG = fp64_regions<C>(h->d_top, h->d_bot);
     pa.e2f = h->d_e2f; pa.perm = h->d_perm;
     pa.rt = RG.rt; pa.rt_es = RG.rt_es; pa.rt_rs = RG.rt_rs;
     pa.rb = RG.rb; pa.rb_es = RG.rb_es; pa.rb_rs = RG.rb_rs;
     pa.vcoef = h->d_vcoef; pa.fcoef = h->d_fcoef; pa.dq0 = h->d_dq0;
+    pa.ftag = h->d_ftag; pa.ub = h->d_ub;
     BlkArgs<double> ba;
-    ba.vcoef = h->d_vcoef; ba.fcoef = h->d_fcoef; ba.geo = h->d_geo; ba.tab = h->tab;
+    ba.vcoef = h->d_vcoef; ba.fcoef = h->d_fcoef; ba.geo = h->d_geo; ba.tab = h->tab; ba.ftag = h->d_ftag;
     ba.R = RG; ba.dt = la.dt; ba.a_ii = la.a_ii; ba.tau = h->phys.tau;
     for (int64_t e0 = 0; e0 < h->E; e0 += h->chunk) {
         const int64_t ne = std::min<int64_t>(h->chunk, h->E - e0);
         pa.e0 = e0; ba.e0 = e0;
         prof_begin(h, HDG_K_POINT);
-        k_point<C, PT><<<(unsigned)ne, PT, sm_point, st>>>(pa);
+        k_point<C, PT, double><<<(unsigned)ne, PT, sm_point, st>>>(pa);
         prof_end(h);
         prof_begin(h, HDG_K_BLOCKS);
         kblk<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
@@ -925,6 +972,7 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
     h->have_system = true;
     h->sys_prec = HDG_PREC_FP64;
     h->bj_ready = false;
+    h->asm_ready = false;
     return HDG_OK;
 }
 

@@ -15,7 +15,7 @@ namespace hdg {
 
 // one (up to) 64 x 64 tile of A22 -= L21 U12 in type T; rows/cols >= r_end/c_end skipped
 template <int NII, int NJJ, int NB, int TCW, class T, class RowP>
-__device__ __forceinline__ void trail_tile_t(RowP rowp, const double* pan, const T* ust, int rb, int ct, int k0,
+__device__ __forceinline__ void trail_tile_t(RowP rowp, const T* pan, const T* ust, int rb, int ct, int lrow0,
                                              int kb, int tx, int ty, int r_end, int c_end) {
     T acc[NII][NJJ];
     T* rp[NII];
@@ -34,7 +34,7 @@ __device__ __forceinline__ void trail_tile_t(RowP rowp, const double* pan, const
 #pragma unroll
         for (int ii = 0; ii < NII; ++ii) {
             int r = rb + ty + 16 * ii;
-            lv[ii] = (r < r_end) ? (T)pan[(size_t)(r - k0) * NB + j] : T(0);
+            lv[ii] = (r < r_end) ? pan[(size_t)(r - lrow0) * NB + j] : T(0);
         }
 #pragma unroll
         for (int jj = 0; jj < NJJ; ++jj) uv[jj] = ust[j * TCW + tx + 16 * jj];
@@ -59,7 +59,7 @@ __device__ __forceinline__ void trail_tile_t(RowP rowp, const double* pan, const
 // row j at urow(j)
 template <class T, int NB, int NTH, class RowP, class URow>
 __device__ void trailing_region(RowP rowp, URow urow, int r_begin, int r_end, int c_begin, int c_end,
-                                const double* pan, int k0, int kb, T* ust) {
+                                const T* pan, int lrow0, int kb, T* ust) {
     constexpr int TCW = 64;
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
 #pragma unroll 1
@@ -76,7 +76,7 @@ __device__ void trailing_region(RowP rowp, URow urow, int r_begin, int r_end, in
             int nii = 0;
             while (nii < 4 && rb + 16 * nii < r_end) ++nii;
             switch (nii * 4 + njj - 5) {
-#define HDG_TT(I, J) case (I) * 4 + (J) - 5: trail_tile_t<I, J, NB, TCW, T>(rowp, pan, ust, rb, ct, k0, kb, tx, ty, r_end, c_end); break;
+#define HDG_TT(I, J) case (I) * 4 + (J) - 5: trail_tile_t<I, J, NB, TCW, T>(rowp, pan, ust, rb, ct, lrow0, kb, tx, ty, r_end, c_end); break;
                 HDG_TT(1, 1) HDG_TT(1, 2) HDG_TT(1, 3) HDG_TT(1, 4)
                 HDG_TT(2, 1) HDG_TT(2, 2) HDG_TT(2, 3) HDG_TT(2, 4)
                 HDG_TT(3, 1) HDG_TT(3, 2) HDG_TT(3, 3) HDG_TT(3, 4)
@@ -90,10 +90,13 @@ __device__ void trailing_region(RowP rowp, URow urow, int r_begin, int r_end, in
 }
 
 template <class C, int NB>
-constexpr int elim_mixed_smem_bytes() { return (C::NR * NB + NB * 64) * 8 + NB * 64 * 4; }
+constexpr int elim_mixed_smem_bytes() {
+    return C::NU * NB * 8 + NB * 64 * 8 +                     // top panel (FP64), U12 staging (FP64)
+           (C::NT * NB + C::NU * NB + NB * 64 + NB) * 4;      // bottom panel, top panel copy, staging, pivot row (FP32)
+}
 
 template <class C, int NB, int NTH>
-__global__ void __launch_bounds__(NTH, 1) k_elim_mixed(Regions<float> R, int64_t e0, int32_t* status) {
+__global__ void __launch_bounds__(NTH, 2) k_elim_mixed(Regions<float> R, int64_t e0, int32_t* status) {
     constexpr int NU = C::NU, NT = C::NT, NR = C::NR;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t el = blockIdx.x, e = e0 + el;
@@ -103,9 +106,12 @@ __global__ void __launch_bounds__(NTH, 1) k_elim_mixed(Regions<float> R, int64_t
     double* rt = R.rt + e * R.rt_es;
     const int64_t s11 = R.a11_rs, s12 = R.a12_rs, s21 = R.a21_rs, srt = R.rt_rs;
     extern __shared__ double sm[];
-    double* pan = sm;                              // [NR][NB]
-    double* ust64 = pan + NR * NB;                 // [NB][64]
-    float* ust32 = reinterpret_cast<float*>(ust64 + NB * 64);
+    double* pan = sm;                                        // [NU][NB]  rows of At (FP64), relative to k0
+    double* ust64 = pan + NU * NB;                           // [NB][64]
+    float* panb = reinterpret_cast<float*>(ust64 + NB * 64); // [NT][NB]  rows of Ct (FP32)
+    float* pant = panb + NT * NB;                            // [NU][NB]  FP32 copy of pan
+    float* ust32 = pant + NU * NB;                           // [NB][64]
+    float* prow = ust32 + NB * 64;                           // [NB]      pivot row (FP32)
     __shared__ int piv[NB];
     __shared__ double rv[NTH / 32];
     __shared__ int ri[NTH / 32];
@@ -113,11 +119,16 @@ __global__ void __launch_bounds__(NTH, 1) k_elim_mixed(Regions<float> R, int64_t
     if (tid == 0) sflag = 0;
 
     for (int k0 = 0; k0 < NU; k0 += NB) {
-        const int kb = min(NB, NU - k0), nrows = NR - k0, ntop = NU - k0;
+        const int kb = min(NB, NU - k0), ntop = NU - k0;
 #pragma unroll 1
-        for (int idx = tid; idx < nrows * kb; idx += NTH) {
-            int rr = idx / kb, c = idx - rr * kb, r = k0 + rr;
-            pan[rr * NB + c] = r < NU ? A11[r * s11 + k0 + c] : (double)A21[(r - NU) * s21 + k0 + c];
+        for (int idx = tid; idx < ntop * kb; idx += NTH) {
+            int rr = idx / kb, c = idx - rr * kb;
+            pan[rr * NB + c] = A11[(k0 + rr) * s11 + k0 + c];
+        }
+#pragma unroll 1
+        for (int idx = tid; idx < NT * kb; idx += NTH) {
+            int rr = idx / kb, c = idx - rr * kb;
+            panb[rr * NB + c] = A21[rr * s21 + k0 + c];
         }
         __syncthreads();
         for (int j = 0; j < kb; ++j) {
@@ -145,12 +156,14 @@ __global__ void __launch_bounds__(NTH, 1) k_elim_mixed(Regions<float> R, int64_t
             }
             __syncthreads();
             const int pr = piv[j];
-            if (pr != j)
-                for (int c = tid; c < kb; c += NTH) {
+            for (int c = tid; c < kb; c += NTH) {
+                if (pr != j) {
                     double t = pan[j * NB + c];
                     pan[j * NB + c] = pan[pr * NB + c];
                     pan[pr * NB + c] = t;
                 }
+                prow[c] = (float)pan[j * NB + c];
+            }
             __syncthreads();
             double pv = pan[j * NB + j];
             if (pv == 0.0 || !isfinite(pv)) {
@@ -158,55 +171,74 @@ __global__ void __launch_bounds__(NTH, 1) k_elim_mixed(Regions<float> R, int64_t
                 pv = 1.0;
             }
             const double inv = 1.0 / pv;
+            const float invf = (float)inv;
 #pragma unroll 1
-            for (int rr = j + 1 + tid; rr < nrows; rr += NTH) {
+            for (int rr = j + 1 + tid; rr < ntop; rr += NTH) {       // rows of At: FP64
                 double l = pan[rr * NB + j] * inv;
                 pan[rr * NB + j] = l;
                 for (int c = j + 1; c < kb; ++c) pan[rr * NB + c] = fma(-l, pan[j * NB + c], pan[rr * NB + c]);
             }
+#pragma unroll 1
+            for (int rr = tid; rr < NT; rr += NTH) {                 // rows of Ct: FP32 multipliers
+                float l = panb[rr * NB + j] * invf;
+                panb[rr * NB + j] = l;
+                for (int c = j + 1; c < kb; ++c) panb[rr * NB + c] = fmaf(-l, prow[c], panb[rr * NB + c]);
+            }
             __syncthreads();
         }
 #pragma unroll 1
-        for (int idx = tid; idx < nrows * kb; idx += NTH) {
-            int rr = idx / kb, c = idx - rr * kb, r = k0 + rr;
-            if (r < NU) A11[r * s11 + k0 + c] = pan[rr * NB + c];
-            else A21[(r - NU) * s21 + k0 + c] = (float)pan[rr * NB + c];
+        for (int idx = tid; idx < ntop * kb; idx += NTH) {
+            int rr = idx / kb, c = idx - rr * kb;
+            A11[(k0 + rr) * s11 + k0 + c] = pan[rr * NB + c];
+            pant[rr * NB + c] = (float)pan[rr * NB + c];
         }
-        // trailing columns of the interior rows: swaps and U12 = L11^{-1} A12,
-        // columns [c0, NU) of At, all columns of Bt, and Rt
-        const int c0 = k0 + kb;
-        const int ncols = (NU - c0) + NT + 1;
 #pragma unroll 1
-        for (int cc = tid; cc < ncols; cc += NTH) {
-            const int kind = cc < NU - c0 ? 0 : (cc < NU - c0 + NT ? 1 : 2);
-            auto at = [&](int r) -> double {
-                if (kind == 0) return A11[r * s11 + c0 + cc];
-                if (kind == 1) return (double)A12[r * s12 + (cc - (NU - c0))];
-                return rt[r * srt];
-            };
-            auto put = [&](int r, double v) {
-                if (kind == 0) A11[r * s11 + c0 + cc] = v;
-                else if (kind == 1) A12[r * s12 + (cc - (NU - c0))] = (float)v;
-                else rt[r * srt] = v;
-            };
-            for (int j = 0; j < kb; ++j) {
-                int pr = piv[j];
-                if (pr != j) {
-                    double x = at(k0 + j), y = at(k0 + pr);
-                    put(k0 + j, y);
-                    put(k0 + pr, x);
+        for (int idx = tid; idx < NT * kb; idx += NTH) {
+            int rr = idx / kb, c = idx - rr * kb;
+            A21[rr * s21 + k0 + c] = panb[rr * NB + c];
+        }
+        __syncthreads();
+        // interior rows of the trailing columns: swaps, then U12 = L11^{-1} A12
+        const int c0 = k0 + kb;
+        const int nd = NU - c0 + 1;                               // FP64 columns: At [c0, NU) and Rt
+#pragma unroll 1
+        for (int cc = tid; cc < nd + NT; cc += NTH) {
+            if (cc < nd) {
+                double* col = cc < nd - 1 ? A11 + c0 + cc : rt;
+                const int64_t st = cc < nd - 1 ? s11 : srt;
+                for (int j = 0; j < kb; ++j) {
+                    int pr = piv[j];
+                    if (pr != j) { double t = col[(k0 + j) * st]; col[(k0 + j) * st] = col[(k0 + pr) * st]; col[(k0 + pr) * st] = t; }
                 }
-            }
-            double xv[NB];
+                double xv[NB];
 #pragma unroll
-            for (int j = 0; j < NB; ++j) {
-                if (j < kb) {
-                    double s = at(k0 + j);
+                for (int j = 0; j < NB; ++j) {
+                    if (j < kb) {
+                        double s = col[(k0 + j) * st];
 #pragma unroll
-                    for (int i = 0; i < NB; ++i)
-                        if (i < j) s = fma(-pan[j * NB + i], xv[i], s);
-                    xv[j] = s;
-                    put(k0 + j, s);
+                        for (int i = 0; i < NB; ++i)
+                            if (i < j) s = fma(-pan[j * NB + i], xv[i], s);
+                        xv[j] = s;
+                        col[(k0 + j) * st] = s;
+                    }
+                }
+            } else {
+                float* col = A12 + (cc - nd);
+                for (int j = 0; j < kb; ++j) {
+                    int pr = piv[j];
+                    if (pr != j) { float t = col[(k0 + j) * s12]; col[(k0 + j) * s12] = col[(k0 + pr) * s12]; col[(k0 + pr) * s12] = t; }
+                }
+                float xv[NB];
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    if (j < kb) {
+                        float s = col[(k0 + j) * s12];
+#pragma unroll
+                        for (int i = 0; i < NB; ++i)
+                            if (i < j) s = fmaf(-pant[j * NB + i], xv[i], s);
+                        xv[j] = s;
+                        col[(k0 + j) * s12] = s;
+                    }
                 }
             }
         }
@@ -215,14 +247,14 @@ __global__ void __launch_bounds__(NTH, 1) k_elim_mixed(Regions<float> R, int64_t
         trailing_region<double, NB, NTH>([&](int r) { return A11 + r * s11; },
                                          [&](int j) { return (const double*)(A11 + (k0 + j) * s11); },
                                          c0, NU, c0, NU, pan, k0, kb, ust64);
-        // Ct multipliers (FP32): rows [NU, NR) x cols [c0, NU)
-        trailing_region<float, NB, NTH>([&](int r) { return A21 + (r - NU) * s21; },
+        // Ct multipliers (FP32): rows of Ct x cols [c0, NU)
+        trailing_region<float, NB, NTH>([&](int r) { return A21 + r * s21; },
                                         [&](int j) { return (const double*)(A11 + (k0 + j) * s11); },
-                                        NU, NR, c0, NU, pan, k0, kb, ust32);
+                                        0, NT, c0, NU, panb, 0, kb, ust32);
         // Bt (FP32): rows [c0, NU) x all t columns
         trailing_region<float, NB, NTH>([&](int r) { return A12 + r * s12; },
                                         [&](int j) { return (const float*)(A12 + (k0 + j) * s12); },
-                                        c0, NU, 0, NT, pan, k0, kb, ust32);
+                                        c0, NU, 0, NT, pant, k0, kb, ust32);
         // Rt (FP64): rows [c0, NU)
 #pragma unroll 1
         for (int r = c0 + tid; r < NU; r += NTH) {
@@ -370,6 +402,42 @@ __global__ void __launch_bounds__(MvShape<C>::NTH) k_matvec_t(const int32_t* row
     }
 }
 
+// y = S x with FP32 blocks and an FP32 copy of x: products and the sum within
+// each block in FP32, the sum over a row's blocks in FP64
+__global__ void k_to_f32(const double* x, float* y, int64_t n);   // solve_vec.cu
+
+template <class C>
+__global__ void __launch_bounds__(MvShape<C>::NTH) k_matvec_f32(const int32_t* rowptr, const int32_t* col,
+                                                                const float* vals, const float* x, double* y) {
+    constexpr int BS = C::BS, RB = MvShape<C>::RB, GROUPS = MvShape<C>::GROUPS;
+    __shared__ double part[GROUPS][RB];
+    const int64_t F = blockIdx.x;
+    const int grp = threadIdx.x / RB, r = threadIdx.x - grp * RB;
+    double acc = 0.0;
+    if (r < BS) {
+        for (int b = rowptr[F] + grp; b < rowptr[F + 1]; b += GROUPS) {
+            const float* xs = x + (size_t)col[b] * BS;
+            const float* v = vals + (size_t)b * BS * BS + r;
+            float a0 = 0.f, a1 = 0.f;
+            int c = 0;
+#pragma unroll 4
+            for (; c + 1 < BS; c += 2) {
+                a0 = fmaf(v[(size_t)c * BS], xs[c], a0);
+                a1 = fmaf(v[(size_t)(c + 1) * BS], xs[c + 1], a1);
+            }
+            if (c < BS) a0 = fmaf(v[(size_t)c * BS], xs[c], a0);
+            acc += (double)(a0 + a1);
+        }
+    }
+    part[grp][r] = acc;
+    __syncthreads();
+    if (grp == 0 && r < BS) {
+        double s = part[0][r];
+        for (int g2 = 1; g2 < GROUPS; ++g2) s += part[g2][r];
+        y[F * BS + r] = s;
+    }
+}
+
 // recovery from region views: dU = -U^{-1}(z + Z dUhat), dQ = dq0 - L dU + Lambda dUhat
 template <class C, class TL, int NTH>
 __global__ void __launch_bounds__(NTH) k_recover_r(Regions<TL> R, RecArgs A) {
@@ -494,12 +562,13 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
         if ((rc = mixed_alloc(h, &h->d_m22, ch * C::NT * C::NT))) return rc;
         if ((rc = mixed_alloc(h, &h->d_mrb, ch * C::NT))) return rc;
         if ((rc = mixed_alloc(h, &h->d_vals32, (size_t)h->nnzb * C::BS * C::BS))) return rc;
+        if ((rc = mixed_alloc(h, &h->d_x32, (size_t)h->F * C::BS))) return rc;
     }
     auto kblk = k_blocks<C, BC::TY, BC::TX, BC::KC, float, float>;
     const size_t sm_point = sizeof(double) * point_smem_doubles<C>();
     const size_t sm_blk = sizeof(float) * BS_::smem;
     const size_t sm_elim = elim_mixed_smem_bytes<C, NB>();
-    HDG_CK(cudaFuncSetAttribute(k_point<C, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_point));
+    HDG_CK(cudaFuncSetAttribute(k_point<C, PT, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_point));
     HDG_CK(cudaFuncSetAttribute(kblk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
     HDG_CK(cudaFuncSetAttribute(k_elim_mixed<C, NB, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
     cudaStream_t st = h->stream;
@@ -508,19 +577,21 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
     const Regions<float> RM = mixed_regions(h);
     PointArgs pa;
     pa.U = la.U; pa.Q = la.Q; pa.UH = la.UH; pa.Ustar = la.Ustar; pa.nu = la.nu;
-    pa.dt = la.dt; pa.a_ii = la.a_ii; pa.ph = h->phys; pa.tab = h->tab; pa.geo = h->d_geo;
+    pa.dt = la.dt; pa.a_ii = la.a_ii; pa.ph = phys_t<double>(h->phys); pa.phf = phys_t<float>(h->phys);
+    pa.tau = h->phys.tau; pa.tab = h->tab; pa.geo = h->d_geo;
     pa.e2f = h->d_e2f; pa.perm = h->d_perm;
     pa.rt = RM.rt; pa.rt_es = RM.rt_es; pa.rt_rs = RM.rt_rs;
     pa.rb = RM.rb; pa.rb_es = RM.rb_es; pa.rb_rs = RM.rb_rs;
     pa.vcoef = h->d_vcoef; pa.fcoef = h->d_fcoef; pa.dq0 = h->d_dq0;
+    pa.ftag = h->d_ftag; pa.ub = h->d_ub;
     BlkArgs<float> ba;
-    ba.vcoef = h->d_vcoef; ba.fcoef = h->d_fcoef; ba.geo = h->d_geo; ba.tab = h->tab;
+    ba.vcoef = h->d_vcoef; ba.fcoef = h->d_fcoef; ba.geo = h->d_geo; ba.tab = h->tab; ba.ftag = h->d_ftag;
     ba.R = RM; ba.dt = la.dt; ba.a_ii = la.a_ii; ba.tau = h->phys.tau;
     for (int64_t e0 = 0; e0 < h->E; e0 += h->chunk) {
         const int64_t ne = std::min<int64_t>(h->chunk, h->E - e0);
         pa.e0 = e0; ba.e0 = e0;
         prof_begin(h, HDG_K_POINT);
-        k_point<C, PT><<<(unsigned)ne, PT, sm_point, st>>>(pa);
+        k_point<C, PT, float><<<(unsigned)ne, PT, sm_point, st>>>(pa);
         prof_end(h);
         prof_begin(h, HDG_K_BLOCKS);
         kblk<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
@@ -560,6 +631,7 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
     h->have_system = true;
     h->sys_prec = HDG_PREC_MIXED;
     h->bj_ready = false;
+    h->asm_ready = false;
     return HDG_OK;
 }
 
@@ -567,9 +639,12 @@ template <int D, int P>
 int run_matvec(hdg_ctx* h, const double* x, double* y) {
     using C = Cfg<D, P>;
     prof_begin(h, HDG_K_MATVEC);
-    if (h->sys_prec == HDG_PREC_MIXED)
-        k_matvec_t<C, float><<<(unsigned)h->F, MvShape<C>::NTH, 0, h->stream>>>(h->d_rowptr, h->d_col, h->d_vals32, x, y);
-    else
+    if (h->sys_prec == HDG_PREC_MIXED) {
+        const int64_t n = h->F * C::BS;
+        k_to_f32<<<(unsigned)std::min<int64_t>(1216, (n + 255) / 256), 256, 0, h->stream>>>(x, h->d_x32, n);
+        k_matvec_f32<C><<<(unsigned)h->F, MvShape<C>::NTH, 0, h->stream>>>(h->d_rowptr, h->d_col, h->d_vals32,
+                                                                          h->d_x32, y);
+    } else
         k_matvec<C><<<(unsigned)h->F, MvShape<C>::NTH, 0, h->stream>>>(h->d_rowptr, h->d_col, h->d_vals, x, y);
     prof_end(h);
     HDG_CK(cudaGetLastError());

@@ -1,47 +1,82 @@
 // Compressible Navier-Stokes fluxes on the device (Sec. 2.1), generic in the
-// scalar type so that one code path gives values (double) and directional
-// derivatives with respect to the state (Dir: value + one tangent).
+// scalar type: S = double or float for values, DirT<S> (value + one tangent)
+// for directional derivatives with respect to the state.  All constants come
+// from PhysT<S>, so a float evaluation never promotes to double.
 #pragma once
 
 #include "common.h"
 
 namespace hdg {
 
-struct Dir {
-    double v, t;  // value, tangent
+template <class S>
+struct DirT {
+    S v, t;  // value, tangent
 };
-__device__ __forceinline__ Dir operator+(Dir a, Dir b) { return {a.v + b.v, a.t + b.t}; }
-__device__ __forceinline__ Dir operator-(Dir a, Dir b) { return {a.v - b.v, a.t - b.t}; }
-__device__ __forceinline__ Dir operator*(Dir a, Dir b) { return {a.v * b.v, a.t * b.v + a.v * b.t}; }
-__device__ __forceinline__ Dir operator+(Dir a, double b) { return {a.v + b, a.t}; }
-__device__ __forceinline__ Dir operator-(Dir a, double b) { return {a.v - b, a.t}; }
-__device__ __forceinline__ Dir operator*(Dir a, double b) { return {a.v * b, a.t * b}; }
-__device__ __forceinline__ Dir operator*(double b, Dir a) { return {a.v * b, a.t * b}; }
-__device__ __forceinline__ Dir recip(Dir a) { double r = 1.0 / a.v; return {r, -a.t * r * r}; }
+template <class S> __device__ __forceinline__ DirT<S> operator+(DirT<S> a, DirT<S> b) { return {a.v + b.v, a.t + b.t}; }
+template <class S> __device__ __forceinline__ DirT<S> operator-(DirT<S> a, DirT<S> b) { return {a.v - b.v, a.t - b.t}; }
+template <class S> __device__ __forceinline__ DirT<S> operator*(DirT<S> a, DirT<S> b) { return {a.v * b.v, a.t * b.v + a.v * b.t}; }
+template <class S> __device__ __forceinline__ DirT<S> operator+(DirT<S> a, S b) { return {a.v + b, a.t}; }
+template <class S> __device__ __forceinline__ DirT<S> operator-(DirT<S> a, S b) { return {a.v - b, a.t}; }
+template <class S> __device__ __forceinline__ DirT<S> operator*(DirT<S> a, S b) { return {a.v * b, a.t * b}; }
+template <class S> __device__ __forceinline__ DirT<S> operator*(S b, DirT<S> a) { return {a.v * b, a.t * b}; }
+template <class S> __device__ __forceinline__ DirT<S> recip(DirT<S> a) { S r = S(1) / a.v; return {r, -a.t * r * r}; }
 __device__ __forceinline__ double recip(double a) { return 1.0 / a; }
-__device__ __forceinline__ Dir dsqrt(Dir a) { double s = sqrt(a.v); return {s, 0.5 * a.t / s}; }
+__device__ __forceinline__ float recip(float a) { return 1.0f / a; }
+template <class S> __device__ __forceinline__ DirT<S> dsqrt(DirT<S> a) { S s = sqrt(a.v); return {s, S(0.5) * a.t / s}; }
 __device__ __forceinline__ double dsqrt(double a) { return sqrt(a); }
-__device__ __forceinline__ Dir zero_like(Dir) { return {0.0, 0.0}; }
+__device__ __forceinline__ float dsqrt(float a) { return sqrtf(a); }
+template <class S> __device__ __forceinline__ DirT<S> zero_like(DirT<S>) { return {S(0), S(0)}; }
 __device__ __forceinline__ double zero_like(double) { return 0.0; }
+__device__ __forceinline__ float zero_like(float) { return 0.0f; }
 
-// Effective viscosity mu~(T~)/Re with T~ = gamma (gamma - 1) M^2 e
-// (eq. sutherland in the nondimensional form of eq. tgv-sutherland).
-template <class T>
-__device__ __forceinline__ T viscosity(T e, const Phys& ph) {
-    if (ph.visc_law == 0) return zero_like(e) + 1.0 / ph.re;
-    T Tt = e * (ph.gamma * (ph.gamma - 1.0) * ph.mach * ph.mach);
-    return (ph.c1 / ph.re) * Tt * dsqrt(Tt) * recip(Tt + ph.s);
+using Dir = DirT<double>;
+
+// Physical constants in the evaluation type.
+template <class S>
+struct PhysT {
+    S gm1;          // gamma - 1
+    S re_inv;       // 1 / Re
+    S kap;          // gamma / Pr (heat flux (gamma mu / Pr) d e)
+    S c1_re;        // C1 / Re (Sutherland)
+    S suth_s;       // S~
+    S tmul;         // gamma (gamma - 1) M^2: T~ = tmul e
+    S half, two_thirds;
+    int visc_law;
+};
+
+template <class S>
+inline PhysT<S> phys_t(const Phys& p) {
+    PhysT<S> q;
+    q.gm1 = (S)(p.gamma - 1.0);
+    q.re_inv = (S)(1.0 / p.re);
+    q.kap = (S)(p.gamma / p.pr);
+    q.c1_re = (S)(p.c1 / p.re);
+    q.suth_s = (S)p.s;
+    q.tmul = (S)(p.gamma * (p.gamma - 1.0) * p.mach * p.mach);
+    q.half = (S)0.5;
+    q.two_thirds = (S)(2.0 / 3.0);
+    q.visc_law = p.visc_law;
+    return q;
+}
+
+// Effective viscosity mu~(T~)/Re (eq. sutherland in the nondimensional form of
+// eq. tgv-sutherland), T~ = gamma (gamma - 1) M^2 e.
+template <class T, class S>
+__device__ __forceinline__ T viscosity(T e, const PhysT<S>& ph) {
+    if (ph.visc_law == 0) return zero_like(e) + ph.re_inv;
+    T Tt = e * ph.tmul;
+    return ph.c1_re * Tt * dsqrt(Tt) * recip(Tt + ph.suth_s);
 }
 
 // Convective flux f^c_j (eq. convective-flux), component a in direction k.
-template <int D, class T>
-__device__ __forceinline__ void conv_flux(const T* u, const Phys& ph, T (*F)[D]) {
+template <int D, class T, class S>
+__device__ __forceinline__ void conv_flux(const T* u, const PhysT<S>& ph, T (*F)[D]) {
     constexpr int M = D + 2;
     T irho = recip(u[0]);
     T v[D];
     T kin = zero_like(u[0]);
     for (int i = 0; i < D; ++i) { v[i] = u[1 + i] * irho; kin = kin + v[i] * u[1 + i]; }
-    T p = (u[M - 1] - kin * 0.5) * (ph.gamma - 1.0);
+    T p = (u[M - 1] - kin * ph.half) * ph.gm1;
     for (int k = 0; k < D; ++k) {
         F[0][k] = u[1 + k];
         for (int i = 0; i < D; ++i) {
@@ -54,16 +89,15 @@ __device__ __forceinline__ void conv_flux(const T* u, const Phys& ph, T (*F)[D])
 
 // Viscous plus artificial-viscosity flux f^v_j + nu q_j (eqs. viscous-flux,
 // stress-heat, thermal-conductivity, av-total); linear in q.
-template <int D, class T>
-__device__ __forceinline__ void visc_flux(const T* u, const double (*q)[D], double nu, const Phys& ph,
-                                          T (*F)[D]) {
+template <int D, class T, class S>
+__device__ __forceinline__ void visc_flux(const T* u, const S (*q)[D], S nu, const PhysT<S>& ph, T (*F)[D]) {
     constexpr int M = D + 2;
     T irho = recip(u[0]);
     T v[D];
     T kin = zero_like(u[0]);
     for (int i = 0; i < D; ++i) { v[i] = u[1 + i] * irho; kin = kin + v[i] * v[i]; }
     T E = u[M - 1] * irho;
-    T e = E - kin * 0.5;
+    T e = E - kin * ph.half;
     T mu = viscosity(e, ph);
     T dv[D][D];
     T dE[D];
@@ -73,15 +107,14 @@ __device__ __forceinline__ void visc_flux(const T* u, const double (*q)[D], doub
     }
     T div = dv[0][0];
     for (int i = 1; i < D; ++i) div = div + dv[i][i];
-    const double kap = ph.gamma / ph.pr;
     for (int j = 0; j < D; ++j) {
         T de = dE[j];
         for (int i = 0; i < D; ++i) de = de - v[i] * dv[i][j];
-        T fe = de * mu * kap;
+        T fe = de * mu * ph.kap;
         F[0][j] = zero_like(u[0]) + nu * q[0][j];
         for (int i = 0; i < D; ++i) {
             T tij = (dv[i][j] + dv[j][i]) * mu;
-            if (i == j) tij = tij - div * mu * (2.0 / 3.0);
+            if (i == j) tij = tij - div * mu * ph.two_thirds;
             F[1 + i][j] = tij + nu * q[1 + i][j];
             fe = fe + v[i] * tij;
         }

@@ -4,6 +4,8 @@
 // live on the device; only the Hessenberg column of each iteration is read
 // back for the Givens rotations.
 #include <cmath>
+#include <cstring>
+#include <initializer_list>
 #include <vector>
 
 #include "solve.cuh"
@@ -70,15 +72,114 @@ void dev_dot(hdg_ctx* h, const double* x, const double* y, int64_t n, double* ou
 
 int precond_apply(hdg_ctx* h, const double* x, double* y) {
     int rc;
-    DISPATCH_S(run_bj_apply, h, x, y);
+    if (h->pc_kind == HDG_PC_SCHWARZ) {
+        DISPATCH_S(run_asm_apply, h, x, y);
+    } else {
+        DISPATCH_S(run_bj_apply, h, x, y);
+    }
     return rc;
 }
+
+bool precond_ready(const hdg_ctx* h) { return h->pc_kind == HDG_PC_SCHWARZ ? h->asm_ready : h->bj_ready; }
+
+int schwarz_setup(hdg_ctx* h) {
+    const int prec = h->sys_prec == HDG_PREC_MIXED ? HDG_PREC_MIXED : HDG_PREC_FP64;
+    const int lda = (h->NT + 3) & ~3;
+    const size_t need = (prec == HDG_PREC_MIXED ? sizeof(float) : sizeof(double)) * (size_t)h->E * h->NT * lda;
+    int rc;
+    if (h->asm_bytes < need) {
+        if ((rc = alloc(h, &h->d_asmlu, need))) return rc;
+        h->asm_bytes = need;
+    }
+    if (!h->d_asmpiv) {
+        if ((rc = alloc(h, (void**)&h->d_asmpiv, sizeof(int32_t) * h->E * h->NT))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_asmz, sizeof(double) * h->E * h->NT))) return rc;
+    }
+    if ((rc = ensure_residual_storage(h))) return rc;       // face-to-element maps
+    DISPATCH_S(run_asm_setup, h);
+    if (rc) return rc;
+    h->asm_prec = prec;
+    h->asm_ready = true;
+    return HDG_OK;
+}
+
+int precond_setup(hdg_ctx* h);
 
 int matvec(hdg_ctx* h, const double* x, double* y) {
     int rc;
     DISPATCH_S(run_matvec, h, x, y);
     return rc;
 }
+
+// workspace of the synchronisation-free solver: Krylov basis, Newton work, device scalars
+int ensure_fixed_workspace(hdg_ctx* h, int m) {
+    const int64_t N = h->F * h->BS;
+    int rc;
+    if (h->gm_cap < m) {
+        if ((rc = alloc(h, (void**)&h->d_V, sizeof(double) * (size_t)(m + 1) * N))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_w, sizeof(double) * N))) return rc;
+        if (!h->d_red && (rc = alloc(h, (void**)&h->d_red, sizeof(double) * kRedBlocks))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_h, sizeof(double) * (m + 2)))) return rc;
+        h->gm_cap = m;
+    }
+    if (h->fx_cap < m) {
+        const size_t n = 1 + (size_t)m * m + 3 * (size_t)m + 1 + (m + 1);
+        if ((rc = alloc(h, (void**)&h->d_fx, sizeof(double) * n))) return rc;
+        h->fx_cap = m;
+    }
+    if (!h->d_nw) {
+        size_t n = (size_t)h->E * (h->NU + h->NQV) + 2 * (size_t)h->F * h->BS;
+        if ((rc = alloc(h, (void**)&h->d_nw, sizeof(double) * n))) return rc;
+    }
+    if (!h->d_hist) {
+        if ((rc = alloc(h, (void**)&h->d_hist, sizeof(double) * 4096))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_hcount, sizeof(int)))) return rc;
+    }
+    return ensure_residual_storage(h);
+}
+
+// GMRES(m) from x = 0, exactly m iterations, no host synchronisation: the Givens
+// rotations and the triangular solve run on the device.
+int gmres_fixed_async(hdg_ctx* h, const double* b, double* x, int m) {
+    const int64_t N = h->F * h->BS;
+    double* V = h->d_V;
+    double* w = h->d_w;
+    double* beta = h->d_fx;
+    double* R = beta + 1;
+    double* cs = R + (size_t)m * m;
+    double* sn = cs + m;
+    double* y = sn + m;
+    double* gv = y + m;
+    double* hc = h->d_h;
+    int rc;
+    if ((rc = precond_apply(h, b, V))) return rc;
+    dev_dot(h, V, V, N, beta, true);
+    k_set_first<<<1, 64, 0, h->stream>>>(beta, gv, m);
+    k_scale_safe<<<grid_for(N), 256, 0, h->stream>>>(V, beta, V, N);
+    for (int j = 0; j < m; ++j) {
+        double* vj = V + (size_t)j * N;
+        double* vn = V + (size_t)(j + 1) * N;
+        if ((rc = matvec(h, vj, w))) return rc;
+        if ((rc = precond_apply(h, w, vn))) return rc;
+        for (int i = 0; i <= j; ++i) {
+            dev_dot(h, vn, V + (size_t)i * N, N, hc + i, false);
+            k_axpy_dev<<<grid_for(N), 256, 0, h->stream>>>(hc + i, -1.0, V + (size_t)i * N, vn, N);
+        }
+        dev_dot(h, vn, vn, N, hc + j + 1, true);
+        k_scale_safe<<<grid_for(N), 256, 0, h->stream>>>(vn, hc + j + 1, vn, N);
+        k_givens_step<<<1, 1, 0, h->stream>>>(hc, j, m, R, cs, sn, gv);
+    }
+    k_backsolve<<<1, 1, 0, h->stream>>>(R, gv, m, m, y);
+    CKS(cudaMemsetAsync(x, 0, sizeof(double) * N, h->stream));
+    k_combine<<<grid_for(N), 256, 0, h->stream>>>(V, N, y, m, x, N);
+    CKS(cudaGetLastError());
+    return HDG_OK;
+}
+
+// one Newton iteration of the stage equations, asynchronous on the handle's stream;
+// the residual norm before the update is appended to the device history
+int newton_iteration_async(hdg_ctx* h, double* U, double* Q, double* UH, const double* Ustar, const double* nu,
+                           double dt, double a_ii, int m);
 
 }  // namespace
 
@@ -104,6 +205,15 @@ int hdg_residual(hdg_handle h, const double* U, const double* Q, const double* U
         norms[0] = tmp[0]; norms[1] = tmp[1]; norms[2] = tmp[2];
     }
     return HDG_OK;
+}
+
+int hdg_lift_gradient(hdg_handle h, const double* U, const double* UH, double* Q) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
+    if (!U || !UH || !Q) return fail(h, HDG_EINVAL, "U, UH and Q are required");
+    int rc;
+    DISPATCH_S(run_lift, h, U, UH, Q);
+    return rc;
 }
 
 int hdg_update_state(hdg_handle h, double* U, double* Q, double* UH, const double* dU, const double* dQ,
@@ -133,11 +243,36 @@ int hdg_blockjacobi_setup(hdg_handle h) {
     return HDG_OK;
 }
 
+int hdg_set_preconditioner(hdg_handle h, int kind) {
+    if (!h) return HDG_EINVAL;
+    if (kind != HDG_PC_BLOCKJACOBI && kind != HDG_PC_SCHWARZ)
+        return fail(h, HDG_EINVAL, "preconditioner must be HDG_PC_BLOCKJACOBI or HDG_PC_SCHWARZ");
+    h->pc_kind = kind;
+    return HDG_OK;
+}
+
+int hdg_schwarz_setup(hdg_handle h) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
+    return schwarz_setup(h);
+}
+
+int hdg_schwarz_apply(hdg_handle h, const double* x, double* y) {
+    if (!h) return HDG_EINVAL;
+    if (!h->asm_ready) return fail(h, HDG_EINVAL, "additive Schwarz factors not set up");
+    if (!x || !y || x == y) return fail(h, HDG_EINVAL, "x and y must be distinct device arrays");
+    int rc;
+    DISPATCH_S(run_asm_apply, h, x, y);
+    return rc;
+}
+
 int hdg_blockjacobi_apply(hdg_handle h, const double* x, double* y) {
     if (!h) return HDG_EINVAL;
     if (!h->bj_ready) return fail(h, HDG_EINVAL, "block-Jacobi factors not set up");
     if (!x || !y || x == y) return fail(h, HDG_EINVAL, "x and y must be distinct device arrays");
-    return precond_apply(h, x, y);
+    int rc;
+    DISPATCH_S(run_bj_apply, h, x, y);
+    return rc;
 }
 
 int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_iter, double rtol, int precond,
@@ -147,7 +282,8 @@ int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_ite
     if (!b || !x || b == x) return fail(h, HDG_EINVAL, "b and x must be distinct device arrays");
     if (restart < 1 || restart > 500 || max_iter < 1 || !(rtol > 0.0))
         return fail(h, HDG_EINVAL, "restart in 1..500, max_iter >= 1, rtol > 0 required");
-    if (precond && !h->bj_ready) return fail(h, HDG_EINVAL, "precond = 1 needs hdg_blockjacobi_setup");
+    if (precond && !precond_ready(h))
+        return fail(h, HDG_EINVAL, "precond = 1 needs the selected preconditioner set up (hdg_blockjacobi_setup / hdg_schwarz_setup)");
     const int64_t N = h->F * h->BS;
     int rc;
     if (h->gm_cap < restart) {
@@ -264,7 +400,7 @@ int hdg_newton(hdg_handle h, double* U, double* Q, double* UH, const double* Ust
         if (nrm[0] <= tol || k >= max_newton) break;
         if ((rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr))) return rc;
         if ((rc = hdg_trace_rhs(h, g))) return rc;
-        if ((rc = hdg_blockjacobi_setup(h))) return rc;
+        if ((rc = precond_setup(h))) return rc;
         CKS(cudaMemsetAsync(dUH, 0, sizeof(double) * h->F * h->BS, h->stream));
         int it = 0;
         double rel = 0.0;
@@ -277,6 +413,182 @@ int hdg_newton(hdg_handle h, double* U, double* Q, double* UH, const double* Ust
     if (newton_iters) *newton_iters = k;
     if (gmres_iters) *gmres_iters = total;
     if (nrm[0] > tol) return fail(h, HDG_ENOCONV, "Newton stopped at ||F|| = " + std::to_string(nrm[0]));
+    return HDG_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+int precond_setup(hdg_ctx* h) { return h->pc_kind == HDG_PC_SCHWARZ ? schwarz_setup(h) : hdg_blockjacobi_setup(h); }
+
+int newton_iteration_async(hdg_ctx* h, double* U, double* Q, double* UH, const double* Ustar, const double* nu,
+                           double dt, double a_ii, int m) {
+    double* dU = h->d_nw;
+    double* dQ = dU + (size_t)h->E * h->NU;
+    double* dUH = dQ + (size_t)h->E * h->NQV;
+    double* g = dUH + (size_t)h->F * h->BS;
+    int rc;
+    if ((rc = hdg_residual(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr, nullptr, nullptr, nullptr))) return rc;
+    k_hist_push<<<1, 32, 0, h->stream>>>(h->d_norms, h->d_hist, h->d_hcount, 4096);
+    if ((rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr))) return rc;
+    if ((rc = hdg_trace_rhs(h, g))) return rc;
+    if ((rc = precond_setup(h))) return rc;
+    if ((rc = gmres_fixed_async(h, g, dUH, m))) return rc;
+    if ((rc = hdg_recover_interior(h, dUH, dQ, dU))) return rc;
+    return hdg_update_state(h, U, Q, UH, dU, dQ, dUH, 1.0);
+}
+
+// run `body` either directly or as a CUDA graph captured once and replayed
+template <class Body>
+int run_maybe_graph(hdg_ctx* h, bool use_graph, uint64_t key, Body body) {
+    if (!use_graph) return body();
+    if (!h->gstream) CKS(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+    if (!h->gexec || h->gkey != key) {
+        if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+        cudaStream_t user = h->stream;
+        const bool prof = h->prof;
+        h->prof = false;
+        h->stream = h->gstream;
+        cudaGraph_t graph = nullptr;
+        CKS(cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeThreadLocal));
+        int rc = body();
+        cudaError_t ce = cudaStreamEndCapture(h->gstream, &graph);
+        h->stream = user;
+        h->prof = prof;
+        if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+        if (ce != cudaSuccess) return fail(h, HDG_ECUDA, std::string("stream capture: ") + cudaGetErrorString(ce));
+        ce = cudaGraphInstantiate(&h->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) { h->gexec = nullptr; return fail(h, HDG_ECUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce)); }
+        h->gkey = key;
+    }
+    CKS(cudaGraphLaunch(h->gexec, h->stream));
+    return HDG_OK;
+}
+
+uint64_t mix_key(std::initializer_list<uint64_t> v) {
+    uint64_t k = 1469598103934665603ull;
+    for (uint64_t x : v) { k ^= x; k *= 1099511628211ull; }
+    return k;
+}
+
+uint64_t dbits(double d) { uint64_t u; std::memcpy(&u, &d, 8); return u; }
+
+// device stage states of a DIRK step
+int ensure_dirk_storage(hdg_ctx* h, int s) {
+    if (h->dirk_cap >= s) return HDG_OK;
+    int rc;
+    const size_t n = (size_t)h->E * h->NU;
+    if ((rc = alloc(h, (void**)&h->d_dirk, sizeof(double) * n * (s + 2)))) return rc;
+    h->dirk_cap = s;
+    return HDG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hdg_newton_fixed(hdg_handle h, double* U, double* Q, double* UH, const double* Ustar, const double* nu,
+                     double dt, double a_ii, int n_newton, int m, int use_graph, double* hist) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
+    if (!U || !Q || !UH || !Ustar) return fail(h, HDG_EINVAL, "U, Q, UH and Ustar are required");
+    if (n_newton < 1 || n_newton > 1000 || m < 1 || m > 256) return fail(h, HDG_EINVAL, "1 <= n_newton <= 1000, 1 <= m <= 256");
+    if (!(dt > 0.0) || !(a_ii > 0.0)) return fail(h, HDG_EINVAL, "dt and a_ii must be positive");
+    int rc;
+    if ((rc = ensure_fixed_workspace(h, m))) return rc;
+    const uint64_t key = mix_key({1, (uint64_t)U, (uint64_t)Q, (uint64_t)UH, (uint64_t)Ustar, (uint64_t)nu, dbits(dt),
+                                  dbits(a_ii), (uint64_t)m, (uint64_t)h->precision, (uint64_t)h->schur_mode,
+                                  (uint64_t)h->d_V, (uint64_t)h->d_fx});
+    if (use_graph && (!h->gexec || h->gkey != key)) {
+        // one linearization outside the capture: every lazily allocated buffer exists before it
+        if ((rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr))) return rc;
+        if ((rc = precond_setup(h))) return rc;
+    }
+    CKS(cudaMemsetAsync(h->d_hcount, 0, sizeof(int), h->stream));
+    for (int k = 0; k < n_newton; ++k) {
+        rc = run_maybe_graph(h, use_graph != 0, key,
+                             [&]() { return newton_iteration_async(h, U, Q, UH, Ustar, nu, dt, a_ii, m); });
+        if (rc) return rc;
+    }
+    if ((rc = hdg_residual(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr, nullptr, nullptr, nullptr))) return rc;
+    k_hist_push<<<1, 32, 0, h->stream>>>(h->d_norms, h->d_hist, h->d_hcount, 4096);
+    if (hist) {
+        CKS(cudaMemcpyAsync(hist, h->d_hist, sizeof(double) * (n_newton + 1), cudaMemcpyDeviceToHost, h->stream));
+    }
+    CKS(cudaStreamSynchronize(h->stream));
+    return HDG_OK;
+}
+
+int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* nu, double dt, int s,
+                  const double* A, const double* b, int n_newton, int m, int use_graph, double* hist) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
+    if (!U || !Q || !UH || !A || !b) return fail(h, HDG_EINVAL, "NULL argument");
+    if (s < 1 || s > 8 || n_newton < 1 || n_newton > 100 || m < 1 || m > 256)
+        return fail(h, HDG_EINVAL, "1 <= s <= 8, 1 <= n_newton <= 100, 1 <= m <= 256");
+    if (!(dt > 0.0)) return fail(h, HDG_EINVAL, "dt must be positive");
+    // Butcher matrix: lower triangular with a positive diagonal; d = A^{-1}; e_j = sum_i b_i d_ij
+    double d[8][8] = {};
+    for (int i = 0; i < s; ++i) {
+        if (!(A[i * s + i] > 0.0)) return fail(h, HDG_EINVAL, "DIRK diagonal must be positive");
+        for (int j = i + 1; j < s; ++j)
+            if (A[i * s + j] != 0.0) return fail(h, HDG_EINVAL, "Butcher matrix must be lower triangular");
+    }
+    for (int j = 0; j < s; ++j) {            // forward substitution column by column
+        for (int i = 0; i < s; ++i) {
+            double r = (i == j) ? 1.0 : 0.0;
+            for (int k = 0; k < i; ++k) r -= A[i * s + k] * d[k][j];
+            d[i][j] = r / A[i * s + i];
+        }
+    }
+    double e[8] = {};
+    for (int j = 0; j < s; ++j)
+        for (int i = 0; i < s; ++i) e[j] += b[i] * d[i][j];
+    for (int j = 0; j < s - 1; ++j)
+        if (std::fabs(e[j]) > 1e-12) return fail(h, HDG_EUNSUPPORTED, "only stiffly accurate tableaus (b = last row of A)");
+    int rc;
+    if ((rc = ensure_fixed_workspace(h, m))) return rc;
+    if ((rc = ensure_dirk_storage(h, s))) return rc;
+    const int64_t n = h->E * h->NU;
+    double* Un = h->d_dirk;                  // U^n
+    double* Us = Un + n;                     // U* of the current stage
+    double* St = Us + n;                     // stage states U^{n,1..s}
+    uint64_t key = mix_key({2, (uint64_t)U, (uint64_t)Q, (uint64_t)UH, (uint64_t)nu, dbits(dt), (uint64_t)s,
+                            (uint64_t)n_newton, (uint64_t)m, (uint64_t)h->precision, (uint64_t)h->schur_mode,
+                            (uint64_t)h->d_V, (uint64_t)h->d_fx, (uint64_t)h->d_dirk});
+    for (int i = 0; i < s * s; ++i) key = mix_key({key, dbits(A[i])});
+    if (use_graph && (!h->gexec || h->gkey != key)) {
+        // one linearization outside the capture: every lazily allocated buffer exists before it
+        CKS(cudaMemcpyAsync(Us, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+        if ((rc = hdg_linearize_condense(h, U, Q, UH, Us, nu, dt, A[0], nullptr))) return rc;
+        if ((rc = precond_setup(h))) return rc;
+    }
+    CKS(cudaMemsetAsync(h->d_hcount, 0, sizeof(int), h->stream));
+    auto body = [&]() -> int {
+        int r;
+        if (cudaMemcpyAsync(Un, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess)
+            return fail(h, HDG_ECUDA, "copy of U^n failed");
+        for (int i = 0; i < s; ++i) {
+            const double aii = A[i * s + i];
+            // U* = U^n - a_ii sum_{j<i} d_ij (U^{n,j} - U^n)   (eq. dirk-stage, d_ii = 1/a_ii)
+            cudaMemcpyAsync(Us, Un, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream);
+            for (int j = 0; j < i; ++j)
+                k_lincomb3<<<grid_for(n), 256, 0, h->stream>>>(-aii * d[i][j], St + (size_t)j * n, aii * d[i][j], Un,
+                                                               1.0, Us, n);
+            for (int k = 0; k < n_newton; ++k)
+                if ((r = newton_iteration_async(h, U, Q, UH, Us, nu, dt, aii, m))) return r;
+            if ((r = hdg_residual(h, U, Q, UH, Us, nu, dt, aii, nullptr, nullptr, nullptr, nullptr))) return r;
+            k_hist_push<<<1, 32, 0, h->stream>>>(h->d_norms, h->d_hist, h->d_hcount, 4096);
+            cudaMemcpyAsync(St + (size_t)i * n, U, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream);
+        }
+        // stiffly accurate: U^{n+1} = U^{n,s} (eq. dirk-update with e = (0, .., 0, 1)); Q, UH of the last stage
+        return cudaGetLastError() == cudaSuccess ? HDG_OK : fail(h, HDG_ECUDA, "launch failed in DIRK step");
+    };
+    if ((rc = run_maybe_graph(h, use_graph != 0, key, body))) return rc;
+    if (hist) CKS(cudaMemcpyAsync(hist, h->d_hist, sizeof(double) * s * (n_newton + 1), cudaMemcpyDeviceToHost, h->stream));
+    CKS(cudaStreamSynchronize(h->stream));
     return HDG_OK;
 }
 

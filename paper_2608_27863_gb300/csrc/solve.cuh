@@ -6,6 +6,7 @@
 #pragma once
 
 #include "mixed.cuh"
+#include "schwarz.cuh"
 
 namespace hdg {
 
@@ -15,18 +16,75 @@ namespace hdg {
 struct ResArgs {
     const double* U; const double* Q; const double* UH; const double* Ustar; const double* nu;
     double dt, a_ii;
-    Phys ph;
+    PhysT<double> ph;
+    double tau;
     DeviceTables tab;
     const double* geo;
     const int32_t* e2f; const int32_t* perm;
     double* Rq; double* Ru;      // optional outputs [E][d][m][Np], [E][m][Np]
     double* rk;                  // [E][nf][m][Nfp] element contributions to R_uhat
     double* part;                // [E] sum of squares of R_q and R_u of the element
+    const int32_t* ftag;         // [E][nf] boundary tags or NULL
+    const double* ub;            // [m] tag-1 boundary state
 };
+
+// Lifted gradient at node i of component a (eq. hdg-grad with R_q = 0):
+// Q_lift = M^{-1}(-C U + E Uhat), from the element's staged U and Uhat.
+template <class C>
+__device__ __forceinline__ void lift_at_node(const DeviceTables& T, const double* sU, const double* sUH,
+                                             const double* Jinv, const double* NW, double detJ, int a, int i,
+                                             double (&ql)[C::D]) {
+    constexpr int D = C::D, M = C::M, NP = C::NP, NF = C::NF, NFP = C::NFP;
+    double t[D], ef[NF];
+    for (int r = 0; r < D; ++r) {
+        double s = 0.0;
+        const double* mc = T.minv_c + ((size_t)r * NP + i) * NP;
+        for (int j = 0; j < NP; ++j) s += mc[j] * sU[a * NP + j];
+        t[r] = s;
+    }
+    for (int f = 0; f < NF; ++f) {
+        double s = 0.0;
+        const double* me = T.minv_e + ((size_t)f * NP + i) * NFP;
+        for (int l = 0; l < NFP; ++l) s += me[l] * sUH[(f * M + a) * NFP + l];
+        ef[f] = s;
+    }
+    for (int l = 0; l < D; ++l) {
+        double v = 0.0;
+        for (int r = 0; r < D; ++r) v -= Jinv[r * D + l] * t[r];
+        for (int f = 0; f < NF; ++f) v += NW[f * D + l] / detJ * ef[f];
+        ql[l] = v;
+    }
+}
+
+// Q = Q_lift(U, Uhat) for every element: the gradient for which R_q = 0
+template <class C, int NTH>
+__global__ void __launch_bounds__(NTH) k_lift(const double* __restrict__ U, const double* __restrict__ UH,
+                                              double* __restrict__ Q, DeviceTables T, const double* __restrict__ geog,
+                                              const int32_t* __restrict__ e2f, const int32_t* __restrict__ perm) {
+    constexpr int D = C::D, M = C::M, NP = C::NP, NF = C::NF, NFP = C::NFP, NU = C::NU, NT = C::NT;
+    constexpr int GEO = Geo<D>::N;
+    __shared__ double sU[NU], sUH[NT], geo[GEO];
+    const int tid = threadIdx.x;
+    const int64_t e = blockIdx.x;
+    for (int i = tid; i < NU; i += NTH) sU[i] = U[e * NU + i];
+    for (int i = tid; i < NT; i += NTH) {
+        int f = i / (M * NFP), rem = i - f * M * NFP, a = rem / NFP, l = rem - a * NFP;
+        int64_t F = e2f[e * NF + f];
+        sUH[i] = UH[(F * M + a) * NFP + perm[(e * NF + f) * NFP + l]];
+    }
+    for (int i = tid; i < GEO; i += NTH) geo[i] = geog[e * GEO + i];
+    __syncthreads();
+    for (int idx = tid; idx < M * NP; idx += NTH) {
+        int a = idx / NP, i = idx - a * NP;
+        double ql[D];
+        lift_at_node<C>(T, sU, sUH, geo + 1, geo + 1 + D * D, geo[0], a, i, ql);
+        for (int l = 0; l < D; ++l) Q[e * C::NQV + (l * M + a) * NP + i] = ql[l];
+    }
+}
 
 template <class C>
 constexpr int res_smem_doubles() {
-    return C::NU + 2 * C::NQV + C::NP + 2 * C::NT + C::D * C::M * C::NQ + C::NF * C::M * C::NFQ + 32;
+    return C::NU + 2 * C::NQV + C::NP + 2 * C::NT + C::D * C::M * C::NQ + 2 * C::NF * C::M * C::NFQ + 32;
 }
 
 template <class C, int NTH>
@@ -45,7 +103,8 @@ __global__ void __launch_bounds__(NTH) k_residual(ResArgs A) {
     double* sF = sUH + NT;               // [d][m][Nq]
     double* sFH = sF + D * M * NQ;       // [nf][m][Nfq]
     double* sRh = sFH + NF * M * NFQ;    // [nf][m][Nfp]
-    double* red = sRh + NT;              // [32]
+    double* sFB = sRh + NT;              // [nf][m][Nfq] bhat on tag-1 faces
+    double* red = sFB + NF * M * NFQ;    // [32]
     __shared__ double geo[GEO];
     const DeviceTables& T = A.tab;
     for (int i = tid; i < NU; i += NTH) sU[i] = A.U[e * NU + i];
@@ -64,27 +123,11 @@ __global__ void __launch_bounds__(NTH) k_residual(ResArgs A) {
     // Q_lift = M^{-1}(-C U + E Uhat), so R_q = M (Q - Q_lift) (eq. hdg-grad)
     for (int idx = tid; idx < M * NP; idx += NTH) {
         int a = idx / NP, i = idx - a * NP;
-        double t[D], ef[NF];
-        for (int r = 0; r < D; ++r) {
-            double s = 0.0;
-            const double* mc = T.minv_c + ((size_t)r * NP + i) * NP;
-            for (int j = 0; j < NP; ++j) s += mc[j] * sU[a * NP + j];
-            t[r] = s;
-        }
-        for (int f = 0; f < NF; ++f) {
-            double s = 0.0;
-            const double* me = T.minv_e + ((size_t)f * NP + i) * NFP;
-            for (int l = 0; l < NFP; ++l) s += me[l] * sUH[(f * M + a) * NFP + l];
-            ef[f] = s;
-        }
-        for (int l = 0; l < D; ++l) {
-            double ql = 0.0;
-            for (int r = 0; r < D; ++r) ql -= Jinv[r * D + l] * t[r];
-            for (int f = 0; f < NF; ++f) ql += NW[f * D + l] / detJ * ef[f];
-            sQL[(l * M + a) * NP + i] = sQ[(l * M + a) * NP + i] - ql;   // Q - Q_lift
-        }
+        double ql[D];
+        lift_at_node<C>(T, sU, sUH, Jinv, NW, detJ, a, i, ql);
+        for (int l = 0; l < D; ++l) sQL[(l * M + a) * NP + i] = sQ[(l * M + a) * NP + i] - ql[l];   // Q - Q_lift
     }
-    const Phys ph = A.ph;
+    const PhysT<double>& ph = A.ph;
     for (int g = tid; g < NQ; g += NTH) {
         double u[M], q[M][D], nuv = 0.0;
         for (int a = 0; a < M; ++a) { u[a] = 0.0; for (int l = 0; l < D; ++l) q[a][l] = 0.0; }
@@ -98,8 +141,8 @@ __global__ void __launch_bounds__(NTH) k_residual(ResArgs A) {
         }
         const double wJ = -A.dt * T.wq[g] * detJ;
         double Fc[M][D], Fv[M][D];
-        conv_flux<D, double>(u, ph, Fc);
-        visc_flux<D, double>(u, q, nuv, ph, Fv);
+        conv_flux<D, double, double>(u, ph, Fc);
+        visc_flux<D, double, double>(u, q, nuv, ph, Fv);
         for (int r = 0; r < D; ++r)
             for (int a = 0; a < M; ++a) {
                 double s = 0.0;
@@ -126,21 +169,25 @@ __global__ void __launch_bounds__(NTH) k_residual(ResArgs A) {
         for (int k = 0; k < D; ++k) nrm += nw[k] * nw[k];
         nrm = sqrt(nrm);
         double Fc[M][D], Fv[M][D];
-        conv_flux<D, double>(uh, ph, Fc);
-        visc_flux<D, double>(uh, q, nuv, ph, Fv);
+        conv_flux<D, double, double>(uh, ph, Fc);
+        visc_flux<D, double, double>(uh, q, nuv, ph, Fv);
         for (int a = 0; a < M; ++a) {
             double fn = 0.0;
             for (int k = 0; k < D; ++k) fn += (Fc[a][k] - Fv[a][k]) * nw[k];
-            sFH[(f * M + a) * NFQ + s] = T.wf[s] * (fn + nrm * ph.tau * (u[a] - uh[a]));
+            sFH[(f * M + a) * NFQ + s] = T.wf[s] * (fn + nrm * A.tau * (u[a] - uh[a]));
+            sFB[(f * M + a) * NFQ + s] = (A.ftag && A.ftag[e * NF + f] == 1) ? T.wf[s] * nrm * (uh[a] - A.ub[a]) : 0.0;
         }
     }
     __syncthreads();
     for (int idx = tid; idx < NT; idx += NTH) {
         int f = idx / (M * NFP), rem = idx - f * M * NFP, a = rem / NFP, l = rem - a * NFP;
-        double s = 0.0;
-        for (int q = 0; q < NFQ; ++q) s += T.mu[q * NFP + l] * sFH[(f * M + a) * NFQ + q];
+        double s = 0.0, sb = 0.0;
+        for (int q = 0; q < NFQ; ++q) {
+            s += T.mu[q * NFP + l] * sFH[(f * M + a) * NFQ + q];
+            sb += T.mu[q * NFP + l] * sFB[(f * M + a) * NFQ + q];
+        }
         sRh[idx] = s;
-        A.rk[e * NT + idx] = s;
+        A.rk[e * NT + idx] = (A.ftag && A.ftag[e * NF + f] != 0) ? sb : s;
     }
     __syncthreads();
     double ss = 0.0;
@@ -304,6 +351,12 @@ __global__ void k_scale_dev(const double* x, const double* div, double* y, int64
 __global__ void k_axpby(double a, const double* x, double b, double* y, int64_t n);
 __global__ void k_combine(const double* V, int64_t ldv, const double* coef, int k, double* x, int64_t n);
 __global__ void k_sum_parts(const double* p1, int64_t n1, const double* p2, int64_t n2, double* out);
+__global__ void k_scale_safe(const double* x, const double* div, double* y, int64_t n);
+__global__ void k_givens_step(const double* hcol, int j, int m, double* R, double* cs, double* sn, double* gv);
+__global__ void k_backsolve(const double* R, const double* gv, int k, int m, double* y);
+__global__ void k_set_first(const double* beta, double* gv, int m);
+__global__ void k_hist_push(const double* norms, double* hist, int* counter, int cap);
+__global__ void k_lincomb3(double a, const double* x, double b, const double* y, double c, double* z, int64_t n);
 
 // ----------------------------------------------------------------------------
 // launchers
@@ -316,11 +369,19 @@ int run_residual(hdg_ctx* h, const LinArgs& la, double* Rq, double* Ru, double* 
     HDG_CK(cudaFuncSetAttribute(k_residual<C, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ResArgs ra;
     ra.U = la.U; ra.Q = la.Q; ra.UH = la.UH; ra.Ustar = la.Ustar; ra.nu = la.nu; ra.dt = la.dt; ra.a_ii = la.a_ii;
-    ra.ph = h->phys; ra.tab = h->tab; ra.geo = h->d_geo; ra.e2f = h->d_e2f; ra.perm = h->d_perm;
-    ra.Rq = Rq; ra.Ru = Ru; ra.rk = h->d_rk; ra.part = h->d_part;
+    ra.ph = phys_t<double>(h->phys); ra.tau = h->phys.tau; ra.tab = h->tab; ra.geo = h->d_geo; ra.e2f = h->d_e2f; ra.perm = h->d_perm;
+    ra.Rq = Rq; ra.Ru = Ru; ra.rk = h->d_rk; ra.part = h->d_part; ra.ftag = h->d_ftag; ra.ub = h->d_ub;
     k_residual<C, NTH><<<(unsigned)h->E, NTH, smem, h->stream>>>(ra);
     k_trace_residual<C><<<(unsigned)((h->F + 7) / 8), 256, 0, h->stream>>>(h->d_rk, h->d_f2e, h->d_f2lf, h->d_iperm,
                                                                         Ruh, h->d_part + h->E, h->F);
+    HDG_CK(cudaGetLastError());
+    return HDG_OK;
+}
+
+template <int D, int P>
+int run_lift(hdg_ctx* h, const double* U, const double* UH, double* Q) {
+    using C = Cfg<D, P>;
+    k_lift<C, 128><<<(unsigned)h->E, 128, 0, h->stream>>>(U, UH, Q, h->tab, h->d_geo, h->d_e2f, h->d_perm);
     HDG_CK(cudaGetLastError());
     return HDG_OK;
 }
@@ -352,6 +413,9 @@ int run_bj_apply(hdg_ctx* h, const double* x, double* y) {
 
 #define HDG_INSTANTIATE_SOLVE(D, P)                                                       \
     template int run_residual<D, P>(hdg_ctx*, const LinArgs&, double*, double*, double*); \
+    template int run_lift<D, P>(hdg_ctx*, const double*, const double*, double*);         \
+    template int run_asm_setup<D, P>(hdg_ctx*);                                           \
+    template int run_asm_apply<D, P>(hdg_ctx*, const double*, double*);                   \
     template int run_bj_setup<D, P>(hdg_ctx*);                                            \
     template int run_bj_apply<D, P>(hdg_ctx*, const double*, double*);
 

@@ -73,4 +73,70 @@ __global__ void k_sum_parts(const double* p1, int64_t n1, const double* p2, int6
     }
 }
 
+// y = x / div, or 0 when div is zero (lucky breakdown of the Arnoldi process)
+__global__ void k_scale_safe(const double* x, const double* div, double* y, int64_t n) {
+    const double d = *div;
+    const double s = d != 0.0 ? 1.0 / d : 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = x[i] * s;
+}
+
+// Device-side Givens QR of the Hessenberg matrix, one column per call (single thread):
+// hcol[0..j+1] is column j of H; R [m][m] upper triangle, cs/sn rotations, gv the rotated rhs.
+__global__ void k_givens_step(const double* hcol, int j, int m, double* R, double* cs, double* sn, double* gv) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double h[2];
+    double col[512];
+    for (int i = 0; i <= j + 1 && i < 512; ++i) col[i] = hcol[i];
+    for (int i = 0; i < j; ++i) {
+        double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    h[0] = col[j];
+    h[1] = col[j + 1];
+    const double den = hypot(h[0], h[1]);
+    cs[j] = den > 0.0 ? h[0] / den : 1.0;
+    sn[j] = den > 0.0 ? h[1] / den : 0.0;
+    col[j] = den;
+    for (int i = 0; i <= j; ++i) R[(size_t)i * m + j] = col[i];
+    gv[j + 1] = -sn[j] * gv[j];
+    gv[j] = cs[j] * gv[j];
+}
+
+// y = R^{-1} gv (k x k upper triangle, zero diagonals skipped)
+__global__ void k_backsolve(const double* R, const double* gv, int k, int m, double* y) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = gv[i];
+        for (int l = i + 1; l < k; ++l) s -= R[(size_t)i * m + l] * y[l];
+        const double d = R[(size_t)i * m + i];
+        y[i] = d != 0.0 ? s / d : 0.0;
+    }
+}
+
+__global__ void k_set_first(const double* beta, double* gv, int m) {
+    for (int i = threadIdx.x; i <= m; i += blockDim.x) gv[i] = (i == 0) ? *beta : 0.0;
+}
+
+// append the residual norm to a device-side history
+__global__ void k_hist_push(const double* norms, double* hist, int* counter, int cap) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        int k = *counter;
+        if (k < cap) hist[k] = norms[0];
+        *counter = k + 1;
+    }
+}
+
+// z = a x + b y + c z
+__global__ void k_lincomb3(double a, const double* x, double b, const double* y, double c, double* z, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        z[i] = a * x[i] + b * y[i] + c * z[i];
+}
+
+__global__ void k_to_f32(const double* x, float* y, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
+}
+
 }  // namespace hdg

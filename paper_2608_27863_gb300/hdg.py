@@ -35,7 +35,9 @@ EXPORTS = [
     "hdg_query_sizes", "hdg_get_connectivity", "hdg_linearize_condense", "hdg_trace_matvec",
     "hdg_trace_rhs", "hdg_recover_interior", "hdg_get_blocks", "hdg_status", "hdg_profile",
     "hdg_profile_read", "hdg_linearize_condense_static", "hdg_residual", "hdg_update_state",
-    "hdg_blockjacobi_setup", "hdg_blockjacobi_apply", "hdg_gmres", "hdg_newton",
+    "hdg_blockjacobi_setup", "hdg_blockjacobi_apply", "hdg_gmres", "hdg_newton", "hdg_set_bc_state",
+    "hdg_newton_fixed", "hdg_dirk_step", "hdg_lift_gradient", "hdg_set_preconditioner", "hdg_schwarz_setup",
+    "hdg_schwarz_apply",
 ]
 KERNEL_CLASSES = ["point", "blocks", "elim", "assemble", "matvec", "recover", "schur"]
 
@@ -82,6 +84,7 @@ def lib():
         "hdg_destroy": [vp],
         "hdg_set_params": [vp, ctypes.POINTER(hdg_params)],
         "hdg_set_stream": [vp, vp],
+        "hdg_set_bc_state": [vp, i32, vp],
         "hdg_query_sizes": [vp, ctypes.POINTER(hdg_sizes)],
         "hdg_get_connectivity": [vp] * 7,
         "hdg_linearize_condense": [vp, vp, vp, vp, vp, vp, dbl, dbl, vp],
@@ -99,6 +102,12 @@ def lib():
         "hdg_blockjacobi_apply": [vp, vp, vp],
         "hdg_gmres": [vp, vp, vp, i32, i32, dbl, i32, vp, vp],
         "hdg_newton": [vp, vp, vp, vp, vp, vp, dbl, dbl, dbl, i32, i32, i32, dbl, vp, vp, vp],
+        "hdg_lift_gradient": [vp, vp, vp, vp],
+        "hdg_set_preconditioner": [vp, i32],
+        "hdg_schwarz_setup": [vp],
+        "hdg_schwarz_apply": [vp, vp, vp],
+        "hdg_newton_fixed": [vp, vp, vp, vp, vp, vp, dbl, dbl, i32, i32, i32, vp],
+        "hdg_dirk_step": [vp, vp, vp, vp, vp, dbl, i32, vp, vp, i32, i32, i32, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -167,6 +176,11 @@ def hdg_last_error(h):
 def hdg_set_params(h, tau=5.0, visc_law=0, suth_c1=1.4042, suth_s=0.40417, precision=HDG_PREC_FP64):
     prm = hdg_params(tau, visc_law, suth_c1, suth_s, precision)
     _check(h, lib().hdg_set_params(h, ctypes.byref(prm)))
+
+
+def hdg_set_bc_state(h, tag, ub):
+    ub = np.ascontiguousarray(ub, dtype=np.float64)
+    _check(h, lib().hdg_set_bc_state(h, int(tag), ub.ctypes.data))
 
 
 def hdg_set_stream(h, stream_handle):
@@ -276,3 +290,55 @@ def hdg_newton(h, U, Q, UH, Ustar, nu, dt, a_ii, tol=1e-8, max_newton=10, restar
     if rc != HDG_OK and (raise_on_noconv or rc != HDG_ENOCONV):
         _check(h, rc)
     return nit.value, git.value, hist[:nit.value + 1].copy()
+
+
+def hdg_newton_fixed(h, U, Q, UH, Ustar, nu, dt, a_ii, n_newton=4, m=30, use_graph=True):
+    """n_newton synchronisation-free Newton iterations; returns the residual history."""
+    hist = np.zeros(n_newton + 1, np.float64)
+    _check(h, lib().hdg_newton_fixed(h, _ptr(U), _ptr(Q), _ptr(UH), _ptr(Ustar), _ptr(nu), float(dt), float(a_ii),
+                                     int(n_newton), int(m), 1 if use_graph else 0, hist.ctypes.data))
+    return hist
+
+
+# Alexander's three-stage, third-order, L-stable SDIRK (stiffly accurate)
+SDIRK3_GAMMA = 0.43586652150845899941601945
+def sdirk3_tableau():
+    g = SDIRK3_GAMMA
+    b1 = -(6 * g * g - 16 * g + 1) / 4
+    b2 = (6 * g * g - 20 * g + 5) / 4
+    A = np.array([[g, 0, 0], [(1 - g) / 2, g, 0], [b1, b2, g]], dtype=np.float64)
+    return A, A[-1].copy()
+
+
+def hdg_dirk_step(h, U, Q, UH, nu, dt, A=None, b=None, n_newton=4, m=30, use_graph=True):
+    """One DIRK step in place on (U, Q, UH); returns the residual history per stage."""
+    if A is None:
+        A, b = sdirk3_tableau()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    s = A.shape[0]
+    hist = np.zeros(s * (n_newton + 1), np.float64)
+    _check(h, lib().hdg_dirk_step(h, _ptr(U), _ptr(Q), _ptr(UH), _ptr(nu), float(dt), int(s), A.ctypes.data,
+                                  b.ctypes.data, int(n_newton), int(m), 1 if use_graph else 0, hist.ctypes.data))
+    return hist.reshape(s, n_newton + 1)
+
+
+def hdg_lift_gradient(h, U, UH, Q):
+    """Q <- the lifted gradient of (U, UH) (device arrays)."""
+    _check(h, lib().hdg_lift_gradient(h, _ptr(U), _ptr(UH), _ptr(Q)))
+
+
+HDG_PC_BLOCKJACOBI = 1
+HDG_PC_SCHWARZ = 2
+
+
+def hdg_set_preconditioner(h, kind):
+    _check(h, lib().hdg_set_preconditioner(h, int(kind)))
+
+
+def hdg_schwarz_setup(h):
+    _check(h, lib().hdg_schwarz_setup(h))
+
+
+def hdg_schwarz_apply(h, x, y):
+    _check(h, lib().hdg_schwarz_apply(h, _ptr(x), _ptr(y)))

@@ -13,6 +13,8 @@ def create(P, host_only=False):
                      host_only=host_only)
     if not host_only:
         H.hdg_set_params(h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s)
+        if np.any(m.bnd_tag):
+            H.hdg_set_bc_state(h, 1, P.ubc)
     return h
 
 

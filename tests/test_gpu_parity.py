@@ -116,6 +116,12 @@ def test_skewed_scrambled_nonuniform_mesh():
     compare(P, rows=[0, 5, 33, 70, 107])
 
 
+@pytest.mark.parametrize("dim,p,per", [(2, 2, (True, False)), (3, 1, (True, False, True)), (2, 3, (False, False))])
+def test_dirichlet_boundary_faces(dim, p, per):
+    """Tag-1 faces (bhat = uhat - u_b): trace rows, assembly with one-sided faces."""
+    compare(synth.tiny(dim, p, periodic=per, visc_law=1, av=1e-3), check_matvec=True)
+
+
 def test_chunking_is_bitwise_invisible():
     P = synth.config2(n=3)
     a = GpuRun(P).linearize()
@@ -160,4 +166,21 @@ def test_nonfinite_input_is_reported():
     run.U.copy_(torch.from_numpy(synth.tiny(2, 2).U).cuda())
     run.linearize()
     assert H.hdg_status(run.h) == 0
+    run.close()
+
+
+@pytest.mark.parametrize("make", [synth.config1, lambda: synth.tiny(2, 3, periodic=(True, False)),
+                                  lambda: synth.config2(n=3), lambda: synth.tiny(3, 1, periodic=(False, True, True))],
+                         ids=["quad-p2", "quad-p3-dirichlet", "hex-p2", "hex-p1-dirichlet"])
+def test_lift_gradient_matches_oracle(make):
+    import torch
+    from paper_2608_27863_gb300 import hdg as H
+    P = make()
+    run = GpuRun(P)
+    Q = torch.full_like(run.Q, np.nan)
+    H.hdg_lift_gradient(run.h, run.U, run.UH, Q)
+    torch.cuda.synchronize()
+    oq = Problem(P).lift_gradient(P.U, P.UH)
+    q = Q.cpu().numpy()
+    assert np.linalg.norm(q - oq) <= TOL * np.linalg.norm(oq)
     run.close()

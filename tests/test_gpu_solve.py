@@ -30,8 +30,9 @@ def rel(a, b):
 
 
 @pytest.mark.parametrize("make", [synth.config1, lambda: synth.config2(n=3), lambda: synth.config3(n=3),
-                                  lambda: synth.tiny(2, 3, visc_law=1, av=2e-3)],
-                         ids=["quad-p2", "hex-p2", "hex-p3-av", "quad-p3-av"])
+                                  lambda: synth.tiny(2, 3, visc_law=1, av=2e-3),
+                                  lambda: synth.tiny(3, 1, periodic=(True, False, True))],
+                         ids=["quad-p2", "hex-p2", "hex-p3-av", "quad-p3-av", "hex-p1-dirichlet"])
 def test_residual_matches_oracle(make):
     import torch
     from paper_2608_27863_gb300 import hdg as H
@@ -148,4 +149,17 @@ def test_newton_hex_p2_small():
                                   max_newton=10, restart=40, max_gmres=800, gmres_rtol=1e-11)
     assert hist[-1] <= 1e-9
     assert all(hist[i + 1] < hist[i] for i in range(len(hist) - 1))
+    run.close()
+
+
+def test_newton_with_dirichlet_boundary_matches_oracle():
+    from paper_2608_27863_gb300 import hdg as H
+    P = synth.tiny(2, 2, periodic=(True, False))
+    run = GpuRun(P)
+    nit, git, hist = H.hdg_newton(run.h, run.U, run.Q, run.UH, run.Ustar, run.nu, P.dt, P.a_ii, tol=1e-11,
+                                  max_newton=8, restart=40, max_gmres=600, gmres_rtol=1e-12)
+    assert hist[-1] <= 1e-11
+    oq, ou, oh, ohist = oracle_newton(P, 1e-11)
+    assert rel(run.U.cpu().numpy(), ou) < 1e-11
+    assert rel(run.UH.cpu().numpy(), oh) < 1e-11
     run.close()

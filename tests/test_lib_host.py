@@ -38,6 +38,31 @@ def test_library_exports_every_declared_symbol(H):
     assert sorted(H.EXPORTS) == syms
 
 
+def test_connectivity_bit_exact_with_boundaries(H):
+    for dim, per in ((2, (True, False)), (3, (True, False, True)), (3, (False, False, False))):
+        mesh = synth.box_mesh(dim, (3, 4, 3)[:dim], (0,) * dim, (1.0,) * dim, per)
+        h = H.hdg_create_host(dim, mesh.vert_xyz, mesh.elem_vert, mesh.periodic_map, mesh.bnd_tag, 2,
+                              1.4, 100.0, 0.72, 0.3)
+        c = H.hdg_get_connectivity(h)
+        H.hdg_destroy(h)
+        o = Connectivity(mesh, 2)
+        assert np.array_equal(c["f2e"], o.f2e[:, :, 0]) and np.array_equal(c["f2lf"], o.f2e[:, :, 1])
+        assert np.array_equal(c["perm"], o.perm) and np.array_equal(c["col"], o.col)
+        assert np.array_equal(c["rowptr"], o.rowptr)
+
+
+def test_boundary_tag_checks(H):
+    mesh = synth.box_mesh(2, (3, 3), (0, 0), (1, 1), (True, False))
+    bad = mesh.bnd_tag.copy()
+    bad[bad == 1] = 3
+    with pytest.raises(H.HDGError) as ex:
+        H.hdg_create_host(2, mesh.vert_xyz, mesh.elem_vert, mesh.periodic_map, bad, 2, 1.4, 100.0, 0.72, 0.3)
+    assert ex.value.code == H.HDG_EUNSUPPORTED
+    with pytest.raises(H.HDGError) as ex:   # boundary faces without tags
+        H.hdg_create_host(2, mesh.vert_xyz, mesh.elem_vert, mesh.periodic_map, None, 2, 1.4, 100.0, 0.72, 0.3)
+    assert ex.value.code == H.HDG_EINVAL
+
+
 def mesh_cases():
     cases = []
     for dim, n in ((2, (3, 4)), (3, (3, 3, 4))):
