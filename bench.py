@@ -30,6 +30,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "HDG linearize+condense elements/s & % of FP64/TC peak; mixed vs FP64 at tol"
+
+# DRAM bytes (read + write) per element of the dominant kernel, from one ncu
+# capture of the unchanged kernel on the 8^3 hex p=2 case (512 elements, above
+# L2); every CTA works on its own element, so traffic scales with the element
+# count of a launch.
+DRAM_BYTES_PER_ELEMENT = {("elim", 3, 2): 16.45e6}
 L2_BYTES = 129 * 1024 * 1024
 
 WORKLOADS = {
@@ -384,7 +390,11 @@ def run_ours(args, rank, world, local_rank):
                    "faces": H.hdg_query_sizes(h)["n_faces"], "parallelism": "replicas" if world > 1 else "single",
                    "precision": "fp64", "l2": "flushed between timed steps (256 MiB write)"},
         "roofline": {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": (DRAM_BYTES_PER_ELEMENT[(dom, m.dim, P.p)] * per_launch_elems
+                                 if (dom, m.dim, P.p) in DRAM_BYTES_PER_ELEMENT else None),
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_%s launch on the "
+                                       "8^3 case, per element, times the elements of one launch" % dom,
                      "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz (derived); cuBLAS DGEMM "
                                     "measured in this run: %.3f TFLOP/s" % (smmax, dgemm),
                      "flops_per_element": fl[dom]},

@@ -179,6 +179,21 @@ int hdg_lift_gradient(hdg_handle h, const double* U, const double* UH, double* Q
 /* Newton update W <- W + alpha dW (eq. newton-update) on device arrays. */
 int hdg_update_state(hdg_handle h, double* U, double* Q, double* UH, const double* dU, const double* dQ,
                      const double* dUH, double alpha);
+/* Reduced-basis initial guess (Sec. 3.4, eq. rb-min).  A window of at most
+ * nb_max (<= 20) accepted trace corrections W and their products Z = S W
+ * (each taken with the trace operator current at insertion) lives on the
+ * device.  hdg_rb_setup allocates and clears it (nb_max = 0 disables it);
+ * when enabled, hdg_newton, hdg_newton_fixed and hdg_dirk_step start every
+ * GMRES solve from the guess and insert the accepted correction afterwards.
+ * hdg_rb_push inserts w (device [F][m][Nfp]) with z = S w (one matvec),
+ * discarding the oldest column when full; hdg_rb_guess writes x0 = W c,
+ * c = argmin ||g - Z c||_2, solved through the normal equations by
+ * Cholesky with diagonal pivoting (pivots below 1e-13 of the largest
+ * diagonal are dropped, so an empty window gives x0 = 0).  Asynchronous. */
+int hdg_rb_setup(hdg_handle h, int nb_max);
+int hdg_rb_push(hdg_handle h, const double* w);
+int hdg_rb_guess(hdg_handle h, const double* g, double* x0);
+
 /* Preconditioner used by hdg_gmres (precond != 0), hdg_newton,
  * hdg_newton_fixed and hdg_dirk_step: HDG_PC_BLOCKJACOBI (default) or
  * HDG_PC_SCHWARZ. */
@@ -202,10 +217,12 @@ int hdg_schwarz_apply(hdg_handle h, const double* x, double* y);
 int hdg_blockjacobi_setup(hdg_handle h);
 int hdg_blockjacobi_apply(hdg_handle h, const double* x, double* y);
 /* Restarted GMRES(restart) on S x = b with FP64 modified Gram-Schmidt
- * Arnoldi (Sec. 3.2), left-preconditioned by block-Jacobi when precond != 0.
+ * Arnoldi (Sec. 3.2), left-preconditioned by the selected preconditioner
+ * (hdg_set_preconditioner; block-Jacobi by default) when precond != 0.
  * x holds the initial guess and receives the solution (device arrays
- * [F][m][Nfp]).  Stops when the preconditioned residual drops below
- * rtol x its initial value or after max_iter iterations (HDG_ENOCONV).
+ * [F][m][Nfp]).  Stops when the preconditioned residual ||M^{-1}(b - S x)||
+ * drops below rtol x ||M^{-1} b|| (so a good initial guess saves
+ * iterations) or after max_iter iterations (HDG_ENOCONV).
  * iters / relres (host, optional) receive the iteration count and the final
  * relative preconditioned residual.  Workspace is allocated on first use. */
 int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_iter, double rtol, int precond,

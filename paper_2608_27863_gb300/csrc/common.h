@@ -134,6 +134,8 @@ struct hdg_ctx {
     void* d_asmlu = nullptr;               // [E][NT][LDA] LU factors of S_r (FP64, or FP32 for the mixed form)
     int32_t* d_asmpiv = nullptr;           // [E][NT]
     double* d_asmz = nullptr;              // [E][NT] patch corrections
+    int32_t* d_asmperm = nullptr;          // [E][NT] row permutation of each patch as a gather map
+    void* d_asmdinv = nullptr;             // [E][NBLK][2][32][32] inverses of the diagonal blocks of L and U
     size_t asm_bytes = 0;
     int asm_prec = -1;                     // precision of the stored factors
     bool asm_ready = false;
@@ -145,6 +147,13 @@ struct hdg_ctx {
     double* d_h = nullptr;                 // [restart + 2]
     int gm_cap = 0;
     double* d_nw = nullptr;                // Newton work: dU, dQ, dUH, g
+    // reduced-basis initial guess: window of accepted trace corrections and their products
+    double* d_rbW = nullptr;               // [rb_max][N]
+    double* d_rbZ = nullptr;               // [rb_max][N]
+    double* d_rbpart = nullptr;            // [kRbBlocks][256] Gram partial sums
+    double* d_rbc = nullptr;               // [rb_max] coefficients
+    int* d_rbhead = nullptr;               // [2]: next slot, columns stored
+    int rb_max = 0;
     // synchronisation-free Newton / DIRK driver and its CUDA graph
     double* d_fx = nullptr;                // device GMRES scalars: beta, R, cs, sn, y, g
     int fx_cap = 0;

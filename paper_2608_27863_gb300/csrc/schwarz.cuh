@@ -10,7 +10,8 @@
 // are kept in the system's storage type: FP64 for the FP64 form, FP32 for the
 // mixed form, where the preconditioner only needs to be a good approximation.
 // Apply: one CTA per element solves its patch in FP64 arithmetic (blocked
-// triangular solves, one warp per 32-row diagonal block), writes z_r, and a
+// triangular solves with the 32 x 32 diagonal blocks pre-inverted at setup,
+// warp-per-row products for the off-diagonal blocks), writes z_r, and a
 // face kernel sums the (at most two) patch corrections of each face in a
 // fixed order, so the result is bitwise reproducible.
 #pragma once
@@ -153,80 +154,138 @@ __global__ void __launch_bounds__(NTH) k_asm_factor(const T* __restrict__ vals, 
     if (tid == 0 && sflag) atomicOr(status, sflag);
 }
 
-// z_r = S_r^{-1} R_r x for every element r (FP64 arithmetic on T-stored factors)
+template <class C>
+struct AsmBlk {
+    static constexpr int NBLK = (AsmShape<C>::N + 31) / 32;   // 32-row diagonal blocks of the factors
+};
+
+// After the factorisation: the row permutation as a gather map (perm[i] = the
+// patch row that ends up in row i) and the inverses of the 32 x 32 diagonal
+// blocks of L (unit) and U, stored transposed (inv[c][i]) so that a solve
+// reads them coalesced.  A partial last block is padded with the identity.
 template <class C, class T, int NTH>
-__global__ void __launch_bounds__(NTH) k_asm_solve(const T* __restrict__ lu, const int32_t* __restrict__ piv,
-                                                   const int32_t* __restrict__ e2f, const double* __restrict__ x,
-                                                   double* __restrict__ z) {
+__global__ void __launch_bounds__(NTH) k_asm_prep(const T* __restrict__ lu, const int32_t* __restrict__ piv,
+                                                  int32_t* __restrict__ perm, T* __restrict__ dinv) {
+    constexpr int N = AsmShape<C>::N, LDA = AsmShape<C>::LDA, NBLK = AsmBlk<C>::NBLK;
+    __shared__ int p[N];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t e = blockIdx.x;
+    const T* A = lu + e * (size_t)N * LDA;
+    for (int i = tid; i < N; i += NTH) p[i] = i;
+    __syncthreads();
+    if (tid == 0)
+        for (int i = 0; i < N; ++i) {
+            const int q = piv[e * N + i];
+            if (q != i) { const int t = p[i]; p[i] = p[q]; p[q] = t; }
+        }
+    __syncthreads();
+    for (int i = tid; i < N; i += NTH) perm[e * N + i] = p[i];
+    // lane c of a warp computes column c of inv(L_kk) and of inv(U_kk)
+    for (int kb = warp; kb < NBLK; kb += NTH / 32) {
+        const int k0 = 32 * kb, nb = min(32, N - k0);
+        T* DL = dinv + ((size_t)e * NBLK + kb) * 2048;
+        T* DU = DL + 1024;
+        double x[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {             // L x = e_c, L unit lower
+            double s = (i == lane) ? 1.0 : 0.0;
+            if (i < nb) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j < i) s -= (double)A[(size_t)(k0 + i) * LDA + k0 + j] * x[j];
+            }
+            x[i] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) DL[lane * 32 + i] = (T)x[i];
+#pragma unroll
+        for (int i = 31; i >= 0; --i) {            // U x = e_c
+            double s = (i == lane) ? 1.0 : 0.0;
+            if (i < nb) {
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j > i && j < nb) s -= (double)A[(size_t)(k0 + i) * LDA + k0 + j] * x[j];
+                s /= (double)A[(size_t)(k0 + i) * LDA + k0 + i];
+            }
+            x[i] = s;
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) DU[lane * 32 + i] = (T)x[i];
+    }
+}
+
+// z_r = S_r^{-1} R_r x for every element r: permuted gather, then blocked
+// forward and backward substitution (diagonal blocks by their stored
+// inverses, off-diagonal blocks as warp-per-row products), FP64 arithmetic.
+template <class C, class T, int NTH>
+__global__ void __launch_bounds__(NTH) k_asm_solve(const T* __restrict__ lu, const int32_t* __restrict__ perm,
+                                                   const T* __restrict__ dinv, const int32_t* __restrict__ e2f,
+                                                   const double* __restrict__ x, double* __restrict__ z) {
     constexpr int N = AsmShape<C>::N, LDA = AsmShape<C>::LDA, NF = C::NF, BS = C::BS;
-    constexpr int NW = NTH / 32;
+    constexpr int NBLK = AsmBlk<C>::NBLK, NW = NTH / 32;
+    static_assert(NTH == 256, "diagonal-block product assumes 8 warps");
     __shared__ double xs[N];
+    __shared__ double red[NW][32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t e = blockIdx.x;
     const T* A = lu + e * (size_t)N * LDA;
     for (int i = tid; i < N; i += NTH) {
-        const int f = i / BS;
-        xs[i] = x[(size_t)e2f[e * NF + f] * BS + (i - f * BS)];
+        const int j = perm[e * N + i], f = j / BS;
+        xs[i] = x[(size_t)e2f[e * NF + f] * BS + (j - f * BS)];
     }
     __syncthreads();
-    if (tid == 0)
-        for (int i = 0; i < N; ++i) {
-            const int p = piv[e * N + i];
-            if (p != i) { const double t = xs[i]; xs[i] = xs[p]; xs[p] = t; }
+    // xs[k0 .. k0+32) <- inv(D_kk) xs[k0 .. k0+32): warp w sums columns 4w .. 4w+3
+    auto diag_product = [&](const T* Dt, int k0, int nb) {
+        double s = 0.0;
+        if (lane < nb) {
+#pragma unroll
+            for (int c = 4 * warp; c < 4 * warp + 4; ++c)
+                if (c < nb) s = fma((double)Dt[c * 32 + lane], xs[k0 + c], s);
         }
-    __syncthreads();
-    // forward substitution with the unit lower factor
+        red[warp][lane] = s;
+        __syncthreads();
+        if (tid < nb) {
+            double t = 0.0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) t += red[w][tid];
+            xs[k0 + tid] = t;
+        }
+        __syncthreads();
+    };
+    // xs[r] -= sum_j A[r][k0 + j] xs[k0 + j] for r in [r0, r1), one warp per row
+    auto offdiag_update = [&](int k0, int nb, int r0, int r1) {
+        const double xv = lane < nb ? xs[k0 + lane] : 0.0;
 #pragma unroll 1
-    for (int k0 = 0; k0 < N; k0 += 32) {
-        const int kb = min(32, N - k0);
-        if (warp == 0) {
-            double row[32];
+        for (int r = r0 + warp; r < r1; r += 4 * NW) {
+            double s[4];
 #pragma unroll
-            for (int j = 0; j < 32; ++j) row[j] = (lane < kb && j < kb) ? (double)A[(size_t)(k0 + lane) * LDA + k0 + j] : 0.0;
-            double v = lane < kb ? xs[k0 + lane] : 0.0;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const double xj = __shfl_sync(0xffffffffu, v, j);
-                if (lane > j) v = fma(-row[j], xj, v);
+            for (int u = 0; u < 4; ++u) {
+                const int rr = r + u * NW;
+                s[u] = (rr < r1 && lane < nb) ? (double)A[(size_t)rr * LDA + k0 + lane] * xv : 0.0;
             }
-            if (lane < kb) xs[k0 + lane] = v;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                for (int off = 16; off > 0; off >>= 1) s[u] += __shfl_down_sync(0xffffffffu, s[u], off);
+            if (lane == 0) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (r + u * NW < r1) xs[r + u * NW] -= s[u];
+            }
         }
         __syncthreads();
+    };
+    const T* D = dinv + (size_t)e * NBLK * 2048;
 #pragma unroll 1
-        for (int r = k0 + kb + warp; r < N; r += NW) {
-            double s = lane < kb ? (double)A[(size_t)r * LDA + k0 + lane] * xs[k0 + lane] : 0.0;
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-            if (lane == 0) xs[r] -= s;
-        }
-        __syncthreads();
+    for (int kb = 0; kb < NBLK; ++kb) {
+        const int k0 = 32 * kb, nb = min(32, N - k0);
+        diag_product(D + (size_t)kb * 2048, k0, nb);
+        if (k0 + nb < N) offdiag_update(k0, nb, k0 + nb, N);
     }
-    // backward substitution with the upper factor
 #pragma unroll 1
-    for (int k1 = N; k1 > 0; k1 -= 32) {
-        const int k0 = max(0, k1 - 32), kb = k1 - k0;
-        if (warp == 0) {
-            double row[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) row[j] = (lane < kb && j < kb) ? (double)A[(size_t)(k0 + lane) * LDA + k0 + j] : 0.0;
-            double v = lane < kb ? xs[k0 + lane] : 0.0;
-#pragma unroll
-            for (int j = 31; j >= 0; --j) {
-                if (j < kb) {
-                    if (lane == j) v = v / row[j];
-                    const double xj = __shfl_sync(0xffffffffu, v, j);
-                    if (lane < j) v = fma(-row[j], xj, v);
-                }
-            }
-            if (lane < kb) xs[k0 + lane] = v;
-        }
-        __syncthreads();
-#pragma unroll 1
-        for (int r = warp; r < k0; r += NW) {
-            double s = lane < kb ? (double)A[(size_t)r * LDA + k0 + lane] * xs[k0 + lane] : 0.0;
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-            if (lane == 0) xs[r] -= s;
-        }
-        __syncthreads();
+    for (int kb = NBLK - 1; kb >= 0; --kb) {
+        const int k0 = 32 * kb, nb = min(32, N - k0);
+        diag_product(D + (size_t)kb * 2048 + 1024, k0, nb);
+        if (k0 > 0) offdiag_update(k0, nb, 0, k0);
     }
     for (int i = tid; i < N; i += NTH) z[e * (size_t)N + i] = xs[i];
 }
@@ -263,6 +322,12 @@ int run_asm_setup(hdg_ctx* h) {
         k_asm_factor<C, double, NB, 256><<<(unsigned)h->E, 256, smem, h->stream>>>(
             h->d_vals, h->d_blk, (double*)h->d_asmlu, h->d_asmpiv, h->d_status);
     }
+    if (h->sys_prec == HDG_PREC_MIXED)
+        k_asm_prep<C, float, 256><<<(unsigned)h->E, 256, 0, h->stream>>>((const float*)h->d_asmlu, h->d_asmpiv,
+                                                                        h->d_asmperm, (float*)h->d_asmdinv);
+    else
+        k_asm_prep<C, double, 256><<<(unsigned)h->E, 256, 0, h->stream>>>((const double*)h->d_asmlu, h->d_asmpiv,
+                                                                         h->d_asmperm, (double*)h->d_asmdinv);
     HDG_CK(cudaGetLastError());
     return HDG_OK;
 }
@@ -271,11 +336,11 @@ template <int D, int P>
 int run_asm_apply(hdg_ctx* h, const double* x, double* y) {
     using C = Cfg<D, P>;
     if (h->asm_prec == HDG_PREC_MIXED)
-        k_asm_solve<C, float, 256><<<(unsigned)h->E, 256, 0, h->stream>>>((const float*)h->d_asmlu, h->d_asmpiv,
-                                                                         h->d_e2f, x, h->d_asmz);
+        k_asm_solve<C, float, 256><<<(unsigned)h->E, 256, 0, h->stream>>>(
+            (const float*)h->d_asmlu, h->d_asmperm, (const float*)h->d_asmdinv, h->d_e2f, x, h->d_asmz);
     else
-        k_asm_solve<C, double, 256><<<(unsigned)h->E, 256, 0, h->stream>>>((const double*)h->d_asmlu, h->d_asmpiv,
-                                                                          h->d_e2f, x, h->d_asmz);
+        k_asm_solve<C, double, 256><<<(unsigned)h->E, 256, 0, h->stream>>>(
+            (const double*)h->d_asmlu, h->d_asmperm, (const double*)h->d_asmdinv, h->d_e2f, x, h->d_asmz);
     const int64_t n = h->F * C::BS;
     k_asm_sum<C><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->d_asmz, h->d_f2e, h->d_f2lf, y, h->F);
     HDG_CK(cudaGetLastError());

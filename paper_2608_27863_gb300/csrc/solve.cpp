@@ -87,12 +87,16 @@ int schwarz_setup(hdg_ctx* h) {
     const int lda = (h->NT + 3) & ~3;
     const size_t need = (prec == HDG_PREC_MIXED ? sizeof(float) : sizeof(double)) * (size_t)h->E * h->NT * lda;
     int rc;
+    const size_t nblk = (h->NT + 31) / 32;
+    const size_t need_d = (prec == HDG_PREC_MIXED ? sizeof(float) : sizeof(double)) * (size_t)h->E * nblk * 2048;
     if (h->asm_bytes < need) {
         if ((rc = alloc(h, &h->d_asmlu, need))) return rc;
+        if ((rc = alloc(h, &h->d_asmdinv, need_d))) return rc;
         h->asm_bytes = need;
     }
     if (!h->d_asmpiv) {
         if ((rc = alloc(h, (void**)&h->d_asmpiv, sizeof(int32_t) * h->E * h->NT))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_asmperm, sizeof(int32_t) * h->E * h->NT))) return rc;
         if ((rc = alloc(h, (void**)&h->d_asmz, sizeof(double) * h->E * h->NT))) return rc;
     }
     if ((rc = ensure_residual_storage(h))) return rc;       // face-to-element maps
@@ -104,6 +108,29 @@ int schwarz_setup(hdg_ctx* h) {
 }
 
 int precond_setup(hdg_ctx* h);
+int matvec(hdg_ctx* h, const double* x, double* y);
+
+// dUhat_0 = W c with c = argmin ||g - Z c|| over the window (eq. rb-min)
+int rb_guess(hdg_ctx* h, const double* g, double* x0) {
+    const int64_t N = h->F * h->BS;
+    k_rb_gram_part<<<kRbBlocks, 256, 0, h->stream>>>(h->d_rbZ, h->rb_max, g, N, h->d_rbpart);
+    k_rb_solve<<<1, 256, 0, h->stream>>>(h->d_rbpart, kRbBlocks, h->rb_max, h->d_rbc);
+    CKS(cudaMemsetAsync(x0, 0, sizeof(double) * N, h->stream));
+    k_combine<<<grid_for(N), 256, 0, h->stream>>>(h->d_rbW, N, h->d_rbc, h->rb_max, x0, N);
+    CKS(cudaGetLastError());
+    return HDG_OK;
+}
+
+// insert an accepted correction w with z = S w (one trace matvec), dropping the oldest column when full
+int rb_push(hdg_ctx* h, const double* w) {
+    const int64_t N = h->F * h->BS;
+    int rc;
+    if ((rc = matvec(h, w, h->d_w))) return rc;
+    k_rb_store<<<grid_for(N), 256, 0, h->stream>>>(w, h->d_w, h->d_rbW, h->d_rbZ, h->d_rbhead, N);
+    k_rb_advance<<<1, 32, 0, h->stream>>>(h->d_rbhead, h->rb_max);
+    CKS(cudaGetLastError());
+    return HDG_OK;
+}
 
 int matvec(hdg_ctx* h, const double* x, double* y) {
     int rc;
@@ -140,7 +167,7 @@ int ensure_fixed_workspace(hdg_ctx* h, int m) {
 
 // GMRES(m) from x = 0, exactly m iterations, no host synchronisation: the Givens
 // rotations and the triangular solve run on the device.
-int gmres_fixed_async(hdg_ctx* h, const double* b, double* x, int m) {
+int gmres_fixed_async(hdg_ctx* h, const double* b, double* x, int m, bool use_x0) {
     const int64_t N = h->F * h->BS;
     double* V = h->d_V;
     double* w = h->d_w;
@@ -152,7 +179,13 @@ int gmres_fixed_async(hdg_ctx* h, const double* b, double* x, int m) {
     double* gv = y + m;
     double* hc = h->d_h;
     int rc;
-    if ((rc = precond_apply(h, b, V))) return rc;
+    if (use_x0) {                               // r0 = b - S x0
+        if ((rc = matvec(h, x, w))) return rc;
+        k_axpby<<<grid_for(N), 256, 0, h->stream>>>(1.0, b, -1.0, w, N);
+        if ((rc = precond_apply(h, w, V))) return rc;
+    } else if ((rc = precond_apply(h, b, V))) {
+        return rc;
+    }
     dev_dot(h, V, V, N, beta, true);
     k_set_first<<<1, 64, 0, h->stream>>>(beta, gv, m);
     k_scale_safe<<<grid_for(N), 256, 0, h->stream>>>(V, beta, V, N);
@@ -170,7 +203,7 @@ int gmres_fixed_async(hdg_ctx* h, const double* b, double* x, int m) {
         k_givens_step<<<1, 1, 0, h->stream>>>(hc, j, m, R, cs, sn, gv);
     }
     k_backsolve<<<1, 1, 0, h->stream>>>(R, gv, m, m, y);
-    CKS(cudaMemsetAsync(x, 0, sizeof(double) * N, h->stream));
+    if (!use_x0) CKS(cudaMemsetAsync(x, 0, sizeof(double) * N, h->stream));
     k_combine<<<grid_for(N), 256, 0, h->stream>>>(V, N, y, m, x, N);
     CKS(cudaGetLastError());
     return HDG_OK;
@@ -266,6 +299,44 @@ int hdg_schwarz_apply(hdg_handle h, const double* x, double* y) {
     return rc;
 }
 
+int hdg_rb_setup(hdg_handle h, int nb_max) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
+    if (nb_max < 0 || nb_max > kRbMax) return fail(h, HDG_EINVAL, "nb_max must be in 0..20");
+    h->rb_max = 0;
+    if (nb_max == 0) return HDG_OK;
+    const int64_t N = h->F * h->BS;
+    int rc;
+    if ((rc = alloc(h, (void**)&h->d_rbW, sizeof(double) * (size_t)nb_max * N))) return rc;
+    if ((rc = alloc(h, (void**)&h->d_rbZ, sizeof(double) * (size_t)nb_max * N))) return rc;
+    if (!h->d_rbpart) {
+        if ((rc = alloc(h, (void**)&h->d_rbpart, sizeof(double) * kRbBlocks * 256))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_rbc, sizeof(double) * kRbMax))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_rbhead, sizeof(int) * 2))) return rc;
+    }
+    if (!h->d_w && (rc = alloc(h, (void**)&h->d_w, sizeof(double) * N))) return rc;
+    CKS(cudaMemsetAsync(h->d_rbW, 0, sizeof(double) * (size_t)nb_max * N, h->stream));
+    CKS(cudaMemsetAsync(h->d_rbZ, 0, sizeof(double) * (size_t)nb_max * N, h->stream));
+    CKS(cudaMemsetAsync(h->d_rbhead, 0, sizeof(int) * 2, h->stream));
+    h->rb_max = nb_max;
+    return HDG_OK;
+}
+
+int hdg_rb_push(hdg_handle h, const double* w) {
+    if (!h) return HDG_EINVAL;
+    if (h->rb_max <= 0) return fail(h, HDG_EINVAL, "reduced basis not set up (hdg_rb_setup)");
+    if (!h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
+    if (!w) return fail(h, HDG_EINVAL, "w is NULL");
+    return rb_push(h, w);
+}
+
+int hdg_rb_guess(hdg_handle h, const double* g, double* x0) {
+    if (!h) return HDG_EINVAL;
+    if (h->rb_max <= 0) return fail(h, HDG_EINVAL, "reduced basis not set up (hdg_rb_setup)");
+    if (!g || !x0 || g == x0) return fail(h, HDG_EINVAL, "g and x0 must be distinct device arrays");
+    return rb_guess(h, g, x0);
+}
+
 int hdg_blockjacobi_apply(hdg_handle h, const double* x, double* y) {
     if (!h) return HDG_EINVAL;
     if (!h->bj_ready) return fail(h, HDG_EINVAL, "block-Jacobi factors not set up");
@@ -302,6 +373,14 @@ int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_ite
     int it = 0;
     double beta0 = -1.0, res = 0.0;
     bool done = false;
+    {   // reference norm ||M^{-1} b||: the tolerance does not depend on the initial guess
+        if (precond) { if ((rc = precond_apply(h, b, V))) return rc; }
+        else CKS(cudaMemcpyAsync(V, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, h->stream));
+        dev_dot(h, V, V, N, dh, true);
+        CKS(cudaMemcpyAsync(&beta0, dh, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CKS(cudaStreamSynchronize(h->stream));
+        if (!std::isfinite(beta0)) return fail(h, HDG_ENONFINITE, "non-finite right-hand side in GMRES");
+    }
     while (!done) {
         // r = M^{-1} (b - S x) into V_0
         if ((rc = matvec(h, x, w))) return rc;
@@ -313,7 +392,6 @@ int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_ite
         CKS(cudaMemcpyAsync(&beta, dh, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
         CKS(cudaStreamSynchronize(h->stream));
         if (!std::isfinite(beta)) return fail(h, HDG_ENONFINITE, "non-finite residual in GMRES");
-        if (beta0 < 0.0) beta0 = beta;
         res = beta;
         if (beta == 0.0 || beta <= rtol * beta0 || it >= max_iter) break;
         k_scale_dev<<<grid_for(N), 256, 0, h->stream>>>(V, dh, V, N);
@@ -401,12 +479,17 @@ int hdg_newton(hdg_handle h, double* U, double* Q, double* UH, const double* Ust
         if ((rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr))) return rc;
         if ((rc = hdg_trace_rhs(h, g))) return rc;
         if ((rc = precond_setup(h))) return rc;
-        CKS(cudaMemsetAsync(dUH, 0, sizeof(double) * h->F * h->BS, h->stream));
+        if (h->rb_max > 0) {
+            if ((rc = rb_guess(h, g, dUH))) return rc;
+        } else {
+            CKS(cudaMemsetAsync(dUH, 0, sizeof(double) * h->F * h->BS, h->stream));
+        }
         int it = 0;
         double rel = 0.0;
         rc = hdg_gmres(h, g, dUH, restart, max_gmres, gmres_rtol, 1, &it, &rel);
         total += it;
         if (rc && rc != HDG_ENOCONV) return rc;
+        if (h->rb_max > 0 && (rc = rb_push(h, dUH))) return rc;
         if ((rc = hdg_recover_interior(h, dUH, dQ, dU))) return rc;
         if ((rc = hdg_update_state(h, U, Q, UH, dU, dQ, dUH, 1.0))) return rc;
     }
@@ -434,7 +517,13 @@ int newton_iteration_async(hdg_ctx* h, double* U, double* Q, double* UH, const d
     if ((rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr))) return rc;
     if ((rc = hdg_trace_rhs(h, g))) return rc;
     if ((rc = precond_setup(h))) return rc;
-    if ((rc = gmres_fixed_async(h, g, dUH, m))) return rc;
+    if (h->rb_max > 0) {
+        if ((rc = rb_guess(h, g, dUH))) return rc;
+        if ((rc = gmres_fixed_async(h, g, dUH, m, true))) return rc;
+        if ((rc = rb_push(h, dUH))) return rc;
+    } else if ((rc = gmres_fixed_async(h, g, dUH, m, false))) {
+        return rc;
+    }
     if ((rc = hdg_recover_interior(h, dUH, dQ, dU))) return rc;
     return hdg_update_state(h, U, Q, UH, dU, dQ, dUH, 1.0);
 }
@@ -500,7 +589,8 @@ int hdg_newton_fixed(hdg_handle h, double* U, double* Q, double* UH, const doubl
     if ((rc = ensure_fixed_workspace(h, m))) return rc;
     const uint64_t key = mix_key({1, (uint64_t)U, (uint64_t)Q, (uint64_t)UH, (uint64_t)Ustar, (uint64_t)nu, dbits(dt),
                                   dbits(a_ii), (uint64_t)m, (uint64_t)h->precision, (uint64_t)h->schur_mode,
-                                  (uint64_t)h->d_V, (uint64_t)h->d_fx});
+                                  (uint64_t)h->d_V, (uint64_t)h->d_fx, (uint64_t)h->rb_max, (uint64_t)h->d_rbW,
+                                  (uint64_t)h->pc_kind});
     if (use_graph && (!h->gexec || h->gkey != key)) {
         // one linearization outside the capture: every lazily allocated buffer exists before it
         if ((rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr))) return rc;
@@ -557,7 +647,8 @@ int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* 
     double* St = Us + n;                     // stage states U^{n,1..s}
     uint64_t key = mix_key({2, (uint64_t)U, (uint64_t)Q, (uint64_t)UH, (uint64_t)nu, dbits(dt), (uint64_t)s,
                             (uint64_t)n_newton, (uint64_t)m, (uint64_t)h->precision, (uint64_t)h->schur_mode,
-                            (uint64_t)h->d_V, (uint64_t)h->d_fx, (uint64_t)h->d_dirk});
+                            (uint64_t)h->d_V, (uint64_t)h->d_fx, (uint64_t)h->d_dirk, (uint64_t)h->rb_max,
+                            (uint64_t)h->d_rbW, (uint64_t)h->pc_kind});
     for (int i = 0; i < s * s; ++i) key = mix_key({key, dbits(A[i])});
     if (use_graph && (!h->gexec || h->gkey != key)) {
         // one linearization outside the capture: every lazily allocated buffer exists before it

@@ -357,6 +357,12 @@ __global__ void k_backsolve(const double* R, const double* gv, int k, int m, dou
 __global__ void k_set_first(const double* beta, double* gv, int m);
 __global__ void k_hist_push(const double* norms, double* hist, int* counter, int cap);
 __global__ void k_lincomb3(double a, const double* x, double b, const double* y, double c, double* z, int64_t n);
+constexpr int kRbMax = 20;            // largest reduced-basis window
+constexpr int kRbBlocks = 304;        // row-tile blocks of the Gram reduction
+__global__ void k_rb_gram_part(const double* Z, int nb, const double* g, int64_t n, double* part);
+__global__ void k_rb_solve(const double* part, int nparts, int nb, double* c);
+__global__ void k_rb_store(const double* w, const double* z, double* W, double* Z, const int* head, int64_t n);
+__global__ void k_rb_advance(int* head, int nb);
 
 // ----------------------------------------------------------------------------
 // launchers

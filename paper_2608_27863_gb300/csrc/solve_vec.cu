@@ -134,6 +134,113 @@ __global__ void k_lincomb3(double a, const double* x, double b, const double* y,
         z[i] = a * x[i] + b * y[i] + c * z[i];
 }
 
+// Reduced-basis window: partial sums of the Gram matrix Z^T Z (pairs k <= l)
+// and of Z^T g over row tiles; thread t of a block owns quantity t.
+__global__ void k_rb_gram_part(const double* Z, int nb, const double* g, int64_t n, double* part) {
+    constexpr int TR = 128;
+    __shared__ double zs[kRbMax][TR];
+    __shared__ double gs[TR];
+    const int t = threadIdx.x;
+    const int npair = nb * (nb + 1) / 2;
+    int k = -1, l = -1;                     // quantity t: pair (k, l) with k <= l, or (k, g) when l == nb
+    if (t < npair) {
+        int r = t;
+        k = 0;
+        while (r >= nb - k) { r -= nb - k; ++k; }
+        l = k + r;
+    } else if (t < npair + nb) {
+        k = t - npair;
+        l = nb;
+    }
+    double acc = 0.0;
+    for (int64_t r0 = (int64_t)blockIdx.x * TR; r0 < n; r0 += (int64_t)gridDim.x * TR) {
+        __syncthreads();
+        for (int idx = t; idx < (nb + 1) * TR; idx += blockDim.x) {
+            const int c = idx / TR, i = idx - c * TR;
+            const int64_t row = r0 + i;
+            const double v = row < n ? (c < nb ? Z[(size_t)c * n + row] : g[row]) : 0.0;
+            if (c < nb) zs[c][i] = v; else gs[i] = v;
+        }
+        __syncthreads();
+        if (k >= 0) {
+            const double* b = (l < nb) ? zs[l] : gs;
+            for (int i = 0; i < TR; ++i) acc = fma(zs[k][i], b[i], acc);
+        }
+    }
+    part[(size_t)blockIdx.x * blockDim.x + t] = acc;
+}
+
+// Sums the partials in block order, then solves the normal equations
+// (Z^T Z) c = Z^T g by Cholesky with diagonal pivoting; pivots below
+// 1e-13 of the largest diagonal are dropped (their coefficients are zero), so
+// an empty or rank-deficient window gives a finite least-squares solution.
+__global__ void k_rb_solve(const double* part, int nparts, int nb, double* c) {
+    __shared__ double q[kRbMax * (kRbMax + 1) / 2 + kRbMax];
+    const int t = threadIdx.x;
+    const int nq = nb * (nb + 1) / 2 + nb;
+    if (t < nq) {
+        double s = 0.0;
+        for (int b = 0; b < nparts; ++b) s += part[(size_t)b * blockDim.x + t];
+        q[t] = s;
+    }
+    __syncthreads();
+    if (t != 0) return;
+    double G[kRbMax][kRbMax], rhs[kRbMax], y[kRbMax];
+    int pidx[kRbMax];
+    int idx = 0;
+    for (int k = 0; k < nb; ++k)
+        for (int l = k; l < nb; ++l) { G[k][l] = q[idx]; G[l][k] = q[idx]; ++idx; }
+    for (int k = 0; k < nb; ++k) { rhs[k] = q[idx + k]; pidx[k] = k; c[k] = 0.0; }
+    double dmax = 0.0;
+    for (int k = 0; k < nb; ++k) dmax = fmax(dmax, G[k][k]);
+    int r = 0;                               // accepted pivots
+    for (; r < nb; ++r) {
+        int best = r;
+        for (int i = r + 1; i < nb; ++i)
+            if (G[pidx[i]][pidx[i]] > G[pidx[best]][pidx[best]]) best = i;
+        const int tmp = pidx[r]; pidx[r] = pidx[best]; pidx[best] = tmp;
+        const int pr = pidx[r];
+        const double d = G[pr][pr];
+        if (!(d > 1e-13 * dmax)) break;
+        const double ld = sqrt(d);
+        G[pr][pr] = ld;
+        for (int i = r + 1; i < nb; ++i) G[pidx[i]][pr] /= ld;     // column r of L, stored at (pidx[i], pr)
+        for (int i = r + 1; i < nb; ++i)
+            for (int j = r + 1; j <= i; ++j) {
+                const double v = G[pidx[i]][pidx[j]] - G[pidx[i]][pr] * G[pidx[j]][pr];
+                G[pidx[i]][pidx[j]] = v;
+                G[pidx[j]][pidx[i]] = v;
+            }
+    }
+    for (int i = 0; i < r; ++i) {            // L y = P rhs
+        double s = rhs[pidx[i]];
+        for (int j = 0; j < i; ++j) s -= G[pidx[i]][pidx[j]] * y[j];
+        y[i] = s / G[pidx[i]][pidx[i]];
+    }
+    for (int i = r - 1; i >= 0; --i) {       // L^T x = y
+        double s = y[i];
+        for (int j = i + 1; j < r; ++j) s -= G[pidx[j]][pidx[i]] * y[j];
+        y[i] = s / G[pidx[i]][pidx[i]];
+    }
+    for (int i = 0; i < r; ++i) c[pidx[i]] = y[i];
+}
+
+// insert (w, z) into slot head[0] of the window
+__global__ void k_rb_store(const double* w, const double* z, double* W, double* Z, const int* head, int64_t n) {
+    const int slot = head[0];
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        W[(size_t)slot * n + i] = w[i];
+        Z[(size_t)slot * n + i] = z[i];
+    }
+}
+
+__global__ void k_rb_advance(int* head, int nb) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        head[0] = (head[0] + 1) % nb;
+        head[1] = min(head[1] + 1, nb);
+    }
+}
+
 __global__ void k_to_f32(const double* x, float* y, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = (float)x[i];

@@ -37,7 +37,7 @@ EXPORTS = [
     "hdg_profile_read", "hdg_linearize_condense_static", "hdg_residual", "hdg_update_state",
     "hdg_blockjacobi_setup", "hdg_blockjacobi_apply", "hdg_gmres", "hdg_newton", "hdg_set_bc_state",
     "hdg_newton_fixed", "hdg_dirk_step", "hdg_lift_gradient", "hdg_set_preconditioner", "hdg_schwarz_setup",
-    "hdg_schwarz_apply",
+    "hdg_schwarz_apply", "hdg_rb_setup", "hdg_rb_push", "hdg_rb_guess",
 ]
 KERNEL_CLASSES = ["point", "blocks", "elim", "assemble", "matvec", "recover", "schur"]
 
@@ -106,6 +106,9 @@ def lib():
         "hdg_set_preconditioner": [vp, i32],
         "hdg_schwarz_setup": [vp],
         "hdg_schwarz_apply": [vp, vp, vp],
+        "hdg_rb_setup": [vp, i32],
+        "hdg_rb_push": [vp, vp],
+        "hdg_rb_guess": [vp, vp, vp],
         "hdg_newton_fixed": [vp, vp, vp, vp, vp, vp, dbl, dbl, i32, i32, i32, vp],
         "hdg_dirk_step": [vp, vp, vp, vp, vp, dbl, i32, vp, vp, i32, i32, i32, vp],
     }
@@ -342,3 +345,16 @@ def hdg_schwarz_setup(h):
 
 def hdg_schwarz_apply(h, x, y):
     _check(h, lib().hdg_schwarz_apply(h, _ptr(x), _ptr(y)))
+
+
+def hdg_rb_setup(h, nb_max):
+    """Allocate and clear the reduced-basis window (nb_max = 0 disables it)."""
+    _check(h, lib().hdg_rb_setup(h, int(nb_max)))
+
+
+def hdg_rb_push(h, w):
+    _check(h, lib().hdg_rb_push(h, _ptr(w)))
+
+
+def hdg_rb_guess(h, g, x0):
+    _check(h, lib().hdg_rb_guess(h, _ptr(g), _ptr(x0)))
