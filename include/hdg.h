@@ -179,6 +179,23 @@ int hdg_lift_gradient(hdg_handle h, const double* U, const double* UH, double* Q
 /* Newton update W <- W + alpha dW (eq. newton-update) on device arrays. */
 int hdg_update_state(hdg_handle h, double* U, double* Q, double* UH, const double* dU, const double* dQ,
                      const double* dUH, double alpha);
+/* Artificial-viscosity field (Sec. 2.2, eq. av-coeffs) from the nodal state
+ * U [E][m][Np] and gradient Q [E][d][m][Np] (device): at every node
+ * s = sqrt(h_m / p) L(-div v) / c* * L(-div v)^2 / (L(-div v)^2 + |curl v|^2
+ * + 1e-12), c* = sqrt(gamma p / rho), L = clamp to >= 0; nu_raw = c_av
+ * min(max(s, 0), s_max); the elemental raw value is the maximum over the
+ * element's nodes.  Smoothing: two passes of averaging to the (periodic
+ * master) vertices with the element mean of its vertices in between, then
+ * multilinear interpolation to the nodes.  Writes nu [E][Np] (device), the
+ * field hdg_linearize_condense takes (frozen over a step).  Asynchronous. */
+int hdg_av_field(hdg_handle h, const double* U, const double* Q, double c_av, double h_m, double s_max, double* nu);
+/* Volume-integrated diagnostics (Sec. 5.1, eqs. tgv-kinetic-energy and
+ * tgv-total-dissipation) with the volume quadrature: out (host, 4 doubles)
+ * = (E_k, eps_S, eps_D, |Omega|), E_k = int rho v.v / (2 |Omega|),
+ * eps_S = int mu~ |curl v|^2 / (Re |Omega|), eps_D = 4 int mu~ (div v)^2 /
+ * (3 Re |Omega|), u and grad u from U and Q.  Fixed-order sums; synchronises. */
+int hdg_tgv_diagnostics(hdg_handle h, const double* U, const double* Q, double* out);
+
 /* Reduced-basis initial guess (Sec. 3.4, eq. rb-min).  A window of at most
  * nb_max (<= 20) accepted trace corrections W and their products Z = S W
  * (each taken with the trace operator current at insertion) lives on the
@@ -260,6 +277,29 @@ int hdg_newton_fixed(hdg_handle h, double* U, double* Q, double* UH, const doubl
  * receives the residual norms.  Synchronises at the end. */
 int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* nu, double dt, int s,
                   const double* A, const double* b, int n_newton, int m, int use_graph, double* hist);
+
+/* Autotuner (not from the paper).  Times every kernel variant that computes
+ * the same quantities to the same accuracy on the caller's own inputs
+ * (reps linearize + condense calls each, after one warm-up, CUDA events on
+ * the handle's stream) and keeps the fastest for later calls:
+ *  - FP64 form: the elimination kernel's panel width (16 or 8 columns) and
+ *    the residency it is compiled for (2 or 1 CTAs per SM); results differ
+ *    only by rounding order;
+ *  - mixed form requested as HDG_PREC_MIXED: the Schur product as FP32 SIMT
+ *    (schur_mode 0) or 3xTF32 tensor cores (2), both FP32-accurate;
+ *    TF32 / 3xTF32 requested explicitly are kept.
+ * out (host, optional) receives the choice and every candidate's time.
+ * hdg_set_tuning applies a stored choice.  Both synchronise; the system
+ * left assembled is that of the last candidate timed. */
+typedef struct {
+    int elim_nb, elim_minb, schur_mode;   /* the chosen variant */
+    int n_cand;                           /* candidates timed (<= 8) */
+    int cand[8][3];                       /* (elim_nb, elim_minb, schur_mode) of each candidate */
+    double ms[8];                         /* mean time of one linearize + condense, ms */
+} hdg_tune;
+int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* UH, const double* Ustar,
+                 const double* nu, double dt, double a_ii, int reps, hdg_tune* out);
+int hdg_set_tuning(hdg_handle h, const hdg_tune* t);
 
 /* Per-kernel timing with CUDA events recorded on the handle's stream around
  * every kernel launch (not from the paper: instrumentation for rooflines).

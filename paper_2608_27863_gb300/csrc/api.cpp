@@ -121,6 +121,7 @@ int create_host(hdg_ctx* h, const hdg_mesh* mesh, int p, double gamma, double Re
     }
     int rc = build_skeleton(*mesh, p, h->sk, h->err);
     if (rc) return rc;
+    if ((rc = build_vertex_map(*mesh, h->av_ev, h->av_vrow, h->av_vcol, h->err))) return rc;
     h->F = h->sk.n_faces;
     h->nnzb = h->sk.rowptr[h->F];
     // boundary tags: 0 on interior / periodic faces, 1 (Dirichlet / far-field, bhat = uhat - u_b) on
@@ -276,6 +277,76 @@ int hdg_set_params(hdg_handle h, const hdg_params* prm) {
     h->phys.s = prm->suth_s;
     h->precision = prm->precision == HDG_PREC_FP64 ? HDG_PREC_FP64 : HDG_PREC_MIXED;
     h->schur_mode = prm->precision == HDG_PREC_FP64 ? 0 : prm->precision - HDG_PREC_MIXED;
+    h->prec_req = prm->precision;
+    return HDG_OK;
+}
+
+int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* UH, const double* Ustar,
+                 const double* nu, double dt, double a_ii, int reps, hdg_tune* out) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
+    if (reps < 1 || reps > 100) return fail(h, HDG_EINVAL, "reps must be in 1..100");
+    // candidates: variants that compute the same quantities to the same accuracy
+    int cand[8][3];
+    int n = 0;
+    if (h->precision == HDG_PREC_FP64) {
+        const int nbs[2] = {16, 8}, minbs[2] = {2, 1};
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) { cand[n][0] = nbs[a]; cand[n][1] = minbs[b]; cand[n][2] = h->schur_mode; ++n; }
+    } else if (h->prec_req == HDG_PREC_MIXED) {
+        // FP32 SIMT and 3xTF32 tensor-core Schur products are both FP32-accurate
+        for (int sm : {0, 2}) { cand[n][0] = h->elim_nb; cand[n][1] = h->elim_minb; cand[n][2] = sm; ++n; }
+    } else {
+        cand[n][0] = h->elim_nb; cand[n][1] = h->elim_minb; cand[n][2] = h->schur_mode; ++n;
+    }
+    cudaEvent_t ev[2];
+    CKH(cudaEventCreate(&ev[0]));
+    CKH(cudaEventCreate(&ev[1]));
+    double ms[8];
+    int best = 0, rc = HDG_OK;
+    for (int c = 0; c < n && rc == HDG_OK; ++c) {
+        h->elim_nb = cand[c][0];
+        h->elim_minb = cand[c][1];
+        h->schur_mode = cand[c][2];
+        if ((rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr))) break;   // warm-up
+        cudaEventRecord(ev[0], h->stream);
+        for (int r = 0; r < reps && rc == HDG_OK; ++r) rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr);
+        cudaEventRecord(ev[1], h->stream);
+        float t = 0.f;
+        if (cudaEventSynchronize(ev[1]) != cudaSuccess || cudaEventElapsedTime(&t, ev[0], ev[1]) != cudaSuccess) {
+            rc = fail(h, HDG_ECUDA, "event timing failed in autotune");
+            break;
+        }
+        ms[c] = t / reps;
+        if (ms[c] < ms[best]) best = c;
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (rc) return rc;
+    h->elim_nb = cand[best][0];
+    h->elim_minb = cand[best][1];
+    h->schur_mode = cand[best][2];
+    if (out) {
+        out->elim_nb = h->elim_nb; out->elim_minb = h->elim_minb; out->schur_mode = h->schur_mode;
+        out->n_cand = n;
+        for (int c = 0; c < 8; ++c) {
+            for (int k = 0; k < 3; ++k) out->cand[c][k] = c < n ? cand[c][k] : 0;
+            out->ms[c] = c < n ? ms[c] : 0.0;
+        }
+    }
+    return HDG_OK;
+}
+
+int hdg_set_tuning(hdg_handle h, const hdg_tune* t) {
+    if (!h || !t) return fail(h, HDG_EINVAL, "NULL argument");
+    if ((t->elim_nb != 8 && t->elim_nb != 16) || (t->elim_minb != 1 && t->elim_minb != 2) ||
+        t->schur_mode < 0 || t->schur_mode > 2)
+        return fail(h, HDG_EINVAL, "elim_nb 8 or 16, elim_minb 1 or 2, schur_mode 0..2");
+    if (h->precision == HDG_PREC_MIXED && h->prec_req != HDG_PREC_MIXED && t->schur_mode != h->schur_mode)
+        return fail(h, HDG_EINVAL, "the Schur precision was fixed by hdg_set_params");
+    h->elim_nb = t->elim_nb;
+    h->elim_minb = t->elim_minb;
+    if (h->precision == HDG_PREC_MIXED) h->schur_mode = t->schur_mode;
     return HDG_OK;
 }
 

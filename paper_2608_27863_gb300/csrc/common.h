@@ -59,6 +59,8 @@ struct Skeleton {
     std::vector<int32_t> frank;                     // [E][nf]: rank of the element on the face
 };
 int build_skeleton(const hdg_mesh& mesh, int p, Skeleton& s, std::string& err);
+int build_vertex_map(const hdg_mesh& mesh, std::vector<int32_t>& ev, std::vector<int32_t>& vrow,
+                     std::vector<int32_t>& vcol, std::string& err);
 
 // Physical and numerical parameters seen by the kernels.
 struct Phys {
@@ -88,6 +90,7 @@ struct hdg_ctx {
     bool device = false;
     hdg::Phys phys{};
     int precision = HDG_PREC_FP64;
+    int prec_req = HDG_PREC_FP64;          // precision as requested through hdg_set_params
     cudaStream_t stream = nullptr;
     std::string err;
 
@@ -147,6 +150,14 @@ struct hdg_ctx {
     double* d_h = nullptr;                 // [restart + 2]
     int gm_cap = 0;
     double* d_nw = nullptr;                // Newton work: dU, dQ, dUH, g
+    // artificial-viscosity smoothing: master vertex of every corner and vertex -> element lists
+    std::vector<int32_t> av_ev, av_vrow, av_vcol;
+    int32_t* d_avev = nullptr;             // [E][2^d]
+    int32_t* d_avvrow = nullptr;           // [V + 1]
+    int32_t* d_avvcol = nullptr;           // [E * 2^d]
+    double* d_avv = nullptr;               // [V] vertex field
+    double* d_ave = nullptr;               // [E] elemental field
+    double* d_diag = nullptr;              // [E][4] diagnostic partial integrals, then [4] totals
     // reduced-basis initial guess: window of accepted trace corrections and their products
     double* d_rbW = nullptr;               // [rb_max][N]
     double* d_rbZ = nullptr;               // [rb_max][N]
@@ -178,6 +189,7 @@ struct hdg_ctx {
     int64_t chunk = 0;
     bool have_system = false;
     int elim_minb = 2;                     // k_elim variant: resident CTAs per SM the kernel is built for
+    int elim_nb = 16;                      // k_elim variant: panel width (16 or 8)
 
     // instrumentation: event pairs around kernel launches
     bool prof = false;
@@ -204,6 +216,9 @@ template <int D, int P> int run_recover(hdg_ctx* h, const double* dUH, double* d
 template <int D, int P> int run_residual(hdg_ctx* h, const LinArgs& a, double* Rq, double* Ru, double* Ruh);
 template <int D, int P> int run_asm_setup(hdg_ctx* h);
 template <int D, int P> int run_asm_apply(hdg_ctx* h, const double* x, double* y);
+template <int D, int P> int run_av_field(hdg_ctx* h, const double* U, const double* Q, double c_av, double h_m,
+                                         double s_max, double* nu);
+template <int D, int P> int run_diagnostics(hdg_ctx* h, const double* U, const double* Q);
 template <int D, int P> int run_lift(hdg_ctx* h, const double* U, const double* UH, double* Q);
 template <int D, int P> int run_linearize_mixed(hdg_ctx* h, const LinArgs& a);
 template <int D, int P> int run_bj_setup(hdg_ctx* h);

@@ -172,4 +172,32 @@ int build_skeleton(const hdg_mesh& mesh, int p, Skeleton& s, std::string& err) {
     return HDG_OK;
 }
 
+// Master vertices of every element corner, renumbered compactly in order of
+// first appearance, and the vertex -> element lists (ascending element ids):
+// the vertex averaging of the artificial-viscosity smoothing.
+int build_vertex_map(const hdg_mesh& mesh, std::vector<int32_t>& ev, std::vector<int32_t>& vrow,
+                     std::vector<int32_t>& vcol, std::string& err) {
+    const int nv = 1 << mesh.dim;
+    const int64_t E = mesh.n_elem;
+    std::vector<int32_t> id((size_t)mesh.n_vert, -1);
+    ev.assign((size_t)E * nv, 0);
+    int32_t nmaster = 0;
+    for (int64_t e = 0; e < E; ++e)
+        for (int c = 0; c < nv; ++c) {
+            bool ok = true;
+            const int64_t v = master_of(mesh, mesh.elem_vert[(size_t)e * nv + c], ok);
+            if (!ok) { err = "periodic_map out of range or cyclic"; return HDG_EINVAL; }
+            if (id[v] < 0) id[v] = nmaster++;
+            ev[(size_t)e * nv + c] = id[v];
+        }
+    vrow.assign((size_t)nmaster + 1, 0);
+    for (int64_t i = 0; i < E * nv; ++i) ++vrow[ev[i] + 1];
+    for (int32_t v = 0; v < nmaster; ++v) vrow[v + 1] += vrow[v];
+    vcol.assign((size_t)E * nv, 0);
+    std::vector<int32_t> fill(vrow.begin(), vrow.end() - 1);
+    for (int64_t e = 0; e < E; ++e)
+        for (int c = 0; c < nv; ++c) vcol[fill[ev[(size_t)e * nv + c]]++] = (int32_t)e;
+    return HDG_OK;
+}
+
 }  // namespace hdg

@@ -1,4 +1,4 @@
-// Kernel instantiations for one group of (d, p) configurations.
+// Kernel instantiations for one (d, p) configuration.
 #include "solve.cuh"
 namespace hdg {
 HDG_INSTANTIATE(3, 1)

@@ -92,7 +92,7 @@ constexpr int point_smem_doubles() {
 template <class C, int NTH, class TJ>
 __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
     constexpr int D = C::D, M = C::M, NP = C::NP, NQ = C::NQ, NF = C::NF, NFP = C::NFP, NFQ = C::NFQ;
-    constexpr int NU = C::NU, NQV = C::NQV, NT = C::NT, LD = C::LD, NC = C::NC, NCOEF = C::NCOEF;
+    constexpr int NU = C::NU, NQV = C::NQV, NT = C::NT, NCOEF = C::NCOEF;
     constexpr int GEO = Geo<D>::N;
     const int tid = threadIdx.x;
     const int64_t el = blockIdx.x, e = A.e0 + el;
@@ -377,7 +377,7 @@ struct BlkShape {
 template <class C, int TY, int TX, int KC, class TA, class TL>
 __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
     constexpr int D = C::D, M = C::M, NP = C::NP, NQ = C::NQ, NF = C::NF, NFP = C::NFP, NFQ = C::NFQ;
-    constexpr int NU = C::NU, NT = C::NT, LD = C::LD, NCOEF = C::NCOEF;
+    constexpr int NCOEF = C::NCOEF;
     using S = BlkShape<C, TY, TX, KC>;
     constexpr int NCB = S::NCB, TM = S::TM, TN = S::TN, NPP = S::NPP, NCBP = S::NCBP;
     constexpr int K = D * NQ, NTH = TY * TX;
@@ -918,14 +918,17 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
     using BC = BlkCfg<C>;
     using BS_ = BlkShape<C, BC::TY, BC::TX, BC::KC>;
     auto kblk = k_blocks<C, BC::TY, BC::TX, BC::KC, double, double>;
-    constexpr int PT = 128, NB = 16;
+    constexpr int PT = 128;
     const size_t sm_point = sizeof(double) * point_smem_doubles<C>();
     const size_t sm_blk = sizeof(double) * BS_::smem;
-    const size_t sm_elim = sizeof(double) * elim_smem_doubles<C, NB>();
+    const size_t sm_elim16 = sizeof(double) * elim_smem_doubles<C, 16>();
+    const size_t sm_elim8 = sizeof(double) * elim_smem_doubles<C, 8>();
     HDG_CK(cudaFuncSetAttribute(k_point<C, PT, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_point));
     HDG_CK(cudaFuncSetAttribute(kblk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
-    HDG_CK(cudaFuncSetAttribute(k_elim<C, NB, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
-    HDG_CK(cudaFuncSetAttribute(k_elim<C, NB, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
+    HDG_CK(cudaFuncSetAttribute(k_elim<C, 16, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim16));
+    HDG_CK(cudaFuncSetAttribute(k_elim<C, 16, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim16));
+    HDG_CK(cudaFuncSetAttribute(k_elim<C, 8, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim8));
+    HDG_CK(cudaFuncSetAttribute(k_elim<C, 8, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim8));
     cudaStream_t st = h->stream;
     HDG_CK(cudaMemsetAsync(h->d_vals, 0, sizeof(double) * h->nnzb * C::BS * C::BS, st));
     HDG_CK(cudaMemsetAsync(h->d_g, 0, sizeof(double) * h->F * C::BS, st));
@@ -952,10 +955,18 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
         kblk<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
         prof_end(h);
         prof_begin(h, HDG_K_ELIM);
-        if (h->elim_minb == 1)
-            k_elim<C, NB, 256, 1><<<(unsigned)ne, 256, sm_elim, st>>>(h->d_top, h->d_bot, e0, h->d_status);
-        else
-            k_elim<C, NB, 256, 2><<<(unsigned)ne, 256, sm_elim, st>>>(h->d_top, h->d_bot, e0, h->d_status);
+        // variant chosen by the autotuner: panel width 16 or 8, built for 1 or 2 resident CTAs per SM
+        if (h->elim_nb == 8) {
+            if (h->elim_minb == 1)
+                k_elim<C, 8, 256, 1><<<(unsigned)ne, 256, sm_elim8, st>>>(h->d_top, h->d_bot, e0, h->d_status);
+            else
+                k_elim<C, 8, 256, 2><<<(unsigned)ne, 256, sm_elim8, st>>>(h->d_top, h->d_bot, e0, h->d_status);
+        } else {
+            if (h->elim_minb == 1)
+                k_elim<C, 16, 256, 1><<<(unsigned)ne, 256, sm_elim16, st>>>(h->d_top, h->d_bot, e0, h->d_status);
+            else
+                k_elim<C, 16, 256, 2><<<(unsigned)ne, 256, sm_elim16, st>>>(h->d_top, h->d_bot, e0, h->d_status);
+        }
         prof_end(h);
         for (int pass = 0; pass < 2; ++pass) {
             prof_begin(h, HDG_K_ASSEMBLE);

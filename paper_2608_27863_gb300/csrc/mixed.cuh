@@ -97,7 +97,7 @@ constexpr int elim_mixed_smem_bytes() {
 
 template <class C, int NB, int NTH>
 __global__ void __launch_bounds__(NTH, 2) k_elim_mixed(Regions<float> R, int64_t e0, int32_t* status) {
-    constexpr int NU = C::NU, NT = C::NT, NR = C::NR;
+    constexpr int NU = C::NU, NT = C::NT;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t el = blockIdx.x, e = e0 + el;
     double* A11 = R.a11 + e * R.a11_es;

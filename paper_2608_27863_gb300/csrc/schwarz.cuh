@@ -9,9 +9,9 @@
 // panels in shared memory, LAPACK-style full-row interchanges).  The factors
 // are kept in the system's storage type: FP64 for the FP64 form, FP32 for the
 // mixed form, where the preconditioner only needs to be a good approximation.
-// Apply: one CTA per element solves its patch in FP64 arithmetic (blocked
+// Apply: one CTA per element solves its patch in the storage precision (blocked
 // triangular solves with the 32 x 32 diagonal blocks pre-inverted at setup,
-// warp-per-row products for the off-diagonal blocks), writes z_r, and a
+// one dot product per row and thread for the off-diagonal blocks), writes z_r, and a
 // face kernel sums the (at most two) patch corrections of each face in a
 // fixed order, so the result is bitwise reproducible.
 #pragma once
@@ -41,7 +41,7 @@ __global__ void __launch_bounds__(NTH) k_asm_factor(const T* __restrict__ vals, 
     T* pan = reinterpret_cast<T*>(smraw);   // [N][NB], row index relative to k0
     T* ust = pan + N * NB;                  // [NB][64]
     __shared__ int piv[NB];
-    __shared__ double rv[NTH / 32];
+    __shared__ T rv[NTH / 32];
     __shared__ int ri[NTH / 32];
     __shared__ int sflag;
     if (tid == 0) sflag = 0;
@@ -69,22 +69,22 @@ __global__ void __launch_bounds__(NTH) k_asm_factor(const T* __restrict__ vals, 
         __syncthreads();
 #pragma unroll 1
         for (int j = 0; j < kb; ++j) {
-            double bv = -1.0;
+            T bv = T(-1);                      // pivot search in the storage type (no FP64 work for FP32)
             int bi = INT_MAX;
 #pragma unroll 1
             for (int rr = j + tid; rr < nrows; rr += NTH) {
-                const double v = fabs((double)pan[rr * NB + j]);
+                const T v = fabs(pan[rr * NB + j]);
                 if (v > bv) { bv = v; bi = rr; }
             }
             for (int off = 16; off > 0; off >>= 1) {
-                const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+                const T ov = __shfl_down_sync(0xffffffffu, bv, off);
                 const int oi = __shfl_down_sync(0xffffffffu, bi, off);
                 if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
             }
             if (lane == 0) { rv[warp] = bv; ri[warp] = bi; }
             __syncthreads();
             if (tid == 0) {
-                double b2 = rv[0];
+                T b2 = rv[0];
                 int i2 = ri[0];
                 for (int w = 1; w < NTH / 32; ++w)
                     if (rv[w] > b2 || (rv[w] == b2 && ri[w] < i2)) { b2 = rv[w]; i2 = ri[w]; }
@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(NTH) k_asm_factor(const T* __restrict__ vals, 
                 }
             __syncthreads();
             T pv = pan[j * NB + j];
-            if (pv == T(0) || !isfinite((double)pv)) {
+            if (pv == T(0) || !isfinite(pv)) {
                 if (tid == 0) sflag |= (pv == T(0)) ? 1 : 2;
                 pv = T(1);
             }
@@ -216,7 +216,39 @@ __global__ void __launch_bounds__(NTH) k_asm_prep(const T* __restrict__ lu, cons
 
 // z_r = S_r^{-1} R_r x for every element r: permuted gather, then blocked
 // forward and backward substitution (diagonal blocks by their stored
-// inverses, off-diagonal blocks as warp-per-row products), FP64 arithmetic.
+// inverses, off-diagonal blocks as one dot product per row and thread).  The
+// arithmetic runs in the storage type T: FP64 for the FP64 system; FP32 for
+// the mixed one, where FP64 work would bound the kernel (GB300 has 1/64 of
+// the FP32 rate in FP64) and the FP32 factors fix the accuracy anyway.
+template <class T, int NB>
+__device__ __forceinline__ T row_dot(const T* __restrict__ a, const T* __restrict__ x, int nb) {
+    T s = T(0);
+    if (nb == 32) {
+        if (sizeof(T) == 4) {
+            const float4* a4 = reinterpret_cast<const float4*>(a);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const float4 v = __ldg(a4 + j);
+                s = fma((T)v.x, x[4 * j], s);
+                s = fma((T)v.y, x[4 * j + 1], s);
+                s = fma((T)v.z, x[4 * j + 2], s);
+                s = fma((T)v.w, x[4 * j + 3], s);
+            }
+        } else {
+            const double2* a2 = reinterpret_cast<const double2*>(a);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const double2 v = __ldg(a2 + j);
+                s = fma((T)v.x, x[2 * j], s);
+                s = fma((T)v.y, x[2 * j + 1], s);
+            }
+        }
+    } else {
+        for (int j = 0; j < nb; ++j) s = fma(a[j], x[j], s);
+    }
+    return s;
+}
+
 template <class C, class T, int NTH>
 __global__ void __launch_bounds__(NTH) k_asm_solve(const T* __restrict__ lu, const int32_t* __restrict__ perm,
                                                    const T* __restrict__ dinv, const int32_t* __restrict__ e2f,
@@ -224,54 +256,38 @@ __global__ void __launch_bounds__(NTH) k_asm_solve(const T* __restrict__ lu, con
     constexpr int N = AsmShape<C>::N, LDA = AsmShape<C>::LDA, NF = C::NF, BS = C::BS;
     constexpr int NBLK = AsmBlk<C>::NBLK, NW = NTH / 32;
     static_assert(NTH == 256, "diagonal-block product assumes 8 warps");
-    __shared__ double xs[N];
-    __shared__ double red[NW][32];
+    __shared__ __align__(16) T xs[N];
+    __shared__ T red[NW][32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t e = blockIdx.x;
     const T* A = lu + e * (size_t)N * LDA;
     for (int i = tid; i < N; i += NTH) {
         const int j = perm[e * N + i], f = j / BS;
-        xs[i] = x[(size_t)e2f[e * NF + f] * BS + (j - f * BS)];
+        xs[i] = (T)x[(size_t)e2f[e * NF + f] * BS + (j - f * BS)];
     }
     __syncthreads();
     // xs[k0 .. k0+32) <- inv(D_kk) xs[k0 .. k0+32): warp w sums columns 4w .. 4w+3
     auto diag_product = [&](const T* Dt, int k0, int nb) {
-        double s = 0.0;
+        T s = T(0);
         if (lane < nb) {
 #pragma unroll
             for (int c = 4 * warp; c < 4 * warp + 4; ++c)
-                if (c < nb) s = fma((double)Dt[c * 32 + lane], xs[k0 + c], s);
+                if (c < nb) s = fma(Dt[c * 32 + lane], xs[k0 + c], s);
         }
         red[warp][lane] = s;
         __syncthreads();
         if (tid < nb) {
-            double t = 0.0;
+            T t = T(0);
 #pragma unroll
             for (int w = 0; w < NW; ++w) t += red[w][tid];
             xs[k0 + tid] = t;
         }
         __syncthreads();
     };
-    // xs[r] -= sum_j A[r][k0 + j] xs[k0 + j] for r in [r0, r1), one warp per row
+    // xs[r] -= A[r][k0 .. k0+nb) . xs[k0 .. k0+nb) for r in [r0, r1)
     auto offdiag_update = [&](int k0, int nb, int r0, int r1) {
-        const double xv = lane < nb ? xs[k0 + lane] : 0.0;
 #pragma unroll 1
-        for (int r = r0 + warp; r < r1; r += 4 * NW) {
-            double s[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int rr = r + u * NW;
-                s[u] = (rr < r1 && lane < nb) ? (double)A[(size_t)rr * LDA + k0 + lane] * xv : 0.0;
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                for (int off = 16; off > 0; off >>= 1) s[u] += __shfl_down_sync(0xffffffffu, s[u], off);
-            if (lane == 0) {
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (r + u * NW < r1) xs[r + u * NW] -= s[u];
-            }
-        }
+        for (int r = r0 + tid; r < r1; r += NTH) xs[r] -= row_dot<T, 32>(A + (size_t)r * LDA + k0, xs + k0, nb);
         __syncthreads();
     };
     const T* D = dinv + (size_t)e * NBLK * 2048;
@@ -287,7 +303,7 @@ __global__ void __launch_bounds__(NTH) k_asm_solve(const T* __restrict__ lu, con
         diag_product(D + (size_t)kb * 2048 + 1024, k0, nb);
         if (k0 > 0) offdiag_update(k0, nb, 0, k0);
     }
-    for (int i = tid; i < N; i += NTH) z[e * (size_t)N + i] = xs[i];
+    for (int i = tid; i < N; i += NTH) z[e * (size_t)N + i] = (double)xs[i];
 }
 
 // y_F = sum over the (one or two) elements of face F of their patch corrections, side 0 first

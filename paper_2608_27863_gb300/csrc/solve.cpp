@@ -299,6 +299,46 @@ int hdg_schwarz_apply(hdg_handle h, const double* x, double* y) {
     return rc;
 }
 
+int hdg_av_field(hdg_handle h, const double* U, const double* Q, double c_av, double h_m, double s_max, double* nu) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
+    if (!U || !Q || !nu) return fail(h, HDG_EINVAL, "U, Q and nu are required");
+    if (!(c_av >= 0.0) || !(h_m > 0.0) || !(s_max >= 0.0)) return fail(h, HDG_EINVAL, "c_av >= 0, h_m > 0, s_max >= 0 required");
+    int rc;
+    if (!h->d_avev) {
+        const int64_t V = (int64_t)h->av_vrow.size() - 1;
+        if ((rc = alloc(h, (void**)&h->d_avev, sizeof(int32_t) * h->av_ev.size()))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_avvrow, sizeof(int32_t) * h->av_vrow.size()))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_avvcol, sizeof(int32_t) * h->av_vcol.size()))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_avv, sizeof(double) * std::max<int64_t>(V, 1)))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_ave, sizeof(double) * h->E))) return rc;
+        CKS(cudaMemcpy(h->d_avev, h->av_ev.data(), sizeof(int32_t) * h->av_ev.size(), cudaMemcpyHostToDevice));
+        CKS(cudaMemcpy(h->d_avvrow, h->av_vrow.data(), sizeof(int32_t) * h->av_vrow.size(), cudaMemcpyHostToDevice));
+        CKS(cudaMemcpy(h->d_avvcol, h->av_vcol.data(), sizeof(int32_t) * h->av_vcol.size(), cudaMemcpyHostToDevice));
+    }
+    DISPATCH_S(run_av_field, h, U, Q, c_av, h_m, s_max, nu);
+    return rc;
+}
+
+int hdg_tgv_diagnostics(hdg_handle h, const double* U, const double* Q, double* out) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
+    if (!U || !Q || !out) return fail(h, HDG_EINVAL, "U, Q and out are required");
+    int rc;
+    if (!h->d_diag && (rc = alloc(h, (void**)&h->d_diag, sizeof(double) * (4 * h->E + 4)))) return rc;
+    DISPATCH_S(run_diagnostics, h, U, Q);
+    if (rc) return rc;
+    double t[4];
+    CKS(cudaMemcpyAsync(t, h->d_diag + 4 * h->E, sizeof(t), cudaMemcpyDeviceToHost, h->stream));
+    CKS(cudaStreamSynchronize(h->stream));
+    const double vol = t[3], re = h->phys.re;
+    out[0] = t[0] / (2.0 * vol);
+    out[1] = t[1] / (re * vol);
+    out[2] = 4.0 * t[2] / (3.0 * re * vol);
+    out[3] = vol;
+    return HDG_OK;
+}
+
 int hdg_rb_setup(hdg_handle h, int nb_max) {
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");

@@ -7,6 +7,7 @@
 
 #include "mixed.cuh"
 #include "schwarz.cuh"
+#include "av.cuh"
 
 namespace hdg {
 
@@ -421,6 +422,8 @@ int run_bj_apply(hdg_ctx* h, const double* x, double* y) {
     template int run_residual<D, P>(hdg_ctx*, const LinArgs&, double*, double*, double*); \
     template int run_lift<D, P>(hdg_ctx*, const double*, const double*, double*);         \
     template int run_asm_setup<D, P>(hdg_ctx*);                                           \
+    template int run_av_field<D, P>(hdg_ctx*, const double*, const double*, double, double, double, double*); \
+    template int run_diagnostics<D, P>(hdg_ctx*, const double*, const double*);           \
     template int run_asm_apply<D, P>(hdg_ctx*, const double*, double*);                   \
     template int run_bj_setup<D, P>(hdg_ctx*);                                            \
     template int run_bj_apply<D, P>(hdg_ctx*, const double*, double*);

@@ -241,6 +241,41 @@ __global__ void k_rb_advance(int* head, int nb) {
     }
 }
 
+__global__ void k_av_vertex(const double* __restrict__ fe, const int32_t* __restrict__ vrow,
+                            const int32_t* __restrict__ vcol, double* __restrict__ fv, int64_t V) {
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    double s = 0.0;
+    for (int32_t k = vrow[v]; k < vrow[v + 1]; ++k) s += fe[vcol[k]];
+    const int32_t n = vrow[v + 1] - vrow[v];
+    fv[v] = n > 0 ? s / n : 0.0;
+}
+
+__global__ void k_av_emean(const double* __restrict__ fv, const int32_t* __restrict__ ev, int nc,
+                           double* __restrict__ fe, int64_t E) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    double s = 0.0;
+    for (int c = 0; c < nc; ++c) s += fv[ev[e * nc + c]];
+    fe[e] = s / nc;
+}
+
+__global__ void k_diag_sum(const double* __restrict__ part, int64_t E, double* __restrict__ out) {
+    __shared__ double red[4][256];
+    const int t = threadIdx.x;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int64_t e = t; e < E; e += blockDim.x)
+        for (int k = 0; k < 4; ++k) a[k] += part[e * 4 + k];
+    for (int k = 0; k < 4; ++k) red[k][t] = a[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (t < w)
+            for (int k = 0; k < 4; ++k) red[k][t] += red[k][t + w];
+        __syncthreads();
+    }
+    if (t < 4) out[t] = red[t][0];
+}
+
 __global__ void k_to_f32(const double* x, float* y, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         y[i] = (float)x[i];

@@ -37,7 +37,8 @@ EXPORTS = [
     "hdg_profile_read", "hdg_linearize_condense_static", "hdg_residual", "hdg_update_state",
     "hdg_blockjacobi_setup", "hdg_blockjacobi_apply", "hdg_gmres", "hdg_newton", "hdg_set_bc_state",
     "hdg_newton_fixed", "hdg_dirk_step", "hdg_lift_gradient", "hdg_set_preconditioner", "hdg_schwarz_setup",
-    "hdg_schwarz_apply", "hdg_rb_setup", "hdg_rb_push", "hdg_rb_guess",
+    "hdg_schwarz_apply", "hdg_rb_setup", "hdg_rb_push", "hdg_rb_guess", "hdg_av_field", "hdg_tgv_diagnostics",
+    "hdg_autotune", "hdg_set_tuning",
 ]
 KERNEL_CLASSES = ["point", "blocks", "elim", "assemble", "matvec", "recover", "schur"]
 
@@ -107,6 +108,10 @@ def lib():
         "hdg_schwarz_setup": [vp],
         "hdg_schwarz_apply": [vp, vp, vp],
         "hdg_rb_setup": [vp, i32],
+        "hdg_autotune": [vp, vp, vp, vp, vp, vp, dbl, dbl, i32, vp],
+        "hdg_set_tuning": [vp, vp],
+        "hdg_av_field": [vp, vp, vp, dbl, dbl, dbl, vp],
+        "hdg_tgv_diagnostics": [vp, vp, vp, vp],
         "hdg_rb_push": [vp, vp],
         "hdg_rb_guess": [vp, vp, vp],
         "hdg_newton_fixed": [vp, vp, vp, vp, vp, vp, dbl, dbl, i32, i32, i32, vp],
@@ -358,3 +363,35 @@ def hdg_rb_push(h, w):
 
 def hdg_rb_guess(h, g, x0):
     _check(h, lib().hdg_rb_guess(h, _ptr(g), _ptr(x0)))
+
+
+def hdg_av_field(h, U, Q, nu, c_av, h_m, s_max=1.0):
+    """nu <- smoothed artificial viscosity of the state (U, Q) (device arrays)."""
+    _check(h, lib().hdg_av_field(h, _ptr(U), _ptr(Q), float(c_av), float(h_m), float(s_max), _ptr(nu)))
+
+
+def hdg_tgv_diagnostics(h, U, Q):
+    """(E_k, eps_S, eps_D, |Omega|) of the state (U, Q)."""
+    out = np.zeros(4, np.float64)
+    _check(h, lib().hdg_tgv_diagnostics(h, _ptr(U), _ptr(Q), out.ctypes.data))
+    return out
+
+
+class hdg_tune(ctypes.Structure):
+    _fields_ = [("elim_nb", ctypes.c_int), ("elim_minb", ctypes.c_int), ("schur_mode", ctypes.c_int),
+                ("n_cand", ctypes.c_int), ("cand", (ctypes.c_int * 3) * 8), ("ms", ctypes.c_double * 8)]
+
+
+def hdg_autotune(h, U, Q, UH, Ustar, nu, dt, a_ii, reps=2):
+    """Time the equivalent kernel variants on these inputs and keep the fastest; returns a dict."""
+    t = hdg_tune()
+    _check(h, lib().hdg_autotune(h, _ptr(U), _ptr(Q), _ptr(UH), _ptr(Ustar), _ptr(nu), float(dt), float(a_ii),
+                                 int(reps), ctypes.byref(t)))
+    return {"elim_nb": t.elim_nb, "elim_minb": t.elim_minb, "schur_mode": t.schur_mode,
+            "candidates": [(tuple(t.cand[i]), t.ms[i]) for i in range(t.n_cand)]}
+
+
+def hdg_set_tuning(h, elim_nb=16, elim_minb=2, schur_mode=0):
+    t = hdg_tune()
+    t.elim_nb, t.elim_minb, t.schur_mode = elim_nb, elim_minb, schur_mode
+    _check(h, lib().hdg_set_tuning(h, ctypes.byref(t)))

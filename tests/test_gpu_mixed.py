@@ -128,3 +128,19 @@ def test_tensor_core_newton_3xtf32():
     assert np.linalg.norm(x - y) <= 1e-10 * np.linalg.norm(x)
     a.close()
     b.close()
+
+
+def test_autotune_mixed_picks_fp32_accurate_schur():
+    from paper_2608_27863_gb300 import hdg as H
+    P = synth.config2(n=3)
+    run = GpuRun(P)
+    H.hdg_set_params(run.h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s,
+                     precision=H.HDG_PREC_MIXED)
+    rep = H.hdg_autotune(run.h, run.U, run.Q, run.UH, run.Ustar, run.nu, P.dt, P.a_ii, reps=1)
+    assert {c[2] for c, _ in rep["candidates"]} == {0, 2} and rep["schur_mode"] in (0, 2)
+    # an explicit TF32 request is not overridden
+    H.hdg_set_params(run.h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s,
+                     precision=H.HDG_PREC_MIXED_TF32)
+    rep = H.hdg_autotune(run.h, run.U, run.Q, run.UH, run.Ustar, run.nu, P.dt, P.a_ii, reps=1)
+    assert len(rep["candidates"]) == 1 and rep["schur_mode"] == 1
+    run.close()

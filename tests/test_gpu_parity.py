@@ -184,3 +184,27 @@ def test_lift_gradient_matches_oracle(make):
     q = Q.cpu().numpy()
     assert np.linalg.norm(q - oq) <= TOL * np.linalg.norm(oq)
     run.close()
+
+
+def test_autotuned_variants_keep_parity():
+    """Every FP64 elimination variant the autotuner may pick meets the parity bar."""
+    from paper_2608_27863_gb300 import hdg as H
+    P = synth.config2(n=3)
+    run = GpuRun(P)
+    rep = H.hdg_autotune(run.h, run.U, run.Q, run.UH, run.Ustar, run.nu, P.dt, P.a_ii, reps=1)
+    cands = rep["candidates"]
+    assert len(cands) == 4 and all(ms > 0 for _, ms in cands)
+    assert min(ms for _, ms in cands) == [ms for c, ms in cands if c[:2] == (rep["elim_nb"], rep["elim_minb"])][0]
+    run.close()
+    for (nb, minb, _), _ms in cands:
+        h = create(P)
+        H.hdg_set_tuning(h, elim_nb=nb, elim_minb=minb)
+        compare_handle = GpuRun(P, h)
+        compare_handle.linearize()
+        vals = compare_handle.blocks()
+        pb = Problem(P)
+        rows = [0, 40, 77]
+        blocks = [b for F in rows for b in range(pb.conn.rowptr[F], pb.conn.rowptr[F + 1])]
+        orc, _ = pb.assemble(blocks=blocks)
+        assert max(block_rel_errors(vals, orc).values()) < TOL, (nb, minb)
+        compare_handle.close()
