@@ -80,8 +80,14 @@ typedef struct {
     const double* vert_xyz;       /* [n_vert][dim] */
     const int64_t* elem_vert;     /* [n_elem][2^dim] */
     const int64_t* periodic_map;  /* [n_vert] master vertex of each vertex, or NULL */
-    const int32_t* bnd_tag;       /* [n_elem][2 dim] 0 = interior / periodic, 1 = Dirichlet / far-field
-                                     (bhat = uhat - u_b, state set by hdg_set_bc_state), or NULL */
+    const int32_t* bnd_tag;       /* [n_elem][2 dim] per local face: 0 interior / periodic; on faces with
+                                     one element the boundary kind (Sec. 2.2; the forms are readings):
+                                     1 far-field / supersonic inflow, bhat = uhat - u_b;
+                                     2 supersonic outflow, bhat = uhat - u (extrapolated);
+                                     3 isothermal no-slip wall, bhat = [fhat_rho; uhat_rhov;
+                                       uhat_rhoE - uhat_rho c_v T_w];
+                                     4 adiabatic no-slip wall, bhat = [fhat_rho; uhat_rhov; fhat_rhoE].
+                                     NULL for a fully periodic mesh. */
 } hdg_mesh;
 
 /* Solver parameters (hdg_set_params).  tau: constant scalar stabilization of
@@ -122,10 +128,16 @@ const char* hdg_last_error(hdg_handle h);
 
 int hdg_set_params(hdg_handle h, const hdg_params* prm);
 int hdg_set_stream(hdg_handle h, void* cuda_stream);
-/* State u_b [m] (host) of the tag-1 boundary faces: their trace equation is
- * <uhat - u_b, mu> = 0 (the prescribed-state boundary of Sec. 2.1, the bhat of
- * eq. hdg-trace); required before linearizing a mesh with tag-1 faces. */
+/* Boundary data (host): tag 1, the state u_b [m] of the far-field / inflow
+ * faces (trace equation <uhat - u_b, mu> = 0); tag 3, ub[0] = the wall
+ * temperature T~_w (T~ = gamma M^2 p / rho, so T~_inf = 1).  Required before
+ * linearizing a mesh with faces of that tag. */
 int hdg_set_bc_state(hdg_handle h, int tag, const double* ub);
+/* Nodal tag-1 data: ubf [F][m][Nfp] (device, canonical face-node order; only
+ * the rows of tag-1 faces are read), copied into the handle on the stream;
+ * it replaces the constant state (e.g. an inflow profile).  NULL returns to
+ * the constant state. */
+int hdg_set_bc_field(hdg_handle h, const double* ubf);
 int hdg_query_sizes(hdg_handle h, hdg_sizes* out);
 
 /* Host copies of the integer skeleton data (any pointer may be NULL):

@@ -9,7 +9,11 @@ Oracle (test infrastructure only).  Follows Sec. 2.2-2.5:
     R_u[a,i]   = (1/a_ii) (M (U - U*))_{a,i}
                  + dt [ -(F^c - F^v)_{a,k}, d_k phi_i)_K + <fhat_a, phi_i>_dK ]
     R_uhat^K[f,a,l] = <fhat_a, mu_l>_F          (interior / periodic faces)
-                    = <uhat_a - u_b,a, mu_l>_F    (tag-1 Dirichlet faces, a reading)
+                    = <bhat_a, mu_l>_F            (boundary faces, readings of Sec. 2.2):
+      tag 1 far-field / supersonic inflow  bhat = uhat - u_b
+      tag 2 supersonic outflow             bhat = uhat - u
+      tag 3 isothermal no-slip wall        bhat = [fhat_rho; uhat_rhov; uhat_rhoE - uhat_rho c_v T_w]
+      tag 4 adiabatic no-slip wall         bhat = [fhat_rho; uhat_rhov; fhat_rhoE]
 
   with fhat = (F^c(uhat) - F^v(uhat, q)) . n + tau (u - uhat) (eq. num-flux-hdg)
   and a constant scalar tau (a reading of "face-based stabilization").
@@ -102,6 +106,9 @@ class Problem:
         self.nu = None if prob.nu is None else np.asarray(prob.nu, float)
         self.ubc = None if prob.ubc is None else np.asarray(prob.ubc, float)
         self.bnd = np.asarray(mesh.bnd_tag)
+        # wall internal energy c_v T_w = T~_w / (gamma (gamma - 1) M^2) (T~ = gamma M^2 p / rho)
+        tw = getattr(prob, "twall", 1.0)
+        self.e_wall = tw / (prob.gamma * (prob.gamma - 1.0) * prob.mach ** 2)
         self.X = mesh.vert_xyz[mesh.elem_vert]
         self._geom = {}
         r = self.ref
@@ -109,6 +116,14 @@ class Problem:
         self.nu_dofs = r.m * r.Np
         self.n_int = self.nq_dofs + self.nu_dofs
         self.t = r.nf * r.m * r.Nfp
+
+    def boundary_state(self, e: int, f: int):
+        """u_b at the face quadrature points of a tag-1 face: a constant state
+        [m], or nodal data [F][m][Nfp] in the face's canonical node order."""
+        if self.ubc.ndim == 1:
+            return self.ubc
+        F = self.conn.e2f[e, f]
+        return (self.ubc[F][:, self.conn.perm[e, f]] @ self.ref.mu.T).T
 
     def geom(self, e: int) -> Geometry:
         if e not in self._geom:
@@ -151,12 +166,22 @@ class Problem:
             Rq = Rq - np.einsum("s,...sa,sk,sj->...kaj", G.omega[f], uh_s, G.n[f], r.phif[f], optimize=True)
             tag = int(self.bnd[e, f])
             if tag == 0:
-                Rh[..., f, :, :] = np.einsum("s,...sa,sl->...al", G.omega[f], fhat, r.mu, optimize=True)
-            elif tag == 1:
-                bh = uh_s - self.ubc
-                Rh[..., f, :, :] = np.einsum("s,...sa,sl->...al", G.omega[f], bh, r.mu, optimize=True)
+                bh = fhat
+            elif tag == 1:                       # far-field / supersonic inflow: all variables prescribed
+                bh = uh_s - self.boundary_state(e, f)
+            elif tag == 2:                       # supersonic outflow: interior state extrapolated
+                bh = uh_s - u_s
+            elif tag in (3, 4):                  # no-slip wall: mass flux, uhat_v = 0, thermal condition
+                d = self.d
+                bh = uh_s.copy()
+                bh[..., 0] = fhat[..., 0]
+                if tag == 3:                     # isothermal: rho e = rho c_v T_w at vhat = 0
+                    bh[..., d + 1] = uh_s[..., d + 1] - uh_s[..., 0] * self.e_wall
+                else:                            # adiabatic: zero normal energy flux
+                    bh[..., d + 1] = fhat[..., d + 1]
             else:
                 raise ValueError("boundary tag %d not in the oracle" % tag)
+            Rh[..., f, :, :] = np.einsum("s,...sa,sl->...al", G.omega[f], bh, r.mu, optimize=True)
         return Rq, Ru, Rh
 
     # --------------------------------------------------------------- Jacobian

@@ -124,25 +124,25 @@ int create_host(hdg_ctx* h, const hdg_mesh* mesh, int p, double gamma, double Re
     if ((rc = build_vertex_map(*mesh, h->av_ev, h->av_vrow, h->av_vcol, h->err))) return rc;
     h->F = h->sk.n_faces;
     h->nnzb = h->sk.rowptr[h->F];
-    // boundary tags: 0 on interior / periodic faces, 1 (Dirichlet / far-field, bhat = uhat - u_b) on
-    // faces with a single element
+    // boundary tags: 0 on interior / periodic faces; on faces with a single element
+    // 1 far-field / supersonic inflow, 2 supersonic outflow, 3 isothermal wall, 4 adiabatic wall
     h->ftag.assign((size_t)h->E * h->nf, 0);
     if (mesh->bnd_tag)
         for (int64_t i = 0; i < h->E * h->nf; ++i) {
-            if (mesh->bnd_tag[i] != 0 && mesh->bnd_tag[i] != 1)
-                return fail(h, HDG_EUNSUPPORTED, "boundary tag " + std::to_string(mesh->bnd_tag[i]) + " not supported (0, 1)");
+            if (mesh->bnd_tag[i] < 0 || mesh->bnd_tag[i] > 4)
+                return fail(h, HDG_EUNSUPPORTED, "boundary tag " + std::to_string(mesh->bnd_tag[i]) + " not supported (0..4)");
             h->ftag[i] = mesh->bnd_tag[i];
         }
     for (int64_t F = 0; F < h->F; ++F) {
         const int32_t e0 = h->sk.f2e[2 * F], f0 = h->sk.f2lf[2 * F];
         const bool single = h->sk.f2e[2 * F + 1] < 0;
-        if (single != (h->ftag[(size_t)e0 * h->nf + f0] == 1))
-            return fail(h, HDG_EINVAL, "face " + std::to_string(F) + ": tag 1 must mark exactly the faces with one element");
+        if (single != (h->ftag[(size_t)e0 * h->nf + f0] != 0))
+            return fail(h, HDG_EINVAL, "face " + std::to_string(F) + ": tags 1..4 must mark exactly the faces with one element");
         if (!single && h->ftag[(size_t)h->sk.f2e[2 * F + 1] * h->nf + h->sk.f2lf[2 * F + 1]] != 0)
             return fail(h, HDG_EINVAL, "face " + std::to_string(F) + ": interior face tagged as boundary");
     }
     h->has_bnd = false;
-    for (int32_t t : h->ftag) h->has_bnd |= (t != 0);
+    for (int32_t t : h->ftag) { h->has_bnd |= (t != 0); h->has_tag[t] = true; }
     return build_geometry(h, *mesh);
 }
 
@@ -352,10 +352,36 @@ int hdg_set_tuning(hdg_handle h, const hdg_tune* t) {
 
 int hdg_set_bc_state(hdg_handle h, int tag, const double* ub) {
     if (!h || !ub) return fail(h, HDG_EINVAL, "NULL argument");
-    if (tag != 1) return fail(h, HDG_EUNSUPPORTED, "only tag 1 (Dirichlet / far-field) carries a state");
+    if (tag != 1 && tag != 3) return fail(h, HDG_EUNSUPPORTED, "only tags 1 (state) and 3 (wall temperature) carry data");
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
-    if (!h->has_bnd) return fail(h, HDG_EINVAL, "the mesh has no tag-1 faces");
+    if (!h->has_tag[tag]) return fail(h, HDG_EINVAL, "the mesh has no faces of tag " + std::to_string(tag));
+    if (tag == 3) {
+        if (!(ub[0] > 0.0)) return fail(h, HDG_EINVAL, "wall temperature must be positive");
+        const double g = h->phys.gamma, M = h->phys.mach;
+        h->e_wall = ub[0] / (g * (g - 1.0) * M * M);      // c_v T_w with T~ = gamma M^2 p / rho
+        h->tw_set = true;
+        return HDG_OK;
+    }
     CKH(cudaMemcpy(h->d_ub, ub, sizeof(double) * h->m, cudaMemcpyHostToDevice));
+    h->ub_set = true;
+    return HDG_OK;
+}
+
+int hdg_set_bc_field(hdg_handle h, const double* ubf) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
+    if (!h->has_tag[1]) return fail(h, HDG_EINVAL, "the mesh has no tag-1 faces");
+    const size_t n = (size_t)h->F * h->BS;
+    if (!ubf) {                                           // back to the constant state
+        h->d_ubf = nullptr;
+        return HDG_OK;
+    }
+    if (!h->ubf_store) {
+        int rc;
+        if ((rc = dev_alloc(h, &h->ubf_store, n))) return rc;
+    }
+    CKH(cudaMemcpyAsync(h->ubf_store, ubf, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+    h->d_ubf = h->ubf_store;
     h->ub_set = true;
     return HDG_OK;
 }
@@ -394,7 +420,8 @@ int hdg_linearize_condense(hdg_handle h, const double* U, const double* Q, const
     if (!U || !Q || !UH || !Ustar) return fail(h, HDG_EINVAL, "U, Q, UH and Ustar are required");
     if (res_norm) return fail(h, HDG_EINVAL, "res_norm must be NULL");
     if (!(dt > 0.0) || !(a_ii > 0.0)) return fail(h, HDG_EINVAL, "dt and a_ii must be positive");
-    if (h->has_bnd && !h->ub_set) return fail(h, HDG_EINVAL, "boundary state of tag 1 not set (hdg_set_bc_state)");
+    if (h->has_tag[1] && !h->ub_set) return fail(h, HDG_EINVAL, "boundary state of tag 1 not set (hdg_set_bc_state)");
+    if (h->has_tag[3] && !h->tw_set) return fail(h, HDG_EINVAL, "wall temperature of tag 3 not set (hdg_set_bc_state)");
     CKH(cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), h->stream));
     LinArgs a{U, Q, UH, Ustar, nu, dt, a_ii};
     if (h->precision == HDG_PREC_MIXED) {

@@ -121,6 +121,11 @@ struct hdg_ctx {
     int32_t* d_status = nullptr;           // [1]
     int32_t* d_ftag = nullptr;             // [E][nf] boundary tags, NULL for fully periodic meshes
     double* d_ub = nullptr;                // [m] state of tag-1 boundary faces
+    double* d_ubf = nullptr;               // [F][m][Nfp] nodal tag-1 data (hdg_set_bc_field), or NULL
+    double e_wall = 0.0;                   // c_v T_w of tag-3 (isothermal wall) faces
+    bool has_tag[5] = {};                  // boundary kinds present in the mesh
+    bool tw_set = false;
+    double* ubf_store = nullptr;           // owned copy of the nodal tag-1 data
     std::vector<int32_t> ftag;             // host copy of the tags
     bool ub_set = false;
     bool has_bnd = false;

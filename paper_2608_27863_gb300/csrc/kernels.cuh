@@ -77,8 +77,48 @@ struct PointArgs {
     double* dq0;
     const int32_t* ftag;        // [E][nf] boundary tag of each element face (0 interior / periodic)
     const double* ub;           // [m] boundary state of tag-1 faces
+    const double* ubf;          // [F][m][Nfp] nodal tag-1 boundary data (canonical order), or NULL
+    double ew;                  // wall internal energy c_v T_w of tag-3 faces
     int64_t e0;
 };
+
+// Boundary form bhat_a at one face quadrature point, scaled by w_s |J_s| like
+// the numerical flux fh = w_s |J_s| fhat_a it may take rows from (Sec. 2.2;
+// the forms are readings):
+//   tag 1 far-field / supersonic inflow   uhat - u_b
+//   tag 2 supersonic outflow              uhat - u      (interior state extrapolated)
+//   tag 3 isothermal no-slip wall         [fhat_rho; uhat_rhov; uhat_rhoE - uhat_rho e_w]
+//   tag 4 adiabatic no-slip wall          [fhat_rho; uhat_rhov; fhat_rhoE]
+template <int M>
+__device__ __forceinline__ double boundary_form(int tag, int a, double fh, double wn, const double* u,
+                                                const double* uh, double ub_a, double ew) {
+    switch (tag) {
+        case 1: return wn * (uh[a] - ub_a);
+        case 2: return wn * (uh[a] - u[a]);
+        case 3: return a == 0 ? fh : (a == M - 1 ? wn * (uh[a] - uh[0] * ew) : wn * uh[a]);
+        case 4: return (a == 0 || a == M - 1) ? fh : wn * uh[a];
+        default: return fh;
+    }
+}
+
+// trace rows of a boundary face that are copies of the numerical-flux rows
+template <int M>
+__device__ __forceinline__ bool boundary_row_is_flux(int tag, int a) {
+    return tag == 0 || (tag == 3 && a == 0) || (tag == 4 && (a == 0 || a == M - 1));
+}
+
+// u_b,a at face quadrature point s of local face f of element e (tag-1 faces)
+template <int NF, int M, int NFP>
+__device__ __forceinline__ double boundary_state(const double* ub, const double* ubf, const int32_t* e2f,
+                                                 const int32_t* perm, const double* mu, int64_t e, int f, int s,
+                                                 int a) {
+    if (!ubf) return ub[a];
+    const int64_t F = e2f[e * NF + f];
+    double v = 0.0;
+    for (int lam = 0; lam < NFP; ++lam)
+        v += mu[s * NFP + lam] * ubf[(F * M + a) * NFP + perm[(e * NF + f) * NFP + lam]];
+    return v;
+}
 
 template <class S> __device__ __forceinline__ const PhysT<S>& jac_phys(const PointArgs& A);
 template <> __device__ __forceinline__ const PhysT<double>& jac_phys<double>(const PointArgs& A) { return A.ph; }
@@ -105,7 +145,7 @@ __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
     double* sFres = sUH + NT;            // [d][m][Nq]
     double* sFH = sFres + D * M * NQ;    // [nf][m][Nfq]
     double* sRh = sFH + NF * M * NFQ;    // [nf][m][Nfp]
-    double* sFB = sRh + NT;              // [nf][m][Nfq] boundary form bhat on tag-1 faces
+    double* sFB = sRh + NT;              // [nf][m][Nfq] boundary form bhat (boundary faces)
     __shared__ double geo[GEO];
     const DeviceTables& T = A.tab;
 
@@ -259,12 +299,14 @@ __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
             double Fc[M][D], Fv[M][D];
             conv_flux<D, double, double>(uh, ph, Fc);
             visc_flux<D, double, double>(uh, ql, nuv, ph, Fv);
+            const int tag = A.ftag ? A.ftag[e * NF + f] : 0;
             for (int a = 0; a < M; ++a) {
                 double fn = 0.0;
                 for (int k = 0; k < D; ++k) fn += (Fc[a][k] - Fv[a][k]) * nw[k];
-                sFH[(f * M + a) * NFQ + s] = ws * (fn + nrm * A.tau * (u[a] - uh[a]));
-                // tag-1 (Dirichlet / far-field) faces: bhat = uhat - u_b
-                sFB[(f * M + a) * NFQ + s] = (A.ftag && A.ftag[e * NF + f] == 1) ? ws * nrm * (uh[a] - A.ub[a]) : 0.0;
+                const double fh = ws * (fn + nrm * A.tau * (u[a] - uh[a]));
+                sFH[(f * M + a) * NFQ + s] = fh;
+                const double ub_a = tag == 1 ? boundary_state<NF, M, NFP>(A.ub, A.ubf, A.e2f, A.perm, T.mu, e, f, s, a) : 0.0;
+                sFB[(f * M + a) * NFQ + s] = boundary_form<M>(tag, a, fh, ws * nrm, u, uh, ub_a, A.ew);
             }
         }
         TJ uhj[M], qj[M][D], nwj[D];
@@ -356,6 +398,7 @@ struct BlkArgs {
     DeviceTables tab;
     Regions<TL> R;
     double dt, a_ii, tau;
+    double ew;                              // wall internal energy of tag-3 faces
     int64_t e0;
 };
 
@@ -516,8 +559,14 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
         for (int k = 0; k < D; ++k) nrm += NW[f * D + k] * NW[f * D + k];
         nrm = sqrt(nrm);
         const TA taun = (TA)(A.tau * nrm), dtt = (TA)A.dt;
-        const bool bnd = A.ftag && A.ftag[e * NF + f] != 0;
+        const int tag = A.ftag ? A.ftag[e * NF + f] : 0;
+        // trace rows of a boundary face: copies of the numerical-flux rows, or algebraic in
+        // (uhat, u) with d bhat_a / d uhat_b = cb * face mass and d bhat_a / d u_b = cu * face mass
+        const bool flux_row = boundary_row_is_flux<M>(tag, a);
         const TA nrmt = (TA)nrm;
+        TA cb = (a == b) ? (TA)1 : (TA)0, cu = (TA)0;
+        if (tag == 3 && a == M - 1 && b == 0) cb = (TA)(-A.ew);
+        if (tag == 2 && a == b) cu = (TA)(-1);
         for (int idx = tid; idx < NFP * NCB; idx += NTH) {
             int lam = idx / NCB, c = idx - lam * NCB;
             TA v = 0;
@@ -525,22 +574,20 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
             const int64_t trow = (f * M + a) * NFP + lam;
             const int64_t irow = a * NP + T.fnode[f * NFP + lam];
             if (c < NP) {
-                if (a == b) {
-                    for (int k = 0; k < D; ++k) {
-                        int nfc = T.node_face[c * D + k];
-                        if (nfc >= 0 && nfc / NFP == f) v += taun * tmf[lam * NFP + (nfc - f * NFP)];
-                    }
+                TA vu = 0;                         // face mass coupling of node c, if it lies on face f
+                for (int k = 0; k < D; ++k) {
+                    int nfc = T.node_face[c * D + k];
+                    if (nfc >= 0 && nfc / NFP == f) vu = tmf[lam * NFP + (nfc - f * NFP)];
                 }
+                if (a == b) v += taun * vu;
                 const int col = b * NP + c;
-                // trace rows of a boundary face do not depend on the interior state
-                A21[trow * A.R.a21_rs + col] = bnd ? (TL)0 : (TL)v;
+                A21[trow * A.R.a21_rs + col] = flux_row ? (TL)v : (TL)(cu * nrmt * vu);
                 A11[irow * A.R.a11_rs + col] += A.dt * (double)v;
             } else {
                 int c2 = c - NP, f2 = c2 / NFP, l2 = c2 - f2 * NFP;
                 const int col = (f2 * M + b) * NFP + l2;
-                // boundary face: d bhat / d uhat = face mass matrix, diagonal in components
-                const TA vb = (f2 == f && a == b) ? nrmt * tmf[lam * NFP + l2] : (TA)0;
-                A22[trow * A.R.a22_rs + col] = bnd ? (TL)vb : (TL)v;
+                const TA vb = (f2 == f) ? cb * nrmt * tmf[lam * NFP + l2] : (TA)0;
+                A22[trow * A.R.a22_rs + col] = flux_row ? (TL)v : (TL)vb;
                 A12[irow * A.R.a12_rs + col] = (TL)(A12[irow * A.R.a12_rs + col] + dtt * v);
             }
         }
@@ -941,9 +988,10 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
     pa.rt = RG.rt; pa.rt_es = RG.rt_es; pa.rt_rs = RG.rt_rs;
     pa.rb = RG.rb; pa.rb_es = RG.rb_es; pa.rb_rs = RG.rb_rs;
     pa.vcoef = h->d_vcoef; pa.fcoef = h->d_fcoef; pa.dq0 = h->d_dq0;
-    pa.ftag = h->d_ftag; pa.ub = h->d_ub;
+    pa.ftag = h->d_ftag; pa.ub = h->d_ub; pa.ubf = h->d_ubf; pa.ew = h->e_wall;
     BlkArgs<double> ba;
     ba.vcoef = h->d_vcoef; ba.fcoef = h->d_fcoef; ba.geo = h->d_geo; ba.tab = h->tab; ba.ftag = h->d_ftag;
+    ba.ew = h->e_wall;
     ba.R = RG; ba.dt = la.dt; ba.a_ii = la.a_ii; ba.tau = h->phys.tau;
     for (int64_t e0 = 0; e0 < h->E; e0 += h->chunk) {
         const int64_t ne = std::min<int64_t>(h->chunk, h->E - e0);

@@ -27,6 +27,8 @@ struct ResArgs {
     double* part;                // [E] sum of squares of R_q and R_u of the element
     const int32_t* ftag;         // [E][nf] boundary tags or NULL
     const double* ub;            // [m] tag-1 boundary state
+    const double* ubf;           // [F][m][Nfp] nodal tag-1 boundary data, or NULL
+    double ew;                   // wall internal energy of tag-3 faces
 };
 
 // Lifted gradient at node i of component a (eq. hdg-grad with R_q = 0):
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(NTH) k_residual(ResArgs A) {
     double* sF = sUH + NT;               // [d][m][Nq]
     double* sFH = sF + D * M * NQ;       // [nf][m][Nfq]
     double* sRh = sFH + NF * M * NFQ;    // [nf][m][Nfp]
-    double* sFB = sRh + NT;              // [nf][m][Nfq] bhat on tag-1 faces
+    double* sFB = sRh + NT;              // [nf][m][Nfq] bhat on boundary faces
     double* red = sFB + NF * M * NFQ;    // [32]
     __shared__ double geo[GEO];
     const DeviceTables& T = A.tab;
@@ -172,11 +174,14 @@ __global__ void __launch_bounds__(NTH) k_residual(ResArgs A) {
         double Fc[M][D], Fv[M][D];
         conv_flux<D, double, double>(uh, ph, Fc);
         visc_flux<D, double, double>(uh, q, nuv, ph, Fv);
+        const int tag = A.ftag ? A.ftag[e * NF + f] : 0;
         for (int a = 0; a < M; ++a) {
             double fn = 0.0;
             for (int k = 0; k < D; ++k) fn += (Fc[a][k] - Fv[a][k]) * nw[k];
-            sFH[(f * M + a) * NFQ + s] = T.wf[s] * (fn + nrm * A.tau * (u[a] - uh[a]));
-            sFB[(f * M + a) * NFQ + s] = (A.ftag && A.ftag[e * NF + f] == 1) ? T.wf[s] * nrm * (uh[a] - A.ub[a]) : 0.0;
+            const double fh = T.wf[s] * (fn + nrm * A.tau * (u[a] - uh[a]));
+            sFH[(f * M + a) * NFQ + s] = fh;
+            const double ub_a = tag == 1 ? boundary_state<NF, M, NFP>(A.ub, A.ubf, A.e2f, A.perm, T.mu, e, f, s, a) : 0.0;
+            sFB[(f * M + a) * NFQ + s] = boundary_form<M>(tag, a, fh, T.wf[s] * nrm, u, uh, ub_a, A.ew);
         }
     }
     __syncthreads();
@@ -378,6 +383,7 @@ int run_residual(hdg_ctx* h, const LinArgs& la, double* Rq, double* Ru, double* 
     ra.U = la.U; ra.Q = la.Q; ra.UH = la.UH; ra.Ustar = la.Ustar; ra.nu = la.nu; ra.dt = la.dt; ra.a_ii = la.a_ii;
     ra.ph = phys_t<double>(h->phys); ra.tau = h->phys.tau; ra.tab = h->tab; ra.geo = h->d_geo; ra.e2f = h->d_e2f; ra.perm = h->d_perm;
     ra.Rq = Rq; ra.Ru = Ru; ra.rk = h->d_rk; ra.part = h->d_part; ra.ftag = h->d_ftag; ra.ub = h->d_ub;
+    ra.ubf = h->d_ubf; ra.ew = h->e_wall;
     k_residual<C, NTH><<<(unsigned)h->E, NTH, smem, h->stream>>>(ra);
     k_trace_residual<C><<<(unsigned)((h->F + 7) / 8), 256, 0, h->stream>>>(h->d_rk, h->d_f2e, h->d_f2lf, h->d_iperm,
                                                                         Ruh, h->d_part + h->E, h->F);

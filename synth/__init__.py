@@ -288,7 +288,8 @@ class Problem:
     UH: np.ndarray           # [F][m][Nfp]
     Ustar: np.ndarray        # [E][m][Np]
     nu: np.ndarray | None    # [E][Np] or None
-    ubc: np.ndarray | None = None  # boundary state for tag-1 faces
+    ubc: np.ndarray | None = None  # tag-1 boundary state: [m], or nodal [F][m][Nfp] (canonical order)
+    twall: float = 1.0             # wall temperature T~_w of tag-3 faces (T~_inf = 1)
 
 
 def _stage_state(mesh: Mesh, p: int, fun, ubg: np.ndarray, seed: int, noise: float,

@@ -13,8 +13,15 @@ def create(P, host_only=False):
                      host_only=host_only)
     if not host_only:
         H.hdg_set_params(h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s)
-        if np.any(m.bnd_tag):
-            H.hdg_set_bc_state(h, 1, P.ubc)
+        if np.any(m.bnd_tag == 1):
+            ubc = np.asarray(P.ubc, dtype=np.float64)
+            if ubc.ndim == 1:
+                H.hdg_set_bc_state(h, 1, ubc)
+            else:
+                import torch
+                H.hdg_set_bc_field(h, torch.from_numpy(np.ascontiguousarray(ubc)).cuda())
+        if np.any(m.bnd_tag == 3):
+            H.hdg_set_bc_state(h, 3, np.array([P.twall]))
     return h
 
 

@@ -208,3 +208,43 @@ def test_autotuned_variants_keep_parity():
         orc, _ = pb.assemble(blocks=blocks)
         assert max(block_rel_errors(vals, orc).values()) < TOL, (nb, minb)
         compare_handle.close()
+
+
+def tagged(P, side_tags, twall=1.0):
+    bt = P.mesh.bnd_tag.copy()
+    for (r, s), t in side_tags.items():
+        col = bt[:, 2 * r + s]
+        col[col != 0] = t
+    P.mesh.bnd_tag = bt
+    P.twall = twall
+    return P
+
+
+BOUNDARY_CASES = {
+    "quad-p2-inflow-outflow": lambda: tagged(synth.tiny(2, 2, periodic=(False, True), visc_law=1, av=1e-3),
+                                             {(0, 0): 1, (0, 1): 2}),
+    "quad-p3-isothermal": lambda: tagged(synth.tiny(2, 3, periodic=(True, False), visc_law=1),
+                                         {(1, 0): 3, (1, 1): 1}, twall=0.8),
+    "quad-p1-adiabatic-box": lambda: tagged(synth.tiny(2, 1, periodic=False, av=2e-3),
+                                            {(r, s): 4 for r in range(2) for s in (0, 1)}),
+    "hex-p2-wall-channel": lambda: tagged(synth.tiny(3, 2, periodic=(True, False, True), visc_law=1),
+                                          {(1, 0): 3, (1, 1): 4}, twall=1.2),
+    "hex-p1-all-kinds": lambda: tagged(synth.tiny(3, 1, periodic=False, av=1e-3),
+                                       {(0, 0): 1, (0, 1): 2, (1, 0): 3, (1, 1): 4, (2, 0): 3, (2, 1): 1}, twall=0.9),
+}
+
+
+@pytest.mark.parametrize("name", list(BOUNDARY_CASES))
+def test_boundary_kinds(name):
+    """Outflow and no-slip wall faces (tags 2-4) next to far-field faces: full comparison."""
+    compare(BOUNDARY_CASES[name](), check_matvec=True)
+
+
+def test_nodal_inflow_profile():
+    """Tag-1 faces with nodal boundary data (an inflow profile) instead of a constant state."""
+    P = tagged(synth.tiny(2, 2, periodic=(False, True)), {(0, 0): 1, (0, 1): 2})
+    cn = Problem(P).conn
+    ubc = np.broadcast_to(np.asarray(P.ubc)[None, :, None], (cn.n_faces, 4, 3)).copy()
+    ubc[:, 1, :] *= 1.0 + 0.1 * synth.uniform(3, ubc[:, 1, :].size).reshape(ubc[:, 1, :].shape)
+    P.ubc = ubc
+    compare(P, check_matvec=True)

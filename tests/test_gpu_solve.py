@@ -163,3 +163,24 @@ def test_newton_with_dirichlet_boundary_matches_oracle():
     assert rel(run.U.cpu().numpy(), ou) < 1e-11
     assert rel(run.UH.cpu().numpy(), oh) < 1e-11
     run.close()
+
+
+@pytest.mark.parametrize("tags", [{(0, 0): 1, (0, 1): 2}, {(1, 0): 3, (1, 1): 4}], ids=["inflow-outflow", "walls"])
+def test_residual_and_newton_with_walls(tags):
+    import torch
+    from paper_2608_27863_gb300 import hdg as H
+    from tests.test_gpu_parity import tagged
+    per = (False, True) if (0, 0) in tags else (True, False)
+    P = tagged(synth.tiny(2, 2, periodic=per, visc_law=1, mach=0.4), tags, twall=1.1)
+    run = GpuRun(P)
+    Rq, Ru, Ruh = torch.empty_like(run.Q), torch.empty_like(run.U), torch.empty_like(run.UH)
+    H.hdg_residual(run.h, run.U, run.Q, run.UH, run.Ustar, run.nu, P.dt, P.a_ii, Rq, Ru, Ruh)
+    pb = Problem(P)
+    oq, ou, oh = pb.global_residual(pb.Q, pb.U, pb.UH)
+    assert rel(Ruh.cpu().numpy(), oh) < TOL and rel(Ru.cpu().numpy(), ou) < TOL
+    nit, git, hist = H.hdg_newton(run.h, run.U, run.Q, run.UH, run.Ustar, run.nu, P.dt, P.a_ii, tol=1e-11,
+                                  max_newton=10, restart=60, max_gmres=600, gmres_rtol=1e-12)
+    assert hist[-1] <= 1e-11
+    oq2, ou2, oh2, _ = oracle_newton(P, 1e-11, maxit=10)
+    assert rel(run.U.cpu().numpy(), ou2) < 1e-10 and rel(run.UH.cpu().numpy(), oh2) < 1e-10
+    run.close()

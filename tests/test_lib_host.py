@@ -54,10 +54,20 @@ def test_connectivity_bit_exact_with_boundaries(H):
 def test_boundary_tag_checks(H):
     mesh = synth.box_mesh(2, (3, 3), (0, 0), (1, 1), (True, False))
     bad = mesh.bnd_tag.copy()
-    bad[bad == 1] = 3
+    bad[bad == 1] = 7
     with pytest.raises(H.HDGError) as ex:
         H.hdg_create_host(2, mesh.vert_xyz, mesh.elem_vert, mesh.periodic_map, bad, 2, 1.4, 100.0, 0.72, 0.3)
     assert ex.value.code == H.HDG_EUNSUPPORTED
+    for t in (2, 3, 4):                     # outflow, isothermal and adiabatic walls are accepted
+        ok = mesh.bnd_tag.copy()
+        ok[ok == 1] = t
+        H.hdg_destroy(H.hdg_create_host(2, mesh.vert_xyz, mesh.elem_vert, mesh.periodic_map, ok, 2, 1.4, 100.0,
+                                        0.72, 0.3))
+    inner = mesh.bnd_tag.copy()
+    inner[4, 0] = 3                         # an interior face marked as a wall
+    with pytest.raises(H.HDGError) as ex:
+        H.hdg_create_host(2, mesh.vert_xyz, mesh.elem_vert, mesh.periodic_map, inner, 2, 1.4, 100.0, 0.72, 0.3)
+    assert ex.value.code == H.HDG_EINVAL
     with pytest.raises(H.HDGError) as ex:   # boundary faces without tags
         H.hdg_create_host(2, mesh.vert_xyz, mesh.elem_vert, mesh.periodic_map, None, 2, 1.4, 100.0, 0.72, 0.3)
     assert ex.value.code == H.HDG_EINVAL
