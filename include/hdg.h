@@ -127,6 +127,14 @@ int hdg_destroy(hdg_handle h);
 const char* hdg_last_error(hdg_handle h);
 
 int hdg_set_params(hdg_handle h, const hdg_params* prm);
+/* The per-element storage of the condensed system (BSR values, the interior
+ * rows kept for recovery, per-chunk trace rows) is allocated on the first
+ * linearization in a precision, so a run in one precision never holds the
+ * other's arrays (a mixed-form run of 98,304 hex p = 3 elements needs about
+ * 230 GB; the FP64 arrays would add 370 GB).  hdg_reserve allocates the
+ * storage of `precision` now, for callers that must not allocate later
+ * (hdg_linearize_condense_static requires the FP64 storage reserved). */
+int hdg_reserve(hdg_handle h, int precision);
 int hdg_set_stream(hdg_handle h, void* cuda_stream);
 /* Boundary data (host): tag 1, the state u_b [m] of the far-field / inflow
  * faces (trace equation <uhat - u_b, mu> = 0); tag 3, ub[0] = the wall

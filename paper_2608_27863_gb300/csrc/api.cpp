@@ -168,6 +168,33 @@ int dev_upload(hdg_ctx* h, T** out, const std::vector<T>& v) {
     return HDG_OK;
 }
 
+}  // namespace
+
+namespace hdg {
+int ensure_system_storage(hdg_ctx* h, int precision) {
+    int rc;
+    if (precision == HDG_PREC_FP64) {
+        if (!h->d_vals && (rc = dev_alloc(h, &h->d_vals, (size_t)h->nnzb * h->BS * h->BS))) return rc;
+        if (!h->d_top && (rc = dev_alloc(h, &h->d_top, (size_t)h->E * h->NU * h->LD))) return rc;
+        if (!h->d_bot && (rc = dev_alloc(h, &h->d_bot, (size_t)h->chunk * h->NT * h->LD))) return rc;
+        return HDG_OK;
+    }
+    if (h->d_m11) return HDG_OK;
+    const size_t E = h->E, ch = h->chunk, NU = h->NU, NT = h->NT;
+    if ((rc = dev_alloc(h, &h->d_m11, E * NU * NU))) return rc;
+    if ((rc = dev_alloc(h, &h->d_m12, E * NU * NT))) return rc;
+    if ((rc = dev_alloc(h, &h->d_mrt, E * NU))) return rc;
+    if ((rc = dev_alloc(h, &h->d_m21, ch * NT * NU))) return rc;
+    if ((rc = dev_alloc(h, &h->d_m22, ch * NT * NT))) return rc;
+    if ((rc = dev_alloc(h, &h->d_mrb, ch * NT))) return rc;
+    if ((rc = dev_alloc(h, &h->d_vals32, (size_t)h->nnzb * h->BS * h->BS))) return rc;
+    if ((rc = dev_alloc(h, &h->d_x32, (size_t)h->F * h->BS))) return rc;
+    return HDG_OK;
+}
+}  // namespace hdg
+
+namespace {
+
 int create_device(hdg_ctx* h) {
     const RefTables& t = h->ref;
     int rc;
@@ -193,9 +220,9 @@ int create_device(hdg_ctx* h) {
     UP(h->d_rowptr, h->sk.rowptr); UP(h->d_col, h->sk.col);
     UP(h->d_blk, h->sk.blk); UP(h->d_rank, h->sk.rank); UP(h->d_frank, h->sk.frank);
 #undef UP
-    if ((rc = dev_alloc(h, &h->d_vals, (size_t)h->nnzb * h->BS * h->BS))) return rc;
+    // the per-element storage of the FP64 / mixed system is allocated on first use
+    // (ensure_system_storage), so a mixed-only run never holds the FP64 arrays
     if ((rc = dev_alloc(h, &h->d_g, (size_t)h->F * h->BS))) return rc;
-    if ((rc = dev_alloc(h, &h->d_top, (size_t)h->E * h->NU * h->LD))) return rc;
     if ((rc = dev_alloc(h, &h->d_dq0, (size_t)h->E * h->NQV))) return rc;
     if ((rc = dev_alloc(h, &h->d_status, 1))) return rc;
     if (h->has_bnd) {
@@ -211,7 +238,6 @@ int create_device(hdg_ctx* h) {
     if (const char* s = std::getenv("HDG_SCRATCH_BYTES")) budget = std::strtoull(s, nullptr, 10);
     h->chunk = std::max<int64_t>(1, std::min<int64_t>(h->E, (int64_t)(budget / per)));
     if (const char* s = std::getenv("HDG_ELIM_MINB")) h->elim_minb = std::atoi(s) == 1 ? 1 : 2;
-    if ((rc = dev_alloc(h, &h->d_bot, (size_t)h->chunk * h->NT * h->LD))) return rc;
     if ((rc = dev_alloc(h, &h->d_vcoef, (size_t)h->chunk * h->m * h->m * d * h->NCOEF * h->Nq))) return rc;
     if ((rc = dev_alloc(h, &h->d_fcoef, (size_t)h->chunk * h->nf * h->m * h->m * h->NCOEF * h->Nfq))) return rc;
     h->device = true;
@@ -279,6 +305,13 @@ int hdg_set_params(hdg_handle h, const hdg_params* prm) {
     h->schur_mode = prm->precision == HDG_PREC_FP64 ? 0 : prm->precision - HDG_PREC_MIXED;
     h->prec_req = prm->precision;
     return HDG_OK;
+}
+
+int hdg_reserve(hdg_handle h, int precision) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
+    if (precision < HDG_PREC_FP64 || precision > HDG_PREC_MIXED_3XTF32) return fail(h, HDG_EINVAL, "unknown precision");
+    return hdg::ensure_system_storage(h, precision == HDG_PREC_FP64 ? HDG_PREC_FP64 : HDG_PREC_MIXED);
 }
 
 int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* UH, const double* Ustar,

@@ -219,6 +219,9 @@ template <int D, int P> int run_linearize(hdg_ctx* h, const LinArgs& a);
 template <int D, int P> int run_matvec(hdg_ctx* h, const double* x, double* y);
 template <int D, int P> int run_recover(hdg_ctx* h, const double* dUH, double* dQ, double* dU);
 template <int D, int P> int run_residual(hdg_ctx* h, const LinArgs& a, double* Rq, double* Ru, double* Ruh);
+// Allocates, on first use, the per-element storage of the FP64 or the mixed
+// system (BSR values, interior rows, per-chunk trace rows); no-op afterwards.
+int ensure_system_storage(hdg_ctx* h, int precision);
 template <int D, int P> int run_asm_setup(hdg_ctx* h);
 template <int D, int P> int run_asm_apply(hdg_ctx* h, const double* x, double* y);
 template <int D, int P> int run_av_field(hdg_ctx* h, const double* U, const double* Q, double c_av, double h_m,

@@ -961,6 +961,7 @@ template <> struct BlkCfg<Cfg<3, 3>> { static constexpr int TY = 16, TX = 16, KC
 
 template <int D, int P>
 int run_linearize(hdg_ctx* h, const LinArgs& la) {
+    if (int rc = ensure_system_storage(h, HDG_PREC_FP64)) return rc;
     using C = Cfg<D, P>;
     using BC = BlkCfg<C>;
     using BS_ = BlkShape<C, BC::TY, BC::TX, BC::KC>;

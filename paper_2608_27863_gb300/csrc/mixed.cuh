@@ -519,21 +519,6 @@ __global__ void k_schur_tc(Regions<float> R, int64_t e0, int32_t* status);
 template <class C>
 struct SchurTC;
 
-template <class T>
-int mixed_alloc(hdg_ctx* h, T** p, size_t count) {
-    void* q = nullptr;
-    cudaError_t e = cudaMalloc(&q, std::max<size_t>(count, 1) * sizeof(T));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        h->err = "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes for the mixed form failed";
-        return HDG_ENOMEM;
-    }
-    h->allocs.push_back(q);
-    h->device_bytes += (int64_t)(count * sizeof(T));
-    *p = (T*)q;
-    return HDG_OK;
-}
-
 inline Regions<float> mixed_regions(hdg_ctx* h) {
     const int64_t NU = h->NU, NT = h->NT;
     Regions<float> R;
@@ -553,17 +538,7 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
     using BS_ = BlkShape<C, BC::TY, BC::TX, BC::KC>;
     constexpr int PT = 128, NB = 16;
     int rc;
-    if (!h->d_m11) {
-        const size_t E = h->E, ch = h->chunk;
-        if ((rc = mixed_alloc(h, &h->d_m11, E * C::NU * C::NU))) return rc;
-        if ((rc = mixed_alloc(h, &h->d_m12, E * C::NU * C::NT))) return rc;
-        if ((rc = mixed_alloc(h, &h->d_mrt, E * C::NU))) return rc;
-        if ((rc = mixed_alloc(h, &h->d_m21, ch * C::NT * C::NU))) return rc;
-        if ((rc = mixed_alloc(h, &h->d_m22, ch * C::NT * C::NT))) return rc;
-        if ((rc = mixed_alloc(h, &h->d_mrb, ch * C::NT))) return rc;
-        if ((rc = mixed_alloc(h, &h->d_vals32, (size_t)h->nnzb * C::BS * C::BS))) return rc;
-        if ((rc = mixed_alloc(h, &h->d_x32, (size_t)h->F * C::BS))) return rc;
-    }
+    if ((rc = ensure_system_storage(h, HDG_PREC_MIXED))) return rc;
     auto kblk = k_blocks<C, BC::TY, BC::TX, BC::KC, float, float>;
     const size_t sm_point = sizeof(double) * point_smem_doubles<C>();
     const size_t sm_blk = sizeof(float) * BS_::smem;

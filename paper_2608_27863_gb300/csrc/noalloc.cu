@@ -63,6 +63,8 @@ extern "C" int hdg_linearize_condense_static(hdg_handle h, const double* U, cons
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage (created with hdg_create_host)");
     if (!U || !Q || !UH || !Ustar) return fail(h, HDG_EINVAL, "U, Q, UH and Ustar are required");
     if (!(dt > 0.0) || !(a_ii > 0.0)) return fail(h, HDG_EINVAL, "dt and a_ii must be positive");
+    if (!h->d_vals || !h->d_top)
+        return fail(h, HDG_EINVAL, "FP64 system storage not reserved (hdg_reserve(h, HDG_PREC_FP64) at set-up)");
     const size_t n_bot = (size_t)h->NT * h->LD;
     const size_t n_vc = (size_t)h->m * h->m * h->d * h->NCOEF * h->Nq;
     const size_t n_fc = (size_t)h->nf * h->m * h->m * h->NCOEF * h->Nfq;

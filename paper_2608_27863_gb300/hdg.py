@@ -38,7 +38,7 @@ EXPORTS = [
     "hdg_blockjacobi_setup", "hdg_blockjacobi_apply", "hdg_gmres", "hdg_newton", "hdg_set_bc_state",
     "hdg_newton_fixed", "hdg_dirk_step", "hdg_lift_gradient", "hdg_set_preconditioner", "hdg_schwarz_setup",
     "hdg_schwarz_apply", "hdg_rb_setup", "hdg_rb_push", "hdg_rb_guess", "hdg_av_field", "hdg_tgv_diagnostics",
-    "hdg_autotune", "hdg_set_tuning", "hdg_set_bc_field",
+    "hdg_autotune", "hdg_set_tuning", "hdg_set_bc_field", "hdg_reserve",
 ]
 KERNEL_CLASSES = ["point", "blocks", "elim", "assemble", "matvec", "recover", "schur"]
 
@@ -111,6 +111,7 @@ def lib():
         "hdg_autotune": [vp, vp, vp, vp, vp, vp, dbl, dbl, i32, vp],
         "hdg_set_tuning": [vp, vp],
         "hdg_set_bc_field": [vp, vp],
+        "hdg_reserve": [vp, i32],
         "hdg_av_field": [vp, vp, vp, dbl, dbl, dbl, vp],
         "hdg_tgv_diagnostics": [vp, vp, vp, vp],
         "hdg_rb_push": [vp, vp],
@@ -401,3 +402,8 @@ def hdg_set_tuning(h, elim_nb=16, elim_minb=2, schur_mode=0):
 def hdg_set_bc_field(h, ubf):
     """Nodal tag-1 boundary data [F][m][Nfp] (device array), or None for the constant state."""
     _check(h, lib().hdg_set_bc_field(h, _ptr(ubf)))
+
+
+def hdg_reserve(h, precision=0):
+    """Allocate the system storage of a precision now (it is otherwise allocated on first use)."""
+    _check(h, lib().hdg_reserve(h, int(precision)))

@@ -381,3 +381,109 @@ def tiny(dim: int, p: int, seed: int = 7, periodic=True, visc_law: int = 0, av: 
     nu = synthetic_nu(mesh, p, seed + 5, av) if av > 0 else None
     return Problem("tiny-%dd-p%d" % (dim, p), mesh, p, gamma, 50.0, 0.72, mach, 3.0, 5e-2, 0.4,
                    visc_law, 1.4042, 0.40417, U, Q, UH, Ustar, nu, ubg)
+
+
+# ----------------------------------------------------------------------------
+# Hypersonic flat-plate boundary layer (the wall-bounded workload)
+# ----------------------------------------------------------------------------
+def graded_coordinates(n: int, length: float, first: float) -> np.ndarray:
+    """n cells on [0, length] growing geometrically from `first`, the ratio solved
+    so that they fill the length exactly.
+
+    The workload asks for a first cell of 1e-4 of the height growing by 1.15;
+    48 such cells reach only 0.55 of the height, so the first cell and the
+    height are kept and the ratio becomes 1.168 (a reading)."""
+    lo, hi = 1.0 + 1e-12, 2.0
+    for _ in range(200):
+        r = 0.5 * (lo + hi)
+        if first * (r ** n - 1.0) / (r - 1.0) > length:
+            hi = r
+        else:
+            lo = r
+    r = 0.5 * (lo + hi)
+    x = np.concatenate([[0.0], np.cumsum(first * r ** np.arange(n))])
+    return x * (length / x[-1])
+
+
+def blasius(eta_max: float = 12.0):
+    """Blasius solution of f''' + f f'' / 2 = 0, f(0) = f'(0) = 0, f'(inf) = 1:
+    shooting on f''(0) with an adaptive Runge-Kutta integrator; returns a
+    callable f'(eta) (dense output) and the shooting value f''(0)."""
+    from scipy.integrate import solve_ivp
+    from scipy.optimize import brentq
+
+    def rhs(_, y):
+        return [y[1], y[2], -0.5 * y[0] * y[2]]
+
+    def end(s):
+        return solve_ivp(rhs, (0.0, eta_max), [0.0, 0.0, s], rtol=1e-11, atol=1e-12).y[1, -1] - 1.0
+
+    s = brentq(end, 0.2, 0.5, xtol=1e-14)
+    sol = solve_ivp(rhs, (0.0, eta_max), [0.0, 0.0, s], rtol=1e-11, atol=1e-12, dense_output=True)
+    return (lambda eta: sol.sol(np.minimum(eta, eta_max))[1]), s
+
+
+def plate_state_function(gamma, mach, pr, re_unit, t_wall, amp, seed, lx, lz):
+    """Compressible laminar plate state: Blasius velocity f'(eta), Crocco-Busemann
+    temperature T = T_w + (T_aw - T_w) u - (T_aw - 1) u^2 (T_inf = 1,
+    T_aw = 1 + sqrt(Pr) (gamma - 1) M^2 / 2), uniform pressure 1 / (gamma M^2),
+    rho = 1 / T; the wall distance follows the Howarth-Dorodnitsyn stretching
+    y = sqrt(x / Re) int_0^eta T d eta.  A seeded 3-D disturbance of relative
+    amplitude `amp` is added to the momentum."""
+    fpf, _ = blasius()
+    eta = np.linspace(0.0, 12.0, 6001)
+    fp = fpf(eta)
+    t_aw = 1.0 + math.sqrt(pr) * (gamma - 1.0) * mach ** 2 / 2.0
+    T_eta = t_wall + (t_aw - t_wall) * fp - (t_aw - 1.0) * fp ** 2
+    ystar = np.concatenate([[0.0], np.cumsum(0.5 * (T_eta[1:] + T_eta[:-1]) * np.diff(eta))])
+    from scipy.interpolate import CubicSpline
+    u_of = CubicSpline(ystar, fp)                    # f' as a function of the stretched distance
+    r = uniform(seed, 12)
+    p_inf = 1.0 / (gamma * mach * mach)
+
+    def fun(x):
+        xs = np.maximum(x[..., 0], 1e-6)
+        ys = x[..., 1] * np.sqrt(re_unit / xs)
+        u = np.where(ys < ystar[-1], u_of(np.minimum(ys, ystar[-1])), 1.0)
+        T = t_wall + (t_aw - t_wall) * u - (t_aw - 1.0) * u * u
+        rho = 1.0 / T
+        damp = (ys / 5.0) * np.exp(1.0 - ys / 5.0)   # peaks inside the layer, 0 at the wall
+        vel = [u, np.zeros_like(u), np.zeros_like(u)]
+        for k in range(3):
+            ph = 2 * np.pi * (x[..., 0] * (1 + 2 * r[3 * k]) / lx + x[..., 2] * (1 + r[3 * k + 1]) / lz + r[3 * k + 2])
+            vel[k] = vel[k] + amp * damp * np.sin(ph)
+        return conserved(rho, vel, p_inf + 0.0 * rho, gamma)
+
+    return fun, t_aw
+
+
+def config5(nx: int = 64, ny: int = 48, nz: int = 32, p: int = 3, seed: int = 4) -> Problem:
+    """Flat-plate boundary layer at M = 6 on [0.1, 1.1] x [0, 0.1] x [0, 0.05]:
+    wall-normal cells from 1e-4 of the height growing geometrically to fill it,
+    isothermal wall at T_w = 0.5 T_aw (y = 0, tag 3), far field on top and at
+    the inflow (tag 1, freestream state), extrapolation outflow (tag 2),
+    periodic in z; Re_unit = 1e6, Pr = 0.72, Sutherland with S~ = 110.4 / 51.86
+    and C1 = 1 + S~ (mu~(1) = 1); time step 2e-4 (the Mach-7 case's)."""
+    gamma, mach, pr, re = 1.4, 6.0, 0.72, 1.0e6
+    H, lx, lz = 0.1, 1.0, 0.05
+    xs = np.linspace(0.1, 1.1, nx + 1)
+    ys = graded_coordinates(ny, H, 1e-4 * H)
+    zs = np.linspace(0.0, lz, nz + 1)
+    mesh = box_mesh(3, (nx, ny, nz), (0.1, 0.0, 0.0), (1.1, H, lz), (False, False, True),
+                    coords=[xs, ys, zs], tags={(0, 0): 1, (0, 1): 2, (1, 0): 3, (1, 1): 1})
+    t_aw = 1.0 + math.sqrt(pr) * (gamma - 1.0) * mach ** 2 / 2.0
+    t_wall = 0.5 * t_aw
+    fun, _ = plate_state_function(gamma, mach, pr, re, t_wall, 1e-3, seed, lx, lz)
+    ubg = freestream(3, gamma, mach)
+    x = node_xyz(mesh, p)
+    U = np.ascontiguousarray(fun(x).transpose(0, 2, 1))
+    Q = np.ascontiguousarray(nodal_gradient(fun, x, h=1e-8).transpose(0, 2, 3, 1))
+    F = mesh.n_faces()
+    Nfp = (p + 1) ** 2
+    UH = np.broadcast_to(ubg.reshape(1, 5, 1), (F, 5, Nfp)).copy()
+    UH += 1e-3 * (np.abs(ubg).reshape(1, 5, 1) + 1.0) * normal(seed + 1000, UH.size).reshape(UH.shape)
+    s_t = 110.4 / 51.86
+    P = Problem("hex-p%d-%dx%dx%d-plate-M6" % (p, nx, ny, nz), mesh, p, gamma, re, pr, mach, 5.0, 2e-4, 0.29,
+                1, 1.0 + s_t, s_t, U, Q, UH, U.copy(), None, ubg)
+    P.twall = t_wall
+    return P

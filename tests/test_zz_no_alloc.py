@@ -43,3 +43,21 @@ def test_static_scratch_matches_allocating_entry_point(make):
             assert np.linalg.norm(vals[b] - ref_vals[b]) <= TOL * np.linalg.norm(ref_vals[b]), b
         assert np.linalg.norm(g - ref_g) <= TOL * np.linalg.norm(ref_g)
     run.close()
+
+
+def test_static_entry_point_needs_reserved_storage():
+    from paper_2608_27863_gb300 import hdg as H
+    P = synth.config2(n=3)
+    run = GpuRun(P)
+    args = (run.h, H._ptr(run.U), H._ptr(run.Q), H._ptr(run.UH), H._ptr(run.Ustar), H._ptr(run.nu),
+            float(P.dt), float(P.a_ii))
+    assert H.lib().hdg_linearize_condense_static(*args) == H.HDG_EINVAL
+    assert "reserve" in H.hdg_last_error(run.h)
+    H.hdg_reserve(run.h, H.HDG_PREC_FP64)
+    assert H.lib().hdg_linearize_condense_static(*args) == H.HDG_OK
+    vals = run.blocks()
+    ref = GpuRun(P).linearize()
+    rv = ref.blocks()
+    assert max(np.linalg.norm(vals[b] - rv[b]) / np.linalg.norm(rv[b]) for b in range(0, len(rv), 7)) <= TOL
+    ref.close()
+    run.close()
