@@ -183,6 +183,7 @@ struct hdg_ctx {
     // mixed form (allocated on the first mixed linearization)
     int sys_prec = HDG_PREC_FP64;          // precision of the assembled system
     int schur_mode = 0;                    // mixed Schur product: 0 FP32 SIMT, 1 TF32, 2 3xTF32 tensor cores
+    int blocks_mode = 1;                   // mixed volume contraction: 0 FP32 SIMT, 1 3xTF32 tensor cores (3-D)
     double* d_m11 = nullptr;               // [E][NU][NU] interior block / its LU factors (FP64)
     float* d_m12 = nullptr;                // [E][NU][NT] Bt, then Z = L^{-1} P Bt
     double* d_mrt = nullptr;               // [E][NU] Rt, then z

@@ -417,7 +417,9 @@ struct BlkShape {
     static constexpr int smem = main_smem > face_smem ? main_smem : face_smem;
 };
 
-template <class C, int TY, int TX, int KC, class TA, class TL>
+// VOL = false skips the volume contraction (done on tensor cores by
+// k_blocks_tc in the mixed form) and adds only the face terms.
+template <class C, int TY, int TX, int KC, class TA, class TL, bool VOL = true>
 __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
     constexpr int D = C::D, M = C::M, NP = C::NP, NQ = C::NQ, NF = C::NF, NFP = C::NFP, NFQ = C::NFQ;
     constexpr int NCOEF = C::NCOEF;
@@ -464,7 +466,7 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
         }
     }
 
-    for (int k0 = 0; k0 < K; k0 += KC) {
+    for (int k0 = 0; VOL && k0 < K; k0 += KC) {
         const int kc = min(KC, K - k0);
         for (int idx = tid; idx < kc * NCOEF; idx += NTH) {
             int kk = idx / NCOEF, c = idx - kk * NCOEF, k = k0 + kk, r = k / NQ, g = k - r * NQ;
@@ -516,7 +518,7 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
 #pragma unroll
     for (int s = 0; s < SL; ++s) {
         const int i = ri[s], c = ci[s];
-        if (i < 0 || i >= NP || c >= NCB) continue;
+        if (!VOL || i < 0 || i >= NP || c >= NCB) continue;
         const int64_t row = a * NP + i;
         if (c < NP) {
             double v = (double)acc[s];

@@ -518,6 +518,10 @@ template <class C, bool SPLIT3>
 __global__ void k_schur_tc(Regions<float> R, int64_t e0, int32_t* status);
 template <class C>
 struct SchurTC;
+template <class C>
+struct BlkTC;
+template <class C>
+__global__ void k_blocks_tc(BlkArgs<float> A, int32_t* status);
 
 inline Regions<float> mixed_regions(hdg_ctx* h) {
     const int64_t NU = h->NU, NT = h->NT;
@@ -540,11 +544,15 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
     int rc;
     if ((rc = ensure_system_storage(h, HDG_PREC_MIXED))) return rc;
     auto kblk = k_blocks<C, BC::TY, BC::TX, BC::KC, float, float>;
+    auto kface = k_blocks<C, BC::TY, BC::TX, BC::KC, float, float, false>;
     const size_t sm_point = sizeof(double) * point_smem_doubles<C>();
     const size_t sm_blk = sizeof(float) * BS_::smem;
     const size_t sm_elim = elim_mixed_smem_bytes<C, NB>();
     HDG_CK(cudaFuncSetAttribute(k_point<C, PT, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_point));
     HDG_CK(cudaFuncSetAttribute(kblk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
+    HDG_CK(cudaFuncSetAttribute(kface, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
+    if (C::D == 3)
+        HDG_CK(cudaFuncSetAttribute(k_blocks_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, BlkTC<C>::smem_bytes()));
     HDG_CK(cudaFuncSetAttribute(k_elim_mixed<C, NB, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
     cudaStream_t st = h->stream;
     HDG_CK(cudaMemsetAsync(h->d_vals32, 0, sizeof(float) * h->nnzb * C::BS * C::BS, st));
@@ -570,7 +578,14 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
         k_point<C, PT, float><<<(unsigned)ne, PT, sm_point, st>>>(pa);
         prof_end(h);
         prof_begin(h, HDG_K_BLOCKS);
-        kblk<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
+        if (h->blocks_mode == 1 && C::D == 3) {
+            // volume contraction on tensor cores (3xTF32), face terms added by the SIMT kernel
+            using BT = BlkTC<C>;
+            k_blocks_tc<C><<<(unsigned)(ne * BT::NMT), 128, BT::smem_bytes(), st>>>(ba, h->d_status);
+            kface<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
+        } else {
+            kblk<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
+        }
         prof_end(h);
         prof_begin(h, HDG_K_ELIM);
         k_elim_mixed<C, NB, 256><<<(unsigned)ne, 256, sm_elim, st>>>(RM, e0, h->d_status);
@@ -818,6 +833,169 @@ __global__ void __launch_bounds__(128) k_schur_tc(Regions<float> R, int64_t e0, 
                 for (int j = 0; j < 16; ++j) {
                     const int c = n0 + c0 + j;
                     if (c0 + j < NTN && c < NT) Dm[r * sd + c] -= __uint_as_float(v[j]);
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(S::TCOLS));
+}
+
+// ----------------------------------------------------------------------------
+// A2 on tensor cores (mixed form): the volume contraction
+//   Out[(a,b,c)][i] = sum_k G_ab[k][c] dphi[k][i],   k = (direction, quadrature point),
+// one GEMM per element with M = m^2 (Np + nf Nfp) rows (component pair, block
+// column), N = Np (test function, padded to a multiple of 16) and
+// K = d Nq.  The operand G is generated on the fly from the point
+// coefficients and the FP32 basis tables exactly as in k_blocks (one core
+// matrix per warp step, so the shared-memory writes are contiguous); dphi is
+// the reference derivative table.  3xTF32 (hi/lo split of both operands),
+// FP32 accumulation in tensor memory, epilogue to Ã (FP64, with the DIRK mass
+// term) and B̃ (FP32).  One CTA (4 warps) per (element, 128-row tile); waits
+// on the MMA barrier are bounded as in k_schur_tc.
+// ----------------------------------------------------------------------------
+template <class C>
+struct BlkTC {
+    static constexpr int NCB = C::NP + C::NF * C::NFP;
+    static constexpr int MR = C::M * C::M * NCB;
+    static constexpr int MT = 128, KC = 32;
+    static constexpr int NMT = (MR + MT - 1) / MT;
+    static constexpr int K = C::D * C::NQ;
+    static constexpr int NTN = (C::NP + 15) / 16 * 16;
+    static constexpr int TCOLS = NTN <= 32 ? 32 : NTN <= 64 ? 64 : 128;
+    static_assert(NTN <= 128, "N tile too wide");
+    __host__ __device__ static constexpr int smem_bytes() { return 2 * (MT * KC + NTN * KC) * 4 + 64; }
+};
+
+template <class C>
+__global__ void __launch_bounds__(128) k_blocks_tc(BlkArgs<float> A, int32_t* status) {
+    using S = BlkTC<C>;
+    constexpr int D = C::D, M = C::M, NP = C::NP, NQ = C::NQ, NFP = C::NFP, NCOEF = C::NCOEF;
+    constexpr int NCB = S::NCB, MR = S::MR, MT = S::MT, KC = S::KC, K = S::K, NTN = S::NTN;
+    constexpr int GEO = Geo<D>::N;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t bid = blockIdx.x;
+    const int mt = (int)(bid % S::NMT);
+    const int64_t el = bid / S::NMT, e = A.e0 + el;
+    const int m0 = mt * MT;
+    const DeviceTables& T = A.tab;
+    const float* cfe = reinterpret_cast<const float*>(A.vcoef) + (size_t)el * M * M * D * NCOEF * NQ;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    float* Ah = reinterpret_cast<float*>(smraw);
+    float* Bh = Ah + MT * KC;
+    float* Al = Bh + NTN * KC;
+    float* Bl = Al + MT * KC;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(smraw + S::smem_bytes() - 64);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(tslot)),
+                     "r"(S::TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = *tslot;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NTN >> 3) << 17) | ((uint32_t)(MT >> 4) << 24);
+    const uint32_t bar = smem_u32(mbar);
+    uint32_t phase = 0;
+    bool ok = true;
+    const int rr = lane >> 2, kq = lane & 3;          // position inside an 8 x 4 core matrix
+    for (int k0 = 0; k0 < K; k0 += KC) {
+        // generated operand: 128 rows x KC, one core matrix (8 rows x 4 k) per warp step
+        for (int core = warp; core < (MT / 8) * (KC / 4); core += 4) {
+            const int r = m0 + (core / (KC / 4)) * 8 + rr, k = k0 + (core % (KC / 4)) * 4 + kq;
+            float v = 0.f;
+            if (r < MR && k < K) {
+                const int ab = r / NCB, c = r - ab * NCB, dir = k / NQ, g = k - dir * NQ;
+                const float* cc = cfe + ((size_t)ab * D + dir) * NCOEF * NQ + g;
+                if (c < NP) {
+                    v = cc[0] * T.fphi[g * NP + c];
+                    for (int r2 = 0; r2 < D; ++r2) v -= cc[(1 + r2) * NQ] * T.fpsi[((size_t)r2 * NQ + g) * NP + c];
+                } else {
+                    const int c2 = c - NP, f = c2 / NFP, l = c2 - f * NFP;
+                    v = cc[(1 + D + f) * NQ] * T.ftheta[((size_t)f * NQ + g) * NFP + l];
+                }
+            }
+            const float hi = tf32_round(v);
+            Ah[core * 32 + lane] = hi;
+            Al[core * 32 + lane] = tf32_round(v - hi);
+        }
+        for (int core = warp; core < (NTN / 8) * (KC / 4); core += 4) {
+            const int n = (core / (KC / 4)) * 8 + rr, k = k0 + (core % (KC / 4)) * 4 + kq;
+            const float v = (n < NP && k < K) ? T.fdphi[(size_t)k * NP + n] : 0.f;
+            const float hi = tf32_round(v);
+            Bh[core * 32 + lane] = hi;
+            Bl[core * 32 + lane] = tf32_round(v - hi);
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const int nsteps = (min(KC, K - k0) + 7) / 8;
+            for (int s = 0; s < nsteps; ++s) {
+                const uint32_t off = s * 256;
+                const uint64_t ah = umma_desc(smem_u32(Ah) + off, 128, (KC / 4) * 128);
+                const uint64_t bh = umma_desc(smem_u32(Bh) + off, 128, (KC / 4) * 128);
+                const uint64_t al = umma_desc(smem_u32(Al) + off, 128, (KC / 4) * 128);
+                const uint64_t bl = umma_desc(smem_u32(Bl) + off, 128, (KC / 4) * 128);
+                uint32_t acc = (k0 > 0 || s > 0) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                             :: "r"(tmem), "l"(ah), "l"(bh), "r"(idesc), "r"(acc));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
+                             :: "r"(tmem), "l"(ah), "l"(bl), "r"(idesc));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
+                             :: "r"(tmem), "l"(al), "l"(bh), "r"(idesc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar));
+        }
+        if (!mbar_wait_bounded(bar, phase, 1 << 24)) {
+            ok = false;
+            if (tid == 0) atomicOr(status, 4);
+            mbar_wait_bounded(bar, phase, 1 << 24);
+        }
+        phase ^= 1;
+        __syncthreads();
+        if (!ok) break;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok) {
+        const int r = m0 + warp * 32 + lane;
+        const int ab = r / NCB, c = r - ab * NCB, a = ab / M, b = ab - a * M;
+        const double detJ = A.geo[e * GEO];
+        double* A11 = A.R.a11 + e * A.R.a11_es;
+        float* A12 = A.R.a12 + e * A.R.a12_es;
+#pragma unroll 1
+        for (int c0 = 0; c0 < NTN; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                           "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                         : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (r < MR) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int i = c0 + j;
+                    if (i >= NP) continue;
+                    const float x = __uint_as_float(v[j]);
+                    const int64_t row = a * NP + i;
+                    if (c < NP) {
+                        double w = (double)x;
+                        if (a == b) w += detJ / A.a_ii * T.mhat[i * NP + c];
+                        A11[row * A.R.a11_rs + b * NP + c] = w;
+                    } else {
+                        const int c2 = c - NP, f = c2 / NFP, l = c2 - f * NFP;
+                        A12[row * A.R.a12_rs + (f * M + b) * NFP + l] = x;
+                    }
                 }
             }
         }
