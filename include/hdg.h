@@ -305,7 +305,8 @@ int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* 
  *  - FP64 form: the elimination kernel's panel width (16 or 8 columns) and
  *    the residency it is compiled for (2 or 1 CTAs per SM); results differ
  *    only by rounding order;
- *  - mixed form: the volume contraction as FP32 SIMT (blocks_mode 0) or
+ *  - mixed form: the elimination kernel's residency (2 or 3 CTAs per SM),
+ *    the volume contraction as FP32 SIMT (blocks_mode 0) or
  *    3xTF32 tensor cores (1, 3-D), and, when requested as HDG_PREC_MIXED,
  *    the Schur product as FP32 SIMT (schur_mode 0) or 3xTF32 tensor cores
  *    (2) — all FP32-accurate; TF32 / 3xTF32 requested explicitly are kept.
@@ -314,9 +315,9 @@ int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* 
  * left assembled is that of the last candidate timed. */
 typedef struct {
     int elim_nb, elim_minb, schur_mode;   /* the chosen variant */
-    int blocks_mode;
+    int blocks_mode, elim_mixed_minb;
     int n_cand;                           /* candidates timed (<= 8) */
-    int cand[8][4];                       /* (elim_nb, elim_minb, schur_mode, blocks_mode) of each candidate */
+    int cand[8][5];                       /* (elim_nb, elim_minb, schur_mode, blocks_mode, elim_mixed_minb) */
     double ms[8];                         /* mean time of one linearize + condense, ms */
 } hdg_tune;
 int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* UH, const double* Ustar,

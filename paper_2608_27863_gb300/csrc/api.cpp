@@ -320,13 +320,14 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (reps < 1 || reps > 100) return fail(h, HDG_EINVAL, "reps must be in 1..100");
     // candidates: variants that compute the same quantities to the same accuracy
-    int cand[8][4];
+    int cand[8][5];
     int n = 0;
     if (h->precision == HDG_PREC_FP64) {
         const int nbs[2] = {16, 8}, minbs[2] = {2, 1};
         for (int a = 0; a < 2; ++a)
             for (int b = 0; b < 2; ++b) {
-                cand[n][0] = nbs[a]; cand[n][1] = minbs[b]; cand[n][2] = h->schur_mode; cand[n][3] = h->blocks_mode; ++n;
+                cand[n][0] = nbs[a]; cand[n][1] = minbs[b]; cand[n][2] = h->schur_mode; cand[n][3] = h->blocks_mode;
+                cand[n][4] = h->elim_mixed_minb; ++n;
             }
     } else {
         // FP32 SIMT and 3xTF32 tensor-core products are both FP32-accurate: the volume
@@ -336,8 +337,10 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
             if (!free_schur && sm != 0) continue;
             for (int bm : {0, 1}) {
                 if (bm == 1 && h->d != 3) continue;
-                cand[n][0] = h->elim_nb; cand[n][1] = h->elim_minb; cand[n][2] = free_schur ? sm : h->schur_mode;
-                cand[n][3] = bm; ++n;
+                for (int mb : {2, 3}) {
+                    cand[n][0] = h->elim_nb; cand[n][1] = h->elim_minb; cand[n][2] = free_schur ? sm : h->schur_mode;
+                    cand[n][3] = bm; cand[n][4] = mb; ++n;
+                }
             }
         }
     }
@@ -351,6 +354,7 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
         h->elim_minb = cand[c][1];
         h->schur_mode = cand[c][2];
         h->blocks_mode = cand[c][3];
+        h->elim_mixed_minb = cand[c][4];
         if ((rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr))) break;   // warm-up
         cudaEventRecord(ev[0], h->stream);
         for (int r = 0; r < reps && rc == HDG_OK; ++r) rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr);
@@ -370,12 +374,13 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
     h->elim_minb = cand[best][1];
     h->schur_mode = cand[best][2];
     h->blocks_mode = cand[best][3];
+    h->elim_mixed_minb = cand[best][4];
     if (out) {
         out->elim_nb = h->elim_nb; out->elim_minb = h->elim_minb; out->schur_mode = h->schur_mode;
-        out->blocks_mode = h->blocks_mode;
+        out->blocks_mode = h->blocks_mode; out->elim_mixed_minb = h->elim_mixed_minb;
         out->n_cand = n;
         for (int c = 0; c < 8; ++c) {
-            for (int k = 0; k < 4; ++k) out->cand[c][k] = c < n ? cand[c][k] : 0;
+            for (int k = 0; k < 5; ++k) out->cand[c][k] = c < n ? cand[c][k] : 0;
             out->ms[c] = c < n ? ms[c] : 0.0;
         }
     }
@@ -385,13 +390,16 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
 int hdg_set_tuning(hdg_handle h, const hdg_tune* t) {
     if (!h || !t) return fail(h, HDG_EINVAL, "NULL argument");
     if ((t->elim_nb != 8 && t->elim_nb != 16) || (t->elim_minb != 1 && t->elim_minb != 2) ||
-        t->schur_mode < 0 || t->schur_mode > 2 || t->blocks_mode < 0 || t->blocks_mode > 1)
-        return fail(h, HDG_EINVAL, "elim_nb 8 or 16, elim_minb 1 or 2, schur_mode 0..2, blocks_mode 0..1");
+        t->schur_mode < 0 || t->schur_mode > 2 || t->blocks_mode < 0 || t->blocks_mode > 1 ||
+        (t->elim_mixed_minb != 2 && t->elim_mixed_minb != 3))
+        return fail(h, HDG_EINVAL, "elim_nb 8 or 16, elim_minb 1 or 2, schur_mode 0..2, blocks_mode 0..1, "
+                                   "elim_mixed_minb 2 or 3");
     if (h->precision == HDG_PREC_MIXED && h->prec_req != HDG_PREC_MIXED && t->schur_mode != h->schur_mode)
         return fail(h, HDG_EINVAL, "the Schur precision was fixed by hdg_set_params");
     h->elim_nb = t->elim_nb;
     h->elim_minb = t->elim_minb;
     h->blocks_mode = t->blocks_mode;
+    h->elim_mixed_minb = t->elim_mixed_minb;
     if (h->precision == HDG_PREC_MIXED) h->schur_mode = t->schur_mode;
     return HDG_OK;
 }

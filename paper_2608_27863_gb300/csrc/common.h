@@ -196,6 +196,7 @@ struct hdg_ctx {
     bool have_system = false;
     int elim_minb = 2;                     // k_elim variant: resident CTAs per SM the kernel is built for
     int elim_nb = 16;                      // k_elim variant: panel width (16 or 8)
+    int elim_mixed_minb = 2;               // k_elim_mixed variant: resident CTAs per SM (2 or 3)
 
     // instrumentation: event pairs around kernel launches
     bool prof = false;

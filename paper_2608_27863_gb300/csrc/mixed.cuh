@@ -95,8 +95,8 @@ constexpr int elim_mixed_smem_bytes() {
            (C::NT * NB + C::NU * NB + NB * 64 + NB) * 4;      // bottom panel, top panel copy, staging, pivot row (FP32)
 }
 
-template <class C, int NB, int NTH>
-__global__ void __launch_bounds__(NTH, 2) k_elim_mixed(Regions<float> R, int64_t e0, int32_t* status) {
+template <class C, int NB, int NTH, int MINB = 2>
+__global__ void __launch_bounds__(NTH, MINB) k_elim_mixed(Regions<float> R, int64_t e0, int32_t* status) {
     constexpr int NU = C::NU, NT = C::NT;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t el = blockIdx.x, e = e0 + el;
@@ -553,7 +553,8 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
     HDG_CK(cudaFuncSetAttribute(kface, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
     if (C::D == 3)
         HDG_CK(cudaFuncSetAttribute(k_blocks_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, BlkTC<C>::smem_bytes()));
-    HDG_CK(cudaFuncSetAttribute(k_elim_mixed<C, NB, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
+    HDG_CK(cudaFuncSetAttribute(k_elim_mixed<C, NB, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
+    HDG_CK(cudaFuncSetAttribute(k_elim_mixed<C, NB, 256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
     cudaStream_t st = h->stream;
     HDG_CK(cudaMemsetAsync(h->d_vals32, 0, sizeof(float) * h->nnzb * C::BS * C::BS, st));
     HDG_CK(cudaMemsetAsync(h->d_g, 0, sizeof(double) * h->F * C::BS, st));
@@ -588,7 +589,11 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
         }
         prof_end(h);
         prof_begin(h, HDG_K_ELIM);
-        k_elim_mixed<C, NB, 256><<<(unsigned)ne, 256, sm_elim, st>>>(RM, e0, h->d_status);
+        // variant chosen by the autotuner: built for 2 or 3 resident CTAs per SM
+        if (h->elim_mixed_minb == 3)
+            k_elim_mixed<C, NB, 256, 3><<<(unsigned)ne, 256, sm_elim, st>>>(RM, e0, h->d_status);
+        else
+            k_elim_mixed<C, NB, 256, 2><<<(unsigned)ne, 256, sm_elim, st>>>(RM, e0, h->d_status);
         prof_end(h);
         prof_begin(h, HDG_K_SCHUR);
         if (h->schur_mode == 0) {

@@ -142,8 +142,8 @@ def test_autotune_mixed_picks_fp32_accurate_schur():
     H.hdg_set_params(run.h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s,
                      precision=H.HDG_PREC_MIXED_TF32)
     rep = H.hdg_autotune(run.h, run.U, run.Q, run.UH, run.Ustar, run.nu, P.dt, P.a_ii, reps=1)
-    assert len(rep["candidates"]) == 2 and rep["schur_mode"] == 1
-    assert {c[3] for c, _ in rep["candidates"]} == {0, 1}
+    assert len(rep["candidates"]) == 4 and rep["schur_mode"] == 1
+    assert {c[3] for c, _ in rep["candidates"]} == {0, 1} and {c[4] for c, _ in rep["candidates"]} == {2, 3}
     run.close()
 
 
