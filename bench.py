@@ -35,7 +35,8 @@ METRIC = "HDG linearize+condense elements/s & % of FP64/TC peak; mixed vs FP64 a
 # capture of the unchanged kernel on the 8^3 hex p=2 case (512 elements, above
 # L2); every CTA works on its own element, so traffic scales with the element
 # count of a launch.
-DRAM_BYTES_PER_ELEMENT = {("elim", 3, 2): 16.45e6}
+# Keyed by (kernel, d, p, elimination panel width).
+DRAM_BYTES_PER_ELEMENT = {("elim", 3, 2, 16): 16.45e6}
 L2_BYTES = 129 * 1024 * 1024
 
 # fn/kw: the synth generator; mixed_only: the FP64 arrays would not fit in HBM, so only
@@ -295,7 +296,11 @@ def run_ours(args, rank, world, local_rank):
 
     def tune():
         # the project's autotuner picks among equivalent kernel variants on these inputs (untimed)
-        if args.no_autotune:
+        if args.no_autotune or args.elim_nb:
+            if args.elim_nb:      # a fixed variant (profiling runs)
+                H.hdg_set_tuning(h, elim_nb=args.elim_nb, elim_minb=2,
+                                 schur_mode={"fp32": 0, "tf32": 1, "3xtf32": 2}[args.mixed_prec],
+                                 blocks_mode=1 if m.dim == 3 else 0, elim_mixed_minb=2)
             return None
         rep = H.hdg_autotune(h, U, Q, UH, Us, nu, P.dt, P.a_ii, reps=1)
         return {k: rep[k] for k in ("elim_nb", "elim_minb", "schur_mode", "blocks_mode", "elim_mixed_minb")}
@@ -400,6 +405,7 @@ def run_ours(args, rank, world, local_rank):
         H.hdg_destroy(h)
         return out
     fl = flop_counts(m.dim, P.p)
+    nb_used = (tuning.get("fp64") or {}).get("elim_nb", args.elim_nb or 16)
     kern = {}
     for k, (ms, n) in prof.items():
         if n:
@@ -407,6 +413,7 @@ def run_ours(args, rank, world, local_rank):
     kern["elim"]["tflops"] = fl["elim"] * E / (prof["elim"][0] / args.steps) / 1e9
     kern["blocks"]["tflops"] = fl["blocks"] * E / (prof["blocks"][0] / args.steps) / 1e9
     dom = max(("elim", "blocks"), key=lambda k: prof[k][0])
+    traffic_key = (dom, m.dim, P.p, nb_used if dom == "elim" else 0)
     avg_launch_ms = prof[dom][0] / max(prof[dom][1], 1)
     per_launch_elems = E / max(prof[dom][1] / args.steps, 1)
     achieved = fl[dom] * per_launch_elems / (avg_launch_ms * 1e-3) / 1e12
@@ -436,8 +443,8 @@ def run_ours(args, rank, world, local_rank):
                    "precision": "fp64", "l2": "flushed between timed steps (256 MiB write)"},
         "roofline": {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": (DRAM_BYTES_PER_ELEMENT[(dom, m.dim, P.p)] * per_launch_elems
-                                 if (dom, m.dim, P.p) in DRAM_BYTES_PER_ELEMENT else None),
+                     "traffic": (DRAM_BYTES_PER_ELEMENT[traffic_key] * per_launch_elems
+                                 if traffic_key in DRAM_BYTES_PER_ELEMENT else None),
                      "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_%s launch on the "
                                        "8^3 case, per element, times the elements of one launch" % dom,
                      "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz (derived); cuBLAS DGEMM "
@@ -540,6 +547,8 @@ def main():
     ap.add_argument("--no-newton", action="store_true")
     ap.add_argument("--mixed-prec", choices=["fp32", "tf32", "3xtf32"], default="3xtf32")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--elim-nb", type=int, choices=[8, 16], default=None,
+                    help="fix the FP64 elimination panel width instead of autotuning (profiling runs)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

@@ -196,7 +196,8 @@ def test_autotuned_variants_keep_parity():
     assert len(cands) == 4 and all(ms > 0 for _, ms in cands)
     assert min(ms for _, ms in cands) == [ms for c, ms in cands if c[:2] == (rep["elim_nb"], rep["elim_minb"])][0]
     run.close()
-    for (nb, minb, _), _ms in cands:
+    for cand, _ms in cands:
+        nb, minb = cand[0], cand[1]
         h = create(P)
         H.hdg_set_tuning(h, elim_nb=nb, elim_minb=minb)
         compare_handle = GpuRun(P, h)
@@ -247,4 +248,17 @@ def test_nodal_inflow_profile():
     ubc = np.broadcast_to(np.asarray(P.ubc)[None, :, None], (cn.n_faces, 4, 3)).copy()
     ubc[:, 1, :] *= 1.0 + 0.1 * synth.uniform(3, ubc[:, 1, :].size).reshape(ubc[:, 1, :].shape)
     P.ubc = ubc
+    compare(P, check_matvec=True)
+
+
+@pytest.mark.parametrize("dim,p", [(2, 3), (3, 2)])
+def test_single_element_box(dim, p):
+    """The degenerate mesh of one element whose faces are all boundary faces."""
+    mesh = synth.box_mesh(dim, (1,) * dim, (0.0,) * dim, (1.0,) * dim, (False,) * dim)
+    ub = synth.freestream(dim, 1.4, 0.5)
+    fun = lambda x: synth.conserved(1.0 + 0.1 * np.sin(3 * x[..., 0]), [0.3 + 0.1 * x[..., 1]] +
+                                    [0.05 * x[..., 0]] * (dim - 1), 2.857 + 0.1 * x[..., 0], 1.4)
+    U, Q, UH, Ustar = synth._stage_state(mesh, p, fun, ub, 3, 1e-3, 1e-2, 1e-3)
+    P = synth.Problem("one-element", mesh, p, 1.4, 50.0, 0.72, 0.5, 3.0, 5e-2, 0.4, 1, 1.4042, 0.40417,
+                      U, Q, UH, Ustar, None, ub)
     compare(P, check_matvec=True)

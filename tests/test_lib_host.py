@@ -134,3 +134,32 @@ def test_argument_errors(H):
     assert rc == H.HDG_EINVAL
     assert "assembled" in H.hdg_last_error(h) or "device" in H.hdg_last_error(h)
     H.hdg_destroy(h)
+
+
+def test_empty_and_degenerate_meshes(H):
+    mesh = synth.box_mesh(2, (3, 3), (0, 0), (1, 1), (True, True))
+    empty = np.zeros((0, 4), dtype=np.int64)
+    with pytest.raises(H.HDGError) as ex:          # no elements
+        H.hdg_create_host(2, mesh.vert_xyz, empty, mesh.periodic_map, None, 2, 1.4, 100.0, 0.72, 0.3)
+    assert ex.value.code == H.HDG_EINVAL
+    flat = mesh.vert_xyz.copy()
+    flat[:, 1] = 0.0                                # zero-area elements
+    with pytest.raises(H.HDGError) as ex:
+        H.hdg_create_host(2, flat, mesh.elem_vert, mesh.periodic_map, None, 2, 1.4, 100.0, 0.72, 0.3)
+    assert ex.value.code in (H.HDG_EINVAL, H.HDG_EUNSUPPORTED)
+    bad = mesh.elem_vert.copy()
+    bad[0, 0] = mesh.n_vert + 5                     # vertex index out of range
+    with pytest.raises(H.HDGError) as ex:
+        H.hdg_create_host(2, mesh.vert_xyz, bad, mesh.periodic_map, None, 2, 1.4, 100.0, 0.72, 0.3)
+    assert ex.value.code == H.HDG_EINVAL
+
+
+def test_single_element_thick_mesh_is_rejected_or_consistent(H):
+    """An open box of one element (all faces boundary) is a valid mesh: four boundary faces."""
+    mesh = synth.box_mesh(2, (1, 1), (0, 0), (1, 1), (False, False))
+    h = H.hdg_create_host(2, mesh.vert_xyz, mesh.elem_vert, mesh.periodic_map, mesh.bnd_tag, 1, 1.4, 100.0, 0.72,
+                          0.3)
+    c = H.hdg_get_connectivity(h)
+    H.hdg_destroy(h)
+    assert c["f2e"].shape[0] == 4 and np.all(c["f2e"][:, 1] == -1)
+    assert np.array_equal(c["rowptr"], [0, 4, 8, 12, 16])
