@@ -36,7 +36,7 @@ METRIC = "HDG linearize+condense elements/s & % of FP64/TC peak; mixed vs FP64 a
 # L2); every CTA works on its own element, so traffic scales with the element
 # count of a launch.
 # Keyed by (kernel, d, p, elimination panel width).
-DRAM_BYTES_PER_ELEMENT = {("elim", 3, 2, 16): 16.45e6}
+DRAM_BYTES_PER_ELEMENT = {("elim", 3, 2, 16): 16.45e6, ("elim", 3, 2, 8): 30.84e6}
 L2_BYTES = 129 * 1024 * 1024
 
 # fn/kw: the synth generator; mixed_only: the FP64 arrays would not fit in HBM, so only
