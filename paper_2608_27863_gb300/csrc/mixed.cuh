@@ -683,7 +683,7 @@ template <class C>
 struct SchurTC {
     static constexpr int NT = C::NT, NU = C::NU;
     static constexpr int MT = 128, KC = 32;
-    static constexpr int NNT = (NT + 255) / 256;                          // column tiles
+    static constexpr int NNT = (NT + 127) / 128;                          // column tiles (<= 128 TMEM columns each)
     static constexpr int NTN = (((NT + NNT - 1) / NNT) + 15) / 16 * 16;   // columns per tile (mult. of 16)
     static constexpr int NMT = (NT + MT - 1) / MT;                        // row tiles
     static constexpr int TCOLS = NTN <= 32 ? 32 : NTN <= 64 ? 64 : NTN <= 128 ? 128 : 256;
@@ -719,10 +719,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase, 
     return done != 0;
 }
 
-template <int KC>
-__device__ __forceinline__ int core_off(int r, int k) {
-    return ((r >> 3) * (KC / 4) + (k >> 2)) * 32 + (r & 7) * 4 + (k & 3);
-}
 
 template <class C, bool SPLIT3>
 __global__ void __launch_bounds__(128) k_schur_tc(Regions<float> R, int64_t e0, int32_t* status) {
@@ -773,20 +769,22 @@ __global__ void __launch_bounds__(128) k_schur_tc(Regions<float> R, int64_t e0, 
     const uint32_t bar = smem_u32(mbar);
     uint32_t phase = 0;
     bool ok = true;
+    const int rr = lane >> 2, kq = lane & 3;          // position inside an 8 x 4 core matrix
     for (int k0 = 0; k0 < NU; k0 += KC) {
-        for (int idx = tid; idx < MT * KC; idx += 128) {
-            int r = idx / KC, k = idx - r * KC;
-            float v = (m0 + r < NT && k0 + k < NU) ? W[(m0 + r) * sw + k0 + k] : 0.f;
-            float hi = tf32_round(v);
-            Ah[core_off<KC>(r, k)] = hi;
-            if (SPLIT3) Al[core_off<KC>(r, k)] = tf32_round(v - hi);
+        // one core matrix per warp step: contiguous, conflict-free shared-memory stores
+        for (int core = warp; core < (MT / 8) * (KC / 4); core += 4) {
+            const int r = (core / (KC / 4)) * 8 + rr, k = (core % (KC / 4)) * 4 + kq;
+            const float v = (m0 + r < NT && k0 + k < NU) ? W[(m0 + r) * sw + k0 + k] : 0.f;
+            const float hi = tf32_round(v);
+            Ah[core * 32 + lane] = hi;
+            if (SPLIT3) Al[core * 32 + lane] = tf32_round(v - hi);
         }
-        for (int idx = tid; idx < NTN * KC; idx += 128) {
-            int k = idx / NTN, n = idx - k * NTN;
-            float v = (n0 + n < NT && k0 + k < NU) ? Z[(k0 + k) * sz + n0 + n] : 0.f;
-            float hi = tf32_round(v);
-            Bh[core_off<KC>(n, k)] = hi;
-            if (SPLIT3) Bl[core_off<KC>(n, k)] = tf32_round(v - hi);
+        for (int core = warp; core < (NTN / 8) * (KC / 4); core += 4) {
+            const int n = (core / (KC / 4)) * 8 + rr, k = (core % (KC / 4)) * 4 + kq;
+            const float v = (n0 + n < NT && k0 + k < NU) ? Z[(k0 + k) * sz + n0 + n] : 0.f;
+            const float hi = tf32_round(v);
+            Bh[core * 32 + lane] = hi;
+            if (SPLIT3) Bl[core * 32 + lane] = tf32_round(v - hi);
         }
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
