@@ -415,6 +415,10 @@ struct BlkShape {
     static constexpr int main_smem = KC * (NPP + NCBP + C::NCOEF);
     static constexpr int face_smem = C::NCOEF * C::NFQ + C::NFQ * NCB;
     static constexpr int smem = main_smem > face_smem ? main_smem : face_smem;
+    // FP32 form: the face terms of the interior block are summed over the faces in a
+    // [Np][Np] shared tile and added to the FP64 block once
+    static constexpr int face_acc_smem = face_smem + C::NP * C::NP;
+    static constexpr int smem_f32 = main_smem > face_acc_smem ? main_smem : face_acc_smem;
 };
 
 // VOL = false skips the volume contraction (done on tensor cores by
@@ -536,6 +540,12 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
     TL* A22 = A.R.a22 + el * A.R.a22_es;
     TA* Fc = sm;                           // [NCOEF][Nfq]
     TA* Tt = Fc + NCOEF * NFQ;             // [Nfq][NCB]
+    constexpr bool FACC = sizeof(TA) == 4;  // FP32 form: sum the At face terms in shared memory
+    TA* Acc = Tt + NFQ * NCB;              // [Np][Np] (FP32 form only)
+    if (FACC) {
+        for (int idx = tid; idx < NP * NP; idx += NTH) Acc[idx] = (TA)0;
+        __syncthreads();
+    }
     const double* NW = G + 1 + D * D;
     const double* Jg = G + 1;
     (void)Jg;
@@ -584,7 +594,10 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
                 if (a == b) v += taun * vu;
                 const int col = b * NP + c;
                 A21[trow * A.R.a21_rs + col] = flux_row ? (TL)v : (TL)(cu * nrmt * vu);
-                A11[irow * A.R.a11_rs + col] += A.dt * (double)v;
+                if (FACC)   // one thread per (node, column) within a face; faces run one after another
+                    Acc[T.fnode[f * NFP + lam] * NP + c] += dtt * v;
+                else
+                    A11[irow * A.R.a11_rs + col] += A.dt * (double)v;
             } else {
                 int c2 = c - NP, f2 = c2 / NFP, l2 = c2 - f2 * NFP;
                 const int col = (f2 * M + b) * NFP + l2;
@@ -595,6 +608,12 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
         }
         __syncthreads();
     }
+    if (FACC)
+        for (int idx = tid; idx < NP * NP; idx += NTH) {
+            const int i = idx / NP, c = idx - i * NP;
+            const TA v = Acc[idx];
+            if (v != (TA)0) A11[(a * NP + i) * A.R.a11_rs + b * NP + c] += (double)v;
+        }
 }
 
 // ----------------------------------------------------------------------------

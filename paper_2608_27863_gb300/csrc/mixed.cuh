@@ -461,25 +461,47 @@ __global__ void __launch_bounds__(NTH) k_recover_r(Regions<TL> R, RecArgs A) {
     const double* U11 = R.a11 + e * R.a11_es;
     const TL* Z = R.a12 + e * R.a12_es;
     const double* z = R.rt + e * R.rt_es;
+    // w = Z dUhat + z: each lane sums its products in the storage type (Z is FP32), the
+    // lanes' partial sums are combined in FP64 (FP64 work would bound the kernel on GB300)
     for (int i = warp; i < NU; i += NTH / 32) {
         const TL* row = Z + (size_t)i * R.a12_rs;
-        double s = 0.0;
-        for (int c = lane; c < NT; c += 32) s = fma((double)row[c], duh[c], s);
+        TL p = (TL)0;
+        for (int c = lane; c < NT; c += 32) p = fma(row[c], (TL)duh[c], p);
+        double s = (double)p;
         for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
         if (lane == 0) w[i] = s + z[i * R.rt_rs];
     }
     __syncthreads();
-    if (warp == 0) {
-        for (int i = NU - 1; i >= 0; --i) {
-            const double* row = U11 + (size_t)i * R.a11_rs;
-            double s = 0.0;
-            for (int j = i + 1 + lane; j < NU; j += 32) s = fma(row[j], x[j], s);
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-            if (lane == 0) x[i] = (w[i] - s) / row[i];
-            __syncwarp();
+    // x = U^{-1} w (FP64): 32-row diagonal blocks solved by warp 0 from registers, the
+    // rows above updated with one dot product per row and thread
+#pragma unroll 1
+    for (int k1 = NU; k1 > 0; k1 -= 32) {
+        const int k0 = max(0, k1 - 32), nb = k1 - k0;
+        if (warp == 0) {
+            double ur[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) ur[j] = (lane < nb && j < nb) ? U11[(size_t)(k0 + lane) * R.a11_rs + k0 + j] : 0.0;
+            double v = lane < nb ? w[k0 + lane] : 0.0;
+#pragma unroll
+            for (int j = 31; j >= 0; --j) {
+                if (j < nb) {
+                    if (lane == j) v = v / ur[j];
+                    const double xj = __shfl_sync(0xffffffffu, v, j);
+                    if (lane < j) v = fma(-ur[j], xj, v);
+                }
+            }
+            if (lane < nb) x[k0 + lane] = v;
         }
+        __syncthreads();
+#pragma unroll 1
+        for (int r = tid; r < k0; r += NTH) {
+            const double* row = U11 + (size_t)r * R.a11_rs + k0;
+            double s = 0.0;
+            for (int j = 0; j < nb; ++j) s = fma(row[j], x[k0 + j], s);
+            w[r] -= s;
+        }
+        __syncthreads();
     }
-    __syncthreads();
     for (int i = tid; i < NU; i += NTH) A.dU[e * NU + i] = -x[i];
     const double detJ = geo[0];
     const double* Jinv = geo + 1;
@@ -546,7 +568,7 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
     auto kblk = k_blocks<C, BC::TY, BC::TX, BC::KC, float, float>;
     auto kface = k_blocks<C, BC::TY, BC::TX, BC::KC, float, float, false>;
     const size_t sm_point = sizeof(double) * point_smem_doubles<C>();
-    const size_t sm_blk = sizeof(float) * BS_::smem;
+    const size_t sm_blk = sizeof(float) * BS_::smem_f32;
     const size_t sm_elim = elim_mixed_smem_bytes<C, NB>();
     HDG_CK(cudaFuncSetAttribute(k_point<C, PT, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_point));
     HDG_CK(cudaFuncSetAttribute(kblk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
