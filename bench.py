@@ -65,7 +65,7 @@ def make_problem(name, cpu_sample=False):
 # ----------------------------------------------------------------------------
 # algorithmic FLOP counts per element (the executed reduced-structure counts)
 # ----------------------------------------------------------------------------
-def flop_counts(d, p):
+def flop_counts(d, p, sum_factorised=False):
     m, n1, q1 = d + 2, p + 1, p + 2
     Np, Nq, nf, Nfp, Nfq = n1 ** d, q1 ** d, 2 * d, n1 ** (d - 1), q1 ** (d - 1)
     NU, NT = m * Np, nf * m * Nfp
@@ -73,7 +73,12 @@ def flop_counts(d, p):
     elim = sum(2 * (NR - k - 1) * (NC - k - 1) + (NR - k - 1) for k in range(NU))
     NCB = Np + nf * Nfp
     K = d * Nq
-    blocks = m * m * (2 * Np * NCB * K                 # contraction GEMM
+    if sum_factorised:       # one 1-D contraction per axis, per column and direction
+        axes = q1 * q1 * n1 * q1 + q1 * n1 * n1 * q1 + n1 ** 3 * q1 if d == 3 else q1 * n1 * q1 + n1 * n1 * q1
+        contraction = 2 * axes * NCB * d
+    else:
+        contraction = 2 * Np * NCB * K
+    blocks = m * m * (contraction                       # contraction
                       + K * (2 * (1 + d) * Np + nf * Nfp)  # generated operand
                       + nf * (2 * Nfq * NCB * (d + 1) + 2 * Nfp * NCB * Nfq))  # face terms
     return {"elim": elim, "blocks": blocks, "total": elim + blocks}
@@ -218,6 +223,26 @@ def fp64_peak_tflops(torch):
     return 2 * n ** 3 / best / 1e9
 
 
+# ----------------------------------------------------------------------------
+# replicas under torchrun: every rank runs the whole workload (elements are
+# independent, no data-path collective); the step time is the maximum over ranks
+# ----------------------------------------------------------------------------
+def max_over_ranks(t_ms, world, device):
+    """The largest of the ranks' times (ms); identity on one rank."""
+    if world <= 1:
+        return t_ms
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_ms], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_throughput(world, n_elem, steps, t_ms):
+    """Whole-job elements/s: every rank processed n_elem elements per step."""
+    return world * n_elem * steps / (t_ms * 1e-3)
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -286,11 +311,8 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         prof = H.hdg_profile_read(h)
         H.hdg_profile(h, False)
-        t_ms = sum(times)
+        t_ms = max_over_ranks(sum(times), world, dev)
         if world > 1:
-            tt = torch.tensor([t_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t_ms = float(tt.item())
             dist.barrier()
         return t_ms, prof, clk.summary()
 
@@ -303,7 +325,8 @@ def run_ours(args, rank, world, local_rank):
                                  blocks_mode=1 if m.dim == 3 else 0, elim_mixed_minb=2)
             return None
         rep = H.hdg_autotune(h, U, Q, UH, Us, nu, P.dt, P.a_ii, reps=1)
-        return {k: rep[k] for k in ("elim_nb", "elim_minb", "schur_mode", "blocks_mode", "elim_mixed_minb")}
+        return {k: rep[k] for k in ("elim_nb", "elim_minb", "schur_mode", "blocks_mode", "elim_mixed_minb",
+                                    "blocks64_mode")}
 
     # FP64 form (the headline value); skipped when its arrays would not fit in HBM
     dgemm = fp64_peak_tflops(torch)
@@ -356,10 +379,7 @@ def run_ours(args, rank, world, local_rank):
         e.record(stream)
         e.synchronize()
         e2e_ms += s.elapsed_time(e)
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
 
     if pool is not None:
         n_sample = make_problem(args.workload, cpu_sample=True).mesh.n_elem if "cpu" in wl else m.n_elem
@@ -404,8 +424,9 @@ def run_ours(args, rank, world, local_rank):
             out["cpu_baseline"] = cpu
         H.hdg_destroy(h)
         return out
-    fl = flop_counts(m.dim, P.p)
-    nb_used = (tuning.get("fp64") or {}).get("elim_nb", args.elim_nb or 16)
+    t64 = tuning.get("fp64") or {}
+    fl = flop_counts(m.dim, P.p, sum_factorised=t64.get("blocks64_mode", 1) == 1)
+    nb_used = t64.get("elim_nb", args.elim_nb or 16)
     kern = {}
     for k, (ms, n) in prof.items():
         if n:
@@ -420,8 +441,8 @@ def run_ours(args, rank, world, local_rank):
     smmax = clocks.get("sm_max_mhz") or 2070.0
     peak = fp64_peak_derived(smmax)
     launches = sum(n for _, n in prof.values()) / args.steps
-    value = world * E * args.steps / (t_ms * 1e-3)
-    mixed = {"value": world * E * args.steps / (tm_ms * 1e-3), "unit": "elements/s", "ms_per_step": tm_ms / args.steps,
+    value = replica_throughput(world, E, args.steps, t_ms)
+    mixed = {"value": replica_throughput(world, E, args.steps, tm_ms), "unit": "elements/s", "ms_per_step": tm_ms / args.steps,
              "speedup_vs_fp64_step": t_ms / tm_ms,
              "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
                          for k, v in prof_m.items() if v[1]},
@@ -453,7 +474,7 @@ def run_ours(args, rank, world, local_rank):
         "gflops_total": fl["total"] * E * args.steps / (t_ms * 1e-3) / 1e9,
         "kernels": kern,
         "mixed": mixed,
-        "e2e": {"value": world * E * args.steps / (e2e_ms * 1e-3), "unit": "elements/s",
+        "e2e": {"value": replica_throughput(world, E, args.steps, e2e_ms), "unit": "elements/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
@@ -485,7 +506,7 @@ def mixed_only_line(args, world, E, P, m, h, tm_ms, prof_m, clocks_m, e2e_ms, h2
     kern = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
             for k, v in prof_m.items() if v[1]}
     return {
-        "metric": METRIC, "value": world * E * args.steps / (tm_ms * 1e-3), "unit": "elements/s", "n_gpus": world,
+        "metric": METRIC, "value": replica_throughput(world, E, args.steps, tm_ms), "unit": "elements/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tm_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "mixed", "data": "synthetic",
         "config": {"workload": args.workload, "elements_per_gpu": E, "degree": P.p, "dim": m.dim,
@@ -501,7 +522,7 @@ def mixed_only_line(args, world, E, P, m, h, tm_ms, prof_m, clocks_m, e2e_ms, h2
                                     "measured in this run: %.3f TFLOP/s; flops: the FP64 interior LU only" %
                                     (smmax, dgemm)},
         "kernels": kern,
-        "e2e": {"value": world * E * args.steps / (e2e_ms * 1e-3), "unit": "elements/s",
+        "e2e": {"value": replica_throughput(world, E, args.steps, e2e_ms), "unit": "elements/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": sum(n for _, n in prof_m.values()) / args.steps,
         "clocks": clocks_m,

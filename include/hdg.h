@@ -302,9 +302,11 @@ int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* 
  * the same quantities to the same accuracy on the caller's own inputs
  * (reps linearize + condense calls each, after one warm-up, CUDA events on
  * the handle's stream) and keeps the fastest for later calls:
- *  - FP64 form: the elimination kernel's panel width (16 or 8 columns) and
- *    the residency it is compiled for (2 or 1 CTAs per SM); results differ
- *    only by rounding order;
+ *  - FP64 form: the volume contraction as a dense GEMM (blocks64_mode 0)
+ *    or by sum factorisation over the tensor-product basis (1), the
+ *    elimination kernel's panel width (16 or 8 columns) and the residency it
+ *    is compiled for (2 or 1 CTAs per SM); results differ only by rounding
+ *    order;
  *  - mixed form: the elimination kernel's residency (2 or 3 CTAs per SM),
  *    the volume contraction as FP32 SIMT (blocks_mode 0) or
  *    3xTF32 tensor cores (1, 3-D), and, when requested as HDG_PREC_MIXED,
@@ -315,9 +317,10 @@ int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* 
  * left assembled is that of the last candidate timed. */
 typedef struct {
     int elim_nb, elim_minb, schur_mode;   /* the chosen variant */
-    int blocks_mode, elim_mixed_minb;
+    int blocks_mode, elim_mixed_minb, blocks64_mode;
     int n_cand;                           /* candidates timed (<= 8) */
-    int cand[8][5];                       /* (elim_nb, elim_minb, schur_mode, blocks_mode, elim_mixed_minb) */
+    int cand[8][6];                       /* (elim_nb, elim_minb, schur_mode, blocks_mode, elim_mixed_minb,
+                                             blocks64_mode) of each candidate */
     double ms[8];                         /* mean time of one linearize + condense, ms */
 } hdg_tune;
 int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* UH, const double* Ustar,

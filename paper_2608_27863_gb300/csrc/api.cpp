@@ -203,6 +203,7 @@ int create_device(hdg_ctx* h) {
     UP(h->tab.mu, t.mu); UP(h->tab.wf, t.wf); UP(h->tab.fnode, t.fnode); UP(h->tab.node_face, t.node_face);
     UP(h->tab.mhat, t.mhat); UP(h->tab.mf, t.mf); UP(h->tab.minv_c, t.minv_c); UP(h->tab.minv_e, t.minv_e);
     UP(h->tab.psi, t.psi); UP(h->tab.theta, t.theta); UP(h->tab.psi_f, t.psi_f); UP(h->tab.theta_f, t.theta_f);
+    UP(h->tab.b1, t.b1); UP(h->tab.d1, t.d1);
     auto f32 = [](const std::vector<double>& v) { return std::vector<float>(v.begin(), v.end()); };
     UP(h->tab.fphi, f32(t.phi)); UP(h->tab.fdphi, f32(t.dphi)); UP(h->tab.fpsi, f32(t.psi));
     UP(h->tab.ftheta, f32(t.theta)); UP(h->tab.fpsi_f, f32(t.psi_f)); UP(h->tab.ftheta_f, f32(t.theta_f));
@@ -320,15 +321,16 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (reps < 1 || reps > 100) return fail(h, HDG_EINVAL, "reps must be in 1..100");
     // candidates: variants that compute the same quantities to the same accuracy
-    int cand[8][5];
+    int cand[8][6];
     int n = 0;
     if (h->precision == HDG_PREC_FP64) {
         const int nbs[2] = {16, 8}, minbs[2] = {2, 1};
-        for (int a = 0; a < 2; ++a)
-            for (int b = 0; b < 2; ++b) {
-                cand[n][0] = nbs[a]; cand[n][1] = minbs[b]; cand[n][2] = h->schur_mode; cand[n][3] = h->blocks_mode;
-                cand[n][4] = h->elim_mixed_minb; ++n;
-            }
+        for (int bm64 : {1, 0})
+            for (int a = 0; a < 2; ++a)
+                for (int b = 0; b < 2; ++b) {
+                    cand[n][0] = nbs[a]; cand[n][1] = minbs[b]; cand[n][2] = h->schur_mode; cand[n][3] = h->blocks_mode;
+                    cand[n][4] = h->elim_mixed_minb; cand[n][5] = bm64; ++n;
+                }
     } else {
         // FP32 SIMT and 3xTF32 tensor-core products are both FP32-accurate: the volume
         // contraction always, the Schur product unless TF32 / 3xTF32 was requested explicitly
@@ -339,7 +341,7 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
                 if (bm == 1 && h->d != 3) continue;
                 for (int mb : {2, 3}) {
                     cand[n][0] = h->elim_nb; cand[n][1] = h->elim_minb; cand[n][2] = free_schur ? sm : h->schur_mode;
-                    cand[n][3] = bm; cand[n][4] = mb; ++n;
+                    cand[n][3] = bm; cand[n][4] = mb; cand[n][5] = h->blocks64_mode; ++n;
                 }
             }
         }
@@ -355,6 +357,7 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
         h->schur_mode = cand[c][2];
         h->blocks_mode = cand[c][3];
         h->elim_mixed_minb = cand[c][4];
+        h->blocks64_mode = cand[c][5];
         if ((rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr))) break;   // warm-up
         cudaEventRecord(ev[0], h->stream);
         for (int r = 0; r < reps && rc == HDG_OK; ++r) rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr);
@@ -375,12 +378,14 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
     h->schur_mode = cand[best][2];
     h->blocks_mode = cand[best][3];
     h->elim_mixed_minb = cand[best][4];
+    h->blocks64_mode = cand[best][5];
     if (out) {
         out->elim_nb = h->elim_nb; out->elim_minb = h->elim_minb; out->schur_mode = h->schur_mode;
         out->blocks_mode = h->blocks_mode; out->elim_mixed_minb = h->elim_mixed_minb;
+        out->blocks64_mode = h->blocks64_mode;
         out->n_cand = n;
         for (int c = 0; c < 8; ++c) {
-            for (int k = 0; k < 5; ++k) out->cand[c][k] = c < n ? cand[c][k] : 0;
+            for (int k = 0; k < 6; ++k) out->cand[c][k] = c < n ? cand[c][k] : 0;
             out->ms[c] = c < n ? ms[c] : 0.0;
         }
     }
@@ -391,15 +396,16 @@ int hdg_set_tuning(hdg_handle h, const hdg_tune* t) {
     if (!h || !t) return fail(h, HDG_EINVAL, "NULL argument");
     if ((t->elim_nb != 8 && t->elim_nb != 16) || (t->elim_minb != 1 && t->elim_minb != 2) ||
         t->schur_mode < 0 || t->schur_mode > 2 || t->blocks_mode < 0 || t->blocks_mode > 1 ||
-        (t->elim_mixed_minb != 2 && t->elim_mixed_minb != 3))
+        (t->elim_mixed_minb != 2 && t->elim_mixed_minb != 3) || t->blocks64_mode < 0 || t->blocks64_mode > 1)
         return fail(h, HDG_EINVAL, "elim_nb 8 or 16, elim_minb 1 or 2, schur_mode 0..2, blocks_mode 0..1, "
-                                   "elim_mixed_minb 2 or 3");
+                                   "elim_mixed_minb 2 or 3, blocks64_mode 0..1");
     if (h->precision == HDG_PREC_MIXED && h->prec_req != HDG_PREC_MIXED && t->schur_mode != h->schur_mode)
         return fail(h, HDG_EINVAL, "the Schur precision was fixed by hdg_set_params");
     h->elim_nb = t->elim_nb;
     h->elim_minb = t->elim_minb;
     h->blocks_mode = t->blocks_mode;
     h->elim_mixed_minb = t->elim_mixed_minb;
+    h->blocks64_mode = t->blocks64_mode;
     if (h->precision == HDG_PREC_MIXED) h->schur_mode = t->schur_mode;
     return HDG_OK;
 }

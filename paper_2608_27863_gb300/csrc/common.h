@@ -45,6 +45,7 @@ struct RefTables {
     std::vector<double> minv_c, minv_e;             // [d][Np][Np], [nf][Np][Nfp]
     std::vector<double> psi, theta;                 // [d][Nq][Np], [nf][Nq][Nfp]
     std::vector<double> psi_f, theta_f;             // [nf][d][Nfq][Np], [nf][nf][Nfq][Nfp]
+    std::vector<double> b1, d1;                     // [p+2][p+1] 1-D basis values / derivatives at Gauss points
 };
 void build_ref_tables(int d, int p, RefTables& t);
 
@@ -76,6 +77,7 @@ struct DeviceTables {
     double* mhat; double* mf;
     double* minv_c; double* minv_e;
     double* psi; double* theta; double* psi_f; double* theta_f;
+    double* b1; double* d1;          // 1-D tables of the tensor-product basis (sum factorisation)
     // float copies for the mixed form's FP32 contraction
     float* fphi; float* fdphi; float* fpsi; float* ftheta; float* fpsi_f; float* ftheta_f; float* fmu; float* fmf;
 };
@@ -184,6 +186,7 @@ struct hdg_ctx {
     int sys_prec = HDG_PREC_FP64;          // precision of the assembled system
     int schur_mode = 0;                    // mixed Schur product: 0 FP32 SIMT, 1 TF32, 2 3xTF32 tensor cores
     int blocks_mode = 1;                   // mixed volume contraction: 0 FP32 SIMT, 1 3xTF32 tensor cores (3-D)
+    int blocks64_mode = 1;                 // FP64 volume contraction: 0 dense GEMM, 1 sum factorisation
     double* d_m11 = nullptr;               // [E][NU][NU] interior block / its LU factors (FP64)
     float* d_m12 = nullptr;                // [E][NU][NT] Bt, then Z = L^{-1} P Bt
     double* d_mrt = nullptr;               // [E][NU] Rt, then z

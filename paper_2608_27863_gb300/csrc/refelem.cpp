@@ -144,6 +144,8 @@ void build_ref_tables(int d, int p, RefTables& t) {
     for (int g = 0; g < q1; ++g) L.eval(t.gq1[g], &B[(size_t)g * n1], &Dd[(size_t)g * n1]);
     L.eval(-1.0, &Be[0], &De[0]);
     L.eval(1.0, &Be[n1], &De[n1]);
+    t.b1 = B;
+    t.d1 = Dd;
 
     auto digit = [](int idx, int base, int r) { for (int k = 0; k < r; ++k) idx /= base; return idx % base; };
 

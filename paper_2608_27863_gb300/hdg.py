@@ -381,8 +381,8 @@ def hdg_tgv_diagnostics(h, U, Q):
 
 class hdg_tune(ctypes.Structure):
     _fields_ = [("elim_nb", ctypes.c_int), ("elim_minb", ctypes.c_int), ("schur_mode", ctypes.c_int),
-                ("blocks_mode", ctypes.c_int), ("elim_mixed_minb", ctypes.c_int), ("n_cand", ctypes.c_int),
-                ("cand", (ctypes.c_int * 5) * 8), ("ms", ctypes.c_double * 8)]
+                ("blocks_mode", ctypes.c_int), ("elim_mixed_minb", ctypes.c_int), ("blocks64_mode", ctypes.c_int),
+                ("n_cand", ctypes.c_int), ("cand", (ctypes.c_int * 6) * 8), ("ms", ctypes.c_double * 8)]
 
 
 def hdg_autotune(h, U, Q, UH, Ustar, nu, dt, a_ii, reps=2):
@@ -391,14 +391,14 @@ def hdg_autotune(h, U, Q, UH, Ustar, nu, dt, a_ii, reps=2):
     _check(h, lib().hdg_autotune(h, _ptr(U), _ptr(Q), _ptr(UH), _ptr(Ustar), _ptr(nu), float(dt), float(a_ii),
                                  int(reps), ctypes.byref(t)))
     return {"elim_nb": t.elim_nb, "elim_minb": t.elim_minb, "schur_mode": t.schur_mode,
-            "blocks_mode": t.blocks_mode, "elim_mixed_minb": t.elim_mixed_minb,
+            "blocks_mode": t.blocks_mode, "elim_mixed_minb": t.elim_mixed_minb, "blocks64_mode": t.blocks64_mode,
             "candidates": [(tuple(t.cand[i]), t.ms[i]) for i in range(t.n_cand)]}
 
 
-def hdg_set_tuning(h, elim_nb=16, elim_minb=2, schur_mode=0, blocks_mode=1, elim_mixed_minb=2):
+def hdg_set_tuning(h, elim_nb=16, elim_minb=2, schur_mode=0, blocks_mode=1, elim_mixed_minb=2, blocks64_mode=1):
     t = hdg_tune()
     t.elim_nb, t.elim_minb, t.schur_mode, t.blocks_mode = elim_nb, elim_minb, schur_mode, blocks_mode
-    t.elim_mixed_minb = elim_mixed_minb
+    t.elim_mixed_minb, t.blocks64_mode = elim_mixed_minb, blocks64_mode
     _check(h, lib().hdg_set_tuning(h, ctypes.byref(t)))
 
 

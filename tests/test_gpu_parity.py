@@ -193,13 +193,15 @@ def test_autotuned_variants_keep_parity():
     run = GpuRun(P)
     rep = H.hdg_autotune(run.h, run.U, run.Q, run.UH, run.Ustar, run.nu, P.dt, P.a_ii, reps=1)
     cands = rep["candidates"]
-    assert len(cands) == 4 and all(ms > 0 for _, ms in cands)
-    assert min(ms for _, ms in cands) == [ms for c, ms in cands if c[:2] == (rep["elim_nb"], rep["elim_minb"])][0]
+    assert len(cands) == 8 and all(ms > 0 for _, ms in cands)
+    chosen = (rep["elim_nb"], rep["elim_minb"], rep["blocks64_mode"])
+    assert min(ms for _, ms in cands) == [ms for c, ms in cands if (c[0], c[1], c[5]) == chosen][0]
+    assert {c[5] for c, _ in cands} == {0, 1}      # dense and sum-factorised contraction
     run.close()
     for cand, _ms in cands:
         nb, minb = cand[0], cand[1]
         h = create(P)
-        H.hdg_set_tuning(h, elim_nb=nb, elim_minb=minb)
+        H.hdg_set_tuning(h, elim_nb=nb, elim_minb=minb, blocks64_mode=cand[5])
         compare_handle = GpuRun(P, h)
         compare_handle.linearize()
         vals = compare_handle.blocks()
@@ -207,7 +209,7 @@ def test_autotuned_variants_keep_parity():
         rows = [0, 40, 77]
         blocks = [b for F in rows for b in range(pb.conn.rowptr[F], pb.conn.rowptr[F + 1])]
         orc, _ = pb.assemble(blocks=blocks)
-        assert max(block_rel_errors(vals, orc).values()) < TOL, (nb, minb)
+        assert max(block_rel_errors(vals, orc).values()) < TOL, cand
         compare_handle.close()
 
 
