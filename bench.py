@@ -318,11 +318,17 @@ def run_ours(args, rank, world, local_rank):
 
     def tune():
         # the project's autotuner picks among equivalent kernel variants on these inputs (untimed)
-        if args.no_autotune or args.elim_nb:
-            if args.elim_nb:      # a fixed variant (profiling runs)
-                H.hdg_set_tuning(h, elim_nb=args.elim_nb, elim_minb=2,
-                                 schur_mode={"fp32": 0, "tf32": 1, "3xtf32": 2}[args.mixed_prec],
-                                 blocks_mode=1 if m.dim == 3 else 0, elim_mixed_minb=2)
+        if args.no_autotune or args.elim_nb or args.tuning:
+            if args.elim_nb or args.tuning:      # a fixed variant (profiling runs)
+                kw = dict(elim_nb=args.elim_nb or 16, elim_minb=2,
+                          schur_mode={"fp32": 0, "tf32": 1, "3xtf32": 2}[args.mixed_prec],
+                          blocks_mode=1 if m.dim == 3 else 0, elim_mixed_minb=2, blocks64_mode=1)
+                for item in (args.tuning or "").split(","):
+                    if item:
+                        k, v = item.split("=")
+                        kw[k] = int(v)
+                H.hdg_set_tuning(h, **kw)
+                return dict(kw, fixed=True)
             return None
         rep = H.hdg_autotune(h, U, Q, UH, Us, nu, P.dt, P.a_ii, reps=1)
         return {k: rep[k] for k in ("elim_nb", "elim_minb", "schur_mode", "blocks_mode", "elim_mixed_minb",
@@ -570,6 +576,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--elim-nb", type=int, choices=[8, 16], default=None,
                     help="fix the FP64 elimination panel width instead of autotuning (profiling runs)")
+    ap.add_argument("--tuning", default=None,
+                    help="fixed kernel variants instead of autotuning, e.g. elim_nb=8,elim_minb=1,"
+                         "blocks64_mode=1,blocks_mode=1,elim_mixed_minb=3 (profiling runs)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

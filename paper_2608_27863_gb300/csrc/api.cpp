@@ -208,6 +208,7 @@ int create_device(hdg_ctx* h) {
     UP(h->tab.fphi, f32(t.phi)); UP(h->tab.fdphi, f32(t.dphi)); UP(h->tab.fpsi, f32(t.psi));
     UP(h->tab.ftheta, f32(t.theta)); UP(h->tab.fpsi_f, f32(t.psi_f)); UP(h->tab.ftheta_f, f32(t.theta_f));
     UP(h->tab.fmu, f32(t.mu)); UP(h->tab.fmf, f32(t.mf));
+    UP(h->tab.fb1, f32(t.b1)); UP(h->tab.fd1, f32(t.d1));
     const int d = h->d, G = 1 + d * d + h->nf * d;
     std::vector<double> geo((size_t)h->E * G);
     for (int64_t e = 0; e < h->E; ++e) {
@@ -334,11 +335,14 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
     } else {
         // FP32 SIMT and 3xTF32 tensor-core products are both FP32-accurate: the volume
         // contraction always, the Schur product unless TF32 / 3xTF32 was requested explicitly
+        // contraction: tensor cores (3-D) or FP32 sum factorisation; the dense FP32 SIMT
+        // contraction only when the Schur precision is fixed (the candidate list holds 8)
         const bool free_schur = h->prec_req == HDG_PREC_MIXED;
         for (int sm : {0, 2}) {
             if (!free_schur && sm != 0) continue;
-            for (int bm : {0, 1}) {
+            for (int bm : {1, 2, 0}) {
                 if (bm == 1 && h->d != 3) continue;
+                if (bm == 0 && free_schur) continue;
                 for (int mb : {2, 3}) {
                     cand[n][0] = h->elim_nb; cand[n][1] = h->elim_minb; cand[n][2] = free_schur ? sm : h->schur_mode;
                     cand[n][3] = bm; cand[n][4] = mb; cand[n][5] = h->blocks64_mode; ++n;
@@ -395,9 +399,9 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
 int hdg_set_tuning(hdg_handle h, const hdg_tune* t) {
     if (!h || !t) return fail(h, HDG_EINVAL, "NULL argument");
     if ((t->elim_nb != 8 && t->elim_nb != 16) || (t->elim_minb != 1 && t->elim_minb != 2) ||
-        t->schur_mode < 0 || t->schur_mode > 2 || t->blocks_mode < 0 || t->blocks_mode > 1 ||
+        t->schur_mode < 0 || t->schur_mode > 2 || t->blocks_mode < 0 || t->blocks_mode > 2 ||
         (t->elim_mixed_minb != 2 && t->elim_mixed_minb != 3) || t->blocks64_mode < 0 || t->blocks64_mode > 1)
-        return fail(h, HDG_EINVAL, "elim_nb 8 or 16, elim_minb 1 or 2, schur_mode 0..2, blocks_mode 0..1, "
+        return fail(h, HDG_EINVAL, "elim_nb 8 or 16, elim_minb 1 or 2, schur_mode 0..2, blocks_mode 0..2, "
                                    "elim_mixed_minb 2 or 3, blocks64_mode 0..1");
     if (h->precision == HDG_PREC_MIXED && h->prec_req != HDG_PREC_MIXED && t->schur_mode != h->schur_mode)
         return fail(h, HDG_EINVAL, "the Schur precision was fixed by hdg_set_params");

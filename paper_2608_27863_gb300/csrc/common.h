@@ -78,6 +78,7 @@ struct DeviceTables {
     double* minv_c; double* minv_e;
     double* psi; double* theta; double* psi_f; double* theta_f;
     double* b1; double* d1;          // 1-D tables of the tensor-product basis (sum factorisation)
+    float* fb1; float* fd1;
     // float copies for the mixed form's FP32 contraction
     float* fphi; float* fdphi; float* fpsi; float* ftheta; float* fpsi_f; float* ftheta_f; float* fmu; float* fmf;
 };
@@ -185,7 +186,8 @@ struct hdg_ctx {
     // mixed form (allocated on the first mixed linearization)
     int sys_prec = HDG_PREC_FP64;          // precision of the assembled system
     int schur_mode = 0;                    // mixed Schur product: 0 FP32 SIMT, 1 TF32, 2 3xTF32 tensor cores
-    int blocks_mode = 1;                   // mixed volume contraction: 0 FP32 SIMT, 1 3xTF32 tensor cores (3-D)
+    int blocks_mode = 1;                   // mixed volume contraction: 0 FP32 SIMT, 1 3xTF32 tensor cores (3-D),
+                                           // 2 FP32 sum factorisation
     int blocks64_mode = 1;                 // FP64 volume contraction: 0 dense GEMM, 1 sum factorisation
     double* d_m11 = nullptr;               // [E][NU][NU] interior block / its LU factors (FP64)
     float* d_m12 = nullptr;                // [E][NU][NT] Bt, then Z = L^{-1} P Bt

@@ -638,11 +638,11 @@ struct SfShape {
     static constexpr int NY = (C::D == 3) ? Q1 * N1 * N1 : 0;            // after the second (3-D)
     static constexpr int NTH = 128;
     static constexpr int SLOTS = (C::NP * CW + NTH - 1) / NTH;
-    static constexpr int smem_doubles = C::NCOEF * C::NQ + CW * (C::NQ + NX + NY);
+    static constexpr int smem_words = C::NCOEF * C::NQ + CW * (C::NQ + NX + NY);   // in the accumulation type
 };
 
-template <class C>
-__global__ void __launch_bounds__(SfShape<C>::NTH) k_blocks_sf(BlkArgs<double> A) {
+template <class C, class TA, class TL>
+__global__ void __launch_bounds__(SfShape<C>::NTH) k_blocks_sf(BlkArgs<TL> A) {
     using S = SfShape<C>;
     constexpr int D = C::D, M = C::M, NP = C::NP, NQ = C::NQ, NFP = C::NFP, NCOEF = C::NCOEF;
     constexpr int N1 = S::N1, Q1 = S::Q1, NCB = S::NCB, CW = S::CW, NTH = S::NTH;
@@ -652,21 +652,28 @@ __global__ void __launch_bounds__(SfShape<C>::NTH) k_blocks_sf(BlkArgs<double> A
     const int b = (int)(bid % M), a = (int)((bid / M) % M);
     const int64_t el = bid / (M * M), e = A.e0 + el;
     const DeviceTables& T = A.tab;
-    extern __shared__ double sm[];
-    double* cs = sm;                     // [NCOEF][Nq] coefficients of one direction
-    double* Gs = cs + NCOEF * NQ;        // [Nq][CW]
-    double* Xs = Gs + NQ * CW;           // [NX][CW]
-    double* Ys = Xs + S::NX * CW;        // [NY][CW] (3-D)
-    const double* cf = static_cast<const double*>(A.vcoef) + (((size_t)el * M + a) * M + b) * (size_t)(D * NCOEF * NQ);
+    // tables in the accumulation type (FP64 form: double; mixed form: float)
+    constexpr bool F32 = sizeof(TA) == 4;
+    const TA* tphi = F32 ? (const TA*)T.fphi : (const TA*)T.phi;
+    const TA* tpsi = F32 ? (const TA*)T.fpsi : (const TA*)T.psi;
+    const TA* ttheta = F32 ? (const TA*)T.ftheta : (const TA*)T.theta;
+    const TA* tb1 = F32 ? (const TA*)T.fb1 : (const TA*)T.b1;
+    const TA* td1 = F32 ? (const TA*)T.fd1 : (const TA*)T.d1;
+    extern __shared__ double sm_raw[];
+    TA* cs = reinterpret_cast<TA*>(sm_raw);   // [NCOEF][Nq] coefficients of one direction
+    TA* Gs = cs + NCOEF * NQ;        // [Nq][CW]
+    TA* Xs = Gs + NQ * CW;           // [NX][CW]
+    TA* Ys = Xs + S::NX * CW;        // [NY][CW] (3-D)
+    const TA* cf = static_cast<const TA*>(A.vcoef) + (((size_t)el * M + a) * M + b) * (size_t)(D * NCOEF * NQ);
     const double detJ = A.geo[e * GEO];
     double* A11 = A.R.a11 + e * A.R.a11_es;
-    double* A12 = A.R.a12 + e * A.R.a12_es;
+    TL* A12 = A.R.a12 + e * A.R.a12_es;
 #pragma unroll 1
     for (int c0 = 0; c0 < NCB; c0 += CW) {
         const int cw = min(CW, NCB - c0);
-        double acc[S::SLOTS];
+        TA acc[S::SLOTS];
 #pragma unroll
-        for (int s = 0; s < S::SLOTS; ++s) acc[s] = 0.0;
+        for (int s = 0; s < S::SLOTS; ++s) acc[s] = (TA)0;
 #pragma unroll 1
         for (int k = 0; k < D; ++k) {
             __syncthreads();                 // the previous direction is done with cs / Gs
@@ -674,27 +681,27 @@ __global__ void __launch_bounds__(SfShape<C>::NTH) k_blocks_sf(BlkArgs<double> A
             __syncthreads();
             for (int idx = tid; idx < NQ * CW; idx += NTH) {
                 const int g = idx / CW, cc = idx - g * CW, c = c0 + cc;
-                double v = 0.0;
+                TA v = (TA)0;
                 if (cc < cw) {
                     if (c < NP) {
-                        v = cs[g] * T.phi[g * NP + c];
-                        for (int r2 = 0; r2 < D; ++r2) v -= cs[(1 + r2) * NQ + g] * T.psi[((size_t)r2 * NQ + g) * NP + c];
+                        v = cs[g] * tphi[g * NP + c];
+                        for (int r2 = 0; r2 < D; ++r2) v -= cs[(1 + r2) * NQ + g] * tpsi[((size_t)r2 * NQ + g) * NP + c];
                     } else {
                         const int c2 = c - NP, f = c2 / NFP, l = c2 - f * NFP;
-                        v = cs[(1 + D + f) * NQ + g] * T.theta[((size_t)f * NQ + g) * NFP + l];
+                        v = cs[(1 + D + f) * NQ + g] * ttheta[((size_t)f * NQ + g) * NFP + l];
                     }
                 }
                 Gs[idx] = v;
             }
             __syncthreads();
-            const double* T0 = (k == 0) ? T.d1 : T.b1;
-            const double* T1 = (k == 1) ? T.d1 : T.b1;
+            const TA* T0 = (k == 0) ? td1 : tb1;
+            const TA* T1 = (k == 1) ? td1 : tb1;
             if (D == 3) {
-                const double* T2 = (k == 2) ? T.d1 : T.b1;
+                const TA* T2 = (k == 2) ? td1 : tb1;
                 // X[j2][g1][g0] = sum_g2 T2[g2][j2] G[g0 + Q1 g1 + Q1^2 g2]
                 for (int idx = tid; idx < S::NX * CW; idx += NTH) {
                     const int cc = idx % CW, rest = idx / CW, j2 = rest % N1, g01 = rest / N1;
-                    double s = 0.0;
+                    TA s = (TA)0;
 #pragma unroll
                     for (int g2 = 0; g2 < Q1; ++g2) s = fma(T2[g2 * N1 + j2], Gs[(g01 + Q1 * Q1 * g2) * CW + cc], s);
                     Xs[(j2 * Q1 * Q1 + g01) * CW + cc] = s;
@@ -704,7 +711,7 @@ __global__ void __launch_bounds__(SfShape<C>::NTH) k_blocks_sf(BlkArgs<double> A
                 for (int idx = tid; idx < S::NY * CW; idx += NTH) {
                     const int cc = idx % CW, rest = idx / CW, g0 = rest % Q1, j12 = rest / Q1;
                     const int j1 = j12 % N1, j2 = j12 / N1;
-                    double s = 0.0;
+                    TA s = (TA)0;
 #pragma unroll
                     for (int g1 = 0; g1 < Q1; ++g1) s = fma(T1[g1 * N1 + j1], Xs[(j2 * Q1 * Q1 + g1 * Q1 + g0) * CW + cc], s);
                     Ys[(j12 * Q1 + g0) * CW + cc] = s;
@@ -716,7 +723,7 @@ __global__ void __launch_bounds__(SfShape<C>::NTH) k_blocks_sf(BlkArgs<double> A
                     const int idx = tid + NTH * s;
                     if (idx < NP * CW) {
                         const int cc = idx % CW, j = idx / CW, j0 = j % N1, j12 = j / N1;
-                        double t = 0.0;
+                        TA t = (TA)0;
 #pragma unroll
                         for (int g0 = 0; g0 < Q1; ++g0) t = fma(T0[g0 * N1 + j0], Ys[(j12 * Q1 + g0) * CW + cc], t);
                         acc[s] += t;
@@ -726,7 +733,7 @@ __global__ void __launch_bounds__(SfShape<C>::NTH) k_blocks_sf(BlkArgs<double> A
                 // X[j1][g0] = sum_g1 T1[g1][j1] G[g0 + Q1 g1]
                 for (int idx = tid; idx < S::NX * CW; idx += NTH) {
                     const int cc = idx % CW, rest = idx / CW, g0 = rest % Q1, j1 = rest / Q1;
-                    double s = 0.0;
+                    TA s = (TA)0;
 #pragma unroll
                     for (int g1 = 0; g1 < Q1; ++g1) s = fma(T1[g1 * N1 + j1], Gs[(g0 + Q1 * g1) * CW + cc], s);
                     Xs[(j1 * Q1 + g0) * CW + cc] = s;
@@ -737,7 +744,7 @@ __global__ void __launch_bounds__(SfShape<C>::NTH) k_blocks_sf(BlkArgs<double> A
                     const int idx = tid + NTH * s;
                     if (idx < NP * CW) {
                         const int cc = idx % CW, j = idx / CW, j0 = j % N1, j1 = j / N1;
-                        double t = 0.0;
+                        TA t = (TA)0;
 #pragma unroll
                         for (int g0 = 0; g0 < Q1; ++g0) t = fma(T0[g0 * N1 + j0], Xs[(j1 * Q1 + g0) * CW + cc], t);
                         acc[s] += t;
@@ -754,12 +761,12 @@ __global__ void __launch_bounds__(SfShape<C>::NTH) k_blocks_sf(BlkArgs<double> A
             if (cc >= cw) continue;
             const int64_t row = a * NP + i;
             if (c < NP) {
-                double v = acc[s];
+                double v = (double)acc[s];
                 if (a == b) v += detJ / A.a_ii * T.mhat[i * NP + c];
                 A11[row * A.R.a11_rs + b * NP + c] = v;
             } else {
                 const int c2 = c - NP, f = c2 / NFP, l = c2 - f * NFP;
-                A12[row * A.R.a12_rs + (f * M + b) * NFP + l] = acc[s];
+                A12[row * A.R.a12_rs + (f * M + b) * NFP + l] = (TL)acc[s];
             }
         }
     }
@@ -1138,7 +1145,7 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
     auto kblk = k_blocks<C, BC::TY, BC::TX, BC::KC, double, double>;
     auto kface = k_blocks<C, BC::TY, BC::TX, BC::KC, double, double, false>;
     constexpr int PT = 128;
-    const size_t sm_sf = sizeof(double) * SfShape<C>::smem_doubles;
+    const size_t sm_sf = sizeof(double) * SfShape<C>::smem_words;
     const size_t sm_point = sizeof(double) * point_smem_doubles<C>();
     const size_t sm_blk = sizeof(double) * BS_::smem;
     const size_t sm_elim16 = sizeof(double) * elim_smem_doubles<C, 16>();
@@ -1146,7 +1153,7 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
     HDG_CK(cudaFuncSetAttribute(k_point<C, PT, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_point));
     HDG_CK(cudaFuncSetAttribute(kblk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
     HDG_CK(cudaFuncSetAttribute(kface, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
-    HDG_CK(cudaFuncSetAttribute(k_blocks_sf<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sf));
+    HDG_CK(cudaFuncSetAttribute(k_blocks_sf<C, double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sf));
     HDG_CK(cudaFuncSetAttribute(k_elim<C, 16, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim16));
     HDG_CK(cudaFuncSetAttribute(k_elim<C, 16, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim16));
     HDG_CK(cudaFuncSetAttribute(k_elim<C, 8, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim8));
@@ -1176,7 +1183,7 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
         prof_end(h);
         prof_begin(h, HDG_K_BLOCKS);
         if (h->blocks64_mode == 1) {         // sum-factorised volume terms, then the face terms
-            k_blocks_sf<C><<<(unsigned)(ne * C::M * C::M), SfShape<C>::NTH, sm_sf, st>>>(ba);
+            k_blocks_sf<C, double, double><<<(unsigned)(ne * C::M * C::M), SfShape<C>::NTH, sm_sf, st>>>(ba);
             kface<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
         } else {
             kblk<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);

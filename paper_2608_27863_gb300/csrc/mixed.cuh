@@ -575,6 +575,8 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
     HDG_CK(cudaFuncSetAttribute(kface, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
     if (C::D == 3)
         HDG_CK(cudaFuncSetAttribute(k_blocks_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, BlkTC<C>::smem_bytes()));
+    const size_t sm_sf32 = sizeof(float) * SfShape<C>::smem_words;
+    HDG_CK(cudaFuncSetAttribute(k_blocks_sf<C, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sf32));
     HDG_CK(cudaFuncSetAttribute(k_elim_mixed<C, NB, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
     HDG_CK(cudaFuncSetAttribute(k_elim_mixed<C, NB, 256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
     cudaStream_t st = h->stream;
@@ -605,6 +607,10 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
             // volume contraction on tensor cores (3xTF32), face terms added by the SIMT kernel
             using BT = BlkTC<C>;
             k_blocks_tc<C><<<(unsigned)(ne * BT::NMT), 128, BT::smem_bytes(), st>>>(ba, h->d_status);
+            kface<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
+        } else if (h->blocks_mode == 2) {
+            // volume contraction by FP32 sum factorisation, then the face terms
+            k_blocks_sf<C, float, float><<<(unsigned)(ne * C::M * C::M), SfShape<C>::NTH, sm_sf32, st>>>(ba);
             kface<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
         } else {
             kblk<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);

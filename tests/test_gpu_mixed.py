@@ -142,19 +142,20 @@ def test_autotune_mixed_picks_fp32_accurate_schur():
     H.hdg_set_params(run.h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s,
                      precision=H.HDG_PREC_MIXED_TF32)
     rep = H.hdg_autotune(run.h, run.U, run.Q, run.UH, run.Ustar, run.nu, P.dt, P.a_ii, reps=1)
-    assert len(rep["candidates"]) == 4 and rep["schur_mode"] == 1
-    assert {c[3] for c, _ in rep["candidates"]} == {0, 1} and {c[4] for c, _ in rep["candidates"]} == {2, 3}
+    assert len(rep["candidates"]) == 6 and rep["schur_mode"] == 1
+    assert {c[3] for c, _ in rep["candidates"]} == {0, 1, 2} and {c[4] for c, _ in rep["candidates"]} == {2, 3}
     run.close()
 
 
 @pytest.mark.parametrize("make", [lambda: synth.config2(n=3), lambda: synth.config3(n=3)], ids=["hex-p2", "hex-p3"])
 def test_tensor_core_contraction_matches_simt(make):
-    """The 3xTF32 tcgen05 volume contraction and the FP32 SIMT one agree to FP32 accuracy."""
+    """The 3xTF32 tcgen05 volume contraction, the FP32 sum-factorised one and the
+    dense FP32 SIMT one agree to FP32 accuracy."""
     import torch
     from paper_2608_27863_gb300 import hdg as H
     P = make()
     out = {}
-    for bm in (0, 1):
+    for bm in (0, 1, 2):
         run = GpuRun(P)
         H.hdg_set_params(run.h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s,
                          precision=H.HDG_PREC_MIXED)
@@ -166,6 +167,8 @@ def test_tensor_core_contraction_matches_simt(make):
         H.hdg_get_blocks(run.h, v)
         out[bm] = (v.cpu().numpy().astype(np.float64), run.rhs())
         run.close()
-    (v0, g0), (v1, g1) = out[0], out[1]
-    assert np.linalg.norm(v1 - v0) <= 2e-6 * np.linalg.norm(v0)
-    assert np.linalg.norm(g1 - g0) <= 2e-6 * np.linalg.norm(g0)
+    v0, g0 = out[0]
+    for bm in (1, 2):
+        v1, g1 = out[bm]
+        assert np.linalg.norm(v1 - v0) <= 2e-6 * np.linalg.norm(v0), bm
+        assert np.linalg.norm(g1 - g0) <= 2e-6 * np.linalg.norm(g0), bm
