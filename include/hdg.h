@@ -248,14 +248,16 @@ int hdg_set_preconditioner(hdg_handle h, int kind);
 int hdg_schwarz_setup(hdg_handle h);
 int hdg_schwarz_apply(hdg_handle h, const double* x, double* y);
 
-/* Block-Jacobi preconditioner of the trace system: partial-pivot LU of every
- * diagonal block S_FF of the current S (the one-face special case of the
- * additive Schwarz method, eq. additive-schwarz), and y = M^{-1} x. */
+/* Block-Jacobi preconditioner of the trace system: the inverse of every
+ * diagonal block S_FF of the current S (partial-pivot LU in FP64, kept in the
+ * system's storage precision; the one-face special case of the additive
+ * Schwarz method, eq. additive-schwarz), and y = M^{-1} x. */
 int hdg_blockjacobi_setup(hdg_handle h);
 int hdg_blockjacobi_apply(hdg_handle h, const double* x, double* y);
-/* Restarted GMRES(restart) on S x = b with FP64 modified Gram-Schmidt
- * Arnoldi (Sec. 3.2), left-preconditioned by the selected preconditioner
- * (hdg_set_preconditioner; block-Jacobi by default) when precond != 0.
+/* Restarted GMRES(restart) on S x = b with FP64 Arnoldi (Sec. 3.2; classical
+ * Gram-Schmidt with one reorthogonalisation, CGS2), left-preconditioned by
+ * the selected preconditioner (hdg_set_preconditioner; block-Jacobi by
+ * default) when precond != 0.
  * x holds the initial guess and receives the solution (device arrays
  * [F][m][Nfp]).  Stops when the preconditioned residual ||M^{-1}(b - S x)||
  * drops below rtol x ||M^{-1} b|| (so a good initial guess saves

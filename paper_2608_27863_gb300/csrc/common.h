@@ -138,8 +138,9 @@ struct hdg_ctx {
     double* d_part = nullptr;              // [E + F] partial sums of squares
     double* d_norms = nullptr;             // [3]
     // block-Jacobi factors (allocated on first set-up)
-    double* d_bjlu = nullptr;              // [F][BS][BS]
-    int32_t* d_bjpiv = nullptr;            // [F][BS]
+    double* d_bjlu = nullptr;              // [F][BS][BS] inverses of the diagonal blocks (column-major;
+                                           // FP32 values for the mixed system)
+    int bj_prec = HDG_PREC_FP64;
     bool bj_ready = false;
     // additive Schwarz factors on element face patches (allocated on first set-up)
     void* d_asmlu = nullptr;               // [E][NT][LDA] LU factors of S_r (FP64, or FP32 for the mixed form)

@@ -833,8 +833,6 @@ __global__ void __launch_bounds__(NTH, MINB) k_elim(double* top, double* bot, in
     double* pan = sm;                       // [NR][NB], row index relative to k0
     double* ust = pan + NR * NB;            // [NB][TCW]
     __shared__ int piv[NB];
-    __shared__ double rv[NTH / 32];
-    __shared__ int ri[NTH / 32];
     __shared__ int sflag;
     if (tid == 0) sflag = 0;
 
@@ -847,36 +845,33 @@ __global__ void __launch_bounds__(NTH, MINB) k_elim(double* top, double* bot, in
         }
         __syncthreads();
         for (int j = 0; j < kb; ++j) {
-            double bv = -1.0;
-            int bi = INT_MAX;
+            // warp 0 alone: pivot search (largest magnitude, lowest row on ties) and the row
+            // interchange inside the panel; one barrier per step
+            if (warp == 0) {
+                double bv = -1.0;
+                int bi = INT_MAX;
 #pragma unroll 1
-            for (int rr = j + tid; rr < ntop; rr += NTH) {
-                double v = fabs(pan[rr * NB + j]);
-                if (v > bv) { bv = v; bi = rr; }
-            }
-            for (int off = 16; off > 0; off >>= 1) {
-                double ov = __shfl_down_sync(0xffffffffu, bv, off);
-                int oi = __shfl_down_sync(0xffffffffu, bi, off);
-                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-            }
-            if (lane == 0) { rv[warp] = bv; ri[warp] = bi; }
-            __syncthreads();
-            if (tid == 0) {
-                double b2 = rv[0];
-                int i2 = ri[0];
-                for (int w = 1; w < NTH / 32; ++w)
-                    if (rv[w] > b2 || (rv[w] == b2 && ri[w] < i2)) { b2 = rv[w]; i2 = ri[w]; }
-                if (i2 == INT_MAX) { i2 = j; sflag |= 2; }
-                piv[j] = i2;
-            }
-            __syncthreads();
-            const int pr = piv[j];
-            if (pr != j)
-                for (int c = tid; c < kb; c += NTH) {
-                    double t = pan[j * NB + c];
-                    pan[j * NB + c] = pan[pr * NB + c];
-                    pan[pr * NB + c] = t;
+                for (int rr = j + lane; rr < ntop; rr += 32) {
+                    const double v = fabs(pan[rr * NB + j]);
+                    if (v > bv) { bv = v; bi = rr; }
                 }
+                for (int off = 16; off > 0; off >>= 1) {
+                    const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+                    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+                }
+                int pr = __shfl_sync(0xffffffffu, bi, 0);
+                if (pr == INT_MAX) {
+                    pr = j;
+                    if (lane == 0) sflag |= 2;
+                }
+                if (lane < kb && pr != j) {
+                    const double t = pan[j * NB + lane];
+                    pan[j * NB + lane] = pan[pr * NB + lane];
+                    pan[pr * NB + lane] = t;
+                }
+                if (lane == 0) piv[j] = pr;
+            }
             __syncthreads();
             double pv = pan[j * NB + j];
             if (pv == 0.0 || !isfinite(pv)) {

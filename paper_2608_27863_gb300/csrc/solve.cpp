@@ -1,8 +1,10 @@
 // Host side of the trace-space solve: FP64 stage residual, Newton update,
-// block-Jacobi preconditioner and restarted, left-preconditioned GMRES with
-// modified Gram-Schmidt Arnoldi in FP64 (Sec. 3.2).  The Krylov coefficients
-// live on the device; only the Hessenberg column of each iteration is read
-// back for the Givens rotations.
+// block-Jacobi and additive Schwarz preconditioners, the reduced-basis guess,
+// and restarted, left-preconditioned GMRES with FP64 Arnoldi (classical
+// Gram-Schmidt with one reorthogonalisation; Sec. 3.2).  The Krylov
+// coefficients live on the device; the host-driven solver reads back only the
+// Hessenberg column of each iteration for the Givens rotations, the
+// synchronisation-free one does those on the device as well.
 #include <cmath>
 #include <cstring>
 #include <initializer_list>
@@ -138,6 +140,23 @@ int matvec(hdg_ctx* h, const double* x, double* y) {
     return rc;
 }
 
+// Classical Gram-Schmidt with one reorthogonalisation (CGS2) of vn against
+// V_0 .. V_j: hcol[0..j] = the projection coefficients (FP64, fixed-order
+// reductions), vn orthogonalised in place.  Eight dot products per pass over
+// the data instead of one kernel pair per basis vector as modified Gram-Schmidt needs.
+void cgs2(hdg_ctx* h, const double* V, int64_t N, int j, double* vn, double* hcol, double* htmp) {
+    const int k = j + 1;
+    for (int pass = 0; pass < 2; ++pass) {
+        double* hp = pass == 0 ? hcol : htmp;
+        for (int j0 = 0; j0 < k; j0 += 8) {
+            k_mdot_part<<<kRedBlocks, 256, 0, h->stream>>>(V, N, j0, k, vn, N, h->d_red);
+            k_mdot_final<<<1, 32, 0, h->stream>>>(h->d_red, kRedBlocks, j0, k, hp);
+        }
+        k_msub<<<grid_for(N), 256, 0, h->stream>>>(V, N, hp, k, vn, N);
+    }
+    k_vadd<<<1, 64, 0, h->stream>>>(hcol, htmp, k);
+}
+
 // workspace of the synchronisation-free solver: Krylov basis, Newton work, device scalars
 int ensure_fixed_workspace(hdg_ctx* h, int m) {
     const int64_t N = h->F * h->BS;
@@ -145,8 +164,8 @@ int ensure_fixed_workspace(hdg_ctx* h, int m) {
     if (h->gm_cap < m) {
         if ((rc = alloc(h, (void**)&h->d_V, sizeof(double) * (size_t)(m + 1) * N))) return rc;
         if ((rc = alloc(h, (void**)&h->d_w, sizeof(double) * N))) return rc;
-        if (!h->d_red && (rc = alloc(h, (void**)&h->d_red, sizeof(double) * kRedBlocks))) return rc;
-        if ((rc = alloc(h, (void**)&h->d_h, sizeof(double) * (m + 2)))) return rc;
+        if (!h->d_red && (rc = alloc(h, (void**)&h->d_red, sizeof(double) * kRedBlocks * 8))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_h, sizeof(double) * 2 * (m + 2)))) return rc;
         h->gm_cap = m;
     }
     if (h->fx_cap < m) {
@@ -194,10 +213,7 @@ int gmres_fixed_async(hdg_ctx* h, const double* b, double* x, int m, bool use_x0
         double* vn = V + (size_t)(j + 1) * N;
         if ((rc = matvec(h, vj, w))) return rc;
         if ((rc = precond_apply(h, w, vn))) return rc;
-        for (int i = 0; i <= j; ++i) {
-            dev_dot(h, vn, V + (size_t)i * N, N, hc + i, false);
-            k_axpy_dev<<<grid_for(N), 256, 0, h->stream>>>(hc + i, -1.0, V + (size_t)i * N, vn, N);
-        }
+        cgs2(h, V, N, j, vn, hc, hc + m + 2);
         dev_dot(h, vn, vn, N, hc + j + 1, true);
         k_scale_safe<<<grid_for(N), 256, 0, h->stream>>>(vn, hc + j + 1, vn, N);
         k_givens_step<<<1, 1, 0, h->stream>>>(hc, j, m, R, cs, sn, gv);
@@ -268,7 +284,6 @@ int hdg_blockjacobi_setup(hdg_handle h) {
     int rc;
     if (!h->d_bjlu) {
         if ((rc = alloc(h, (void**)&h->d_bjlu, sizeof(double) * h->F * h->BS * h->BS))) return rc;
-        if ((rc = alloc(h, (void**)&h->d_bjpiv, sizeof(int32_t) * h->F * h->BS))) return rc;
     }
     DISPATCH_S(run_bj_setup, h);
     if (rc) return rc;
@@ -401,8 +416,8 @@ int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_ite
         // workspace grows to the largest restart length requested; kept until destroy
         if ((rc = alloc(h, (void**)&h->d_V, sizeof(double) * (size_t)(restart + 1) * N))) return rc;
         if ((rc = alloc(h, (void**)&h->d_w, sizeof(double) * N))) return rc;
-        if (!h->d_red && (rc = alloc(h, (void**)&h->d_red, sizeof(double) * kRedBlocks))) return rc;
-        if ((rc = alloc(h, (void**)&h->d_h, sizeof(double) * (restart + 2)))) return rc;
+        if (!h->d_red && (rc = alloc(h, (void**)&h->d_red, sizeof(double) * kRedBlocks * 8))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_h, sizeof(double) * 2 * (restart + 2)))) return rc;
         h->gm_cap = restart;
     }
     double* V = h->d_V;
@@ -447,10 +462,7 @@ int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_ite
             } else if ((rc = matvec(h, vj, vn))) {
                 return rc;
             }
-            for (int i = 0; i <= j; ++i) {      // modified Gram-Schmidt
-                dev_dot(h, vn, V + (size_t)i * N, N, dh + i, false);
-                k_axpy_dev<<<grid_for(N), 256, 0, h->stream>>>(dh + i, -1.0, V + (size_t)i * N, vn, N);
-            }
+            cgs2(h, V, N, j, vn, dh, dh + m + 2);   // Gram-Schmidt with reorthogonalisation
             dev_dot(h, vn, vn, N, dh + j + 1, true);
             k_scale_dev<<<grid_for(N), 256, 0, h->stream>>>(vn, dh + j + 1, vn, N);
             CKS(cudaMemcpyAsync(hc.data(), dh, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, h->stream));

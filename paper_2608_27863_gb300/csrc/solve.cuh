@@ -1,8 +1,9 @@
 // Consumer side of the condensed system (FP64): the nonlinear stage residual
 // F(W) = [R_q; R_u; R_uhat] (eq. nonlinear-residual), the Newton state update
 // W <- W + alpha dW (eq. newton-update), a block-Jacobi preconditioner made of
-// the diagonal face blocks S_FF of the trace operator (the single-face special
-// case of eq. additive-schwarz), and the vector kernels of restarted GMRES.
+// the inverses of the diagonal face blocks S_FF of the trace operator (the
+// single-face special case of eq. additive-schwarz), and the vector kernels
+// of restarted GMRES.
 #pragma once
 
 #include "mixed.cuh"
@@ -259,14 +260,18 @@ __global__ void k_trace_residual(const double* rk, const int32_t* f2e, const int
 }
 
 // ----------------------------------------------------------------------------
-// block-Jacobi: LU (partial pivoting) of the diagonal blocks, then solves
+// block-Jacobi: the explicit inverses of the diagonal blocks S_FF (LU with
+// partial pivoting in FP64, then one triangular solve pair per unit column),
+// stored column-major in the system's storage type (FP64, or FP32 for the
+// mixed system); the apply is then one dense product per face with a
+// coalesced column sweep and no reductions.
 // ----------------------------------------------------------------------------
 template <class C, class TL>
-__global__ void k_bj_setup(const int32_t* rowptr, const int32_t* col, const TL* vals, double* lu,
-                           int32_t* piv, int32_t* status) {
+__global__ void k_bj_setup(const int32_t* rowptr, const int32_t* col, const TL* vals, TL* inv, int32_t* status) {
     constexpr int BS = C::BS, LDA = BS + 1;
     extern __shared__ double a[];          // [BS][BS + 1]
     __shared__ int p_s;
+    __shared__ int pv_s[BS];
     const int64_t f = blockIdx.x;
     int bd = -1;
     for (int b = rowptr[f]; b < rowptr[f + 1]; ++b)
@@ -289,7 +294,7 @@ __global__ void k_bj_setup(const int32_t* rowptr, const int32_t* col, const TL* 
                 if (fabs(a[r * LDA + j]) > bv) { bv = fabs(a[r * LDA + j]); pr = r; }
             if (bv == 0.0 || !isfinite(bv)) atomicOr(status, bv == 0.0 ? 1 : 2);
             p_s = pr;
-            piv[f * BS + j] = pr;
+            pv_s[j] = pr;
         }
         __syncthreads();
         const int pr = p_s;
@@ -307,42 +312,55 @@ __global__ void k_bj_setup(const int32_t* rowptr, const int32_t* col, const TL* 
         }
         __syncthreads();
     }
-    for (int idx = threadIdx.x; idx < BS * BS; idx += blockDim.x) {
-        int r = idx / BS, c = idx - r * BS;
-        lu[(size_t)f * BS * BS + idx] = a[r * LDA + c];   // row-major factors
+    // column c of the inverse: x = U^{-1} L^{-1} P e_c, one thread per column
+    TL* out = inv + (size_t)f * BS * BS;
+    for (int c = threadIdx.x; c < BS; c += blockDim.x) {
+        double x[BS];
+        for (int i = 0; i < BS; ++i) x[i] = (i == c) ? 1.0 : 0.0;
+        for (int j = 0; j < BS; ++j) {
+            const int pr = pv_s[j];
+            if (pr != j) { const double t = x[j]; x[j] = x[pr]; x[pr] = t; }
+        }
+        for (int j = 0; j < BS; ++j)
+            for (int i = j + 1; i < BS; ++i) x[i] = fma(-a[i * LDA + j], x[j], x[i]);
+        for (int j = BS - 1; j >= 0; --j) {
+            double d = a[j * LDA + j];
+            if (d == 0.0 || !isfinite(d)) d = 1.0;
+            x[j] /= d;
+            for (int i = 0; i < j; ++i) x[i] = fma(-a[i * LDA + j], x[j], x[i]);
+        }
+        for (int i = 0; i < BS; ++i) out[(size_t)c * BS + i] = (TL)x[i];
     }
 }
 
-template <class C>
-__global__ void k_bj_apply(const double* lu, const int32_t* piv, const double* x, double* y, int64_t F) {
-    constexpr int BS = C::BS;
+// y_F = inv(S_FF) x_F: one warp per face, lane i owns rows i, i + 32, ...
+template <class C, class TL>
+__global__ void k_bj_apply(const TL* inv, const double* x, double* y, int64_t F) {
+    constexpr int BS = C::BS, RPL = (BS + 31) / 32;
     const int64_t f = (int64_t)blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (f >= F) return;
-    __shared__ double buf[8][BS];
-    double* z = buf[threadIdx.x >> 5];
-    for (int i = lane; i < BS; i += 32) z[i] = x[f * BS + i];
+    __shared__ TL buf[8][BS];
+    TL* z = buf[threadIdx.x >> 5];
+    for (int i = lane; i < BS; i += 32) z[i] = (TL)x[f * BS + i];
     __syncwarp();
-    const double* A = lu + (size_t)f * BS * BS;
-    if (lane == 0)
-        for (int j = 0; j < BS; ++j) {
-            int pr = piv[f * BS + j];
-            if (pr != j) { double t = z[j]; z[j] = z[pr]; z[pr] = t; }
+    const TL* A = inv + (size_t)f * BS * BS;
+    TL acc[RPL];
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) acc[r] = (TL)0;
+    for (int j = 0; j < BS; ++j) {
+        const TL zj = z[j];
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const int i = lane + 32 * r;
+            if (i < BS) acc[r] = fma(A[(size_t)j * BS + i], zj, acc[r]);
         }
-    __syncwarp();
-    for (int j = 0; j < BS; ++j) {          // forward, unit lower
-        double zj = z[j];
-        for (int i = j + 1 + lane; i < BS; i += 32) z[i] = fma(-A[i * BS + j], zj, z[i]);
-        __syncwarp();
     }
-    for (int j = BS - 1; j >= 0; --j) {     // backward
-        if (lane == 0) z[j] = z[j] / A[j * BS + j];
-        __syncwarp();
-        double zj = z[j];
-        for (int i = lane; i < j; i += 32) z[i] = fma(-A[i * BS + j], zj, z[i]);
-        __syncwarp();
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        const int i = lane + 32 * r;
+        if (i < BS) y[f * BS + i] = (double)acc[r];
     }
-    for (int i = lane; i < BS; i += 32) y[f * BS + i] = z[i];
 }
 
 // ----------------------------------------------------------------------------
@@ -353,6 +371,10 @@ constexpr int kRedBlocks = 304;  // 2 per SM
 __global__ void k_dot_part(const double* x, const double* y, int64_t n, double* part);
 __global__ void k_dot_final(const double* part, int nparts, double* out, int take_sqrt);
 __global__ void k_axpy_dev(const double* coef, double sign, const double* x, double* y, int64_t n);
+__global__ void k_mdot_part(const double* V, int64_t ldv, int j0, int k, const double* w, int64_t n, double* part);
+__global__ void k_mdot_final(const double* part, int nparts, int j0, int k, double* out);
+__global__ void k_msub(const double* V, int64_t ldv, const double* coef, int k, double* w, int64_t n);
+__global__ void k_vadd(double* a, const double* b, int k);
 __global__ void k_scale_dev(const double* x, const double* div, double* y, int64_t n);
 __global__ void k_axpby(double a, const double* x, double b, double* y, int64_t n);
 __global__ void k_combine(const double* V, int64_t ldv, const double* coef, int k, double* x, int64_t n);
@@ -406,12 +428,13 @@ int run_bj_setup(hdg_ctx* h) {
     if (h->sys_prec == HDG_PREC_MIXED) {
         HDG_CK(cudaFuncSetAttribute(k_bj_setup<C, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_bj_setup<C, float><<<(unsigned)h->F, 128, smem, h->stream>>>(h->d_rowptr, h->d_col, h->d_vals32,
-                                                                       h->d_bjlu, h->d_bjpiv, h->d_status);
+                                                                       (float*)h->d_bjlu, h->d_status);
     } else {
         HDG_CK(cudaFuncSetAttribute(k_bj_setup<C, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         k_bj_setup<C, double><<<(unsigned)h->F, 128, smem, h->stream>>>(h->d_rowptr, h->d_col, h->d_vals,
-                                                                        h->d_bjlu, h->d_bjpiv, h->d_status);
+                                                                        h->d_bjlu, h->d_status);
     }
+    h->bj_prec = h->sys_prec;
     HDG_CK(cudaGetLastError());
     return HDG_OK;
 }
@@ -419,7 +442,10 @@ int run_bj_setup(hdg_ctx* h) {
 template <int D, int P>
 int run_bj_apply(hdg_ctx* h, const double* x, double* y) {
     using C = Cfg<D, P>;
-    k_bj_apply<C><<<(unsigned)((h->F + 7) / 8), 256, 0, h->stream>>>(h->d_bjlu, h->d_bjpiv, x, y, h->F);
+    if (h->bj_prec == HDG_PREC_MIXED)
+        k_bj_apply<C, float><<<(unsigned)((h->F + 7) / 8), 256, 0, h->stream>>>((const float*)h->d_bjlu, x, y, h->F);
+    else
+        k_bj_apply<C, double><<<(unsigned)((h->F + 7) / 8), 256, 0, h->stream>>>(h->d_bjlu, x, y, h->F);
     HDG_CK(cudaGetLastError());
     return HDG_OK;
 }

@@ -28,6 +28,59 @@ __global__ void k_dot_final(const double* part, int nparts, double* out, int tak
     }
 }
 
+// Partial sums of the dot products of w with vectors j0 .. j0+7 of V (fewer
+// when k - j0 < 8), one set per block: part[block][8].
+__global__ void k_mdot_part(const double* V, int64_t ldv, int j0, int k, const double* w, int64_t n, double* part) {
+    __shared__ double red[8][8];
+    const int nv = min(8, k - j0);
+    double acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double wi = w[i];
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+            if (q < nv) acc[q] = fma(V[(size_t)(j0 + q) * ldv + i], wi, acc[q]);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        double s = acc[q];
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) red[q][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        double t = 0.0;
+        for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += red[threadIdx.x][w2];
+        part[(size_t)blockIdx.x * 8 + threadIdx.x] = t;
+    }
+}
+
+// out[j0 + q] = sum over blocks (in block order) of part[b][q], q < min(8, k - j0)
+__global__ void k_mdot_final(const double* part, int nparts, int j0, int k, double* out) {
+    const int q = threadIdx.x;
+    if (q < 8 && j0 + q < k) {
+        double t = 0.0;
+        for (int b = 0; b < nparts; ++b) t += part[(size_t)b * 8 + q];
+        out[j0 + q] = t;
+    }
+}
+
+// w -= sum_j coef[j] V_j
+__global__ void k_msub(const double* V, int64_t ldv, const double* coef, int k, double* w, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = w[i];
+        for (int j = 0; j < k; ++j) s = fma(-coef[j], V[(size_t)j * ldv + i], s);
+        w[i] = s;
+    }
+}
+
+// a[i] += b[i], i < k (small vectors)
+__global__ void k_vadd(double* a, const double* b, int k) {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) a[i] += b[i];
+}
+
 __global__ void k_axpy_dev(const double* coef, double sign, const double* x, double* y, int64_t n) {
     const double a = sign * (*coef);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
