@@ -332,7 +332,7 @@ def run_ours(args, rank, world, local_rank):
             return None
         rep = H.hdg_autotune(h, U, Q, UH, Us, nu, P.dt, P.a_ii, reps=1)
         return {k: rep[k] for k in ("elim_nb", "elim_minb", "schur_mode", "blocks_mode", "elim_mixed_minb",
-                                    "blocks64_mode")}
+                                    "blocks64_mode", "elim_mixed_split")}
 
     # FP64 form (the headline value); skipped when its arrays would not fit in HBM
     dgemm = fp64_peak_tflops(torch)

@@ -309,7 +309,8 @@ int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* 
  *    elimination kernel's panel width (16 or 8 columns) and the residency it
  *    is compiled for (2 or 1 CTAs per SM); results differ only by rounding
  *    order;
- *  - mixed form: the elimination kernel's residency (2 or 3 CTAs per SM),
+ *  - mixed form: the elimination as one fused kernel (at 2 or 3 CTAs per
+ *    SM) or split into an FP64 LU and two FP32 triangular solves,
  *    the volume contraction as FP32 SIMT (blocks_mode 0) or
  *    3xTF32 tensor cores (1, 3-D), and, when requested as HDG_PREC_MIXED,
  *    the Schur product as FP32 SIMT (schur_mode 0) or 3xTF32 tensor cores
@@ -319,11 +320,11 @@ int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* 
  * left assembled is that of the last candidate timed. */
 typedef struct {
     int elim_nb, elim_minb, schur_mode;   /* the chosen variant */
-    int blocks_mode, elim_mixed_minb, blocks64_mode;
-    int n_cand;                           /* candidates timed (<= 8) */
-    int cand[8][6];                       /* (elim_nb, elim_minb, schur_mode, blocks_mode, elim_mixed_minb,
-                                             blocks64_mode) of each candidate */
-    double ms[8];                         /* mean time of one linearize + condense, ms */
+    int blocks_mode, elim_mixed_minb, blocks64_mode, elim_mixed_split;
+    int n_cand;                           /* candidates timed (<= 16) */
+    int cand[16][7];                      /* (elim_nb, elim_minb, schur_mode, blocks_mode, elim_mixed_minb,
+                                             blocks64_mode, elim_mixed_split) of each candidate */
+    double ms[16];                        /* mean time of one linearize + condense, ms */
 } hdg_tune;
 int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* UH, const double* Ustar,
                  const double* nu, double dt, double a_ii, int reps, hdg_tune* out);

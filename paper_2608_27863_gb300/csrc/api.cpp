@@ -189,6 +189,7 @@ int ensure_system_storage(hdg_ctx* h, int precision) {
     if ((rc = dev_alloc(h, &h->d_mrb, ch * NT))) return rc;
     if ((rc = dev_alloc(h, &h->d_vals32, (size_t)h->nnzb * h->BS * h->BS))) return rc;
     if ((rc = dev_alloc(h, &h->d_x32, (size_t)h->F * h->BS))) return rc;
+    if ((rc = dev_alloc(h, &h->d_mpiv, E * NU))) return rc;
     return HDG_OK;
 }
 }  // namespace hdg
@@ -322,7 +323,7 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (reps < 1 || reps > 100) return fail(h, HDG_EINVAL, "reps must be in 1..100");
     // candidates: variants that compute the same quantities to the same accuracy
-    int cand[8][6];
+    int cand[16][7];
     int n = 0;
     if (h->precision == HDG_PREC_FP64) {
         const int nbs[2] = {16, 8}, minbs[2] = {2, 1};
@@ -330,7 +331,7 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
             for (int a = 0; a < 2; ++a)
                 for (int b = 0; b < 2; ++b) {
                     cand[n][0] = nbs[a]; cand[n][1] = minbs[b]; cand[n][2] = h->schur_mode; cand[n][3] = h->blocks_mode;
-                    cand[n][4] = h->elim_mixed_minb; cand[n][5] = bm64; ++n;
+                    cand[n][4] = h->elim_mixed_minb; cand[n][5] = bm64; cand[n][6] = h->elim_mixed_split; ++n;
                 }
     } else {
         // FP32 SIMT and 3xTF32 tensor-core products are both FP32-accurate: the volume
@@ -343,9 +344,10 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
             for (int bm : {1, 2, 0}) {
                 if (bm == 1 && h->d != 3) continue;
                 if (bm == 0 && free_schur) continue;
-                for (int mb : {2, 3}) {
+                for (int ev : {0, 2, 3}) {       // elimination: split (0), fused at 2 or 3 CTAs per SM
                     cand[n][0] = h->elim_nb; cand[n][1] = h->elim_minb; cand[n][2] = free_schur ? sm : h->schur_mode;
-                    cand[n][3] = bm; cand[n][4] = mb; cand[n][5] = h->blocks64_mode; ++n;
+                    cand[n][3] = bm; cand[n][4] = ev == 0 ? h->elim_mixed_minb : ev; cand[n][5] = h->blocks64_mode;
+                    cand[n][6] = ev == 0 ? 1 : 0; ++n;
                 }
             }
         }
@@ -353,7 +355,7 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
     cudaEvent_t ev[2];
     CKH(cudaEventCreate(&ev[0]));
     CKH(cudaEventCreate(&ev[1]));
-    double ms[8];
+    double ms[16];
     int best = 0, rc = HDG_OK;
     for (int c = 0; c < n && rc == HDG_OK; ++c) {
         h->elim_nb = cand[c][0];
@@ -362,6 +364,7 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
         h->blocks_mode = cand[c][3];
         h->elim_mixed_minb = cand[c][4];
         h->blocks64_mode = cand[c][5];
+        h->elim_mixed_split = cand[c][6];
         if ((rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr))) break;   // warm-up
         cudaEventRecord(ev[0], h->stream);
         for (int r = 0; r < reps && rc == HDG_OK; ++r) rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr);
@@ -383,13 +386,14 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
     h->blocks_mode = cand[best][3];
     h->elim_mixed_minb = cand[best][4];
     h->blocks64_mode = cand[best][5];
+    h->elim_mixed_split = cand[best][6];
     if (out) {
         out->elim_nb = h->elim_nb; out->elim_minb = h->elim_minb; out->schur_mode = h->schur_mode;
         out->blocks_mode = h->blocks_mode; out->elim_mixed_minb = h->elim_mixed_minb;
-        out->blocks64_mode = h->blocks64_mode;
+        out->blocks64_mode = h->blocks64_mode; out->elim_mixed_split = h->elim_mixed_split;
         out->n_cand = n;
-        for (int c = 0; c < 8; ++c) {
-            for (int k = 0; k < 6; ++k) out->cand[c][k] = c < n ? cand[c][k] : 0;
+        for (int c = 0; c < 16; ++c) {
+            for (int k = 0; k < 7; ++k) out->cand[c][k] = c < n ? cand[c][k] : 0;
             out->ms[c] = c < n ? ms[c] : 0.0;
         }
     }
@@ -400,9 +404,10 @@ int hdg_set_tuning(hdg_handle h, const hdg_tune* t) {
     if (!h || !t) return fail(h, HDG_EINVAL, "NULL argument");
     if ((t->elim_nb != 8 && t->elim_nb != 16) || (t->elim_minb != 1 && t->elim_minb != 2) ||
         t->schur_mode < 0 || t->schur_mode > 2 || t->blocks_mode < 0 || t->blocks_mode > 2 ||
-        (t->elim_mixed_minb != 2 && t->elim_mixed_minb != 3) || t->blocks64_mode < 0 || t->blocks64_mode > 1)
+        (t->elim_mixed_minb != 2 && t->elim_mixed_minb != 3) || t->blocks64_mode < 0 || t->blocks64_mode > 1 ||
+        t->elim_mixed_split < 0 || t->elim_mixed_split > 1)
         return fail(h, HDG_EINVAL, "elim_nb 8 or 16, elim_minb 1 or 2, schur_mode 0..2, blocks_mode 0..2, "
-                                   "elim_mixed_minb 2 or 3, blocks64_mode 0..1");
+                                   "elim_mixed_minb 2 or 3, blocks64_mode 0..1, elim_mixed_split 0..1");
     if (h->precision == HDG_PREC_MIXED && h->prec_req != HDG_PREC_MIXED && t->schur_mode != h->schur_mode)
         return fail(h, HDG_EINVAL, "the Schur precision was fixed by hdg_set_params");
     h->elim_nb = t->elim_nb;
@@ -410,6 +415,7 @@ int hdg_set_tuning(hdg_handle h, const hdg_tune* t) {
     h->blocks_mode = t->blocks_mode;
     h->elim_mixed_minb = t->elim_mixed_minb;
     h->blocks64_mode = t->blocks64_mode;
+    h->elim_mixed_split = t->elim_mixed_split;
     if (h->precision == HDG_PREC_MIXED) h->schur_mode = t->schur_mode;
     return HDG_OK;
 }

@@ -196,6 +196,7 @@ struct hdg_ctx {
     float* d_m21 = nullptr;                // [chunk][NT][NU] Ct, then W
     float* d_m22 = nullptr;                // [chunk][NT][NT] Dt, then S^K
     double* d_mrb = nullptr;               // [chunk][NT] Rh, then -g^K
+    int32_t* d_mpiv = nullptr;             // [E][NU] interchanges of the interior LU (split elimination)
     float* d_vals32 = nullptr;             // [nnzb][BS][BS] condensed blocks (FP32)
     float* d_x32 = nullptr;                // [F][BS] FP32 copy of a matvec operand
     int64_t chunk = 0;
@@ -203,6 +204,7 @@ struct hdg_ctx {
     int elim_minb = 2;                     // k_elim variant: resident CTAs per SM the kernel is built for
     int elim_nb = 16;                      // k_elim variant: panel width (16 or 8)
     int elim_mixed_minb = 2;               // k_elim_mixed variant: resident CTAs per SM (2 or 3)
+    int elim_mixed_split = 0;              // mixed elimination: 0 fused kernel, 1 FP64 LU + FP32 triangular solves
 
     // instrumentation: event pairs around kernel launches
     bool prof = false;

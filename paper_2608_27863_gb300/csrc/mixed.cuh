@@ -264,6 +264,261 @@ __global__ void __launch_bounds__(NTH, MINB) k_elim_mixed(Regions<float> R, int6
 
 // S^K = Dt - W Z (in place over Dt) and Rh <- Rh - W z, FP32 SIMT with FP32
 // accumulation (W [t][n_u] = Ct region, Z [n_u][t] = Bt region after k_elim_mixed)
+// ----------------------------------------------------------------------------
+// A3 + A4 of the mixed form, split by precision.  k_lu_mixed factors the
+// interior block in FP64 alone, P At = L U with partial pivoting (blocked
+// panels, pivot step in one warp, LAPACK-style full-row interchanges), and
+// forms z = L^{-1} P Rt; it stores the interchanges.  The FP32 border then
+// needs two triangular solves with many right-hand sides, each independent
+// per column (or row) and run by its own kernels:
+//   k_trsm_z:  Z = L^{-1} P Bt   (columns of Bt)
+//   k_trsm_w:  W = Ct U^{-1}     (rows of Ct)
+// 32-row blocks of the factor are staged in shared memory as FP32; the
+// off-diagonal part of each block step is a small product (threads over
+// rows x columns), the diagonal 32 x 32 triangle is solved per column.
+// ----------------------------------------------------------------------------
+template <class C, int NB>
+constexpr int lu_mixed_smem_bytes() { return (C::NU * NB + NB * 64) * 8; }
+
+template <class C, int NB, int NTH>
+__global__ void __launch_bounds__(NTH, 2) k_lu_mixed(Regions<float> R, int32_t* __restrict__ piv_out,
+                                                     int64_t e0, int32_t* status) {
+    constexpr int NU = C::NU;
+    static_assert(NTH == 256, "trailing-update layout assumes 256 threads");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t e = e0 + blockIdx.x;
+    double* A = R.a11 + e * R.a11_es;
+    double* rt = R.rt + e * R.rt_es;
+    const int64_t rs = R.a11_rs, srt = R.rt_rs;
+    auto rowp = [&](int r) -> double* { return A + (size_t)r * rs; };
+    extern __shared__ double sm[];
+    double* pan = sm;                    // [NU][NB], row index relative to k0
+    double* ust = pan + NU * NB;         // [NB][64]
+    __shared__ int piv[NB];
+    __shared__ int sflag;
+    if (tid == 0) sflag = 0;
+    __syncthreads();
+#pragma unroll 1
+    for (int k0 = 0; k0 < NU; k0 += NB) {
+        const int kb = min(NB, NU - k0), nrows = NU - k0;
+#pragma unroll 1
+        for (int idx = tid; idx < nrows * kb; idx += NTH) {
+            const int rr = idx / kb, c = idx - rr * kb;
+            pan[rr * NB + c] = rowp(k0 + rr)[k0 + c];
+        }
+        __syncthreads();
+#pragma unroll 1
+        for (int j = 0; j < kb; ++j) {
+            if (warp == 0) {
+                double bv = -1.0;
+                int bi = INT_MAX;
+#pragma unroll 1
+                for (int rr = j + lane; rr < nrows; rr += 32) {
+                    const double v = fabs(pan[rr * NB + j]);
+                    if (v > bv) { bv = v; bi = rr; }
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+                    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+                }
+                int pr = __shfl_sync(0xffffffffu, bi, 0);
+                if (pr == INT_MAX) {
+                    pr = j;
+                    if (lane == 0) sflag |= 2;
+                }
+                if (lane < kb && pr != j) {
+                    const double t = pan[j * NB + lane];
+                    pan[j * NB + lane] = pan[pr * NB + lane];
+                    pan[pr * NB + lane] = t;
+                }
+                if (lane == 0) piv[j] = pr;
+            }
+            __syncthreads();
+            double pv = pan[j * NB + j];
+            if (pv == 0.0 || !isfinite(pv)) {
+                if (tid == 0) sflag |= (pv == 0.0) ? 1 : 2;
+                pv = 1.0;
+            }
+            const double inv = 1.0 / pv;
+#pragma unroll 1
+            for (int rr = j + 1 + tid; rr < nrows; rr += NTH) {
+                const double l = pan[rr * NB + j] * inv;
+                pan[rr * NB + j] = l;
+                for (int c = j + 1; c < kb; ++c) pan[rr * NB + c] = fma(-l, pan[j * NB + c], pan[rr * NB + c]);
+            }
+            __syncthreads();
+        }
+#pragma unroll 1
+        for (int idx = tid; idx < nrows * kb; idx += NTH) {
+            const int rr = idx / kb, c = idx - rr * kb;
+            rowp(k0 + rr)[k0 + c] = pan[rr * NB + c];
+        }
+        // interchanges outside the panel (factor columns to the left, trailing columns
+        // and the right-hand side), then U12 = L11^{-1} A12 and the same for Rt
+        const int c0 = k0 + kb;
+#pragma unroll 1
+        for (int c = tid; c <= NU; c += NTH) {
+            if (c >= k0 && c < c0) continue;
+            double* col = c < NU ? A + c : rt;
+            const int64_t st = c < NU ? rs : srt;
+            for (int j = 0; j < kb; ++j) {
+                const int pr = piv[j];
+                if (pr != j) {
+                    const double t = col[(k0 + j) * st];
+                    col[(k0 + j) * st] = col[(k0 + pr) * st];
+                    col[(k0 + pr) * st] = t;
+                }
+            }
+            if (c >= c0) {
+                double xv[NB];
+#pragma unroll
+                for (int j = 0; j < NB; ++j) {
+                    if (j < kb) {
+                        double s = col[(k0 + j) * st];
+#pragma unroll
+                        for (int i = 0; i < NB; ++i)
+                            if (i < j) s = fma(-pan[j * NB + i], xv[i], s);
+                        xv[j] = s;
+                        col[(k0 + j) * st] = s;
+                    }
+                }
+            }
+        }
+        if (tid < kb) piv_out[e * NU + k0 + tid] = k0 + piv[tid];
+        __syncthreads();
+        trailing_region<double, NB, NTH>(rowp, [&](int j) { return rowp(k0 + j); }, c0, NU, c0, NU, pan, k0, kb, ust);
+        // right-hand side: rt[r] -= L21[r] . z1 for the rows below the panel
+#pragma unroll 1
+        for (int r = c0 + tid; r < NU; r += NTH) {
+            double s = rt[r * srt];
+            for (int j = 0; j < kb; ++j) s = fma(-pan[(r - k0) * NB + j], rt[(k0 + j) * srt], s);
+            rt[r * srt] = s;
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && sflag) atomicOr(status, sflag);
+}
+
+template <class C>
+struct TrsmShape {
+    static constexpr int CW = 64;                           // right-hand sides per CTA
+    static constexpr int NTH = 256;
+    static constexpr int smem_floats = C::NU * CW + 32 * C::NU;   // the block of right-hand sides, one factor block row
+};
+
+// Z = L^{-1} P Bt for columns [c0, c0 + CW) of Bt (FP32, in place); L unit lower (FP64 storage)
+template <class C>
+__global__ void __launch_bounds__(TrsmShape<C>::NTH) k_trsm_z(Regions<float> R, const int32_t* __restrict__ piv,
+                                                              int64_t e0) {
+    constexpr int NU = C::NU, NT = C::NT, CW = TrsmShape<C>::CW, NTH = TrsmShape<C>::NTH;
+    constexpr int NCT = (NT + CW - 1) / CW;
+    const int tid = threadIdx.x;
+    const int64_t e = e0 + blockIdx.x / NCT;
+    const int c0 = (int)(blockIdx.x % NCT) * CW;
+    const int cw = min(CW, NT - c0);
+    const double* A = R.a11 + e * R.a11_es;
+    float* Bt = R.a12 + e * R.a12_es;
+    const int64_t rs = R.a11_rs, bs = R.a12_rs;
+    extern __shared__ float smf[];
+    float* X = smf;                       // [NU][CW]
+    float* Lb = X + NU * CW;              // [32][NU] one block row of L
+    __shared__ int perm[NU];
+    if (tid == 0) {                       // the interchange sequence as a gather map
+        for (int i = 0; i < NU; ++i) perm[i] = i;
+        for (int i = 0; i < NU; ++i) {
+            const int q = piv[e * NU + i];
+            if (q != i) { const int t = perm[i]; perm[i] = perm[q]; perm[q] = t; }
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NU * CW; idx += NTH) {
+        const int i = idx / CW, c = idx - i * CW;
+        X[idx] = c < cw ? Bt[(size_t)perm[i] * bs + c0 + c] : 0.f;
+    }
+#pragma unroll 1
+    for (int i0 = 0; i0 < NU; i0 += 32) {
+        const int nb = min(32, NU - i0);
+        __syncthreads();
+        for (int idx = tid; idx < nb * (i0 + nb); idx += NTH) {
+            const int r = idx / (i0 + nb), j = idx - r * (i0 + nb);
+            Lb[r * NU + j] = (float)A[(size_t)(i0 + r) * rs + j];
+        }
+        __syncthreads();
+        // X[i0 + r][c] -= sum_{j < i0} L[i0 + r][j] X[j][c]
+        for (int idx = tid; idx < nb * CW; idx += NTH) {
+            const int r = idx / CW, c = idx - r * CW;
+            float s = X[(i0 + r) * CW + c];
+            for (int j = 0; j < i0; ++j) s = fmaf(-Lb[r * NU + j], X[j * CW + c], s);
+            X[(i0 + r) * CW + c] = s;
+        }
+        __syncthreads();
+        // the unit-lower diagonal block, one column per thread
+        for (int c = tid; c < CW; c += NTH)
+            for (int r = 1; r < nb; ++r) {
+                float s = X[(i0 + r) * CW + c];
+                for (int j = 0; j < r; ++j) s = fmaf(-Lb[r * NU + i0 + j], X[(i0 + j) * CW + c], s);
+                X[(i0 + r) * CW + c] = s;
+            }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NU * CW; idx += NTH) {
+        const int i = idx / CW, c = idx - i * CW;
+        if (c < cw) Bt[(size_t)i * bs + c0 + c] = X[idx];
+    }
+}
+
+// W = Ct U^{-1} for rows [r0, r0 + CW) of Ct (FP32, in place, chunk-local); U upper (FP64 storage)
+template <class C>
+__global__ void __launch_bounds__(TrsmShape<C>::NTH) k_trsm_w(Regions<float> R, int64_t e0) {
+    constexpr int NU = C::NU, NT = C::NT, CW = TrsmShape<C>::CW, NTH = TrsmShape<C>::NTH;
+    constexpr int NCT = (NT + CW - 1) / CW;
+    const int tid = threadIdx.x;
+    const int64_t el = blockIdx.x / NCT, e = e0 + el;
+    const int r0 = (int)(blockIdx.x % NCT) * CW;
+    const int rw = min(CW, NT - r0);
+    const double* A = R.a11 + e * R.a11_es;
+    float* Ct = R.a21 + el * R.a21_es;
+    const int64_t rs = R.a11_rs, cs = R.a21_rs;
+    extern __shared__ float smf[];
+    float* X = smf;                       // [NU][CW]: X[j][r] = Ct[r0 + r][j]
+    float* Ub = X + NU * CW;              // [32][NU]: Ub[q][j] = U[j][i0 + q], j < i0 + nb
+    for (int idx = tid; idx < NU * CW; idx += NTH) {
+        const int r = idx / NU, j = idx - r * NU;
+        X[j * CW + r] = r < rw ? Ct[(size_t)(r0 + r) * cs + j] : 0.f;
+    }
+#pragma unroll 1
+    for (int i0 = 0; i0 < NU; i0 += 32) {
+        const int nb = min(32, NU - i0);
+        __syncthreads();
+        for (int idx = tid; idx < (i0 + nb) * nb; idx += NTH) {
+            const int j = idx / nb, q = idx - j * nb;
+            Ub[q * NU + j] = (float)A[(size_t)j * rs + i0 + q];
+        }
+        __syncthreads();
+        // X[i0 + q][r] -= sum_{j < i0} U[j][i0 + q] X[j][r]
+        for (int idx = tid; idx < nb * CW; idx += NTH) {
+            const int q = idx / CW, r = idx - q * CW;
+            float s = X[(i0 + q) * CW + r];
+            for (int j = 0; j < i0; ++j) s = fmaf(-Ub[q * NU + j], X[j * CW + r], s);
+            X[(i0 + q) * CW + r] = s;
+        }
+        __syncthreads();
+        for (int r = tid; r < CW; r += NTH)
+            for (int q = 0; q < nb; ++q) {
+                float s = X[(i0 + q) * CW + r];
+                for (int j = 0; j < q; ++j) s = fmaf(-Ub[q * NU + i0 + j], X[(i0 + j) * CW + r], s);
+                const float d = Ub[q * NU + i0 + q];
+                X[(i0 + q) * CW + r] = s / (d != 0.f ? d : 1.f);
+            }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < NU * CW; idx += NTH) {
+        const int r = idx / NU, j = idx - r * NU;
+        if (r < rw) Ct[(size_t)(r0 + r) * cs + j] = X[j * CW + r];
+    }
+}
+
 template <class C, int NTH>
 __global__ void __launch_bounds__(NTH) k_schur_simt(Regions<float> R, int64_t e0) {
     constexpr int NU = C::NU, NT = C::NT, KC = 32, TW = 64;
@@ -574,6 +829,11 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
     HDG_CK(cudaFuncSetAttribute(k_blocks_sf<C, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sf32));
     HDG_CK(cudaFuncSetAttribute(k_elim_mixed<C, NB, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
     HDG_CK(cudaFuncSetAttribute(k_elim_mixed<C, NB, 256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
+    const int sm_lu = lu_mixed_smem_bytes<C, NB>();
+    const int sm_trsm = (int)sizeof(float) * TrsmShape<C>::smem_floats;
+    HDG_CK(cudaFuncSetAttribute(k_lu_mixed<C, NB, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_lu));
+    HDG_CK(cudaFuncSetAttribute(k_trsm_z<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_trsm));
+    HDG_CK(cudaFuncSetAttribute(k_trsm_w<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_trsm));
     cudaStream_t st = h->stream;
     HDG_CK(cudaMemsetAsync(h->d_vals32, 0, sizeof(float) * h->nnzb * C::BS * C::BS, st));
     HDG_CK(cudaMemsetAsync(h->d_g, 0, sizeof(double) * h->F * C::BS, st));
@@ -612,11 +872,18 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
         }
         prof_end(h);
         prof_begin(h, HDG_K_ELIM);
-        // variant chosen by the autotuner: built for 2 or 3 resident CTAs per SM
-        if (h->elim_mixed_minb == 3)
+        if (h->elim_mixed_split) {
+            // FP64 interior LU alone, then the FP32 border by two triangular solves
+            using TS = TrsmShape<C>;
+            constexpr int NCT = (C::NT + TS::CW - 1) / TS::CW;
+            k_lu_mixed<C, NB, 256><<<(unsigned)ne, 256, sm_lu, st>>>(RM, h->d_mpiv, e0, h->d_status);
+            k_trsm_z<C><<<(unsigned)(ne * NCT), TS::NTH, sm_trsm, st>>>(RM, h->d_mpiv, e0);
+            k_trsm_w<C><<<(unsigned)(ne * NCT), TS::NTH, sm_trsm, st>>>(RM, e0);
+        } else if (h->elim_mixed_minb == 3) {  // fused kernel, built for 3 or 2 resident CTAs per SM
             k_elim_mixed<C, NB, 256, 3><<<(unsigned)ne, 256, sm_elim, st>>>(RM, e0, h->d_status);
-        else
+        } else {
             k_elim_mixed<C, NB, 256, 2><<<(unsigned)ne, 256, sm_elim, st>>>(RM, e0, h->d_status);
+        }
         prof_end(h);
         prof_begin(h, HDG_K_SCHUR);
         if (h->schur_mode == 0) {

@@ -382,7 +382,8 @@ def hdg_tgv_diagnostics(h, U, Q):
 class hdg_tune(ctypes.Structure):
     _fields_ = [("elim_nb", ctypes.c_int), ("elim_minb", ctypes.c_int), ("schur_mode", ctypes.c_int),
                 ("blocks_mode", ctypes.c_int), ("elim_mixed_minb", ctypes.c_int), ("blocks64_mode", ctypes.c_int),
-                ("n_cand", ctypes.c_int), ("cand", (ctypes.c_int * 6) * 8), ("ms", ctypes.c_double * 8)]
+                ("elim_mixed_split", ctypes.c_int), ("n_cand", ctypes.c_int), ("cand", (ctypes.c_int * 7) * 16),
+                ("ms", ctypes.c_double * 16)]
 
 
 def hdg_autotune(h, U, Q, UH, Ustar, nu, dt, a_ii, reps=2):
@@ -392,13 +393,15 @@ def hdg_autotune(h, U, Q, UH, Ustar, nu, dt, a_ii, reps=2):
                                  int(reps), ctypes.byref(t)))
     return {"elim_nb": t.elim_nb, "elim_minb": t.elim_minb, "schur_mode": t.schur_mode,
             "blocks_mode": t.blocks_mode, "elim_mixed_minb": t.elim_mixed_minb, "blocks64_mode": t.blocks64_mode,
+            "elim_mixed_split": t.elim_mixed_split,
             "candidates": [(tuple(t.cand[i]), t.ms[i]) for i in range(t.n_cand)]}
 
 
-def hdg_set_tuning(h, elim_nb=16, elim_minb=2, schur_mode=0, blocks_mode=1, elim_mixed_minb=2, blocks64_mode=1):
+def hdg_set_tuning(h, elim_nb=16, elim_minb=2, schur_mode=0, blocks_mode=1, elim_mixed_minb=2, blocks64_mode=1,
+                   elim_mixed_split=0):
     t = hdg_tune()
     t.elim_nb, t.elim_minb, t.schur_mode, t.blocks_mode = elim_nb, elim_minb, schur_mode, blocks_mode
-    t.elim_mixed_minb, t.blocks64_mode = elim_mixed_minb, blocks64_mode
+    t.elim_mixed_minb, t.blocks64_mode, t.elim_mixed_split = elim_mixed_minb, blocks64_mode, elim_mixed_split
     _check(h, lib().hdg_set_tuning(h, ctypes.byref(t)))
 
 

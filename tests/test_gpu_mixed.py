@@ -142,8 +142,8 @@ def test_autotune_mixed_picks_fp32_accurate_schur():
     H.hdg_set_params(run.h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s,
                      precision=H.HDG_PREC_MIXED_TF32)
     rep = H.hdg_autotune(run.h, run.U, run.Q, run.UH, run.Ustar, run.nu, P.dt, P.a_ii, reps=1)
-    assert len(rep["candidates"]) == 6 and rep["schur_mode"] == 1
-    assert {c[3] for c, _ in rep["candidates"]} == {0, 1, 2} and {c[4] for c, _ in rep["candidates"]} == {2, 3}
+    assert len(rep["candidates"]) == 9 and rep["schur_mode"] == 1
+    assert {c[3] for c, _ in rep["candidates"]} == {0, 1, 2} and {c[6] for c, _ in rep["candidates"]} == {0, 1}
     run.close()
 
 
@@ -172,3 +172,34 @@ def test_tensor_core_contraction_matches_simt(make):
         v1, g1 = out[bm]
         assert np.linalg.norm(v1 - v0) <= 2e-6 * np.linalg.norm(v0), bm
         assert np.linalg.norm(g1 - g0) <= 2e-6 * np.linalg.norm(g0), bm
+
+
+
+@pytest.mark.parametrize("make", [lambda: synth.config2(n=3), lambda: synth.config3(n=3),
+                                  lambda: synth.tiny(2, 3, periodic=(True, False), visc_law=1, av=1e-3)],
+                         ids=["hex-p2", "hex-p3", "quad-p3-dirichlet"])
+def test_split_elimination_matches_fused(make):
+    """FP64 interior LU + FP32 triangular solves give the fused elimination's
+    condensed system to FP32 accuracy, and the same recovery."""
+    import torch
+    from paper_2608_27863_gb300 import hdg as H
+    P = make()
+    out = {}
+    for split in (0, 1):
+        run = GpuRun(P)
+        H.hdg_set_params(run.h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s,
+                         precision=H.HDG_PREC_MIXED_3XTF32)
+        H.hdg_set_tuning(run.h, schur_mode=2, blocks_mode=1 if P.mesh.dim == 3 else 0, elim_mixed_split=split)
+        run.linearize()
+        assert H.hdg_status(run.h) == 0
+        s = run.sizes
+        v = torch.empty(s["nnzb"] * s["block"] ** 2, dtype=torch.float32, device="cuda")
+        H.hdg_get_blocks(run.h, v)
+        rng = np.random.default_rng(2)
+        dq, du = run.recover(rng.normal(size=P.UH.shape) * 1e-3)
+        out[split] = (v.cpu().numpy().astype(np.float64), run.rhs(), du)
+        run.close()
+    (v0, g0, u0), (v1, g1, u1) = out[0], out[1]
+    assert np.linalg.norm(v1 - v0) <= 1e-5 * np.linalg.norm(v0)
+    assert np.linalg.norm(g1 - g0) <= 1e-5 * np.linalg.norm(g0)
+    assert np.linalg.norm(u1 - u0) <= 1e-5 * np.linalg.norm(u0)
