@@ -400,6 +400,34 @@ __global__ void __launch_bounds__(NTH, 2) k_lu_mixed(Regions<float> R, int32_t* 
     if (tid == 0 && sflag) atomicOr(status, sflag);
 }
 
+// X[i0 + r][c] -= sum_{j < i0} F[r][j] X[j][c] for r < nb, c < CW (F a staged factor
+// block row, row stride NU): each thread owns a 4-row x 2-column tile, so one pair
+// of shared loads feeds eight multiply-adds
+template <int NU, int CW, int NTH>
+__device__ __forceinline__ void trsm_offdiag_tile(const float* F, float* X, int i0, int nb) {
+    static_assert(32 * CW == 8 * NTH, "tile layout assumes 32 x CW outputs over NTH threads");
+    const int tid = threadIdx.x, cp = tid % (CW / 2), rq = tid / (CW / 2);
+    const int c = 2 * cp, r = 4 * rq;
+    float acc[4][2] = {};
+    if (i0 > 0) {
+        for (int j = 0; j < i0; ++j) {
+            const float x0 = X[j * CW + c], x1 = X[j * CW + c + 1];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float f = F[(r + u) * NU + j];
+                acc[u][0] = fmaf(f, x0, acc[u][0]);
+                acc[u][1] = fmaf(f, x1, acc[u][1]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (r + u < nb) {
+                X[(i0 + r + u) * CW + c] -= acc[u][0];
+                X[(i0 + r + u) * CW + c + 1] -= acc[u][1];
+            }
+    }
+}
+
 template <class C>
 struct TrsmShape {
     static constexpr int CW = 64;                           // right-hand sides per CTA
@@ -445,21 +473,26 @@ __global__ void __launch_bounds__(TrsmShape<C>::NTH) k_trsm_z(Regions<float> R, 
             Lb[r * NU + j] = (float)A[(size_t)(i0 + r) * rs + j];
         }
         __syncthreads();
-        // X[i0 + r][c] -= sum_{j < i0} L[i0 + r][j] X[j][c]
-        for (int idx = tid; idx < nb * CW; idx += NTH) {
-            const int r = idx / CW, c = idx - r * CW;
-            float s = X[(i0 + r) * CW + c];
-            for (int j = 0; j < i0; ++j) s = fmaf(-Lb[r * NU + j], X[j * CW + c], s);
-            X[(i0 + r) * CW + c] = s;
-        }
+        // X[i0 + r][c] -= sum_{j < i0} L[i0 + r][j] X[j][c]: each thread a 4 x 2 tile
+        trsm_offdiag_tile<NU, CW, NTH>(Lb, X, i0, nb);
         __syncthreads();
-        // the unit-lower diagonal block, one column per thread
-        for (int c = tid; c < CW; c += NTH)
-            for (int r = 1; r < nb; ++r) {
-                float s = X[(i0 + r) * CW + c];
-                for (int j = 0; j < r; ++j) s = fmaf(-Lb[r * NU + i0 + j], X[(i0 + j) * CW + c], s);
-                X[(i0 + r) * CW + c] = s;
+        // the unit-lower diagonal block, one column per thread, the column in registers
+        for (int c = tid; c < CW; c += NTH) {
+            float x[32];
+#pragma unroll
+            for (int r = 0; r < 32; ++r) x[r] = r < nb ? X[(i0 + r) * CW + c] : 0.f;
+#pragma unroll
+            for (int r = 1; r < 32; ++r) {
+                float s = x[r];
+#pragma unroll
+                for (int j = 0; j < 32; ++j)      // rows past nb read nothing: the staged block ends there
+                    if (j < r && r < nb) s = fmaf(-Lb[r * NU + i0 + j], x[j], s);
+                x[r] = r < nb ? s : 0.f;
             }
+#pragma unroll
+            for (int r = 0; r < 32; ++r)
+                if (r < nb) X[(i0 + r) * CW + c] = x[r];
+        }
     }
     __syncthreads();
     for (int idx = tid; idx < NU * CW; idx += NTH) {
@@ -496,21 +529,26 @@ __global__ void __launch_bounds__(TrsmShape<C>::NTH) k_trsm_w(Regions<float> R, 
             Ub[q * NU + j] = (float)A[(size_t)j * rs + i0 + q];
         }
         __syncthreads();
-        // X[i0 + q][r] -= sum_{j < i0} U[j][i0 + q] X[j][r]
-        for (int idx = tid; idx < nb * CW; idx += NTH) {
-            const int q = idx / CW, r = idx - q * CW;
-            float s = X[(i0 + q) * CW + r];
-            for (int j = 0; j < i0; ++j) s = fmaf(-Ub[q * NU + j], X[j * CW + r], s);
-            X[(i0 + q) * CW + r] = s;
-        }
+        // X[i0 + q][r] -= sum_{j < i0} U[j][i0 + q] X[j][r]: each thread a 4 x 2 tile
+        trsm_offdiag_tile<NU, CW, NTH>(Ub, X, i0, nb);
         __syncthreads();
-        for (int r = tid; r < CW; r += NTH)
-            for (int q = 0; q < nb; ++q) {
-                float s = X[(i0 + q) * CW + r];
-                for (int j = 0; j < q; ++j) s = fmaf(-Ub[q * NU + i0 + j], X[(i0 + j) * CW + r], s);
-                const float d = Ub[q * NU + i0 + q];
-                X[(i0 + q) * CW + r] = s / (d != 0.f ? d : 1.f);
+        for (int r = tid; r < CW; r += NTH) {
+            float x[32];
+#pragma unroll
+            for (int q = 0; q < 32; ++q) x[q] = q < nb ? X[(i0 + q) * CW + r] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                float s = x[q];
+#pragma unroll
+                for (int j = 0; j < 32; ++j)
+                    if (j < q && q < nb) s = fmaf(-Ub[q * NU + i0 + j], x[j], s);
+                const float d = q < nb ? Ub[q * NU + i0 + q] : 1.f;
+                x[q] = q < nb ? s / (d != 0.f ? d : 1.f) : 0.f;
             }
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                if (q < nb) X[(i0 + q) * CW + r] = x[q];
+        }
     }
     __syncthreads();
     for (int idx = tid; idx < NU * CW; idx += NTH) {
