@@ -369,6 +369,81 @@ int hdg_profile_read(hdg_handle h, double* ms, int64_t* launches);
 int hdg_linearize_condense_static(hdg_handle h, const double* U, const double* Q, const double* UH,
                                   const double* Ustar, const double* nu, double dt, double a_ii);
 
+/* ------------------------------------------------------------------------
+ * Tetrahedral meshes of per-element degree on quadratic geometry (the
+ * batched workload of Sec. 4: curved anisotropic tetrahedra with a mix of
+ * degrees).  Readings:
+ *   element space: total degree p_K in 1..4 on each tetrahedron, nodal
+ *     Lagrange basis on the equispaced lattice (i, j, k), i + j + k <= p_K,
+ *     node at xi = -1 + 2 (i, j, k) / p_K, k slowest and i fastest, on the
+ *     reference tetrahedron v0 = (-1,-1,-1), v1 = (1,-1,-1), v2 = (-1,1,-1),
+ *     v3 = (-1,-1,1); local face f is opposite vertex f;
+ *   trace space of a face: total degree p_F = max(p_L, p_R) (p_K on the
+ *     boundary), Lagrange on the equispaced lattice (i, j) of the face in its
+ *     canonical frame: vertices g0 < g1 < g2 by master id, node (i, j), j
+ *     slowest, at barycentric weights ((p_F - i - j), i, j) / p_F;
+ *   quadrature: collapsed Gauss-Jacobi rules with p_K + 2 points per
+ *     collapsed direction in the element, p_F + 2 on a face (exact to degree
+ *     2p + 3), face points placed in the canonical frame;
+ *   geometry: the isoparametric 10-node quadratic map (vertices, then the
+ *     midpoints of edges 01, 02, 03, 12, 13, 23), evaluated at every
+ *     quadrature point of curved elements; straight-sided elements keep one
+ *     affine record.
+ * Packed device layouts (FP64):
+ *   U, Ustar  per element [m][Np_e] back to back (offsets uoff, m = 5)
+ *   Q         per element [3][m][Np_e] (offset 3 uoff)
+ *   UH, g, x  per face [m][Nfp_F] back to back (offsets hoff)
+ *   blocks    block b (row face F, column face G) at boff[b], bs_F x bs_G,
+ *             bs = m Nfp, column-major: value (r, c) at boff[b] + c bs_F + r,
+ *             r = a Nfp_F + l.
+ * ---------------------------------------------------------------------- */
+#define HDG_TET 3
+
+typedef struct {
+    int64_t n_elem;
+    int64_t n_vert;
+    const double* vert_xyz;       /* [n_vert][3] */
+    const int64_t* elem_vert;     /* [n_elem][4], positively oriented */
+    const int64_t* periodic_map;  /* [n_vert] master vertex, or NULL */
+    const int32_t* bnd_tag;       /* [n_elem][4] per local face (kinds as for hdg_mesh), or NULL */
+    const int32_t* elem_p;        /* [n_elem] degrees 1..4 */
+    const double* geo;            /* [n_elem][10][3] quadratic nodes, or NULL for straight-sided elements */
+} hdg_tet_mesh;
+
+typedef struct {
+    int64_t n_elem, n_faces, nnzb;
+    int64_t n_u;                  /* sum of m Np_e: length of U (Q is 3 n_u) */
+    int64_t n_trace;              /* sum of m Nfp_F: length of UH, g, x */
+    int64_t n_vals;               /* sum of bs_F bs_G: length of the block values */
+    int64_t n_curved;             /* elements with per-point geometry */
+    int64_t device_bytes;
+} hdg_tet_sizes;
+
+/* Build tables, skeleton, geometry and device storage of a tetrahedral mesh.
+ * HDG_EUNSUPPORTED for degrees outside 1..4; HDG_EINVAL for inconsistent
+ * meshes (a face of more than two elements, repeated vertices, untagged
+ * boundary faces, tagged interior faces, a non-positive Jacobian at a
+ * quadrature point).  Supported calls on the handle: hdg_set_params (tau,
+ * viscosity law; FP64 only), hdg_set_bc_state, hdg_set_stream,
+ * hdg_linearize_condense (packed layouts; nu must be NULL), hdg_trace_matvec,
+ * hdg_trace_rhs, hdg_recover_interior, hdg_get_blocks, hdg_status,
+ * hdg_profile*, hdg_destroy; the others return HDG_EUNSUPPORTED. */
+int hdg_create_tet(hdg_handle* out, const hdg_tet_mesh* mesh, double gamma, double Re, double Pr, double Mach);
+int hdg_create_tet_host(hdg_handle* out, const hdg_tet_mesh* mesh, double gamma, double Re, double Pr,
+                        double Mach);
+int hdg_tet_query(hdg_handle h, hdg_tet_sizes* out);
+/* Host copies (any pointer may be NULL): uoff [E+1], hoff [F+1], face_p [F],
+ * f2e [F][2] (-1 on the boundary), e2f [E][4], frame [E][4][3] (local
+ * vertices of each face in canonical order), rowptr [F+1], col [nnzb]
+ * (ascending), boff [nnzb+1]. */
+int hdg_tet_layout(hdg_handle h, int64_t* uoff, int64_t* hoff, int32_t* face_p, int32_t* f2e, int32_t* e2f,
+                   int32_t* frame, int32_t* rowptr, int32_t* col, int64_t* boff);
+/* Reference tables (host): the element rule xq [Nq][3], wq [Nq] and basis
+ * phi [Nq][Np], dphi [3][Nq][Np] of degree p; the face rule xs [Nfq][2],
+ * ws [Nfq] and trace basis mu [Nfq][Nfp] of degree pF.  NULL skips. */
+int hdg_tet_ref_tables(int p, double* xq, double* wq, double* phi, double* dphi);
+int hdg_tri_ref_tables(int pF, double* xs, double* ws, double* mu);
+
 #ifdef __cplusplus
 }
 #endif

@@ -8,6 +8,7 @@
 #include <new>
 
 #include "common.h"
+#include "tet.h"
 
 using namespace hdg;
 
@@ -286,6 +287,7 @@ int hdg_destroy(hdg_handle h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
     if (h->gstream) cudaStreamDestroy(h->gstream);
     for (void* p : h->allocs) cudaFree(p);
+    if (h->tet) hdg::tet::destroy(h);
     delete h;
     return HDG_OK;
 }
@@ -300,6 +302,8 @@ int hdg_set_params(hdg_handle h, const hdg_params* prm) {
         return fail(h, HDG_EINVAL, "Sutherland constants must be positive");
     if (prm->precision < HDG_PREC_FP64 || prm->precision > HDG_PREC_MIXED_3XTF32)
         return fail(h, HDG_EUNSUPPORTED, "precision mode not available");
+    if (h->tet && prm->precision != HDG_PREC_FP64)
+        return fail(h, HDG_EUNSUPPORTED, "tetrahedral handles compute in FP64");
     h->phys.tau = prm->tau;
     h->phys.visc_law = prm->visc_law;
     h->phys.c1 = prm->suth_c1;
@@ -311,6 +315,7 @@ int hdg_set_params(hdg_handle h, const hdg_params* prm) {
 }
 
 int hdg_reserve(hdg_handle h, int precision) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (precision < HDG_PREC_FP64 || precision > HDG_PREC_MIXED_3XTF32) return fail(h, HDG_EINVAL, "unknown precision");
@@ -319,6 +324,7 @@ int hdg_reserve(hdg_handle h, int precision) {
 
 int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* UH, const double* Ustar,
                  const double* nu, double dt, double a_ii, int reps, hdg_tune* out) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (reps < 1 || reps > 100) return fail(h, HDG_EINVAL, "reps must be in 1..100");
@@ -401,6 +407,7 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
 }
 
 int hdg_set_tuning(hdg_handle h, const hdg_tune* t) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h || !t) return fail(h, HDG_EINVAL, "NULL argument");
     if ((t->elim_nb != 8 && t->elim_nb != 16) || (t->elim_minb != 1 && t->elim_minb != 2) ||
         t->schur_mode < 0 || t->schur_mode > 2 || t->blocks_mode < 0 || t->blocks_mode > 2 ||
@@ -438,6 +445,7 @@ int hdg_set_bc_state(hdg_handle h, int tag, const double* ub) {
 }
 
 int hdg_set_bc_field(hdg_handle h, const double* ubf) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (!h->has_tag[1]) return fail(h, HDG_EINVAL, "the mesh has no tag-1 faces");
@@ -463,6 +471,7 @@ int hdg_set_stream(hdg_handle h, void* stream) {
 }
 
 int hdg_query_sizes(hdg_handle h, hdg_sizes* o) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h || !o) return fail(h, HDG_EINVAL, "NULL argument");
     o->dim = h->d; o->p = h->p; o->m = h->m; o->Np = h->Np; o->Nq = h->Nq; o->nf = h->nf;
     o->Nfp = h->Nfp; o->Nfq = h->Nfq; o->n_u = h->NU; o->n_q = h->NQV; o->t = h->NT; o->block = h->BS;
@@ -472,6 +481,7 @@ int hdg_query_sizes(hdg_handle h, hdg_sizes* o) {
 
 int hdg_get_connectivity(hdg_handle h, int32_t* f2e, int32_t* f2lf, int32_t* e2f, int32_t* perm,
                          int32_t* rowptr, int32_t* col) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     const Skeleton& s = h->sk;
     if (f2e) std::memcpy(f2e, s.f2e.data(), s.f2e.size() * sizeof(int32_t));
@@ -493,6 +503,10 @@ int hdg_linearize_condense(hdg_handle h, const double* U, const double* Q, const
     if (h->has_tag[1] && !h->ub_set) return fail(h, HDG_EINVAL, "boundary state of tag 1 not set (hdg_set_bc_state)");
     if (h->has_tag[3] && !h->tw_set) return fail(h, HDG_EINVAL, "wall temperature of tag 3 not set (hdg_set_bc_state)");
     CKH(cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), h->stream));
+    if (h->tet) {
+        if (nu) return fail(h, HDG_EUNSUPPORTED, "artificial viscosity is not available on tetrahedral handles");
+        return hdg::tet::linearize(h, U, Q, UH, Ustar, dt, a_ii);
+    }
     LinArgs a{U, Q, UH, Ustar, nu, dt, a_ii};
     if (h->precision == HDG_PREC_MIXED) {
         DISPATCH(run_linearize_mixed, h, a);
@@ -502,6 +516,11 @@ int hdg_linearize_condense(hdg_handle h, const double* U, const double* Q, const
 
 int hdg_trace_matvec(hdg_handle h, const double* x, double* y) {
     if (!h) return HDG_EINVAL;
+    if (h->tet) {
+        if (!h->device || !h->tet->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
+        if (!x || !y || x == y) return fail(h, HDG_EINVAL, "x and y must be distinct device arrays");
+        return hdg::tet::matvec(h, x, y);
+    }
     if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
     if (!x || !y || x == y) return fail(h, HDG_EINVAL, "x and y must be distinct device arrays");
     DISPATCH(run_matvec, h, x, y);
@@ -509,6 +528,12 @@ int hdg_trace_matvec(hdg_handle h, const double* x, double* y) {
 
 int hdg_trace_rhs(hdg_handle h, double* g) {
     if (!h) return HDG_EINVAL;
+    if (h->tet) {
+        if (!h->device || !h->tet->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
+        if (!g) return fail(h, HDG_EINVAL, "g is NULL");
+        CKH(cudaMemcpyAsync(g, h->tet->d_g, sizeof(double) * h->tet->n_trace, cudaMemcpyDeviceToDevice, h->stream));
+        return HDG_OK;
+    }
     if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
     if (!g) return fail(h, HDG_EINVAL, "g is NULL");
     CKH(cudaMemcpyAsync(g, h->d_g, sizeof(double) * h->F * h->BS, cudaMemcpyDeviceToDevice, h->stream));
@@ -517,6 +542,11 @@ int hdg_trace_rhs(hdg_handle h, double* g) {
 
 int hdg_recover_interior(hdg_handle h, const double* dUH, double* dQ, double* dU) {
     if (!h) return HDG_EINVAL;
+    if (h->tet) {
+        if (!h->device || !h->tet->have_system) return fail(h, HDG_EINVAL, "no linearization to recover from");
+        if (!dUH || !dQ || !dU) return fail(h, HDG_EINVAL, "NULL argument");
+        return hdg::tet::recover(h, dUH, dQ, dU);
+    }
     if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no linearization to recover from");
     if (!dUH || !dQ || !dU) return fail(h, HDG_EINVAL, "NULL argument");
     DISPATCH(run_recover, h, dUH, dQ, dU);
@@ -524,6 +554,13 @@ int hdg_recover_interior(hdg_handle h, const double* dUH, double* dQ, double* dU
 
 int hdg_get_blocks(hdg_handle h, double* vals) {
     if (!h) return HDG_EINVAL;
+    if (h->tet) {
+        if (!h->device || !h->tet->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
+        if (!vals) return fail(h, HDG_EINVAL, "vals is NULL");
+        CKH(cudaMemcpyAsync(vals, h->tet->d_vals, sizeof(double) * h->tet->n_vals, cudaMemcpyDeviceToDevice,
+                            h->stream));
+        return HDG_OK;
+    }
     if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
     if (!vals) return fail(h, HDG_EINVAL, "vals is NULL");
     const size_t bytes = (h->sys_prec == HDG_PREC_MIXED ? sizeof(float) : sizeof(double)) * h->nnzb * h->BS * h->BS;
@@ -567,6 +604,52 @@ int hdg_profile_read(hdg_handle h, double* ms, int64_t* launches) {
     }
     h->ev_kind.clear();
     h->ev_used = 0;
+    return HDG_OK;
+}
+
+int hdg_create_tet_host(hdg_handle* out, const hdg_tet_mesh* mesh, double gamma, double Re, double Pr,
+                        double Mach) {
+    if (!out) return HDG_EINVAL;
+    *out = nullptr;
+    hdg_ctx* h = new (std::nothrow) hdg_ctx();
+    if (!h) return HDG_ENOMEM;
+    *out = h;  // returned even on failure so that hdg_last_error works
+    if (!(gamma > 1.0) || !(Re > 0.0) || !(Pr > 0.0) || !(Mach > 0.0))
+        return fail(h, HDG_EINVAL, "gamma > 1, Re > 0, Pr > 0, Mach > 0 required");
+    h->phys = Phys{gamma, Re, Pr, Mach, 5.0, 0, 1.4042, 0.40417};
+    return hdg::tet::create_host(h, mesh, h->err);
+}
+
+int hdg_create_tet(hdg_handle* out, const hdg_tet_mesh* mesh, double gamma, double Re, double Pr, double Mach) {
+    int rc = hdg_create_tet_host(out, mesh, gamma, Re, Pr, Mach);
+    if (rc) return rc;
+    return hdg::tet::create_device(*out, (*out)->err);
+}
+
+int hdg_tet_query(hdg_handle h, hdg_tet_sizes* o) {
+    if (!h || !o) return fail(h, HDG_EINVAL, "NULL argument");
+    if (!h->tet) return fail(h, HDG_EINVAL, "not a tetrahedral handle");
+    const hdg::tet::Ctx* c = h->tet;
+    o->n_elem = c->E; o->n_faces = c->F; o->nnzb = c->nnzb; o->n_u = c->n_u; o->n_trace = c->n_trace;
+    o->n_vals = c->n_vals; o->n_curved = c->n_curved; o->device_bytes = h->device_bytes;
+    return HDG_OK;
+}
+
+int hdg_tet_layout(hdg_handle h, int64_t* uoff, int64_t* hoff, int32_t* face_p, int32_t* f2e, int32_t* e2f,
+                   int32_t* frame, int32_t* rowptr, int32_t* col, int64_t* boff) {
+    if (!h) return HDG_EINVAL;
+    if (!h->tet) return fail(h, HDG_EINVAL, "not a tetrahedral handle");
+    const hdg::tet::Ctx* c = h->tet;
+    auto cp = [](void* dst, const void* src, size_t bytes) { if (dst) std::memcpy(dst, src, bytes); };
+    cp(uoff, c->uoff.data(), c->uoff.size() * sizeof(int64_t));
+    cp(hoff, c->hoff.data(), c->hoff.size() * sizeof(int64_t));
+    cp(face_p, c->face_p.data(), c->face_p.size() * sizeof(int32_t));
+    cp(f2e, c->f2e.data(), c->f2e.size() * sizeof(int32_t));
+    cp(e2f, c->e2f.data(), c->e2f.size() * sizeof(int32_t));
+    cp(frame, c->frame.data(), c->frame.size() * sizeof(int32_t));
+    cp(rowptr, c->rowptr.data(), c->rowptr.size() * sizeof(int32_t));
+    cp(col, c->col.data(), c->col.size() * sizeof(int32_t));
+    cp(boff, c->boff.data(), c->boff.size() * sizeof(int64_t));
     return HDG_OK;
 }
 

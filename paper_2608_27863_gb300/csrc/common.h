@@ -83,9 +83,11 @@ struct DeviceTables {
     float* fphi; float* fdphi; float* fpsi; float* ftheta; float* fpsi_f; float* ftheta_f; float* fmu; float* fmf;
 };
 
+namespace tet { struct Ctx; }
 }  // namespace hdg
 
 struct hdg_ctx {
+    hdg::tet::Ctx* tet = nullptr;          // tetrahedral handles (hdg_create_tet), else NULL
     int d = 0, p = 0;
     int m = 0, Np = 0, Nq = 0, nf = 0, Nfp = 0, Nfq = 0;
     int NU = 0, NQV = 0, NT = 0, NR = 0, NC = 0, LD = 0, BS = 0, NCOEF = 0;

@@ -59,6 +59,7 @@ int dispatch(hdg_ctx* h, const hdg::LinArgs& a) {
 
 extern "C" int hdg_linearize_condense_static(hdg_handle h, const double* U, const double* Q, const double* UH,
                                               const double* Ustar, const double* nu, double dt, double a_ii) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage (created with hdg_create_host)");
     if (!U || !Q || !UH || !Ustar) return fail(h, HDG_EINVAL, "U, Q, UH and Ustar are required");

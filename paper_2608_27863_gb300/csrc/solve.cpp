@@ -236,6 +236,7 @@ extern "C" {
 
 int hdg_residual(hdg_handle h, const double* U, const double* Q, const double* UH, const double* Ustar,
                  const double* nu, double dt, double a_ii, double* Rq, double* Ru, double* Ruh, double* norms) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (!U || !Q || !UH || !Ustar) return fail(h, HDG_EINVAL, "U, Q, UH and Ustar are required");
@@ -257,6 +258,7 @@ int hdg_residual(hdg_handle h, const double* U, const double* Q, const double* U
 }
 
 int hdg_lift_gradient(hdg_handle h, const double* U, const double* UH, double* Q) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (!U || !UH || !Q) return fail(h, HDG_EINVAL, "U, UH and Q are required");
@@ -267,6 +269,7 @@ int hdg_lift_gradient(hdg_handle h, const double* U, const double* UH, double* Q
 
 int hdg_update_state(hdg_handle h, double* U, double* Q, double* UH, const double* dU, const double* dQ,
                      const double* dUH, double alpha) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (!U || !Q || !UH || !dU || !dQ || !dUH) return fail(h, HDG_EINVAL, "NULL argument");
@@ -279,6 +282,7 @@ int hdg_update_state(hdg_handle h, double* U, double* Q, double* UH, const doubl
 }
 
 int hdg_blockjacobi_setup(hdg_handle h) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
     int rc;
@@ -292,6 +296,7 @@ int hdg_blockjacobi_setup(hdg_handle h) {
 }
 
 int hdg_set_preconditioner(hdg_handle h, int kind) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (kind != HDG_PC_BLOCKJACOBI && kind != HDG_PC_SCHWARZ)
         return fail(h, HDG_EINVAL, "preconditioner must be HDG_PC_BLOCKJACOBI or HDG_PC_SCHWARZ");
@@ -300,12 +305,14 @@ int hdg_set_preconditioner(hdg_handle h, int kind) {
 }
 
 int hdg_schwarz_setup(hdg_handle h) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
     return schwarz_setup(h);
 }
 
 int hdg_schwarz_apply(hdg_handle h, const double* x, double* y) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->asm_ready) return fail(h, HDG_EINVAL, "additive Schwarz factors not set up");
     if (!x || !y || x == y) return fail(h, HDG_EINVAL, "x and y must be distinct device arrays");
@@ -315,6 +322,7 @@ int hdg_schwarz_apply(hdg_handle h, const double* x, double* y) {
 }
 
 int hdg_av_field(hdg_handle h, const double* U, const double* Q, double c_av, double h_m, double s_max, double* nu) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (!U || !Q || !nu) return fail(h, HDG_EINVAL, "U, Q and nu are required");
@@ -336,6 +344,7 @@ int hdg_av_field(hdg_handle h, const double* U, const double* Q, double c_av, do
 }
 
 int hdg_tgv_diagnostics(hdg_handle h, const double* U, const double* Q, double* out) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (!U || !Q || !out) return fail(h, HDG_EINVAL, "U, Q and out are required");
@@ -355,6 +364,7 @@ int hdg_tgv_diagnostics(hdg_handle h, const double* U, const double* Q, double* 
 }
 
 int hdg_rb_setup(hdg_handle h, int nb_max) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (nb_max < 0 || nb_max > kRbMax) return fail(h, HDG_EINVAL, "nb_max must be in 0..20");
@@ -378,6 +388,7 @@ int hdg_rb_setup(hdg_handle h, int nb_max) {
 }
 
 int hdg_rb_push(hdg_handle h, const double* w) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (h->rb_max <= 0) return fail(h, HDG_EINVAL, "reduced basis not set up (hdg_rb_setup)");
     if (!h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
@@ -386,6 +397,7 @@ int hdg_rb_push(hdg_handle h, const double* w) {
 }
 
 int hdg_rb_guess(hdg_handle h, const double* g, double* x0) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (h->rb_max <= 0) return fail(h, HDG_EINVAL, "reduced basis not set up (hdg_rb_setup)");
     if (!g || !x0 || g == x0) return fail(h, HDG_EINVAL, "g and x0 must be distinct device arrays");
@@ -393,6 +405,7 @@ int hdg_rb_guess(hdg_handle h, const double* g, double* x0) {
 }
 
 int hdg_blockjacobi_apply(hdg_handle h, const double* x, double* y) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->bj_ready) return fail(h, HDG_EINVAL, "block-Jacobi factors not set up");
     if (!x || !y || x == y) return fail(h, HDG_EINVAL, "x and y must be distinct device arrays");
@@ -403,6 +416,7 @@ int hdg_blockjacobi_apply(hdg_handle h, const double* x, double* y) {
 
 int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_iter, double rtol, int precond,
               int* iters_out, double* relres_out) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
     if (!b || !x || b == x) return fail(h, HDG_EINVAL, "b and x must be distinct device arrays");
@@ -508,6 +522,7 @@ int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_ite
 int hdg_newton(hdg_handle h, double* U, double* Q, double* UH, const double* Ustar, const double* nu, double dt,
                double a_ii, double tol, int max_newton, int restart, int max_gmres, double gmres_rtol,
                double* hist, int* newton_iters, int* gmres_iters) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (!U || !Q || !UH || !Ustar) return fail(h, HDG_EINVAL, "U, Q, UH and Ustar are required");
@@ -632,6 +647,7 @@ extern "C" {
 
 int hdg_newton_fixed(hdg_handle h, double* U, double* Q, double* UH, const double* Ustar, const double* nu,
                      double dt, double a_ii, int n_newton, int m, int use_graph, double* hist) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (!U || !Q || !UH || !Ustar) return fail(h, HDG_EINVAL, "U, Q, UH and Ustar are required");
@@ -665,6 +681,7 @@ int hdg_newton_fixed(hdg_handle h, double* U, double* Q, double* UH, const doubl
 
 int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* nu, double dt, int s,
                   const double* A, const double* b, int n_newton, int m, int use_graph, double* hist) {
+    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (!U || !Q || !UH || !A || !b) return fail(h, HDG_EINVAL, "NULL argument");

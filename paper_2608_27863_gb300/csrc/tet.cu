@@ -1,0 +1,984 @@
+// Tetrahedral elements of mixed degree on quadratic geometry on the device:
+// one persistent FP64 launch performs, element after element from a
+// cost-ordered work list, the quadrature-point fluxes and Jacobians (A1), the
+// exact elimination of the gradient q (per-element mass matrix and lifting
+// operators, curved geometry included), the contraction into the bordered
+// element matrix (A2) and its elimination into the Schur complement (A3, A4);
+// then the block assembly (A5), the trace matvec (A6) and the interior
+// recovery (A7) with variable block sizes.
+#include <algorithm>
+#include <climits>
+#include <cstring>
+
+#include "kernels.cuh"
+#include "tet.h"
+
+namespace hdg {
+namespace tet {
+
+static_assert(sizeof(TetElem) % 8 == 0, "descriptor copied as 64-bit words");
+
+constexpr int NTH = 256;
+constexpr int NPT = NQMAX + 4 * NFQMAX;   // volume + face points
+constexpr int NCM = NPMAX + 4 * NFPMAX;   // columns of one component: U nodes + trace nodes
+constexpr int KC = 40;                    // contraction: points staged per step
+constexpr int SRP = 36;                   // staged row-basis stride (NPMAX rounded up to 4)
+constexpr int STP = 96;                   // staged column stride (NCM rounded up to 4)
+constexpr int NB = 16;                    // elimination panel width
+constexpr int TCW = 64;                   // elimination column tile
+constexpr int NRMAX = M * NPMAX + 4 * M * NFPMAX;
+
+// per-CTA workspace layout (doubles)
+constexpr int64_t W_GV = 0;                              // [NQMAX][10] w|J|, J^{-1}[r][k]
+constexpr int64_t W_GF = W_GV + NQMAX * 10;              // [4 NFQMAX][3] w_s |J| J^{-T} nu
+constexpr int64_t W_PU = W_GF + 4 * NFQMAX * 3;          // [NPT][m] u
+constexpr int64_t W_PQ = W_PU + NPT * M;                 // [NPT][m][3] q
+constexpr int64_t W_PL = W_PQ + NPT * M * 3;             // [NPT][m][3] lifted q
+constexpr int64_t W_PH = W_PL + NPT * M * 3;             // [4 NFQMAX][m] uhat
+constexpr int64_t W_CV = W_PH + 4 * NFQMAX * M;          // [NQMAX][a][r][b][kind 4]
+constexpr int64_t W_CF = W_CV + (int64_t)NQMAX * 300;    // [4 NFQMAX][a][b][kind 5]  element rows (dt folded)
+constexpr int64_t W_CB = W_CF + 4 * NFQMAX * 125;        // [4 NFQMAX][a][b][kind 5]  trace rows
+constexpr int64_t W_RV = W_CB + 4 * NFQMAX * 125;        // [NQMAX][a][r]
+constexpr int64_t W_RF = W_RV + NQMAX * 15;              // [4 NFQMAX][a]
+constexpr int64_t W_RB = W_RF + 4 * NFQMAX * M;          // [4 NFQMAX][a]
+constexpr int64_t W_MM = W_RB + 4 * NFQMAX * M;          // [NPMAX][NPMAX] mass matrix, then its Cholesky factor
+constexpr int64_t W_DP = W_MM + NPMAX * NPMAX;           // [NQMAX][3][NPMAX] physical gradients
+constexpr int64_t W_VQ = W_DP + NQMAX * 3 * NPMAX;       // [3][NPT][NCM] psi | chi
+constexpr int64_t W_END = W_VQ + 3LL * NPT * NCM;
+
+// shared memory layout (doubles)
+constexpr int S_U = 0;                                   // [m][Np]
+constexpr int S_US = S_U + M * NPMAX;                    // [m][Np] Ustar
+constexpr int S_Q = S_US + M * NPMAX;                    // [3][m][Np]
+constexpr int S_QL = S_Q + 3 * M * NPMAX;                // [3][m][Np] lifted gradient
+constexpr int S_UH = S_QL + 3 * M * NPMAX;               // [t] element trace
+constexpr int S_DYN = S_UH + 4 * M * NFPMAX;             // phase scratch
+constexpr int S_GEMM = KC * (SRP + STP);
+constexpr int S_ELIM = NRMAX * NB + NB * TCW;
+constexpr int S_TOTAL = S_DYN + (S_GEMM > S_ELIM ? S_GEMM : S_ELIM);
+
+struct KArgs {
+    const TetElem* el; const int32_t* order; int64_t E; int32_t* next;
+    const double* tab; const double* gvol; const double* gface;
+    const double* U; const double* Q; const double* UH; const double* Ustar;
+    double* mat; double* rec; double* work; int64_t wstride;
+    PhysT<double> ph; double dt, a_ii, tau; const double* ub; double ew;
+    int32_t* status;
+};
+
+__device__ __forceinline__ int face_of_point(const TetElem& d, int r) {
+    int f = 0;
+    while (f < 3 && r >= d.soff[f + 1]) ++f;
+    return f;
+}
+
+// element basis row at point x (volume points first, then the face points)
+__device__ __forceinline__ const double* basis_row(const KArgs& A, const TetElem& d, int x) {
+    if (x < d.Nq) return A.tab + d.vtab + (size_t)x * d.Np;
+    const int r = x - d.Nq, f = face_of_point(d, r);
+    return A.tab + d.ftab[f] + (size_t)(r - d.soff[f]) * d.Np;
+}
+
+// runtime-sized tile of the trailing update A22 -= L21 U12 (rows rb + ty + 16 ii,
+// columns ct + tx + 16 jj)
+template <int NII, int NJJ, class RowP>
+__device__ __forceinline__ void trail_tile_rt(RowP rowp, const double* pan, const double* ust, int rb, int ct, int k0,
+                                              int kb, int tx, int ty, int NR, int NC) {
+    double acc[NII][NJJ];
+    double* rp[NII];
+#pragma unroll
+    for (int ii = 0; ii < NII; ++ii) {
+        const int r = rb + ty + 16 * ii;
+        rp[ii] = (r < NR) ? rowp(r) : nullptr;
+#pragma unroll
+        for (int jj = 0; jj < NJJ; ++jj) {
+            const int c = ct + tx + 16 * jj;
+            acc[ii][jj] = (rp[ii] && c < NC) ? rp[ii][c] : 0.0;
+        }
+    }
+    const double* lp = pan + (size_t)(rb + ty - k0) * NB;
+    for (int j = 0; j < kb; ++j) {
+        double lv[NII], uv[NJJ];
+#pragma unroll
+        for (int ii = 0; ii < NII; ++ii) lv[ii] = (rb + ty + 16 * ii < NR) ? lp[16 * ii * NB + j] : 0.0;
+#pragma unroll
+        for (int jj = 0; jj < NJJ; ++jj) uv[jj] = ust[j * TCW + tx + 16 * jj];
+#pragma unroll
+        for (int ii = 0; ii < NII; ++ii)
+#pragma unroll
+            for (int jj = 0; jj < NJJ; ++jj) acc[ii][jj] = fma(-lv[ii], uv[jj], acc[ii][jj]);
+    }
+#pragma unroll
+    for (int ii = 0; ii < NII; ++ii) {
+        if (!rp[ii]) continue;
+#pragma unroll
+        for (int jj = 0; jj < NJJ; ++jj) {
+            const int c = ct + tx + 16 * jj;
+            if (c < NC) rp[ii][c] = acc[ii][jj];
+        }
+    }
+}
+
+// Bordered elimination of the row-major matrix Mx [NR][LD] (columns NC = NR + 1):
+// LU with partial pivoting in the top NU rows (largest magnitude, lowest row on
+// ties), rows interchanged across all columns, trace rows eliminated, so that
+// the bottom-right block becomes S = Dt - Ct At^{-1} Bt and the last column
+// Rh - Ct At^{-1} Rt.
+__device__ void bordered_elim(double* Mx, int NU, int NR, int NC, int LD, double* pan, double* ust, int* piv,
+                              int* sflag) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    auto rowp = [&](int r) -> double* { return Mx + (size_t)r * LD; };
+    for (int k0 = 0; k0 < NU; k0 += NB) {
+        const int kb = min(NB, NU - k0), nrows = NR - k0, ntop = NU - k0;
+#pragma unroll 1
+        for (int idx = tid; idx < nrows * kb; idx += NTH) {
+            const int rr = idx / kb, c = idx - rr * kb;
+            pan[rr * NB + c] = rowp(k0 + rr)[k0 + c];
+        }
+        __syncthreads();
+        for (int j = 0; j < kb; ++j) {
+            if (warp == 0) {
+                double bv = -1.0;
+                int bi = INT_MAX;
+#pragma unroll 1
+                for (int rr = j + lane; rr < ntop; rr += 32) {
+                    const double v = fabs(pan[rr * NB + j]);
+                    if (v > bv) { bv = v; bi = rr; }
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+                    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+                }
+                int pr = __shfl_sync(0xffffffffu, bi, 0);
+                if (pr == INT_MAX) {
+                    pr = j;
+                    if (lane == 0) *sflag |= 2;
+                }
+                if (lane < kb && pr != j) {
+                    const double t = pan[j * NB + lane];
+                    pan[j * NB + lane] = pan[pr * NB + lane];
+                    pan[pr * NB + lane] = t;
+                }
+                if (lane == 0) piv[j] = pr;
+            }
+            __syncthreads();
+            double pv = pan[j * NB + j];
+            if (pv == 0.0 || !isfinite(pv)) {
+                if (tid == 0) *sflag |= (pv == 0.0) ? 1 : 2;
+                pv = 1.0;
+            }
+            const double inv = 1.0 / pv;
+#pragma unroll 1
+            for (int rr = j + 1 + tid; rr < nrows; rr += NTH) {
+                const double l = pan[rr * NB + j] * inv;
+                pan[rr * NB + j] = l;
+                for (int c = j + 1; c < kb; ++c) pan[rr * NB + c] = fma(-l, pan[j * NB + c], pan[rr * NB + c]);
+            }
+            __syncthreads();
+        }
+#pragma unroll 1
+        for (int idx = tid; idx < nrows * kb; idx += NTH) {
+            const int rr = idx / kb, c = idx - rr * kb;
+            rowp(k0 + rr)[k0 + c] = pan[rr * NB + c];
+        }
+        const int c0 = k0 + kb;
+#pragma unroll 1
+        for (int c = c0 + tid; c < NC; c += NTH) {
+            for (int j = 0; j < kb; ++j) {
+                const int pr = piv[j];
+                if (pr != j) {
+                    double* x = rowp(k0 + j) + c;
+                    double* y = rowp(k0 + pr) + c;
+                    const double t = *x;
+                    *x = *y;
+                    *y = t;
+                }
+            }
+            double xv[NB];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                if (j < kb) {
+                    double s = rowp(k0 + j)[c];
+#pragma unroll
+                    for (int i = 0; i < NB; ++i)
+                        if (i < j) s = fma(-pan[j * NB + i], xv[i], s);
+                    xv[j] = s;
+                    rowp(k0 + j)[c] = s;
+                }
+            }
+        }
+        __syncthreads();
+        const int tx = tid & 15, ty = tid >> 4;
+#pragma unroll 1
+        for (int ct = c0; ct < NC; ct += TCW) {
+            for (int idx = tid; idx < kb * TCW; idx += NTH) {
+                const int j = idx / TCW, cc = idx - j * TCW;
+                ust[j * TCW + cc] = (ct + cc < NC) ? rowp(k0 + j)[ct + cc] : 0.0;
+            }
+            __syncthreads();
+            int njj = 0;
+            while (njj < 4 && ct + 16 * njj < NC) ++njj;
+#pragma unroll 1
+            for (int rb = c0; rb < NR; rb += 64) {
+                int nii = 0;
+                while (nii < 4 && rb + 16 * nii < NR) ++nii;
+                switch (nii * 4 + njj - 5) {
+#define HDG_TT(I, J) \
+    case (I) * 4 + (J) - 5: trail_tile_rt<I, J>(rowp, pan, ust, rb, ct, k0, kb, tx, ty, NR, NC); break;
+                    HDG_TT(1, 1) HDG_TT(1, 2) HDG_TT(1, 3) HDG_TT(1, 4)
+                    HDG_TT(2, 1) HDG_TT(2, 2) HDG_TT(2, 3) HDG_TT(2, 4)
+                    HDG_TT(3, 1) HDG_TT(3, 2) HDG_TT(3, 3) HDG_TT(3, 4)
+                    HDG_TT(4, 1) HDG_TT(4, 2) HDG_TT(4, 3) HDG_TT(4, 4)
+#undef HDG_TT
+                    default: break;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// column index in the bordered matrix of column c (of component b) of the contraction
+__device__ __forceinline__ int bcol(const TetElem& d, int b, int c) {
+    if (c < d.Np) return b * d.Np + c;
+    int r = c - d.Np, f = 0;
+    while (f < 3 && r >= d.nfp[f]) { r -= d.nfp[f]; ++f; }
+    return d.NU + d.toff[f] + b * d.nfp[f] + r;
+}
+
+// one out[i][c] += sum_k R[k][i] T[k][c] pass over a staged chunk; 4 x 4 register tiles
+__device__ __forceinline__ void gemm_chunk(const double* sR, const double* sT, int kc, int ti, int tc, double acc[4][4]) {
+    for (int k = 0; k < kc; ++k) {
+        double rv[4], tv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { rv[u] = sR[k * SRP + 4 * ti + u]; tv[u] = sT[k * STP + 4 * tc + u]; }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(rv[u], tv[v], acc[u][v]);
+    }
+}
+
+__device__ void process_element(const KArgs& A, const TetElem& d, double* W, double* sm, int* sflag) {
+    const int tid = threadIdx.x;
+    const int Np = d.Np, Nq = d.Nq, NU = d.NU, t = d.t, LD = d.LD, sfq = d.sfq;
+    const int sfp = t / M, Nc = Np + sfp, npt = Nq + sfq;
+    const double* phi = A.tab + d.vtab;
+    const double* dphi = phi + (size_t)Nq * Np;
+    const double* wq = dphi + (size_t)3 * Nq * Np;
+    double* Mx = A.mat + d.moff;
+    double* Gk = A.rec + d.roff;                     // [3][Np][Np]
+    double* Hk = Gk + 3 * Np * Np;                   // [3][Np][sfp]
+    double* dq0 = Hk + 3 * Np * sfp;                 // [3][m][Np]
+    double* sU = sm + S_U;
+    double* sUs = sm + S_US;
+    double* sQ = sm + S_Q;
+    double* sQL = sm + S_QL;
+    double* sUH = sm + S_UH;
+    double* sD = sm + S_DYN;
+    double* gv = W + W_GV;
+    double* gf = W + W_GF;
+    int fpo[4];
+    fpo[0] = 0;
+    for (int f = 1; f < 4; ++f) fpo[f] = fpo[f - 1] + d.nfp[f - 1];
+
+    // A0: gather
+    for (int i = tid; i < NU; i += NTH) { sU[i] = A.U[d.uoff + i]; sUs[i] = A.Ustar[d.uoff + i]; }
+    for (int i = tid; i < 3 * NU; i += NTH) sQ[i] = A.Q[3 * d.uoff + i];
+    for (int i = tid; i < t; i += NTH) {
+        int f = 0, r = i;
+        while (f < 3 && r >= M * d.nfp[f]) { r -= M * d.nfp[f]; ++f; }
+        sUH[i] = A.UH[d.hoff[f] + r];
+    }
+    // geometry at the quadrature points
+    for (int g = tid; g < Nq; g += NTH) {
+        double* o = gv + g * 10;
+        if (d.curved) {
+            for (int k = 0; k < 10; ++k) o[k] = A.gvol[d.goff + (int64_t)g * 10 + k];
+        } else {
+            o[0] = wq[g] * d.detJ;
+            for (int k = 0; k < 9; ++k) o[1 + k] = d.Jinv[k];
+        }
+    }
+    for (int r = tid; r < sfq; r += NTH) {
+        double* o = gf + r * 3;
+        if (d.curved) {
+            for (int k = 0; k < 3; ++k) o[k] = A.gface[d.gfoff + (int64_t)r * 3 + k];
+        } else {
+            const int f = face_of_point(d, r), s = r - d.soff[f];
+            const double* nu = A.tab + d.ftab[f] + (size_t)d.nfq[f] * Np;
+            const double ws = A.tab[d.ttab[f] + (size_t)d.nfq[f] * d.nfp[f] + s];
+            for (int k = 0; k < 3; ++k)
+                o[k] = ws * d.detJ * (d.Jinv[0 * 3 + k] * nu[0] + d.Jinv[1 * 3 + k] * nu[1] + d.Jinv[2 * 3 + k] * nu[2]);
+        }
+    }
+    __syncthreads();
+    // physical gradients at the volume points, mass matrix
+    double* dp = W + W_DP;
+    for (int idx = tid; idx < Nq * Np; idx += NTH) {
+        const int g = idx / Np, i = idx - g * Np;
+        const double* Ji = gv + g * 10 + 1;
+        const double d0 = dphi[(size_t)g * Np + i], d1 = dphi[((size_t)Nq + g) * Np + i],
+                     d2 = dphi[((size_t)2 * Nq + g) * Np + i];
+        for (int k = 0; k < 3; ++k) dp[(g * 3 + k) * NPMAX + i] = Ji[0 * 3 + k] * d0 + Ji[1 * 3 + k] * d1 + Ji[2 * 3 + k] * d2;
+    }
+    double* Mm = W + W_MM;
+    for (int idx = tid; idx < Np * Np; idx += NTH) {
+        const int i = idx / Np, j = idx - i * Np;
+        double s = 0.0;
+        for (int g = 0; g < Nq; ++g) s += gv[g * 10] * phi[(size_t)g * Np + i] * phi[(size_t)g * Np + j];
+        Mm[i * NPMAX + j] = s;
+    }
+    __syncthreads();
+    // E_k = (phi_j, d_k phi_i) into G; B_q,k = -<phi_i mu_l n_k> into H
+    for (int idx = tid; idx < 3 * Np * Np; idx += NTH) {
+        const int k = idx / (Np * Np), rem = idx - k * Np * Np, i = rem / Np, j = rem - i * Np;
+        double s = 0.0;
+        for (int g = 0; g < Nq; ++g) s += gv[g * 10] * dp[(g * 3 + k) * NPMAX + i] * phi[(size_t)g * Np + j];
+        Gk[idx] = s;
+    }
+    for (int idx = tid; idx < 3 * Np * sfp; idx += NTH) {
+        const int k = idx / (Np * sfp), rem = idx - k * Np * sfp, i = rem / sfp, cp = rem - i * sfp;
+        int f = 0, l = cp;
+        while (f < 3 && l >= d.nfp[f]) { l -= d.nfp[f]; ++f; }
+        const double* phf = A.tab + d.ftab[f];
+        const double* mu = A.tab + d.ttab[f];
+        double s = 0.0;
+        for (int q = 0; q < d.nfq[f]; ++q)
+            s += gf[(d.soff[f] + q) * 3 + k] * phf[(size_t)q * Np + i] * mu[(size_t)q * d.nfp[f] + l];
+        Hk[idx] = -s;
+    }
+    // Cholesky factor of the mass matrix (one warp)
+    if (tid < 32) {
+        for (int j = 0; j < Np; ++j) {
+            if (tid == 0) {
+                double s = Mm[j * NPMAX + j];
+                for (int k = 0; k < j; ++k) s -= Mm[j * NPMAX + k] * Mm[j * NPMAX + k];
+                Mm[j * NPMAX + j] = s > 0.0 ? sqrt(s) : 1.0;
+                if (!(s > 0.0)) atomicOr(sflag, 1);
+            }
+            __syncwarp();
+            const double ljj = Mm[j * NPMAX + j];
+            for (int i = j + 1 + tid; i < Np; i += 32) {
+                double s = Mm[i * NPMAX + j];
+                for (int k = 0; k < j; ++k) s -= Mm[i * NPMAX + k] * Mm[j * NPMAX + k];
+                Mm[i * NPMAX + j] = s / ljj;
+            }
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+    // G_k = M^{-1} E_k, H_k = M^{-1} B_q,k: one column per thread (forward, backward substitution)
+    for (int col = tid; col < 3 * Nc; col += NTH) {
+        const int k = col / Nc, c = col - k * Nc;
+        double* x;
+        int st;
+        if (c < Np) { x = Gk + (size_t)k * Np * Np + c; st = Np; }
+        else { x = Hk + (size_t)k * Np * sfp + (c - Np); st = sfp; }
+        for (int i = 0; i < Np; ++i) {
+            double s = x[i * st];
+            for (int j = 0; j < i; ++j) s -= Mm[i * NPMAX + j] * x[j * st];
+            x[i * st] = s / Mm[i * NPMAX + i];
+        }
+        for (int i = Np - 1; i >= 0; --i) {
+            double s = x[i * st];
+            for (int j = i + 1; j < Np; ++j) s -= Mm[j * NPMAX + i] * x[j * st];
+            x[i * st] = s / Mm[i * NPMAX + i];
+        }
+    }
+    __syncthreads();
+    // lifted gradient Q_lift = -G U - H Uhat (the gradient equations hold exactly)
+    for (int idx = tid; idx < 3 * NU; idx += NTH) {
+        const int k = idx / NU, rem = idx - k * NU, a = rem / Np, i = rem - a * Np;
+        double s = 0.0;
+        for (int j = 0; j < Np; ++j) s += Gk[((size_t)k * Np + i) * Np + j] * sU[a * Np + j];
+        for (int f = 0; f < 4; ++f)
+            for (int l = 0; l < d.nfp[f]; ++l)
+                s += Hk[((size_t)k * Np + i) * sfp + fpo[f] + l] * sUH[d.toff[f] + a * d.nfp[f] + l];
+        sQL[idx] = -s;
+        dq0[idx] = -s - sQ[idx];
+    }
+    __syncthreads();
+    // values at the points; psi | chi (the q variation of unit U / Uhat columns)
+    double* pu = W + W_PU;
+    double* pq = W + W_PQ;
+    double* pl = W + W_PL;
+    double* ph = W + W_PH;
+    for (int x = tid; x < npt; x += NTH) {
+        const double* br = basis_row(A, d, x);
+        double u[M], q[M][3], ql[M][3];
+        for (int a = 0; a < M; ++a) { u[a] = 0.0; for (int k = 0; k < 3; ++k) { q[a][k] = 0.0; ql[a][k] = 0.0; } }
+        for (int j = 0; j < Np; ++j) {
+            const double w = br[j];
+            for (int a = 0; a < M; ++a) {
+                u[a] += w * sU[a * Np + j];
+                for (int k = 0; k < 3; ++k) {
+                    q[a][k] += w * sQ[(k * M + a) * Np + j];
+                    ql[a][k] += w * sQL[(k * M + a) * Np + j];
+                }
+            }
+        }
+        for (int a = 0; a < M; ++a) {
+            pu[x * M + a] = u[a];
+            for (int k = 0; k < 3; ++k) { pq[(x * M + a) * 3 + k] = q[a][k]; pl[(x * M + a) * 3 + k] = ql[a][k]; }
+        }
+        if (x >= Nq) {
+            const int r = x - Nq, f = face_of_point(d, r), s = r - d.soff[f];
+            const double* mu = A.tab + d.ttab[f] + (size_t)s * d.nfp[f];
+            for (int a = 0; a < M; ++a) {
+                double v = 0.0;
+                for (int l = 0; l < d.nfp[f]; ++l) v += mu[l] * sUH[d.toff[f] + a * d.nfp[f] + l];
+                ph[r * M + a] = v;
+            }
+        }
+    }
+    double* vq = W + W_VQ;
+    for (int idx = tid; idx < 3 * npt * Nc; idx += NTH) {
+        const int k = idx / (npt * Nc), rem = idx - k * npt * Nc, x = rem / Nc, c = rem - x * Nc;
+        const double* br = basis_row(A, d, x);
+        double s = 0.0;
+        if (c < Np) {
+            const double* G = Gk + (size_t)k * Np * Np + c;
+            for (int j = 0; j < Np; ++j) s += br[j] * G[j * Np];
+        } else {
+            const double* H = Hk + (size_t)k * Np * sfp + (c - Np);
+            for (int j = 0; j < Np; ++j) s += br[j] * H[j * sfp];
+        }
+        vq[((size_t)k * NPT + x) * NCM + c] = s;
+    }
+    __syncthreads();
+    // A1: fluxes and their Jacobians at the points
+    const PhysT<double>& P = A.ph;
+    double* cv = W + W_CV;
+    double* cf = W + W_CF;
+    double* cb = W + W_CB;
+    double* rv = W + W_RV;
+    double* rf = W + W_RF;
+    double* rb = W + W_RB;
+    for (int x = tid; x < npt; x += NTH) {
+        double u[M], q[M][3], ql[M][3];
+        for (int a = 0; a < M; ++a) {
+            u[a] = pu[x * M + a];
+            for (int k = 0; k < 3; ++k) { q[a][k] = pq[(x * M + a) * 3 + k]; ql[a][k] = pl[(x * M + a) * 3 + k]; }
+        }
+        if (x < Nq) {
+            const double* g = gv + x * 10;
+            const double wJ = -A.dt * g[0];
+            const double* Ji = g + 1;
+            double Fc[M][3], Fv[M][3];
+            conv_flux<3, double, double>(u, P, Fc);
+            visc_flux<3, double, double>(u, ql, 0.0, P, Fv);
+            for (int a = 0; a < M; ++a)
+                for (int r = 0; r < 3; ++r) {
+                    double s = 0.0;
+                    for (int k = 0; k < 3; ++k) s += Ji[r * 3 + k] * (Fc[a][k] - Fv[a][k]);
+                    rv[(x * M + a) * 3 + r] = wJ * s;
+                }
+            double* o = cv + (size_t)x * 300;
+            for (int b = 0; b < M; ++b) {
+                Dir ud[M];
+                for (int a = 0; a < M; ++a) ud[a] = {u[a], a == b ? 1.0 : 0.0};
+                Dir Fcd[M][3], Fvd[M][3];
+                conv_flux<3, Dir, double>(ud, P, Fcd);
+                visc_flux<3, Dir, double>(ud, q, 0.0, P, Fvd);
+                for (int a = 0; a < M; ++a)
+                    for (int r = 0; r < 3; ++r) {
+                        double s = 0.0;
+                        for (int k = 0; k < 3; ++k) s += Ji[r * 3 + k] * (Fcd[a][k].t - Fvd[a][k].t);
+                        o[((a * 3 + r) * M + b) * 4 + 0] = wJ * s;
+                    }
+                for (int l = 0; l < 3; ++l) {
+                    double qe[M][3];
+                    for (int a = 0; a < M; ++a) for (int k = 0; k < 3; ++k) qe[a][k] = (a == b && k == l) ? 1.0 : 0.0;
+                    double Fq[M][3];
+                    visc_flux<3, double, double>(u, qe, 0.0, P, Fq);
+                    for (int a = 0; a < M; ++a)
+                        for (int r = 0; r < 3; ++r) {
+                            double s = 0.0;
+                            for (int k = 0; k < 3; ++k) s += Ji[r * 3 + k] * Fq[a][k];
+                            o[((a * 3 + r) * M + b) * 4 + 1 + l] = -wJ * s;
+                        }
+                }
+            }
+        } else {
+            const int r = x - Nq, f = face_of_point(d, r), tag = d.tag[f];
+            const double* nw = gf + r * 3;
+            const double nrm = sqrt(nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2]);
+            const double taun = A.tau * nrm;
+            double uh[M];
+            for (int a = 0; a < M; ++a) uh[a] = ph[r * M + a];
+            double Fc[M][3], Fv[M][3];
+            conv_flux<3, double, double>(uh, P, Fc);
+            visc_flux<3, double, double>(uh, ql, 0.0, P, Fv);
+            for (int a = 0; a < M; ++a) {
+                double fn = 0.0;
+                for (int k = 0; k < 3; ++k) fn += (Fc[a][k] - Fv[a][k]) * nw[k];
+                const double fh = fn + taun * (u[a] - uh[a]);
+                rf[r * M + a] = A.dt * fh;
+                const double ub_a = tag == 1 ? A.ub[a] : 0.0;
+                rb[r * M + a] = boundary_form<M>(tag, a, fh, nrm, u, uh, ub_a, A.ew);
+            }
+            double* of = cf + (size_t)r * 125;
+            double* ob = cb + (size_t)r * 125;
+            // element rows take dt * dfhat; trace rows dfhat on flux rows, the algebraic forms
+            // otherwise (tag 1 uhat - u_b, tag 2 uhat - u, tags 3 / 4 uhat_v, and on isothermal
+            // walls uhat_rhoE - uhat_rho e_w)
+            auto put = [&](int a, int b, int kind, double v) {
+                of[(a * M + b) * 5 + kind] = A.dt * v;
+                double w = v;
+                if (!boundary_row_is_flux<M>(tag, a)) {
+                    w = 0.0;
+                    if (kind == 1 && a == b) w = nrm;
+                    if (tag == 2 && kind == 0 && a == b) w = -nrm;
+                    if (tag == 3 && a == M - 1 && kind == 1 && b == 0) w = -nrm * A.ew;
+                }
+                ob[(a * M + b) * 5 + kind] = w;
+            };
+            for (int b = 0; b < M; ++b) {
+                Dir ud[M];
+                for (int a = 0; a < M; ++a) ud[a] = {uh[a], a == b ? 1.0 : 0.0};
+                Dir Fcd[M][3], Fvd[M][3];
+                conv_flux<3, Dir, double>(ud, P, Fcd);
+                visc_flux<3, Dir, double>(ud, q, 0.0, P, Fvd);
+                for (int a = 0; a < M; ++a) {
+                    double fn = 0.0;
+                    for (int k = 0; k < 3; ++k) fn += (Fcd[a][k].t - Fvd[a][k].t) * nw[k];
+                    put(a, b, 0, a == b ? taun : 0.0);
+                    put(a, b, 1, fn - (a == b ? taun : 0.0));
+                }
+                for (int l = 0; l < 3; ++l) {
+                    double qe[M][3];
+                    for (int a = 0; a < M; ++a) for (int k = 0; k < 3; ++k) qe[a][k] = (a == b && k == l) ? 1.0 : 0.0;
+                    double Fq[M][3];
+                    visc_flux<3, double, double>(uh, qe, 0.0, P, Fq);
+                    for (int a = 0; a < M; ++a) {
+                        double fn = 0.0;
+                        for (int k = 0; k < 3; ++k) fn += Fq[a][k] * nw[k];
+                        put(a, b, 2 + l, -fn);
+                    }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // A2: contraction into the bordered matrix, one (a, b) component pair at a time
+    double* sR = sD;                     // [KC][SRP] row basis
+    double* sT = sD + KC * SRP;          // [KC][STP] column variations times coefficients
+    const int nrt = (Np + 3) / 4, nct = (Nc + 3) / 4;
+    const int ti = tid / nct, tc = tid - ti * nct;
+    const bool act = tid < nrt * nct;
+    const int K1 = 3 * Nq + sfq;         // element rows: volume (g, r) then face points
+    for (int ab = 0; ab < M * M; ++ab) {
+        const int a = ab / M, b = ab - a * M;
+        double acc[4][4] = {};
+        for (int k0 = 0; k0 < K1; k0 += KC) {
+            const int kc = min(KC, K1 - k0);
+            for (int idx = tid; idx < kc * SRP; idx += NTH) {
+                const int kk = idx / SRP, i = idx - kk * SRP, K = k0 + kk;
+                double v = 0.0;
+                if (i < Np) {
+                    if (K < 3 * Nq) v = dphi[((size_t)(K % 3) * Nq + K / 3) * Np + i];
+                    else v = basis_row(A, d, Nq + K - 3 * Nq)[i];
+                }
+                sR[idx] = v;
+            }
+            for (int idx = tid; idx < kc * STP; idx += NTH) {
+                const int kk = idx / STP, c = idx - kk * STP, K = k0 + kk;
+                double v = 0.0;
+                if (c < Nc) {
+                    if (K < 3 * Nq) {
+                        const int g = K / 3, r = K - 3 * g;
+                        const double* o = cv + (size_t)g * 300 + ((a * 3 + r) * M + b) * 4;
+                        if (c < Np) v = o[0] * phi[(size_t)g * Np + c];
+                        for (int l = 0; l < 3; ++l) v -= o[1 + l] * vq[((size_t)l * NPT + g) * NCM + c];
+                    } else {
+                        const int rr = K - 3 * Nq, x = Nq + rr;
+                        const double* o = cf + (size_t)rr * 125 + (a * M + b) * 5;
+                        if (c < Np) {
+                            v = o[0] * basis_row(A, d, x)[c];
+                        } else {
+                            const int f = face_of_point(d, rr);
+                            const int l = c - Np - fpo[f];
+                            if (l >= 0 && l < d.nfp[f]) v = o[1] * A.tab[d.ttab[f] + (size_t)(rr - d.soff[f]) * d.nfp[f] + l];
+                        }
+                        for (int l = 0; l < 3; ++l) v -= o[2 + l] * vq[((size_t)l * NPT + x) * NCM + c];
+                    }
+                }
+                sT[idx] = v;
+            }
+            __syncthreads();
+            if (act) gemm_chunk(sR, sT, kc, ti, tc, acc);
+            __syncthreads();
+        }
+        if (act)
+            for (int u = 0; u < 4; ++u) {
+                const int i = 4 * ti + u;
+                if (i >= Np) continue;
+                for (int v = 0; v < 4; ++v) {
+                    const int c = 4 * tc + v;
+                    if (c >= Nc) continue;
+                    Mx[(size_t)(a * Np + i) * LD + bcol(d, b, c)] = acc[u][v];   // mass term added below
+                }
+            }
+        // trace rows (f', a, l'): K = the points of face f'
+        for (int f2 = 0; f2 < 4; ++f2) {
+            const int nfq = d.nfq[f2], nfp = d.nfp[f2];
+            const double* mu = A.tab + d.ttab[f2];
+            for (int idx = tid; idx < nfq * SRP; idx += NTH) {
+                const int kk = idx / SRP, l = idx - kk * SRP;
+                sR[idx] = l < nfp ? mu[(size_t)kk * nfp + l] : 0.0;
+            }
+            for (int idx = tid; idx < nfq * STP; idx += NTH) {
+                const int kk = idx / STP, c = idx - kk * STP, rr = d.soff[f2] + kk, x = Nq + rr;
+                double v = 0.0;
+                if (c < Nc) {
+                    const double* o = cb + (size_t)rr * 125 + (a * M + b) * 5;
+                    if (c < Np) {
+                        v = o[0] * basis_row(A, d, x)[c];
+                    } else {
+                        const int l = c - Np - fpo[f2];
+                        if (l >= 0 && l < nfp) v = o[1] * mu[(size_t)kk * nfp + l];
+                    }
+                    for (int l = 0; l < 3; ++l) v -= o[2 + l] * vq[((size_t)l * NPT + x) * NCM + c];
+                }
+                sT[idx] = v;
+            }
+            __syncthreads();
+            const int nrt2 = (nfp + 3) / 4;
+            const int ti2 = tid / nct, tc2 = tid - ti2 * nct;
+            if (tid < nrt2 * nct) {
+                double acc2[4][4] = {};
+                gemm_chunk(sR, sT, nfq, ti2, tc2, acc2);
+                for (int u = 0; u < 4; ++u) {
+                    const int l = 4 * ti2 + u;
+                    if (l >= nfp) continue;
+                    for (int v = 0; v < 4; ++v) {
+                        const int c = 4 * tc2 + v;
+                        if (c >= Nc) continue;
+                        Mx[(size_t)(NU + d.toff[f2] + a * nfp + l) * LD + bcol(d, b, c)] = acc2[u][v];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    // mass term (1/a_ii) M_ij on the diagonal component blocks: M = L L^T from the factor
+    for (int idx = tid; idx < Np * Np; idx += NTH) {
+        const int i = idx / Np, j = idx - i * Np;
+        double s = 0.0;
+        for (int k = 0; k <= min(i, j); ++k) s += Mm[i * NPMAX + k] * Mm[j * NPMAX + k];
+        const double mv = s / A.a_ii;
+        for (int a = 0; a < M; ++a) Mx[(size_t)(a * Np + i) * LD + a * Np + j] += mv;
+    }
+    // right-hand-side column: R_u at the lifted gradient (interior rows), the trace residual
+    const int NR = NU + t;
+    for (int idx = tid; idx < NR; idx += NTH) {
+        double s = 0.0;
+        if (idx < NU) {
+            const int a = idx / Np, i = idx - a * Np;
+            double mass = 0.0;
+            for (int j = 0; j < Np; ++j) {
+                double mij = 0.0;
+                for (int k = 0; k <= min(i, j); ++k) mij += Mm[i * NPMAX + k] * Mm[j * NPMAX + k];
+                mass += mij * (sU[a * Np + j] - sUs[a * Np + j]);
+            }
+            s = mass / A.a_ii;
+            for (int g = 0; g < Nq; ++g)
+                for (int r = 0; r < 3; ++r) s += dphi[((size_t)r * Nq + g) * Np + i] * rv[(g * M + a) * 3 + r];
+            for (int rr = 0; rr < sfq; ++rr) s += basis_row(A, d, Nq + rr)[i] * rf[rr * M + a];
+        } else {
+            int f = 0, rem = idx - NU;
+            while (f < 3 && rem >= M * d.nfp[f]) { rem -= M * d.nfp[f]; ++f; }
+            const int a = rem / d.nfp[f], l = rem - a * d.nfp[f];
+            const double* mu = A.tab + d.ttab[f];
+            for (int q = 0; q < d.nfq[f]; ++q) s += mu[(size_t)q * d.nfp[f] + l] * rb[(d.soff[f] + q) * M + a];
+        }
+        Mx[(size_t)idx * LD + NR] = s;
+    }
+    __syncthreads();
+    // A3 + A4: bordered elimination
+    __shared__ int piv[NB];
+    bordered_elim(Mx, NU, NR, NR + 1, LD, sD, sD + NRMAX * NB, piv, sflag);
+}
+
+__global__ void __launch_bounds__(NTH, 2) k_tet_linearize(KArgs A) {
+    extern __shared__ double sm[];
+    __shared__ TetElem d;
+    __shared__ int s_idx, sflag;
+    const int tid = threadIdx.x;
+    double* W = A.work + (int64_t)blockIdx.x * A.wstride;
+    if (tid == 0) sflag = 0;
+    for (;;) {
+        if (tid == 0) s_idx = atomicAdd(A.next, 1);
+        __syncthreads();
+        const int idx = s_idx;
+        if (idx >= A.E) break;
+        const int64_t e = A.order[idx];
+        constexpr int NW = (int)(sizeof(TetElem) / 8);
+        for (int i = tid; i < NW; i += NTH)
+            reinterpret_cast<int64_t*>(&d)[i] = reinterpret_cast<const int64_t*>(A.el + e)[i];
+        __syncthreads();
+        process_element(A, d, W, sm, &sflag);
+        __syncthreads();
+    }
+    if (tid == 0 && sflag) atomicOr(A.status, sflag);
+}
+
+// A5: block values, column-major per block, summed over the block's element
+// contributions in ascending element order; g = -(trace rows' last column)
+__global__ void k_tet_assemble(const TetElem* el, const double* mat, const int64_t* hoff, const int64_t* boff,
+                               const int32_t* rowptr, const int32_t* col, const int32_t* cptr, const int32_t* centry,
+                               int64_t F, int64_t nnzb, double* vals) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t b = wid; b < nnzb; b += nw) {
+        int64_t lo = 0, hi = F;                  // row face: rowptr[Fr] <= b < rowptr[Fr + 1]
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (rowptr[mid] <= b) lo = mid; else hi = mid;
+        }
+        const int64_t Fr = lo, G = col[b];
+        const int bsF = (int)(hoff[Fr + 1] - hoff[Fr]), bsG = (int)(hoff[G + 1] - hoff[G]);
+        double* out = vals + boff[b];
+        for (int idx = lane; idx < bsF * bsG; idx += 32) {
+            const int c = idx / bsF, r = idx - c * bsF;
+            double s = 0.0;
+            for (int k = cptr[b]; k < cptr[b + 1]; ++k) {
+                const TetElem& d = el[centry[3 * k]];
+                const int fl = centry[3 * k + 1], gl = centry[3 * k + 2];
+                s += mat[d.moff + (int64_t)(d.NU + d.toff[fl] + r) * d.LD + d.NU + d.toff[gl] + c];
+            }
+            out[idx] = s;
+        }
+    }
+}
+
+__global__ void k_tet_assemble_g(const TetElem* el, const double* mat, const int64_t* hoff, const int32_t* f2e,
+                                 const int32_t* f2lf, int64_t F, double* g) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t Fr = wid; Fr < F; Fr += nw) {
+        int e0 = f2e[2 * Fr], e1 = f2e[2 * Fr + 1], l0 = f2lf[2 * Fr], l1 = f2lf[2 * Fr + 1];
+        if (e1 >= 0 && e1 < e0) { int t = e0; e0 = e1; e1 = t; t = l0; l0 = l1; l1 = t; }
+        const int bs = (int)(hoff[Fr + 1] - hoff[Fr]);
+        for (int r = lane; r < bs; r += 32) {
+            double s = 0.0;
+            for (int side = 0; side < 2; ++side) {
+                const int e = side ? e1 : e0, fl = side ? l1 : l0;
+                if (e < 0) continue;
+                const TetElem& d = el[e];
+                s -= mat[d.moff + (int64_t)(d.NU + d.toff[fl] + r) * d.LD + d.NU + d.t];
+            }
+            g[hoff[Fr] + r] = s;
+        }
+    }
+}
+
+// A6: y = S x, one warp per block row, lanes over the rows of the block row
+__global__ void k_tet_matvec(const double* vals, const int64_t* hoff, const int64_t* boff, const int32_t* rowptr,
+                             const int32_t* col, int64_t F, const double* x, double* y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t Fr = wid; Fr < F; Fr += nw) {
+        const int bsF = (int)(hoff[Fr + 1] - hoff[Fr]);
+        for (int r0 = 0; r0 < bsF; r0 += 32) {
+            const int r = r0 + lane;
+            double s = 0.0;
+            for (int b = rowptr[Fr]; b < rowptr[Fr + 1]; ++b) {
+                const int64_t G = col[b];
+                const int bsG = (int)(hoff[G + 1] - hoff[G]);
+                const double* vb = vals + boff[b];
+                const double* xg = x + hoff[G];
+                if (r < bsF)
+                    for (int c = 0; c < bsG; ++c) s = fma(vb[(int64_t)c * bsF + r], xg[c], s);
+            }
+            if (r < bsF) y[hoff[Fr] + r] = s;
+        }
+    }
+}
+
+// A7: dU = -U^{-1} (z + Z dUhat_K), dQ = dq0 - G dU - H dUhat_K
+__global__ void __launch_bounds__(NTH) k_tet_recover(const TetElem* el, const double* mat, const double* rec,
+                                                      const double* dUH, double* dQ, double* dU, int64_t E) {
+    __shared__ double sH[4 * M * NFPMAX];
+    __shared__ double sx[M * NPMAX];
+    const int tid = threadIdx.x;
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        const TetElem& d = el[e];
+        const int Np = d.Np, NU = d.NU, t = d.t, LD = d.LD, sfp = t / M;
+        const double* Mx = mat + d.moff;
+        for (int i = tid; i < t; i += NTH) {
+            int f = 0, r = i;
+            while (f < 3 && r >= M * d.nfp[f]) { r -= M * d.nfp[f]; ++f; }
+            sH[i] = dUH[d.hoff[f] + r];
+        }
+        __syncthreads();
+        for (int i = tid; i < NU; i += NTH) {
+            const double* row = Mx + (int64_t)i * LD;
+            double s = row[NU + t];
+            for (int c = 0; c < t; ++c) s = fma(row[NU + c], sH[c], s);
+            sx[i] = s;
+        }
+        __syncthreads();
+        for (int i = NU - 1; i >= 0; --i) {
+            const double xi = sx[i] / Mx[(int64_t)i * LD + i];
+            __syncthreads();
+            if (tid == 0) sx[i] = xi;
+            for (int j = tid; j < i; j += NTH) sx[j] -= Mx[(int64_t)j * LD + i] * xi;
+            __syncthreads();
+        }
+        for (int i = tid; i < NU; i += NTH) dU[d.uoff + i] = -sx[i];
+        const double* Gk = rec + d.roff;
+        const double* Hk = Gk + 3 * Np * Np;
+        const double* dq0 = Hk + 3 * Np * sfp;
+        for (int idx = tid; idx < 3 * NU; idx += NTH) {
+            const int k = idx / NU, rem = idx - k * NU, a = rem / Np, i = rem - a * Np;
+            double s = dq0[idx];
+            for (int j = 0; j < Np; ++j) s += Gk[((int64_t)k * Np + i) * Np + j] * sx[a * Np + j];
+            int cp = 0;
+            for (int f = 0; f < 4; ++f)
+                for (int l = 0; l < d.nfp[f]; ++l, ++cp)
+                    s -= Hk[((int64_t)k * Np + i) * sfp + cp] * sH[d.toff[f] + a * d.nfp[f] + l];
+            dQ[3 * d.uoff + idx] = s;
+        }
+        __syncthreads();
+    }
+}
+
+namespace {
+
+template <class T>
+int tet_alloc(hdg_ctx* h, T** out, size_t count, std::string& err) {
+    void* p = nullptr;
+    const size_t bytes = std::max<size_t>(1, count) * sizeof(T);
+    const cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        err = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? HDG_ENOMEM : HDG_ECUDA;
+    }
+    h->allocs.push_back(p);
+    h->device_bytes += (int64_t)bytes;
+    *out = static_cast<T*>(p);
+    return HDG_OK;
+}
+
+template <class T>
+int tet_upload(hdg_ctx* h, T** out, const std::vector<T>& v, std::string& err) {
+    int rc = tet_alloc(h, out, v.size(), err);
+    if (rc) return rc;
+    if (!v.empty() && cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess) {
+        err = "cudaMemcpy of set-up data failed";
+        return HDG_ECUDA;
+    }
+    return HDG_OK;
+}
+
+#define TET_CK(call)                                                                   \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            h->err = std::string(#call) + ": " + cudaGetErrorString(e_);               \
+            return HDG_ECUDA;                                                          \
+        }                                                                              \
+    } while (0)
+
+}  // namespace
+
+int create_device(hdg_ctx* h, std::string& err) {
+    Ctx* c = h->tet;
+    int rc;
+#define UP(dst, src) if ((rc = tet_upload(h, &(dst), (src), err))) return rc
+    UP(c->d_el, c->el); UP(c->d_order, c->order); UP(c->d_tab, c->tab);
+    UP(c->d_gvol, c->gvol); UP(c->d_gface, c->gface); UP(c->d_hoff, c->hoff); UP(c->d_boff, c->boff);
+    UP(c->d_rowptr, c->rowptr); UP(c->d_col, c->col); UP(c->d_cptr, c->cptr); UP(c->d_centry, c->centry);
+    UP(c->d_f2e, c->f2e); UP(c->d_f2lf, c->f2lf);
+#undef UP
+    if ((rc = tet_alloc(h, &c->d_mat, (size_t)c->n_mat, err))) return rc;
+    if ((rc = tet_alloc(h, &c->d_rec, (size_t)c->n_rec, err))) return rc;
+    if ((rc = tet_alloc(h, &c->d_vals, (size_t)c->n_vals, err))) return rc;
+    if ((rc = tet_alloc(h, &c->d_g, (size_t)c->n_trace, err))) return rc;
+    if ((rc = tet_alloc(h, &c->d_next, 1, err))) return rc;
+    if ((rc = tet_alloc(h, &h->d_status, 1, err))) return rc;
+    if ((rc = tet_alloc(h, &h->d_ub, M, err))) return rc;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaFuncSetAttribute(k_tet_linearize, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(S_TOTAL * sizeof(double))) != cudaSuccess) {
+        err = "shared-memory opt-in of the tetrahedral kernel failed";
+        return HDG_ECUDA;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tet_linearize, NTH, S_TOTAL * sizeof(double));
+    c->n_slots = std::max(1, nsm * std::max(1, per_sm));
+    c->work_stride = W_END;
+    if ((rc = tet_alloc(h, &c->d_work, (size_t)c->n_slots * W_END, err))) return rc;
+    if (cudaMemset(h->d_status, 0, sizeof(int32_t)) != cudaSuccess ||
+        cudaMemset(h->d_ub, 0, M * sizeof(double)) != cudaSuccess) {
+        err = "cudaMemset failed";
+        return HDG_ECUDA;
+    }
+    h->device = true;
+    return HDG_OK;
+}
+
+void destroy(hdg_ctx* h) {
+    delete h->tet;
+    h->tet = nullptr;
+}
+
+int linearize(hdg_ctx* h, const double* U, const double* Q, const double* UH, const double* Ustar, double dt,
+              double a_ii) {
+    Ctx* c = h->tet;
+    KArgs A;
+    A.el = c->d_el; A.order = c->d_order; A.E = c->E; A.next = c->d_next;
+    A.tab = c->d_tab; A.gvol = c->d_gvol; A.gface = c->d_gface;
+    A.U = U; A.Q = Q; A.UH = UH; A.Ustar = Ustar;
+    A.mat = c->d_mat; A.rec = c->d_rec; A.work = c->d_work; A.wstride = c->work_stride;
+    A.ph = phys_t<double>(h->phys); A.dt = dt; A.a_ii = a_ii; A.tau = h->phys.tau;
+    A.ub = h->d_ub; A.ew = h->e_wall; A.status = h->d_status;
+    cudaStream_t st = h->stream;
+    TET_CK(cudaMemsetAsync(c->d_next, 0, sizeof(int32_t), st));
+    prof_begin(h, HDG_K_ELIM);
+    k_tet_linearize<<<c->n_slots, NTH, S_TOTAL * sizeof(double), st>>>(A);
+    prof_end(h);
+    TET_CK(cudaGetLastError());
+    prof_begin(h, HDG_K_ASSEMBLE);
+    const unsigned gb = (unsigned)std::min<int64_t>(65535, (c->nnzb + 7) / 8);
+    k_tet_assemble<<<gb, 256, 0, st>>>(c->d_el, c->d_mat, c->d_hoff, c->d_boff, c->d_rowptr, c->d_col, c->d_cptr,
+                                       c->d_centry, c->F, c->nnzb, c->d_vals);
+    const unsigned gf = (unsigned)std::min<int64_t>(65535, (c->F + 7) / 8);
+    k_tet_assemble_g<<<gf, 256, 0, st>>>(c->d_el, c->d_mat, c->d_hoff, c->d_f2e, c->d_f2lf, c->F, c->d_g);
+    prof_end(h);
+    TET_CK(cudaGetLastError());
+    c->have_system = true;
+    return HDG_OK;
+}
+
+int matvec(hdg_ctx* h, const double* x, double* y) {
+    Ctx* c = h->tet;
+    const unsigned gf = (unsigned)std::min<int64_t>(65535, (c->F + 7) / 8);
+    prof_begin(h, HDG_K_MATVEC);
+    k_tet_matvec<<<gf, 256, 0, h->stream>>>(c->d_vals, c->d_hoff, c->d_boff, c->d_rowptr, c->d_col, c->F, x, y);
+    prof_end(h);
+    TET_CK(cudaGetLastError());
+    return HDG_OK;
+}
+
+int recover(hdg_ctx* h, const double* dUH, double* dQ, double* dU) {
+    Ctx* c = h->tet;
+    const unsigned g = (unsigned)std::min<int64_t>(c->E, 4 * 152);
+    prof_begin(h, HDG_K_RECOVER);
+    k_tet_recover<<<g, NTH, 0, h->stream>>>(c->d_el, c->d_mat, c->d_rec, dUH, dQ, dU, c->E);
+    prof_end(h);
+    TET_CK(cudaGetLastError());
+    return HDG_OK;
+}
+
+}  // namespace tet
+}  // namespace hdg

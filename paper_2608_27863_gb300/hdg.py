@@ -25,6 +25,7 @@ HDG_ENOCONV = -6
 HDG_EUNSUPPORTED = -7
 HDG_QUAD = 1
 HDG_HEX = 2
+HDG_TET = 3
 HDG_PREC_FP64 = 0
 HDG_PREC_MIXED = 1
 HDG_PREC_MIXED_TF32 = 2
@@ -38,7 +39,8 @@ EXPORTS = [
     "hdg_blockjacobi_setup", "hdg_blockjacobi_apply", "hdg_gmres", "hdg_newton", "hdg_set_bc_state",
     "hdg_newton_fixed", "hdg_dirk_step", "hdg_lift_gradient", "hdg_set_preconditioner", "hdg_schwarz_setup",
     "hdg_schwarz_apply", "hdg_rb_setup", "hdg_rb_push", "hdg_rb_guess", "hdg_av_field", "hdg_tgv_diagnostics",
-    "hdg_autotune", "hdg_set_tuning", "hdg_set_bc_field", "hdg_reserve",
+    "hdg_autotune", "hdg_set_tuning", "hdg_set_bc_field", "hdg_reserve", "hdg_create_tet", "hdg_create_tet_host",
+    "hdg_tet_query", "hdg_tet_layout", "hdg_tet_ref_tables", "hdg_tri_ref_tables",
 ]
 KERNEL_CLASSES = ["point", "blocks", "elim", "assemble", "matvec", "recover", "schur"]
 
@@ -64,6 +66,17 @@ class hdg_sizes(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("dim", "p", "m", "Np", "Nq", "nf", "Nfp", "Nfq", "n_u", "n_q", "t",
                                                "block")] + \
                [(n, ctypes.c_int64) for n in ("n_elem", "n_faces", "nnzb", "device_bytes")]
+
+
+class hdg_tet_mesh(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int64), ("n_vert", ctypes.c_int64), ("vert_xyz", ctypes.c_void_p),
+                ("elem_vert", ctypes.c_void_p), ("periodic_map", ctypes.c_void_p), ("bnd_tag", ctypes.c_void_p),
+                ("elem_p", ctypes.c_void_p), ("geo", ctypes.c_void_p)]
+
+
+class hdg_tet_sizes(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("n_elem", "n_faces", "nnzb", "n_u", "n_trace", "n_vals", "n_curved",
+                                               "device_bytes")]
 
 
 _lib = None
@@ -118,6 +131,12 @@ def lib():
         "hdg_rb_guess": [vp, vp, vp],
         "hdg_newton_fixed": [vp, vp, vp, vp, vp, vp, dbl, dbl, i32, i32, i32, vp],
         "hdg_dirk_step": [vp, vp, vp, vp, vp, dbl, i32, vp, vp, i32, i32, i32, vp],
+        "hdg_create_tet": [ctypes.POINTER(vp), ctypes.POINTER(hdg_tet_mesh), dbl, dbl, dbl, dbl],
+        "hdg_create_tet_host": [ctypes.POINTER(vp), ctypes.POINTER(hdg_tet_mesh), dbl, dbl, dbl, dbl],
+        "hdg_tet_query": [vp, ctypes.POINTER(hdg_tet_sizes)],
+        "hdg_tet_layout": [vp] * 10,
+        "hdg_tet_ref_tables": [i32, vp, vp, vp, vp],
+        "hdg_tri_ref_tables": [i32, vp, vp, vp],
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -413,3 +432,61 @@ def hdg_set_bc_field(h, ubf):
 def hdg_reserve(h, precision=0):
     """Allocate the system storage of a precision now (it is otherwise allocated on first use)."""
     _check(h, lib().hdg_reserve(h, int(precision)))
+
+
+# ----------------------------------------------------------------------------
+# tetrahedral meshes of per-element degree on quadratic geometry
+# ----------------------------------------------------------------------------
+def hdg_create_tet(vert_xyz, elem_vert, periodic_map, bnd_tag, elem_p, geo, gamma, Re, Pr, Mach, host_only=False):
+    """Handle of a tetrahedral mesh (host arrays; geo [E][10][3] or None for straight sides)."""
+    keep = [np.ascontiguousarray(vert_xyz, dtype=np.float64), np.ascontiguousarray(elem_vert, dtype=np.int64),
+            None if periodic_map is None else np.ascontiguousarray(periodic_map, dtype=np.int64),
+            None if bnd_tag is None else np.ascontiguousarray(bnd_tag, dtype=np.int32),
+            np.ascontiguousarray(elem_p, dtype=np.int32),
+            None if geo is None else np.ascontiguousarray(geo, dtype=np.float64)]
+    ms = hdg_tet_mesh(keep[1].shape[0], keep[0].shape[0], *[None if a is None else a.ctypes.data for a in keep])
+    h = ctypes.c_void_p()
+    fn = lib().hdg_create_tet_host if host_only else lib().hdg_create_tet
+    rc = fn(ctypes.byref(h), ctypes.byref(ms), float(gamma), float(Re), float(Pr), float(Mach))
+    if rc != HDG_OK:
+        msg = lib().hdg_last_error(h).decode() if h else "error"
+        if h:
+            lib().hdg_destroy(h)
+        raise HDGError(rc, msg)
+    return h
+
+
+def hdg_tet_query(h):
+    s = hdg_tet_sizes()
+    _check(h, lib().hdg_tet_query(h, ctypes.byref(s)))
+    return {n: getattr(s, n) for n, _ in hdg_tet_sizes._fields_}
+
+
+def hdg_tet_layout(h):
+    s = hdg_tet_query(h)
+    E, F, nnzb = s["n_elem"], s["n_faces"], s["nnzb"]
+    out = {"uoff": np.zeros(E + 1, np.int64), "hoff": np.zeros(F + 1, np.int64), "face_p": np.zeros(F, np.int32),
+           "f2e": np.zeros((F, 2), np.int32), "e2f": np.zeros((E, 4), np.int32),
+           "frame": np.zeros((E, 4, 3), np.int32), "rowptr": np.zeros(F + 1, np.int32),
+           "col": np.zeros(nnzb, np.int32), "boff": np.zeros(nnzb + 1, np.int64)}
+    _check(h, lib().hdg_tet_layout(h, *[out[k].ctypes.data for k in
+                                        ("uoff", "hoff", "face_p", "f2e", "e2f", "frame", "rowptr", "col", "boff")]))
+    return out
+
+
+def hdg_tet_ref_tables(p):
+    Np, Nq = (p + 1) * (p + 2) * (p + 3) // 6, (p + 2) ** 3
+    out = {"xq": np.zeros((Nq, 3)), "wq": np.zeros(Nq), "phi": np.zeros((Nq, Np)), "dphi": np.zeros((3, Nq, Np))}
+    rc = lib().hdg_tet_ref_tables(int(p), *[out[k].ctypes.data for k in ("xq", "wq", "phi", "dphi")])
+    if rc != HDG_OK:
+        raise HDGError(rc, "hdg_tet_ref_tables")
+    return out
+
+
+def hdg_tri_ref_tables(p):
+    Nfp, Nfq = (p + 1) * (p + 2) // 2, (p + 2) ** 2
+    out = {"xs": np.zeros((Nfq, 2)), "ws": np.zeros(Nfq), "mu": np.zeros((Nfq, Nfp))}
+    rc = lib().hdg_tri_ref_tables(int(p), *[out[k].ctypes.data for k in ("xs", "ws", "mu")])
+    if rc != HDG_OK:
+        raise HDGError(rc, "hdg_tri_ref_tables")
+    return out
