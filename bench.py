@@ -51,8 +51,186 @@ WORKLOADS = {
     "hex-p3-64x48x32-plate": dict(fn="config5", kw={}, mixed_only=True, av=(2e-3, 0.1 / 48),
                                   cpu=dict(fn="config5", kw={"nx": 6, "ny": 8, "nz": 4})),
     "hex-p2-8x12x6-plate": dict(fn="config5", kw={"nx": 8, "ny": 12, "nz": 6, "p": 2}, av=(2e-3, 0.1 / 12)),
+    # curved anisotropic tetrahedra, degrees 1..4 per element (seeded), 6 Kuhn tets per cell
+    "tet-p1to4-30x20x28-curved": dict(kind="tet", kw={}),
+    "tet-p1to4-10x20x6-curved": dict(kind="tet", kw={"nx": 10, "nz": 6}),
 }
 DEFAULT_WORKLOAD = "hex-p2-16^3-tgv"
+
+
+def make_tet_problem(name, host_layout=None):
+    """Mesh, physics and packed seeded state of a tetrahedral workload.  The trace
+    sizes come from the library's layout when given (GPU leg), else from the
+    oracle's connectivity (CPU leg); both give the same numbers."""
+    import numpy as np
+    from synth import tetmesh as tm
+    m = tm.config4_mesh(**WORKLOADS[name]["kw"])
+    P = tm.config4_problem(m)
+    if host_layout is None:
+        from oracle.tet import TetConnectivity
+        nfp = TetConnectivity(m).nfp
+    else:
+        nfp = np.diff(host_layout["hoff"]) // 5
+    fun = tm.sinusoids(P.gamma, P.mach, 3, 1e-3)
+    P.U, P.Q, P.UH, P.Ustar = tm.packed_state(m, fun, nfp, P.ubc, 7)
+    return P, m
+
+
+def tet_flops(layout, elem_p):
+    """Algorithmic FP64 flops per element of the tetrahedral linearize + condense kernel:
+    point values and lifting operators, contraction (element and trace rows, with the
+    per-point column variations), and the bordered elimination."""
+    import numpy as np
+    E = len(elem_p)
+    fp = layout["face_p"][layout["e2f"]]                      # [E][4]
+    Np = (elem_p + 1) * (elem_p + 2) * (elem_p + 3) // 6
+    Nq = (elem_p + 2) ** 3
+    nfp = (fp + 1) * (fp + 2) // 2
+    nfq = (fp + 2) ** 2
+    sfp, sfq = nfp.sum(1), nfq.sum(1)
+    Nc = Np + sfp
+    NU, t = 5 * Np, 5 * sfp
+    lift = 3 * Np * Np * Nq + 9 * Np * Np * Nq + 9 * Np * sfp * nfq.max(1) + Np ** 3 / 3 + 6 * Nc * Np * Np \
+        + 2 * 15 * Np * (Np + sfp) + 2 * 3 * (Nq + sfq) * Nc * Np
+    contr = 2 * 25 * Np * Nc * (3 * Nq + sfq) + 2 * 25 * (nfp * nfq).sum(1) * Nc \
+        + 25 * Nc * (3 * Nq * 8 + sfq * 10 + sfq * 10)
+    elim = np.zeros(E)
+    for e in range(E):
+        k = np.arange(NU[e])
+        NR = NU[e] + t[e]
+        elim[e] = np.sum(2.0 * (NR - k - 1) * (NR - k) + (NR - k - 1))
+    return {"lift": lift, "contraction": contr, "elim": elim, "total": lift + contr + elim}
+
+
+def run_tet(args, rank, world, local_rank):
+    """Tetrahedral workload (mixed degree, curved and affine elements, one persistent
+    FP64 launch): linearize + condense, trace matvec and recovery per step."""
+    import numpy as np
+    import torch
+
+    from paper_2608_27863_gb300 import build as B
+    from paper_2608_27863_gb300 import hdg as H
+
+    pool = None
+    ncores = os.cpu_count() or 1
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = oracle_pool(args.workload, ncores)      # before the first GPU call
+    torch.cuda.set_device(local_rank)
+    B.build()
+    from synth import tetmesh as tm
+    m0 = tm.config4_mesh(**WORKLOADS[args.workload]["kw"])
+    hh = H.hdg_create_tet(m0.vert_xyz, m0.elem_vert, m0.periodic_map, m0.bnd_tag, m0.elem_p, m0.geo, 1.4, 1e5,
+                          0.72, 0.5, host_only=True)
+    layout = H.hdg_tet_layout(hh)
+    H.hdg_destroy(hh)
+    P, m = make_tet_problem(args.workload, host_layout=layout)
+    h = H.hdg_create_tet(m.vert_xyz, m.elem_vert, m.periodic_map, m.bnd_tag, m.elem_p, m.geo, P.gamma, P.re, P.pr,
+                         P.mach)
+    H.hdg_set_params(h, tau=P.tau)
+    H.hdg_set_bc_state(h, 1, P.ubc)
+    sizes = H.hdg_tet_query(h)
+    stream = torch.cuda.current_stream()
+    H.hdg_set_stream(h, stream.cuda_stream)
+    dev = torch.device("cuda", local_rank)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    U, Q, UH, Us = t(P.U), t(P.Q), t(P.UH), t(P.Ustar)
+    x = t(np.random.default_rng(rank).normal(size=P.UH.shape))
+    y = torch.empty_like(UH)
+    dQ, dU = torch.empty_like(Q), torch.empty_like(U)
+    flush = torch.empty(2 * L2_BYTES // 8, dtype=torch.float64, device=dev)
+
+    def step():
+        H.hdg_linearize_condense(h, U, Q, UH, Us, None, P.dt, P.a_ii)
+        H.hdg_trace_matvec(h, x, y)
+        H.hdg_recover_interior(h, y, dQ, dU)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if H.hdg_status(h) != 0:
+        raise RuntimeError("device status: " + H.hdg_last_error(h))
+    H.hdg_profile_read(h)
+    H.hdg_profile(h, True)
+    times = []
+    with ClockSampler(local_rank) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record(stream)
+            step()
+            e.record(stream)
+            e.synchronize()
+            times.append(s.elapsed_time(e))
+    torch.cuda.synchronize()
+    prof = H.hdg_profile_read(h)
+    H.hdg_profile(h, False)
+    clocks = clk.summary()
+    t_ms = max_over_ranks(sum(times), world, dev)
+    # end to end from pinned host memory
+    hU, hQ, hUH, hUs = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (P.U, P.Q, P.UH, P.Ustar))
+    hdQ = torch.empty(dQ.shape, dtype=torch.float64).pin_memory()
+    hdU = torch.empty(dU.shape, dtype=torch.float64).pin_memory()
+    h2d = sum(a.numel() * 8 for a in (hU, hQ, hUH, hUs))
+    d2h = (hdQ.numel() + hdU.numel()) * 8
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        U.copy_(hU, non_blocking=True)
+        Q.copy_(hQ, non_blocking=True)
+        UH.copy_(hUH, non_blocking=True)
+        Us.copy_(hUs, non_blocking=True)
+        step()
+        hdQ.copy_(dQ, non_blocking=True)
+        hdU.copy_(dU, non_blocking=True)
+        e.record(stream)
+        e.synchronize()
+        e2e_ms += s.elapsed_time(e)
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    cpu = None
+    if pool is not None:
+        rate, n_done, secs = oracle_rate(pool, ncores, m.n_elem, args.cpu_seconds, 100)
+        pool.close()
+        cpu = {"value": rate, "unit": "elements/s", "cores": ncores, "kind": "oracle",
+               "sample": "%d seeded elements of the workload in %.1f s: per-element residual, complex-step "
+                         "Jacobian, dense FP64 LU of the (q,u) block and Schur complement" % (n_done, secs)}
+    E = m.n_elem
+    fl = tet_flops(layout, m.elem_p.astype(np.int64))
+    kern = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+            for k, v in prof.items() if v[1]}
+    lin_ms = prof["elim"][0] / max(prof["elim"][1], 1)
+    achieved = fl["total"].sum() / (lin_ms * 1e-3) / 1e12
+    smmax = clocks.get("sm_max_mhz") or 2070.0
+    peak = fp64_peak_derived(smmax)
+    counts = np.bincount(m.elem_p, minlength=5)[1:]
+    out = {
+        "metric": METRIC, "value": replica_throughput(world, E, args.steps, t_ms), "unit": "elements/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "elements_per_gpu": E, "element": "tetrahedron",
+                   "degrees": {"p%d" % (i + 1): int(c) for i, c in enumerate(counts)},
+                   "curved_elements": sizes["n_curved"], "faces": sizes["n_faces"], "blocks": sizes["nnzb"],
+                   "block_values": sizes["n_vals"], "device_bytes": sizes["device_bytes"],
+                   "launch": "one persistent launch over a cost-ordered element list",
+                   "parallelism": "replicas" if world > 1 else "single", "precision": "fp64",
+                   "l2": "flushed between timed steps (256 MiB write)"},
+        "roofline": {"bound": "alu", "kernel": "k_tet_linearize", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz (derived)" % smmax,
+                     "flops_per_element": float(fl["total"].mean()),
+                     "flops_split": {k: float(v.sum()) for k, v in fl.items()}},
+        "kernels": kern,
+        "e2e": {"value": replica_throughput(world, E, args.steps, e2e_ms), "unit": "elements/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": sum(v[1] for v in prof.values()) / args.steps,
+        "clocks": clocks,
+    }
+    if cpu is not None:
+        out["cpu_baseline"] = cpu
+    H.hdg_destroy(h)
+    return out
 
 
 def make_problem(name, cpu_sample=False):
@@ -149,6 +327,10 @@ _W = {}
 def _worker_init(name):
     sys.path.insert(0, ROOT)
     import numpy as np
+    if WORKLOADS[name].get("kind") == "tet":
+        from oracle.tet import TetProblem
+        _W["pb"] = TetProblem(make_tet_problem(name, host_layout=None)[0])
+        return
     from oracle.hdg import Problem
     P = make_problem(name, cpu_sample=True)
     if P.nu is None and "av" in WORKLOADS[name]:
@@ -540,13 +722,19 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     ncores = os.cpu_count() or 1
-    P = make_problem(args.workload, cpu_sample=True)      # the elements the oracle samples from
+    if WORKLOADS[args.workload].get("kind") == "tet":
+        from synth import tetmesh as tm
+        n_elem = tm.config4_mesh(**WORKLOADS[args.workload]["kw"]).n_elem
+        degree = "1..4"
+    else:
+        P = make_problem(args.workload, cpu_sample=True)      # the elements the oracle samples from
+        n_elem, degree = P.mesh.n_elem, P.p
     pool = oracle_pool(args.workload, ncores)
     for w in range(args.warmup):
-        oracle_rate(pool, ncores, P.mesh.n_elem, 0.0, 500 + w)
+        oracle_rate(pool, ncores, n_elem, 0.0, 500 + w)
     tot_e, tot_s = 0, 0.0
     for k in range(args.steps):
-        _, n, s = oracle_rate(pool, ncores, P.mesh.n_elem, 0.0, 900 + k)
+        _, n, s = oracle_rate(pool, ncores, n_elem, 0.0, 900 + k)
         tot_e += n
         tot_s += s
     pool.close()
@@ -555,7 +743,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "elements/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "elements_per_gpu": P.mesh.n_elem, "degree": P.p},
+        "config": {"workload": args.workload, "elements_per_gpu": n_elem, "degree": degree},
         "cpu_baseline": {"value": rate, "unit": "elements/s", "cores": ncores, "kind": "oracle",
                          "sample": "each step condenses %d seeded elements (one per core) of the workload" % ncores},
         "e2e": {"value": rate, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -591,7 +779,7 @@ def main():
             import torch.distributed as dist
             torch.cuda.set_device(local_rank)
             dist.init_process_group("nccl")
-        out = run_ours(args, rank, world, local_rank)
+        out = (run_tet if WORKLOADS[args.workload].get("kind") == "tet" else run_ours)(args, rank, world, local_rank)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

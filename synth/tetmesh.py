@@ -81,7 +81,7 @@ def kuhn_box(n, coords, periodic, tags=None, degrees=None, bump=None, curved_lay
                 ii = [i, j, k]
                 jj = [0 if (periodic[r] and ii[r] == n[r]) else ii[r] for r in range(3)]
                 pmap[vid(i, j, k)] = vid(*jj)
-    ev, tag, geo = [], [], []
+    ev, tag, rows = [], [], []
     for k in range(n[2]):
         for j in range(n[1]):
             for i in range(n[0]):
@@ -97,6 +97,7 @@ def kuhn_box(n, coords, periodic, tags=None, degrees=None, bump=None, curved_lay
                         ids[1], ids[2] = ids[2], ids[1]
                         cs[1], cs[2] = cs[2], cs[1]
                     ev.append(ids)
+                    rows.append([j + q[1] for q in cs])
                     cell = (i, j, k)
                     t = []
                     for f in range(4):
@@ -111,27 +112,39 @@ def kuhn_box(n, coords, periodic, tags=None, degrees=None, bump=None, curved_lay
                                     tf = tags.get((r, s), 1)
                         t.append(tf)
                     tag.append(t)
-                    X = [phys[v] for v in ids]
-                    for (a, b) in EDGES:
-                        ja, jb = j + cs[a][1], j + cs[b][1]
-                        if bump is not None and max(ja, jb) <= curved_layers:
-                            mid = 0.5 * (comp[ids[a]] + comp[ids[b]])
-                            X.append(bump(mid[None, :])[0])
-                        else:
-                            X.append(0.5 * (phys[ids[a]] + phys[ids[b]]))
-                    geo.append(X)
+    evv = np.array(ev, dtype=np.int64)
+    rows = np.array(rows)
+    geo = np.zeros((evv.shape[0], 10, 3))
+    geo[:, :4] = phys[evv]
+    for c, (a, b) in enumerate(EDGES):
+        straight = 0.5 * (phys[evv[:, a]] + phys[evv[:, b]])
+        if bump is None:
+            geo[:, 4 + c] = straight
+            continue
+        bent = bump(0.5 * (comp[evv[:, a]] + comp[evv[:, b]]))
+        curved = np.maximum(rows[:, a], rows[:, b]) <= curved_layers
+        geo[:, 4 + c] = np.where(curved[:, None], bent, straight)
     ev = np.array(ev, dtype=np.int64)
     E = ev.shape[0]
     if degrees is None:
         elem_p = (1 + np.floor(pmax * uniform(seed, E))).astype(np.int32)
     else:
         elem_p = np.full(E, int(degrees), dtype=np.int32)
-    return TetMesh(phys.astype(np.float64), ev, pmap, np.array(tag, dtype=np.int32), elem_p,
-                   np.array(geo, dtype=np.float64), n)
+    return TetMesh(phys.astype(np.float64), ev, pmap, np.array(tag, dtype=np.int32), elem_p, geo, n)
 
 
 def lattice(p):
     return [(i, j, k) for k in range(p + 1) for j in range(p + 1 - k) for i in range(p + 1 - j - k)]
+
+
+def node_shape(p):
+    """Quadratic shape functions at the degree-p lattice: [Np][10]."""
+    out = []
+    for (i, j, k) in lattice(p):
+        l1, l2, l3 = i / p, j / p, k / p
+        lam = [1.0 - l1 - l2 - l3, l1, l2, l3]
+        out.append([lam[v] * (2 * lam[v] - 1) for v in range(4)] + [4 * lam[a] * lam[b] for (a, b) in EDGES])
+    return np.array(out)
 
 
 def node_xyz(mesh: TetMesh, e: int) -> np.ndarray:
@@ -181,10 +194,13 @@ def packed_state(mesh: TetMesh, fun, face_nfp, ubg, seed, noise=1e-4, trace_nois
     background state ubg plus relative noise, one [m][Nfp] block per face with
     the sizes ``face_nfp``.
     """
-    U, Q = [], []
-    for e in range(mesh.n_elem):
-        x = node_xyz(mesh, e)
-        U.append(fun(x).T.ravel())
+    U = [None] * mesh.n_elem
+    for p in np.unique(mesh.elem_p):
+        idx = np.nonzero(mesh.elem_p == p)[0]
+        x = np.einsum("nc,eck->enk", node_shape(int(p)), mesh.geo[idx])       # [E_p][Np][3]
+        u = fun(x)                                                             # [E_p][Np][m]
+        for r, e in enumerate(idx):
+            U[e] = u[r].T.ravel()
     U = np.concatenate(U)
     U = U + noise * normal(seed, U.size)
     Q = q_noise * normal(seed + 1, 3 * U.size)
@@ -220,7 +236,14 @@ def config4_mesh(nx=30, ny=20, nz=28, ratio=1.2, aspect=1e3, curved_layers=None,
     h1 = dx / aspect
     ys = np.concatenate([[0.0], np.cumsum(h1 * ratio ** np.arange(ny))])
     coords = [np.linspace(0.0, 1.0, nx + 1), ys, np.linspace(0.0, nz * dx, nz + 1)]
-    cl = ny // 2 if curved_layers is None else curved_layers
+    # curved wall layer: edges become straight only above the first cell layer whose height is six
+    # times the bump's sagitta over one cell (0.05 pi^2 dx^2 / 8), so that the quadratic elements of
+    # the transition stay valid (14 of 20 layers for nx = 30)
+    if curved_layers is None:
+        sag = 0.05 * np.pi ** 2 * dx * dx / 8.0
+        cl = next((j for j in range(ny) if h1 * ratio ** j >= 6.0 * sag), ny)
+    else:
+        cl = curved_layers
     return kuhn_box((nx, ny, nz), coords, (True, False, True), tags={(1, 0): 4, (1, 1): 1}, degrees=degrees,
                     bump=wall_bump(0.05), curved_layers=cl, seed=seed)
 
