@@ -571,3 +571,59 @@ class TetProblem:
             for f, F in enumerate(c.e2f[e]):
                 Rh[c.hoff[F]:c.hoff[F + 1]] += h[f].ravel()
         return Rq, Ru, Rh
+
+
+# ----------------------------------------------------------------------------
+# Newton and DIRK on the tetrahedral stage equations (Sec. 2.3, 2.5)
+# ----------------------------------------------------------------------------
+def newton(pb: TetProblem, Q, U, UH, tol=1e-11, maxit=8, fixed=None):
+    """Newton on the stage equations of pb (its Ustar, a_ii, dt): the condensed
+    trace system assembled and solved densely, interiors recovered, unit step.
+    Stops at ||F|| <= tol, or after exactly `fixed` iterations when given.
+    Returns (Q, U, UH, history of ||F|| before each iteration and at the end)."""
+    c = pb.conn
+    Q, U, UH = (np.array(x, dtype=float, copy=True) for x in (Q, U, UH))
+    hist = []
+    nit = maxit if fixed is None else fixed
+    NT = int(c.hoff[-1])
+    for k in range(nit + 1):
+        a, b, h = pb.global_residual(Q, U, UH)
+        hist.append(float(np.sqrt(a @ a + b @ b + h @ h)))
+        if k == nit or (fixed is None and hist[-1] <= tol):
+            break
+        pb.Q, pb.U, pb.UH = Q, U, UH
+        vals, cache = pb.assemble()
+        S = np.zeros((NT, NT))
+        for F in range(c.n_faces):
+            for bb in range(c.rowptr[F], c.rowptr[F + 1]):
+                G = c.col[bb]
+                S[c.hoff[F]:c.hoff[F + 1], c.hoff[G]:c.hoff[G + 1]] = vals[bb]
+        dUH = np.linalg.solve(S, pb.assemble_g(cache))
+        dQ, dU = np.zeros_like(Q), np.zeros_like(U)
+        for e in range(len(c.elem_p)):
+            q, u = pb.recover(e, cache[e], dUH)
+            dQ[c.qoff[e]:c.qoff[e + 1]] = q.ravel()
+            dU[c.uoff[e]:c.uoff[e + 1]] = u.ravel()
+        Q, U, UH = Q + dQ, U + dU, UH + dUH
+    return Q, U, UH, hist
+
+
+def dirk_step(prob, A, b, tol=1e-11, maxit=8, fixed=None):
+    """One DIRK step of the tetrahedral HDG system from (prob.Q, prob.U, prob.UH),
+    each stage solved by Newton from the previous stage (oracle.dirk.dirk_step)."""
+    from .dirk import dirk_step as generic_step
+    pb = TetProblem(prob)
+    Un = np.array(prob.U, dtype=float, copy=True)
+    state = {"Q": np.array(prob.Q, float), "U": Un.copy(), "UH": np.array(prob.UH, float)}
+    hists = []
+
+    def solve_stage(i, Us, a_ii):
+        pb.Ustar = Us
+        pb.a_ii = a_ii
+        Q, U, UH, h = newton(pb, state["Q"], state["U"], state["UH"], tol, maxit, fixed)
+        state.update(Q=Q, U=U, UH=UH)
+        hists.append(h)
+        return U
+
+    Unew, _ = generic_step(solve_stage, Un, A, b)
+    return state["Q"], Unew, state["UH"], hists

@@ -11,6 +11,7 @@
 #include <vector>
 
 #include "solve.cuh"
+#include "tet.h"
 
 using namespace hdg;
 
@@ -20,6 +21,11 @@ int fail(hdg_ctx* h, int code, const std::string& m) {
     h->err = m;
     return code;
 }
+
+// vector lengths of the state and trace unknowns (packed layouts on tetrahedral handles)
+int64_t len_u(const hdg_ctx* h) { return h->tet ? h->tet->n_u : h->E * h->NU; }
+int64_t len_q(const hdg_ctx* h) { return h->tet ? 3 * h->tet->n_u : h->E * h->NQV; }
+int64_t len_t(const hdg_ctx* h) { return h->tet ? h->tet->n_trace : h->F * h->BS; }
 
 #define CKS(call)                                                                         \
     do {                                                                                  \
@@ -54,6 +60,7 @@ int alloc(hdg_ctx* h, void** p, size_t bytes) {
 unsigned grid_for(int64_t n) { return (unsigned)std::min<int64_t>(kRedBlocks * 4, (n + 255) / 256); }
 
 int ensure_residual_storage(hdg_ctx* h) {
+    if (h->tet) return h->d_norms ? HDG_OK : alloc(h, (void**)&h->d_norms, sizeof(double) * 4);
     if (h->d_rk) return HDG_OK;
     int rc;
     if ((rc = alloc(h, (void**)&h->d_rk, sizeof(double) * h->E * h->NT))) return rc;
@@ -73,6 +80,7 @@ void dev_dot(hdg_ctx* h, const double* x, const double* y, int64_t n, double* ou
 }
 
 int precond_apply(hdg_ctx* h, const double* x, double* y) {
+    if (h->tet) return hdg::tet::bj_apply(h, x, y);
     int rc;
     if (h->pc_kind == HDG_PC_SCHWARZ) {
         DISPATCH_S(run_asm_apply, h, x, y);
@@ -82,7 +90,10 @@ int precond_apply(hdg_ctx* h, const double* x, double* y) {
     return rc;
 }
 
-bool precond_ready(const hdg_ctx* h) { return h->pc_kind == HDG_PC_SCHWARZ ? h->asm_ready : h->bj_ready; }
+bool precond_ready(const hdg_ctx* h) {
+    if (h->tet) return h->tet->bj_ready;
+    return h->pc_kind == HDG_PC_SCHWARZ ? h->asm_ready : h->bj_ready;
+}
 
 int schwarz_setup(hdg_ctx* h) {
     const int prec = h->sys_prec == HDG_PREC_MIXED ? HDG_PREC_MIXED : HDG_PREC_FP64;
@@ -114,7 +125,7 @@ int matvec(hdg_ctx* h, const double* x, double* y);
 
 // dUhat_0 = W c with c = argmin ||g - Z c|| over the window (eq. rb-min)
 int rb_guess(hdg_ctx* h, const double* g, double* x0) {
-    const int64_t N = h->F * h->BS;
+    const int64_t N = len_t(h);
     k_rb_gram_part<<<kRbBlocks, 256, 0, h->stream>>>(h->d_rbZ, h->rb_max, g, N, h->d_rbpart);
     k_rb_solve<<<1, 256, 0, h->stream>>>(h->d_rbpart, kRbBlocks, h->rb_max, h->d_rbc);
     CKS(cudaMemsetAsync(x0, 0, sizeof(double) * N, h->stream));
@@ -125,7 +136,7 @@ int rb_guess(hdg_ctx* h, const double* g, double* x0) {
 
 // insert an accepted correction w with z = S w (one trace matvec), dropping the oldest column when full
 int rb_push(hdg_ctx* h, const double* w) {
-    const int64_t N = h->F * h->BS;
+    const int64_t N = len_t(h);
     int rc;
     if ((rc = matvec(h, w, h->d_w))) return rc;
     k_rb_store<<<grid_for(N), 256, 0, h->stream>>>(w, h->d_w, h->d_rbW, h->d_rbZ, h->d_rbhead, N);
@@ -135,6 +146,7 @@ int rb_push(hdg_ctx* h, const double* w) {
 }
 
 int matvec(hdg_ctx* h, const double* x, double* y) {
+    if (h->tet) return hdg::tet::matvec(h, x, y);
     int rc;
     DISPATCH_S(run_matvec, h, x, y);
     return rc;
@@ -159,7 +171,7 @@ void cgs2(hdg_ctx* h, const double* V, int64_t N, int j, double* vn, double* hco
 
 // workspace of the synchronisation-free solver: Krylov basis, Newton work, device scalars
 int ensure_fixed_workspace(hdg_ctx* h, int m) {
-    const int64_t N = h->F * h->BS;
+    const int64_t N = len_t(h);
     int rc;
     if (h->gm_cap < m) {
         if ((rc = alloc(h, (void**)&h->d_V, sizeof(double) * (size_t)(m + 1) * N))) return rc;
@@ -174,7 +186,7 @@ int ensure_fixed_workspace(hdg_ctx* h, int m) {
         h->fx_cap = m;
     }
     if (!h->d_nw) {
-        size_t n = (size_t)h->E * (h->NU + h->NQV) + 2 * (size_t)h->F * h->BS;
+        size_t n = (size_t)(len_u(h) + len_q(h) + 2 * len_t(h));
         if ((rc = alloc(h, (void**)&h->d_nw, sizeof(double) * n))) return rc;
     }
     if (!h->d_hist) {
@@ -187,7 +199,7 @@ int ensure_fixed_workspace(hdg_ctx* h, int m) {
 // GMRES(m) from x = 0, exactly m iterations, no host synchronisation: the Givens
 // rotations and the triangular solve run on the device.
 int gmres_fixed_async(hdg_ctx* h, const double* b, double* x, int m, bool use_x0) {
-    const int64_t N = h->F * h->BS;
+    const int64_t N = len_t(h);
     double* V = h->d_V;
     double* w = h->d_w;
     double* beta = h->d_fx;
@@ -236,17 +248,21 @@ extern "C" {
 
 int hdg_residual(hdg_handle h, const double* U, const double* Q, const double* UH, const double* Ustar,
                  const double* nu, double dt, double a_ii, double* Rq, double* Ru, double* Ruh, double* norms) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (!U || !Q || !UH || !Ustar) return fail(h, HDG_EINVAL, "U, Q, UH and Ustar are required");
     if (!(dt > 0.0) || !(a_ii > 0.0)) return fail(h, HDG_EINVAL, "dt and a_ii must be positive");
     int rc = ensure_residual_storage(h);
     if (rc) return rc;
-    LinArgs a{U, Q, UH, Ustar, nu, dt, a_ii};
-    DISPATCH_S(run_residual, h, a, Rq, Ru, Ruh);
-    if (rc) return rc;
-    k_sum_parts<<<1, 256, 0, h->stream>>>(h->d_part, h->E, h->d_part + h->E, h->F, h->d_norms);
+    if (h->tet) {
+        if (nu) return fail(h, HDG_EUNSUPPORTED, "artificial viscosity is not available on tetrahedral handles");
+        if ((rc = hdg::tet::residual(h, U, Q, UH, Ustar, dt, a_ii, Rq, Ru, Ruh, h->d_norms))) return rc;
+    } else {
+        LinArgs a{U, Q, UH, Ustar, nu, dt, a_ii};
+        DISPATCH_S(run_residual, h, a, Rq, Ru, Ruh);
+        if (rc) return rc;
+        k_sum_parts<<<1, 256, 0, h->stream>>>(h->d_part, h->E, h->d_part + h->E, h->F, h->d_norms);
+    }
     CKS(cudaGetLastError());
     if (norms) {
         double tmp[3];
@@ -269,11 +285,10 @@ int hdg_lift_gradient(hdg_handle h, const double* U, const double* UH, double* Q
 
 int hdg_update_state(hdg_handle h, double* U, double* Q, double* UH, const double* dU, const double* dQ,
                      const double* dUH, double alpha) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (!U || !Q || !UH || !dU || !dQ || !dUH) return fail(h, HDG_EINVAL, "NULL argument");
-    const int64_t nU = h->E * h->NU, nQ = h->E * h->NQV, nH = h->F * h->BS;
+    const int64_t nU = len_u(h), nQ = len_q(h), nH = len_t(h);
     k_axpby<<<grid_for(nU), 256, 0, h->stream>>>(alpha, dU, 1.0, U, nU);
     k_axpby<<<grid_for(nQ), 256, 0, h->stream>>>(alpha, dQ, 1.0, Q, nQ);
     k_axpby<<<grid_for(nH), 256, 0, h->stream>>>(alpha, dUH, 1.0, UH, nH);
@@ -282,9 +297,9 @@ int hdg_update_state(hdg_handle h, double* U, double* Q, double* UH, const doubl
 }
 
 int hdg_blockjacobi_setup(hdg_handle h) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
+    if (h->tet) return hdg::tet::bj_setup(h);
     int rc;
     if (!h->d_bjlu) {
         if ((rc = alloc(h, (void**)&h->d_bjlu, sizeof(double) * h->F * h->BS * h->BS))) return rc;
@@ -296,10 +311,11 @@ int hdg_blockjacobi_setup(hdg_handle h) {
 }
 
 int hdg_set_preconditioner(hdg_handle h, int kind) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (kind != HDG_PC_BLOCKJACOBI && kind != HDG_PC_SCHWARZ)
         return fail(h, HDG_EINVAL, "preconditioner must be HDG_PC_BLOCKJACOBI or HDG_PC_SCHWARZ");
+    if (h->tet && kind != HDG_PC_BLOCKJACOBI)
+        return fail(h, HDG_EUNSUPPORTED, "tetrahedral handles use the block-Jacobi preconditioner");
     h->pc_kind = kind;
     return HDG_OK;
 }
@@ -364,13 +380,12 @@ int hdg_tgv_diagnostics(hdg_handle h, const double* U, const double* Q, double* 
 }
 
 int hdg_rb_setup(hdg_handle h, int nb_max) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (nb_max < 0 || nb_max > kRbMax) return fail(h, HDG_EINVAL, "nb_max must be in 0..20");
     h->rb_max = 0;
     if (nb_max == 0) return HDG_OK;
-    const int64_t N = h->F * h->BS;
+    const int64_t N = len_t(h);
     int rc;
     if ((rc = alloc(h, (void**)&h->d_rbW, sizeof(double) * (size_t)nb_max * N))) return rc;
     if ((rc = alloc(h, (void**)&h->d_rbZ, sizeof(double) * (size_t)nb_max * N))) return rc;
@@ -388,7 +403,6 @@ int hdg_rb_setup(hdg_handle h, int nb_max) {
 }
 
 int hdg_rb_push(hdg_handle h, const double* w) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (h->rb_max <= 0) return fail(h, HDG_EINVAL, "reduced basis not set up (hdg_rb_setup)");
     if (!h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
@@ -397,7 +411,6 @@ int hdg_rb_push(hdg_handle h, const double* w) {
 }
 
 int hdg_rb_guess(hdg_handle h, const double* g, double* x0) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (h->rb_max <= 0) return fail(h, HDG_EINVAL, "reduced basis not set up (hdg_rb_setup)");
     if (!g || !x0 || g == x0) return fail(h, HDG_EINVAL, "g and x0 must be distinct device arrays");
@@ -405,10 +418,10 @@ int hdg_rb_guess(hdg_handle h, const double* g, double* x0) {
 }
 
 int hdg_blockjacobi_apply(hdg_handle h, const double* x, double* y) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
-    if (!h->bj_ready) return fail(h, HDG_EINVAL, "block-Jacobi factors not set up");
+    if (!(h->tet ? h->tet->bj_ready : h->bj_ready)) return fail(h, HDG_EINVAL, "block-Jacobi factors not set up");
     if (!x || !y || x == y) return fail(h, HDG_EINVAL, "x and y must be distinct device arrays");
+    if (h->tet) return hdg::tet::bj_apply(h, x, y);
     int rc;
     DISPATCH_S(run_bj_apply, h, x, y);
     return rc;
@@ -416,7 +429,6 @@ int hdg_blockjacobi_apply(hdg_handle h, const double* x, double* y) {
 
 int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_iter, double rtol, int precond,
               int* iters_out, double* relres_out) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
     if (!b || !x || b == x) return fail(h, HDG_EINVAL, "b and x must be distinct device arrays");
@@ -424,7 +436,7 @@ int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_ite
         return fail(h, HDG_EINVAL, "restart in 1..500, max_iter >= 1, rtol > 0 required");
     if (precond && !precond_ready(h))
         return fail(h, HDG_EINVAL, "precond = 1 needs the selected preconditioner set up (hdg_blockjacobi_setup / hdg_schwarz_setup)");
-    const int64_t N = h->F * h->BS;
+    const int64_t N = len_t(h);
     int rc;
     if (h->gm_cap < restart) {
         // workspace grows to the largest restart length requested; kept until destroy
@@ -522,20 +534,19 @@ int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_ite
 int hdg_newton(hdg_handle h, double* U, double* Q, double* UH, const double* Ustar, const double* nu, double dt,
                double a_ii, double tol, int max_newton, int restart, int max_gmres, double gmres_rtol,
                double* hist, int* newton_iters, int* gmres_iters) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (!U || !Q || !UH || !Ustar) return fail(h, HDG_EINVAL, "U, Q, UH and Ustar are required");
     if (!(tol > 0.0) || max_newton < 0) return fail(h, HDG_EINVAL, "tol > 0 and max_newton >= 0 required");
     int rc;
     if (!h->d_nw) {
-        size_t n = (size_t)h->E * (h->NU + h->NQV) + 2 * (size_t)h->F * h->BS;
+        size_t n = (size_t)(len_u(h) + len_q(h) + 2 * len_t(h));
         if ((rc = alloc(h, (void**)&h->d_nw, sizeof(double) * n))) return rc;
     }
     double* dU = h->d_nw;
-    double* dQ = dU + (size_t)h->E * h->NU;
-    double* dUH = dQ + (size_t)h->E * h->NQV;
-    double* g = dUH + (size_t)h->F * h->BS;
+    double* dQ = dU + (size_t)len_u(h);
+    double* dUH = dQ + (size_t)len_q(h);
+    double* g = dUH + (size_t)len_t(h);
     int total = 0, k = 0;
     double nrm[3];
     for (;; ++k) {
@@ -549,7 +560,7 @@ int hdg_newton(hdg_handle h, double* U, double* Q, double* UH, const double* Ust
         if (h->rb_max > 0) {
             if ((rc = rb_guess(h, g, dUH))) return rc;
         } else {
-            CKS(cudaMemsetAsync(dUH, 0, sizeof(double) * h->F * h->BS, h->stream));
+            CKS(cudaMemsetAsync(dUH, 0, sizeof(double) * len_t(h), h->stream));
         }
         int it = 0;
         double rel = 0.0;
@@ -575,9 +586,9 @@ int precond_setup(hdg_ctx* h) { return h->pc_kind == HDG_PC_SCHWARZ ? schwarz_se
 int newton_iteration_async(hdg_ctx* h, double* U, double* Q, double* UH, const double* Ustar, const double* nu,
                            double dt, double a_ii, int m) {
     double* dU = h->d_nw;
-    double* dQ = dU + (size_t)h->E * h->NU;
-    double* dUH = dQ + (size_t)h->E * h->NQV;
-    double* g = dUH + (size_t)h->F * h->BS;
+    double* dQ = dU + (size_t)len_u(h);
+    double* dUH = dQ + (size_t)len_q(h);
+    double* g = dUH + (size_t)len_t(h);
     int rc;
     if ((rc = hdg_residual(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr, nullptr, nullptr, nullptr))) return rc;
     k_hist_push<<<1, 32, 0, h->stream>>>(h->d_norms, h->d_hist, h->d_hcount, 4096);
@@ -635,7 +646,7 @@ uint64_t dbits(double d) { uint64_t u; std::memcpy(&u, &d, 8); return u; }
 int ensure_dirk_storage(hdg_ctx* h, int s) {
     if (h->dirk_cap >= s) return HDG_OK;
     int rc;
-    const size_t n = (size_t)h->E * h->NU;
+    const size_t n = (size_t)len_u(h);
     if ((rc = alloc(h, (void**)&h->d_dirk, sizeof(double) * n * (s + 2)))) return rc;
     h->dirk_cap = s;
     return HDG_OK;
@@ -647,7 +658,6 @@ extern "C" {
 
 int hdg_newton_fixed(hdg_handle h, double* U, double* Q, double* UH, const double* Ustar, const double* nu,
                      double dt, double a_ii, int n_newton, int m, int use_graph, double* hist) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (!U || !Q || !UH || !Ustar) return fail(h, HDG_EINVAL, "U, Q, UH and Ustar are required");
@@ -681,7 +691,6 @@ int hdg_newton_fixed(hdg_handle h, double* U, double* Q, double* UH, const doubl
 
 int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* nu, double dt, int s,
                   const double* A, const double* b, int n_newton, int m, int use_graph, double* hist) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (!U || !Q || !UH || !A || !b) return fail(h, HDG_EINVAL, "NULL argument");
@@ -710,7 +719,7 @@ int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* 
     int rc;
     if ((rc = ensure_fixed_workspace(h, m))) return rc;
     if ((rc = ensure_dirk_storage(h, s))) return rc;
-    const int64_t n = h->E * h->NU;
+    const int64_t n = len_u(h);
     double* Un = h->d_dirk;                  // U^n
     double* Us = Un + n;                     // U* of the current stage
     double* St = Us + n;                     // stage states U^{n,1..s}

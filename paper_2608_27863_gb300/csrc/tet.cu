@@ -11,6 +11,7 @@
 #include <cstring>
 
 #include "kernels.cuh"
+#include "solve.cuh"
 #include "tet.h"
 
 namespace hdg {
@@ -64,6 +65,7 @@ struct KArgs {
     double* mat; double* rec; double* work; int64_t wstride;
     PhysT<double> ph; double dt, a_ii, tau; const double* ub; double ew;
     int32_t* status;
+    double* Rq; double* Ru; double* rk; double* part;     // residual evaluation outputs
 };
 
 __device__ __forceinline__ int face_of_point(const TetElem& d, int r) {
@@ -260,13 +262,54 @@ __device__ __forceinline__ void gemm_chunk(const double* sR, const double* sT, i
     }
 }
 
+
+// A0: gather the element's nodal state and trace into shared memory
+__device__ void gather_element(const KArgs& A, const TetElem& d, double* sm) {
+    const int tid = threadIdx.x, NU = d.NU, t = d.t;
+    for (int i = tid; i < NU; i += NTH) { sm[S_U + i] = A.U[d.uoff + i]; sm[S_US + i] = A.Ustar[d.uoff + i]; }
+    for (int i = tid; i < 3 * NU; i += NTH) sm[S_Q + i] = A.Q[3 * d.uoff + i];
+    for (int i = tid; i < t; i += NTH) {
+        int f = 0, r = i;
+        while (f < 3 && r >= M * d.nfp[f]) { r -= M * d.nfp[f]; ++f; }
+        sm[S_UH + i] = A.UH[d.hoff[f] + r];
+    }
+}
+
+// geometry at the quadrature points: volume records (w |J|, J^{-1}) and face
+// records (w_s |J| J^{-T} nu), from the per-point data of curved elements or the
+// affine element's constant Jacobian
+__device__ void load_geometry(const KArgs& A, const TetElem& d, double* gv, double* gf) {
+    const int tid = threadIdx.x;
+    const double* wq = A.tab + d.vtab + (size_t)4 * d.Nq * d.Np;
+    for (int g = tid; g < d.Nq; g += NTH) {
+        double* o = gv + g * 10;
+        if (d.curved) {
+            for (int k = 0; k < 10; ++k) o[k] = A.gvol[d.goff + (int64_t)g * 10 + k];
+        } else {
+            o[0] = wq[g] * d.detJ;
+            for (int k = 0; k < 9; ++k) o[1 + k] = d.Jinv[k];
+        }
+    }
+    for (int r = tid; r < d.sfq; r += NTH) {
+        double* o = gf + r * 3;
+        if (d.curved) {
+            for (int k = 0; k < 3; ++k) o[k] = A.gface[d.gfoff + (int64_t)r * 3 + k];
+        } else {
+            const int f = face_of_point(d, r), s = r - d.soff[f];
+            const double* nu = A.tab + d.ftab[f] + (size_t)d.nfq[f] * d.Np;
+            const double ws = A.tab[d.ttab[f] + (size_t)d.nfq[f] * d.nfp[f] + s];
+            for (int k = 0; k < 3; ++k)
+                o[k] = ws * d.detJ * (d.Jinv[0 * 3 + k] * nu[0] + d.Jinv[1 * 3 + k] * nu[1] + d.Jinv[2 * 3 + k] * nu[2]);
+        }
+    }
+}
+
 __device__ void process_element(const KArgs& A, const TetElem& d, double* W, double* sm, int* sflag) {
     const int tid = threadIdx.x;
     const int Np = d.Np, Nq = d.Nq, NU = d.NU, t = d.t, LD = d.LD, sfq = d.sfq;
     const int sfp = t / M, Nc = Np + sfp, npt = Nq + sfq;
     const double* phi = A.tab + d.vtab;
     const double* dphi = phi + (size_t)Nq * Np;
-    const double* wq = dphi + (size_t)3 * Nq * Np;
     double* Mx = A.mat + d.moff;
     double* Gk = A.rec + d.roff;                     // [3][Np][Np]
     double* Hk = Gk + 3 * Np * Np;                   // [3][Np][sfp]
@@ -283,36 +326,8 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
     fpo[0] = 0;
     for (int f = 1; f < 4; ++f) fpo[f] = fpo[f - 1] + d.nfp[f - 1];
 
-    // A0: gather
-    for (int i = tid; i < NU; i += NTH) { sU[i] = A.U[d.uoff + i]; sUs[i] = A.Ustar[d.uoff + i]; }
-    for (int i = tid; i < 3 * NU; i += NTH) sQ[i] = A.Q[3 * d.uoff + i];
-    for (int i = tid; i < t; i += NTH) {
-        int f = 0, r = i;
-        while (f < 3 && r >= M * d.nfp[f]) { r -= M * d.nfp[f]; ++f; }
-        sUH[i] = A.UH[d.hoff[f] + r];
-    }
-    // geometry at the quadrature points
-    for (int g = tid; g < Nq; g += NTH) {
-        double* o = gv + g * 10;
-        if (d.curved) {
-            for (int k = 0; k < 10; ++k) o[k] = A.gvol[d.goff + (int64_t)g * 10 + k];
-        } else {
-            o[0] = wq[g] * d.detJ;
-            for (int k = 0; k < 9; ++k) o[1 + k] = d.Jinv[k];
-        }
-    }
-    for (int r = tid; r < sfq; r += NTH) {
-        double* o = gf + r * 3;
-        if (d.curved) {
-            for (int k = 0; k < 3; ++k) o[k] = A.gface[d.gfoff + (int64_t)r * 3 + k];
-        } else {
-            const int f = face_of_point(d, r), s = r - d.soff[f];
-            const double* nu = A.tab + d.ftab[f] + (size_t)d.nfq[f] * Np;
-            const double ws = A.tab[d.ttab[f] + (size_t)d.nfq[f] * d.nfp[f] + s];
-            for (int k = 0; k < 3; ++k)
-                o[k] = ws * d.detJ * (d.Jinv[0 * 3 + k] * nu[0] + d.Jinv[1 * 3 + k] * nu[1] + d.Jinv[2 * 3 + k] * nu[2]);
-        }
-    }
+    gather_element(A, d, sm);
+    load_geometry(A, d, gv, gf);
     __syncthreads();
     // physical gradients at the volume points, mass matrix
     double* dp = W + W_DP;
@@ -850,6 +865,255 @@ __global__ void __launch_bounds__(NTH) k_tet_recover(const TetElem* el, const do
     }
 }
 
+
+// FP64 stage residual of one element (eq. hdg-weak with the DIRK mass term):
+// R_q, R_u into Rq / Ru (when given), the element's trace residual R_uhat^K
+// into rk, the sum of squares of (R_q, R_u) into part[e]
+__device__ void residual_element(const KArgs& A, const TetElem& d, int64_t e, double* W, double* sm) {
+    const int tid = threadIdx.x;
+    const int Np = d.Np, Nq = d.Nq, NU = d.NU, sfq = d.sfq, npt = Nq + sfq;
+    const double* phi = A.tab + d.vtab;
+    const double* dphi = phi + (size_t)Nq * Np;
+    double* sU = sm + S_U;
+    double* sUs = sm + S_US;
+    double* sQ = sm + S_Q;
+    double* sUH = sm + S_UH;
+    double* gv = W + W_GV;
+    double* gf = W + W_GF;
+    double* pu = W + W_PU;
+    double* pq = W + W_PQ;
+    double* pd = W + W_PL;          // [NQMAX][m]: (U - U*) at the volume points
+    double* ph = W + W_PH;
+    double* rv = W + W_RV;
+    double* rf = W + W_RF;
+    double* rb = W + W_RB;
+    gather_element(A, d, sm);
+    load_geometry(A, d, gv, gf);
+    __syncthreads();
+    for (int x = tid; x < npt; x += NTH) {
+        const double* br = basis_row(A, d, x);
+        double u[M], q[M][3], du[M];
+        for (int a = 0; a < M; ++a) { u[a] = 0.0; du[a] = 0.0; for (int k = 0; k < 3; ++k) q[a][k] = 0.0; }
+        for (int j = 0; j < Np; ++j) {
+            const double w = br[j];
+            for (int a = 0; a < M; ++a) {
+                u[a] += w * sU[a * Np + j];
+                du[a] += w * (sU[a * Np + j] - sUs[a * Np + j]);
+                for (int k = 0; k < 3; ++k) q[a][k] += w * sQ[(k * M + a) * Np + j];
+            }
+        }
+        for (int a = 0; a < M; ++a) {
+            pu[x * M + a] = u[a];
+            for (int k = 0; k < 3; ++k) pq[(x * M + a) * 3 + k] = q[a][k];
+        }
+        if (x < Nq) {
+            for (int a = 0; a < M; ++a) pd[x * M + a] = du[a];
+            const double* g = gv + x * 10;
+            const double wJ = -A.dt * g[0];
+            double Fc[M][3], Fv[M][3];
+            conv_flux<3, double, double>(u, A.ph, Fc);
+            visc_flux<3, double, double>(u, q, 0.0, A.ph, Fv);
+            for (int a = 0; a < M; ++a)
+                for (int r = 0; r < 3; ++r) {
+                    double s2 = 0.0;
+                    for (int k = 0; k < 3; ++k) s2 += g[1 + r * 3 + k] * (Fc[a][k] - Fv[a][k]);
+                    rv[(x * M + a) * 3 + r] = wJ * s2;
+                }
+        } else {
+            const int r = x - Nq, f = face_of_point(d, r), s2 = r - d.soff[f], tag = d.tag[f];
+            const double* mu = A.tab + d.ttab[f] + (size_t)s2 * d.nfp[f];
+            double uh[M];
+            for (int a = 0; a < M; ++a) {
+                double v = 0.0;
+                for (int l = 0; l < d.nfp[f]; ++l) v += mu[l] * sUH[d.toff[f] + a * d.nfp[f] + l];
+                uh[a] = v;
+                ph[r * M + a] = v;
+            }
+            const double* nw = gf + r * 3;
+            const double nrm = sqrt(nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2]);
+            double Fc[M][3], Fv[M][3];
+            conv_flux<3, double, double>(uh, A.ph, Fc);
+            visc_flux<3, double, double>(uh, q, 0.0, A.ph, Fv);
+            for (int a = 0; a < M; ++a) {
+                double fn = 0.0;
+                for (int k = 0; k < 3; ++k) fn += (Fc[a][k] - Fv[a][k]) * nw[k];
+                const double fh = fn + A.tau * nrm * (u[a] - uh[a]);
+                rf[r * M + a] = A.dt * fh;
+                rb[r * M + a] = boundary_form<M>(tag, a, fh, nrm, u, uh, tag == 1 ? A.ub[a] : 0.0, A.ew);
+            }
+        }
+    }
+    __syncthreads();
+    double sq = 0.0;
+    for (int idx = tid; idx < 4 * NU; idx += NTH) {
+        double v = 0.0;
+        if (idx < 3 * NU) {                   // R_q[k][a][i]
+            const int k = idx / NU, rem = idx - k * NU, a = rem / Np, i = rem - a * Np;
+            for (int g = 0; g < Nq; ++g) {
+                const double* G = gv + g * 10;
+                const double dk = G[1 + 0 * 3 + k] * dphi[(size_t)g * Np + i] +
+                                  G[1 + 1 * 3 + k] * dphi[((size_t)Nq + g) * Np + i] +
+                                  G[1 + 2 * 3 + k] * dphi[((size_t)2 * Nq + g) * Np + i];
+                v += G[0] * (pq[(g * M + a) * 3 + k] * phi[(size_t)g * Np + i] + pu[g * M + a] * dk);
+            }
+            for (int r = 0; r < sfq; ++r) v -= gf[r * 3 + k] * ph[r * M + a] * basis_row(A, d, Nq + r)[i];
+            if (A.Rq) A.Rq[3 * d.uoff + idx] = v;
+        } else {                              // R_u[a][i]
+            const int rem = idx - 3 * NU, a = rem / Np, i = rem - a * Np;
+            double mass = 0.0;
+            for (int g = 0; g < Nq; ++g) {
+                mass += gv[g * 10] * phi[(size_t)g * Np + i] * pd[g * M + a];
+                for (int r = 0; r < 3; ++r) v += dphi[((size_t)r * Nq + g) * Np + i] * rv[(g * M + a) * 3 + r];
+            }
+            v += mass / A.a_ii;
+            for (int r = 0; r < sfq; ++r) v += basis_row(A, d, Nq + r)[i] * rf[r * M + a];
+            if (A.Ru) A.Ru[d.uoff + rem] = v;
+        }
+        sq += v * v;
+    }
+    for (int idx = tid; idx < d.t; idx += NTH) {   // R_uhat^K[f][a][l]
+        int f = 0, rem = idx;
+        while (f < 3 && rem >= M * d.nfp[f]) { rem -= M * d.nfp[f]; ++f; }
+        const int a = rem / d.nfp[f], l = rem - a * d.nfp[f];
+        const double* mu = A.tab + d.ttab[f];
+        double v = 0.0;
+        for (int q = 0; q < d.nfq[f]; ++q) v += mu[(size_t)q * d.nfp[f] + l] * rb[(d.soff[f] + q) * M + a];
+        A.rk[d.koff + idx] = v;
+    }
+    __shared__ double red[NTH / 32];
+    for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
+    if ((tid & 31) == 0) red[tid >> 5] = sq;
+    __syncthreads();
+    if (tid == 0) {
+        double s2 = 0.0;
+        for (int w = 0; w < NTH / 32; ++w) s2 += red[w];
+        A.part[e] = s2;
+    }
+}
+
+__global__ void __launch_bounds__(NTH, 2) k_tet_residual(KArgs A) {
+    extern __shared__ double sm[];
+    __shared__ TetElem d;
+    const int tid = threadIdx.x;
+    double* W = A.work + (int64_t)blockIdx.x * A.wstride;
+    for (int64_t e = blockIdx.x; e < A.E; e += gridDim.x) {
+        constexpr int NW = (int)(sizeof(TetElem) / 8);
+        for (int i = tid; i < NW; i += NTH)
+            reinterpret_cast<int64_t*>(&d)[i] = reinterpret_cast<const int64_t*>(A.el + e)[i];
+        __syncthreads();
+        residual_element(A, d, e, W, sm);
+        __syncthreads();
+    }
+}
+
+// R_uhat of every face: the element contributions in ascending element order; squares into part
+__global__ void k_tet_residual_faces(const TetElem* el, const double* rk, const int64_t* hoff, const int32_t* f2e,
+                                     const int32_t* f2lf, int64_t F, double* Ruh, double* part) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t Fr = wid; Fr < F; Fr += nw) {
+        int e0 = f2e[2 * Fr], e1 = f2e[2 * Fr + 1], l0 = f2lf[2 * Fr], l1 = f2lf[2 * Fr + 1];
+        if (e1 >= 0 && e1 < e0) { int t = e0; e0 = e1; e1 = t; t = l0; l0 = l1; l1 = t; }
+        const int bs = (int)(hoff[Fr + 1] - hoff[Fr]);
+        double sq = 0.0;
+        for (int r = lane; r < bs; r += 32) {
+            double v = rk[el[e0].koff + el[e0].toff[l0] + r];
+            if (e1 >= 0) v += rk[el[e1].koff + el[e1].toff[l1] + r];
+            if (Ruh) Ruh[hoff[Fr] + r] = v;
+            sq += v * v;
+        }
+        for (int off = 16; off > 0; off >>= 1) sq += __shfl_down_sync(0xffffffffu, sq, off);
+        if (lane == 0) part[Fr] = sq;
+    }
+}
+
+// block-Jacobi set-up: explicit inverse of every diagonal block S_FF by
+// Gauss-Jordan elimination with partial pivoting (column-major result)
+__global__ void __launch_bounds__(128) k_tet_bj_setup(const double* vals, const int64_t* boff, const int32_t* diagb,
+                                                       const int64_t* hoff, const int64_t* bjoff, int64_t F,
+                                                       double* inv, int32_t* status) {
+    extern __shared__ double sa[];                // [bs][2 bs] augmented rows
+    __shared__ int pr;
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int64_t Fr = blockIdx.x; Fr < F; Fr += gridDim.x) {
+        const int bs = (int)(hoff[Fr + 1] - hoff[Fr]), w2 = 2 * bs;
+        const double* B = vals + boff[diagb[Fr]];
+        for (int idx = tid; idx < bs * w2; idx += 128) {
+            const int r = idx / w2, c = idx - r * w2;
+            sa[idx] = c < bs ? B[(int64_t)c * bs + r] : (c - bs == r ? 1.0 : 0.0);
+        }
+        __syncthreads();
+        for (int c = 0; c < bs; ++c) {
+            if (tid < 32) {
+                double bv = -1.0;
+                int bi = INT_MAX;
+                for (int r = c + lane; r < bs; r += 32) {
+                    const double v = fabs(sa[r * w2 + c]);
+                    if (v > bv) { bv = v; bi = r; }
+                }
+                for (int off = 16; off > 0; off >>= 1) {
+                    const double ov = __shfl_down_sync(0xffffffffu, bv, off);
+                    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+                }
+                if (lane == 0) pr = (bi == INT_MAX) ? c : bi;
+            }
+            __syncthreads();
+            const int p = pr;
+            if (p != c)
+                for (int k = tid; k < w2; k += 128) {
+                    const double t = sa[c * w2 + k];
+                    sa[c * w2 + k] = sa[p * w2 + k];
+                    sa[p * w2 + k] = t;
+                }
+            __syncthreads();
+            double pv = sa[c * w2 + c];
+            if (pv == 0.0 || !isfinite(pv)) {
+                if (tid == 0) atomicOr(status, pv == 0.0 ? 1 : 2);
+                pv = 1.0;
+            }
+            const double ip = 1.0 / pv;
+            __syncthreads();
+            for (int k = tid; k < w2; k += 128) sa[c * w2 + k] *= ip;
+            __syncthreads();
+            for (int idx = tid; idx < bs * w2; idx += 128) {
+                const int r = idx / w2, k = idx - r * w2;
+                if (r == c) continue;
+                const double f = sa[r * w2 + c];
+                if (k != c) sa[idx] = fma(-f, sa[c * w2 + k], sa[idx]);
+            }
+            __syncthreads();
+            for (int r = tid; r < bs; r += 128)
+                if (r != c) sa[r * w2 + c] = 0.0;
+            __syncthreads();
+        }
+        double* o = inv + bjoff[Fr];
+        for (int idx = tid; idx < bs * bs; idx += 128) {
+            const int c = idx / bs, r = idx - c * bs;
+            o[idx] = sa[r * w2 + bs + c];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_tet_bj_apply(const double* inv, const int64_t* hoff, const int64_t* bjoff, int64_t F,
+                               const double* x, double* y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t Fr = wid; Fr < F; Fr += nw) {
+        const int bs = (int)(hoff[Fr + 1] - hoff[Fr]);
+        const double* B = inv + bjoff[Fr];
+        const double* xf = x + hoff[Fr];
+        for (int r = lane; r < bs; r += 32) {
+            double s = 0.0;
+            for (int c = 0; c < bs; ++c) s = fma(B[(int64_t)c * bs + r], xf[c], s);
+            y[hoff[Fr] + r] = s;
+        }
+    }
+}
+
 namespace {
 
 template <class T>
@@ -896,13 +1160,22 @@ int create_device(hdg_ctx* h, std::string& err) {
     UP(c->d_el, c->el); UP(c->d_order, c->order); UP(c->d_tab, c->tab);
     UP(c->d_gvol, c->gvol); UP(c->d_gface, c->gface); UP(c->d_hoff, c->hoff); UP(c->d_boff, c->boff);
     UP(c->d_rowptr, c->rowptr); UP(c->d_col, c->col); UP(c->d_cptr, c->cptr); UP(c->d_centry, c->centry);
-    UP(c->d_f2e, c->f2e); UP(c->d_f2lf, c->f2lf);
+    UP(c->d_f2e, c->f2e); UP(c->d_f2lf, c->f2lf); UP(c->d_diagb, c->diagb); UP(c->d_bjoff, c->bjoff);
 #undef UP
     if ((rc = tet_alloc(h, &c->d_mat, (size_t)c->n_mat, err))) return rc;
     if ((rc = tet_alloc(h, &c->d_rec, (size_t)c->n_rec, err))) return rc;
     if ((rc = tet_alloc(h, &c->d_vals, (size_t)c->n_vals, err))) return rc;
     if ((rc = tet_alloc(h, &c->d_g, (size_t)c->n_trace, err))) return rc;
     if ((rc = tet_alloc(h, &c->d_next, 1, err))) return rc;
+    if ((rc = tet_alloc(h, &c->d_rk, (size_t)c->n_rk, err))) return rc;           // residual scratch: allocated
+    if ((rc = tet_alloc(h, &c->d_part, (size_t)(c->E + c->F), err))) return rc;   // here so graphs can capture it
+    int bsmax = 0;
+    for (int64_t F = 0; F < c->F; ++F) bsmax = std::max<int>(bsmax, (int)(c->hoff[F + 1] - c->hoff[F]));
+    if (cudaFuncSetAttribute(k_tet_bj_setup, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * 2 * (size_t)bsmax * bsmax)) != cudaSuccess) {
+        err = "shared-memory opt-in of the block-Jacobi kernel failed";
+        return HDG_ECUDA;
+    }
     if ((rc = tet_alloc(h, &h->d_status, 1, err))) return rc;
     if ((rc = tet_alloc(h, &h->d_ub, M, err))) return rc;
     int dev = 0, nsm = 0;
@@ -911,6 +1184,11 @@ int create_device(hdg_ctx* h, std::string& err) {
     if (cudaFuncSetAttribute(k_tet_linearize, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(S_TOTAL * sizeof(double))) != cudaSuccess) {
         err = "shared-memory opt-in of the tetrahedral kernel failed";
+        return HDG_ECUDA;
+    }
+    if (cudaFuncSetAttribute(k_tet_residual, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(S_TOTAL * sizeof(double))) != cudaSuccess) {
+        err = "shared-memory opt-in of the tetrahedral residual kernel failed";
         return HDG_ECUDA;
     }
     int per_sm = 0;
@@ -957,6 +1235,8 @@ int linearize(hdg_ctx* h, const double* U, const double* Q, const double* UH, co
     prof_end(h);
     TET_CK(cudaGetLastError());
     c->have_system = true;
+    h->have_system = true;
+    c->bj_ready = false;       // the diagonal blocks changed
     return HDG_OK;
 }
 
@@ -976,6 +1256,64 @@ int recover(hdg_ctx* h, const double* dUH, double* dQ, double* dU) {
     prof_begin(h, HDG_K_RECOVER);
     k_tet_recover<<<g, NTH, 0, h->stream>>>(c->d_el, c->d_mat, c->d_rec, dUH, dQ, dU, c->E);
     prof_end(h);
+    TET_CK(cudaGetLastError());
+    return HDG_OK;
+}
+
+namespace {
+KArgs base_args(hdg_ctx* h, const double* U, const double* Q, const double* UH, const double* Ustar, double dt,
+                double a_ii) {
+    Ctx* c = h->tet;
+    KArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.el = c->d_el; A.order = c->d_order; A.E = c->E; A.next = c->d_next;
+    A.tab = c->d_tab; A.gvol = c->d_gvol; A.gface = c->d_gface;
+    A.U = U; A.Q = Q; A.UH = UH; A.Ustar = Ustar;
+    A.mat = c->d_mat; A.rec = c->d_rec; A.work = c->d_work; A.wstride = c->work_stride;
+    A.ph = phys_t<double>(h->phys); A.dt = dt; A.a_ii = a_ii; A.tau = h->phys.tau;
+    A.ub = h->d_ub; A.ew = h->e_wall; A.status = h->d_status;
+    return A;
+}
+}  // namespace
+
+int residual(hdg_ctx* h, const double* U, const double* Q, const double* UH, const double* Ustar, double dt,
+             double a_ii, double* Rq, double* Ru, double* Ruh, double* norms) {
+    Ctx* c = h->tet;
+    KArgs A = base_args(h, U, Q, UH, Ustar, dt, a_ii);
+    A.Rq = Rq; A.Ru = Ru; A.rk = c->d_rk; A.part = c->d_part;
+    cudaStream_t st = h->stream;
+    prof_begin(h, HDG_K_POINT);
+    k_tet_residual<<<c->n_slots, NTH, S_TOTAL * sizeof(double), st>>>(A);
+    const unsigned gf = (unsigned)std::min<int64_t>(65535, (c->F + 7) / 8);
+    k_tet_residual_faces<<<gf, 256, 0, st>>>(c->d_el, c->d_rk, c->d_hoff, c->d_f2e, c->d_f2lf, c->F, Ruh,
+                                             c->d_part + c->E);
+    k_sum_parts<<<1, 256, 0, st>>>(c->d_part, c->E, c->d_part + c->E, c->F, norms);
+    prof_end(h);
+    TET_CK(cudaGetLastError());
+    return HDG_OK;
+}
+
+int bj_setup(hdg_ctx* h) {
+    Ctx* c = h->tet;
+    if (!c->have_system) { h->err = "no assembled trace system"; return HDG_EINVAL; }
+    std::string err;
+    int rc;
+    if (!c->d_bj && (rc = tet_alloc(h, &c->d_bj, (size_t)c->bjoff[c->F], err))) { h->err = err; return rc; }
+    int bsmax = 0;
+    for (int64_t F = 0; F < c->F; ++F) bsmax = std::max<int>(bsmax, (int)(c->hoff[F + 1] - c->hoff[F]));
+    const size_t smem = sizeof(double) * (size_t)bsmax * 2 * bsmax;
+    const unsigned g = (unsigned)std::min<int64_t>(c->F, 152 * 4);
+    k_tet_bj_setup<<<g, 128, smem, h->stream>>>(c->d_vals, c->d_boff, c->d_diagb, c->d_hoff, c->d_bjoff, c->F,
+                                               c->d_bj, h->d_status);
+    TET_CK(cudaGetLastError());
+    c->bj_ready = true;
+    return HDG_OK;
+}
+
+int bj_apply(hdg_ctx* h, const double* x, double* y) {
+    Ctx* c = h->tet;
+    const unsigned gf = (unsigned)std::min<int64_t>(65535, (c->F + 7) / 8);
+    k_tet_bj_apply<<<gf, 256, 0, h->stream>>>(c->d_bj, c->d_hoff, c->d_bjoff, c->F, x, y);
     TET_CK(cudaGetLastError());
     return HDG_OK;
 }

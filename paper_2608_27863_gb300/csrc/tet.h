@@ -52,6 +52,7 @@ struct TetElem {
     int64_t roff;      // recovery data: G [3][Np][Np], H [3][Np][sum nfp], dq0 [3][m][Np]
     int64_t goff;      // curved: volume records [Nq][10] (w |J|, J^{-1} row-major [r][k])
     int64_t gfoff;     // curved: face records [sfq][3] (w_s |J| J^{-T} nu)
+    int64_t koff;      // element trace residual R_uhat^K [t] (residual evaluation)
     int32_t vtab, ftab[4], ttab[4], pad;   // table offsets: volume, face (p, pF, code), trace (pF)
     double detJ, Jinv[9];                  // affine elements
 };
@@ -63,6 +64,9 @@ struct Ctx {
     std::vector<int64_t> uoff, hoff, boff;
     std::vector<int32_t> rowptr, col;
     std::vector<int32_t> cptr, centry;     // contributions of each block: (e, fl, gl) ascending e
+    std::vector<int32_t> diagb;            // [F] index of the diagonal block of each block row
+    std::vector<int64_t> bjoff;            // [F+1] offsets of the diagonal-block inverses (bs_F^2 each)
+    int64_t n_rk = 0;                      // sum of element trace sizes
     std::vector<TetElem> el;
     std::vector<int32_t> order;            // elements by decreasing cost
     std::vector<double> tab;               // all tables
@@ -88,6 +92,12 @@ struct Ctx {
     double* d_vals = nullptr;              // assembled blocks
     double* d_g = nullptr;                 // [n_trace]
     double* d_work = nullptr;              // per-CTA workspace
+    int32_t* d_diagb = nullptr;
+    int64_t* d_bjoff = nullptr;
+    double* d_bj = nullptr;                // block-Jacobi inverses (allocated on first set-up)
+    double* d_rk = nullptr;                // element trace residuals (allocated on first residual)
+    double* d_part = nullptr;              // [E + F] partial sums of squares
+    bool bj_ready = false;
     int32_t* d_next = nullptr;             // work counter of the persistent launch
     int n_slots = 0;
     int64_t work_stride = 0;
@@ -104,6 +114,12 @@ int linearize(hdg_ctx* h, const double* U, const double* Q, const double* UH, co
               double a_ii);
 int matvec(hdg_ctx* h, const double* x, double* y);
 int recover(hdg_ctx* h, const double* dUH, double* dQ, double* dU);
+// FP64 stage residual: optional outputs Rq [3 n_u], Ru [n_u], Ruh [n_trace]; the norms
+// ||F||, ||(R_q, R_u)||, ||R_uhat|| go to norms (device, 3 doubles)
+int residual(hdg_ctx* h, const double* U, const double* Q, const double* UH, const double* Ustar, double dt,
+             double a_ii, double* Rq, double* Ru, double* Ruh, double* norms);
+int bj_setup(hdg_ctx* h);
+int bj_apply(hdg_ctx* h, const double* x, double* y);
 
 }  // namespace tet
 }  // namespace hdg

@@ -439,6 +439,14 @@ int create_host(hdg_ctx* h, const hdg_tet_mesh* mesh, std::string& err) {
             c->cptr[b + 1] = (int32_t)(c->centry.size() / 3);
         }
     c->n_vals = c->boff[c->nnzb];
+    c->diagb.assign(F, -1);
+    c->bjoff.assign(F + 1, 0);
+    for (int64_t Fi = 0; Fi < F; ++Fi) {
+        for (int32_t b = c->rowptr[Fi]; b < c->rowptr[Fi + 1]; ++b)
+            if (c->col[b] == (int32_t)Fi) c->diagb[Fi] = b;
+        const int64_t bs = c->hoff[Fi + 1] - c->hoff[Fi];
+        c->bjoff[Fi + 1] = c->bjoff[Fi] + bs * bs;
+    }
     // reference tables
     c->vtab.assign(PMAX + 1, -1);
     c->ttab.assign(PMAX + 1, -1);
@@ -471,7 +479,7 @@ int create_host(hdg_ctx* h, const hdg_tet_mesh* mesh, std::string& err) {
             }
     // per-element geometry and layout
     c->el.resize(E);
-    int64_t moff = 0, roff = 0;
+    int64_t moff = 0, roff = 0, koff = 0;
     for (int64_t e = 0; e < E; ++e) {
         TetElem& d = c->el[e];
         std::memset(&d, 0, sizeof(d));
@@ -507,6 +515,8 @@ int create_host(hdg_ctx* h, const hdg_tet_mesh* mesh, std::string& err) {
         moff += (int64_t)(d.NU + t) * d.LD;
         d.roff = roff;
         roff += 3LL * d.Np * d.Np + 3LL * d.Np * sfp + 3LL * M * d.Np;
+        d.koff = koff;
+        koff += t;
         // geometry: quadratic nodes (given, or the straight-sided midpoints)
         double X[10][3];
         for (int v = 0; v < 4; ++v)
@@ -579,6 +589,7 @@ int create_host(hdg_ctx* h, const hdg_tet_mesh* mesh, std::string& err) {
     }
     c->n_mat = moff;
     c->n_rec = roff;
+    c->n_rk = koff;
     // persistent launch order: decreasing estimated FP64 work, ties by element id
     std::vector<double> cost(E);
     for (int64_t e = 0; e < E; ++e) {

@@ -128,3 +128,73 @@ def test_tet_freestream_gives_zero_rhs(H):
         assert g.abs().max().item() < 1e-12
     finally:
         H.hdg_destroy(h)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_tet_residual_parity(H, k):
+    """FP64 stage residual (R_q, R_u, assembled R_uhat) against the oracle."""
+    mesh = mesh_case(k)
+    prob, pb, h, dev = setup(H, mesh, twall=0.8 if k == 2 else None)
+    try:
+        s = H.hdg_tet_query(h)
+        Rq = torch.zeros(3 * s["n_u"], dtype=torch.float64, device="cuda")
+        Ru = torch.zeros(s["n_u"], dtype=torch.float64, device="cuda")
+        Rh = torch.zeros(s["n_trace"], dtype=torch.float64, device="cuda")
+        nrm = H.hdg_residual(h, dev["U"], dev["Q"], dev["UH"], dev["Ustar"], None, prob.dt, prob.a_ii, Rq, Ru, Rh)
+        oq, ou, oh = pb.global_residual(pb.Q, pb.U, pb.UH)
+        # each residual is a difference of quadrature sums of the size of the state (R_q: (q, phi)
+        # + (u, grad phi) - <uhat, phi n>, O(|U|) terms that nearly cancel for a smooth state), so
+        # rounding is relative to |U| and |UH| rather than to the residual itself
+        scale = np.linalg.norm(pb.U) + np.linalg.norm(pb.UH)
+        for got, ref in ((Rq, oq), (Ru, ou), (Rh, oh)):
+            assert np.linalg.norm(got.cpu().numpy() - ref) < 1e-12 * max(np.linalg.norm(ref), 1e-2 * scale)
+        ref_norm = np.sqrt(oq @ oq + ou @ ou + oh @ oh)
+        assert abs(nrm[0] - ref_norm) < 1e-12 * ref_norm
+    finally:
+        H.hdg_destroy(h)
+
+
+def test_tet_newton_iterates_match_oracle(H):
+    """Two Newton iterations (GMRES to 1e-13 with block-Jacobi) against the oracle's
+    dense Newton on the curved mixed-degree mesh; then convergence below 1e-10."""
+    mesh = mesh_case(0)
+    prob, pb, h, dev = setup(H, mesh)
+    try:
+        U, Q, UH = dev["U"].clone(), dev["Q"].clone(), dev["UH"].clone()
+        nit, git, hist = H.hdg_newton(h, U, Q, UH, dev["Ustar"], None, prob.dt, prob.a_ii, tol=1e-30,
+                                      max_newton=2, restart=60, max_gmres=600, gmres_rtol=1e-13,
+                                      raise_on_noconv=False)
+        oQ, oU, oUH, ohist = ot.newton(pb, pb.Q, pb.U, pb.UH, fixed=2)
+        assert np.linalg.norm(U.cpu().numpy() - oU) < 1e-10 * np.linalg.norm(oU)
+        assert np.linalg.norm(UH.cpu().numpy() - oUH) < 1e-10 * np.linalg.norm(oUH)
+        assert np.linalg.norm(Q.cpu().numpy() - oQ) < 1e-9 * np.linalg.norm(oQ)
+        assert abs(hist[0] - ohist[0]) < 1e-12 * ohist[0]
+        nit, git, hist = H.hdg_newton(h, U, Q, UH, dev["Ustar"], None, prob.dt, prob.a_ii, tol=1e-10,
+                                      max_newton=6, restart=60, max_gmres=600, gmres_rtol=1e-12)
+        assert hist[-1] <= 1e-10
+    finally:
+        H.hdg_destroy(h)
+
+
+def test_tet_dirk_step_graph_matches_oracle(H):
+    """One SDIRK3 step, 3 stages x 3 Newton iterations captured as one CUDA graph,
+    against the oracle's DIRK step with the same fixed iteration counts."""
+    mesh = mesh_case(0)
+    prob, pb, h, dev = setup(H, mesh)
+    try:
+        A, b = H.sdirk3_tableau()
+        U, Q, UH = dev["U"].clone(), dev["Q"].clone(), dev["UH"].clone()
+        hist = H.hdg_dirk_step(h, U, Q, UH, None, prob.dt, A, b, n_newton=3, m=80, use_graph=True)
+        prob2 = prob
+        prob2.Ustar = prob.U.copy()
+        oQ, oU, oUH, ohist = ot.dirk_step(prob2, A, b, fixed=3)
+        assert np.linalg.norm(U.cpu().numpy() - oU) < 1e-9 * np.linalg.norm(oU)
+        assert np.linalg.norm(UH.cpu().numpy() - oUH) < 1e-9 * np.linalg.norm(oUH)
+        for i in range(3):
+            assert hist[i, -1] < 1e-8, hist
+        # replaying the graph from the new state advances another step
+        U0 = U.clone()
+        H.hdg_dirk_step(h, U, Q, UH, None, prob.dt, A, b, n_newton=3, m=80, use_graph=True)
+        assert torch.linalg.norm(U - U0).item() > 0
+    finally:
+        H.hdg_destroy(h)

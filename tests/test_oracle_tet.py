@@ -297,3 +297,15 @@ def test_uniform_degree_affine_elements_share_reference_blocks():
     s0, s1 = pb.condense(e0)["S"], pb.condense(e1)["S"]
     # same canonical frames up to the cell shift: compare in the elements' own face order
     assert np.allclose(s0, s1, atol=1e-12 * np.abs(s0).max())
+
+
+def test_tet_newton_converges_quadratically():
+    """The oracle's Newton on a curved mixed-degree mesh: quadratic decrease of ||F||."""
+    mesh = small_mesh(n=(2, 1, 1))
+    prob, pb = make_problem(mesh)
+    prob.Ustar = prob.U + 1e-3 * np.cos(np.arange(prob.U.size))
+    pb = ot.TetProblem(prob)
+    _, _, _, hist = ot.newton(pb, pb.Q, pb.U, pb.UH, tol=1e-12, maxit=6)
+    assert hist[-1] < 1e-11
+    rates = [np.log(hist[k + 1]) / np.log(hist[k]) for k in range(1, len(hist) - 1) if hist[k] < 1e-2]
+    assert rates and min(rates) > 1.6

@@ -86,7 +86,8 @@ def test_tet_argument_errors(H):
     assert ex.value.code == H.HDG_EINVAL
     h = H.hdg_create_tet(*args, mesh.elem_p, mesh.geo, 1.4, 1e5, 0.72, 0.5, host_only=True)
     try:                                                   # hex-only entry points refuse tetrahedral handles
-        assert H.lib().hdg_residual(h, *([None] * 5), 1.0, 1.0, None, None, None, None) == H.HDG_EUNSUPPORTED
+        assert H.lib().hdg_lift_gradient(h, None, None, None) == H.HDG_EUNSUPPORTED
         assert H.lib().hdg_reserve(h, 0) == H.HDG_EUNSUPPORTED
+        assert H.lib().hdg_set_preconditioner(h, H.HDG_PC_SCHWARZ) == H.HDG_EUNSUPPORTED
     finally:
         H.hdg_destroy(h)
