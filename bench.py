@@ -54,6 +54,7 @@ WORKLOADS = {
     # curved anisotropic tetrahedra, degrees 1..4 per element (seeded), 6 Kuhn tets per cell
     "tet-p1to4-30x20x28-curved": dict(kind="tet", kw={}),
     "tet-p1to4-10x20x6-curved": dict(kind="tet", kw={"nx": 10, "nz": 6}),
+    "tet-p1to4-10x20x3-curved": dict(kind="tet", kw={"nx": 10, "nz": 3}),
 }
 DEFAULT_WORKLOAD = "hex-p2-16^3-tgv"
 
@@ -144,28 +145,35 @@ def run_tet(args, rank, world, local_rank):
         H.hdg_trace_matvec(h, x, y)
         H.hdg_recover_interior(h, y, dQ, dU)
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    if H.hdg_status(h) != 0:
-        raise RuntimeError("device status: " + H.hdg_last_error(h))
-    H.hdg_profile_read(h)
-    H.hdg_profile(h, True)
-    times = []
-    with ClockSampler(local_rank) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1.0)
-            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            s.record(stream)
+    def timed():
+        for _ in range(args.warmup):
             step()
-            e.record(stream)
-            e.synchronize()
-            times.append(s.elapsed_time(e))
-    torch.cuda.synchronize()
-    prof = H.hdg_profile_read(h)
-    H.hdg_profile(h, False)
-    clocks = clk.summary()
-    t_ms = max_over_ranks(sum(times), world, dev)
+        torch.cuda.synchronize()
+        if H.hdg_status(h) != 0:
+            raise RuntimeError("device status: " + H.hdg_last_error(h))
+        H.hdg_profile_read(h)
+        H.hdg_profile(h, True)
+        times = []
+        with ClockSampler(local_rank) as clk:
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s.record(stream)
+                step()
+                e.record(stream)
+                e.synchronize()
+                times.append(s.elapsed_time(e))
+        torch.cuda.synchronize()
+        prof = H.hdg_profile_read(h)
+        H.hdg_profile(h, False)
+        return max_over_ranks(sum(times), world, dev), prof, clk.summary()
+
+    H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_FP64)
+    t_ms, prof, clocks = timed()
+    if not args.no_mixed:
+        H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_MIXED)
+        tm_ms, prof_m, clocks_m = timed()
+        H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_FP64)
     # end to end from pinned host memory
     hU, hQ, hUH, hUs = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (P.U, P.Q, P.UH, P.Ustar))
     hdQ = torch.empty(dQ.shape, dtype=torch.float64).pin_memory()
@@ -205,6 +213,33 @@ def run_tet(args, rank, world, local_rank):
     smmax = clocks.get("sm_max_mhz") or 2070.0
     peak = fp64_peak_derived(smmax)
     counts = np.bincount(m.elem_p, minlength=5)[1:]
+    mixed = None if args.no_mixed else {"value": replica_throughput(world, E, args.steps, tm_ms), "unit": "elements/s",
+             "ms_per_step": tm_ms / args.steps, "speedup_vs_fp64_step": t_ms / tm_ms,
+             "kernels": {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
+                         for k, v in prof_m.items() if v[1]},
+             "dtype": "fp64 pointwise terms, lifting operators, elimination and residual; fp32 Jacobian "
+                      "coefficients, column variations and contraction",
+             "clocks": clocks_m}
+    if not args.no_newton and mixed is not None:
+        newton = {}
+        for name, prec in (("fp64", H.HDG_PREC_FP64), ("mixed", H.HDG_PREC_MIXED)):
+            H.hdg_set_params(h, tau=P.tau, precision=prec)
+            U2, Q2, UH2 = U.clone(), Q.clone(), UH.clone()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            nit, git, hist = H.hdg_newton(h, U2, Q2, UH2, Us, None, P.dt, P.a_ii, tol=1e-8, max_newton=10,
+                                          restart=40, max_gmres=400, gmres_rtol=1e-9, raise_on_noconv=False)
+            torch.cuda.synchronize()
+            newton[name] = {"seconds": time.perf_counter() - t0, "newton_iters": nit, "gmres_iters": git,
+                            "residual_history": [float(v) for v in hist]}
+            newton[name + "_U"] = U2
+        newton["state_rel_diff_U"] = float(torch.linalg.norm(newton["mixed_U"] - newton["fp64_U"]) /
+                                           torch.linalg.norm(newton["fp64_U"]))
+        del newton["mixed_U"], newton["fp64_U"]
+        newton["tol"] = 1e-8
+        newton["speedup"] = newton["fp64"]["seconds"] / newton["mixed"]["seconds"]
+        mixed["newton"] = newton
+        H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_FP64)
     out = {
         "metric": METRIC, "value": replica_throughput(world, E, args.steps, t_ms), "unit": "elements/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_ms / args.steps,
@@ -222,6 +257,7 @@ def run_tet(args, rank, world, local_rank):
                      "flops_per_element": float(fl["total"].mean()),
                      "flops_split": {k: float(v.sum()) for k, v in fl.items()}},
         "kernels": kern,
+        "mixed": mixed,
         "e2e": {"value": replica_throughput(world, E, args.steps, e2e_ms), "unit": "elements/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": sum(v[1] for v in prof.values()) / args.steps,
@@ -760,6 +796,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-newton", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="tetrahedral workloads: time the FP64 form only")
     ap.add_argument("--mixed-prec", choices=["fp32", "tf32", "3xtf32"], default="3xtf32")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--elim-nb", type=int, choices=[8, 16], default=None,

@@ -302,8 +302,6 @@ int hdg_set_params(hdg_handle h, const hdg_params* prm) {
         return fail(h, HDG_EINVAL, "Sutherland constants must be positive");
     if (prm->precision < HDG_PREC_FP64 || prm->precision > HDG_PREC_MIXED_3XTF32)
         return fail(h, HDG_EUNSUPPORTED, "precision mode not available");
-    if (h->tet && prm->precision != HDG_PREC_FP64)
-        return fail(h, HDG_EUNSUPPORTED, "tetrahedral handles compute in FP64");
     h->phys.tau = prm->tau;
     h->phys.visc_law = prm->visc_law;
     h->phys.c1 = prm->suth_c1;

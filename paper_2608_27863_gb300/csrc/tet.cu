@@ -45,7 +45,8 @@ constexpr int64_t W_RB = W_RF + 4 * NFQMAX * M;          // [4 NFQMAX][a]
 constexpr int64_t W_MM = W_RB + 4 * NFQMAX * M;          // [NPMAX][NPMAX] mass matrix, then its Cholesky factor
 constexpr int64_t W_DP = W_MM + NPMAX * NPMAX;           // [NQMAX][3][NPMAX] physical gradients
 constexpr int64_t W_VQ = W_DP + NQMAX * 3 * NPMAX;       // [3][NPT][NCM] psi | chi
-constexpr int64_t W_END = W_VQ + 3LL * NPT * NCM;
+constexpr int64_t W_GHF = W_VQ + 3LL * NPT * NCM;       // mixed form: FP32 copies of G | H
+constexpr int64_t W_END = W_GHF + (3LL * NPMAX * NCM + 1) / 2;
 
 // shared memory layout (doubles)
 constexpr int S_U = 0;                                   // [m][Np]
@@ -60,7 +61,7 @@ constexpr int S_TOTAL = S_DYN + (S_GEMM > S_ELIM ? S_GEMM : S_ELIM);
 
 struct KArgs {
     const TetElem* el; const int32_t* order; int64_t E; int32_t* next;
-    const double* tab; const double* gvol; const double* gface;
+    const double* tab; const float* tabf; const double* gvol; const double* gface;
     const double* U; const double* Q; const double* UH; const double* Ustar;
     double* mat; double* rec; double* work; int64_t wstride;
     PhysT<double> ph; double dt, a_ii, tau; const double* ub; double ew;
@@ -75,11 +76,20 @@ __device__ __forceinline__ int face_of_point(const TetElem& d, int r) {
 }
 
 // element basis row at point x (volume points first, then the face points)
-__device__ __forceinline__ const double* basis_row(const KArgs& A, const TetElem& d, int x) {
-    if (x < d.Nq) return A.tab + d.vtab + (size_t)x * d.Np;
+template <class T>
+__device__ __forceinline__ const T* basis_row_t(const T* tab, const TetElem& d, int x) {
+    if (x < d.Nq) return tab + d.vtab + (size_t)x * d.Np;
     const int r = x - d.Nq, f = face_of_point(d, r);
-    return A.tab + d.ftab[f] + (size_t)(r - d.soff[f]) * d.Np;
+    return tab + d.ftab[f] + (size_t)(r - d.soff[f]) * d.Np;
 }
+__device__ __forceinline__ const double* basis_row(const KArgs& A, const TetElem& d, int x) {
+    return basis_row_t(A.tab, d, x);
+}
+
+// tables in the contraction type: FP64, or their FP32 copy in the mixed form
+template <class T> __device__ __forceinline__ const T* jtab(const KArgs& A);
+template <> __device__ __forceinline__ const double* jtab<double>(const KArgs& A) { return A.tab; }
+template <> __device__ __forceinline__ const float* jtab<float>(const KArgs& A) { return A.tabf; }
 
 // runtime-sized tile of the trailing update A22 -= L21 U12 (rows rb + ty + 16 ii,
 // columns ct + tx + 16 jj)
@@ -250,9 +260,10 @@ __device__ __forceinline__ int bcol(const TetElem& d, int b, int c) {
 }
 
 // one out[i][c] += sum_k R[k][i] T[k][c] pass over a staged chunk; 4 x 4 register tiles
-__device__ __forceinline__ void gemm_chunk(const double* sR, const double* sT, int kc, int ti, int tc, double acc[4][4]) {
+template <class T>
+__device__ __forceinline__ void gemm_chunk(const T* sR, const T* sT, int kc, int ti, int tc, T acc[4][4]) {
     for (int k = 0; k < kc; ++k) {
-        double rv[4], tv[4];
+        T rv[4], tv[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) { rv[u] = sR[k * SRP + 4 * ti + u]; tv[u] = sT[k * STP + 4 * tc + u]; }
 #pragma unroll
@@ -304,6 +315,10 @@ __device__ void load_geometry(const KArgs& A, const TetElem& d, double* gv, doub
     }
 }
 
+// TJ: type of the Jacobian coefficients, the column variations and the
+// contraction (double: FP64 form; float: mixed form).  Pointwise terms, lifting
+// operators, mass term, right-hand side and the elimination are FP64 in both.
+template <class TJ>
 __device__ void process_element(const KArgs& A, const TetElem& d, double* W, double* sm, int* sflag) {
     const int tid = threadIdx.x;
     const int Np = d.Np, Nq = d.Nq, NU = d.NU, t = d.t, LD = d.LD, sfq = d.sfq;
@@ -448,16 +463,29 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
             }
         }
     }
-    double* vq = W + W_VQ;
+    const TJ* tabJ = jtab<TJ>(A);
+    const TJ* GJ;
+    const TJ* HJ;
+    if constexpr (sizeof(TJ) == sizeof(double)) {
+        GJ = reinterpret_cast<const TJ*>(Gk);
+        HJ = reinterpret_cast<const TJ*>(Hk);
+    } else {
+        TJ* gh = reinterpret_cast<TJ*>(W + W_GHF);
+        for (int i = tid; i < 3 * Np * (Np + sfp); i += NTH) gh[i] = (TJ)Gk[i];   // G and H are contiguous
+        GJ = gh;
+        HJ = gh + 3 * Np * Np;
+        __syncthreads();
+    }
+    TJ* vq = reinterpret_cast<TJ*>(W + W_VQ);
     for (int idx = tid; idx < 3 * npt * Nc; idx += NTH) {
         const int k = idx / (npt * Nc), rem = idx - k * npt * Nc, x = rem / Nc, c = rem - x * Nc;
-        const double* br = basis_row(A, d, x);
-        double s = 0.0;
+        const TJ* br = basis_row_t(tabJ, d, x);
+        TJ s = 0;
         if (c < Np) {
-            const double* G = Gk + (size_t)k * Np * Np + c;
+            const TJ* G = GJ + (size_t)k * Np * Np + c;
             for (int j = 0; j < Np; ++j) s += br[j] * G[j * Np];
         } else {
-            const double* H = Hk + (size_t)k * Np * sfp + (c - Np);
+            const TJ* H = HJ + (size_t)k * Np * sfp + (c - Np);
             for (int j = 0; j < Np; ++j) s += br[j] * H[j * sfp];
         }
         vq[((size_t)k * NPT + x) * NCM + c] = s;
@@ -465,9 +493,9 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
     __syncthreads();
     // A1: fluxes and their Jacobians at the points
     const PhysT<double>& P = A.ph;
-    double* cv = W + W_CV;
-    double* cf = W + W_CF;
-    double* cb = W + W_CB;
+    TJ* cv = reinterpret_cast<TJ*>(W + W_CV);
+    TJ* cf = reinterpret_cast<TJ*>(W + W_CF);
+    TJ* cb = reinterpret_cast<TJ*>(W + W_CB);
     double* rv = W + W_RV;
     double* rf = W + W_RF;
     double* rb = W + W_RB;
@@ -490,7 +518,7 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
                     for (int k = 0; k < 3; ++k) s += Ji[r * 3 + k] * (Fc[a][k] - Fv[a][k]);
                     rv[(x * M + a) * 3 + r] = wJ * s;
                 }
-            double* o = cv + (size_t)x * 300;
+            TJ* o = cv + (size_t)x * 300;
             for (int b = 0; b < M; ++b) {
                 Dir ud[M];
                 for (int a = 0; a < M; ++a) ud[a] = {u[a], a == b ? 1.0 : 0.0};
@@ -501,7 +529,7 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
                     for (int r = 0; r < 3; ++r) {
                         double s = 0.0;
                         for (int k = 0; k < 3; ++k) s += Ji[r * 3 + k] * (Fcd[a][k].t - Fvd[a][k].t);
-                        o[((a * 3 + r) * M + b) * 4 + 0] = wJ * s;
+                        o[((a * 3 + r) * M + b) * 4 + 0] = (TJ)(wJ * s);
                     }
                 for (int l = 0; l < 3; ++l) {
                     double qe[M][3];
@@ -512,7 +540,7 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
                         for (int r = 0; r < 3; ++r) {
                             double s = 0.0;
                             for (int k = 0; k < 3; ++k) s += Ji[r * 3 + k] * Fq[a][k];
-                            o[((a * 3 + r) * M + b) * 4 + 1 + l] = -wJ * s;
+                            o[((a * 3 + r) * M + b) * 4 + 1 + l] = (TJ)(-wJ * s);
                         }
                 }
             }
@@ -534,13 +562,13 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
                 const double ub_a = tag == 1 ? A.ub[a] : 0.0;
                 rb[r * M + a] = boundary_form<M>(tag, a, fh, nrm, u, uh, ub_a, A.ew);
             }
-            double* of = cf + (size_t)r * 125;
-            double* ob = cb + (size_t)r * 125;
+            TJ* of = cf + (size_t)r * 125;
+            TJ* ob = cb + (size_t)r * 125;
             // element rows take dt * dfhat; trace rows dfhat on flux rows, the algebraic forms
             // otherwise (tag 1 uhat - u_b, tag 2 uhat - u, tags 3 / 4 uhat_v, and on isothermal
             // walls uhat_rhoE - uhat_rho e_w)
             auto put = [&](int a, int b, int kind, double v) {
-                of[(a * M + b) * 5 + kind] = A.dt * v;
+                of[(a * M + b) * 5 + kind] = (TJ)(A.dt * v);
                 double w = v;
                 if (!boundary_row_is_flux<M>(tag, a)) {
                     w = 0.0;
@@ -548,7 +576,7 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
                     if (tag == 2 && kind == 0 && a == b) w = -nrm;
                     if (tag == 3 && a == M - 1 && kind == 1 && b == 0) w = -nrm * A.ew;
                 }
-                ob[(a * M + b) * 5 + kind] = w;
+                ob[(a * M + b) * 5 + kind] = (TJ)w;
             };
             for (int b = 0; b < M; ++b) {
                 Dir ud[M];
@@ -578,44 +606,46 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
     }
     __syncthreads();
     // A2: contraction into the bordered matrix, one (a, b) component pair at a time
-    double* sR = sD;                     // [KC][SRP] row basis
-    double* sT = sD + KC * SRP;          // [KC][STP] column variations times coefficients
+    TJ* sR = reinterpret_cast<TJ*>(sD);  // [KC][SRP] row basis
+    TJ* sT = sR + KC * SRP;              // [KC][STP] column variations times coefficients
+    const TJ* dphiJ = tabJ + d.vtab + (size_t)Nq * Np;
+    const TJ* phiJ = tabJ + d.vtab;
     const int nrt = (Np + 3) / 4, nct = (Nc + 3) / 4;
     const int ti = tid / nct, tc = tid - ti * nct;
     const bool act = tid < nrt * nct;
     const int K1 = 3 * Nq + sfq;         // element rows: volume (g, r) then face points
     for (int ab = 0; ab < M * M; ++ab) {
         const int a = ab / M, b = ab - a * M;
-        double acc[4][4] = {};
+        TJ acc[4][4] = {};
         for (int k0 = 0; k0 < K1; k0 += KC) {
             const int kc = min(KC, K1 - k0);
             for (int idx = tid; idx < kc * SRP; idx += NTH) {
                 const int kk = idx / SRP, i = idx - kk * SRP, K = k0 + kk;
-                double v = 0.0;
+                TJ v = 0;
                 if (i < Np) {
-                    if (K < 3 * Nq) v = dphi[((size_t)(K % 3) * Nq + K / 3) * Np + i];
-                    else v = basis_row(A, d, Nq + K - 3 * Nq)[i];
+                    if (K < 3 * Nq) v = dphiJ[((size_t)(K % 3) * Nq + K / 3) * Np + i];
+                    else v = basis_row_t(tabJ, d, Nq + K - 3 * Nq)[i];
                 }
                 sR[idx] = v;
             }
             for (int idx = tid; idx < kc * STP; idx += NTH) {
                 const int kk = idx / STP, c = idx - kk * STP, K = k0 + kk;
-                double v = 0.0;
+                TJ v = 0;
                 if (c < Nc) {
                     if (K < 3 * Nq) {
                         const int g = K / 3, r = K - 3 * g;
-                        const double* o = cv + (size_t)g * 300 + ((a * 3 + r) * M + b) * 4;
-                        if (c < Np) v = o[0] * phi[(size_t)g * Np + c];
+                        const TJ* o = cv + (size_t)g * 300 + ((a * 3 + r) * M + b) * 4;
+                        if (c < Np) v = o[0] * phiJ[(size_t)g * Np + c];
                         for (int l = 0; l < 3; ++l) v -= o[1 + l] * vq[((size_t)l * NPT + g) * NCM + c];
                     } else {
                         const int rr = K - 3 * Nq, x = Nq + rr;
-                        const double* o = cf + (size_t)rr * 125 + (a * M + b) * 5;
+                        const TJ* o = cf + (size_t)rr * 125 + (a * M + b) * 5;
                         if (c < Np) {
-                            v = o[0] * basis_row(A, d, x)[c];
+                            v = o[0] * basis_row_t(tabJ, d, x)[c];
                         } else {
                             const int f = face_of_point(d, rr);
                             const int l = c - Np - fpo[f];
-                            if (l >= 0 && l < d.nfp[f]) v = o[1] * A.tab[d.ttab[f] + (size_t)(rr - d.soff[f]) * d.nfp[f] + l];
+                            if (l >= 0 && l < d.nfp[f]) v = o[1] * tabJ[d.ttab[f] + (size_t)(rr - d.soff[f]) * d.nfp[f] + l];
                         }
                         for (int l = 0; l < 3; ++l) v -= o[2 + l] * vq[((size_t)l * NPT + x) * NCM + c];
                     }
@@ -633,24 +663,24 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
                 for (int v = 0; v < 4; ++v) {
                     const int c = 4 * tc + v;
                     if (c >= Nc) continue;
-                    Mx[(size_t)(a * Np + i) * LD + bcol(d, b, c)] = acc[u][v];   // mass term added below
+                    Mx[(size_t)(a * Np + i) * LD + bcol(d, b, c)] = (double)acc[u][v];   // mass term added below
                 }
             }
         // trace rows (f', a, l'): K = the points of face f'
         for (int f2 = 0; f2 < 4; ++f2) {
             const int nfq = d.nfq[f2], nfp = d.nfp[f2];
-            const double* mu = A.tab + d.ttab[f2];
+            const TJ* mu = tabJ + d.ttab[f2];
             for (int idx = tid; idx < nfq * SRP; idx += NTH) {
                 const int kk = idx / SRP, l = idx - kk * SRP;
-                sR[idx] = l < nfp ? mu[(size_t)kk * nfp + l] : 0.0;
+                sR[idx] = l < nfp ? mu[(size_t)kk * nfp + l] : TJ(0);
             }
             for (int idx = tid; idx < nfq * STP; idx += NTH) {
                 const int kk = idx / STP, c = idx - kk * STP, rr = d.soff[f2] + kk, x = Nq + rr;
-                double v = 0.0;
+                TJ v = 0;
                 if (c < Nc) {
-                    const double* o = cb + (size_t)rr * 125 + (a * M + b) * 5;
+                    const TJ* o = cb + (size_t)rr * 125 + (a * M + b) * 5;
                     if (c < Np) {
-                        v = o[0] * basis_row(A, d, x)[c];
+                        v = o[0] * basis_row_t(tabJ, d, x)[c];
                     } else {
                         const int l = c - Np - fpo[f2];
                         if (l >= 0 && l < nfp) v = o[1] * mu[(size_t)kk * nfp + l];
@@ -663,7 +693,7 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
             const int nrt2 = (nfp + 3) / 4;
             const int ti2 = tid / nct, tc2 = tid - ti2 * nct;
             if (tid < nrt2 * nct) {
-                double acc2[4][4] = {};
+                TJ acc2[4][4] = {};
                 gemm_chunk(sR, sT, nfq, ti2, tc2, acc2);
                 for (int u = 0; u < 4; ++u) {
                     const int l = 4 * ti2 + u;
@@ -671,7 +701,7 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
                     for (int v = 0; v < 4; ++v) {
                         const int c = 4 * tc2 + v;
                         if (c >= Nc) continue;
-                        Mx[(size_t)(NU + d.toff[f2] + a * nfp + l) * LD + bcol(d, b, c)] = acc2[u][v];
+                        Mx[(size_t)(NU + d.toff[f2] + a * nfp + l) * LD + bcol(d, b, c)] = (double)acc2[u][v];
                     }
                 }
             }
@@ -718,6 +748,7 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
     bordered_elim(Mx, NU, NR, NR + 1, LD, sD, sD + NRMAX * NB, piv, sflag);
 }
 
+template <class TJ>
 __global__ void __launch_bounds__(NTH, 2) k_tet_linearize(KArgs A) {
     extern __shared__ double sm[];
     __shared__ TetElem d;
@@ -735,7 +766,7 @@ __global__ void __launch_bounds__(NTH, 2) k_tet_linearize(KArgs A) {
         for (int i = tid; i < NW; i += NTH)
             reinterpret_cast<int64_t*>(&d)[i] = reinterpret_cast<const int64_t*>(A.el + e)[i];
         __syncthreads();
-        process_element(A, d, W, sm, &sflag);
+        process_element<TJ>(A, d, W, sm, &sflag);
         __syncthreads();
     }
     if (tid == 0 && sflag) atomicOr(A.status, sflag);
@@ -1158,6 +1189,7 @@ int create_device(hdg_ctx* h, std::string& err) {
     int rc;
 #define UP(dst, src) if ((rc = tet_upload(h, &(dst), (src), err))) return rc
     UP(c->d_el, c->el); UP(c->d_order, c->order); UP(c->d_tab, c->tab);
+    UP(c->d_tabf, std::vector<float>(c->tab.begin(), c->tab.end()));
     UP(c->d_gvol, c->gvol); UP(c->d_gface, c->gface); UP(c->d_hoff, c->hoff); UP(c->d_boff, c->boff);
     UP(c->d_rowptr, c->rowptr); UP(c->d_col, c->col); UP(c->d_cptr, c->cptr); UP(c->d_centry, c->centry);
     UP(c->d_f2e, c->f2e); UP(c->d_f2lf, c->f2lf); UP(c->d_diagb, c->diagb); UP(c->d_bjoff, c->bjoff);
@@ -1181,7 +1213,9 @@ int create_device(hdg_ctx* h, std::string& err) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(k_tet_linearize, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_tet_linearize<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(S_TOTAL * sizeof(double))) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tet_linearize<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(S_TOTAL * sizeof(double))) != cudaSuccess) {
         err = "shared-memory opt-in of the tetrahedral kernel failed";
         return HDG_ECUDA;
@@ -1192,7 +1226,7 @@ int create_device(hdg_ctx* h, std::string& err) {
         return HDG_ECUDA;
     }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tet_linearize, NTH, S_TOTAL * sizeof(double));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tet_linearize<double>, NTH, S_TOTAL * sizeof(double));
     c->n_slots = std::max(1, nsm * std::max(1, per_sm));
     c->work_stride = W_END;
     if ((rc = tet_alloc(h, &c->d_work, (size_t)c->n_slots * W_END, err))) return rc;
@@ -1215,7 +1249,7 @@ int linearize(hdg_ctx* h, const double* U, const double* Q, const double* UH, co
     Ctx* c = h->tet;
     KArgs A;
     A.el = c->d_el; A.order = c->d_order; A.E = c->E; A.next = c->d_next;
-    A.tab = c->d_tab; A.gvol = c->d_gvol; A.gface = c->d_gface;
+    A.tab = c->d_tab; A.tabf = c->d_tabf; A.gvol = c->d_gvol; A.gface = c->d_gface;
     A.U = U; A.Q = Q; A.UH = UH; A.Ustar = Ustar;
     A.mat = c->d_mat; A.rec = c->d_rec; A.work = c->d_work; A.wstride = c->work_stride;
     A.ph = phys_t<double>(h->phys); A.dt = dt; A.a_ii = a_ii; A.tau = h->phys.tau;
@@ -1223,7 +1257,10 @@ int linearize(hdg_ctx* h, const double* U, const double* Q, const double* UH, co
     cudaStream_t st = h->stream;
     TET_CK(cudaMemsetAsync(c->d_next, 0, sizeof(int32_t), st));
     prof_begin(h, HDG_K_ELIM);
-    k_tet_linearize<<<c->n_slots, NTH, S_TOTAL * sizeof(double), st>>>(A);
+    if (h->precision == HDG_PREC_FP64)
+        k_tet_linearize<double><<<c->n_slots, NTH, S_TOTAL * sizeof(double), st>>>(A);
+    else
+        k_tet_linearize<float><<<c->n_slots, NTH, S_TOTAL * sizeof(double), st>>>(A);
     prof_end(h);
     TET_CK(cudaGetLastError());
     prof_begin(h, HDG_K_ASSEMBLE);
@@ -1267,7 +1304,7 @@ KArgs base_args(hdg_ctx* h, const double* U, const double* Q, const double* UH, 
     KArgs A;
     std::memset(&A, 0, sizeof(A));
     A.el = c->d_el; A.order = c->d_order; A.E = c->E; A.next = c->d_next;
-    A.tab = c->d_tab; A.gvol = c->d_gvol; A.gface = c->d_gface;
+    A.tab = c->d_tab; A.tabf = c->d_tabf; A.gvol = c->d_gvol; A.gface = c->d_gface;
     A.U = U; A.Q = Q; A.UH = UH; A.Ustar = Ustar;
     A.mat = c->d_mat; A.rec = c->d_rec; A.work = c->d_work; A.wstride = c->work_stride;
     A.ph = phys_t<double>(h->phys); A.dt = dt; A.a_ii = a_ii; A.tau = h->phys.tau;

@@ -77,6 +77,7 @@ struct Ctx {
     TetElem* d_el = nullptr;
     int32_t* d_order = nullptr;
     double* d_tab = nullptr;
+    float* d_tabf = nullptr;               // FP32 copy of the tables (mixed-form contraction)
     double* d_gvol = nullptr;
     double* d_gface = nullptr;
     int64_t* d_hoff = nullptr;
