@@ -251,6 +251,84 @@ __device__ void bordered_elim(double* Mx, int NU, int NR, int NC, int LD, double
     }
 }
 
+
+// Trace rows of the mixed form, after the FP64 elimination of the top rows
+// (LU of At with pivoting, Z = L^{-1} P Bt, z = L^{-1} P Rt): W = Ct U^{-1} in
+// FP32 (left-looking, one column of U at a time, W kept transposed so that
+// threads over trace rows read consecutive words), S = Dt - W Z in FP32 with
+// 8 x 8 register tiles, and the right-hand side Rh - W z in FP64.
+__device__ void trace_schur_f32(double* Mx, int NU, int t, int LD, float* Wt, float* Zf, float* smf) {
+    const int tid = threadIdx.x, NR = NU + t;
+    for (int idx = tid; idx < NU * t; idx += NTH) {
+        const int i = idx / t, r = idx - i * t;
+        Wt[idx] = (float)Mx[(size_t)(NU + r) * LD + i];
+        Zf[idx] = (float)Mx[(size_t)i * LD + NU + r];
+    }
+    __syncthreads();
+    float* ucol = smf;                                  // [NU] column j of U
+    for (int j = 0; j < NU; ++j) {
+        for (int i = tid; i <= j; i += NTH) ucol[i] = (float)Mx[(size_t)i * LD + j];
+        __syncthreads();
+        const float inv = ucol[j] != 0.0f ? 1.0f / ucol[j] : 1.0f;
+        for (int r = tid; r < t; r += NTH) {
+            float s2 = Wt[(size_t)j * t + r];
+            for (int i = 0; i < j; ++i) s2 = fmaf(-Wt[(size_t)i * t + r], ucol[i], s2);
+            Wt[(size_t)j * t + r] = s2 * inv;
+        }
+        __syncthreads();
+    }
+    // right-hand side of the trace rows: Rh - W z (FP64)
+    for (int r = tid; r < t; r += NTH) {
+        double s2 = Mx[(size_t)(NU + r) * LD + NR];
+        for (int i = 0; i < NU; ++i) s2 -= (double)Wt[(size_t)i * t + r] * Mx[(size_t)i * LD + NR];
+        Mx[(size_t)(NU + r) * LD + NR] = s2;
+    }
+    // S = Dt - W Z
+    constexpr int KS = 16, TP = 304;                    // K staged per step; row stride of the staged panels
+    float* sW = smf;                                    // [KS][TP]
+    float* sZ = smf + KS * TP;                          // [KS][TP]
+    const int n8 = (t + 7) / 8, ntiles = n8 * n8;
+    for (int tile0 = 0; tile0 < ntiles; tile0 += NTH) {
+        const int tile = tile0 + tid;
+        const bool act = tile < ntiles;
+        const int tr = act ? tile / n8 : 0, tc = act ? tile - tr * n8 : 0;
+        float acc[8][8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+#pragma unroll
+            for (int v = 0; v < 8; ++v) acc[u][v] = 0.0f;
+        for (int k0 = 0; k0 < NU; k0 += KS) {
+            const int kc = min(KS, NU - k0);
+            __syncthreads();
+            for (int idx = tid; idx < kc * TP; idx += NTH) {
+                const int kk = idx / TP, c = idx - kk * TP;
+                sW[idx] = c < t ? Wt[(size_t)(k0 + kk) * t + c] : 0.0f;
+                sZ[idx] = c < t ? Zf[(size_t)(k0 + kk) * t + c] : 0.0f;
+            }
+            __syncthreads();
+            if (act)
+                for (int kk = 0; kk < kc; ++kk) {
+                    float wv[8], zv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) { wv[u] = sW[kk * TP + 8 * tr + u]; zv[u] = sZ[kk * TP + 8 * tc + u]; }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+#pragma unroll
+                        for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(wv[u], zv[v], acc[u][v]);
+                }
+        }
+        if (act)
+            for (int u = 0; u < 8; ++u) {
+                const int r = 8 * tr + u;
+                if (r >= t) continue;
+                for (int v = 0; v < 8; ++v) {
+                    const int c = 8 * tc + v;
+                    if (c < t) Mx[(size_t)(NU + r) * LD + NU + c] -= (double)acc[u][v];
+                }
+            }
+    }
+}
+
 // column index in the bordered matrix of column c (of component b) of the contraction
 __device__ __forceinline__ int bcol(const TetElem& d, int b, int c) {
     if (c < d.Np) return b * d.Np + c;
@@ -745,7 +823,15 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
     __syncthreads();
     // A3 + A4: bordered elimination
     __shared__ int piv[NB];
-    bordered_elim(Mx, NU, NR, NR + 1, LD, sD, sD + NRMAX * NB, piv, sflag);
+    if constexpr (sizeof(TJ) == sizeof(double)) {
+        bordered_elim(Mx, NU, NR, NR + 1, LD, sD, sD + NRMAX * NB, piv, sflag);
+    } else {
+        // FP64 LU of At with its right-hand sides (top rows only), then the trace rows in FP32
+        bordered_elim(Mx, NU, NU, NR + 1, LD, sD, sD + NRMAX * NB, piv, sflag);
+        __syncthreads();
+        trace_schur_f32(Mx, NU, t, LD, reinterpret_cast<float*>(W + W_VQ), reinterpret_cast<float*>(W + W_CV),
+                        reinterpret_cast<float*>(sD));
+    }
 }
 
 template <class TJ>
