@@ -910,7 +910,37 @@ __global__ void k_tet_assemble_g(const TetElem* el, const double* mat, const int
     }
 }
 
-// A6: y = S x, one warp per block row, lanes over the rows of the block row
+// y_F (+)= B x for one column-major block B [bsG][bsF] and one warp: for
+// bsF <= 16 the warp splits into ng = 32 / bsF column groups (lane = group
+// * bsF + row), so every load instruction reads ng consecutive columns; the
+// groups are combined by shuffles.  Rows beyond 32 take further passes.
+__device__ __forceinline__ double vbr_partial(const double* B, const double* xg, int bsF, int bsG, int r0, int lane) {
+    const int rows = min(32, bsF - r0);
+    const int ng = rows <= 16 ? 32 / rows : 1;
+    const int r = lane % rows, cg = lane / rows;
+    double s0 = 0.0, s1 = 0.0;
+    if (cg < ng) {
+        int c = cg;
+        for (; c + ng < bsG; c += 2 * ng) {
+            s0 = fma(B[(int64_t)c * bsF + r0 + r], xg[c], s0);
+            s1 = fma(B[(int64_t)(c + ng) * bsF + r0 + r], xg[c + ng], s1);
+        }
+        if (c < bsG) s0 = fma(B[(int64_t)c * bsF + r0 + r], xg[c], s0);
+    }
+    return s0 + s1;
+}
+
+// sum of the column groups' partials into the lanes of group 0
+__device__ __forceinline__ double vbr_reduce(double s, int rows, int lane) {
+    const int ng = rows <= 16 ? 32 / rows : 1;
+    for (int g = 1; g < ng; ++g) {
+        const double o = __shfl_sync(0xffffffffu, s, (lane + g * rows) & 31);
+        if (lane < rows && lane + g * rows < 32) s += o;
+    }
+    return s;
+}
+
+// A6: y = S x, one warp per block row
 __global__ void k_tet_matvec(const double* vals, const int64_t* hoff, const int64_t* boff, const int32_t* rowptr,
                              const int32_t* col, int64_t F, const double* x, double* y) {
     const int lane = threadIdx.x & 31;
@@ -919,17 +949,14 @@ __global__ void k_tet_matvec(const double* vals, const int64_t* hoff, const int6
     for (int64_t Fr = wid; Fr < F; Fr += nw) {
         const int bsF = (int)(hoff[Fr + 1] - hoff[Fr]);
         for (int r0 = 0; r0 < bsF; r0 += 32) {
-            const int r = r0 + lane;
             double s = 0.0;
             for (int b = rowptr[Fr]; b < rowptr[Fr + 1]; ++b) {
                 const int64_t G = col[b];
-                const int bsG = (int)(hoff[G + 1] - hoff[G]);
-                const double* vb = vals + boff[b];
-                const double* xg = x + hoff[G];
-                if (r < bsF)
-                    for (int c = 0; c < bsG; ++c) s = fma(vb[(int64_t)c * bsF + r], xg[c], s);
+                s += vbr_partial(vals + boff[b], x + hoff[G], bsF, (int)(hoff[G + 1] - hoff[G]), r0, lane);
             }
-            if (r < bsF) y[hoff[Fr] + r] = s;
+            const int rows = min(32, bsF - r0);
+            s = vbr_reduce(s, rows, lane);
+            if (lane < rows) y[hoff[Fr] + r0 + lane] = s;
         }
     }
 }
@@ -1221,12 +1248,10 @@ __global__ void k_tet_bj_apply(const double* inv, const int64_t* hoff, const int
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t Fr = wid; Fr < F; Fr += nw) {
         const int bs = (int)(hoff[Fr + 1] - hoff[Fr]);
-        const double* B = inv + bjoff[Fr];
-        const double* xf = x + hoff[Fr];
-        for (int r = lane; r < bs; r += 32) {
-            double s = 0.0;
-            for (int c = 0; c < bs; ++c) s = fma(B[(int64_t)c * bs + r], xf[c], s);
-            y[hoff[Fr] + r] = s;
+        for (int r0 = 0; r0 < bs; r0 += 32) {
+            const int rows = min(32, bs - r0);
+            const double s = vbr_reduce(vbr_partial(inv + bjoff[Fr], x + hoff[Fr], bs, bs, r0, lane), rows, lane);
+            if (lane < rows) y[hoff[Fr] + r0 + lane] = s;
         }
     }
 }
