@@ -424,9 +424,15 @@ typedef struct {
  * meshes (a face of more than two elements, repeated vertices, untagged
  * boundary faces, tagged interior faces, a non-positive Jacobian at a
  * quadrature point).  Supported calls on the handle: hdg_set_params (tau,
- * viscosity law; FP64 only), hdg_set_bc_state, hdg_set_stream,
- * hdg_linearize_condense (packed layouts; nu must be NULL), hdg_trace_matvec,
- * hdg_trace_rhs, hdg_recover_interior, hdg_get_blocks, hdg_status,
+ * viscosity law, precision: any HDG_PREC_MIXED* selects the tetrahedral mixed
+ * form, FP32 Jacobian coefficients, contraction, trace rows of the elimination
+ * and trace blocks with FP64 pointwise terms, interior LU and right-hand
+ * sides), hdg_set_bc_state, hdg_set_stream, hdg_linearize_condense (packed
+ * layouts; nu must be NULL), hdg_trace_matvec, hdg_trace_rhs,
+ * hdg_recover_interior, hdg_get_blocks (FP32 values after a mixed
+ * linearization), hdg_status, hdg_residual, hdg_update_state,
+ * hdg_blockjacobi_setup / _apply, hdg_gmres, hdg_newton, hdg_newton_fixed,
+ * hdg_dirk_step, hdg_rb_*, hdg_set_preconditioner (block-Jacobi only),
  * hdg_profile*, hdg_destroy; the others return HDG_EUNSUPPORTED. */
 int hdg_create_tet(hdg_handle* out, const hdg_tet_mesh* mesh, double gamma, double Re, double Pr, double Mach);
 int hdg_create_tet_host(hdg_handle* out, const hdg_tet_mesh* mesh, double gamma, double Re, double Pr,

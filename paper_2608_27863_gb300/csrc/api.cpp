@@ -555,7 +555,9 @@ int hdg_get_blocks(hdg_handle h, double* vals) {
     if (h->tet) {
         if (!h->device || !h->tet->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
         if (!vals) return fail(h, HDG_EINVAL, "vals is NULL");
-        CKH(cudaMemcpyAsync(vals, h->tet->d_vals, sizeof(double) * h->tet->n_vals, cudaMemcpyDeviceToDevice,
+        const bool f32 = h->tet->sys_prec != HDG_PREC_FP64;
+        CKH(cudaMemcpyAsync(vals, f32 ? (const void*)h->tet->d_vals32 : (const void*)h->tet->d_vals,
+                            (f32 ? sizeof(float) : sizeof(double)) * h->tet->n_vals, cudaMemcpyDeviceToDevice,
                             h->stream));
         return HDG_OK;
     }

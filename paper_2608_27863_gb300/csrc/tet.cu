@@ -860,9 +860,10 @@ __global__ void __launch_bounds__(NTH, 2) k_tet_linearize(KArgs A) {
 
 // A5: block values, column-major per block, summed over the block's element
 // contributions in ascending element order; g = -(trace rows' last column)
+template <class TV>
 __global__ void k_tet_assemble(const TetElem* el, const double* mat, const int64_t* hoff, const int64_t* boff,
                                const int32_t* rowptr, const int32_t* col, const int32_t* cptr, const int32_t* centry,
-                               int64_t F, int64_t nnzb, double* vals) {
+                               int64_t F, int64_t nnzb, TV* vals) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -874,7 +875,7 @@ __global__ void k_tet_assemble(const TetElem* el, const double* mat, const int64
         }
         const int64_t Fr = lo, G = col[b];
         const int bsF = (int)(hoff[Fr + 1] - hoff[Fr]), bsG = (int)(hoff[G + 1] - hoff[G]);
-        double* out = vals + boff[b];
+        TV* out = vals + boff[b];
         for (int idx = lane; idx < bsF * bsG; idx += 32) {
             const int c = idx / bsF, r = idx - c * bsF;
             double s = 0.0;
@@ -883,7 +884,7 @@ __global__ void k_tet_assemble(const TetElem* el, const double* mat, const int64
                 const int fl = centry[3 * k + 1], gl = centry[3 * k + 2];
                 s += mat[d.moff + (int64_t)(d.NU + d.toff[fl] + r) * d.LD + d.NU + d.toff[gl] + c];
             }
-            out[idx] = s;
+            out[idx] = (TV)s;
         }
     }
 }
@@ -914,11 +915,12 @@ __global__ void k_tet_assemble_g(const TetElem* el, const double* mat, const int
 // bsF <= 16 the warp splits into ng = 32 / bsF column groups (lane = group
 // * bsF + row), so every load instruction reads ng consecutive columns; the
 // groups are combined by shuffles.  Rows beyond 32 take further passes.
-__device__ __forceinline__ double vbr_partial(const double* B, const double* xg, int bsF, int bsG, int r0, int lane) {
+template <class T>
+__device__ __forceinline__ T vbr_partial(const T* B, const T* xg, int bsF, int bsG, int r0, int lane) {
     const int rows = min(32, bsF - r0);
     const int ng = rows <= 16 ? 32 / rows : 1;
     const int r = lane % rows, cg = lane / rows;
-    double s0 = 0.0, s1 = 0.0;
+    T s0 = 0, s1 = 0;
     if (cg < ng) {
         int c = cg;
         for (; c + ng < bsG; c += 2 * ng) {
@@ -931,34 +933,42 @@ __device__ __forceinline__ double vbr_partial(const double* B, const double* xg,
 }
 
 // sum of the column groups' partials into the lanes of group 0
-__device__ __forceinline__ double vbr_reduce(double s, int rows, int lane) {
+template <class T>
+__device__ __forceinline__ T vbr_reduce(T s, int rows, int lane) {
     const int ng = rows <= 16 ? 32 / rows : 1;
     for (int g = 1; g < ng; ++g) {
-        const double o = __shfl_sync(0xffffffffu, s, (lane + g * rows) & 31);
+        const T o = __shfl_sync(0xffffffffu, s, (lane + g * rows) & 31);
         if (lane < rows && lane + g * rows < 32) s += o;
     }
     return s;
 }
 
-// A6: y = S x, one warp per block row
-__global__ void k_tet_matvec(const double* vals, const int64_t* hoff, const int64_t* boff, const int32_t* rowptr,
-                             const int32_t* col, int64_t F, const double* x, double* y) {
+// A6: y = S x, one warp per block row (T: the block and operand type; FP32
+// arithmetic for the mixed form's FP32 blocks, the operand converted once)
+template <class T>
+__global__ void k_tet_matvec(const T* vals, const int64_t* hoff, const int64_t* boff, const int32_t* rowptr,
+                             const int32_t* col, int64_t F, const T* x, double* y) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t Fr = wid; Fr < F; Fr += nw) {
         const int bsF = (int)(hoff[Fr + 1] - hoff[Fr]);
         for (int r0 = 0; r0 < bsF; r0 += 32) {
-            double s = 0.0;
+            T s = 0;
             for (int b = rowptr[Fr]; b < rowptr[Fr + 1]; ++b) {
                 const int64_t G = col[b];
                 s += vbr_partial(vals + boff[b], x + hoff[G], bsF, (int)(hoff[G + 1] - hoff[G]), r0, lane);
             }
             const int rows = min(32, bsF - r0);
             s = vbr_reduce(s, rows, lane);
-            if (lane < rows) y[hoff[Fr] + r0 + lane] = s;
+            if (lane < rows) y[hoff[Fr] + r0 + lane] = (double)s;
         }
     }
+}
+
+__global__ void k_tet_to_f32(const double* x, float* y, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)x[i];
 }
 
 // A7: dU = -U^{-1} (z + Z dUhat_K), dQ = dq0 - G dU - H dUhat_K
@@ -1174,15 +1184,16 @@ __global__ void k_tet_residual_faces(const TetElem* el, const double* rk, const 
 
 // block-Jacobi set-up: explicit inverse of every diagonal block S_FF by
 // Gauss-Jordan elimination with partial pivoting (column-major result)
-__global__ void __launch_bounds__(128) k_tet_bj_setup(const double* vals, const int64_t* boff, const int32_t* diagb,
+template <class TV>
+__global__ void __launch_bounds__(128) k_tet_bj_setup(const TV* vals, const int64_t* boff, const int32_t* diagb,
                                                        const int64_t* hoff, const int64_t* bjoff, int64_t F,
-                                                       double* inv, int32_t* status) {
+                                                       TV* inv, int32_t* status) {
     extern __shared__ double sa[];                // [bs][2 bs] augmented rows
     __shared__ int pr;
     const int tid = threadIdx.x, lane = tid & 31;
     for (int64_t Fr = blockIdx.x; Fr < F; Fr += gridDim.x) {
         const int bs = (int)(hoff[Fr + 1] - hoff[Fr]), w2 = 2 * bs;
-        const double* B = vals + boff[diagb[Fr]];
+        const TV* B = vals + boff[diagb[Fr]];
         for (int idx = tid; idx < bs * w2; idx += 128) {
             const int r = idx / w2, c = idx - r * w2;
             sa[idx] = c < bs ? B[(int64_t)c * bs + r] : (c - bs == r ? 1.0 : 0.0);
@@ -1232,17 +1243,18 @@ __global__ void __launch_bounds__(128) k_tet_bj_setup(const double* vals, const 
                 if (r != c) sa[r * w2 + c] = 0.0;
             __syncthreads();
         }
-        double* o = inv + bjoff[Fr];
+        TV* o = inv + bjoff[Fr];
         for (int idx = tid; idx < bs * bs; idx += 128) {
             const int c = idx / bs, r = idx - c * bs;
-            o[idx] = sa[r * w2 + bs + c];
+            o[idx] = (TV)sa[r * w2 + bs + c];
         }
         __syncthreads();
     }
 }
 
-__global__ void k_tet_bj_apply(const double* inv, const int64_t* hoff, const int64_t* bjoff, int64_t F,
-                               const double* x, double* y) {
+template <class T>
+__global__ void k_tet_bj_apply(const T* inv, const int64_t* hoff, const int64_t* bjoff, int64_t F,
+                               const T* x, double* y) {
     const int lane = threadIdx.x & 31;
     const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -1250,8 +1262,8 @@ __global__ void k_tet_bj_apply(const double* inv, const int64_t* hoff, const int
         const int bs = (int)(hoff[Fr + 1] - hoff[Fr]);
         for (int r0 = 0; r0 < bs; r0 += 32) {
             const int rows = min(32, bs - r0);
-            const double s = vbr_reduce(vbr_partial(inv + bjoff[Fr], x + hoff[Fr], bs, bs, r0, lane), rows, lane);
-            if (lane < rows) y[hoff[Fr] + r0 + lane] = s;
+            const T s = vbr_reduce(vbr_partial(inv + bjoff[Fr], x + hoff[Fr], bs, bs, r0, lane), rows, lane);
+            if (lane < rows) y[hoff[Fr] + r0 + lane] = (double)s;
         }
     }
 }
@@ -1314,7 +1326,10 @@ int create_device(hdg_ctx* h, std::string& err) {
     if ((rc = tet_alloc(h, &c->d_part, (size_t)(c->E + c->F), err))) return rc;   // here so graphs can capture it
     int bsmax = 0;
     for (int64_t F = 0; F < c->F; ++F) bsmax = std::max<int>(bsmax, (int)(c->hoff[F + 1] - c->hoff[F]));
-    if (cudaFuncSetAttribute(k_tet_bj_setup, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if ((rc = tet_alloc(h, &c->d_x32, (size_t)c->n_trace, err))) return rc;
+    if (cudaFuncSetAttribute(k_tet_bj_setup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * 2 * (size_t)bsmax * bsmax)) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tet_bj_setup<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(sizeof(double) * 2 * (size_t)bsmax * bsmax)) != cudaSuccess) {
         err = "shared-memory opt-in of the block-Jacobi kernel failed";
         return HDG_ECUDA;
@@ -1366,6 +1381,11 @@ int linearize(hdg_ctx* h, const double* U, const double* Q, const double* UH, co
     A.ph = phys_t<double>(h->phys); A.dt = dt; A.a_ii = a_ii; A.tau = h->phys.tau;
     A.ub = h->d_ub; A.ew = h->e_wall; A.status = h->d_status;
     cudaStream_t st = h->stream;
+    if (h->precision != HDG_PREC_FP64 && !c->d_vals32) {
+        std::string err;
+        const int rc = tet_alloc(h, &c->d_vals32, (size_t)c->n_vals, err);
+        if (rc) { h->err = err; return rc; }
+    }
     TET_CK(cudaMemsetAsync(c->d_next, 0, sizeof(int32_t), st));
     prof_begin(h, HDG_K_ELIM);
     if (h->precision == HDG_PREC_FP64)
@@ -1376,13 +1396,19 @@ int linearize(hdg_ctx* h, const double* U, const double* Q, const double* UH, co
     TET_CK(cudaGetLastError());
     prof_begin(h, HDG_K_ASSEMBLE);
     const unsigned gb = (unsigned)std::min<int64_t>(65535, (c->nnzb + 7) / 8);
-    k_tet_assemble<<<gb, 256, 0, st>>>(c->d_el, c->d_mat, c->d_hoff, c->d_boff, c->d_rowptr, c->d_col, c->d_cptr,
-                                       c->d_centry, c->F, c->nnzb, c->d_vals);
+    if (h->precision == HDG_PREC_FP64) {
+        k_tet_assemble<double><<<gb, 256, 0, st>>>(c->d_el, c->d_mat, c->d_hoff, c->d_boff, c->d_rowptr, c->d_col,
+                                                   c->d_cptr, c->d_centry, c->F, c->nnzb, c->d_vals);
+    } else {
+        k_tet_assemble<float><<<gb, 256, 0, st>>>(c->d_el, c->d_mat, c->d_hoff, c->d_boff, c->d_rowptr, c->d_col,
+                                                  c->d_cptr, c->d_centry, c->F, c->nnzb, c->d_vals32);
+    }
     const unsigned gf = (unsigned)std::min<int64_t>(65535, (c->F + 7) / 8);
     k_tet_assemble_g<<<gf, 256, 0, st>>>(c->d_el, c->d_mat, c->d_hoff, c->d_f2e, c->d_f2lf, c->F, c->d_g);
     prof_end(h);
     TET_CK(cudaGetLastError());
     c->have_system = true;
+    c->sys_prec = h->precision == HDG_PREC_FP64 ? HDG_PREC_FP64 : HDG_PREC_MIXED;
     h->have_system = true;
     c->bj_ready = false;       // the diagonal blocks changed
     return HDG_OK;
@@ -1392,7 +1418,15 @@ int matvec(hdg_ctx* h, const double* x, double* y) {
     Ctx* c = h->tet;
     const unsigned gf = (unsigned)std::min<int64_t>(65535, (c->F + 7) / 8);
     prof_begin(h, HDG_K_MATVEC);
-    k_tet_matvec<<<gf, 256, 0, h->stream>>>(c->d_vals, c->d_hoff, c->d_boff, c->d_rowptr, c->d_col, c->F, x, y);
+    if (c->sys_prec == HDG_PREC_FP64) {
+        k_tet_matvec<double><<<gf, 256, 0, h->stream>>>(c->d_vals, c->d_hoff, c->d_boff, c->d_rowptr, c->d_col, c->F,
+                                                        x, y);
+    } else {
+        k_tet_to_f32<<<(unsigned)std::min<int64_t>(4096, (c->n_trace + 255) / 256), 256, 0, h->stream>>>(
+            x, c->d_x32, c->n_trace);
+        k_tet_matvec<float><<<gf, 256, 0, h->stream>>>(c->d_vals32, c->d_hoff, c->d_boff, c->d_rowptr, c->d_col, c->F,
+                                                       c->d_x32, y);
+    }
     prof_end(h);
     TET_CK(cudaGetLastError());
     return HDG_OK;
@@ -1446,13 +1480,19 @@ int bj_setup(hdg_ctx* h) {
     if (!c->have_system) { h->err = "no assembled trace system"; return HDG_EINVAL; }
     std::string err;
     int rc;
-    if (!c->d_bj && (rc = tet_alloc(h, &c->d_bj, (size_t)c->bjoff[c->F], err))) { h->err = err; return rc; }
+    const bool mixed = c->sys_prec != HDG_PREC_FP64;
+    if (!mixed && !c->d_bj && (rc = tet_alloc(h, &c->d_bj, (size_t)c->bjoff[c->F], err))) { h->err = err; return rc; }
+    if (mixed && !c->d_bj32 && (rc = tet_alloc(h, &c->d_bj32, (size_t)c->bjoff[c->F], err))) { h->err = err; return rc; }
     int bsmax = 0;
     for (int64_t F = 0; F < c->F; ++F) bsmax = std::max<int>(bsmax, (int)(c->hoff[F + 1] - c->hoff[F]));
     const size_t smem = sizeof(double) * (size_t)bsmax * 2 * bsmax;
     const unsigned g = (unsigned)std::min<int64_t>(c->F, 152 * 4);
-    k_tet_bj_setup<<<g, 128, smem, h->stream>>>(c->d_vals, c->d_boff, c->d_diagb, c->d_hoff, c->d_bjoff, c->F,
-                                               c->d_bj, h->d_status);
+    if (!mixed)
+        k_tet_bj_setup<double><<<g, 128, smem, h->stream>>>(c->d_vals, c->d_boff, c->d_diagb, c->d_hoff, c->d_bjoff,
+                                                            c->F, c->d_bj, h->d_status);
+    else
+        k_tet_bj_setup<float><<<g, 128, smem, h->stream>>>(c->d_vals32, c->d_boff, c->d_diagb, c->d_hoff, c->d_bjoff,
+                                                           c->F, c->d_bj32, h->d_status);
     TET_CK(cudaGetLastError());
     c->bj_ready = true;
     return HDG_OK;
@@ -1461,7 +1501,13 @@ int bj_setup(hdg_ctx* h) {
 int bj_apply(hdg_ctx* h, const double* x, double* y) {
     Ctx* c = h->tet;
     const unsigned gf = (unsigned)std::min<int64_t>(65535, (c->F + 7) / 8);
-    k_tet_bj_apply<<<gf, 256, 0, h->stream>>>(c->d_bj, c->d_hoff, c->d_bjoff, c->F, x, y);
+    if (c->sys_prec == HDG_PREC_FP64) {
+        k_tet_bj_apply<double><<<gf, 256, 0, h->stream>>>(c->d_bj, c->d_hoff, c->d_bjoff, c->F, x, y);
+    } else {
+        k_tet_to_f32<<<(unsigned)std::min<int64_t>(4096, (c->n_trace + 255) / 256), 256, 0, h->stream>>>(
+            x, c->d_x32, c->n_trace);
+        k_tet_bj_apply<float><<<gf, 256, 0, h->stream>>>(c->d_bj32, c->d_hoff, c->d_bjoff, c->F, c->d_x32, y);
+    }
     TET_CK(cudaGetLastError());
     return HDG_OK;
 }

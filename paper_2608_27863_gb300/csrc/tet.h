@@ -90,7 +90,11 @@ struct Ctx {
     int32_t* d_f2lf = nullptr;
     double* d_mat = nullptr;               // per-element bordered matrices
     double* d_rec = nullptr;               // per-element recovery data
-    double* d_vals = nullptr;              // assembled blocks
+    double* d_vals = nullptr;              // assembled blocks (FP64 form)
+    float* d_vals32 = nullptr;             // assembled blocks of the mixed form (allocated on first use)
+    float* d_bj32 = nullptr;               // block-Jacobi inverses of the mixed form
+    float* d_x32 = nullptr;                // FP32 copy of a matvec / preconditioner operand
+    int sys_prec = HDG_PREC_FP64;          // precision of the assembled system
     double* d_g = nullptr;                 // [n_trace]
     double* d_work = nullptr;              // per-CTA workspace
     int32_t* d_diagb = nullptr;
