@@ -168,12 +168,28 @@ def run_tet(args, rank, world, local_rank):
         H.hdg_profile(h, False)
         return max_over_ranks(sum(times), world, dev), prof, clk.summary()
 
+    def tune():
+        # the project's autotuner picks the elimination panel width of the persistent kernel (untimed)
+        if args.no_autotune or args.tuning:
+            nb = 16
+            for item in (args.tuning or "").split(","):
+                if item.startswith("elim_nb="):
+                    nb = int(item.split("=")[1])
+            H.hdg_set_tuning(h, elim_nb=nb)
+            return {"elim_nb": nb, "fixed": True}
+        rep = H.hdg_autotune(h, U, Q, UH, Us, None, P.dt, P.a_ii, reps=1)
+        return {"elim_nb": rep["elim_nb"], "candidates_ms": [c[1] for c in rep["candidates"]]}
+
+    tuning = {}
     H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_FP64)
+    tuning["fp64"] = tune()
     t_ms, prof, clocks = timed()
     if not args.no_mixed:
         H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_MIXED)
+        tuning["mixed"] = tune()
         tm_ms, prof_m, clocks_m = timed()
         H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_FP64)
+        H.hdg_set_tuning(h, elim_nb=tuning["fp64"]["elim_nb"])
     # end to end from pinned host memory
     hU, hQ, hUH, hUs = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in (P.U, P.Q, P.UH, P.Ustar))
     hdQ = torch.empty(dQ.shape, dtype=torch.float64).pin_memory()
@@ -224,6 +240,7 @@ def run_tet(args, rank, world, local_rank):
         newton = {}
         for name, prec in (("fp64", H.HDG_PREC_FP64), ("mixed", H.HDG_PREC_MIXED)):
             H.hdg_set_params(h, tau=P.tau, precision=prec)
+            H.hdg_set_tuning(h, elim_nb=tuning[name]["elim_nb"])
             U2, Q2, UH2 = U.clone(), Q.clone(), UH.clone()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -245,6 +262,7 @@ def run_tet(args, rank, world, local_rank):
         # one SDIRK3 step, 3 stages x 4 Newton iterations (GMRES(30) each) captured as one CUDA graph,
         # mixed form; the first call captures (after one eager linearization), the second replays
         H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_MIXED)
+        H.hdg_set_tuning(h, elim_nb=tuning["mixed"]["elim_nb"])
         A3, b3 = H.sdirk3_tableau()
         U2, Q2, UH2 = U.clone(), Q.clone(), UH.clone()
         torch.cuda.synchronize()
@@ -280,6 +298,7 @@ def run_tet(args, rank, world, local_rank):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": sum(v[1] for v in prof.values()) / args.steps,
         "clocks": clocks,
+        "tuning": tuning,
     }
     if cpu is not None:
         out["cpu_baseline"] = cpu

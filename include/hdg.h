@@ -314,7 +314,10 @@ int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* 
  *    the volume contraction as FP32 SIMT (blocks_mode 0) or
  *    3xTF32 tensor cores (1, 3-D), and, when requested as HDG_PREC_MIXED,
  *    the Schur product as FP32 SIMT (schur_mode 0) or 3xTF32 tensor cores
- *    (2) — all FP32-accurate; TF32 / 3xTF32 requested explicitly are kept.
+ *    (2) — all FP32-accurate; TF32 / 3xTF32 requested explicitly are kept;
+ *  - tetrahedral handles: the elimination panel width (16 or 8 columns) of
+ *    the persistent linearize + condense kernel (elim_nb; the other fields
+ *    are zero; hdg_set_tuning reads elim_nb only).
  * out (host, optional) receives the choice and every candidate's time.
  * hdg_set_tuning applies a stored choice.  Both synchronise; the system
  * left assembled is that of the last candidate timed. */
@@ -433,7 +436,8 @@ typedef struct {
  * linearization), hdg_status, hdg_residual, hdg_update_state,
  * hdg_blockjacobi_setup / _apply, hdg_gmres, hdg_newton, hdg_newton_fixed,
  * hdg_dirk_step, hdg_rb_*, hdg_set_preconditioner (block-Jacobi only),
- * hdg_profile*, hdg_destroy; the others return HDG_EUNSUPPORTED. */
+ * hdg_autotune / hdg_set_tuning (panel width), hdg_profile*, hdg_destroy; the
+ * others return HDG_EUNSUPPORTED. */
 int hdg_create_tet(hdg_handle* out, const hdg_tet_mesh* mesh, double gamma, double Re, double Pr, double Mach);
 int hdg_create_tet_host(hdg_handle* out, const hdg_tet_mesh* mesh, double gamma, double Re, double Pr,
                         double Mach);

@@ -322,7 +322,39 @@ int hdg_reserve(hdg_handle h, int precision) {
 
 int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* UH, const double* Ustar,
                  const double* nu, double dt, double a_ii, int reps, hdg_tune* out) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
+    if (h && h->tet) {
+        // tetrahedral handles: the elimination panel width of the persistent kernel
+        if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
+        if (reps < 1 || reps > 100) return fail(h, HDG_EINVAL, "reps must be in 1..100");
+        const int nbs[2] = {16, 8};
+        double best = 1e300;
+        int pick = 16;
+        cudaEvent_t e0, e1;
+        CKH(cudaEventCreate(&e0));
+        CKH(cudaEventCreate(&e1));
+        if (out) { std::memset(out, 0, sizeof(*out)); out->n_cand = 2; }
+        for (int i = 0; i < 2; ++i) {
+            h->tet->nb = nbs[i];
+            int rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr);   // warm-up
+            if (rc) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+            CKH(cudaEventRecord(e0, h->stream));
+            for (int r = 0; r < reps; ++r)
+                if ((rc = hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr))) {
+                    cudaEventDestroy(e0); cudaEventDestroy(e1); return rc;
+                }
+            CKH(cudaEventRecord(e1, h->stream));
+            CKH(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CKH(cudaEventElapsedTime(&ms, e0, e1));
+            if (out) { out->cand[i][0] = nbs[i]; out->ms[i] = ms / reps; }
+            if (ms < best) { best = ms; pick = nbs[i]; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        h->tet->nb = pick;
+        if (out) out->elim_nb = pick;
+        return hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr);
+    }
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
     if (reps < 1 || reps > 100) return fail(h, HDG_EINVAL, "reps must be in 1..100");
@@ -405,7 +437,11 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
 }
 
 int hdg_set_tuning(hdg_handle h, const hdg_tune* t) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
+    if (h && h->tet) {
+        if (!t || (t->elim_nb != 16 && t->elim_nb != 8)) return fail(h, HDG_EINVAL, "elim_nb must be 16 or 8");
+        h->tet->nb = t->elim_nb;
+        return HDG_OK;
+    }
     if (!h || !t) return fail(h, HDG_EINVAL, "NULL argument");
     if ((t->elim_nb != 8 && t->elim_nb != 16) || (t->elim_minb != 1 && t->elim_minb != 2) ||
         t->schur_mode < 0 || t->schur_mode > 2 || t->blocks_mode < 0 || t->blocks_mode > 2 ||

@@ -25,7 +25,7 @@ constexpr int NCM = NPMAX + 4 * NFPMAX;   // columns of one component: U nodes +
 constexpr int KC = 40;                    // contraction: points staged per step
 constexpr int SRP = 36;                   // staged row-basis stride (NPMAX rounded up to 4)
 constexpr int STP = 96;                   // staged column stride (NCM rounded up to 4)
-constexpr int NB = 16;                    // elimination panel width
+constexpr int NB = 16;                    // largest elimination panel width (shared-memory sizing)
 constexpr int TCW = 64;                   // elimination column tile
 constexpr int NRMAX = M * NPMAX + 4 * M * NFPMAX;
 
@@ -93,7 +93,7 @@ template <> __device__ __forceinline__ const float* jtab<float>(const KArgs& A) 
 
 // runtime-sized tile of the trailing update A22 -= L21 U12 (rows rb + ty + 16 ii,
 // columns ct + tx + 16 jj)
-template <int NII, int NJJ, class RowP>
+template <int NII, int NJJ, int NB, class RowP>
 __device__ __forceinline__ void trail_tile_rt(RowP rowp, const double* pan, const double* ust, int rb, int ct, int k0,
                                               int kb, int tx, int ty, int NR, int NC) {
     double acc[NII][NJJ];
@@ -136,6 +136,7 @@ __device__ __forceinline__ void trail_tile_rt(RowP rowp, const double* pan, cons
 // ties), rows interchanged across all columns, trace rows eliminated, so that
 // the bottom-right block becomes S = Dt - Ct At^{-1} Bt and the last column
 // Rh - Ct At^{-1} Rt.
+template <int NB>
 __device__ void bordered_elim(double* Mx, int NU, int NR, int NC, int LD, double* pan, double* ust, int* piv,
                               int* sflag) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -237,7 +238,7 @@ __device__ void bordered_elim(double* Mx, int NU, int NR, int NC, int LD, double
                 while (nii < 4 && rb + 16 * nii < NR) ++nii;
                 switch (nii * 4 + njj - 5) {
 #define HDG_TT(I, J) \
-    case (I) * 4 + (J) - 5: trail_tile_rt<I, J>(rowp, pan, ust, rb, ct, k0, kb, tx, ty, NR, NC); break;
+    case (I) * 4 + (J) - 5: trail_tile_rt<I, J, NB>(rowp, pan, ust, rb, ct, k0, kb, tx, ty, NR, NC); break;
                     HDG_TT(1, 1) HDG_TT(1, 2) HDG_TT(1, 3) HDG_TT(1, 4)
                     HDG_TT(2, 1) HDG_TT(2, 2) HDG_TT(2, 3) HDG_TT(2, 4)
                     HDG_TT(3, 1) HDG_TT(3, 2) HDG_TT(3, 3) HDG_TT(3, 4)
@@ -396,7 +397,7 @@ __device__ void load_geometry(const KArgs& A, const TetElem& d, double* gv, doub
 // TJ: type of the Jacobian coefficients, the column variations and the
 // contraction (double: FP64 form; float: mixed form).  Pointwise terms, lifting
 // operators, mass term, right-hand side and the elimination are FP64 in both.
-template <class TJ>
+template <class TJ, int NBE>
 __device__ void process_element(const KArgs& A, const TetElem& d, double* W, double* sm, int* sflag) {
     const int tid = threadIdx.x;
     const int Np = d.Np, Nq = d.Nq, NU = d.NU, t = d.t, LD = d.LD, sfq = d.sfq;
@@ -824,17 +825,17 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
     // A3 + A4: bordered elimination
     __shared__ int piv[NB];
     if constexpr (sizeof(TJ) == sizeof(double)) {
-        bordered_elim(Mx, NU, NR, NR + 1, LD, sD, sD + NRMAX * NB, piv, sflag);
+        bordered_elim<NBE>(Mx, NU, NR, NR + 1, LD, sD, sD + NRMAX * NB, piv, sflag);
     } else {
         // FP64 LU of At with its right-hand sides (top rows only), then the trace rows in FP32
-        bordered_elim(Mx, NU, NU, NR + 1, LD, sD, sD + NRMAX * NB, piv, sflag);
+        bordered_elim<NBE>(Mx, NU, NU, NR + 1, LD, sD, sD + NRMAX * NB, piv, sflag);
         __syncthreads();
         trace_schur_f32(Mx, NU, t, LD, reinterpret_cast<float*>(W + W_VQ), reinterpret_cast<float*>(W + W_CV),
                         reinterpret_cast<float*>(sD));
     }
 }
 
-template <class TJ>
+template <class TJ, int NBE>
 __global__ void __launch_bounds__(NTH, 2) k_tet_linearize(KArgs A) {
     extern __shared__ double sm[];
     __shared__ TetElem d;
@@ -852,7 +853,7 @@ __global__ void __launch_bounds__(NTH, 2) k_tet_linearize(KArgs A) {
         for (int i = tid; i < NW; i += NTH)
             reinterpret_cast<int64_t*>(&d)[i] = reinterpret_cast<const int64_t*>(A.el + e)[i];
         __syncthreads();
-        process_element<TJ>(A, d, W, sm, &sflag);
+        process_element<TJ, NBE>(A, d, W, sm, &sflag);
         __syncthreads();
     }
     if (tid == 0 && sflag) atomicOr(A.status, sflag);
@@ -1339,9 +1340,13 @@ int create_device(hdg_ctx* h, std::string& err) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaFuncSetAttribute(k_tet_linearize<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (cudaFuncSetAttribute(k_tet_linearize<double, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(S_TOTAL * sizeof(double))) != cudaSuccess ||
-        cudaFuncSetAttribute(k_tet_linearize<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_tet_linearize<float, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(S_TOTAL * sizeof(double))) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tet_linearize<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(S_TOTAL * sizeof(double))) != cudaSuccess ||
+        cudaFuncSetAttribute(k_tet_linearize<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(S_TOTAL * sizeof(double))) != cudaSuccess) {
         err = "shared-memory opt-in of the tetrahedral kernel failed";
         return HDG_ECUDA;
@@ -1352,7 +1357,8 @@ int create_device(hdg_ctx* h, std::string& err) {
         return HDG_ECUDA;
     }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tet_linearize<double>, NTH, S_TOTAL * sizeof(double));
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tet_linearize<double, 16>, NTH,
+                                                  S_TOTAL * sizeof(double));
     c->n_slots = std::max(1, nsm * std::max(1, per_sm));
     c->work_stride = W_END;
     if ((rc = tet_alloc(h, &c->d_work, (size_t)c->n_slots * W_END, err))) return rc;
@@ -1388,10 +1394,14 @@ int linearize(hdg_ctx* h, const double* U, const double* Q, const double* UH, co
     }
     TET_CK(cudaMemsetAsync(c->d_next, 0, sizeof(int32_t), st));
     prof_begin(h, HDG_K_ELIM);
-    if (h->precision == HDG_PREC_FP64)
-        k_tet_linearize<double><<<c->n_slots, NTH, S_TOTAL * sizeof(double), st>>>(A);
-    else
-        k_tet_linearize<float><<<c->n_slots, NTH, S_TOTAL * sizeof(double), st>>>(A);
+    const size_t smem = S_TOTAL * sizeof(double);
+    if (h->precision == HDG_PREC_FP64) {
+        if (c->nb == 8) k_tet_linearize<double, 8><<<c->n_slots, NTH, smem, st>>>(A);
+        else k_tet_linearize<double, 16><<<c->n_slots, NTH, smem, st>>>(A);
+    } else {
+        if (c->nb == 8) k_tet_linearize<float, 8><<<c->n_slots, NTH, smem, st>>>(A);
+        else k_tet_linearize<float, 16><<<c->n_slots, NTH, smem, st>>>(A);
+    }
     prof_end(h);
     TET_CK(cudaGetLastError());
     prof_begin(h, HDG_K_ASSEMBLE);

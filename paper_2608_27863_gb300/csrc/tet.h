@@ -95,6 +95,7 @@ struct Ctx {
     float* d_bj32 = nullptr;               // block-Jacobi inverses of the mixed form
     float* d_x32 = nullptr;                // FP32 copy of a matvec / preconditioner operand
     int sys_prec = HDG_PREC_FP64;          // precision of the assembled system
+    int nb = 16;                           // elimination panel width (autotuned: 16 or 8)
     double* d_g = nullptr;                 // [n_trace]
     double* d_work = nullptr;              // per-CTA workspace
     int32_t* d_diagb = nullptr;

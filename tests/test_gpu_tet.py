@@ -222,3 +222,24 @@ def test_tet_mixed_form_blocks_and_newton(H):
         assert hist[-1] <= 1e-10
     finally:
         H.hdg_destroy(h)
+
+
+def test_tet_autotune_and_panel_width_parity(H):
+    """The autotuner times both panel widths of the persistent kernel and keeps one;
+    the 8-column variant matches the oracle like the 16-column one."""
+    mesh = mesh_case(1)
+    prob, pb, h, dev = setup(H, mesh)
+    try:
+        rep = H.hdg_autotune(h, dev["U"], dev["Q"], dev["UH"], dev["Ustar"], None, prob.dt, prob.a_ii, reps=1)
+        assert rep["elim_nb"] in (16, 8) and len(rep["candidates"]) == 2
+        assert all(c[1] > 0 for c in rep["candidates"])
+        H.hdg_set_tuning(h, elim_nb=8)
+        s = H.hdg_tet_query(h)
+        H.hdg_linearize_condense(h, dev["U"], dev["Q"], dev["UH"], dev["Ustar"], None, prob.dt, prob.a_ii)
+        assert H.hdg_status(h) == H.HDG_OK
+        vals = torch.zeros(s["n_vals"], dtype=torch.float64, device="cuda")
+        H.hdg_get_blocks(h, vals)
+        errs, _, _ = block_errors(H, h, pb, vals.cpu().numpy())
+        assert errs.max() < TOL, errs.max()
+    finally:
+        H.hdg_destroy(h)
