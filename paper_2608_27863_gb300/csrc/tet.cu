@@ -698,38 +698,57 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
         TJ acc[4][4] = {};
         for (int k0 = 0; k0 < K1; k0 += KC) {
             const int kc = min(KC, K1 - k0);
-            for (int idx = tid; idx < kc * SRP; idx += NTH) {
-                const int kk = idx / SRP, i = idx - kk * SRP, K = k0 + kk;
-                TJ v = 0;
-                if (i < Np) {
-                    if (K < 3 * Nq) v = dphiJ[((size_t)(K % 3) * Nq + K / 3) * Np + i];
-                    else v = basis_row_t(tabJ, d, Nq + K - 3 * Nq)[i];
-                }
-                sR[idx] = v;
-            }
-            for (int idx = tid; idx < kc * STP; idx += NTH) {
-                const int kk = idx / STP, c = idx - kk * STP, K = k0 + kk;
-                TJ v = 0;
-                if (c < Nc) {
-                    if (K < 3 * Nq) {
-                        const int g = K / 3, r = K - 3 * g;
-                        const TJ* o = cv + (size_t)g * 300 + ((a * 3 + r) * M + b) * 4;
-                        if (c < Np) v = o[0] * phiJ[(size_t)g * Np + c];
-                        for (int l = 0; l < 3; ++l) v -= o[1 + l] * vq[((size_t)l * NPT + g) * NCM + c];
-                    } else {
-                        const int rr = K - 3 * Nq, x = Nq + rr;
-                        const TJ* o = cf + (size_t)rr * 125 + (a * M + b) * 5;
-                        if (c < Np) {
-                            v = o[0] * basis_row_t(tabJ, d, x)[c];
-                        } else {
-                            const int f = face_of_point(d, rr);
-                            const int l = c - Np - fpo[f];
-                            if (l >= 0 && l < d.nfp[f]) v = o[1] * tabJ[d.ttab[f] + (size_t)(rr - d.soff[f]) * d.nfp[f] + l];
-                        }
-                        for (int l = 0; l < 3; ++l) v -= o[2 + l] * vq[((size_t)l * NPT + x) * NCM + c];
+            // operands of the chunk; four entries per thread per pass, their loads
+            // issued before any store so that they are in flight together
+            for (int base = tid; base < kc * SRP; base += 4 * NTH) {
+                TJ vv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int idx = base + u * NTH;
+                    const int kk = idx / SRP, i = idx - kk * SRP, K = k0 + kk;
+                    TJ v = 0;
+                    if (idx < kc * SRP && i < Np) {
+                        if (K < 3 * Nq) v = dphiJ[((size_t)(K % 3) * Nq + K / 3) * Np + i];
+                        else v = basis_row_t(tabJ, d, Nq + K - 3 * Nq)[i];
                     }
+                    vv[u] = v;
                 }
-                sT[idx] = v;
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (base + u * NTH < kc * SRP) sR[base + u * NTH] = vv[u];
+            }
+            for (int base = tid; base < kc * STP; base += 4 * NTH) {
+                TJ vv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int idx = base + u * NTH;
+                    const int kk = idx / STP, c = idx - kk * STP, K = k0 + kk;
+                    TJ v = 0;
+                    if (idx < kc * STP && c < Nc) {
+                        if (K < 3 * Nq) {
+                            const int g = K / 3, r = K - 3 * g;
+                            const TJ* o = cv + (size_t)g * 300 + ((a * 3 + r) * M + b) * 4;
+                            if (c < Np) v = o[0] * phiJ[(size_t)g * Np + c];
+                            for (int l = 0; l < 3; ++l) v -= o[1 + l] * vq[((size_t)l * NPT + g) * NCM + c];
+                        } else {
+                            const int rr = K - 3 * Nq, x = Nq + rr;
+                            const TJ* o = cf + (size_t)rr * 125 + (a * M + b) * 5;
+                            if (c < Np) {
+                                v = o[0] * basis_row_t(tabJ, d, x)[c];
+                            } else {
+                                const int f = face_of_point(d, rr);
+                                const int l = c - Np - fpo[f];
+                                if (l >= 0 && l < d.nfp[f])
+                                    v = o[1] * tabJ[d.ttab[f] + (size_t)(rr - d.soff[f]) * d.nfp[f] + l];
+                            }
+                            for (int l = 0; l < 3; ++l) v -= o[2 + l] * vq[((size_t)l * NPT + x) * NCM + c];
+                        }
+                    }
+                    vv[u] = v;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    if (base + u * NTH < kc * STP) sT[base + u * NTH] = vv[u];
             }
             __syncthreads();
             if (act) gemm_chunk(sR, sT, kc, ti, tc, acc);
