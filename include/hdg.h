@@ -92,13 +92,18 @@ typedef struct {
 
 /* Solver parameters (hdg_set_params).  tau: constant scalar stabilization of
  * eq. num-flux-hdg; visc_law 0: mu = 1/Re, 1: mu = C1 T^1.5 / (T + S) / Re
- * with T = gamma (gamma-1) M^2 e (eq. sutherland, eq. tgv-sutherland). */
+ * with T = gamma (gamma-1) M^2 e (eq. sutherland, eq. tgv-sutherland).
+ * tau_mode 0: the constant tau; 1: the state-dependent stabilization
+ * tau(uhat) = |vhat . n| + chat + mu(That) / h_K per face point (a wave speed
+ * plus a viscous part over the element length h_K = |K|^{1/d}; the reading of
+ * the paper's description), differentiated exactly in the Jacobians. */
 typedef struct {
     double tau;
     int32_t visc_law;
     double suth_c1;
     double suth_s;
     int32_t precision;            /* HDG_PREC_* */
+    int32_t tau_mode;             /* 0 constant tau, 1 state-dependent */
 } hdg_params;
 
 typedef struct {

@@ -35,7 +35,7 @@ from __future__ import annotations
 import numpy as np
 
 from .mesh import Connectivity
-from .physics import Physics, convective_flux, numerical_flux, viscous_flux
+from .physics import Physics, convective_flux, numerical_flux, stabilization, viscous_flux
 from .refelem import RefElem
 
 H_CS = 1e-30  # complex-step size
@@ -97,6 +97,7 @@ class Problem:
         self.conn = Connectivity(mesh, self.p)
         self.ph = Physics(prob.gamma, prob.re, prob.pr, prob.mach, prob.visc_law, prob.suth_c1, prob.suth_s)
         self.tau = prob.tau
+        self.tau_mode = int(getattr(prob, "tau_mode", 0))     # 0 constant tau, 1 state-dependent
         self.dt = prob.dt
         self.a_ii = prob.a_ii
         self.U = np.asarray(prob.U, float)
@@ -161,7 +162,8 @@ class Problem:
             q_s = np.swapaxes(np.moveaxis(Qe @ r.phif[f].T, -1, -3), -1, -2)
             uh_s = np.swapaxes(UHe[..., f, :, :] @ r.mu.T, -1, -2)   # [..., s, a]
             nu_s = None if nu_nodes is None else r.phif[f] @ nu_nodes
-            fhat = numerical_flux(u_s, uh_s, q_s, nu_s, G.n[f], self.tau, ph)
+            tau = self.tau if self.tau_mode == 0 else stabilization(uh_s, G.n[f], G.W.sum() ** (1.0 / self.d), ph)
+            fhat = numerical_flux(u_s, uh_s, q_s, nu_s, G.n[f], tau, ph)
             Ru = Ru + self.dt * np.einsum("s,...sa,sj->...aj", G.omega[f], fhat, r.phif[f], optimize=True)
             Rq = Rq - np.einsum("s,...sa,sk,sj->...kaj", G.omega[f], uh_s, G.n[f], r.phif[f], optimize=True)
             tag = int(self.bnd[e, f])

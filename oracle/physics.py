@@ -98,7 +98,22 @@ def numerical_flux(u, uh, q, nu, n, tau, ph: Physics):
 
     ``u`` is the element's interior trace, ``uh`` the single-valued trace,
     ``q`` the element's gradient trace, ``n[..., k]`` the outward unit normal and
-    ``tau`` a constant scalar (the reading of the face stabilization).
+    ``tau`` a constant scalar (the reading of the face stabilization), or an
+    array of one value per point (``[..., s]``, the state-dependent variant).
     """
     F = convective_flux(uh, ph) - viscous_flux(uh, q, nu, ph)
+    tau = np.asarray(tau)
+    if tau.ndim:
+        tau = tau[..., None]
     return np.einsum("...ak,...k->...a", F, n) + tau * (u - uh)
+
+
+def stabilization(uh, n, h, ph: Physics):
+    """State-dependent stabilization tau = |vhat . n| + chat + mu(That) / h (Sec. 2.2
+    describes it as a wave speed plus a viscous part over a length; h is the
+    element's length scale |K|^{1/d}).  |x| is written sqrt(x^2) so that the
+    complex-step derivative is sign(x) (x != 0)."""
+    rho, v, E, p = primitives(uh, ph.gamma)
+    vn = np.einsum("...k,...k->...", v, n)
+    c = np.sqrt(ph.gamma * p / rho)
+    return np.sqrt(vn * vn) + c + viscosity(uh, ph) / h

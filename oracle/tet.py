@@ -39,7 +39,7 @@ import numpy as np
 from scipy.special import roots_jacobi
 
 from .mesh import master
-from .physics import Physics, convective_flux, numerical_flux, viscous_flux
+from .physics import Physics, convective_flux, numerical_flux, stabilization, viscous_flux
 
 H_CS = 1e-30
 
@@ -382,6 +382,7 @@ class TetProblem:
         self.conn = TetConnectivity(mesh, self.m)
         self.ph = Physics(prob.gamma, prob.re, prob.pr, prob.mach, prob.visc_law, prob.suth_c1, prob.suth_s)
         self.tau, self.dt, self.a_ii = prob.tau, prob.dt, prob.a_ii
+        self.tau_mode = int(getattr(prob, "tau_mode", 0))     # 0 constant tau, 1 state-dependent
         self.U = np.asarray(prob.U, float)
         self.Q = np.asarray(prob.Q, float)
         self.UH = np.asarray(prob.UH, float)
@@ -452,7 +453,8 @@ class TetProblem:
             u_s = np.swapaxes(Ue @ ph_f.T, -1, -2)
             q_s = np.swapaxes(np.moveaxis(Qe @ ph_f.T, -1, -3), -1, -2)
             uh_s = np.swapaxes(UHe[f] @ G.mu[f].T, -1, -2)
-            fhat = numerical_flux(u_s, uh_s, q_s, None, G.n[f], self.tau, ph)
+            tau = self.tau if self.tau_mode == 0 else stabilization(uh_s, G.n[f], G.W.sum() ** (1.0 / 3.0), ph)
+            fhat = numerical_flux(u_s, uh_s, q_s, None, G.n[f], tau, ph)
             Ru = Ru + self.dt * np.einsum("s,...sa,sj->...aj", G.omega[f], fhat, ph_f, optimize=True)
             Rq = Rq - np.einsum("s,...sa,sk,sj->...kaj", G.omega[f], uh_s, G.n[f], ph_f, optimize=True)
             tag = int(self.bnd[e, f])

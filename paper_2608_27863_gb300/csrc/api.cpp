@@ -244,6 +244,7 @@ int create_device(hdg_ctx* h) {
     if (const char* s = std::getenv("HDG_ELIM_MINB")) h->elim_minb = std::atoi(s) == 1 ? 1 : 2;
     if ((rc = dev_alloc(h, &h->d_vcoef, (size_t)h->chunk * h->m * h->m * d * h->NCOEF * h->Nq))) return rc;
     if ((rc = dev_alloc(h, &h->d_fcoef, (size_t)h->chunk * h->nf * h->m * h->m * h->NCOEF * h->Nfq))) return rc;
+    if ((rc = dev_alloc(h, &h->d_taup, (size_t)h->chunk * h->nf * h->Nfq))) return rc;
     h->device = true;
     return HDG_OK;
 }
@@ -302,7 +303,9 @@ int hdg_set_params(hdg_handle h, const hdg_params* prm) {
         return fail(h, HDG_EINVAL, "Sutherland constants must be positive");
     if (prm->precision < HDG_PREC_FP64 || prm->precision > HDG_PREC_MIXED_3XTF32)
         return fail(h, HDG_EUNSUPPORTED, "precision mode not available");
+    if (prm->tau_mode != 0 && prm->tau_mode != 1) return fail(h, HDG_EINVAL, "tau_mode must be 0 or 1");
     h->phys.tau = prm->tau;
+    h->phys.tau_mode = prm->tau_mode;
     h->phys.visc_law = prm->visc_law;
     h->phys.c1 = prm->suth_c1;
     h->phys.s = prm->suth_s;

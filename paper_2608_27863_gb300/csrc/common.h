@@ -68,6 +68,7 @@ struct Phys {
     double gamma, re, pr, mach, tau;
     int visc_law;
     double c1, s;
+    int tau_mode = 0;     // 0: constant tau; 1: state-dependent tau(uhat) = |v.n| + c + mu / h
 };
 
 struct DeviceTables {
@@ -123,6 +124,7 @@ struct hdg_ctx {
     double* d_vcoef = nullptr;             // [chunk][m][m][d][NCOEF][Nq]
     double* d_fcoef = nullptr;             // [chunk][nf][m][m][NCOEF][Nfq]
     double* d_dq0 = nullptr;               // [E][d][m][Np]
+    double* d_taup = nullptr;              // [chunk][nf][Nfq] per-point tau (state-dependent stabilization)
     int32_t* d_status = nullptr;           // [1]
     int32_t* d_ftag = nullptr;             // [E][nf] boundary tags, NULL for fully periodic meshes
     double* d_ub = nullptr;                // [m] state of tag-1 boundary faces

@@ -79,6 +79,8 @@ struct PointArgs {
     const double* ub;           // [m] boundary state of tag-1 faces
     const double* ubf;          // [F][m][Nfp] nodal tag-1 boundary data (canonical order), or NULL
     double ew;                  // wall internal energy c_v T_w of tag-3 faces
+    int tau_mode;               // 0: constant tau; 1: state-dependent tau(uhat) (stab_tau)
+    double* taup;               // [chunk][nf][Nfq] tau at the face points (tau_mode 1), for the face terms
     int64_t e0;
 };
 
@@ -295,6 +297,11 @@ __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
         for (int k = 0; k < D; ++k) nrm += nw[k] * nw[k];
         nrm = sqrt(nrm);
         const double ws = T.wf[s];
+        double nh[D];
+        for (int k = 0; k < D; ++k) nh[k] = nw[k] / nrm;
+        const double hinv = A.tau_mode ? 1.0 / pow(double(1 << D) * detJ, 1.0 / D) : 0.0;   // |K|^{-1/d}
+        const double tau_s = A.tau_mode ? stab_tau<D, double, double>(uh, nh, hinv, ph) : A.tau;
+        if (A.taup) A.taup[(el * NF + f) * NFQ + s] = tau_s;
         {
             double Fc[M][D], Fv[M][D];
             conv_flux<D, double, double>(uh, ph, Fc);
@@ -303,7 +310,7 @@ __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
             for (int a = 0; a < M; ++a) {
                 double fn = 0.0;
                 for (int k = 0; k < D; ++k) fn += (Fc[a][k] - Fv[a][k]) * nw[k];
-                const double fh = ws * (fn + nrm * A.tau * (u[a] - uh[a]));
+                const double fh = ws * (fn + nrm * tau_s * (u[a] - uh[a]));
                 sFH[(f * M + a) * NFQ + s] = fh;
                 const double ub_a = tag == 1 ? boundary_state<NF, M, NFP>(A.ub, A.ubf, A.e2f, A.perm, T.mu, e, f, s, a) : 0.0;
                 sFB[(f * M + a) * NFQ + s] = boundary_form<M>(tag, a, fh, ws * nrm, u, uh, ub_a, A.ew);
@@ -312,17 +319,22 @@ __global__ void __launch_bounds__(NTH) k_point(PointArgs A) {
         TJ uhj[M], qj[M][D], nwj[D];
         for (int a = 0; a < M; ++a) { uhj[a] = (TJ)uh[a]; for (int l = 0; l < D; ++l) qj[a][l] = (TJ)q[a][l]; }
         for (int k = 0; k < D; ++k) nwj[k] = (TJ)nw[k];
-        const TJ nuj = (TJ)nuv, wsj = (TJ)ws, taun = (TJ)(nrm * A.tau);
+        const TJ nuj = (TJ)nuv, wsj = (TJ)ws, taun = (TJ)(nrm * tau_s);
+        TJ nhj[D];
+        for (int k = 0; k < D; ++k) nhj[k] = (TJ)nh[k];
         for (int b = 0; b < M; ++b) {
             DirT<TJ> ud[M];
             for (int a = 0; a < M; ++a) ud[a] = {uhj[a], a == b ? TJ(1) : TJ(0)};
             DirT<TJ> Fc[M][D], Fv[M][D];
             conv_flux<D, DirT<TJ>, TJ>(ud, pj, Fc);
             visc_flux<D, DirT<TJ>, TJ>(ud, qj, nuj, pj, Fv);
+            // d tau / d uhat_b (state-dependent stabilization): (u_a - uhat_a) |nw| d tau / d uhat_b
+            const TJ dtau = A.tau_mode ? (TJ)nrm * stab_tau<D, DirT<TJ>, TJ>(ud, nhj, (TJ)hinv, pj).t : TJ(0);
             for (int a = 0; a < M; ++a) {
                 TJ fn = 0;
                 for (int k = 0; k < D; ++k) fn += (Fc[a][k].t - Fv[a][k].t) * nwj[k];
                 if (a == b) fn -= taun;
+                fn += ((TJ)u[a] - uhj[a]) * dtau;
                 fc[((((size_t)f * M + a) * M + b) * NCOEF + 0) * NFQ + s] = wsj * fn;
             }
         }
@@ -399,6 +411,7 @@ struct BlkArgs {
     Regions<TL> R;
     double dt, a_ii, tau;
     double ew;                              // wall internal energy of tag-3 faces
+    const double* taup;                     // [chunk][nf][Nfq] per-point tau (state-dependent), or NULL
     int64_t e0;
 };
 
@@ -549,9 +562,18 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
     const double* NW = G + 1 + D * D;
     const double* Jg = G + 1;
     (void)Jg;
+    __shared__ TA mft[NFP * NFP];          // state-dependent tau: face mass weighted by tau(s)
     for (int f = 0; f < NF; ++f) {
         const TA* fsrc = reinterpret_cast<const TA*>(A.fcoef) + ((((size_t)el * NF + f) * M + a) * M + b) * (size_t)(NCOEF * NFQ);
         for (int idx = tid; idx < NCOEF * NFQ; idx += NTH) Fc[idx] = fsrc[idx];
+        if (A.taup)
+            for (int idx = tid; idx < NFP * NFP; idx += NTH) {
+                const int lam = idx / NFP, l = idx - lam * NFP;
+                double w = 0.0;
+                for (int q = 0; q < NFQ; ++q)
+                    w += T.wf[q] * A.taup[(el * NF + f) * NFQ + q] * T.mu[q * NFP + lam] * T.mu[q * NFP + l];
+                mft[idx] = (TA)w;
+            }
         __syncthreads();
         for (int idx = tid; idx < NFQ * NCB; idx += NTH) {
             int s = idx / NCB, c = idx - s * NCB;
@@ -586,12 +608,15 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
             const int64_t trow = (f * M + a) * NFP + lam;
             const int64_t irow = a * NP + T.fnode[f * NFP + lam];
             if (c < NP) {
-                TA vu = 0;                         // face mass coupling of node c, if it lies on face f
+                TA vu = 0, vut = 0;                // face mass coupling of node c, if it lies on face f
                 for (int k = 0; k < D; ++k) {
                     int nfc = T.node_face[c * D + k];
-                    if (nfc >= 0 && nfc / NFP == f) vu = tmf[lam * NFP + (nfc - f * NFP)];
+                    if (nfc >= 0 && nfc / NFP == f) {
+                        vu = tmf[lam * NFP + (nfc - f * NFP)];
+                        if (A.taup) vut = mft[lam * NFP + (nfc - f * NFP)];
+                    }
                 }
-                if (a == b) v += taun * vu;
+                if (a == b) v += A.taup ? nrmt * vut : taun * vu;
                 const int col = b * NP + c;
                 A21[trow * A.R.a21_rs + col] = flux_row ? (TL)v : (TL)(cu * nrmt * vu);
                 if (FACC)   // one thread per (node, column) within a face; faces run one after another
@@ -1166,9 +1191,11 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
     pa.rb = RG.rb; pa.rb_es = RG.rb_es; pa.rb_rs = RG.rb_rs;
     pa.vcoef = h->d_vcoef; pa.fcoef = h->d_fcoef; pa.dq0 = h->d_dq0;
     pa.ftag = h->d_ftag; pa.ub = h->d_ub; pa.ubf = h->d_ubf; pa.ew = h->e_wall;
+    pa.tau_mode = h->phys.tau_mode; pa.taup = h->phys.tau_mode ? h->d_taup : nullptr;
     BlkArgs<double> ba;
     ba.vcoef = h->d_vcoef; ba.fcoef = h->d_fcoef; ba.geo = h->d_geo; ba.tab = h->tab; ba.ftag = h->d_ftag;
     ba.ew = h->e_wall;
+    ba.taup = h->phys.tau_mode ? h->d_taup : nullptr;
     ba.R = RG; ba.dt = la.dt; ba.a_ii = la.a_ii; ba.tau = h->phys.tau;
     for (int64_t e0 = 0; e0 < h->E; e0 += h->chunk) {
         const int64_t ne = std::min<int64_t>(h->chunk, h->E - e0);

@@ -885,9 +885,11 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
     pa.rb = RM.rb; pa.rb_es = RM.rb_es; pa.rb_rs = RM.rb_rs;
     pa.vcoef = h->d_vcoef; pa.fcoef = h->d_fcoef; pa.dq0 = h->d_dq0;
     pa.ftag = h->d_ftag; pa.ub = h->d_ub; pa.ubf = h->d_ubf; pa.ew = h->e_wall;
+    pa.tau_mode = h->phys.tau_mode; pa.taup = h->phys.tau_mode ? h->d_taup : nullptr;
     BlkArgs<float> ba;
     ba.vcoef = h->d_vcoef; ba.fcoef = h->d_fcoef; ba.geo = h->d_geo; ba.tab = h->tab; ba.ftag = h->d_ftag;
     ba.ew = h->e_wall;
+    ba.taup = h->phys.tau_mode ? h->d_taup : nullptr;
     ba.R = RM; ba.dt = la.dt; ba.a_ii = la.a_ii; ba.tau = h->phys.tau;
     for (int64_t e0 = 0; e0 < h->E; e0 += h->chunk) {
         const int64_t ne = std::min<int64_t>(h->chunk, h->E - e0);

@@ -29,6 +29,10 @@ template <class S> __device__ __forceinline__ DirT<S> zero_like(DirT<S>) { retur
 __device__ __forceinline__ double zero_like(double) { return 0.0; }
 __device__ __forceinline__ float zero_like(float) { return 0.0f; }
 
+template <class S> __device__ __forceinline__ DirT<S> dabs(DirT<S> a) { return a.v < S(0) ? DirT<S>{-a.v, -a.t} : a; }
+__device__ __forceinline__ double dabs(double a) { return fabs(a); }
+__device__ __forceinline__ float dabs(float a) { return fabsf(a); }
+
 using Dir = DirT<double>;
 
 // Physical constants in the evaluation type.
@@ -120,6 +124,26 @@ __device__ __forceinline__ void visc_flux(const T* u, const S (*q)[D], S nu, con
         }
         F[M - 1][j] = fe + nu * q[M - 1][j];
     }
+}
+
+// State-dependent stabilization (an option of the face stabilization of eq.
+// num-flux-hdg): tau = |vhat . n| + chat + mu(That) / h, with n the unit normal
+// and h_inv = 1 / h the inverse element length scale |K|^{-1/d}; T = DirT gives
+// its directional derivative with respect to uhat.
+template <int D, class T, class S>
+__device__ __forceinline__ T stab_tau(const T* uh, const S* nh, S h_inv, const PhysT<S>& ph) {
+    constexpr int M = D + 2;
+    T irho = recip(uh[0]);
+    T vn = zero_like(uh[0]);
+    T kin = zero_like(uh[0]);
+    for (int k = 0; k < D; ++k) {
+        T v = uh[1 + k] * irho;
+        vn = vn + v * nh[k];
+        kin = kin + v * uh[1 + k];
+    }
+    T rhoe = uh[M - 1] - kin * ph.half;            // rho e = rho E - rho |v|^2 / 2
+    T c = dsqrt(rhoe * ph.gm1 * (ph.gm1 + S(1)) * irho);
+    return dabs(vn) + c + viscosity(rhoe * irho, ph) * h_inv;
 }
 
 }  // namespace hdg

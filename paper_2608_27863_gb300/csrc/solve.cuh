@@ -20,6 +20,7 @@ struct ResArgs {
     double dt, a_ii;
     PhysT<double> ph;
     double tau;
+    int tau_mode;               // 0 constant tau, 1 state-dependent (stab_tau)
     DeviceTables tab;
     const double* geo;
     const int32_t* e2f; const int32_t* perm;
@@ -172,6 +173,12 @@ __global__ void __launch_bounds__(NTH) k_residual(ResArgs A) {
         double nrm = 0.0;
         for (int k = 0; k < D; ++k) nrm += nw[k] * nw[k];
         nrm = sqrt(nrm);
+        double tau_s = A.tau;
+        if (A.tau_mode) {
+            double nh[D];
+            for (int k = 0; k < D; ++k) nh[k] = nw[k] / nrm;
+            tau_s = stab_tau<D, double, double>(uh, nh, 1.0 / pow(double(1 << D) * detJ, 1.0 / D), ph);
+        }
         double Fc[M][D], Fv[M][D];
         conv_flux<D, double, double>(uh, ph, Fc);
         visc_flux<D, double, double>(uh, q, nuv, ph, Fv);
@@ -179,7 +186,7 @@ __global__ void __launch_bounds__(NTH) k_residual(ResArgs A) {
         for (int a = 0; a < M; ++a) {
             double fn = 0.0;
             for (int k = 0; k < D; ++k) fn += (Fc[a][k] - Fv[a][k]) * nw[k];
-            const double fh = T.wf[s] * (fn + nrm * A.tau * (u[a] - uh[a]));
+            const double fh = T.wf[s] * (fn + nrm * tau_s * (u[a] - uh[a]));
             sFH[(f * M + a) * NFQ + s] = fh;
             const double ub_a = tag == 1 ? boundary_state<NF, M, NFP>(A.ub, A.ubf, A.e2f, A.perm, T.mu, e, f, s, a) : 0.0;
             sFB[(f * M + a) * NFQ + s] = boundary_form<M>(tag, a, fh, T.wf[s] * nrm, u, uh, ub_a, A.ew);
@@ -403,7 +410,7 @@ int run_residual(hdg_ctx* h, const LinArgs& la, double* Rq, double* Ru, double* 
     HDG_CK(cudaFuncSetAttribute(k_residual<C, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     ResArgs ra;
     ra.U = la.U; ra.Q = la.Q; ra.UH = la.UH; ra.Ustar = la.Ustar; ra.nu = la.nu; ra.dt = la.dt; ra.a_ii = la.a_ii;
-    ra.ph = phys_t<double>(h->phys); ra.tau = h->phys.tau; ra.tab = h->tab; ra.geo = h->d_geo; ra.e2f = h->d_e2f; ra.perm = h->d_perm;
+    ra.ph = phys_t<double>(h->phys); ra.tau = h->phys.tau; ra.tau_mode = h->phys.tau_mode; ra.tab = h->tab; ra.geo = h->d_geo; ra.e2f = h->d_e2f; ra.perm = h->d_perm;
     ra.Rq = Rq; ra.Ru = Ru; ra.rk = h->d_rk; ra.part = h->d_part; ra.ftag = h->d_ftag; ra.ub = h->d_ub;
     ra.ubf = h->d_ubf; ra.ew = h->e_wall;
     k_residual<C, NTH><<<(unsigned)h->E, NTH, smem, h->stream>>>(ra);

@@ -65,6 +65,7 @@ struct KArgs {
     const double* U; const double* Q; const double* UH; const double* Ustar;
     double* mat; double* rec; double* work; int64_t wstride;
     PhysT<double> ph; double dt, a_ii, tau; const double* ub; double ew;
+    int tau_mode;                                         // 0 constant tau, 1 state-dependent (stab_tau)
     int32_t* status;
     double* Rq; double* Ru; double* rk; double* part;     // residual evaluation outputs
 };
@@ -627,9 +628,10 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
             const int r = x - Nq, f = face_of_point(d, r), tag = d.tag[f];
             const double* nw = gf + r * 3;
             const double nrm = sqrt(nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2]);
-            const double taun = A.tau * nrm;
             double uh[M];
             for (int a = 0; a < M; ++a) uh[a] = ph[r * M + a];
+            const double nh[3] = {nw[0] / nrm, nw[1] / nrm, nw[2] / nrm};
+            const double taun = nrm * (A.tau_mode ? stab_tau<3, double, double>(uh, nh, d.hinv, P) : A.tau);
             double Fc[M][3], Fv[M][3];
             conv_flux<3, double, double>(uh, P, Fc);
             visc_flux<3, double, double>(uh, ql, 0.0, P, Fv);
@@ -663,11 +665,12 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
                 Dir Fcd[M][3], Fvd[M][3];
                 conv_flux<3, Dir, double>(ud, P, Fcd);
                 visc_flux<3, Dir, double>(ud, q, 0.0, P, Fvd);
+                const double dtau = A.tau_mode ? nrm * stab_tau<3, Dir, double>(ud, nh, d.hinv, P).t : 0.0;
                 for (int a = 0; a < M; ++a) {
                     double fn = 0.0;
                     for (int k = 0; k < 3; ++k) fn += (Fcd[a][k].t - Fvd[a][k].t) * nw[k];
                     put(a, b, 0, a == b ? taun : 0.0);
-                    put(a, b, 1, fn - (a == b ? taun : 0.0));
+                    put(a, b, 1, fn - (a == b ? taun : 0.0) + (u[a] - uh[a]) * dtau);
                 }
                 for (int l = 0; l < 3; ++l) {
                     double qe[M][3];
@@ -1105,13 +1108,15 @@ __device__ void residual_element(const KArgs& A, const TetElem& d, int64_t e, do
             }
             const double* nw = gf + r * 3;
             const double nrm = sqrt(nw[0] * nw[0] + nw[1] * nw[1] + nw[2] * nw[2]);
+            const double nh[3] = {nw[0] / nrm, nw[1] / nrm, nw[2] / nrm};
+            const double tau_s = A.tau_mode ? stab_tau<3, double, double>(uh, nh, d.hinv, A.ph) : A.tau;
             double Fc[M][3], Fv[M][3];
             conv_flux<3, double, double>(uh, A.ph, Fc);
             visc_flux<3, double, double>(uh, q, 0.0, A.ph, Fv);
             for (int a = 0; a < M; ++a) {
                 double fn = 0.0;
                 for (int k = 0; k < 3; ++k) fn += (Fc[a][k] - Fv[a][k]) * nw[k];
-                const double fh = fn + A.tau * nrm * (u[a] - uh[a]);
+                const double fh = fn + tau_s * nrm * (u[a] - uh[a]);
                 rf[r * M + a] = A.dt * fh;
                 rb[r * M + a] = boundary_form<M>(tag, a, fh, nrm, u, uh, tag == 1 ? A.ub[a] : 0.0, A.ew);
             }
@@ -1405,6 +1410,7 @@ int linearize(hdg_ctx* h, const double* U, const double* Q, const double* UH, co
     A.mat = c->d_mat; A.rec = c->d_rec; A.work = c->d_work; A.wstride = c->work_stride;
     A.ph = phys_t<double>(h->phys); A.dt = dt; A.a_ii = a_ii; A.tau = h->phys.tau;
     A.ub = h->d_ub; A.ew = h->e_wall; A.status = h->d_status;
+    A.tau_mode = h->phys.tau_mode;
     cudaStream_t st = h->stream;
     if (h->precision != HDG_PREC_FP64 && !c->d_vals32) {
         std::string err;
@@ -1483,6 +1489,7 @@ KArgs base_args(hdg_ctx* h, const double* U, const double* Q, const double* UH, 
     A.mat = c->d_mat; A.rec = c->d_rec; A.work = c->d_work; A.wstride = c->work_stride;
     A.ph = phys_t<double>(h->phys); A.dt = dt; A.a_ii = a_ii; A.tau = h->phys.tau;
     A.ub = h->d_ub; A.ew = h->e_wall; A.status = h->d_status;
+    A.tau_mode = h->phys.tau_mode;
     return A;
 }
 }  // namespace

@@ -55,6 +55,7 @@ struct TetElem {
     int64_t koff;      // element trace residual R_uhat^K [t] (residual evaluation)
     int32_t vtab, ftab[4], ttab[4], pad;   // table offsets: volume, face (p, pF, code), trace (pF)
     double detJ, Jinv[9];                  // affine elements
+    double hinv;                           // |K|^{-1/3} (state-dependent stabilization)
 };
 
 struct Ctx {

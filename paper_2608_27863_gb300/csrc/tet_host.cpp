@@ -542,6 +542,7 @@ int create_host(hdg_ctx* h, const hdg_tet_mesh* mesh, std::string& err) {
             if (!(d.detJ > 0.0)) { err = "non-positive Jacobian (element orientation)"; return HDG_EINVAL; }
             for (int r = 0; r < 3; ++r)
                 for (int k = 0; k < 3; ++k) d.Jinv[r * 3 + k] = Ji[r][k];
+            d.hinv = 1.0 / std::cbrt(4.0 / 3.0 * d.detJ);
             continue;
         }
         c->n_curved += 1;
@@ -557,15 +558,18 @@ int create_host(hdg_ctx* h, const hdg_tet_mesh* mesh, std::string& err) {
         };
         d.goff = (int64_t)c->gvol.size();
         const VolTab& V = vt[p];
+        double vol = 0.0;
         for (int g = 0; g < d.Nq; ++g) {
             double J[3][3], Ji[3][3];
             jac_at(&V.xq[g * 3], J);
             const double det = jac_inv(J, Ji);
             if (!(det > 0.0)) { err = "non-positive Jacobian at a quadrature point"; return HDG_EINVAL; }
+            vol += V.wq[g] * det;
             c->gvol.push_back(V.wq[g] * det);
             for (int r = 0; r < 3; ++r)
                 for (int k = 0; k < 3; ++k) c->gvol.push_back(Ji[r][k]);
         }
+        d.hinv = 1.0 / std::cbrt(vol);
         d.gfoff = (int64_t)c->gface.size();
         for (int f = 0; f < 4; ++f) {
             const TriTab& T = tt[d.pf[f]];

@@ -59,7 +59,7 @@ class hdg_mesh(ctypes.Structure):
 
 class hdg_params(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_double), ("visc_law", ctypes.c_int32), ("suth_c1", ctypes.c_double),
-                ("suth_s", ctypes.c_double), ("precision", ctypes.c_int32)]
+                ("suth_s", ctypes.c_double), ("precision", ctypes.c_int32), ("tau_mode", ctypes.c_int32)]
 
 
 class hdg_sizes(ctypes.Structure):
@@ -202,8 +202,8 @@ def hdg_last_error(h):
     return lib().hdg_last_error(h).decode()
 
 
-def hdg_set_params(h, tau=5.0, visc_law=0, suth_c1=1.4042, suth_s=0.40417, precision=HDG_PREC_FP64):
-    prm = hdg_params(tau, visc_law, suth_c1, suth_s, precision)
+def hdg_set_params(h, tau=5.0, visc_law=0, suth_c1=1.4042, suth_s=0.40417, precision=HDG_PREC_FP64, tau_mode=0):
+    prm = hdg_params(tau, visc_law, suth_c1, suth_s, precision, tau_mode)
     _check(h, lib().hdg_set_params(h, ctypes.byref(prm)))
 
 

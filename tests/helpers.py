@@ -12,7 +12,8 @@ def create(P, host_only=False):
                      m.bnd_tag if np.any(m.bnd_tag) else None, P.p, P.gamma, P.re, P.pr, P.mach,
                      host_only=host_only)
     if not host_only:
-        H.hdg_set_params(h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s)
+        H.hdg_set_params(h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s,
+                         tau_mode=getattr(P, "tau_mode", 0))
         if np.any(m.bnd_tag == 1):
             ubc = np.asarray(P.ubc, dtype=np.float64)
             if ubc.ndim == 1:
