@@ -243,3 +243,64 @@ def test_tet_autotune_and_panel_width_parity(H):
         assert errs.max() < TOL, errs.max()
     finally:
         H.hdg_destroy(h)
+
+
+def test_config4_full_size_sampled():
+    """The 100,800-element config-4 mesh in the benchmarked launch (one persistent
+    FP64 launch): seeded sample of block rows, their right-hand sides and the
+    recovery of the elements touching them, against the oracle."""
+    from paper_2608_27863_gb300 import hdg as H
+    mesh = tm.config4_mesh()
+    prob = tm.config4_problem(mesh)
+    conn = ot.TetConnectivity(mesh)
+    prob.U, prob.Q, prob.UH, prob.Ustar = tm.packed_state(mesh, tm.sinusoids(prob.gamma, prob.mach, 3, 1e-3),
+                                                          conn.nfp, prob.ubc, 7)
+    h = H.hdg_create_tet(mesh.vert_xyz, mesh.elem_vert, mesh.periodic_map, mesh.bnd_tag, mesh.elem_p, mesh.geo,
+                         prob.gamma, prob.re, prob.pr, prob.mach)
+    try:
+        H.hdg_set_params(h, tau=prob.tau)
+        H.hdg_set_bc_state(h, 1, prob.ubc)
+        d = {k: torch.tensor(getattr(prob, k), dtype=torch.float64, device="cuda") for k in ("U", "Q", "UH", "Ustar")}
+        H.hdg_linearize_condense(h, d["U"], d["Q"], d["UH"], d["Ustar"], None, prob.dt, prob.a_ii)
+        assert H.hdg_status(h) == H.HDG_OK
+        s = H.hdg_tet_query(h)
+        L = H.hdg_tet_layout(h)
+        rng = np.random.default_rng(2024)
+        faces = sorted(int(F) for F in rng.choice(conn.n_faces, 3, replace=False))
+        # include a wall face and a face of a p = 4 element
+        faces.append(int(np.nonzero(conn.f2e[:, 1, 0] < 0)[0][0]))
+        faces.append(int(conn.e2f[int(np.nonzero(mesh.elem_p == 4)[0][0]), 0]))
+        blocks = [b for F in faces for b in range(conn.rowptr[F], conn.rowptr[F + 1])]
+        pb = ot.TetProblem(prob)
+        ov, cache = pb.assemble(blocks=blocks)
+        vals = torch.zeros(s["n_vals"], dtype=torch.float64, device="cuda")
+        H.hdg_get_blocks(h, vals)
+        g = torch.zeros(s["n_trace"], dtype=torch.float64, device="cuda")
+        H.hdg_trace_rhs(h, g)
+        gv, gg = vals.cpu().numpy(), g.cpu().numpy()
+        scale = np.mean([np.linalg.norm(ov[b]) for b in blocks])
+        for b in blocks:
+            F = int(np.searchsorted(conn.rowptr, b, side="right") - 1)
+            bsF = conn.hoff[F + 1] - conn.hoff[F]
+            bsG = conn.hoff[conn.col[b] + 1] - conn.hoff[conn.col[b]]
+            got = gv[L["boff"][b]:L["boff"][b + 1]].reshape(bsG, bsF).T
+            err = np.linalg.norm(got - ov[b]) / max(np.linalg.norm(ov[b]), 1e-3 * scale)
+            assert err < TOL, (b, err)
+        for F in faces:
+            ref = np.zeros(conn.hoff[F + 1] - conn.hoff[F])
+            for (e, f) in sorted(tuple(x) for x in conn.f2e[F] if x[0] >= 0):
+                o = pb.element_trace_offsets(e)
+                ref += cache[e]["g"][o[f]:o[f + 1]]
+            assert np.linalg.norm(gg[conn.hoff[F]:conn.hoff[F + 1]] - ref) < TOL * np.linalg.norm(ref), F
+        dUH = np.cos(0.3 * np.arange(s["n_trace"]))
+        dQ = torch.zeros(3 * s["n_u"], dtype=torch.float64, device="cuda")
+        dU = torch.zeros(s["n_u"], dtype=torch.float64, device="cuda")
+        H.hdg_recover_interior(h, torch.tensor(dUH, device="cuda"), dQ, dU)
+        dQc, dUc = dQ.cpu().numpy(), dU.cpu().numpy()
+        for e in sorted(cache):
+            oq, ou = pb.recover(e, cache[e], dUH)
+            ref = np.concatenate([oq.ravel(), ou.ravel()])
+            got = np.concatenate([dQc[conn.qoff[e]:conn.qoff[e + 1]], dUc[conn.uoff[e]:conn.uoff[e + 1]]])
+            assert np.linalg.norm(got - ref) < TOL * np.linalg.norm(ref), e
+    finally:
+        H.hdg_destroy(h)
