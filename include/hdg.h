@@ -12,8 +12,10 @@
  * matrix, and provides the trace matvec and the interior recovery that GMRES
  * consumes (Sec. 3.2).
  *
- * Conventions shared by every call
- * --------------------------------
+ * Conventions shared by every call on quadrilateral / hexahedral handles
+ * (tetrahedral handles, created by hdg_create_tet, use the packed layouts of
+ * the tetrahedral section at the end of this header)
+ * -----------------------------------------------------------------------
  *  d = 2 (quadrilaterals) or 3 (hexahedra), m = d + 2 conserved variables
  *  u = [rho, rho v_1..rho v_d, rho E]; degree p (1..3); element nodes are the
  *  tensor Gauss-Lobatto points, Np = (p+1)^d, node j = j1 + (p+1) j2 +
@@ -118,7 +120,7 @@ typedef struct {
 
 /* Build tables, connectivity, the BSR pattern and device storage (Sec. 2.2
  * spaces, Sec. 3.5 face partition).  Fails with HDG_EUNSUPPORTED for
- * non-affine elements, p outside 1..3 or boundary tags other than 0 / 1, and
+ * non-affine elements, p outside 1..3 or boundary tags outside 0..4, and
  * HDG_EINVAL for inconsistent meshes (a face shared by more than two
  * elements, a degenerate periodic face, tag 1 not marking exactly the faces
  * with a single element). */
