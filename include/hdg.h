@@ -122,8 +122,8 @@ typedef struct {
  * spaces, Sec. 3.5 face partition).  Fails with HDG_EUNSUPPORTED for
  * non-affine elements, p outside 1..3 or boundary tags outside 0..4, and
  * HDG_EINVAL for inconsistent meshes (a face shared by more than two
- * elements, a degenerate periodic face, tag 1 not marking exactly the faces
- * with a single element). */
+ * elements, a degenerate periodic face, boundary tags 1..4 not marking
+ * exactly the faces with a single element). */
 int hdg_create(hdg_handle* out, const hdg_mesh* mesh, int p, double gamma, double Re,
                double Pr, double Mach);
 /* Same as hdg_create without touching the GPU: connectivity and tables only;
