@@ -317,7 +317,8 @@ int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* 
  *    is compiled for (2 or 1 CTAs per SM); results differ only by rounding
  *    order;
  *  - mixed form: the elimination as one fused kernel (at 2 or 3 CTAs per
- *    SM) or split into an FP64 LU and two FP32 triangular solves,
+ *    SM) or split into an FP64 LU (panel width 16 or 8) and two FP32
+ *    triangular solves,
  *    the volume contraction as FP32 SIMT (blocks_mode 0) or
  *    3xTF32 tensor cores (1, 3-D), and, when requested as HDG_PREC_MIXED,
  *    the Schur product as FP32 SIMT (schur_mode 0) or 3xTF32 tensor cores

@@ -383,10 +383,14 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
             for (int bm : {1, 2, 0}) {
                 if (bm == 1 && h->d != 3) continue;
                 if (bm == 0 && free_schur) continue;
-                for (int ev : {0, 2, 3}) {       // elimination: split (0), fused at 2 or 3 CTAs per SM
-                    cand[n][0] = h->elim_nb; cand[n][1] = h->elim_minb; cand[n][2] = free_schur ? sm : h->schur_mode;
-                    cand[n][3] = bm; cand[n][4] = ev == 0 ? h->elim_mixed_minb : ev; cand[n][5] = h->blocks64_mode;
-                    cand[n][6] = ev == 0 ? 1 : 0; ++n;
+                // elimination: split with the interior LU at panel width 16 or 8 (ev 16, 8), or
+                // fused at 2 or 3 CTAs per SM (ev 2, 3)
+                for (int ev : {16, 8, 2, 3}) {
+                    const bool split = ev >= 8;
+                    cand[n][0] = split ? ev : h->elim_nb; cand[n][1] = h->elim_minb;
+                    cand[n][2] = free_schur ? sm : h->schur_mode;
+                    cand[n][3] = bm; cand[n][4] = split ? h->elim_mixed_minb : ev; cand[n][5] = h->blocks64_mode;
+                    cand[n][6] = split ? 1 : 0; ++n;
                 }
             }
         }

@@ -867,9 +867,10 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
     HDG_CK(cudaFuncSetAttribute(k_blocks_sf<C, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sf32));
     HDG_CK(cudaFuncSetAttribute(k_elim_mixed<C, NB, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
     HDG_CK(cudaFuncSetAttribute(k_elim_mixed<C, NB, 256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
-    const int sm_lu = lu_mixed_smem_bytes<C, NB>();
+    const int sm_lu = lu_mixed_smem_bytes<C, NB>();   // the 8-column variant needs less
     const int sm_trsm = (int)sizeof(float) * TrsmShape<C>::smem_floats;
     HDG_CK(cudaFuncSetAttribute(k_lu_mixed<C, NB, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_lu));
+    HDG_CK(cudaFuncSetAttribute(k_lu_mixed<C, 8, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_lu));
     HDG_CK(cudaFuncSetAttribute(k_trsm_z<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_trsm));
     HDG_CK(cudaFuncSetAttribute(k_trsm_w<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm_trsm));
     cudaStream_t st = h->stream;
@@ -916,7 +917,10 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
             // FP64 interior LU alone, then the FP32 border by two triangular solves
             using TS = TrsmShape<C>;
             constexpr int NCT = (C::NT + TS::CW - 1) / TS::CW;
-            k_lu_mixed<C, NB, 256><<<(unsigned)ne, 256, sm_lu, st>>>(RM, h->d_mpiv, e0, h->d_status);
+            if (h->elim_nb == 8)   // interior LU panel width (the autotuner's elim_nb)
+                k_lu_mixed<C, 8, 256><<<(unsigned)ne, 256, sm_lu, st>>>(RM, h->d_mpiv, e0, h->d_status);
+            else
+                k_lu_mixed<C, NB, 256><<<(unsigned)ne, 256, sm_lu, st>>>(RM, h->d_mpiv, e0, h->d_status);
             k_trsm_z<C><<<(unsigned)(ne * NCT), TS::NTH, sm_trsm, st>>>(RM, h->d_mpiv, e0);
             k_trsm_w<C><<<(unsigned)(ne * NCT), TS::NTH, sm_trsm, st>>>(RM, e0);
         } else if (h->elim_mixed_minb == 3) {  // fused kernel, built for 3 or 2 resident CTAs per SM

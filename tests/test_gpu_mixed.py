@@ -142,8 +142,9 @@ def test_autotune_mixed_picks_fp32_accurate_schur():
     H.hdg_set_params(run.h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s,
                      precision=H.HDG_PREC_MIXED_TF32)
     rep = H.hdg_autotune(run.h, run.U, run.Q, run.UH, run.Ustar, run.nu, P.dt, P.a_ii, reps=1)
-    assert len(rep["candidates"]) == 9 and rep["schur_mode"] == 1
+    assert len(rep["candidates"]) == 12 and rep["schur_mode"] == 1
     assert {c[3] for c, _ in rep["candidates"]} == {0, 1, 2} and {c[6] for c, _ in rep["candidates"]} == {0, 1}
+    assert {c[0] for c, _ in rep["candidates"] if c[6] == 1} == {16, 8}
     run.close()
 
 
@@ -185,11 +186,12 @@ def test_split_elimination_matches_fused(make):
     from paper_2608_27863_gb300 import hdg as H
     P = make()
     out = {}
-    for split in (0, 1):
+    for split, nb in ((0, 16), (1, 16), (1, 8)):
         run = GpuRun(P)
         H.hdg_set_params(run.h, tau=P.tau, visc_law=P.visc_law, suth_c1=P.suth_c1, suth_s=P.suth_s,
                          precision=H.HDG_PREC_MIXED_3XTF32)
-        H.hdg_set_tuning(run.h, schur_mode=2, blocks_mode=1 if P.mesh.dim == 3 else 0, elim_mixed_split=split)
+        H.hdg_set_tuning(run.h, elim_nb=nb, schur_mode=2, blocks_mode=1 if P.mesh.dim == 3 else 0,
+                         elim_mixed_split=split)
         run.linearize()
         assert H.hdg_status(run.h) == 0
         s = run.sizes
@@ -197,9 +199,11 @@ def test_split_elimination_matches_fused(make):
         H.hdg_get_blocks(run.h, v)
         rng = np.random.default_rng(2)
         dq, du = run.recover(rng.normal(size=P.UH.shape) * 1e-3)
-        out[split] = (v.cpu().numpy().astype(np.float64), run.rhs(), du)
+        out[(split, nb)] = (v.cpu().numpy().astype(np.float64), run.rhs(), du)
         run.close()
-    (v0, g0, u0), (v1, g1, u1) = out[0], out[1]
-    assert np.linalg.norm(v1 - v0) <= 1e-5 * np.linalg.norm(v0)
-    assert np.linalg.norm(g1 - g0) <= 1e-5 * np.linalg.norm(g0)
-    assert np.linalg.norm(u1 - u0) <= 1e-5 * np.linalg.norm(u0)
+    v0, g0, u0 = out[(0, 16)]
+    for key in ((1, 16), (1, 8)):
+        v1, g1, u1 = out[key]
+        assert np.linalg.norm(v1 - v0) <= 1e-5 * np.linalg.norm(v0)
+        assert np.linalg.norm(g1 - g0) <= 1e-5 * np.linalg.norm(g0)
+        assert np.linalg.norm(u1 - u0) <= 1e-5 * np.linalg.norm(u0)
