@@ -160,6 +160,7 @@ struct hdg_ctx {
     double* d_V = nullptr;                 // [restart + 1][N]
     double* d_w = nullptr;                 // [N]
     double* d_red = nullptr;               // [kRedBlocks]
+    double* d_mred = nullptr;              // [(restart + 8) / 8][kRedBlocks][8] Gram-Schmidt partials
     double* d_h = nullptr;                 // [restart + 2]
     int gm_cap = 0;
     double* d_nw = nullptr;                // Newton work: dU, dQ, dUH, g

@@ -154,16 +154,15 @@ int matvec(hdg_ctx* h, const double* x, double* y) {
 
 // Classical Gram-Schmidt with one reorthogonalisation (CGS2) of vn against
 // V_0 .. V_j: hcol[0..j] = the projection coefficients (FP64, fixed-order
-// reductions), vn orthogonalised in place.  Eight dot products per pass over
-// the data instead of one kernel pair per basis vector as modified Gram-Schmidt needs.
+// reductions), vn orthogonalised in place.  All k dot products of a pass in one
+// launch (eight basis vectors per block row of the grid) instead of one kernel
+// pair per basis vector as modified Gram-Schmidt needs.
 void cgs2(hdg_ctx* h, const double* V, int64_t N, int j, double* vn, double* hcol, double* htmp) {
     const int k = j + 1;
     for (int pass = 0; pass < 2; ++pass) {
         double* hp = pass == 0 ? hcol : htmp;
-        for (int j0 = 0; j0 < k; j0 += 8) {
-            k_mdot_part<<<kRedBlocks, 256, 0, h->stream>>>(V, N, j0, k, vn, N, h->d_red);
-            k_mdot_final<<<1, 32, 0, h->stream>>>(h->d_red, kRedBlocks, j0, k, hp);
-        }
+        k_mdot_part<<<dim3(kRedBlocks, (k + 7) / 8), 256, 0, h->stream>>>(V, N, k, vn, N, h->d_mred);
+        k_mdot_final<<<(k + 3) / 4, 128, 0, h->stream>>>(h->d_mred, kRedBlocks, k, hp);
         k_msub<<<grid_for(N), 256, 0, h->stream>>>(V, N, hp, k, vn, N);
     }
     k_vadd<<<1, 64, 0, h->stream>>>(hcol, htmp, k);
@@ -177,6 +176,7 @@ int ensure_fixed_workspace(hdg_ctx* h, int m) {
         if ((rc = alloc(h, (void**)&h->d_V, sizeof(double) * (size_t)(m + 1) * N))) return rc;
         if ((rc = alloc(h, (void**)&h->d_w, sizeof(double) * N))) return rc;
         if (!h->d_red && (rc = alloc(h, (void**)&h->d_red, sizeof(double) * kRedBlocks * 8))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_mred, sizeof(double) * kRedBlocks * 8 * ((m + 8) / 8)))) return rc;
         if ((rc = alloc(h, (void**)&h->d_h, sizeof(double) * 2 * (m + 2)))) return rc;
         h->gm_cap = m;
     }
@@ -443,6 +443,7 @@ int hdg_gmres(hdg_handle h, const double* b, double* x, int restart, int max_ite
         if ((rc = alloc(h, (void**)&h->d_V, sizeof(double) * (size_t)(restart + 1) * N))) return rc;
         if ((rc = alloc(h, (void**)&h->d_w, sizeof(double) * N))) return rc;
         if (!h->d_red && (rc = alloc(h, (void**)&h->d_red, sizeof(double) * kRedBlocks * 8))) return rc;
+        if ((rc = alloc(h, (void**)&h->d_mred, sizeof(double) * kRedBlocks * 8 * ((restart + 8) / 8)))) return rc;
         if ((rc = alloc(h, (void**)&h->d_h, sizeof(double) * 2 * (restart + 2)))) return rc;
         h->gm_cap = restart;
     }

@@ -374,12 +374,13 @@ __global__ void k_bj_apply(const TL* inv, const double* x, double* y, int64_t F)
 // vector kernels (FP64, deterministic reductions)
 // ----------------------------------------------------------------------------
 constexpr int kRedBlocks = 304;  // 2 per SM
+constexpr int kMaxBasis = 512;   // Krylov basis vectors (restart + 1 <= 501)
 
 __global__ void k_dot_part(const double* x, const double* y, int64_t n, double* part);
 __global__ void k_dot_final(const double* part, int nparts, double* out, int take_sqrt);
 __global__ void k_axpy_dev(const double* coef, double sign, const double* x, double* y, int64_t n);
-__global__ void k_mdot_part(const double* V, int64_t ldv, int j0, int k, const double* w, int64_t n, double* part);
-__global__ void k_mdot_final(const double* part, int nparts, int j0, int k, double* out);
+__global__ void k_mdot_part(const double* V, int64_t ldv, int k, const double* w, int64_t n, double* part);
+__global__ void k_mdot_final(const double* part, int nparts, int k, double* out);
 __global__ void k_msub(const double* V, int64_t ldv, const double* coef, int k, double* w, int64_t n);
 __global__ void k_vadd(double* a, const double* b, int k);
 __global__ void k_scale_dev(const double* x, const double* div, double* y, int64_t n);

@@ -20,18 +20,29 @@ __global__ void k_dot_part(const double* x, const double* y, int64_t n, double* 
     }
 }
 
+// sum of part[0 .. nparts) by one warp: lane l adds parts l, l + 32, ... in
+// order, then a fixed shuffle tree (stride-8 parts for the Gram-Schmidt partials)
+__device__ __forceinline__ double warp_sum_parts(const double* part, int nparts, int stride) {
+    const int lane = threadIdx.x & 31;
+    double t = 0.0;
+    for (int b = lane; b < nparts; b += 32) t += part[(size_t)b * stride];
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+    return t;
+}
+
 __global__ void k_dot_final(const double* part, int nparts, double* out, int take_sqrt) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < nparts; ++i) t += part[i];
-        *out = take_sqrt ? sqrt(t) : t;
+    if (blockIdx.x == 0 && threadIdx.x < 32) {
+        const double t = warp_sum_parts(part, nparts, 1);
+        if (threadIdx.x == 0) *out = take_sqrt ? sqrt(t) : t;
     }
 }
 
-// Partial sums of the dot products of w with vectors j0 .. j0+7 of V (fewer
-// when k - j0 < 8), one set per block: part[block][8].
-__global__ void k_mdot_part(const double* V, int64_t ldv, int j0, int k, const double* w, int64_t n, double* part) {
+// Partial sums of the dot products of w with vectors 8 y .. 8 y + 7 of V
+// (y = blockIdx.y; fewer in the last group), one set per block x:
+// part[y][block x][8].  All groups run in one launch.
+__global__ void k_mdot_part(const double* V, int64_t ldv, int k, const double* w, int64_t n, double* part) {
     __shared__ double red[8][8];
+    const int j0 = 8 * blockIdx.y;
     const int nv = min(8, k - j0);
     double acc[8];
 #pragma unroll
@@ -53,25 +64,35 @@ __global__ void k_mdot_part(const double* V, int64_t ldv, int j0, int k, const d
     if (threadIdx.x < 8) {
         double t = 0.0;
         for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) t += red[threadIdx.x][w2];
-        part[(size_t)blockIdx.x * 8 + threadIdx.x] = t;
+        part[((size_t)blockIdx.y * gridDim.x + blockIdx.x) * 8 + threadIdx.x] = t;
     }
 }
 
-// out[j0 + q] = sum over blocks (in block order) of part[b][q], q < min(8, k - j0)
-__global__ void k_mdot_final(const double* part, int nparts, int j0, int k, double* out) {
-    const int q = threadIdx.x;
-    if (q < 8 && j0 + q < k) {
-        double t = 0.0;
-        for (int b = 0; b < nparts; ++b) t += part[(size_t)b * 8 + q];
-        out[j0 + q] = t;
+// out[j] = sum over blocks of the partials of vector j, one warp per j < k
+__global__ void k_mdot_final(const double* part, int nparts, int k, double* out) {
+    const int j = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    if (j < k) {
+        const double t = warp_sum_parts(part + (size_t)(j >> 3) * nparts * 8 + (j & 7), nparts, 8);
+        if ((threadIdx.x & 31) == 0) out[j] = t;
     }
 }
 
-// w -= sum_j coef[j] V_j
+// w -= sum_j coef[j] V_j (j ascending; eight basis vectors loaded ahead)
 __global__ void k_msub(const double* V, int64_t ldv, const double* coef, int k, double* w, int64_t n) {
+    __shared__ double cf[kMaxBasis];
+    for (int j = threadIdx.x; j < k; j += blockDim.x) cf[j] = coef[j];
+    __syncthreads();
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         double s = w[i];
-        for (int j = 0; j < k; ++j) s = fma(-coef[j], V[(size_t)j * ldv + i], s);
+        int j = 0;
+        for (; j + 8 <= k; j += 8) {
+            double v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = V[(size_t)(j + q) * ldv + i];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) s = fma(-cf[j + q], v[q], s);
+        }
+        for (; j < k; ++j) s = fma(-cf[j], V[(size_t)j * ldv + i], s);
         w[i] = s;
     }
 }

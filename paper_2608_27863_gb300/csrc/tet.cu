@@ -934,64 +934,96 @@ __global__ void k_tet_assemble_g(const TetElem* el, const double* mat, const int
     }
 }
 
-// y_F (+)= B x for one column-major block B [bsG][bsF] and one warp: for
-// bsF <= 16 the warp splits into ng = 32 / bsF column groups (lane = group
-// * bsF + row), so every load instruction reads ng consecutive columns; the
-// groups are combined by shuffles.  Rows beyond 32 take further passes.
-template <class T>
-__device__ __forceinline__ T vbr_partial(const T* B, const T* xg, int bsF, int bsG, int r0, int lane) {
-    const int rows = min(32, bsF - r0);
-    const int ng = rows <= 16 ? 32 / rows : 1;
-    const int r = lane % rows, cg = lane / rows;
-    T s0 = 0, s1 = 0;
-    if (cg < ng) {
-        int c = cg;
-        for (; c + ng < bsG; c += 2 * ng) {
-            s0 = fma(B[(int64_t)c * bsF + r0 + r], xg[c], s0);
-            s1 = fma(B[(int64_t)(c + ng) * bsF + r0 + r], xg[c + ng], s1);
+// y_F = sum over the row's blocks of B x_G, one CTA per block row F.  A
+// row's blocks are stored back to back, so the row is one column-major
+// bs_F x W matrix (W = rw[F], the summed widths of its column faces; BJ: the
+// single bs_F x bs_F inverse of the diagonal block).  Thread t takes row
+// t % bs_F and every S-th column from t / bs_F (S = 256 / bs_F), so one step
+// of the CTA reads S bs_F consecutive values.  The matrix is streamed in
+// register batches of U columns per thread, the next batch loaded before the
+// current one is used, and the first batch is issued before x is gathered
+// into shared memory (converted to T).  The S partial sums of a row are added
+// in a fixed order.
+constexpr int RMV_THREADS = 256;
+
+template <class T, bool BJ>
+__global__ void __launch_bounds__(RMV_THREADS, 4) k_tet_rowmv(const T* __restrict__ vals,
+                                                           const int64_t* __restrict__ voff,
+                                                           const int64_t* __restrict__ hoff,
+                                                           const int32_t* __restrict__ rowptr,
+                                                           const int32_t* __restrict__ col,
+                                                           const int32_t* __restrict__ rw,
+                                                           const double* __restrict__ x, double* __restrict__ y) {
+    extern __shared__ unsigned char rmv_raw[];
+    T* xs = reinterpret_cast<T*>(rmv_raw);                  // [W]
+    __shared__ T part[RMV_THREADS];
+    __shared__ int cst[33];
+    __shared__ int64_t cg[32];
+    constexpr int U = sizeof(T) == 4 ? 8 : 4;                // columns per thread and batch
+    const int tid = threadIdx.x;
+    const int64_t Fr = blockIdx.x;
+    const int64_t h0 = hoff[Fr];
+    const int bs = (int)(hoff[Fr + 1] - h0);
+    const int b0 = BJ ? 0 : rowptr[Fr];
+    const int nb = BJ ? 1 : rowptr[Fr + 1] - b0;
+    const int W = BJ ? bs : rw[Fr];
+    const T* B = vals + (BJ ? voff[Fr] : voff[b0]);
+    const int S = RMV_THREADS / bs;
+    const int cs = tid / bs, r = tid - cs * bs;
+    const int step = S * bs;                                 // a row holds at most 75 x 525 values
+    const T* p = B + cs * bs + r;
+    int c = cs < S ? cs : W;                                 // threads beyond S bs_F take no columns
+    int o = 0;
+    T v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) v[u] = c + u * S < W ? __ldg(p + u * step) : T(0);
+    if (tid < 32) {                                         // column start of each block (warp scan)
+        int w = 0;
+        int64_t g = 0;
+        if (tid < nb) {
+            const int64_t G = BJ ? Fr : col[b0 + tid];
+            g = hoff[G];
+            w = (int)(hoff[G + 1] - g);
         }
-        if (c < bsG) s0 = fma(B[(int64_t)c * bsF + r0 + r], xg[c], s0);
-    }
-    return s0 + s1;
-}
-
-// sum of the column groups' partials into the lanes of group 0
-template <class T>
-__device__ __forceinline__ T vbr_reduce(T s, int rows, int lane) {
-    const int ng = rows <= 16 ? 32 / rows : 1;
-    for (int g = 1; g < ng; ++g) {
-        const T o = __shfl_sync(0xffffffffu, s, (lane + g * rows) & 31);
-        if (lane < rows && lane + g * rows < 32) s += o;
-    }
-    return s;
-}
-
-// A6: y = S x, one warp per block row (T: the block and operand type; FP32
-// arithmetic for the mixed form's FP32 blocks, the operand converted once)
-template <class T>
-__global__ void k_tet_matvec(const T* vals, const int64_t* hoff, const int64_t* boff, const int32_t* rowptr,
-                             const int32_t* col, int64_t F, const T* x, double* y) {
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t Fr = wid; Fr < F; Fr += nw) {
-        const int bsF = (int)(hoff[Fr + 1] - hoff[Fr]);
-        for (int r0 = 0; r0 < bsF; r0 += 32) {
-            T s = 0;
-            for (int b = rowptr[Fr]; b < rowptr[Fr + 1]; ++b) {
-                const int64_t G = col[b];
-                s += vbr_partial(vals + boff[b], x + hoff[G], bsF, (int)(hoff[G + 1] - hoff[G]), r0, lane);
-            }
-            const int rows = min(32, bsF - r0);
-            s = vbr_reduce(s, rows, lane);
-            if (lane < rows) y[hoff[Fr] + r0 + lane] = (double)s;
+        int sc = w;
+        for (int off = 1; off < 32; off <<= 1) {
+            const int o = __shfl_up_sync(0xffffffffu, sc, off);
+            if (tid >= off) sc += o;
         }
+        if (tid < nb) { cst[tid + 1] = sc; cg[tid] = g; }
+        if (tid == 0) cst[0] = 0;
     }
-}
-
-__global__ void k_tet_to_f32(const double* x, float* y, int64_t n) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        y[i] = (float)x[i];
+    __syncthreads();
+    for (int k = tid; k < W; k += RMV_THREADS) {
+        int b = 0;
+        while (k >= cst[b + 1]) ++b;
+        xs[k] = (T)x[cg[b] + k - cst[b]];
+    }
+    __syncthreads();
+    T a[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) a[u] = 0;
+    for (; c < W; c += U * S) {
+        o += U * step;
+        T nv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) nv[u] = c + (U + u) * S < W ? __ldg(p + (o + u * step)) : T(0);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (c + u * S < W) a[u] = fma(v[u], xs[c + u * S], a[u]);
+#pragma unroll
+        for (int u = 0; u < U; ++u) v[u] = nv[u];
+    }
+    T acc = 0;
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc += a[u];
+    part[tid] = acc;
+    __syncthreads();
+    if (tid < bs) {
+        T sum = part[tid];
+        for (int k = 1; k < S; ++k) sum += part[k * bs + tid];
+        y[h0 + tid] = (double)sum;
+    }
 }
 
 // A7: dU = -U^{-1} (z + Z dUhat_K), dQ = dq0 - G dU - H dUhat_K
@@ -1207,89 +1239,85 @@ __global__ void k_tet_residual_faces(const TetElem* el, const double* rk, const 
     }
 }
 
-// block-Jacobi set-up: explicit inverse of every diagonal block S_FF by
-// Gauss-Jordan elimination with partial pivoting (column-major result)
-template <class TV>
-__global__ void __launch_bounds__(128) k_tet_bj_setup(const TV* vals, const int64_t* boff, const int32_t* diagb,
-                                                       const int64_t* hoff, const int64_t* bjoff, int64_t F,
-                                                       TV* inv, int32_t* status) {
-    extern __shared__ double sa[];                // [bs][2 bs] augmented rows
+// block-Jacobi set-up: explicit inverse of every diagonal block S_FF, one CTA
+// per block, by in-place Gauss-Jordan elimination with partial pivoting in the
+// block's own precision T (FP64 system: FP64; mixed form: FP32).  Step c swaps
+// rows c and p_c, scales the pivot row and eliminates column c from every other
+// row, storing column c of the inverse in place; the row interchanges are then
+// undone as column interchanges in reverse order.  Row-major in shared memory
+// with leading dimension bs + 1; result column-major.
+template <class T>
+__global__ void __launch_bounds__(256) k_tet_bj_setup(const T* vals, const int64_t* boff, const int32_t* diagb,
+                                                       const int64_t* hoff, const int64_t* bjoff, T* inv,
+                                                       int32_t* status) {
+    extern __shared__ unsigned char bj_raw[];
+    T* a = reinterpret_cast<T*>(bj_raw);                    // [bs][bs + 1]
+    __shared__ T rowc[NFPMAX * M], colc[NFPMAX * M];
+    __shared__ int piv[NFPMAX * M], src[NFPMAX * M];
     __shared__ int pr;
     const int tid = threadIdx.x, lane = tid & 31;
-    for (int64_t Fr = blockIdx.x; Fr < F; Fr += gridDim.x) {
-        const int bs = (int)(hoff[Fr + 1] - hoff[Fr]), w2 = 2 * bs;
-        const TV* B = vals + boff[diagb[Fr]];
-        for (int idx = tid; idx < bs * w2; idx += 128) {
-            const int r = idx / w2, c = idx - r * w2;
-            sa[idx] = c < bs ? B[(int64_t)c * bs + r] : (c - bs == r ? 1.0 : 0.0);
+    const int64_t Fr = blockIdx.x;
+    const int bs = (int)(hoff[Fr + 1] - hoff[Fr]), ld = bs + 1;
+    const T* B = vals + boff[diagb[Fr]];
+    for (int idx = tid; idx < bs * bs; idx += 256) {
+        const int c = idx / bs, r = idx - c * bs;
+        a[r * ld + c] = B[idx];
+    }
+    __syncthreads();
+    for (int c = 0; c < bs; ++c) {
+        if (tid < 32) {                                     // pivot: largest |a_rc|, r >= c, lowest r on ties
+            T bv = -1;
+            int bi = INT_MAX;
+            for (int r = c + lane; r < bs; r += 32) {
+                const T v = fabs(a[r * ld + c]);
+                if (v > bv) { bv = v; bi = r; }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                const T ov = __shfl_down_sync(0xffffffffu, bv, off);
+                const int oi = __shfl_down_sync(0xffffffffu, bi, off);
+                if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
+            }
+            if (lane == 0) { pr = bi == INT_MAX ? c : bi; piv[c] = pr; }
         }
         __syncthreads();
-        for (int c = 0; c < bs; ++c) {
-            if (tid < 32) {
-                double bv = -1.0;
-                int bi = INT_MAX;
-                for (int r = c + lane; r < bs; r += 32) {
-                    const double v = fabs(sa[r * w2 + c]);
-                    if (v > bv) { bv = v; bi = r; }
-                }
-                for (int off = 16; off > 0; off >>= 1) {
-                    const double ov = __shfl_down_sync(0xffffffffu, bv, off);
-                    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-                    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-                }
-                if (lane == 0) pr = (bi == INT_MAX) ? c : bi;
-            }
-            __syncthreads();
-            const int p = pr;
-            if (p != c)
-                for (int k = tid; k < w2; k += 128) {
-                    const double t = sa[c * w2 + k];
-                    sa[c * w2 + k] = sa[p * w2 + k];
-                    sa[p * w2 + k] = t;
-                }
-            __syncthreads();
-            double pv = sa[c * w2 + c];
-            if (pv == 0.0 || !isfinite(pv)) {
-                if (tid == 0) atomicOr(status, pv == 0.0 ? 1 : 2);
-                pv = 1.0;
-            }
-            const double ip = 1.0 / pv;
-            __syncthreads();
-            for (int k = tid; k < w2; k += 128) sa[c * w2 + k] *= ip;
-            __syncthreads();
-            for (int idx = tid; idx < bs * w2; idx += 128) {
-                const int r = idx / w2, k = idx - r * w2;
-                if (r == c) continue;
-                const double f = sa[r * w2 + c];
-                if (k != c) sa[idx] = fma(-f, sa[c * w2 + k], sa[idx]);
-            }
-            __syncthreads();
-            for (int r = tid; r < bs; r += 128)
-                if (r != c) sa[r * w2 + c] = 0.0;
-            __syncthreads();
+        const int p = pr;
+        for (int k = tid; k < bs; k += 256) {               // pivot row (after the swap); old row c into row p
+            const T vc = a[c * ld + k], vp = a[p * ld + k];
+            rowc[k] = vp;
+            if (p != c) a[p * ld + k] = vc;
+            colc[k] = k == p ? a[c * ld + c] : a[k * ld + c];   // column c after the swap (entry c unused)
         }
-        TV* o = inv + bjoff[Fr];
-        for (int idx = tid; idx < bs * bs; idx += 128) {
-            const int c = idx / bs, r = idx - c * bs;
-            o[idx] = (TV)sa[r * w2 + bs + c];
+        __syncthreads();
+        T pv = rowc[c];
+        if (pv == T(0) || !isfinite(pv)) {
+            if (tid == 0) atomicOr(status, pv == T(0) ? 1 : 2);
+            pv = 1;
+        }
+        const T ip = T(1) / pv;
+        for (int r = tid >> 5; r < bs; r += 8) {           // warp per row, lanes along the row
+            T* ar = a + r * ld;
+            if (r == c) {
+                for (int k = lane; k < bs; k += 32) ar[k] = k == c ? ip : rowc[k] * ip;
+            } else {
+                const T f = colc[r] * ip;
+                for (int k = lane; k < bs; k += 32) ar[k] = k == c ? -f : fma(-f, rowc[k], ar[k]);
+            }
         }
         __syncthreads();
     }
-}
-
-template <class T>
-__global__ void k_tet_bj_apply(const T* inv, const int64_t* hoff, const int64_t* bjoff, int64_t F,
-                               const T* x, double* y) {
-    const int lane = threadIdx.x & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t Fr = wid; Fr < F; Fr += nw) {
-        const int bs = (int)(hoff[Fr + 1] - hoff[Fr]);
-        for (int r0 = 0; r0 < bs; r0 += 32) {
-            const int rows = min(32, bs - r0);
-            const T s = vbr_reduce(vbr_partial(inv + bjoff[Fr], x + hoff[Fr], bs, bs, r0, lane), rows, lane);
-            if (lane < rows) y[hoff[Fr] + r0 + lane] = (double)s;
+    if (tid == 0) {                                         // column interchanges, last step first
+        for (int j = 0; j < bs; ++j) src[j] = j;
+        for (int c = bs - 1; c >= 0; --c) {
+            const int t = src[c];
+            src[c] = src[piv[c]];
+            src[piv[c]] = t;
         }
+    }
+    __syncthreads();
+    T* o = inv + bjoff[Fr];
+    for (int idx = tid; idx < bs * bs; idx += 256) {
+        const int j = idx / bs, r = idx - j * bs;
+        o[idx] = a[r * ld + src[j]];
     }
 }
 
@@ -1349,13 +1377,20 @@ int create_device(hdg_ctx* h, std::string& err) {
     if ((rc = tet_alloc(h, &c->d_next, 1, err))) return rc;
     if ((rc = tet_alloc(h, &c->d_rk, (size_t)c->n_rk, err))) return rc;           // residual scratch: allocated
     if ((rc = tet_alloc(h, &c->d_part, (size_t)(c->E + c->F), err))) return rc;   // here so graphs can capture it
-    int bsmax = 0;
-    for (int64_t F = 0; F < c->F; ++F) bsmax = std::max<int>(bsmax, (int)(c->hoff[F + 1] - c->hoff[F]));
-    if ((rc = tet_alloc(h, &c->d_x32, (size_t)c->n_trace, err))) return rc;
+    c->bsmax = c->wmax = 0;
+    std::vector<int32_t> rw(c->F);
+    for (int64_t F = 0; F < c->F; ++F) {
+        c->bsmax = std::max<int>(c->bsmax, (int)(c->hoff[F + 1] - c->hoff[F]));
+        int w = 0;
+        for (int32_t b = c->rowptr[F]; b < c->rowptr[F + 1]; ++b) w += (int)(c->hoff[c->col[b] + 1] - c->hoff[c->col[b]]);
+        rw[F] = w;
+        c->wmax = std::max(c->wmax, w);
+        if (c->rowptr[F + 1] - c->rowptr[F] > 32) { err = "more than 32 blocks in a block row"; return HDG_EINVAL; }
+    }
+    if ((rc = tet_upload(h, &c->d_rw, rw, err))) return rc;
+    if (c->bsmax > NFPMAX * M) { err = "trace block larger than the degree-4 face block"; return HDG_EINVAL; }
     if (cudaFuncSetAttribute(k_tet_bj_setup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(double) * 2 * (size_t)bsmax * bsmax)) != cudaSuccess ||
-        cudaFuncSetAttribute(k_tet_bj_setup<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(double) * 2 * (size_t)bsmax * bsmax)) != cudaSuccess) {
+                             (int)(sizeof(double) * (size_t)c->bsmax * (c->bsmax + 1))) != cudaSuccess) {
         err = "shared-memory opt-in of the block-Jacobi kernel failed";
         return HDG_ECUDA;
     }
@@ -1451,17 +1486,14 @@ int linearize(hdg_ctx* h, const double* U, const double* Q, const double* UH, co
 
 int matvec(hdg_ctx* h, const double* x, double* y) {
     Ctx* c = h->tet;
-    const unsigned gf = (unsigned)std::min<int64_t>(65535, (c->F + 7) / 8);
+    const size_t smem = (c->sys_prec == HDG_PREC_FP64 ? sizeof(double) : sizeof(float)) * (size_t)c->wmax;
     prof_begin(h, HDG_K_MATVEC);
-    if (c->sys_prec == HDG_PREC_FP64) {
-        k_tet_matvec<double><<<gf, 256, 0, h->stream>>>(c->d_vals, c->d_hoff, c->d_boff, c->d_rowptr, c->d_col, c->F,
-                                                        x, y);
-    } else {
-        k_tet_to_f32<<<(unsigned)std::min<int64_t>(4096, (c->n_trace + 255) / 256), 256, 0, h->stream>>>(
-            x, c->d_x32, c->n_trace);
-        k_tet_matvec<float><<<gf, 256, 0, h->stream>>>(c->d_vals32, c->d_hoff, c->d_boff, c->d_rowptr, c->d_col, c->F,
-                                                       c->d_x32, y);
-    }
+    if (c->sys_prec == HDG_PREC_FP64)
+        k_tet_rowmv<double, false><<<(unsigned)c->F, RMV_THREADS, smem, h->stream>>>(
+            c->d_vals, c->d_boff, c->d_hoff, c->d_rowptr, c->d_col, c->d_rw, x, y);
+    else
+        k_tet_rowmv<float, false><<<(unsigned)c->F, RMV_THREADS, smem, h->stream>>>(
+            c->d_vals32, c->d_boff, c->d_hoff, c->d_rowptr, c->d_col, c->d_rw, x, y);
     prof_end(h);
     TET_CK(cudaGetLastError());
     return HDG_OK;
@@ -1519,16 +1551,13 @@ int bj_setup(hdg_ctx* h) {
     const bool mixed = c->sys_prec != HDG_PREC_FP64;
     if (!mixed && !c->d_bj && (rc = tet_alloc(h, &c->d_bj, (size_t)c->bjoff[c->F], err))) { h->err = err; return rc; }
     if (mixed && !c->d_bj32 && (rc = tet_alloc(h, &c->d_bj32, (size_t)c->bjoff[c->F], err))) { h->err = err; return rc; }
-    int bsmax = 0;
-    for (int64_t F = 0; F < c->F; ++F) bsmax = std::max<int>(bsmax, (int)(c->hoff[F + 1] - c->hoff[F]));
-    const size_t smem = sizeof(double) * (size_t)bsmax * 2 * bsmax;
-    const unsigned g = (unsigned)std::min<int64_t>(c->F, 152 * 4);
+    const unsigned g = (unsigned)c->F;
     if (!mixed)
-        k_tet_bj_setup<double><<<g, 128, smem, h->stream>>>(c->d_vals, c->d_boff, c->d_diagb, c->d_hoff, c->d_bjoff,
-                                                            c->F, c->d_bj, h->d_status);
+        k_tet_bj_setup<double><<<g, 256, sizeof(double) * (size_t)c->bsmax * (c->bsmax + 1), h->stream>>>(
+            c->d_vals, c->d_boff, c->d_diagb, c->d_hoff, c->d_bjoff, c->d_bj, h->d_status);
     else
-        k_tet_bj_setup<float><<<g, 128, smem, h->stream>>>(c->d_vals32, c->d_boff, c->d_diagb, c->d_hoff, c->d_bjoff,
-                                                           c->F, c->d_bj32, h->d_status);
+        k_tet_bj_setup<float><<<g, 256, sizeof(float) * (size_t)c->bsmax * (c->bsmax + 1), h->stream>>>(
+            c->d_vals32, c->d_boff, c->d_diagb, c->d_hoff, c->d_bjoff, c->d_bj32, h->d_status);
     TET_CK(cudaGetLastError());
     c->bj_ready = true;
     return HDG_OK;
@@ -1536,14 +1565,13 @@ int bj_setup(hdg_ctx* h) {
 
 int bj_apply(hdg_ctx* h, const double* x, double* y) {
     Ctx* c = h->tet;
-    const unsigned gf = (unsigned)std::min<int64_t>(65535, (c->F + 7) / 8);
-    if (c->sys_prec == HDG_PREC_FP64) {
-        k_tet_bj_apply<double><<<gf, 256, 0, h->stream>>>(c->d_bj, c->d_hoff, c->d_bjoff, c->F, x, y);
-    } else {
-        k_tet_to_f32<<<(unsigned)std::min<int64_t>(4096, (c->n_trace + 255) / 256), 256, 0, h->stream>>>(
-            x, c->d_x32, c->n_trace);
-        k_tet_bj_apply<float><<<gf, 256, 0, h->stream>>>(c->d_bj32, c->d_hoff, c->d_bjoff, c->F, c->d_x32, y);
-    }
+    const size_t smem = (c->sys_prec == HDG_PREC_FP64 ? sizeof(double) : sizeof(float)) * (size_t)c->bsmax;
+    if (c->sys_prec == HDG_PREC_FP64)
+        k_tet_rowmv<double, true><<<(unsigned)c->F, RMV_THREADS, smem, h->stream>>>(
+            c->d_bj, c->d_bjoff, c->d_hoff, nullptr, nullptr, nullptr, x, y);
+    else
+        k_tet_rowmv<float, true><<<(unsigned)c->F, RMV_THREADS, smem, h->stream>>>(
+            c->d_bj32, c->d_bjoff, c->d_hoff, nullptr, nullptr, nullptr, x, y);
     TET_CK(cudaGetLastError());
     return HDG_OK;
 }

@@ -85,6 +85,7 @@ struct Ctx {
     int64_t* d_boff = nullptr;
     int32_t* d_rowptr = nullptr;
     int32_t* d_col = nullptr;
+    int32_t* d_rw = nullptr;               // [F] block-row widths (summed column-face sizes)
     int32_t* d_cptr = nullptr;
     int32_t* d_centry = nullptr;
     int32_t* d_f2e = nullptr;
@@ -94,9 +95,9 @@ struct Ctx {
     double* d_vals = nullptr;              // assembled blocks (FP64 form)
     float* d_vals32 = nullptr;             // assembled blocks of the mixed form (allocated on first use)
     float* d_bj32 = nullptr;               // block-Jacobi inverses of the mixed form
-    float* d_x32 = nullptr;                // FP32 copy of a matvec / preconditioner operand
     int sys_prec = HDG_PREC_FP64;          // precision of the assembled system
     int nb = 16;                           // elimination panel width (autotuned: 16 or 8)
+    int bsmax = 0, wmax = 0;               // largest block size and block-row width
     double* d_g = nullptr;                 // [n_trace]
     double* d_work = nullptr;              // per-CTA workspace
     int32_t* d_diagb = nullptr;

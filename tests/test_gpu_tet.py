@@ -224,6 +224,62 @@ def test_tet_mixed_form_blocks_and_newton(H):
         H.hdg_destroy(h)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_tet_block_jacobi_and_matvec_against_blocks(H, prec):
+    """Block-Jacobi on tetrahedra: y_F = S_FF^{-1} x_F against dense FP64 solves with
+    the oracle's diagonal blocks (FP64 form), resp. with the FP32 blocks the mixed form
+    assembled; the bound is 8 bs u cond(S_FF) in the inverse's precision u.  The mixed
+    matvec against the FP64 product of its own FP32 blocks."""
+    mesh = mesh_case(1)
+    prob, pb, h, dev = setup(H, mesh)
+    try:
+        mixed = prec == "mixed"
+        if mixed:
+            H.hdg_set_params(h, tau=prob.tau, precision=H.HDG_PREC_MIXED)
+        s = H.hdg_tet_query(h)
+        H.hdg_linearize_condense(h, dev["U"], dev["Q"], dev["UH"], dev["Ustar"], None, prob.dt, prob.a_ii)
+        H.hdg_blockjacobi_setup(h)
+        assert H.hdg_status(h) == H.HDG_OK
+        c = pb.conn
+        L = H.hdg_tet_layout(h)
+        if mixed:
+            v32 = torch.zeros(s["n_vals"], dtype=torch.float32, device="cuda")
+            H.hdg_get_blocks(h, v32)
+            vg = v32.cpu().numpy().astype(np.float64)
+            blocks = {}
+            for b in range(len(c.col)):
+                F = int(np.searchsorted(c.rowptr, b, side="right") - 1)
+                bsF, bsG = c.hoff[F + 1] - c.hoff[F], c.hoff[c.col[b] + 1] - c.hoff[c.col[b]]
+                blocks[b] = vg[L["boff"][b]:L["boff"][b + 1]].reshape(bsG, bsF).T
+            u = 2.0 ** -24
+        else:
+            blocks, _ = pb.assemble()
+            u = 2.0 ** -53
+        n = s["n_trace"]
+        x = np.sin(0.29 * np.arange(n)) + 0.5 * np.cos(0.07 * np.arange(n))
+        xd = torch.tensor(x, device="cuda")
+        y = torch.zeros(n, dtype=torch.float64, device="cuda")
+        H.hdg_blockjacobi_apply(h, xd, y)
+        yc = y.cpu().numpy()
+        worst = 0.0
+        for F in range(c.n_faces):
+            b = next(b for b in range(c.rowptr[F], c.rowptr[F + 1]) if c.col[b] == F)
+            sl = slice(c.hoff[F], c.hoff[F + 1])
+            ref = np.linalg.solve(blocks[b], x[sl])
+            bound = 8 * blocks[b].shape[0] * u * np.linalg.cond(blocks[b])
+            err = np.linalg.norm(yc[sl] - ref) / np.linalg.norm(ref)
+            worst = max(worst, err / bound)
+            assert err <= bound, (F, err, bound)
+        print("block-Jacobi %s: worst error / bound %.3e" % (prec, worst))
+        if mixed:
+            H.hdg_trace_matvec(h, xd, y)
+            ref = pb.matvec(blocks, x)
+            mag = pb.matvec({b: np.abs(B) for b, B in blocks.items()}, np.abs(x))
+            assert np.all(np.abs(y.cpu().numpy() - ref) <= 1e-5 * mag + 1e-30)
+    finally:
+        H.hdg_destroy(h)
+
+
 def test_tet_autotune_and_panel_width_parity(H):
     """The autotuner times both panel widths of the persistent kernel and keeps one;
     the 8-column variant matches the oracle like the 16-column one."""
