@@ -256,9 +256,12 @@ int hdg_schwarz_setup(hdg_handle h);
 int hdg_schwarz_apply(hdg_handle h, const double* x, double* y);
 
 /* Block-Jacobi preconditioner of the trace system: the inverse of every
- * diagonal block S_FF of the current S (partial-pivot LU in FP64, kept in the
- * system's storage precision; the one-face special case of the additive
- * Schwarz method, eq. additive-schwarz), and y = M^{-1} x. */
+ * diagonal block S_FF of the current S (the one-face special case of the
+ * additive Schwarz method, eq. additive-schwarz), and y = M^{-1} x.  Hex and
+ * quad handles: partial-pivot LU in FP64, kept in the system's storage
+ * precision.  Tetrahedral handles: Gauss-Jordan with partial pivoting in the
+ * system's precision (FP32 for the mixed form).  A zero or non-finite pivot
+ * sets the handle's status (hdg_status). */
 int hdg_blockjacobi_setup(hdg_handle h);
 int hdg_blockjacobi_apply(hdg_handle h, const double* x, double* y);
 /* Restarted GMRES(restart) on S x = b with FP64 Arnoldi (Sec. 3.2; classical
