@@ -5,7 +5,8 @@
 // operators, curved geometry included), the contraction into the bordered
 // element matrix (A2) and its elimination into the Schur complement (A3, A4);
 // then the block assembly (A5), the trace matvec (A6) and the interior
-// recovery (A7) with variable block sizes.
+// recovery (A7) with variable block sizes, the FP64 stage residual and the
+// block-Jacobi preconditioner of the trace system (A8).
 #include <algorithm>
 #include <climits>
 #include <cstring>
