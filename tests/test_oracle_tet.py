@@ -4,14 +4,16 @@ Each check compares the oracle with something it does not compute itself:
 closed-form integrals of barycentric monomials, the Lagrange property,
 orthonormality, exact differentiation of polynomials, the divergence theorem
 on a curved mesh, freestream preservation, the conservation identity, the
-brute-force uncondensed solve, finite differences, and the geometric
-consistency of the two sides of every face.
+brute-force uncondensed solve, finite differences, the geometric
+consistency of the two sides of every face, and the consistency order on an
+exact steady Navier-Stokes solution.
 """
 import math
 
 import numpy as np
 import pytest
 
+import synth
 from oracle import tet as ot
 from synth import tetmesh as tm
 
@@ -207,6 +209,79 @@ def test_conservation_identity_periodic():
     for F in range(c.n_faces):
         rhs += Rh[c.hoff[F]:c.hoff[F + 1]].reshape(5, -1).sum(axis=1)
     assert np.allclose(lhs, pb.dt * rhs, atol=1e-14, rtol=1e-12)
+
+
+COUETTE_GAMMA, COUETTE_PR = 1.4, 0.72
+
+
+def couette(x):
+    return synth.couette_state(x - 0.5, COUETTE_GAMMA, COUETTE_PR)
+
+
+def couette_gradient(x):
+    """d u_a / d x_k of the Couette state, [..., 3, m], in closed form: only y varies,
+    e = e0 - Pr y^2 / (2 gamma), rho = p0 / ((gamma - 1) e), rho v_x = rho y,
+    rho E = p0 / (gamma - 1) + rho y^2 / 2 (p0 = 1, e0 = 2)."""
+    g_, pr = COUETTE_GAMMA, COUETTE_PR
+    y = x[..., 1] - 0.5
+    e = 2.0 - pr * y * y / (2.0 * g_)
+    rho = 1.0 / ((g_ - 1.0) * e)
+    drho = rho / e * (pr * y / g_)
+    out = np.zeros(x.shape[:-1] + (3, 5))
+    out[..., 1, 0] = drho
+    out[..., 1, 1] = rho + y * drho
+    out[..., 1, 4] = 0.5 * y * y * drho + rho * y
+    return out
+
+
+def couette_residuals(n, p, curved):
+    """Max-norm R_u, R_q (over h^3) and interior R_uhat (over h^2) with the exact
+    Couette state interpolated at the element nodes and the trace nodes."""
+    c = [np.linspace(0, 1, n + 1)] * 3
+    mesh = tm.kuhn_box((n, n, n), c, (False, False, False), degrees=p,
+                       bump=tm.wall_bump(0.05) if curved else None, curved_layers=n if curved else 0, seed=1)
+    conn = ot.TetConnectivity(mesh)
+    U, Q = [], []
+    for e in range(mesh.n_elem):
+        x = np.einsum("nc,ck->nk", tm.node_shape(p), mesh.geo[e])
+        U.append(couette(x).T.ravel())
+        Q.append(np.transpose(couette_gradient(x), (1, 2, 0)).ravel())
+    U, Q = np.concatenate(U), np.concatenate(Q)
+    UH = np.zeros(conn.hoff[-1])
+    for F in range(conn.n_faces):
+        e, f = conn.f2e[F, 0]
+        xi = ot.face_points(conn.L[e, f], ot.TriRef(int(conn.face_p[F])).nodes)
+        UH[conn.hoff[F]:conn.hoff[F + 1]] = couette(ot.p2_map(mesh.geo[e], xi)).T.ravel()
+    prob = tm.TetProblem("couette", mesh, COUETTE_GAMMA, 20.0, COUETTE_PR, 0.5, 2.0, 1.0, 1.0, 0, 0.0, 0.0,
+                         couette(np.zeros((1, 3)))[0])
+    prob.U, prob.Q, prob.UH, prob.Ustar = U, Q, UH, U.copy()
+    Rq, Ru, Rh = ot.TetProblem(prob).global_residual(Q, U, UH)
+    h = 1.0 / n
+    inner = np.concatenate([np.arange(conn.hoff[F], conn.hoff[F + 1]) for F in range(conn.n_faces)
+                            if conn.f2e[F, 1, 0] >= 0])
+    return np.abs(Ru).max() / h ** 3, np.abs(Rq).max() / h ** 3, np.abs(Rh[inner]).max() / h ** 2
+
+
+def test_couette_gradient_closed_form():
+    x = np.random.default_rng(0).uniform(0, 1, (20, 3))
+    assert np.allclose(couette_gradient(x), synth.nodal_gradient(couette, x, 1e-5), rtol=0, atol=1e-8)
+
+
+@pytest.mark.parametrize("p,curved,rate", [(2, False, 1.5), (3, False, 2.5), (3, True, 2.0)])
+def test_couette_consistency_order(p, curved, rate):
+    """Exact steady compressible NS solution (plane Couette flow with viscous
+    heating) on affine and curved tetrahedra: the normalised element residuals
+    fall at least at rate p - 1/2 (affine) or p - 1 (curved, pre-asymptotic: the
+    wall bump keeps its amplitude as h halves) from 2^3 to 4^3 cells; a wrong
+    flux, metric or lifting term leaves them O(1).  The interpolated trace is
+    single valued and the element nodes restricted to a face are its trace
+    nodes, so the two sides' face fluxes cancel: interior R_uhat vanishes to
+    rounding on curved faces too."""
+    r1 = couette_residuals(2, p, curved)
+    r2 = couette_residuals(4, p, curved)
+    for a, b in zip(r1[:2], r2[:2]):           # R_u, R_q
+        assert b < a * 2.0 ** (-rate), (r1, r2)
+    assert r1[2] < 1e-13 and r2[2] < 1e-13, (r1, r2)
 
 
 def test_condensed_solve_equals_uncondensed_solve():
