@@ -465,6 +465,42 @@ int hdg_tet_layout(hdg_handle h, int64_t* uoff, int64_t* hoff, int32_t* face_p, 
 int hdg_tet_ref_tables(int p, double* xq, double* wq, double* phi, double* dphi);
 int hdg_tri_ref_tables(int pF, double* xs, double* ws, double* mu);
 
+/* ---- Partition-ready layout (Sec. 3.5) ------------------------------------
+ * For a run over several GPUs, element-local work (linearization, condensation,
+ * recovery) stays on the part that owns the element; parts exchange only trace
+ * data of faces on part interfaces: the condensed blocks of those faces' rows
+ * during assembly, and trace entries (the halo) in every matvec.  These calls
+ * describe the layout on the host (quad, hex and tetrahedral handles, host-only
+ * handles included); no call of the library communicates.
+ *
+ * hdg_partition: recursive coordinate bisection of the element centroids
+ * (vertex means) into n_parts parts.  Each split cuts the longest extent of the
+ * current element set (lowest axis on ties), ordered by (coordinate, element
+ * id), at the element count of its first half of the parts; part q gets
+ * E / n_parts elements, plus one for q < E mod n_parts.  elem_part [E] (host,
+ * out).  HDG_EINVAL for n_parts outside 1..E or a NULL elem_part. */
+int hdg_partition(hdg_handle h, int n_parts, int32_t* elem_part);
+
+typedef struct {
+    int64_t n_elem;             /* elements of the part */
+    int64_t n_interior_elem;    /* of which none has a face on a part interface */
+    int64_t n_faces;            /* faces the part owns: the owner of a face is the smaller part id of its elements */
+    int64_t n_interface_faces;  /* faces between this part and another (owned or not) */
+    int64_t n_halo_faces;       /* faces owned elsewhere whose trace entries the owned block rows reference */
+} hdg_part_sizes;
+
+/* Layout of part `part` under the partition elem_part [E] (any non-negative ids):
+ * elems [n_elem] (interior elements first, then interface elements, ascending
+ * ids within each), faces [n_faces] (owned, ascending), interface_faces and
+ * interface_peer [n_interface_faces] (ascending faces, the other part),
+ * halo_faces and halo_owner [n_halo_faces] (ascending faces, their owner).
+ * Host arrays allocated by the caller from the sizes; any pointer may be NULL,
+ * so a first call with NULL arrays returns the sizes.  HDG_EINVAL for a NULL
+ * elem_part, part < 0 or a negative part id. */
+int hdg_part_layout(hdg_handle h, const int32_t* elem_part, int part, hdg_part_sizes* sizes, int64_t* elems,
+                    int64_t* faces, int64_t* interface_faces, int32_t* interface_peer, int64_t* halo_faces,
+                    int32_t* halo_owner);
+
 #ifdef __cplusplus
 }
 #endif

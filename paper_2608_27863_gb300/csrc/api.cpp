@@ -52,10 +52,13 @@ int build_geometry(hdg_ctx* h, const hdg_mesh& m) {
     h->detJ.assign(h->E, 0.0);
     h->Jinv.assign((size_t)h->E * d * d, 0.0);
     h->NW.assign((size_t)h->E * nf * d, 0.0);
+    h->centroid.assign((size_t)h->E * 3, 0.0);
     for (int64_t e = 0; e < h->E; ++e) {
         double X[8][3] = {};
         for (int c = 0; c < nv; ++c)
             for (int k = 0; k < d; ++k) X[c][k] = m.vert_xyz[(size_t)m.elem_vert[(size_t)e * nv + c] * d + k];
+        for (int c = 0; c < nv; ++c)
+            for (int k = 0; k < d; ++k) h->centroid[(size_t)e * 3 + k] += X[c][k] / nv;
         double J[3][3] = {};  // J[k][r] = d x_k / d xi_r
         for (int r = 0; r < d; ++r)
             for (int k = 0; k < d; ++k) J[k][r] = 0.5 * (X[1 << r][k] - X[0][k]);

@@ -103,6 +103,7 @@ struct hdg_ctx {
     hdg::RefTables ref;
     hdg::Skeleton sk;
     std::vector<double> detJ, Jinv, NW;    // [E], [E][d][d], [E][nf][d]
+    std::vector<double> centroid;          // [E][3] vertex means (mesh partitioning)
 
     // device memory
     std::vector<void*> allocs;

@@ -479,6 +479,7 @@ int create_host(hdg_ctx* h, const hdg_tet_mesh* mesh, std::string& err) {
             }
     // per-element geometry and layout
     c->el.resize(E);
+    h->centroid.assign((size_t)E * 3, 0.0);
     int64_t moff = 0, roff = 0, koff = 0;
     for (int64_t e = 0; e < E; ++e) {
         TetElem& d = c->el[e];
@@ -526,6 +527,7 @@ int create_host(hdg_ctx* h, const hdg_tet_mesh* mesh, std::string& err) {
         double hmax = 0.0;
         for (int v = 1; v < 4; ++v)
             for (int k = 0; k < 3; ++k) hmax = std::max(hmax, std::fabs(X[v][k] - X[0][k]));
+        for (int k = 0; k < 3; ++k) h->centroid[e * 3 + k] = 0.25 * (X[0][k] + X[1][k] + X[2][k] + X[3][k]);
         bool curved = false;
         for (int ed = 0; ed < 6; ++ed)
             for (int k = 0; k < 3; ++k) {

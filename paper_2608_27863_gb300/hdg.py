@@ -40,7 +40,8 @@ EXPORTS = [
     "hdg_newton_fixed", "hdg_dirk_step", "hdg_lift_gradient", "hdg_set_preconditioner", "hdg_schwarz_setup",
     "hdg_schwarz_apply", "hdg_rb_setup", "hdg_rb_push", "hdg_rb_guess", "hdg_av_field", "hdg_tgv_diagnostics",
     "hdg_autotune", "hdg_set_tuning", "hdg_set_bc_field", "hdg_reserve", "hdg_create_tet", "hdg_create_tet_host",
-    "hdg_tet_query", "hdg_tet_layout", "hdg_tet_ref_tables", "hdg_tri_ref_tables",
+    "hdg_tet_query", "hdg_tet_layout", "hdg_tet_ref_tables", "hdg_tri_ref_tables", "hdg_partition",
+    "hdg_part_layout",
 ]
 KERNEL_CLASSES = ["point", "blocks", "elim", "assemble", "matvec", "recover", "schur"]
 
@@ -77,6 +78,11 @@ class hdg_tet_mesh(ctypes.Structure):
 class hdg_tet_sizes(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("n_elem", "n_faces", "nnzb", "n_u", "n_trace", "n_vals", "n_curved",
                                                "device_bytes")]
+
+
+class hdg_part_sizes(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int64), ("n_interior_elem", ctypes.c_int64), ("n_faces", ctypes.c_int64),
+                ("n_interface_faces", ctypes.c_int64), ("n_halo_faces", ctypes.c_int64)]
 
 
 _lib = None
@@ -137,6 +143,8 @@ def lib():
         "hdg_tet_layout": [vp] * 10,
         "hdg_tet_ref_tables": [i32, vp, vp, vp, vp],
         "hdg_tri_ref_tables": [i32, vp, vp, vp],
+        "hdg_partition": [vp, i32, vp],
+        "hdg_part_layout": [vp, vp, i32, ctypes.POINTER(hdg_part_sizes)] + [vp] * 6,
     }
     for name, args in sig.items():
         fn = getattr(L, name)
@@ -489,4 +497,39 @@ def hdg_tri_ref_tables(p):
     rc = lib().hdg_tri_ref_tables(int(p), *[out[k].ctypes.data for k in ("xs", "ws", "mu")])
     if rc != HDG_OK:
         raise HDGError(rc, "hdg_tri_ref_tables")
+    return out
+
+
+def hdg_partition(h, n_parts):
+    """Recursive coordinate bisection of the elements into n_parts parts: elem_part [E]."""
+    E = int(_n_elem(h))
+    part = np.zeros(E, np.int32)
+    _check(h, lib().hdg_partition(h, int(n_parts), part.ctypes.data))
+    return part
+
+
+def _n_elem(h):
+    """Number of elements of a quad / hex or tetrahedral handle."""
+    s = hdg_tet_sizes()
+    if lib().hdg_tet_query(h, ctypes.byref(s)) == HDG_OK:
+        return s.n_elem
+    return hdg_query_sizes(h)["n_elem"]
+
+
+def hdg_part_layout(h, elem_part, part):
+    """Layout of one part: elements (interior first), owned faces, interface faces
+    with the peer part, halo faces with their owner, and the sizes."""
+    ep = np.ascontiguousarray(elem_part, dtype=np.int32)
+    s = hdg_part_sizes()
+    _check(h, lib().hdg_part_layout(h, ep.ctypes.data, int(part), ctypes.byref(s), *([None] * 6)))
+    out = {"sizes": {n: getattr(s, n) for n, _ in hdg_part_sizes._fields_}}
+    out["elems"] = np.zeros(s.n_elem, np.int64)
+    out["faces"] = np.zeros(s.n_faces, np.int64)
+    out["interface_faces"] = np.zeros(s.n_interface_faces, np.int64)
+    out["interface_peer"] = np.zeros(s.n_interface_faces, np.int32)
+    out["halo_faces"] = np.zeros(s.n_halo_faces, np.int64)
+    out["halo_owner"] = np.zeros(s.n_halo_faces, np.int32)
+    _check(h, lib().hdg_part_layout(h, ep.ctypes.data, int(part), ctypes.byref(s),
+                                    *[out[k].ctypes.data for k in ("elems", "faces", "interface_faces",
+                                                                   "interface_peer", "halo_faces", "halo_owner")]))
     return out
