@@ -173,7 +173,11 @@ int hdg_linearize_condense(hdg_handle h, const double* U, const double* Q, const
                            const double* Ustar, const double* nu, double dt, double a_ii,
                            double* res_norm);
 
-/* y = S x on the assembled trace operator (device pointers, [F][m][Nfp]). */
+/* y = S x on the assembled trace operator (device pointers, [F][m][Nfp]; FP64
+ * vectors).  FP64 system: FP64 products and sums.  Mixed system (FP32 blocks):
+ * x is rounded to FP32 and the products are FP32; quad / hex handles sum each
+ * block in FP32 and the blocks of a row in FP64, tetrahedral handles sum the
+ * whole block row in FP32 (in a fixed order, so results are reproducible). */
 int hdg_trace_matvec(hdg_handle h, const double* x, double* y);
 /* Copy the condensed right-hand side g = sum_K (-R_uhat^K + C^K y^K) to g. */
 int hdg_trace_rhs(hdg_handle h, double* g);
