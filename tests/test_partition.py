@@ -39,6 +39,16 @@ def hex_case(H, periodic=(True, False, True), n=(5, 3, 4)):
     return h, f2e, np.asarray(conn.rowptr), np.asarray(conn.col), cen
 
 
+def quad_case(H):
+    mesh = synth.box_mesh(2, (7, 4), (0.0, 0.0), (1.4, 0.5), (True, False))
+    h = H.hdg_create(2, mesh.vert_xyz, mesh.elem_vert, mesh.periodic_map, mesh.bnd_tag, 2, 1.4, 100.0, 0.72, 0.3,
+                     host_only=True)
+    conn = Connectivity(mesh, 2)
+    f2e = np.array(conn.f2e[:, :, 0])
+    cen = mesh.vert_xyz[mesh.elem_vert].mean(axis=1)
+    return h, f2e, np.asarray(conn.rowptr), np.asarray(conn.col), cen
+
+
 def tet_mesh():
     c = [np.linspace(0, 1, 3), np.linspace(0, 0.5, 3), np.linspace(0, 0.5, 2)]
     return tm.kuhn_box((2, 2, 1), c, (False, False, False), bump=tm.wall_bump(0.05), curved_layers=1, seed=3)
@@ -89,11 +99,13 @@ def test_partition_balanced_and_cut_along_longest_extent(H, n_parts):
         assert cen[left, 0].max() <= cen[~left, 0].min()
 
 
-@pytest.mark.parametrize("case", ["hex-periodic", "hex-box", "tet"])
+@pytest.mark.parametrize("case", ["hex-periodic", "hex-box", "quad", "tet"])
 @pytest.mark.parametrize("n_parts", [2, 3, 4])
 def test_part_layout_bit_exact(H, case, n_parts):
     if case == "tet":
         h, f2e, rowptr, col, cen = tet_case(H)
+    elif case == "quad":
+        h, f2e, rowptr, col, cen = quad_case(H)
     else:
         h, f2e, rowptr, col, cen = hex_case(H, periodic=(True, False, True) if case == "hex-periodic"
                                             else (False, False, False))
