@@ -372,18 +372,24 @@ int hdg_profile_read(hdg_handle h, double* ms, int64_t* launches);
  * counterpart).  It is for callers that must not allocate device memory once
  * the handle exists: a host whose memory pool has taken the remaining HBM
  * after set-up, or a step loop that cannot afford the implicit device
- * synchronisation of cudaMalloc / cudaFree.  Same arguments and results as
- * hdg_linearize_condense (res_norm omitted); the per-chunk scratch comes from
- * a 64 MiB file-scope device array of the library instead of the handle's
- * scratch, so elements are condensed in chunks of at most 64 MiB / (scratch
- * of one element) (45 hex p=2, 15 hex p=3 elements).  The call issues no
- * cudaMalloc, cudaFree or other allocating routine.  The first call on each
- * device looks up the array's device address (cudaGetSymbolAddress) with that
- * device current, so make it before any stream capture.  Every call, from any
- * handle, shares the one array: calls whose GPU work overlaps (for example on
- * two streams) race and corrupt each other's results; serialise them.
- * Returns HDG_EINVAL if one element's scratch exceeded the array (no
- * supported (d, p) does). */
+ * synchronisation of cudaMalloc / cudaFree.  It builds the FP64 system only:
+ * the same arguments, preconditions (tag-1 boundary state and tag-3 wall
+ * temperature set where the mesh has such faces) and results as
+ * hdg_linearize_condense on an HDG_PREC_FP64 handle (res_norm omitted); a
+ * handle set to a mixed precision gets HDG_EUNSUPPORTED.  The FP64 system
+ * storage must be reserved at set-up (hdg_reserve(h, HDG_PREC_FP64)), else
+ * HDG_EINVAL.  The per-chunk scratch (trace rows, point coefficients and the
+ * per-point stabilization) comes from a 64 MiB file-scope device array of the
+ * library instead of the handle's scratch, so elements are condensed in
+ * chunks of at most 64 MiB / (scratch of one element) (45 hex p=2, 15 hex
+ * p=3 elements), whatever scratch budget the handle was created with.  The
+ * call issues no cudaMalloc, cudaFree or other allocating routine.  The first
+ * call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current, so make it before any
+ * stream capture.  Every call, from any handle, shares the one array: calls
+ * whose GPU work overlaps (for example on two streams) race and corrupt each
+ * other's results; serialise them.  Returns HDG_EINVAL if one element's
+ * scratch exceeded the array (no supported (d, p) does). */
 int hdg_linearize_condense_static(hdg_handle h, const double* U, const double* Q, const double* UH,
                                   const double* Ustar, const double* nu, double dt, double a_ii);
 

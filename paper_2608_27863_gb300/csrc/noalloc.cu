@@ -1,6 +1,7 @@
-// hdg_linearize_condense_static: the linearize + condense path with its
-// per-chunk scratch taken from a fixed, file-scope device array instead of
-// the handle's scratch allocation.  This entry point calls no allocating
+// hdg_linearize_condense_static: the FP64 linearize + condense path with its
+// per-chunk scratch (trace rows of the bordered matrix, point coefficients and
+// per-point stabilization) taken from a fixed, file-scope device array instead
+// of the handle's scratch allocation.  This entry point calls no allocating
 // CUDA or library routine.
 //
 // The scratch array (64 MiB) is part of the library image: every GPU that
@@ -59,17 +60,23 @@ int dispatch(hdg_ctx* h, const hdg::LinArgs& a) {
 
 extern "C" int hdg_linearize_condense_static(hdg_handle h, const double* U, const double* Q, const double* UH,
                                               const double* Ustar, const double* nu, double dt, double a_ii) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
+    if (h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage (created with hdg_create_host)");
     if (!U || !Q || !UH || !Ustar) return fail(h, HDG_EINVAL, "U, Q, UH and Ustar are required");
     if (!(dt > 0.0) || !(a_ii > 0.0)) return fail(h, HDG_EINVAL, "dt and a_ii must be positive");
+    // the same preconditions as hdg_linearize_condense
+    if (h->has_tag[1] && !h->ub_set) return fail(h, HDG_EINVAL, "boundary state of tag 1 not set (hdg_set_bc_state)");
+    if (h->has_tag[3] && !h->tw_set) return fail(h, HDG_EINVAL, "wall temperature of tag 3 not set (hdg_set_bc_state)");
+    if (h->precision != HDG_PREC_FP64)
+        return fail(h, HDG_EUNSUPPORTED, "the allocation-free entry point builds the FP64 system only");
     if (!h->d_vals || !h->d_top)
         return fail(h, HDG_EINVAL, "FP64 system storage not reserved (hdg_reserve(h, HDG_PREC_FP64) at set-up)");
     const size_t n_bot = (size_t)h->NT * h->LD;
     const size_t n_vc = (size_t)h->m * h->m * h->d * h->NCOEF * h->Nq;
     const size_t n_fc = (size_t)h->nf * h->m * h->m * h->NCOEF * h->Nfq;
-    const size_t per = n_bot + n_vc + n_fc;
+    const size_t n_tp = (size_t)h->nf * h->Nfq;      // per-point tau of the state-dependent stabilization
+    const size_t per = n_bot + n_vc + n_fc + n_tp;
     if (per > kStaticScratchDoubles)
         return fail(h, HDG_EINVAL, "one element needs " + std::to_string(per * 8) +
                                        " bytes of scratch, more than the 64 MiB static scratch");
@@ -82,11 +89,13 @@ extern "C" int hdg_linearize_condense_static(hdg_handle h, const double* U, cons
     double* save_bot = h->d_bot;
     double* save_vc = h->d_vcoef;
     double* save_fc = h->d_fcoef;
+    double* save_tp = h->d_taup;
     const int64_t save_chunk = h->chunk;
     const bool save_prof = h->prof;
     h->d_bot = base;
     h->d_vcoef = base + (size_t)chunk * n_bot;
     h->d_fcoef = h->d_vcoef + (size_t)chunk * n_vc;
+    h->d_taup = h->d_fcoef + (size_t)chunk * n_fc;   // sized for this chunk, not the handle's
     h->chunk = chunk;
     h->prof = false;  // event creation is an allocation
     cudaError_t e = cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), h->stream);
@@ -95,6 +104,7 @@ extern "C" int hdg_linearize_condense_static(hdg_handle h, const double* U, cons
     h->d_bot = save_bot;
     h->d_vcoef = save_vc;
     h->d_fcoef = save_fc;
+    h->d_taup = save_tp;
     h->chunk = save_chunk;
     h->prof = save_prof;
     return rc;
