@@ -167,8 +167,11 @@ int hdg_get_connectivity(hdg_handle h, int32_t* f2e, int32_t* f2lf, int32_t* e2f
  * S dUH = g (eqs. newton-linearization, local-elimination, schur-trace).
  * Inputs are device pointers (layouts above); dt and a_ii enter the stage
  * residual of eq. fully-discrete-local.  The library keeps S (BSR), g and the
- * per-element factors needed by hdg_recover_interior.  res_norm must be NULL
- * (the FP64 residual norm is hdg_residual_norm). */
+ * per-element factors needed by hdg_recover_interior.  res_norm (host,
+ * optional): when not NULL it receives ||F(W)||_2, the FP64 norm of the stage
+ * residual at the same W (eq. nonlinear-residual, as hdg_residual's norms[0],
+ * whatever the handle's precision), and the call then synchronises the
+ * stream; when NULL the call is asynchronous. */
 int hdg_linearize_condense(hdg_handle h, const double* U, const double* Q, const double* UH,
                            const double* Ustar, const double* nu, double dt, double a_ii,
                            double* res_norm);
@@ -310,9 +313,20 @@ int hdg_newton_fixed(hdg_handle h, double* U, double* Q, double* UH, const doubl
  * stage.  With use_graph != 0 the whole step (s stages x n_newton iterations)
  * is captured once as one CUDA graph and replayed.  U, Q, UH hold W^n on entry
  * and W^{n+1} on return; hist (host, optional, s (n_newton + 1) entries)
- * receives the residual norms.  Synchronises at the end. */
+ * receives the residual norms.  A and b both NULL (with s = 3) select
+ * Alexander's SDIRK3 (the tableau of hdg_sdirk3_tableau).  Synchronises at
+ * the end. */
 int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* nu, double dt, int s,
                   const double* A, const double* b, int n_newton, int m, int use_graph, double* hist);
+
+/* Alexander's three-stage, third-order, L-stable, stiffly accurate SDIRK
+ * (the DIRK method the paper cites for its time stepping, Sec. 2.3): writes
+ * the Butcher matrix A (host, [3][3] row-major, lower triangular) and the
+ * weights b (host, [3], equal to the last row of A).  The diagonal gamma is
+ * the root in (1/3, 1/2) of gamma^3 - 3 gamma^2 + 3 gamma / 2 - 1/6 = 0;
+ * a21 = (1 - gamma) / 2, b1 = -(6 gamma^2 - 16 gamma + 1) / 4,
+ * b2 = (6 gamma^2 - 20 gamma + 5) / 4.  Needs no handle. */
+int hdg_sdirk3_tableau(double* A, double* b);
 
 /* Autotuner (not from the paper).  Times every kernel variant that computes
  * the same quantities to the same accuracy on the caller's own inputs

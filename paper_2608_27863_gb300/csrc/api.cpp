@@ -537,25 +537,38 @@ int hdg_get_connectivity(hdg_handle h, int32_t* f2e, int32_t* f2lf, int32_t* e2f
     return HDG_OK;
 }
 
+}  // extern "C"
+
+namespace {
+int linearize_fp64(hdg_ctx* h, const LinArgs& a) { DISPATCH(run_linearize, h, a); }
+int linearize_mixed(hdg_ctx* h, const LinArgs& a) { DISPATCH(run_linearize_mixed, h, a); }
+}  // namespace
+
+extern "C" {
+
 int hdg_linearize_condense(hdg_handle h, const double* U, const double* Q, const double* UH, const double* Ustar,
                            const double* nu, double dt, double a_ii, double* res_norm) {
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage (created with hdg_create_host)");
     if (!U || !Q || !UH || !Ustar) return fail(h, HDG_EINVAL, "U, Q, UH and Ustar are required");
-    if (res_norm) return fail(h, HDG_EINVAL, "res_norm must be NULL");
     if (!(dt > 0.0) || !(a_ii > 0.0)) return fail(h, HDG_EINVAL, "dt and a_ii must be positive");
     if (h->has_tag[1] && !h->ub_set) return fail(h, HDG_EINVAL, "boundary state of tag 1 not set (hdg_set_bc_state)");
     if (h->has_tag[3] && !h->tw_set) return fail(h, HDG_EINVAL, "wall temperature of tag 3 not set (hdg_set_bc_state)");
+    if (h->tet && nu) return fail(h, HDG_EUNSUPPORTED, "artificial viscosity is not available on tetrahedral handles");
     CKH(cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), h->stream));
+    int rc = HDG_OK;
     if (h->tet) {
-        if (nu) return fail(h, HDG_EUNSUPPORTED, "artificial viscosity is not available on tetrahedral handles");
-        return hdg::tet::linearize(h, U, Q, UH, Ustar, dt, a_ii);
+        rc = hdg::tet::linearize(h, U, Q, UH, Ustar, dt, a_ii);
+    } else {
+        LinArgs a{U, Q, UH, Ustar, nu, dt, a_ii};
+        rc = h->precision == HDG_PREC_MIXED ? linearize_mixed(h, a) : linearize_fp64(h, a);
     }
-    LinArgs a{U, Q, UH, Ustar, nu, dt, a_ii};
-    if (h->precision == HDG_PREC_MIXED) {
-        DISPATCH(run_linearize_mixed, h, a);
-    }
-    DISPATCH(run_linearize, h, a);
+    if (rc || !res_norm) return rc;
+    // ||F(W)||_2 of the stage equations at the same W, always in FP64 (eq. nonlinear-residual)
+    double norms[3];
+    if ((rc = hdg_residual(h, U, Q, UH, Ustar, nu, dt, a_ii, nullptr, nullptr, nullptr, norms))) return rc;
+    *res_norm = norms[0];
+    return HDG_OK;
 }
 
 int hdg_trace_matvec(hdg_handle h, const double* x, double* y) {

@@ -690,10 +690,37 @@ int hdg_newton_fixed(hdg_handle h, double* U, double* Q, double* UH, const doubl
     return HDG_OK;
 }
 
+int hdg_sdirk3_tableau(double* A, double* b) {
+    if (!A || !b) return HDG_EINVAL;
+    // gamma: the root in (1/3, 1/2) of gamma^3 - 3 gamma^2 + 3 gamma / 2 - 1/6 = 0, the condition
+    // under which the three-stage, third-order SDIRK is L-stable; Newton from 0.44 converges to it
+    double g = 0.44;
+    for (int it = 0; it < 50; ++it) {
+        const double f = ((g - 3.0) * g + 1.5) * g - 1.0 / 6.0;
+        const double df = (3.0 * g - 6.0) * g + 1.5;
+        const double dg = f / df;
+        g -= dg;
+        if (std::fabs(dg) <= 1e-17) break;
+    }
+    const double b1 = -(6.0 * g * g - 16.0 * g + 1.0) / 4.0;
+    const double b2 = (6.0 * g * g - 20.0 * g + 5.0) / 4.0;
+    const double tab[9] = {g, 0.0, 0.0, (1.0 - g) / 2.0, g, 0.0, b1, b2, g};
+    for (int i = 0; i < 9; ++i) A[i] = tab[i];
+    b[0] = b1; b[1] = b2; b[2] = g;       // stiffly accurate: b is the last row of A
+    return HDG_OK;
+}
+
 int hdg_dirk_step(hdg_handle h, double* U, double* Q, double* UH, const double* nu, double dt, int s,
                   const double* A, const double* b, int n_newton, int m, int use_graph, double* hist) {
     if (!h) return HDG_EINVAL;
     if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
+    double A3[9], b3[3];
+    if (!A && !b) {                           // NULL tableau: Alexander's SDIRK3
+        if (s != 3) return fail(h, HDG_EINVAL, "a NULL tableau means the three-stage SDIRK3 (s = 3)");
+        hdg_sdirk3_tableau(A3, b3);
+        A = A3;
+        b = b3;
+    }
     if (!U || !Q || !UH || !A || !b) return fail(h, HDG_EINVAL, "NULL argument");
     if (s < 1 || s > 8 || n_newton < 1 || n_newton > 100 || m < 1 || m > 256)
         return fail(h, HDG_EINVAL, "1 <= s <= 8, 1 <= n_newton <= 100, 1 <= m <= 256");

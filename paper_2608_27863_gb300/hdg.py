@@ -41,7 +41,7 @@ EXPORTS = [
     "hdg_schwarz_apply", "hdg_rb_setup", "hdg_rb_push", "hdg_rb_guess", "hdg_av_field", "hdg_tgv_diagnostics",
     "hdg_autotune", "hdg_set_tuning", "hdg_set_bc_field", "hdg_reserve", "hdg_create_tet", "hdg_create_tet_host",
     "hdg_tet_query", "hdg_tet_layout", "hdg_tet_ref_tables", "hdg_tri_ref_tables", "hdg_partition",
-    "hdg_part_layout",
+    "hdg_part_layout", "hdg_sdirk3_tableau",
 ]
 KERNEL_CLASSES = ["point", "blocks", "elim", "assemble", "matvec", "recover", "schur"]
 
@@ -137,6 +137,7 @@ def lib():
         "hdg_rb_guess": [vp, vp, vp],
         "hdg_newton_fixed": [vp, vp, vp, vp, vp, vp, dbl, dbl, i32, i32, i32, vp],
         "hdg_dirk_step": [vp, vp, vp, vp, vp, dbl, i32, vp, vp, i32, i32, i32, vp],
+        "hdg_sdirk3_tableau": [vp, vp],
         "hdg_create_tet": [ctypes.POINTER(vp), ctypes.POINTER(hdg_tet_mesh), dbl, dbl, dbl, dbl],
         "hdg_create_tet_host": [ctypes.POINTER(vp), ctypes.POINTER(hdg_tet_mesh), dbl, dbl, dbl, dbl],
         "hdg_tet_query": [vp, ctypes.POINTER(hdg_tet_sizes)],
@@ -241,9 +242,13 @@ def hdg_get_connectivity(h):
     return out
 
 
-def hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii):
+def hdg_linearize_condense(h, U, Q, UH, Ustar, nu, dt, a_ii, res_norm=False):
+    """Linearize + condense at W = (Q, U, UH).  With res_norm=True the call also
+    returns the FP64 ||F(W)||_2 that the library evaluates (and synchronises)."""
+    out = ctypes.c_double(0.0)
     _check(h, lib().hdg_linearize_condense(h, _ptr(U), _ptr(Q), _ptr(UH), _ptr(Ustar), _ptr(nu),
-                                           float(dt), float(a_ii), None))
+                                           float(dt), float(a_ii), ctypes.byref(out) if res_norm else None))
+    return out.value if res_norm else None
 
 
 def hdg_linearize_condense_static(h, U, Q, UH, Ustar, nu, dt, a_ii):
@@ -337,26 +342,26 @@ def hdg_newton_fixed(h, U, Q, UH, Ustar, nu, dt, a_ii, n_newton=4, m=30, use_gra
     return hist
 
 
-# Alexander's three-stage, third-order, L-stable SDIRK (stiffly accurate)
-SDIRK3_GAMMA = 0.43586652150845899941601945
 def sdirk3_tableau():
-    g = SDIRK3_GAMMA
-    b1 = -(6 * g * g - 16 * g + 1) / 4
-    b2 = (6 * g * g - 20 * g + 5) / 4
-    A = np.array([[g, 0, 0], [(1 - g) / 2, g, 0], [b1, b2, g]], dtype=np.float64)
-    return A, A[-1].copy()
+    """Alexander's SDIRK3 (Butcher matrix [3][3], weights [3]) as the library defines it."""
+    A = np.zeros((3, 3), np.float64)
+    b = np.zeros(3, np.float64)
+    _check(None, lib().hdg_sdirk3_tableau(A.ctypes.data, b.ctypes.data))
+    return A, b
 
 
 def hdg_dirk_step(h, U, Q, UH, nu, dt, A=None, b=None, n_newton=4, m=30, use_graph=True):
-    """One DIRK step in place on (U, Q, UH); returns the residual history per stage."""
-    if A is None:
-        A, b = sdirk3_tableau()
-    A = np.ascontiguousarray(A, dtype=np.float64)
-    b = np.ascontiguousarray(b, dtype=np.float64)
-    s = A.shape[0]
+    """One DIRK step in place on (U, Q, UH); returns the residual history per stage.
+    A = b = None passes a NULL tableau: the library's SDIRK3."""
+    if A is None and b is None:
+        s, pa, pb = 3, None, None
+    else:
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        s, pa, pb = A.shape[0], A.ctypes.data, b.ctypes.data
     hist = np.zeros(s * (n_newton + 1), np.float64)
-    _check(h, lib().hdg_dirk_step(h, _ptr(U), _ptr(Q), _ptr(UH), _ptr(nu), float(dt), int(s), A.ctypes.data,
-                                  b.ctypes.data, int(n_newton), int(m), 1 if use_graph else 0, hist.ctypes.data))
+    _check(h, lib().hdg_dirk_step(h, _ptr(U), _ptr(Q), _ptr(UH), _ptr(nu), float(dt), int(s), pa, pb,
+                                  int(n_newton), int(m), 1 if use_graph else 0, hist.ctypes.data))
     return hist.reshape(s, n_newton + 1)
 
 

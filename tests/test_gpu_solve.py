@@ -184,3 +184,24 @@ def test_residual_and_newton_with_walls(tags):
     oq2, ou2, oh2, _ = oracle_newton(P, 1e-11, maxit=10)
     assert rel(run.U.cpu().numpy(), ou2) < 1e-10 and rel(run.UH.cpu().numpy(), oh2) < 1e-10
     run.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_linearize_returns_the_fp64_residual_norm(prec):
+    """res_norm of hdg_linearize_condense: the FP64 ||F(W)||_2 at the linearization
+    point, equal to the oracle's global residual norm whatever the system precision;
+    the condensed system is the same as without it."""
+    from paper_2608_27863_gb300 import hdg as H
+    P = synth.tiny(3, 2, seed=5, periodic=(True, False, True))
+    run = GpuRun(P)
+    if prec == "mixed":
+        H.hdg_set_params(run.h, tau=P.tau, precision=H.HDG_PREC_MIXED)
+    H.hdg_linearize_condense(run.h, run.U, run.Q, run.UH, run.Ustar, run.nu, P.dt, P.a_ii)
+    v0, g0 = run.blocks(), run.rhs()
+    r = H.hdg_linearize_condense(run.h, run.U, run.Q, run.UH, run.Ustar, run.nu, P.dt, P.a_ii, res_norm=True)
+    pb = Problem(P)
+    oq, ou, oh = pb.global_residual(pb.Q, pb.U, pb.UH)
+    full = np.sqrt(np.sum(oq ** 2) + np.sum(ou ** 2) + np.sum(oh ** 2))
+    assert abs(r - full) < TOL * full
+    assert np.array_equal(run.blocks(), v0) and np.array_equal(run.rhs(), g0)
+    run.close()

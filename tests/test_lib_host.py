@@ -163,3 +163,16 @@ def test_single_element_thick_mesh_is_rejected_or_consistent(H):
     H.hdg_destroy(h)
     assert c["f2e"].shape[0] == 4 and np.all(c["f2e"][:, 1] == -1)
     assert np.array_equal(c["rowptr"], [0, 4, 8, 12, 16])
+
+
+def test_sdirk3_tableau_from_the_library(H):
+    """The library's SDIRK3 (gamma from the L-stability cubic) against the oracle's
+    (gamma from the third-order condition): the same tableau; the binding only
+    marshals it."""
+    from oracle.dirk import alexander_sdirk3
+    A, b = H.sdirk3_tableau()
+    Ao, bo, _ = alexander_sdirk3()
+    assert np.allclose(A, Ao, rtol=0, atol=1e-14) and np.allclose(b, bo, rtol=0, atol=1e-14)
+    assert np.array_equal(b, A[-1])
+    c = A.sum(1)
+    assert abs(b @ c ** 2 - 1 / 3) < 1e-14 and abs(b @ A @ c - 1 / 6) < 1e-14
