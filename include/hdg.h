@@ -258,7 +258,15 @@ int hdg_set_preconditioner(hdg_handle h, int kind);
  * FP64 system, FP32 for the mixed one), on the stream; apply computes
  * y = M^{-1} x for device vectors x, y [F][m][Nfp] (distinct), summing the
  * patch corrections of a face in a fixed order (bitwise reproducible).
- * A zero or non-finite pivot sets the status read by hdg_status. */
+ * A zero or non-finite pivot sets the status read by hdg_status.
+ * Tetrahedral handles: the patch of element r holds its four faces' blocks
+ * (t = 60 .. 300 unknowns for face degrees 1..4); S_r is gathered from the
+ * assembled blocks and factored in place by LU with partial pivoting in the
+ * system's precision (P S_r = L U, row-major [t][t rounded up to 4]); the
+ * factors take sum_r t_r^2 values (FP64: 42 GB on the 100,800-element mesh,
+ * FP32: 21 GB), allocated on the first set-up; apply solves L U z = P R_r x
+ * per patch in the factors' precision and sums the corrections of a face over
+ * its elements in ascending element order. */
 int hdg_schwarz_setup(hdg_handle h);
 int hdg_schwarz_apply(hdg_handle h, const double* x, double* y);
 
@@ -382,6 +390,18 @@ int hdg_set_tuning(hdg_handle h, const hdg_tune* t);
 int hdg_profile(hdg_handle h, int enable);
 int hdg_profile_read(hdg_handle h, double* ms, int64_t* launches);
 
+/* Peak-rate probes of the current device (not from the paper: the roofline
+ * denominators, measured).  Each probe is a hand-written kernel that keeps
+ * one arithmetic pipe busy with independent operations on register or
+ * shared-memory data; tflops (host, 6 entries) receives the best of three
+ * timed launches (CUDA events, after one warm-up) in TFLOP/s (TOP/s for
+ * INT8): [0] FP64 FMA, [1] FP64 tensor MMA (mma.sync m8n8k4), [2] FP32 FMA,
+ * [3] TF32 tcgen05.mma (128 x 256 x 8), [4] BF16 tcgen05.mma (128 x 256 x 16),
+ * [5] INT8 mma.sync m16n8k32 (sm_103a has no tcgen05 INT8 kind).  ms (host,
+ * optional, 6 entries) receives the launch times.  Allocates 256 bytes of
+ * device memory for the call; synchronises the device's default stream. */
+int hdg_measure_peaks(double* tflops, double* ms);
+
 /* Allocation-free variant of hdg_linearize_condense (the paper has no
  * counterpart).  It is for callers that must not allocate device memory once
  * the handle exists: a host whose memory pool has taken the remaining HBM
@@ -470,7 +490,8 @@ typedef struct {
  * hdg_recover_interior, hdg_get_blocks (FP32 values after a mixed
  * linearization), hdg_status, hdg_residual, hdg_update_state,
  * hdg_blockjacobi_setup / _apply, hdg_gmres, hdg_newton, hdg_newton_fixed,
- * hdg_dirk_step, hdg_rb_*, hdg_set_preconditioner (block-Jacobi only),
+ * hdg_dirk_step, hdg_rb_*, hdg_set_preconditioner, hdg_schwarz_setup /
+ * _apply,
  * hdg_autotune / hdg_set_tuning (panel width), hdg_profile*, hdg_destroy; the
  * others return HDG_EUNSUPPORTED. */
 int hdg_create_tet(hdg_handle* out, const hdg_tet_mesh* mesh, double gamma, double Re, double Pr, double Mach);

@@ -43,3 +43,15 @@ def block_jacobi_matrix(S: np.ndarray, n_faces: int, bs: int) -> np.ndarray:
         sl = slice(F * bs, (F + 1) * bs)
         Minv[sl, sl] = np.linalg.inv(S[sl, sl])
     return Minv
+
+
+def additive_schwarz_matrix_offsets(S: np.ndarray, e2f: np.ndarray, hoff: np.ndarray) -> np.ndarray:
+    """M_AS^{-1} of eq. additive-schwarz when face blocks differ in size (tetrahedra
+    of mixed degree): face F owns the trace unknowns hoff[F] .. hoff[F+1] - 1, and
+    the patch of element e is the concatenation of its faces e2f[e] in local order."""
+    Minv = np.zeros_like(S)
+    for faces in e2f:
+        idx = np.concatenate([np.arange(hoff[F], hoff[F + 1]) for F in faces])
+        Sr = S[np.ix_(idx, idx)]                      # R_r S R_r^T
+        Minv[np.ix_(idx, idx)] += np.linalg.inv(Sr)   # R_r^T S_r^{-1} R_r
+    return Minv

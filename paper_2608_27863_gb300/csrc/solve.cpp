@@ -80,7 +80,7 @@ void dev_dot(hdg_ctx* h, const double* x, const double* y, int64_t n, double* ou
 }
 
 int precond_apply(hdg_ctx* h, const double* x, double* y) {
-    if (h->tet) return hdg::tet::bj_apply(h, x, y);
+    if (h->tet) return h->pc_kind == HDG_PC_SCHWARZ ? hdg::tet::asm_apply(h, x, y) : hdg::tet::bj_apply(h, x, y);
     int rc;
     if (h->pc_kind == HDG_PC_SCHWARZ) {
         DISPATCH_S(run_asm_apply, h, x, y);
@@ -91,11 +91,12 @@ int precond_apply(hdg_ctx* h, const double* x, double* y) {
 }
 
 bool precond_ready(const hdg_ctx* h) {
-    if (h->tet) return h->tet->bj_ready;
+    if (h->tet) return h->pc_kind == HDG_PC_SCHWARZ ? h->tet->asm_ready : h->tet->bj_ready;
     return h->pc_kind == HDG_PC_SCHWARZ ? h->asm_ready : h->bj_ready;
 }
 
 int schwarz_setup(hdg_ctx* h) {
+    if (h->tet) return hdg::tet::asm_setup(h);
     const int prec = h->sys_prec == HDG_PREC_MIXED ? HDG_PREC_MIXED : HDG_PREC_FP64;
     const int lda = (h->NT + 3) & ~3;
     const size_t need = (prec == HDG_PREC_MIXED ? sizeof(float) : sizeof(double)) * (size_t)h->E * h->NT * lda;
@@ -314,24 +315,21 @@ int hdg_set_preconditioner(hdg_handle h, int kind) {
     if (!h) return HDG_EINVAL;
     if (kind != HDG_PC_BLOCKJACOBI && kind != HDG_PC_SCHWARZ)
         return fail(h, HDG_EINVAL, "preconditioner must be HDG_PC_BLOCKJACOBI or HDG_PC_SCHWARZ");
-    if (h->tet && kind != HDG_PC_BLOCKJACOBI)
-        return fail(h, HDG_EUNSUPPORTED, "tetrahedral handles use the block-Jacobi preconditioner");
     h->pc_kind = kind;
     return HDG_OK;
 }
 
 int hdg_schwarz_setup(hdg_handle h) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
     if (!h->device || !h->have_system) return fail(h, HDG_EINVAL, "no assembled trace system");
     return schwarz_setup(h);
 }
 
 int hdg_schwarz_apply(hdg_handle h, const double* x, double* y) {
-    if (h && h->tet) return fail(h, HDG_EUNSUPPORTED, "not available for tetrahedral handles");
     if (!h) return HDG_EINVAL;
-    if (!h->asm_ready) return fail(h, HDG_EINVAL, "additive Schwarz factors not set up");
+    if (!(h->tet ? h->tet->asm_ready : h->asm_ready)) return fail(h, HDG_EINVAL, "additive Schwarz factors not set up");
     if (!x || !y || x == y) return fail(h, HDG_EINVAL, "x and y must be distinct device arrays");
+    if (h->tet) return hdg::tet::asm_apply(h, x, y);
     int rc;
     DISPATCH_S(run_asm_apply, h, x, y);
     return rc;

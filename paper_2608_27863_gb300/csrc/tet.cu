@@ -14,20 +14,19 @@
 #include "kernels.cuh"
 #include "solve.cuh"
 #include "tet.h"
+#include "tet_elim.cuh"
 
 namespace hdg {
 namespace tet {
 
 static_assert(sizeof(TetElem) % 8 == 0, "descriptor copied as 64-bit words");
 
-constexpr int NTH = 256;
 constexpr int NPT = NQMAX + 4 * NFQMAX;   // volume + face points
 constexpr int NCM = NPMAX + 4 * NFPMAX;   // columns of one component: U nodes + trace nodes
 constexpr int KC = 40;                    // contraction: points staged per step
 constexpr int SRP = 36;                   // staged row-basis stride (NPMAX rounded up to 4)
 constexpr int STP = 96;                   // staged column stride (NCM rounded up to 4)
 constexpr int NB = 16;                    // largest elimination panel width (shared-memory sizing)
-constexpr int TCW = 64;                   // elimination column tile
 constexpr int NRMAX = M * NPMAX + 4 * M * NFPMAX;
 
 // per-CTA workspace layout (doubles)
@@ -92,168 +91,6 @@ __device__ __forceinline__ const double* basis_row(const KArgs& A, const TetElem
 template <class T> __device__ __forceinline__ const T* jtab(const KArgs& A);
 template <> __device__ __forceinline__ const double* jtab<double>(const KArgs& A) { return A.tab; }
 template <> __device__ __forceinline__ const float* jtab<float>(const KArgs& A) { return A.tabf; }
-
-// runtime-sized tile of the trailing update A22 -= L21 U12 (rows rb + ty + 16 ii,
-// columns ct + tx + 16 jj)
-template <int NII, int NJJ, int NB, class RowP>
-__device__ __forceinline__ void trail_tile_rt(RowP rowp, const double* pan, const double* ust, int rb, int ct, int k0,
-                                              int kb, int tx, int ty, int NR, int NC) {
-    double acc[NII][NJJ];
-    double* rp[NII];
-#pragma unroll
-    for (int ii = 0; ii < NII; ++ii) {
-        const int r = rb + ty + 16 * ii;
-        rp[ii] = (r < NR) ? rowp(r) : nullptr;
-#pragma unroll
-        for (int jj = 0; jj < NJJ; ++jj) {
-            const int c = ct + tx + 16 * jj;
-            acc[ii][jj] = (rp[ii] && c < NC) ? rp[ii][c] : 0.0;
-        }
-    }
-    const double* lp = pan + (size_t)(rb + ty - k0) * NB;
-    for (int j = 0; j < kb; ++j) {
-        double lv[NII], uv[NJJ];
-#pragma unroll
-        for (int ii = 0; ii < NII; ++ii) lv[ii] = (rb + ty + 16 * ii < NR) ? lp[16 * ii * NB + j] : 0.0;
-#pragma unroll
-        for (int jj = 0; jj < NJJ; ++jj) uv[jj] = ust[j * TCW + tx + 16 * jj];
-#pragma unroll
-        for (int ii = 0; ii < NII; ++ii)
-#pragma unroll
-            for (int jj = 0; jj < NJJ; ++jj) acc[ii][jj] = fma(-lv[ii], uv[jj], acc[ii][jj]);
-    }
-#pragma unroll
-    for (int ii = 0; ii < NII; ++ii) {
-        if (!rp[ii]) continue;
-#pragma unroll
-        for (int jj = 0; jj < NJJ; ++jj) {
-            const int c = ct + tx + 16 * jj;
-            if (c < NC) rp[ii][c] = acc[ii][jj];
-        }
-    }
-}
-
-// Bordered elimination of the row-major matrix Mx [NR][LD] (columns NC = NR + 1):
-// LU with partial pivoting in the top NU rows (largest magnitude, lowest row on
-// ties), rows interchanged across all columns, trace rows eliminated, so that
-// the bottom-right block becomes S = Dt - Ct At^{-1} Bt and the last column
-// Rh - Ct At^{-1} Rt.
-template <int NB>
-__device__ void bordered_elim(double* Mx, int NU, int NR, int NC, int LD, double* pan, double* ust, int* piv,
-                              int* sflag) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    auto rowp = [&](int r) -> double* { return Mx + (size_t)r * LD; };
-    for (int k0 = 0; k0 < NU; k0 += NB) {
-        const int kb = min(NB, NU - k0), nrows = NR - k0, ntop = NU - k0;
-#pragma unroll 1
-        for (int idx = tid; idx < nrows * kb; idx += NTH) {
-            const int rr = idx / kb, c = idx - rr * kb;
-            pan[rr * NB + c] = rowp(k0 + rr)[k0 + c];
-        }
-        __syncthreads();
-        for (int j = 0; j < kb; ++j) {
-            if (warp == 0) {
-                double bv = -1.0;
-                int bi = INT_MAX;
-#pragma unroll 1
-                for (int rr = j + lane; rr < ntop; rr += 32) {
-                    const double v = fabs(pan[rr * NB + j]);
-                    if (v > bv) { bv = v; bi = rr; }
-                }
-                for (int off = 16; off > 0; off >>= 1) {
-                    const double ov = __shfl_down_sync(0xffffffffu, bv, off);
-                    const int oi = __shfl_down_sync(0xffffffffu, bi, off);
-                    if (ov > bv || (ov == bv && oi < bi)) { bv = ov; bi = oi; }
-                }
-                int pr = __shfl_sync(0xffffffffu, bi, 0);
-                if (pr == INT_MAX) {
-                    pr = j;
-                    if (lane == 0) *sflag |= 2;
-                }
-                if (lane < kb && pr != j) {
-                    const double t = pan[j * NB + lane];
-                    pan[j * NB + lane] = pan[pr * NB + lane];
-                    pan[pr * NB + lane] = t;
-                }
-                if (lane == 0) piv[j] = pr;
-            }
-            __syncthreads();
-            double pv = pan[j * NB + j];
-            if (pv == 0.0 || !isfinite(pv)) {
-                if (tid == 0) *sflag |= (pv == 0.0) ? 1 : 2;
-                pv = 1.0;
-            }
-            const double inv = 1.0 / pv;
-#pragma unroll 1
-            for (int rr = j + 1 + tid; rr < nrows; rr += NTH) {
-                const double l = pan[rr * NB + j] * inv;
-                pan[rr * NB + j] = l;
-                for (int c = j + 1; c < kb; ++c) pan[rr * NB + c] = fma(-l, pan[j * NB + c], pan[rr * NB + c]);
-            }
-            __syncthreads();
-        }
-#pragma unroll 1
-        for (int idx = tid; idx < nrows * kb; idx += NTH) {
-            const int rr = idx / kb, c = idx - rr * kb;
-            rowp(k0 + rr)[k0 + c] = pan[rr * NB + c];
-        }
-        const int c0 = k0 + kb;
-#pragma unroll 1
-        for (int c = c0 + tid; c < NC; c += NTH) {
-            for (int j = 0; j < kb; ++j) {
-                const int pr = piv[j];
-                if (pr != j) {
-                    double* x = rowp(k0 + j) + c;
-                    double* y = rowp(k0 + pr) + c;
-                    const double t = *x;
-                    *x = *y;
-                    *y = t;
-                }
-            }
-            double xv[NB];
-#pragma unroll
-            for (int j = 0; j < NB; ++j) {
-                if (j < kb) {
-                    double s = rowp(k0 + j)[c];
-#pragma unroll
-                    for (int i = 0; i < NB; ++i)
-                        if (i < j) s = fma(-pan[j * NB + i], xv[i], s);
-                    xv[j] = s;
-                    rowp(k0 + j)[c] = s;
-                }
-            }
-        }
-        __syncthreads();
-        const int tx = tid & 15, ty = tid >> 4;
-#pragma unroll 1
-        for (int ct = c0; ct < NC; ct += TCW) {
-            for (int idx = tid; idx < kb * TCW; idx += NTH) {
-                const int j = idx / TCW, cc = idx - j * TCW;
-                ust[j * TCW + cc] = (ct + cc < NC) ? rowp(k0 + j)[ct + cc] : 0.0;
-            }
-            __syncthreads();
-            int njj = 0;
-            while (njj < 4 && ct + 16 * njj < NC) ++njj;
-#pragma unroll 1
-            for (int rb = c0; rb < NR; rb += 64) {
-                int nii = 0;
-                while (nii < 4 && rb + 16 * nii < NR) ++nii;
-                switch (nii * 4 + njj - 5) {
-#define HDG_TT(I, J) \
-    case (I) * 4 + (J) - 5: trail_tile_rt<I, J, NB>(rowp, pan, ust, rb, ct, k0, kb, tx, ty, NR, NC); break;
-                    HDG_TT(1, 1) HDG_TT(1, 2) HDG_TT(1, 3) HDG_TT(1, 4)
-                    HDG_TT(2, 1) HDG_TT(2, 2) HDG_TT(2, 3) HDG_TT(2, 4)
-                    HDG_TT(3, 1) HDG_TT(3, 2) HDG_TT(3, 3) HDG_TT(3, 4)
-                    HDG_TT(4, 1) HDG_TT(4, 2) HDG_TT(4, 3) HDG_TT(4, 4)
-#undef HDG_TT
-                    default: break;
-                }
-            }
-            __syncthreads();
-        }
-    }
-}
-
 
 // Trace rows of the mixed form, after the FP64 elimination of the top rows
 // (LU of At with pivoting, Z = L^{-1} P Bt, z = L^{-1} P Rt): W = Ct U^{-1} in
@@ -1028,50 +865,53 @@ __global__ void __launch_bounds__(RMV_THREADS, 4) k_tet_rowmv(const T* __restric
 }
 
 // A7: dU = -U^{-1} (z + Z dUhat_K), dQ = dq0 - G dU - H dUhat_K
-__global__ void __launch_bounds__(NTH) k_tet_recover(const TetElem* el, const double* mat, const double* rec,
-                                                      const double* dUH, double* dQ, double* dU, int64_t E) {
+constexpr int REC_THREADS = 128;
+
+// Interior recovery dW_K = -y_K - X_K dUhat_K (eq. local-elimination), one CTA
+// per element: w = z + Z dUhat_K (one warp per interior row, lanes along the
+// row), dU = -U^{-1} w by blocked back substitution, then
+// dQ = Q_lift - Q + G dU + H dUhat_K per component and direction.
+__global__ void __launch_bounds__(REC_THREADS) k_tet_recover(const TetElem* el, const double* mat, const double* rec,
+                                                             const double* dUH, double* dQ, double* dU, int64_t E) {
     __shared__ double sH[4 * M * NFPMAX];
+    __shared__ double sw[M * NPMAX];
     __shared__ double sx[M * NPMAX];
-    const int tid = threadIdx.x;
-    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
-        const TetElem& d = el[e];
-        const int Np = d.Np, NU = d.NU, t = d.t, LD = d.LD, sfp = t / M;
-        const double* Mx = mat + d.moff;
-        for (int i = tid; i < t; i += NTH) {
-            int f = 0, r = i;
-            while (f < 3 && r >= M * d.nfp[f]) { r -= M * d.nfp[f]; ++f; }
-            sH[i] = dUH[d.hoff[f] + r];
-        }
-        __syncthreads();
-        for (int i = tid; i < NU; i += NTH) {
-            const double* row = Mx + (int64_t)i * LD;
-            double s = row[NU + t];
-            for (int c = 0; c < t; ++c) s = fma(row[NU + c], sH[c], s);
-            sx[i] = s;
-        }
-        __syncthreads();
-        for (int i = NU - 1; i >= 0; --i) {
-            const double xi = sx[i] / Mx[(int64_t)i * LD + i];
-            __syncthreads();
-            if (tid == 0) sx[i] = xi;
-            for (int j = tid; j < i; j += NTH) sx[j] -= Mx[(int64_t)j * LD + i] * xi;
-            __syncthreads();
-        }
-        for (int i = tid; i < NU; i += NTH) dU[d.uoff + i] = -sx[i];
-        const double* Gk = rec + d.roff;
-        const double* Hk = Gk + 3 * Np * Np;
-        const double* dq0 = Hk + 3 * Np * sfp;
-        for (int idx = tid; idx < 3 * NU; idx += NTH) {
-            const int k = idx / NU, rem = idx - k * NU, a = rem / Np, i = rem - a * Np;
-            double s = dq0[idx];
-            for (int j = 0; j < Np; ++j) s += Gk[((int64_t)k * Np + i) * Np + j] * sx[a * Np + j];
-            int cp = 0;
-            for (int f = 0; f < 4; ++f)
-                for (int l = 0; l < d.nfp[f]; ++l, ++cp)
-                    s -= Hk[((int64_t)k * Np + i) * sfp + cp] * sH[d.toff[f] + a * d.nfp[f] + l];
-            dQ[3 * d.uoff + idx] = s;
-        }
-        __syncthreads();
+    __shared__ double sD[32 * 33];
+    __shared__ double part[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t e = blockIdx.x;
+    if (e >= E) return;
+    const TetElem& d = el[e];
+    const int Np = d.Np, NU = d.NU, t = d.t, LD = d.LD, sfp = t / M;
+    const double* Mx = mat + d.moff;
+    for (int i = tid; i < t; i += REC_THREADS) {
+        int f = 0, r = i;
+        while (f < 3 && r >= M * d.nfp[f]) { r -= M * d.nfp[f]; ++f; }
+        sH[i] = dUH[d.hoff[f] + r];
+    }
+    __syncthreads();
+    for (int i = warp; i < NU; i += REC_THREADS / 32) {
+        const double* row = Mx + (int64_t)i * LD;
+        double s = 0.0;
+        for (int c = lane; c < t; c += 32) s = fma(row[NU + c], sH[c], s);
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane == 0) sw[i] = s + row[NU + t];
+    }
+    __syncthreads();
+    upper_solve_blocked<REC_THREADS>(Mx, LD, NU, sw, sx, sD, part);
+    for (int i = tid; i < NU; i += REC_THREADS) dU[d.uoff + i] = -sx[i];
+    const double* Gk = rec + d.roff;
+    const double* Hk = Gk + 3 * Np * Np;
+    const double* dq0 = Hk + 3 * Np * sfp;
+    for (int idx = tid; idx < 3 * NU; idx += REC_THREADS) {
+        const int k = idx / NU, rem = idx - k * NU, a = rem / Np, i = rem - a * Np;
+        double s = dq0[idx];
+        for (int j = 0; j < Np; ++j) s += Gk[((int64_t)k * Np + i) * Np + j] * sx[a * Np + j];
+        int cp = 0;
+        for (int f = 0; f < 4; ++f)
+            for (int l = 0; l < d.nfp[f]; ++l, ++cp)
+                s -= Hk[((int64_t)k * Np + i) * sfp + cp] * sH[d.toff[f] + a * d.nfp[f] + l];
+        dQ[3 * d.uoff + idx] = s;
     }
 }
 
@@ -1482,6 +1322,7 @@ int linearize(hdg_ctx* h, const double* U, const double* Q, const double* UH, co
     c->sys_prec = h->precision == HDG_PREC_FP64 ? HDG_PREC_FP64 : HDG_PREC_MIXED;
     h->have_system = true;
     c->bj_ready = false;       // the diagonal blocks changed
+    c->asm_ready = false;      // and so did the patches
     return HDG_OK;
 }
 
@@ -1502,9 +1343,8 @@ int matvec(hdg_ctx* h, const double* x, double* y) {
 
 int recover(hdg_ctx* h, const double* dUH, double* dQ, double* dU) {
     Ctx* c = h->tet;
-    const unsigned g = (unsigned)std::min<int64_t>(c->E, 4 * 152);
     prof_begin(h, HDG_K_RECOVER);
-    k_tet_recover<<<g, NTH, 0, h->stream>>>(c->d_el, c->d_mat, c->d_rec, dUH, dQ, dU, c->E);
+    k_tet_recover<<<(unsigned)c->E, REC_THREADS, 0, h->stream>>>(c->d_el, c->d_mat, c->d_rec, dUH, dQ, dU, c->E);
     prof_end(h);
     TET_CK(cudaGetLastError());
     return HDG_OK;

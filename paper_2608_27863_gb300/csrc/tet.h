@@ -110,6 +110,17 @@ struct Ctx {
     int n_slots = 0;
     int64_t work_stride = 0;
     bool have_system = false;
+    // additive Schwarz on element face patches (allocated on the first set-up)
+    int64_t* d_aoff = nullptr;             // [E + 1] offsets of the patch factors, [t][LDA] each, LDA = t rounded to 4
+    int64_t* d_poff = nullptr;             // [E + 1] offsets of the patch vectors, t each
+    double* d_asm = nullptr;               // LU factors of the patches (FP64 system)
+    float* d_asm32 = nullptr;              // LU factors of the patches (mixed form)
+    int32_t* d_asmperm = nullptr;          // [sum t] row permutation of each patch as a gather map
+    double* d_asmz = nullptr;              // [sum t] patch corrections
+    int32_t* d_asmnext = nullptr;          // work counter of the set-up
+    int64_t n_asm = 0, n_patch = 0;
+    int asm_prec = -1;                     // precision of the stored factors
+    bool asm_ready = false;
 };
 
 // Host set-up: tables, skeleton, geometry, layout; error text in err.
@@ -128,6 +139,9 @@ int residual(hdg_ctx* h, const double* U, const double* Q, const double* UH, con
              double a_ii, double* Rq, double* Ru, double* Ruh, double* norms);
 int bj_setup(hdg_ctx* h);
 int bj_apply(hdg_ctx* h, const double* x, double* y);
+// additive Schwarz on element face patches (tet_schwarz.cu)
+int asm_setup(hdg_ctx* h);
+int asm_apply(hdg_ctx* h, const double* x, double* y);
 
 }  // namespace tet
 }  // namespace hdg

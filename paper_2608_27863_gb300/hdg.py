@@ -41,7 +41,7 @@ EXPORTS = [
     "hdg_schwarz_apply", "hdg_rb_setup", "hdg_rb_push", "hdg_rb_guess", "hdg_av_field", "hdg_tgv_diagnostics",
     "hdg_autotune", "hdg_set_tuning", "hdg_set_bc_field", "hdg_reserve", "hdg_create_tet", "hdg_create_tet_host",
     "hdg_tet_query", "hdg_tet_layout", "hdg_tet_ref_tables", "hdg_tri_ref_tables", "hdg_partition",
-    "hdg_part_layout", "hdg_sdirk3_tableau",
+    "hdg_part_layout", "hdg_sdirk3_tableau", "hdg_measure_peaks",
 ]
 KERNEL_CLASSES = ["point", "blocks", "elim", "assemble", "matvec", "recover", "schur"]
 
@@ -138,6 +138,7 @@ def lib():
         "hdg_newton_fixed": [vp, vp, vp, vp, vp, vp, dbl, dbl, i32, i32, i32, vp],
         "hdg_dirk_step": [vp, vp, vp, vp, vp, dbl, i32, vp, vp, i32, i32, i32, vp],
         "hdg_sdirk3_tableau": [vp, vp],
+        "hdg_measure_peaks": [vp, vp],
         "hdg_create_tet": [ctypes.POINTER(vp), ctypes.POINTER(hdg_tet_mesh), dbl, dbl, dbl, dbl],
         "hdg_create_tet_host": [ctypes.POINTER(vp), ctypes.POINTER(hdg_tet_mesh), dbl, dbl, dbl, dbl],
         "hdg_tet_query": [vp, ctypes.POINTER(hdg_tet_sizes)],
@@ -340,6 +341,17 @@ def hdg_newton_fixed(h, U, Q, UH, Ustar, nu, dt, a_ii, n_newton=4, m=30, use_gra
     _check(h, lib().hdg_newton_fixed(h, _ptr(U), _ptr(Q), _ptr(UH), _ptr(Ustar), _ptr(nu), float(dt), float(a_ii),
                                      int(n_newton), int(m), 1 if use_graph else 0, hist.ctypes.data))
     return hist
+
+
+PEAK_NAMES = ["fp64_fma", "fp64_mma", "fp32_fma", "tf32_tcgen05", "bf16_tcgen05", "int8_mma_sync"]
+
+
+def hdg_measure_peaks():
+    """Measured peak rates of the current device (TFLOP/s; TOP/s for INT8) and launch times."""
+    t = np.zeros(6, np.float64)
+    ms = np.zeros(6, np.float64)
+    _check(None, lib().hdg_measure_peaks(t.ctypes.data, ms.ctypes.data))
+    return {n: float(v) for n, v in zip(PEAK_NAMES, t)}, {n: float(v) for n, v in zip(PEAK_NAMES, ms)}
 
 
 def sdirk3_tableau():

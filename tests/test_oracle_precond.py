@@ -72,3 +72,41 @@ def test_block_jacobi_is_exact_on_block_diagonal_operator():
     # and the additive Schwarz operator is exactly twice that on a periodic mesh
     M = additive_schwarz_matrix(S, conn, bs)
     assert np.allclose(M @ S, 2 * np.eye(S.shape[0]), atol=1e-11)
+
+
+def test_variable_block_schwarz_closed_form_and_uniform_case():
+    """Faces of different sizes (tetrahedra of mixed degree): on a block-diagonal
+    operator the patch solves give n_F S_FF^{-1} x_F on every face; with equal
+    sizes the variable-size form is the uniform one."""
+    from oracle.precond import additive_schwarz_matrix_offsets
+    from oracle.tet import TetConnectivity
+    from synth import tetmesh as tm
+    mesh = tm.kuhn_box((3, 1, 2), [np.linspace(0, 1, 4), np.linspace(0, .5, 2), np.linspace(0, .5, 3)],
+                       (True, False, False), seed=3)
+    conn = TetConnectivity(mesh)
+    hoff = np.asarray(conn.hoff)
+    sizes = np.diff(hoff)
+    assert len(set(sizes.tolist())) > 1
+    rng = np.random.default_rng(4)
+    n = hoff[-1]
+    S = np.zeros((n, n))
+    for F in range(len(sizes)):
+        sl = slice(hoff[F], hoff[F + 1])
+        S[sl, sl] = rng.normal(size=(sizes[F], sizes[F])) + 3 * sizes[F] * np.eye(sizes[F])
+    M = additive_schwarz_matrix_offsets(S, np.asarray(conn.e2f), hoff)
+    x = rng.normal(size=n)
+    y = M @ x
+    nF = (np.asarray(conn.f2e)[:, :, 0] >= 0).sum(axis=1)
+    assert (nF == 1).any() and (nF == 2).any()
+    for F in range(len(sizes)):
+        sl = slice(hoff[F], hoff[F + 1])
+        ref = nF[F] * np.linalg.solve(S[sl, sl], x[sl])
+        assert np.allclose(y[sl], ref, rtol=1e-12, atol=1e-12 * np.abs(ref).max())
+    # uniform sizes: the hex form
+    mesh2 = synth.box_mesh(2, (3, 3), (0, 0), (1, 1), (True, True))
+    c2 = Connectivity(mesh2, 1)
+    bs = 4 * 2
+    S2 = pattern_matrix(c2, bs, np.random.default_rng(5))
+    h2 = np.arange(c2.n_faces + 1) * bs
+    assert np.allclose(additive_schwarz_matrix_offsets(S2, c2.e2f, h2), additive_schwarz_matrix(S2, c2, bs),
+                       rtol=0, atol=1e-12 * np.abs(S2).max())

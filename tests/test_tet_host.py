@@ -88,6 +88,7 @@ def test_tet_argument_errors(H):
     try:                                                   # hex-only entry points refuse tetrahedral handles
         assert H.lib().hdg_lift_gradient(h, None, None, None) == H.HDG_EUNSUPPORTED
         assert H.lib().hdg_reserve(h, 0) == H.HDG_EUNSUPPORTED
-        assert H.lib().hdg_set_preconditioner(h, H.HDG_PC_SCHWARZ) == H.HDG_EUNSUPPORTED
+        assert H.lib().hdg_set_preconditioner(h, H.HDG_PC_SCHWARZ) == H.HDG_OK   # patches of mixed size
+        assert H.lib().hdg_schwarz_setup(h) == H.HDG_EINVAL                       # nothing assembled on the host
     finally:
         H.hdg_destroy(h)
