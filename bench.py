@@ -87,6 +87,37 @@ def make_tet_problem(name, host_layout=None):
     return P, m
 
 
+def hbm_peak_gbs():
+    """Measured copy bandwidth of the GB300s (GB/s) and its source."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "MEASURED_PEAKS.json (measured)"
+    except Exception:
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def tet_recover_bytes(layout, elem_p):
+    """Bytes the interior recovery must move per launch: per element the interior
+    rows' trace part and right-hand side NU (t + 1), the upper triangle of the
+    interior factor NU (NU + 1) / 2, the recovery data G, H, dq0 (3 Np^2 +
+    3 Np sum nfp + 3 NU), the element's trace values t; writes dU, dQ (4 NU)."""
+    import numpy as np
+    fp = layout["face_p"][layout["e2f"]]
+    Np = (elem_p + 1) * (elem_p + 2) * (elem_p + 3) // 6
+    sfp = ((fp + 1) * (fp + 2) // 2).sum(1)
+    NU, t = 5 * Np, 5 * sfp
+    words = NU * (t + 1) + NU * (NU + 1) / 2 + 3 * Np * Np + 3 * Np * sfp + 3 * NU + t + 4 * NU
+    return float(8 * words.sum())
+
+
+def hex_recover_bytes(d, p, E):
+    """The same for quad / hex elements: interior rows NU (NT + 1) + NU (NU + 1) / 2,
+    dq0 (NQV), the element trace NT; writes dU, dQ (NU + NQV)."""
+    m, Np = d + 2, (p + 1) ** d
+    NU, NQV, NT = m * Np, d * m * Np, 2 * d * m * (p + 1) ** (d - 1)
+    return 8.0 * E * (NU * (NT + 1) + NU * (NU + 1) / 2 + NQV + NT + NU + NQV)
+
+
 def tet_flops(layout, elem_p):
     """Algorithmic FP64 flops per element of the tetrahedral linearize + condense kernel:
     point values and lifting operators, contraction (element and trace rows, with the
@@ -129,6 +160,7 @@ def run_tet(args, rank, world, local_rank):
         pool = oracle_pool(args.workload, ncores)      # before the first GPU call
     torch.cuda.set_device(local_rank)
     B.build()
+    peaks, _ = H.hdg_measure_peaks()           # hand-written pipe probes on this GPU (untimed)
     from synth import tetmesh as tm
     m0 = tm.config4_mesh(**WORKLOADS[args.workload]["kw"])
     hh = H.hdg_create_tet(m0.vert_xyz, m0.elem_vert, m0.periodic_map, m0.bnd_tag, m0.elem_p, m0.geo, 1.4, 1e5,
@@ -255,6 +287,7 @@ def run_tet(args, rank, world, local_rank):
              "clocks": clocks_m}
     if not args.no_newton and mixed is not None:
         newton = {}
+        H.hdg_set_preconditioner(h, H.HDG_PC_SCHWARZ if args.precond == "schwarz" else H.HDG_PC_BLOCKJACOBI)
         for name, prec in (("fp64", H.HDG_PREC_FP64), ("mixed", H.HDG_PREC_MIXED)):
             H.hdg_set_params(h, tau=P.tau, precision=prec)
             H.hdg_set_tuning(h, elim_nb=tuning[name]["elim_nb"])
@@ -271,7 +304,9 @@ def run_tet(args, rank, world, local_rank):
                                            torch.linalg.norm(newton["fp64_U"]))
         del newton["mixed_U"], newton["fp64_U"]
         newton["tol"] = 1e-8
-        newton["gmres"] = "restart 100, at most 100 iterations per Newton step, relative tolerance 1e-6, block-Jacobi"
+        newton["gmres"] = ("restart 100, at most 100 iterations per Newton step, relative tolerance 1e-6, %s" %
+                           {"schwarz": "additive Schwarz on element face patches (factors in the system's precision)",
+                            "bj": "block-Jacobi"}[args.precond])
         newton["speedup"] = newton["fp64"]["seconds"] / newton["mixed"]["seconds"]
         mixed["newton"] = newton
         H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_FP64)
@@ -311,20 +346,37 @@ def run_tet(args, rank, world, local_rank):
                                        "launch on the 3,600-element mesh of the same generator, per element, times "
                                        "the elements of one launch",
                      "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz (derived)" % smmax,
+                     "peak_measured": peaks["fp64_fma"], "frac_of_measured": achieved / peaks["fp64_fma"],
+                     "peak_measured_source": "DFMA-chain probe (hdg_measure_peaks) in this run",
                      "flops_per_element": float(fl["total"].mean()),
                      "flops_split": {k: float(v.sum()) for k, v in fl.items()}},
         "kernels": kern,
+        "recover_roofline": recover_roofline("k_tet_recover", tet_recover_bytes(layout, m.elem_p.astype(np.int64)),
+                                             prof["recover"]),
         "mixed": mixed,
         "e2e": {"value": replica_throughput(world, E, n_e2e, e2e_ms), "unit": "elements/s", "steps": n_e2e,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": sum(v[1] for v in prof.values()) / args.steps,
         "clocks": clocks,
         "tuning": tuning,
+        "peaks_measured_tflops": peaks,
     }
     if cpu is not None:
         out["cpu_baseline"] = cpu
     H.hdg_destroy(h)
     return out
+
+
+def recover_roofline(kernel, nbytes, prof_entry):
+    """HBM roofline of the interior recovery: algorithmic bytes per launch over the
+    launch's mean event time."""
+    ms, n = prof_entry
+    if not n:
+        return None
+    peak, src = hbm_peak_gbs()
+    gbs = nbytes / (ms / n * 1e-3) / 1e9
+    return {"bound": "hbm", "kernel": kernel, "bytes_per_launch": nbytes, "ms_per_launch": ms / n,
+            "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_source": src}
 
 
 def make_problem(name, cpu_sample=False):
@@ -535,6 +587,7 @@ def run_ours(args, rank, world, local_rank):
 
     torch.cuda.set_device(local_rank)
     B.build()
+    peaks, _ = H.hdg_measure_peaks()           # hand-written pipe probes on this GPU (untimed)
     wl = WORKLOADS[args.workload]
     mixed_only = wl.get("mixed_only", False)
     P = make_problem(args.workload)
@@ -752,15 +805,19 @@ def run_ours(args, rank, world, local_rank):
                                        "8^3 case, per element, times the elements of one launch" % dom,
                      "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz (derived); cuBLAS DGEMM "
                                     "measured in this run: %.3f TFLOP/s" % (smmax, dgemm),
+                     "peak_measured": peaks["fp64_fma"], "frac_of_measured": achieved / peaks["fp64_fma"],
+                     "peak_measured_source": "DFMA-chain probe (hdg_measure_peaks) in this run",
                      "flops_per_element": fl[dom]},
         "gflops_total": fl["total"] * E * args.steps / (t_ms * 1e-3) / 1e9,
         "kernels": kern,
+        "recover_roofline": recover_roofline("k_recover", hex_recover_bytes(m.dim, P.p, E), prof["recover"]),
         "mixed": mixed,
         "e2e": {"value": replica_throughput(world, E, args.steps, e2e_ms), "unit": "elements/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches,
         "clocks": clocks,
         "tuning": tuning,
+        "peaks_measured_tflops": peaks,
     }
     if cpu is not None:
         out["cpu_baseline"] = cpu
@@ -858,6 +915,8 @@ def main():
     ap.add_argument("--dirk", action="store_true",
                     help="tetrahedral workloads: also time one graph-captured SDIRK3 step (3 stages x 4 Newton)")
     ap.add_argument("--mixed-prec", choices=["fp32", "tf32", "3xtf32"], default="3xtf32")
+    ap.add_argument("--precond", choices=["schwarz", "bj"], default="schwarz",
+                    help="tetrahedral workloads: preconditioner of the Newton comparison's GMRES")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--elim-nb", type=int, choices=[8, 16], default=None,
                     help="fix the FP64 elimination panel width instead of autotuning (profiling runs)")

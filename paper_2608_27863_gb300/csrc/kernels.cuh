@@ -1060,6 +1060,47 @@ __global__ void __launch_bounds__(MvShape<C>::NTH) k_matvec(const int32_t* rowpt
 // ----------------------------------------------------------------------------
 // A7: interior recovery dU = -U^{-1}(z + Z dUhat_K), dQ = dq0 - L dU + Lambda dUhat_K
 // ----------------------------------------------------------------------------
+// x = U^{-1} w for an upper-triangular, row-major FP64 matrix U in global
+// memory (row stride ld, n rows), w and x in shared memory, by the whole CTA of
+// NT threads: 32-row diagonal blocks from the bottom; the rows of a block are
+// first reduced by the solved part (one warp per row, lanes along the row, so
+// the reads are coalesced and a whole block's rows are in flight at once), the
+// block's 32 x 32 diagonal part is staged in shared memory, and warp 0 solves
+// it with shuffles.  The serial chain is n / 32 block steps instead of n
+// dependent row reads.  sD: 32 x 33 doubles, part: 32 doubles of shared memory.
+template <int NT>
+__device__ void upper_solve_blocked(const double* U, int64_t ld, int n, const double* w, double* x, double* sD,
+                                    double* part) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = NT / 32;
+#pragma unroll 1
+    for (int b1 = n; b1 > 0; b1 -= 32) {
+        const int b0 = max(0, b1 - 32), nb = b1 - b0;
+        for (int rr = warp; rr < nb; rr += NW) {
+            const double* row = U + (int64_t)(b0 + rr) * ld;
+            double s = 0.0;
+            for (int j = b1 + lane; j < n; j += 32) s = fma(row[j], x[j], s);
+            for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+            if (lane == 0) part[rr] = s;
+        }
+        for (int idx = tid; idx < nb * 32; idx += NT) {
+            const int r = idx >> 5, c = idx & 31;
+            if (c < nb) sD[r * 33 + c] = U[(int64_t)(b0 + r) * ld + b0 + c];
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double v = lane < nb ? w[b0 + lane] - part[lane] : 0.0;
+            for (int k = nb - 1; k >= 0; --k) {
+                if (lane == k) v = v / sD[k * 33 + k];
+                const double xk = __shfl_sync(0xffffffffu, v, k);
+                if (lane < k) v = fma(-sD[lane * 33 + k], xk, v);
+            }
+            if (lane < nb) x[b0 + lane] = v;
+        }
+        __syncthreads();
+    }
+}
+
 struct RecArgs {
     const double* top; const double* dq0; const double* geo;
     DeviceTables tab;
@@ -1078,6 +1119,8 @@ __global__ void __launch_bounds__(NTH) k_recover(RecArgs A) {
     __shared__ double w[NU];
     __shared__ double x[NU];
     __shared__ double geo[GEO];
+    __shared__ double sD[32 * 33];
+    __shared__ double part[32];
     for (int i = tid; i < NT; i += NTH) {
         int f = i / (M * NFP), rem = i - f * M * NFP, a = rem / NFP, l = rem - a * NFP;
         int64_t F = A.e2f[e * NF + f];
@@ -1090,22 +1133,13 @@ __global__ void __launch_bounds__(NTH) k_recover(RecArgs A) {
     for (int i = warp; i < NU; i += NTH / 32) {
         const double* row = Tm + (size_t)i * LD;
         double s = 0.0;
+#pragma unroll
         for (int c = lane; c < NT; c += 32) s = fma(row[NU + c], duh[c], s);
         for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
         if (lane == 0) w[i] = s + row[NC - 1];
     }
     __syncthreads();
-    if (warp == 0) {
-        for (int i = NU - 1; i >= 0; --i) {
-            const double* row = Tm + (size_t)i * LD;
-            double s = 0.0;
-            for (int j = i + 1 + lane; j < NU; j += 32) s = fma(row[j], x[j], s);
-            for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
-            if (lane == 0) x[i] = (w[i] - s) / row[i];
-            __syncwarp();
-        }
-    }
-    __syncthreads();
+    upper_solve_blocked<NTH>(Tm, LD, NU, w, x, sD, part);
     for (int i = tid; i < NU; i += NTH) A.dU[e * NU + i] = -x[i];
     const double detJ = geo[0];
     const double* Jinv = geo + 1;

@@ -140,18 +140,27 @@ def test_chunking_is_bitwise_invisible():
     assert np.array_equal(vb, vc)   # run-to-run determinism
 
 
+def sampled_rows(P, seed, n):
+    """n seeded face rows plus the faces of the first and last elements (which
+    include faces identified across the periodic boundary)."""
+    from oracle.mesh import Connectivity
+    c = Connectivity(P.mesh, P.p)
+    rows = {int(r) for r in synth.splitmix64(seed, n) % np.uint64(c.n_faces)}
+    rows |= {int(F) for e in (0, P.mesh.n_elem - 1) for F in c.e2f[e]}
+    return sorted(rows)
+
+
 def test_config2_full_size_sampled():
-    """16^3 = 4096 hexes p = 2 (the timed workload), sampled block rows."""
+    """16^3 = 4096 hexes p = 2, sampled block rows (24 seeded + 12 periodic-edge faces)."""
     P = synth.config2()
-    rows = list(synth.splitmix64(21, 6) % np.uint64(P.mesh.n_faces()))
-    compare(P, rows=[int(r) for r in rows])
+    compare(P, rows=sampled_rows(P, 21, 24))
 
 
 def test_config3_full_size_sampled():
-    """24^3 = 13824 hexes p = 3, Sutherland + artificial viscosity, sampled rows."""
+    """24^3 = 13824 hexes p = 3, Sutherland + artificial viscosity, sampled rows
+    (10 seeded + 12 periodic-edge faces)."""
     P = synth.config3()
-    rows = list(synth.splitmix64(22, 2) % np.uint64(P.mesh.n_faces()))
-    compare(P, rows=[int(r) for r in rows])
+    compare(P, rows=sampled_rows(P, 22, 10))
 
 
 def test_nonfinite_input_is_reported():
