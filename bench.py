@@ -234,7 +234,7 @@ def run_tet(args, rank, world, local_rank):
     n_mixed, n_e2e = min(args.steps, 5), min(args.steps, 3)
     if not args.no_mixed:
         H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_MIXED)
-        tuning["mixed"] = tune()
+        tuning["mixed"] = tune(False)
         tm_ms, prof_m, clocks_m = timed(n_mixed, min(args.warmup, 2))
         H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_FP64)
         H.hdg_set_tuning(h, elim_nb=tuning["fp64"]["elim_nb"])
@@ -645,17 +645,20 @@ def run_ours(args, rank, world, local_rank):
             dist.barrier()
         return t_ms, prof, clk.summary()
 
-    def tune():
+    def tune(fp64):
         # the project's autotuner picks among equivalent kernel variants on these inputs (untimed)
         if args.no_autotune or args.elim_nb or args.tuning:
             if args.elim_nb or args.tuning:      # a fixed variant (profiling runs)
                 kw = dict(elim_nb=args.elim_nb or 16, elim_minb=2,
-                          schur_mode={"fp32": 0, "tf32": 1, "3xtf32": 2}[args.mixed_prec],
+                          schur_mode=0 if fp64 else {"fp32": 0, "tf32": 1, "3xtf32": 2}[args.mixed_prec],
                           blocks_mode=1 if m.dim == 3 else 0, elim_mixed_minb=2, blocks64_mode=1)
+                # "--tuning k=v,..." sets both legs; "fp64.k=v" / "mixed.k=v" one leg
                 for item in (args.tuning or "").split(","):
                     if item:
                         k, v = item.split("=")
-                        kw[k] = int(v)
+                        leg, _, key = k.rpartition(".")
+                        if not leg or leg == ("fp64" if fp64 else "mixed"):
+                            kw[key] = int(v)
                 H.hdg_set_tuning(h, **kw)
                 return dict(kw, fixed=True)
             return None
@@ -668,7 +671,7 @@ def run_ours(args, rank, world, local_rank):
     tuning = {}
     if not mixed_only:
         set_prec(H.HDG_PREC_FP64)
-        tuning["fp64"] = tune()
+        tuning["fp64"] = tune(True)
         for _ in range(args.warmup):
             step()
         torch.cuda.synchronize()
@@ -680,7 +683,7 @@ def run_ours(args, rank, world, local_rank):
     mixed_prec = {"fp32": H.HDG_PREC_MIXED, "tf32": H.HDG_PREC_MIXED_TF32,
                   "3xtf32": H.HDG_PREC_MIXED_3XTF32}[args.mixed_prec]
     set_prec(mixed_prec)
-    tuning["mixed"] = tune()
+    tuning["mixed"] = tune(False)
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -922,7 +925,8 @@ def main():
                     help="fix the FP64 elimination panel width instead of autotuning (profiling runs)")
     ap.add_argument("--tuning", default=None,
                     help="fixed kernel variants instead of autotuning, e.g. elim_nb=8,elim_minb=1,"
-                         "blocks64_mode=1,blocks_mode=1,elim_mixed_minb=3 (profiling runs)")
+                         "blocks64_mode=1,blocks_mode=1,elim_mixed_minb=3,fp64.schur_mode=3 (profiling runs; "
+                         "a 'fp64.' or 'mixed.' prefix applies an item to one leg)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))

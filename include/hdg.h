@@ -343,8 +343,12 @@ int hdg_sdirk3_tableau(double* A, double* b);
  *  - FP64 form: the volume contraction as a dense GEMM (blocks64_mode 0)
  *    or by sum factorisation over the tensor-product basis (1), the
  *    elimination kernel's panel width (16 or 8 columns) and the residency it
- *    is compiled for (2 or 1 CTAs per SM); results differ only by rounding
- *    order;
+ *    is compiled for (2 or 1 CTAs per SM), and the Schur product
+ *    S = Dt - W Z inside the FP64 elimination (schur_mode 0) or on the BF16
+ *    tensor cores by exact digit splitting of the FP64 factors (schur_mode 3:
+ *    W and Z cut into 6..8 digits of 6..8 bits, products accumulated exactly
+ *    in FP32, combined and subtracted in FP64; truncation below 2^-48 of the
+ *    row / column scales); results agree to FP64 rounding level;
  *  - mixed form: the elimination as one fused kernel (at 2 or 3 CTAs per
  *    SM) or split into an FP64 LU (panel width 16 or 8) and two FP32
  *    triangular solves,

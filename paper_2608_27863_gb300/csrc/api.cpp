@@ -368,13 +368,16 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
     int cand[16][7];
     int n = 0;
     if (h->precision == HDG_PREC_FP64) {
+        // Schur product in the FP64 elimination (schur_mode 0) or on the tensor cores by exact
+        // digit splitting (3); both FP64-accurate
         const int nbs[2] = {16, 8}, minbs[2] = {2, 1};
-        for (int bm64 : {1, 0})
-            for (int a = 0; a < 2; ++a)
-                for (int b = 0; b < 2; ++b) {
-                    cand[n][0] = nbs[a]; cand[n][1] = minbs[b]; cand[n][2] = h->schur_mode; cand[n][3] = h->blocks_mode;
-                    cand[n][4] = h->elim_mixed_minb; cand[n][5] = bm64; cand[n][6] = h->elim_mixed_split; ++n;
-                }
+        for (int sm : {0, 3})
+            for (int bm64 : {1, 0})
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 2; ++b) {
+                        cand[n][0] = nbs[a]; cand[n][1] = minbs[b]; cand[n][2] = sm; cand[n][3] = h->blocks_mode;
+                        cand[n][4] = h->elim_mixed_minb; cand[n][5] = bm64; cand[n][6] = h->elim_mixed_split; ++n;
+                    }
     } else {
         // FP32 SIMT and 3xTF32 tensor-core products are both FP32-accurate: the volume
         // contraction always, the Schur product unless TF32 / 3xTF32 was requested explicitly
@@ -403,10 +406,15 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
     CKH(cudaEventCreate(&ev[1]));
     double ms[16];
     int best = 0, rc = HDG_OK;
+    const bool fp64 = h->precision == HDG_PREC_FP64;
+    auto apply_schur = [&](int sm) {
+        if (fp64) h->schur64_mode = sm == 3 ? 1 : 0;
+        else h->schur_mode = sm;
+    };
     for (int c = 0; c < n && rc == HDG_OK; ++c) {
         h->elim_nb = cand[c][0];
         h->elim_minb = cand[c][1];
-        h->schur_mode = cand[c][2];
+        apply_schur(cand[c][2]);
         h->blocks_mode = cand[c][3];
         h->elim_mixed_minb = cand[c][4];
         h->blocks64_mode = cand[c][5];
@@ -428,13 +436,14 @@ int hdg_autotune(hdg_handle h, const double* U, const double* Q, const double* U
     if (rc) return rc;
     h->elim_nb = cand[best][0];
     h->elim_minb = cand[best][1];
-    h->schur_mode = cand[best][2];
+    apply_schur(cand[best][2]);
     h->blocks_mode = cand[best][3];
     h->elim_mixed_minb = cand[best][4];
     h->blocks64_mode = cand[best][5];
     h->elim_mixed_split = cand[best][6];
     if (out) {
-        out->elim_nb = h->elim_nb; out->elim_minb = h->elim_minb; out->schur_mode = h->schur_mode;
+        out->elim_nb = h->elim_nb; out->elim_minb = h->elim_minb;
+        out->schur_mode = fp64 ? (h->schur64_mode ? 3 : 0) : h->schur_mode;
         out->blocks_mode = h->blocks_mode; out->elim_mixed_minb = h->elim_mixed_minb;
         out->blocks64_mode = h->blocks64_mode; out->elim_mixed_split = h->elim_mixed_split;
         out->n_cand = n;
@@ -453,12 +462,15 @@ int hdg_set_tuning(hdg_handle h, const hdg_tune* t) {
         return HDG_OK;
     }
     if (!h || !t) return fail(h, HDG_EINVAL, "NULL argument");
+    const bool fp64 = h->precision == HDG_PREC_FP64;
     if ((t->elim_nb != 8 && t->elim_nb != 16) || (t->elim_minb != 1 && t->elim_minb != 2) ||
-        t->schur_mode < 0 || t->schur_mode > 2 || t->blocks_mode < 0 || t->blocks_mode > 2 ||
+        (fp64 ? (t->schur_mode != 0 && t->schur_mode != 3) : (t->schur_mode < 0 || t->schur_mode > 2)) ||
+        t->blocks_mode < 0 || t->blocks_mode > 2 ||
         (t->elim_mixed_minb != 2 && t->elim_mixed_minb != 3) || t->blocks64_mode < 0 || t->blocks64_mode > 1 ||
         t->elim_mixed_split < 0 || t->elim_mixed_split > 1)
-        return fail(h, HDG_EINVAL, "elim_nb 8 or 16, elim_minb 1 or 2, schur_mode 0..2, blocks_mode 0..2, "
-                                   "elim_mixed_minb 2 or 3, blocks64_mode 0..1, elim_mixed_split 0..1");
+        return fail(h, HDG_EINVAL, "elim_nb 8 or 16, elim_minb 1 or 2, schur_mode 0..2 (FP64 handles: 0 or 3), "
+                                   "blocks_mode 0..2, elim_mixed_minb 2 or 3, blocks64_mode 0..1, "
+                                   "elim_mixed_split 0..1");
     if (h->precision == HDG_PREC_MIXED && h->prec_req != HDG_PREC_MIXED && t->schur_mode != h->schur_mode)
         return fail(h, HDG_EINVAL, "the Schur precision was fixed by hdg_set_params");
     h->elim_nb = t->elim_nb;
@@ -468,6 +480,7 @@ int hdg_set_tuning(hdg_handle h, const hdg_tune* t) {
     h->blocks64_mode = t->blocks64_mode;
     h->elim_mixed_split = t->elim_mixed_split;
     if (h->precision == HDG_PREC_MIXED) h->schur_mode = t->schur_mode;
+    else h->schur64_mode = t->schur_mode == 3 ? 1 : 0;
     return HDG_OK;
 }
 

@@ -196,6 +196,8 @@ struct hdg_ctx {
     int blocks_mode = 1;                   // mixed volume contraction: 0 FP32 SIMT, 1 3xTF32 tensor cores (3-D),
                                            // 2 FP32 sum factorisation
     int blocks64_mode = 1;                 // FP64 volume contraction: 0 dense GEMM, 1 sum factorisation
+    int schur64_mode = 0;                  // FP64 Schur product: 0 inside the FP64 elimination, 1 on the BF16
+                                           // tensor cores by exact digit splitting (k_schur_ozaki)
     double* d_m11 = nullptr;               // [E][NU][NU] interior block / its LU factors (FP64)
     float* d_m12 = nullptr;                // [E][NU][NT] Bt, then Z = L^{-1} P Bt
     double* d_mrt = nullptr;               // [E][NU] Rt, then z

@@ -844,7 +844,13 @@ __device__ __forceinline__ void trail_tile(RowP rowp, const double* pan, const d
 template <class C, int NB>
 constexpr int elim_smem_doubles() { return C::NR * NB + NB * 64; }
 
-template <class C, int NB, int NTH, int MINB>
+// Bordered elimination of one element.  NOSCHUR: the trace rows' trace columns
+// (Dt) are left untouched, so that afterwards the trace rows hold the
+// multipliers W = Ct U^{-1} in their interior columns and the right-hand side
+// Rh - W z in their last column, and the interior rows hold Z = L^{-1} P Bt in
+// their trace columns; the Schur product S = Dt - W Z is then formed by
+// k_schur_ozaki on the tensor cores.
+template <class C, int NB, int NTH, int MINB, bool NOSCHUR = false>
 __global__ void __launch_bounds__(NTH, MINB) k_elim(double* top, double* bot, int64_t e0, int32_t* status) {
     constexpr int NU = C::NU, NR = C::NR, NC = C::NC, LD = C::LD;
     constexpr int TCW = 64;                 // column tile of the trailing update
@@ -945,6 +951,61 @@ __global__ void __launch_bounds__(NTH, MINB) k_elim(double* top, double* bot, in
         __syncthreads();
         // trailing update A22 -= L21 U12 on rows [c0, NR) x cols [c0, NC)
         const int tx = tid & 15, ty = tid >> 4;
+        if constexpr (NOSCHUR) {
+            // interior rows: all trailing columns; trace rows: interior columns and the
+            // right-hand side only (the trace-trace block waits for the Schur product)
+#pragma unroll 1
+            for (int ct = c0; ct < NC; ct += TCW) {
+                for (int idx = tid; idx < kb * TCW; idx += NTH) {
+                    int j = idx / TCW, cc = idx - j * TCW;
+                    ust[j * TCW + cc] = (ct + cc < NC) ? rowp(k0 + j)[ct + cc] : 0.0;
+                }
+                __syncthreads();
+                int njj = 0;
+                while (njj < 4 && ct + 16 * njj < NC) ++njj;
+#pragma unroll 1
+                for (int rb = c0; rb < NU; rb += 64) {
+                    int nii = 0;
+                    while (nii < 4 && rb + 16 * nii < NU) ++nii;
+                    switch (nii * 4 + njj - 5) {
+#define HDG_TT(I, J) case (I) * 4 + (J) - 5: trail_tile<I, J, NB, NU, NC, TCW>(rowp, pan, ust, rb, ct, k0, kb, tx, ty); break;
+                        HDG_TT(1, 1) HDG_TT(1, 2) HDG_TT(1, 3) HDG_TT(1, 4)
+                        HDG_TT(2, 1) HDG_TT(2, 2) HDG_TT(2, 3) HDG_TT(2, 4)
+                        HDG_TT(3, 1) HDG_TT(3, 2) HDG_TT(3, 3) HDG_TT(3, 4)
+                        HDG_TT(4, 1) HDG_TT(4, 2) HDG_TT(4, 3) HDG_TT(4, 4)
+#undef HDG_TT
+                        default: break;
+                    }
+                }
+                if (ct < NU) {
+                    int njt = 0;
+                    while (njt < 4 && ct + 16 * njt < NU) ++njt;
+#pragma unroll 1
+                    for (int rb = NU; rb < NR; rb += 64) {
+                        int nii = 0;
+                        while (nii < 4 && rb + 16 * nii < NR) ++nii;
+                        switch (nii * 4 + njt - 5) {
+#define HDG_TT(I, J) case (I) * 4 + (J) - 5: trail_tile<I, J, NB, NR, NU, TCW>(rowp, pan, ust, rb, ct, k0, kb, tx, ty); break;
+                            HDG_TT(1, 1) HDG_TT(1, 2) HDG_TT(1, 3) HDG_TT(1, 4)
+                            HDG_TT(2, 1) HDG_TT(2, 2) HDG_TT(2, 3) HDG_TT(2, 4)
+                            HDG_TT(3, 1) HDG_TT(3, 2) HDG_TT(3, 3) HDG_TT(3, 4)
+                            HDG_TT(4, 1) HDG_TT(4, 2) HDG_TT(4, 3) HDG_TT(4, 4)
+#undef HDG_TT
+                            default: break;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+#pragma unroll 1
+            for (int r = NU + tid; r < NR; r += NTH) {       // right-hand side of the trace rows
+                double s = rowp(r)[NC - 1];
+                for (int j = 0; j < kb; ++j) s = fma(-pan[(r - k0) * NB + j], rowp(k0 + j)[NC - 1], s);
+                rowp(r)[NC - 1] = s;
+            }
+            __syncthreads();
+            continue;
+        }
 #pragma unroll 1
         for (int ct = c0; ct < NC; ct += TCW) {
             for (int idx = tid; idx < kb * TCW; idx += NTH) {
@@ -1190,6 +1251,12 @@ template <> struct BlkCfg<Cfg<3, 3>> { static constexpr int TY = 16, TX = 16, KC
         }                                                                              \
     } while (0)
 
+// FP64 Schur product on the tensor cores (ozaki.cuh)
+template <class C>
+struct OzakiCfg;
+template <class C>
+__global__ void k_schur_ozaki(double* top, double* bot, int64_t e0, int32_t* status);
+
 template <int D, int P>
 int run_linearize(hdg_ctx* h, const LinArgs& la) {
     if (int rc = ensure_system_storage(h, HDG_PREC_FP64)) return rc;
@@ -1212,6 +1279,14 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
     HDG_CK(cudaFuncSetAttribute(k_elim<C, 16, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim16));
     HDG_CK(cudaFuncSetAttribute(k_elim<C, 8, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim8));
     HDG_CK(cudaFuncSetAttribute(k_elim<C, 8, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim8));
+    const bool oz = h->schur64_mode == 1;   // Schur product emulated on the tensor cores
+    if (oz) {
+        HDG_CK(cudaFuncSetAttribute(k_elim<C, 16, 256, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim16));
+        HDG_CK(cudaFuncSetAttribute(k_elim<C, 16, 256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim16));
+        HDG_CK(cudaFuncSetAttribute(k_elim<C, 8, 256, 1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim8));
+        HDG_CK(cudaFuncSetAttribute(k_elim<C, 8, 256, 2, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim8));
+        HDG_CK(cudaFuncSetAttribute(k_schur_ozaki<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, OzakiCfg<C>::SMEM));
+    }
     cudaStream_t st = h->stream;
     HDG_CK(cudaMemsetAsync(h->d_vals, 0, sizeof(double) * h->nnzb * C::BS * C::BS, st));
     HDG_CK(cudaMemsetAsync(h->d_g, 0, sizeof(double) * h->F * C::BS, st));
@@ -1247,7 +1322,23 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
         prof_end(h);
         prof_begin(h, HDG_K_ELIM);
         // variant chosen by the autotuner: panel width 16 or 8, built for 1 or 2 resident CTAs per SM
-        if (h->elim_nb == 8) {
+        if (oz) {
+            if (h->elim_nb == 8) {
+                if (h->elim_minb == 1)
+                    k_elim<C, 8, 256, 1, true><<<(unsigned)ne, 256, sm_elim8, st>>>(h->d_top, h->d_bot, e0, h->d_status);
+                else
+                    k_elim<C, 8, 256, 2, true><<<(unsigned)ne, 256, sm_elim8, st>>>(h->d_top, h->d_bot, e0, h->d_status);
+            } else {
+                if (h->elim_minb == 1)
+                    k_elim<C, 16, 256, 1, true><<<(unsigned)ne, 256, sm_elim16, st>>>(h->d_top, h->d_bot, e0, h->d_status);
+                else
+                    k_elim<C, 16, 256, 2, true><<<(unsigned)ne, 256, sm_elim16, st>>>(h->d_top, h->d_bot, e0, h->d_status);
+            }
+            prof_end(h);
+            prof_begin(h, HDG_K_SCHUR);
+            k_schur_ozaki<C><<<(unsigned)(ne * OzakiCfg<C>::NMT * OzakiCfg<C>::NNT), 128, OzakiCfg<C>::SMEM, st>>>(
+                h->d_top, h->d_bot, e0, h->d_status);
+        } else if (h->elim_nb == 8) {
             if (h->elim_minb == 1)
                 k_elim<C, 8, 256, 1><<<(unsigned)ne, 256, sm_elim8, st>>>(h->d_top, h->d_bot, e0, h->d_status);
             else

@@ -7,6 +7,7 @@
 #pragma once
 
 #include "mixed.cuh"
+#include "ozaki.cuh"
 #include "schwarz.cuh"
 #include "av.cuh"
 

@@ -29,9 +29,12 @@ def _built():
     build.build()
 
 
-def compare(P, rows=None, check_matvec=False, seed=0):
-    run = GpuRun(P).linearize()
+def compare(P, rows=None, check_matvec=False, seed=0, tuning=None):
     from paper_2608_27863_gb300 import hdg as H
+    run = GpuRun(P)
+    if tuning:
+        H.hdg_set_tuning(run.h, **tuning)
+    run.linearize()
     assert H.hdg_status(run.h) == 0
     vals = run.blocks()
     g = run.rhs()
@@ -202,15 +205,16 @@ def test_autotuned_variants_keep_parity():
     run = GpuRun(P)
     rep = H.hdg_autotune(run.h, run.U, run.Q, run.UH, run.Ustar, run.nu, P.dt, P.a_ii, reps=1)
     cands = rep["candidates"]
-    assert len(cands) == 8 and all(ms > 0 for _, ms in cands)
-    chosen = (rep["elim_nb"], rep["elim_minb"], rep["blocks64_mode"])
-    assert min(ms for _, ms in cands) == [ms for c, ms in cands if (c[0], c[1], c[5]) == chosen][0]
+    assert len(cands) == 16 and all(ms > 0 for _, ms in cands)
+    chosen = (rep["elim_nb"], rep["elim_minb"], rep["schur_mode"], rep["blocks64_mode"])
+    assert min(ms for _, ms in cands) == [ms for c, ms in cands if (c[0], c[1], c[2], c[5]) == chosen][0]
     assert {c[5] for c, _ in cands} == {0, 1}      # dense and sum-factorised contraction
+    assert {c[2] for c, _ in cands} == {0, 3}      # Schur product on the FP64 pipe / the tensor cores
     run.close()
     for cand, _ms in cands:
         nb, minb = cand[0], cand[1]
         h = create(P)
-        H.hdg_set_tuning(h, elim_nb=nb, elim_minb=minb, blocks64_mode=cand[5])
+        H.hdg_set_tuning(h, elim_nb=nb, elim_minb=minb, schur_mode=cand[2], blocks64_mode=cand[5])
         compare_handle = GpuRun(P, h)
         compare_handle.linearize()
         vals = compare_handle.blocks()
