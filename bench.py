@@ -389,12 +389,25 @@ def make_problem(name, cpu_sample=False):
 # ----------------------------------------------------------------------------
 # algorithmic FLOP counts per element (the executed reduced-structure counts)
 # ----------------------------------------------------------------------------
-def flop_counts(d, p, sum_factorised=False):
+def ozaki_digits(K):
+    """Digit width and count of the tensor-core Schur product for inner size K."""
+    b = 8 if 5 * K * 255 ** 2 < 2 ** 24 else 7 if 5 * K * 127 ** 2 < 2 ** 24 else 6
+    return b, -(-54 // b)
+
+
+def flop_counts(d, p, sum_factorised=False, tc_schur=False):
     m, n1, q1 = d + 2, p + 1, p + 2
     Np, Nq, nf, Nfp, Nfq = n1 ** d, q1 ** d, 2 * d, n1 ** (d - 1), q1 ** (d - 1)
     NU, NT = m * Np, nf * m * Nfp
     NR, NC = NU + NT, NU + NT + 1
     elim = sum(2 * (NR - k - 1) * (NC - k - 1) + (NR - k - 1) for k in range(NU))
+    schur = 2 * NT * NT * NU                  # the trace-trace part of the trailing updates
+    b, s = ozaki_digits(NU)
+    pairs = s * (s + 1) // 2                  # digit pairs kept (i + j <= s + 1)
+    mt, nt = -(-NT // 128) * 128, -(-NT // 32) * 32
+    schur_bf16 = pairs * 2 * mt * nt * (-(-NU // 16) * 16)   # executed BF16 MMA work, padded tiles
+    if tc_schur:
+        elim -= schur
     NCB = Np + nf * Nfp
     K = d * Nq
     if sum_factorised:       # one 1-D contraction per axis, per column and direction
@@ -405,7 +418,10 @@ def flop_counts(d, p, sum_factorised=False):
     blocks = m * m * (contraction                       # contraction
                       + K * (2 * (1 + d) * Np + nf * Nfp)  # generated operand
                       + nf * (2 * Nfq * NCB * (d + 1) + 2 * Nfp * NCB * Nfq))  # face terms
-    return {"elim": elim, "blocks": blocks, "total": elim + blocks}
+    out = {"elim": elim, "blocks": blocks, "total": elim + blocks + (schur if tc_schur else 0)}
+    if tc_schur:
+        out.update(schur=schur, schur_bf16=schur_bf16)
+    return out
 
 
 # ----------------------------------------------------------------------------
@@ -763,7 +779,8 @@ def run_ours(args, rank, world, local_rank):
         H.hdg_destroy(h)
         return out
     t64 = tuning.get("fp64") or {}
-    fl = flop_counts(m.dim, P.p, sum_factorised=t64.get("blocks64_mode", 1) == 1)
+    oz = t64.get("schur_mode", 0) == 3          # FP64 Schur product on the tensor cores
+    fl = flop_counts(m.dim, P.p, sum_factorised=t64.get("blocks64_mode", 1) == 1, tc_schur=oz)
     nb_used = t64.get("elim_nb", args.elim_nb or 16)
     kern = {}
     for k, (ms, n) in prof.items():
@@ -771,8 +788,13 @@ def run_ours(args, rank, world, local_rank):
             kern[k] = {"ms_per_step": ms / args.steps, "launches_per_step": n / args.steps}
     kern["elim"]["tflops"] = fl["elim"] * E / (prof["elim"][0] / args.steps) / 1e9
     kern["blocks"]["tflops"] = fl["blocks"] * E / (prof["blocks"][0] / args.steps) / 1e9
+    if oz and prof["schur"][1]:
+        # FP64-equivalent rate of the emulated product, and the BF16 tensor work it executes
+        kern["schur"]["fp64_equivalent_tflops"] = fl["schur"] * E / (prof["schur"][0] / args.steps) / 1e9
+        kern["schur"]["bf16_tflops_executed"] = fl["schur_bf16"] * E / (prof["schur"][0] / args.steps) / 1e9
+        kern["schur"]["bf16_frac_of_probe"] = kern["schur"]["bf16_tflops_executed"] / peaks["bf16_tcgen05"]
     dom = max(("elim", "blocks"), key=lambda k: prof[k][0])
-    traffic_key = (dom, m.dim, P.p, nb_used if dom == "elim" else 0)
+    traffic_key = (dom, m.dim, P.p, nb_used if dom == "elim" and not oz else 0)
     avg_launch_ms = prof[dom][0] / max(prof[dom][1], 1)
     per_launch_elems = E / max(prof[dom][1] / args.steps, 1)
     achieved = fl[dom] * per_launch_elems / (avg_launch_ms * 1e-3) / 1e12
