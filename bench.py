@@ -87,6 +87,28 @@ def make_tet_problem(name, host_layout=None):
     return P, m
 
 
+def cpu_model():
+    """The host CPU as the OS reports it (model name, or the Arm part and implementer)."""
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return None
+    for key in ("model name", "Model name"):
+        for line in info.splitlines():
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    fields = {}
+    for line in info.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            fields.setdefault(k.strip(), v.strip())
+    if "CPU part" in fields:
+        parts = {"0xd4f": "Neoverse-V2", "0xd40": "Neoverse-V1", "0xd0c": "Neoverse-N1"}
+        return "Arm %s (implementer %s, part %s)" % (parts.get(fields["CPU part"], "core"),
+                                                     fields.get("CPU implementer", "?"), fields["CPU part"])
+    return None
+
+
 def hbm_peak_gbs():
     """Measured copy bandwidth of the GB300s (GB/s) and its source."""
     try:
@@ -234,7 +256,7 @@ def run_tet(args, rank, world, local_rank):
     n_mixed, n_e2e = min(args.steps, 5), min(args.steps, 3)
     if not args.no_mixed:
         H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_MIXED)
-        tuning["mixed"] = tune(False)
+        tuning["mixed"] = tune()
         tm_ms, prof_m, clocks_m = timed(n_mixed, min(args.warmup, 2))
         H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_FP64)
         H.hdg_set_tuning(h, elim_nb=tuning["fp64"]["elim_nb"])
@@ -265,7 +287,7 @@ def run_tet(args, rank, world, local_rank):
     if pool is not None:
         rate, n_done, secs = oracle_rate(pool, ncores, m.n_elem, args.cpu_seconds, 100)
         pool.close()
-        cpu = {"value": rate, "unit": "elements/s", "cores": ncores, "kind": "oracle",
+        cpu = {"value": rate, "unit": "elements/s", "cores": ncores, "cpu_model": cpu_model(), "kind": "oracle",
                "sample": "%d seeded elements of the workload in %.1f s: per-element residual, complex-step "
                          "Jacobian, dense FP64 LU of the (q,u) block and Schur complement" % (n_done, secs)}
     E = m.n_elem
@@ -739,7 +761,7 @@ def run_ours(args, rank, world, local_rank):
         n_sample = make_problem(args.workload, cpu_sample=True).mesh.n_elem if "cpu" in wl else m.n_elem
         rate, n_done, secs = oracle_rate(pool, ncores, n_sample, args.cpu_seconds, 100)
         pool.close()
-        cpu = {"value": rate, "unit": "elements/s", "cores": ncores, "kind": "oracle",
+        cpu = {"value": rate, "unit": "elements/s", "cores": ncores, "cpu_model": cpu_model(), "kind": "oracle",
                "sample": "%d seeded elements of %s in %.1f s: per-element residual, complex-step "
                          "Jacobian, dense FP64 LU of the (q,u) block and Schur complement (assembly, matvec "
                          "and recovery not included)" % (n_done, "a %d-element mesh of the same elements and physics"
@@ -920,7 +942,7 @@ def run_reference(args, rank, world):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": args.workload, "elements_per_gpu": n_elem, "degree": degree},
-        "cpu_baseline": {"value": rate, "unit": "elements/s", "cores": ncores, "kind": "oracle",
+        "cpu_baseline": {"value": rate, "unit": "elements/s", "cores": ncores, "cpu_model": cpu_model(), "kind": "oracle",
                          "sample": "each step condenses %d seeded elements (one per core) of the workload" % ncores},
         "e2e": {"value": rate, "unit": "elements/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }

@@ -192,6 +192,18 @@ int hdg_recover_interior(hdg_handle h, const double* dUH, double* dQ, double* dU
  * The values are FP64 after an FP64 linearization and FP32 (vals then points
  * to float storage of the same shape) after an HDG_PREC_MIXED one. */
 int hdg_get_blocks(hdg_handle h, double* vals);
+/* Per-element Schur complements S^K (eq. schur-trace) as well as the assembled
+ * blocks: after this call every hdg_linearize_condense also writes, for every
+ * element K, its t x t condensed block S^K = D - C A^{-1} B into SK (device,
+ * caller-owned; NULL switches the output off).  Layout: quad / hex handles
+ * [E][t][t] row-major, t = nf m Nfp; tetrahedral handles packed, element e's
+ * t_e x t_e block at offset sum_{e' < e} t_{e'}^2.  Rows and columns follow the
+ * element's local trace order (local face, component, face node; on quad / hex
+ * faces the element's own node order, which hdg_get_connectivity's perm maps to
+ * the canonical one; on tetrahedral faces the canonical order).  Values are
+ * FP64 after an FP64 linearization and FP32 after a mixed one (SK then points to
+ * float storage of the same shape).  Asynchronous on the handle's stream. */
+int hdg_set_element_block_output(hdg_handle h, void* SK);
 /* Read back the latched device status: HDG_OK, HDG_ESINGULAR or
  * HDG_ENONFINITE (synchronises the stream). */
 int hdg_status(hdg_handle h);

@@ -248,6 +248,7 @@ int create_device(hdg_ctx* h) {
     if ((rc = dev_alloc(h, &h->d_vcoef, (size_t)h->chunk * h->m * h->m * d * h->NCOEF * h->Nq))) return rc;
     if ((rc = dev_alloc(h, &h->d_fcoef, (size_t)h->chunk * h->nf * h->m * h->m * h->NCOEF * h->Nfq))) return rc;
     if ((rc = dev_alloc(h, &h->d_taup, (size_t)h->chunk * h->nf * h->Nfq))) return rc;
+    if ((rc = dev_alloc(h, &h->d_ozexp, (size_t)h->chunk * 2 * h->NT))) return rc;
     h->device = true;
     return HDG_OK;
 }
@@ -638,6 +639,14 @@ int hdg_get_blocks(hdg_handle h, double* vals) {
     const size_t bytes = (h->sys_prec == HDG_PREC_MIXED ? sizeof(float) : sizeof(double)) * h->nnzb * h->BS * h->BS;
     CKH(cudaMemcpyAsync(vals, h->sys_prec == HDG_PREC_MIXED ? (const void*)h->d_vals32 : (const void*)h->d_vals,
                         bytes, cudaMemcpyDeviceToDevice, h->stream));
+    return HDG_OK;
+}
+
+int hdg_set_element_block_output(hdg_handle h, void* SK) {
+    if (!h) return HDG_EINVAL;
+    if (!h->device) return fail(h, HDG_EINVAL, "handle has no device storage");
+    if (h->tet) return hdg::tet::set_element_block_output(h, SK);
+    h->d_skout = SK;
     return HDG_OK;
 }
 

@@ -126,6 +126,9 @@ struct hdg_ctx {
     double* d_fcoef = nullptr;             // [chunk][nf][m][m][NCOEF][Nfq]
     double* d_dq0 = nullptr;               // [E][d][m][Np]
     double* d_taup = nullptr;              // [chunk][nf][Nfq] per-point tau (state-dependent stabilization)
+    void* d_skout = nullptr;               // caller's [E][t][t] buffer for the element Schur complements, or NULL
+    int32_t* d_ozexp = nullptr;            // [chunk][2][NT] row / column scale exponents of the tensor-core
+                                           // FP64 Schur product
     int32_t* d_status = nullptr;           // [1]
     int32_t* d_ftag = nullptr;             // [E][nf] boundary tags, NULL for fully periodic meshes
     double* d_ub = nullptr;                // [m] state of tag-1 boundary faces

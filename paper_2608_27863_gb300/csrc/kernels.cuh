@@ -654,11 +654,13 @@ __global__ void __launch_bounds__(TY * TX) k_blocks(BlkArgs<TL> A) {
 // component pair), columns in chunks of CW; the face terms follow in
 // k_blocks<..., VOL = false>.
 // ----------------------------------------------------------------------------
-template <class C>
+template <class C, class TA = double>
 struct SfShape {
     static constexpr int N1 = C::P + 1, Q1 = C::P + 2;
     static constexpr int NCB = C::NP + C::NF * C::NFP;
-    static constexpr int CW = 16;                                        // columns per chunk
+    // columns per chunk: 16 in FP64 (the FP64 pipe bounds the kernel), 32 in FP32, where the
+    // per-chunk barriers and coefficient reloads, not the FMAs, set the time
+    static constexpr int CW = sizeof(TA) == 4 ? 32 : 16;
     static constexpr int NX = (C::D == 3) ? Q1 * Q1 * N1 : Q1 * N1;      // after the first axis
     static constexpr int NY = (C::D == 3) ? Q1 * N1 * N1 : 0;            // after the second (3-D)
     static constexpr int NTH = 128;
@@ -667,8 +669,8 @@ struct SfShape {
 };
 
 template <class C, class TA, class TL>
-__global__ void __launch_bounds__(SfShape<C>::NTH) k_blocks_sf(BlkArgs<TL> A) {
-    using S = SfShape<C>;
+__global__ void __launch_bounds__(SfShape<C, TA>::NTH) k_blocks_sf(BlkArgs<TL> A) {
+    using S = SfShape<C, TA>;
     constexpr int D = C::D, M = C::M, NP = C::NP, NQ = C::NQ, NFP = C::NFP, NCOEF = C::NCOEF;
     constexpr int N1 = S::N1, Q1 = S::Q1, NCB = S::NCB, CW = S::CW, NTH = S::NTH;
     constexpr int GEO = Geo<D>::N;
@@ -1251,11 +1253,29 @@ template <> struct BlkCfg<Cfg<3, 3>> { static constexpr int TY = 16, TX = 16, KC
         }                                                                              \
     } while (0)
 
+// Element Schur complements S^K to the caller's buffer (hdg_set_element_block_output):
+// out[e][r][c] = the element's trace-trace block after condensation, rows and columns
+// in the element's local trace order (local face, component, local face node); one
+// CTA per element of the chunk, src row stride rs, first trace column col0.
+template <class TS, class TO>
+__global__ void k_copy_sk(const TS* src, int64_t src_es, int64_t rs, int64_t col0, int nt, int64_t e0, TO* out) {
+    const int64_t el = blockIdx.x;
+    const TS* S = src + el * src_es + col0;
+    TO* o = out + (e0 + el) * (int64_t)nt * nt;
+    for (int idx = threadIdx.x; idx < nt * nt; idx += blockDim.x) {
+        const int r = idx / nt, c = idx - r * nt;
+        o[idx] = (TO)S[(int64_t)r * rs + c];
+    }
+}
+
 // FP64 Schur product on the tensor cores (ozaki.cuh)
+constexpr int OZ_THREADS = 512;
 template <class C>
 struct OzakiCfg;
 template <class C>
-__global__ void k_schur_ozaki(double* top, double* bot, int64_t e0, int32_t* status);
+__global__ void k_oz_scales(const double* top, const double* bot, int64_t e0, int32_t* ex);
+template <class C>
+__global__ void k_schur_ozaki(double* top, double* bot, int64_t e0, const int32_t* ex, int32_t* status);
 
 template <int D, int P>
 int run_linearize(hdg_ctx* h, const LinArgs& la) {
@@ -1336,8 +1356,9 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
             }
             prof_end(h);
             prof_begin(h, HDG_K_SCHUR);
-            k_schur_ozaki<C><<<(unsigned)(ne * OzakiCfg<C>::NMT * OzakiCfg<C>::NNT), 128, OzakiCfg<C>::SMEM, st>>>(
-                h->d_top, h->d_bot, e0, h->d_status);
+            k_oz_scales<C><<<(unsigned)ne, 256, 0, st>>>(h->d_top, h->d_bot, e0, h->d_ozexp);
+            k_schur_ozaki<C><<<(unsigned)(ne * OzakiCfg<C>::NMT * OzakiCfg<C>::NNT), OZ_THREADS, OzakiCfg<C>::SMEM, st>>>(
+                h->d_top, h->d_bot, e0, h->d_ozexp, h->d_status);
         } else if (h->elim_nb == 8) {
             if (h->elim_minb == 1)
                 k_elim<C, 8, 256, 1><<<(unsigned)ne, 256, sm_elim8, st>>>(h->d_top, h->d_bot, e0, h->d_status);
@@ -1350,6 +1371,9 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
                 k_elim<C, 16, 256, 2><<<(unsigned)ne, 256, sm_elim16, st>>>(h->d_top, h->d_bot, e0, h->d_status);
         }
         prof_end(h);
+        if (h->d_skout)
+            k_copy_sk<double, double><<<(unsigned)ne, 256, 0, st>>>(h->d_bot, (int64_t)C::NT * C::LD, C::LD, C::NU,
+                                                                    C::NT, e0, static_cast<double*>(h->d_skout));
         for (int pass = 0; pass < 2; ++pass) {
             prof_begin(h, HDG_K_ASSEMBLE);
             k_assemble<C><<<(unsigned)(ne * C::NF * C::NF), 256, 0, st>>>(h->d_bot, e0, h->d_blk, h->d_rank,

@@ -863,7 +863,7 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
     HDG_CK(cudaFuncSetAttribute(kface, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_blk));
     if (C::D == 3)
         HDG_CK(cudaFuncSetAttribute(k_blocks_tc<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, BlkTC<C>::smem_bytes()));
-    const size_t sm_sf32 = sizeof(float) * SfShape<C>::smem_words;
+    const size_t sm_sf32 = sizeof(float) * SfShape<C, float>::smem_words;
     HDG_CK(cudaFuncSetAttribute(k_blocks_sf<C, float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sf32));
     HDG_CK(cudaFuncSetAttribute(k_elim_mixed<C, NB, 256, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
     HDG_CK(cudaFuncSetAttribute(k_elim_mixed<C, NB, 256, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_elim));
@@ -906,7 +906,7 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
             kface<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
         } else if (h->blocks_mode == 2) {
             // volume contraction by FP32 sum factorisation, then the face terms
-            k_blocks_sf<C, float, float><<<(unsigned)(ne * C::M * C::M), SfShape<C>::NTH, sm_sf32, st>>>(ba);
+            k_blocks_sf<C, float, float><<<(unsigned)(ne * C::M * C::M), SfShape<C, float>::NTH, sm_sf32, st>>>(ba);
             kface<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
         } else {
             kblk<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
@@ -938,14 +938,17 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
             if (h->schur_mode == 1) {
                 const int smb = ST::smem_bytes(false);
                 HDG_CK(cudaFuncSetAttribute(k_schur_tc<C, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
-                k_schur_tc<C, false><<<grid, 128, smb, st>>>(RM, e0, h->d_status);
+                k_schur_tc<C, false><<<grid, ST::THREADS, smb, st>>>(RM, e0, h->d_status);
             } else {
                 const int smb = ST::smem_bytes(true);
                 HDG_CK(cudaFuncSetAttribute(k_schur_tc<C, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smb));
-                k_schur_tc<C, true><<<grid, 128, smb, st>>>(RM, e0, h->d_status);
+                k_schur_tc<C, true><<<grid, ST::THREADS, smb, st>>>(RM, e0, h->d_status);
             }
         }
         prof_end(h);
+        if (h->d_skout)
+            k_copy_sk<float, float><<<(unsigned)ne, 256, 0, st>>>(RM.a22, RM.a22_es, RM.a22_rs, 0, C::NT, e0,
+                                                                  static_cast<float*>(h->d_skout));
         for (int pass = 0; pass < 2; ++pass) {
             prof_begin(h, HDG_K_ASSEMBLE);
             k_assemble_r<C, float><<<(unsigned)(ne * C::NF * C::NF), 256, 0, st>>>(RM, e0, h->d_blk, h->d_rank,
@@ -1022,9 +1025,12 @@ struct SchurTC {
     static constexpr int NMT = (NT + MT - 1) / MT;                        // row tiles
     static constexpr int TCOLS = NTN <= 32 ? 32 : NTN <= 64 ? 64 : NTN <= 128 ? 128 : 256;
     static_assert(NTN <= 256, "column tile too wide");
+    static constexpr int THREADS = 256;
+    static constexpr int WRS = KC + 4;                                    // raw W row stride (floats)
     __host__ __device__ static constexpr int tile_floats(int rows) { return rows * KC; }
+    __host__ __device__ static constexpr int raw_floats() { return MT * WRS + KC * NTN; }
     __host__ __device__ static constexpr int smem_bytes(bool split3) {
-        return (split3 ? 2 : 1) * (tile_floats(MT) + tile_floats(NTN)) * 4 + 64;
+        return (split3 ? 2 : 1) * (tile_floats(MT) + tile_floats(NTN)) * 4 + raw_floats() * 4 + 64;
     }
 };
 
@@ -1054,10 +1060,19 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t phase, 
 }
 
 
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" :: "r"(smem_u32(dst)), "l"(src), "r"(src_bytes));
+}
+
+// One CTA (8 warps) per (element, 128-row tile, column tile).  The raw FP32 tiles of
+// the next K chunk (W rows, Z rows) are copied into shared memory asynchronously
+// (cp.async) while the tensor cores run the current chunk; the threads then split
+// them into TF32 hi (/ lo) parts and store them in the core-matrix layout, rows
+// fastest so that the 16-byte stores of a quarter warp are contiguous.
 template <class C, bool SPLIT3>
-__global__ void __launch_bounds__(128) k_schur_tc(Regions<float> R, int64_t e0, int32_t* status) {
+__global__ void __launch_bounds__(SchurTC<C>::THREADS) k_schur_tc(Regions<float> R, int64_t e0, int32_t* status) {
     using S = SchurTC<C>;
-    constexpr int NT = S::NT, NU = S::NU, MT = S::MT, KC = S::KC, NTN = S::NTN;
+    constexpr int NT = S::NT, NU = S::NU, MT = S::MT, KC = S::KC, NTN = S::NTN, TH = S::THREADS, WRS = S::WRS;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t bid = blockIdx.x;
     const int nt = (int)(bid % S::NNT), mt = (int)((bid / S::NNT) % S::NMT);
@@ -1072,15 +1087,32 @@ __global__ void __launch_bounds__(128) k_schur_tc(Regions<float> R, int64_t e0, 
     float* Bh = Ah + S::tile_floats(MT);
     float* Al = Bh + S::tile_floats(NTN);
     float* Bl = Al + S::tile_floats(MT);
+    float* Wr = (SPLIT3 ? Bl + S::tile_floats(NTN) : Al);       // [MT][WRS] raw W of the next chunk
+    float* Zr = Wr + MT * WRS;                                  // [KC][NTN] raw Z
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smraw + S::smem_bytes(SPLIT3) - 64);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+
+    auto prefetch = [&](int k0) {
+        for (int it = tid; it < MT * KC; it += TH) {
+            const int r = it / KC, k = it - r * KC;
+            const bool in = m0 + r < NT && k0 + k < NU;
+            cp_async4(Wr + r * WRS + k, in ? (const void*)(W + (m0 + r) * sw + k0 + k) : (const void*)W, in ? 4 : 0);
+        }
+        for (int it = tid; it < KC * NTN; it += TH) {
+            const int k = it / NTN, n = it - k * NTN;
+            const bool in = k0 + k < NU && n0 + n < NT;
+            cp_async4(Zr + k * NTN + n, in ? (const void*)(Z + (k0 + k) * sz + n0 + n) : (const void*)Z, in ? 4 : 0);
+        }
+        asm volatile("cp.async.commit_group;");
+    };
+    prefetch(0);
 
     // right-hand side of this row tile: Rh -= W z (FP64), done by the first column tile
     if (nt == 0) {
         const double* z = R.rt + e * R.rt_es;
         double* rb = R.rb + el * R.rb_es;
         const int r = m0 + tid;
-        if (r < NT) {
+        if (tid < MT && r < NT) {
             double s = rb[r * R.rb_rs];
             for (int k = 0; k < NU; ++k) s -= (double)W[r * sw + k] * z[k * R.rt_rs];
             rb[r * R.rb_rs] = s;
@@ -1102,34 +1134,55 @@ __global__ void __launch_bounds__(128) k_schur_tc(Regions<float> R, int64_t e0, 
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NTN >> 3) << 17) | ((uint32_t)(MT >> 4) << 24);
     const uint32_t bar = smem_u32(mbar);
     uint32_t phase = 0;
-    bool ok = true;
-    const int rr = lane >> 2, kq = lane & 3;          // position inside an 8 x 4 core matrix
+    bool ok = true, pending = false;
     for (int k0 = 0; k0 < NU; k0 += KC) {
-        // one core matrix per warp step: contiguous, conflict-free shared-memory stores
-        for (int core = warp; core < (MT / 8) * (KC / 4); core += 4) {
-            const int r = (core / (KC / 4)) * 8 + rr, k = (core % (KC / 4)) * 4 + kq;
-            const float v = (m0 + r < NT && k0 + k < NU) ? W[(m0 + r) * sw + k0 + k] : 0.f;
-            const float hi = tf32_round(v);
-            Ah[core * 32 + lane] = hi;
-            if (SPLIT3) Al[core * 32 + lane] = tf32_round(v - hi);
+        asm volatile("cp.async.wait_group 0;");
+        if (pending) {                                          // the previous batch still reads the tiles
+            if (!mbar_wait_bounded(bar, phase, 1 << 24)) {
+                ok = false;
+                if (tid == 0) atomicOr(status, 4);
+                mbar_wait_bounded(bar, phase, 1 << 24);
+            }
+            phase ^= 1;
+            pending = false;
         }
-        for (int core = warp; core < (NTN / 8) * (KC / 4); core += 4) {
-            const int n = (core / (KC / 4)) * 8 + rr, k = (core % (KC / 4)) * 4 + kq;
-            const float v = (n0 + n < NT && k0 + k < NU) ? Z[(k0 + k) * sz + n0 + n] : 0.f;
-            const float hi = tf32_round(v);
-            Bh[core * 32 + lane] = hi;
-            if (SPLIT3) Bl[core * 32 + lane] = tf32_round(v - hi);
+        if (__syncthreads_or(ok ? 0 : 1)) {                     // raw tiles visible, operand tiles free
+            ok = false;
+            break;
+        }
+        // item = (row, 4-wide K group q) -> one 16-byte core-matrix row; rows fastest
+        for (int it = tid; it < MT * (KC / 4); it += TH) {
+            const int r = it % MT, q = it / MT;
+            const float4 v = *reinterpret_cast<const float4*>(Wr + r * WRS + q * 4);
+            const int off = ((r >> 3) * (KC / 4) + q) * 32 + (r & 7) * 4;    // floats
+            float4 hi = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+            *reinterpret_cast<float4*>(Ah + off) = hi;
+            if (SPLIT3)
+                *reinterpret_cast<float4*>(Al + off) =
+                    make_float4(tf32_round(v.x - hi.x), tf32_round(v.y - hi.y), tf32_round(v.z - hi.z), tf32_round(v.w - hi.w));
+        }
+        for (int it = tid; it < NTN * (KC / 4); it += TH) {
+            const int n = it % NTN, q = it / NTN;
+            const float4 v = make_float4(Zr[(q * 4 + 0) * NTN + n], Zr[(q * 4 + 1) * NTN + n], Zr[(q * 4 + 2) * NTN + n],
+                                         Zr[(q * 4 + 3) * NTN + n]);
+            const int off = ((n >> 3) * (KC / 4) + q) * 32 + (n & 7) * 4;
+            float4 hi = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z), tf32_round(v.w));
+            *reinterpret_cast<float4*>(Bh + off) = hi;
+            if (SPLIT3)
+                *reinterpret_cast<float4*>(Bl + off) =
+                    make_float4(tf32_round(v.x - hi.x), tf32_round(v.y - hi.y), tf32_round(v.z - hi.z), tf32_round(v.w - hi.w));
         }
         asm volatile("fence.proxy.async.shared::cta;");
-        __syncthreads();
+        __syncthreads();                                        // tiles staged, raw tiles consumed
+        if (k0 + KC < NU) prefetch(k0 + KC);                    // next chunk under this chunk's MMAs
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
             const int nsteps = (min(KC, NU - k0) + 7) / 8;
-            for (int s = 0; s < nsteps; ++s) {
-                const uint32_t off = s * 256;
+            for (int st = 0; st < nsteps; ++st) {
+                const uint32_t off = st * 256;
                 const uint64_t ah = umma_desc(smem_u32(Ah) + off, 128, (KC / 4) * 128);
                 const uint64_t bh = umma_desc(smem_u32(Bh) + off, 128, (KC / 4) * 128);
-                uint32_t acc = (k0 > 0 || s > 0) ? 1u : 0u;
+                uint32_t acc = (k0 > 0 || st > 0) ? 1u : 0u;
                 asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
                              :: "r"(tmem), "l"(ah), "l"(bh), "r"(idesc), "r"(acc));
@@ -1144,22 +1197,28 @@ __global__ void __launch_bounds__(128) k_schur_tc(Regions<float> R, int64_t e0, 
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar));
         }
+        pending = true;
+    }
+    asm volatile("cp.async.wait_group 0;");
+    if (pending && ok) {
         if (!mbar_wait_bounded(bar, phase, 1 << 24)) {
             ok = false;
             if (tid == 0) atomicOr(status, 4);
             mbar_wait_bounded(bar, phase, 1 << 24);
         }
         phase ^= 1;
-        __syncthreads();
-        if (!ok) break;
     }
+    ok = !__syncthreads_or(ok ? 0 : 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok) {
-        const int r = m0 + warp * 32 + lane;
+        // warp w reads lanes 32 (w % 4) .. + 31 and the column half w / 4 of the tile
+        const int lg = warp & 3, half = warp >> 2;
+        const int r = m0 + lg * 32 + lane;
+        constexpr int HC = ((NTN / 2) + 15) / 16 * 16;          // columns per half, in chunks of 16
 #pragma unroll 1
-        for (int c0 = 0; c0 < NTN; c0 += 16) {
+        for (int c0 = half * HC; c0 < min(NTN, (half + 1) * HC); c0 += 16) {
             uint32_t v[16];
-            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            const uint32_t addr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)c0;
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
                            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
@@ -1179,19 +1238,6 @@ __global__ void __launch_bounds__(128) k_schur_tc(Regions<float> R, int64_t e0, 
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(S::TCOLS));
 }
 
-// ----------------------------------------------------------------------------
-// A2 on tensor cores (mixed form): the volume contraction
-//   Out[(a,b,c)][i] = sum_k G_ab[k][c] dphi[k][i],   k = (direction, quadrature point),
-// one GEMM per element with M = m^2 (Np + nf Nfp) rows (component pair, block
-// column), N = Np (test function, padded to a multiple of 16) and
-// K = d Nq.  The operand G is generated on the fly from the point
-// coefficients and the FP32 basis tables exactly as in k_blocks (one core
-// matrix per warp step, so the shared-memory writes are contiguous); dphi is
-// the reference derivative table.  3xTF32 (hi/lo split of both operands),
-// FP32 accumulation in tensor memory, epilogue to Ã (FP64, with the DIRK mass
-// term) and B̃ (FP32).  One CTA (4 warps) per (element, 128-row tile); waits
-// on the MMA barrier are bounded as in k_schur_tc.
-// ----------------------------------------------------------------------------
 template <class C>
 struct BlkTC {
     static constexpr int NCB = C::NP + C::NF * C::NFP;

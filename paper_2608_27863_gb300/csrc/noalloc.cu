@@ -1,6 +1,7 @@
 // hdg_linearize_condense_static: the FP64 linearize + condense path with its
-// per-chunk scratch (trace rows of the bordered matrix, point coefficients and
-// per-point stabilization) taken from a fixed, file-scope device array instead
+// per-chunk scratch (trace rows of the bordered matrix, point coefficients,
+// per-point stabilization and the scale exponents of the tensor-core Schur
+// product) taken from a fixed, file-scope device array instead
 // of the handle's scratch allocation.  This entry point calls no allocating
 // CUDA or library routine.
 //
@@ -76,7 +77,8 @@ extern "C" int hdg_linearize_condense_static(hdg_handle h, const double* U, cons
     const size_t n_vc = (size_t)h->m * h->m * h->d * h->NCOEF * h->Nq;
     const size_t n_fc = (size_t)h->nf * h->m * h->m * h->NCOEF * h->Nfq;
     const size_t n_tp = (size_t)h->nf * h->Nfq;      // per-point tau of the state-dependent stabilization
-    const size_t per = n_bot + n_vc + n_fc + n_tp;
+    const size_t n_oz = (size_t)h->NT;               // 2 NT int32 scale exponents of the tensor-core Schur product
+    const size_t per = n_bot + n_vc + n_fc + n_tp + n_oz;
     if (per > kStaticScratchDoubles)
         return fail(h, HDG_EINVAL, "one element needs " + std::to_string(per * 8) +
                                        " bytes of scratch, more than the 64 MiB static scratch");
@@ -90,12 +92,14 @@ extern "C" int hdg_linearize_condense_static(hdg_handle h, const double* U, cons
     double* save_vc = h->d_vcoef;
     double* save_fc = h->d_fcoef;
     double* save_tp = h->d_taup;
+    int32_t* save_oz = h->d_ozexp;
     const int64_t save_chunk = h->chunk;
     const bool save_prof = h->prof;
     h->d_bot = base;
     h->d_vcoef = base + (size_t)chunk * n_bot;
     h->d_fcoef = h->d_vcoef + (size_t)chunk * n_vc;
     h->d_taup = h->d_fcoef + (size_t)chunk * n_fc;   // sized for this chunk, not the handle's
+    h->d_ozexp = reinterpret_cast<int32_t*>(h->d_taup + (size_t)chunk * n_tp);
     h->chunk = chunk;
     h->prof = false;  // event creation is an allocation
     cudaError_t e = cudaMemsetAsync(h->d_status, 0, sizeof(int32_t), h->stream);
@@ -105,6 +109,7 @@ extern "C" int hdg_linearize_condense_static(hdg_handle h, const double* U, cons
     h->d_vcoef = save_vc;
     h->d_fcoef = save_fc;
     h->d_taup = save_tp;
+    h->d_ozexp = save_oz;
     h->chunk = save_chunk;
     h->prof = save_prof;
     return rc;

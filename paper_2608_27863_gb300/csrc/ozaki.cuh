@@ -23,13 +23,16 @@
 // and the six accumulators sum to 2^{7b} 2^{-e_r - f_c} (W Z)_rc; the epilogue
 // adds them in FP64, scales and subtracts from Dt in FP64.
 //
-// One CTA (4 warps) per (element, 128-row tile, 32-column tile): the CTA
-// computes its rows' and columns' exponents, then for each 32-wide K chunk
-// stages the s digit slices of its W rows and Z columns in shared memory in
+// k_oz_scales first computes every row's and column's exponent once per element.
+// Then one CTA (16 warps) per (element, 128-row tile, 64-column tile) walks K in
+// 32-wide chunks: the raw FP64 tiles of the next chunk are copied into shared
+// memory by cp.async while the tensor cores run the current one; the threads cut
+// the current raw tiles into the s digit slices of its W rows and Z columns, in
 // the canonical K-major layout without swizzle (8-row x 16-byte core matrices,
-// K-adjacent cores 128 B apart, 8-row groups 512 B apart) and one thread
+// K-adjacent cores 128 B apart, 8-row groups 512 B apart), and one thread
 // issues tcgen05.mma kind::f16 (BF16 inputs, FP32 accumulation in tensor
-// memory) for every kept digit pair.  Waits on the MMA completion barrier are
+// memory) for every kept digit pair.  The epilogue combines the six
+// accumulators exactly as 64-bit integers and converts once to FP64.  Waits on the MMA completion barrier are
 // bounded; on timeout the CTA latches status bit 4, waits once more (bounded)
 // and frees its tensor memory.
 #pragma once
@@ -47,49 +50,128 @@ struct OzakiCfg {
     static constexpr int B = (5LL * K * 255 * 255 < (1LL << 24)) ? 8 : (5LL * K * 127 * 127 < (1LL << 24)) ? 7 : 6;
     static constexpr int S = (54 + B - 1) / B;            // digits: b s >= 54
     static constexpr int NACC = 6;                        // groups 2 .. 6 and the rest
-    static constexpr int MT = 128, NTN = 32, KC = 32;
+    static constexpr int MT = 128, NTN = 64, KC = 32;
     static constexpr int NMT = (NT + MT - 1) / MT, NNT = (NT + NTN - 1) / NTN;
-    static constexpr int TCOLS = 256;                     // NACC * NTN = 192 columns allocated as 256
+    static constexpr int TCOLS = 512;                     // NACC * NTN = 384 columns allocated as 512
     static constexpr int A_SLICE = MT * KC * 2, B_SLICE = NTN * KC * 2;   // bytes of one digit slice
-    static constexpr int SMEM = S * (A_SLICE + B_SLICE) + (MT + NTN) * 4 + 64;
-    static_assert(S <= 9 && B * S >= 54, "digit layout");
+    static constexpr int WRS = KC + 2;                    // raw W tile row stride (doubles): conflict-free rows
+    static constexpr int RAW = (MT * WRS + KC * NTN) * 8; // raw FP64 tiles of the next chunk
+    static constexpr int SMEM = S * (A_SLICE + B_SLICE) + RAW + (MT + NTN) * 4 + 64;
+    static_assert(S <= 9 && B * S >= 54 && B * S <= 56, "digit layout");
     static_assert(NACC * NTN <= TCOLS, "tensor-memory columns");
     static_assert((5LL * K * ((1 << B) - 1) * ((1 << B) - 1)) < (1LL << 24), "exact FP32 group accumulation");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
-// exponent e with |v| < 2^e for a normal FP64 v, from its bits; zero / subnormal -> INT_MIN
-__device__ __forceinline__ int oz_exponent(double v) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+// exponent e with |v| < 2^e for a normal FP64 value with bits u; zero / subnormal -> INT_MIN
+__device__ __forceinline__ int oz_exponent(unsigned long long u) {
     const int E = (int)((u >> 52) & 0x7FF);
     return E == 0 ? INT_MIN : E - 1022;
 }
 
-// trunc(|v| 2^{BS - e}) as an integer (< 2^BS), from the FP64 bits; v == 0 or subnormal -> 0
-__device__ __forceinline__ unsigned long long oz_fixed(double v, int e, int BS) {
-    const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+// trunc(|v| 2^{BS - e}) as an integer (< 2^BS <= 2^56) from the FP64 bits u of v
+// (|v| < 2^e); zero or subnormal -> 0
+__device__ __forceinline__ unsigned long long oz_fixed(unsigned long long u, int e, int BS) {
     const int E = (int)((u >> 52) & 0x7FF);
-    if (E == 0) return 0ull;
     const unsigned long long m = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-    const int sh = (E - 1075) + BS - e;                     // |v| 2^{BS - e} = m 2^{sh}
-    if (sh >= 0) return m << sh;                            // sh <= BS - 53 + ... < 64 since |v| < 2^e
-    return sh <= -64 ? 0ull : (m >> (-sh));
+    const int sh = e - BS + 1075 - E;                       // |v| 2^{BS - e} = m 2^{-sh}, sh >= 53 - BS
+    if (E == 0 || sh >= 64) return 0ull;
+    return sh >= 0 ? (m >> sh) : (m << (-sh));
 }
 
-// BF16 bits of the integer d (|d| < 256) times 2^{p}: exact
-__device__ __forceinline__ uint16_t oz_bf16(int d, int p) {
-    if (d == 0) return 0;
-    const uint32_t s = d < 0 ? 0x8000u : 0u;
-    const uint32_t a = (uint32_t)(d < 0 ? -d : d);
-    const int msb = 31 - __clz(a);                          // a = 1.f x 2^msb
-    const uint32_t frac = (a << (7 - msb)) & 0x7Fu;          // 7 fraction bits (a has <= 8 bits)
-    return (uint16_t)(s | ((uint32_t)(127 + msb + p) << 7) | frac);
+// BF16 bits of the signed integer d (|d| < 256) times scale (a power of two): the float
+// of d by the magic-number addition 1.5 2^23 + d (exact for |d| < 2^22), scaled, then
+// its upper half, which is exact because d has at most 8 significant bits
+__device__ __forceinline__ uint32_t oz_digit_bf16(int d, float scale) {
+    return __float_as_uint((__int_as_float(0x4B400000 + d) - 12582912.0f) * scale) >> 16;
+}
+
+// 2^p as a float (compile-time p in the normal range)
+__host__ __device__ constexpr float oz_pow2(int p) {
+    return p >= 0 ? float(1ull << (p > 62 ? 62 : p)) : 1.0f / float(1ull << (-p > 62 ? 62 : -p));
+}
+
+// the S digit slices (8 K-adjacent values of one row / column) of the values with FP64
+// bits u[0..7], scale exponent e, stored as S 16-byte core-matrix rows at dst + i * stride
+template <int S, int B, int SHIFT0>
+__device__ __forceinline__ void oz_store_digits(const unsigned long long (&u)[8], int e, unsigned char* dst,
+                                                int stride) {
+    constexpr int BS = B * S;
+    unsigned long long F[8];
+    int sm[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+        F[v] = oz_fixed(u[v], e, BS);
+        sm[v] = -(int)(u[v] >> 63);                         // 0 or -1: the sign of the value
+    }
+#pragma unroll
+    for (int i = 0; i < S; ++i) {
+        constexpr int mask = (1 << B) - 1;
+        const float scale = oz_pow2(-B * (i + 1 - SHIFT0));  // slice i (digit i + 1) staged times 2^{-b (i + 1 - SHIFT0)}
+        uint32_t w[4];
+#pragma unroll
+        for (int v = 0; v < 8; v += 2) {
+            int d0 = (int)((F[v] >> (B * (S - 1 - i))) & mask);
+            int d1 = (int)((F[v + 1] >> (B * (S - 1 - i))) & mask);
+            d0 = (d0 ^ sm[v]) - sm[v];
+            d1 = (d1 ^ sm[v + 1]) - sm[v + 1];
+            w[v >> 1] = oz_digit_bf16(d0, scale) | (oz_digit_bf16(d1, scale) << 16);
+        }
+        *reinterpret_cast<uint4*>(dst + i * stride) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+// exact accumulator value (FP32 bits: an integer times a power of two) times 2^c as a
+// 64-bit integer (the shared "rest" accumulator rounds toward zero below 2^-c)
+__device__ __forceinline__ long long oz_acc_fixed(uint32_t bits, int c) {
+    const int ea = (int)((bits >> 23) & 0xFF);
+    if (ea == 0) return 0ll;
+    const long long m = (long long)((bits & 0x7FFFFFu) | 0x800000u);
+    const int sh = ea - 150 + c;                               // value 2^c = m 2^{sh}
+    const long long v = sh >= 0 ? (m << sh) : (sh <= -64 ? 0ll : (m >> (-sh)));
+    return (bits >> 31) ? -v : v;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(smem_u32(dst)), "l"(src), "r"(src_bytes));
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" :: "r"(smem_u32(dst)), "l"(src), "r"(src_bytes));
+}
+
+// Scale exponents of one element, written to ex[el][0..NT) (rows of W, one warp per
+// row with lanes along the row) and ex[el][NT..2NT) (columns of Z, one thread per
+// column, coalesced over the columns): e with every |value| < 2^e, 0 for zero rows.
+template <class C>
+__global__ void __launch_bounds__(256) k_oz_scales(const double* top, const double* bot, int64_t e0, int32_t* ex) {
+    constexpr int NU = C::NU, NT = C::NT, LD = C::LD;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int64_t el = blockIdx.x, e = e0 + el;
+    const unsigned long long* Wb = reinterpret_cast<const unsigned long long*>(bot + el * (size_t)NT * LD);
+    const unsigned long long* Zb = reinterpret_cast<const unsigned long long*>(top + e * (size_t)NU * LD + NU);
+    int32_t* out = ex + el * 2 * NT;
+    for (int r = warp; r < NT; r += 8) {
+        int m = INT_MIN;
+#pragma unroll 4
+        for (int k = lane; k < NU; k += 32) m = max(m, oz_exponent(Wb[(size_t)r * LD + k]));
+        m = __reduce_max_sync(0xffffffffu, m);
+        if (lane == 0) out[r] = m == INT_MIN ? 0 : m;
+    }
+    for (int c = tid; c < NT; c += 256) {
+        int m = INT_MIN;
+#pragma unroll 8
+        for (int k = 0; k < NU; ++k) m = max(m, oz_exponent(Zb[(size_t)k * LD + c]));
+        out[NT + c] = m == INT_MIN ? 0 : m;
+    }
 }
 
 template <class C>
-__global__ void __launch_bounds__(128) k_schur_ozaki(double* top, double* bot, int64_t e0, int32_t* status) {
+__global__ void __launch_bounds__(OZ_THREADS, 1) k_schur_ozaki(double* top, double* bot, int64_t e0, const int32_t* ex,
+                                                               int32_t* status) {
     using O = OzakiCfg<C>;
     constexpr int NU = C::NU, NT = C::NT, LD = C::LD;
-    constexpr int MT = O::MT, NTN = O::NTN, KC = O::KC, S = O::S, B = O::B, BS = O::B * O::S;
+    constexpr int MT = O::MT, NTN = O::NTN, KC = O::KC, S = O::S, B = O::B, WRS = O::WRS;
+    constexpr int NW = OZ_THREADS / 32;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t bid = blockIdx.x;
     const int nt = (int)(bid % O::NNT), mt = (int)((bid / O::NNT) % O::NMT);
@@ -97,29 +179,40 @@ __global__ void __launch_bounds__(128) k_schur_ozaki(double* top, double* bot, i
     const int m0 = mt * MT, n0 = nt * NTN;
     const double* Z = top + e * (size_t)NU * LD + NU;          // Z_kc at Z[k * LD + c]
     double* Bm = bot + el * (size_t)NT * LD;                    // W_rk at Bm[r * LD + k], S_rc at Bm[r * LD + NU + c]
+    const unsigned long long* Zb = reinterpret_cast<const unsigned long long*>(Z);
+    const unsigned long long* Wb = reinterpret_cast<const unsigned long long*>(Bm);
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char* As = smraw;                                  // S slices [MT rows][KC] BF16, core layout
-    unsigned char* Bs = smraw + S * O::A_SLICE;                 // S slices [NTN cols][KC]
-    int* er = reinterpret_cast<int*>(Bs + S * O::B_SLICE);      // [MT] row exponents
+    unsigned char* Bs = As + S * O::A_SLICE;                    // S slices [NTN cols][KC]
+    unsigned long long* Wr = reinterpret_cast<unsigned long long*>(Bs + S * O::B_SLICE);   // [MT][WRS] raw W
+    unsigned long long* Zr = Wr + MT * WRS;                     // [KC][NTN] raw Z
+    int* er = reinterpret_cast<int*>(Zr + KC * NTN);            // [MT] row exponents
     int* fc = er + MT;                                          // [NTN] column exponents
     uint64_t* mbar = reinterpret_cast<uint64_t*>(fc + NTN);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
 
-    // row and column scales
-    {
-        const int r = m0 + tid;
-        int m = INT_MIN;
-        if (tid < MT && r < NT)
-            for (int k = 0; k < NU; ++k) m = max(m, oz_exponent(Bm[(size_t)r * LD + k]));
-        er[tid] = m == INT_MIN ? 0 : m;
-    }
-    if (tid < NTN) {
-        const int c = n0 + tid;
-        int m = INT_MIN;
-        if (c < NT)
-            for (int k = 0; k < NU; ++k) m = max(m, oz_exponent(Z[(size_t)k * LD + c]));
-        fc[tid] = m == INT_MIN ? 0 : m;
-    }
+    // raw FP64 tiles of the chunk starting at k0, copied asynchronously; rows past the tile
+    // (W rows >= NT, Z rows >= NU, Z columns >= NT) are zero-filled without reading
+    auto prefetch = [&](int k0) {
+        for (int it = tid; it < MT * (KC / 2); it += OZ_THREADS) {      // W: 16-byte pieces
+            const int r = it / (KC / 2), pz = it - r * (KC / 2);
+            const bool in = m0 + r < NT;                                 // columns k0 .. k0 + 31 < LD
+            cp_async16(Wr + r * WRS + 2 * pz, in ? (const void*)(Wb + (size_t)(m0 + r) * LD + k0 + 2 * pz) : (const void*)Wb,
+                       in ? 16 : 0);
+        }
+        for (int it = tid; it < KC * NTN; it += OZ_THREADS) {            // Z: 8-byte words (row offset NU may be odd)
+            const int k = it / NTN, n = it - k * NTN;
+            const bool in = k0 + k < NU && n0 + n < NT;
+            cp_async8(Zr + k * NTN + n, in ? (const void*)(Zb + (size_t)(k0 + k) * LD + n0 + n) : (const void*)Zb,
+                      in ? 8 : 0);
+        }
+        asm volatile("cp.async.commit_group;");
+    };
+    prefetch(0);
+
+    // row and column scales of this tile (k_oz_scales)
+    for (int i = tid; i < MT; i += OZ_THREADS) er[i] = m0 + i < NT ? ex[el * 2 * NT + m0 + i] : 0;
+    for (int i = tid; i < NTN; i += OZ_THREADS) fc[i] = n0 + i < NT ? ex[el * 2 * NT + NT + n0 + i] : 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(tslot)),
                      "r"(O::TCOLS));
@@ -138,68 +231,52 @@ __global__ void __launch_bounds__(128) k_schur_ozaki(double* top, double* bot, i
                            ((uint32_t)(MT >> 4) << 24);
     const uint32_t bar = smem_u32(mbar);
     uint32_t phase = 0;
-    bool ok = true;
+    bool ok = true, pending = false;                            // an MMA batch reads the digit slices
     unsigned used = 0;                                          // accumulators written so far (thread 0)
     for (int k0 = 0; k0 < NU; k0 += KC) {
-        // A: item = (row r, 8-wide K group q): 8 FP64 values -> S slices of 8 BF16 (16 bytes each)
-        for (int it = tid; it < MT * (KC / 8); it += 128) {
-            const int r = it / (KC / 8), q = it - r * (KC / 8);
-            const int row = m0 + r;
-            uint16_t dig[S][8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int k = k0 + q * 8 + u;
-                const double v = (row < NT && k < NU) ? Bm[(size_t)row * LD + k] : 0.0;
-                const unsigned long long F = oz_fixed(v, er[r], BS);
-                const bool neg = v < 0.0;
-#pragma unroll
-                for (int i = 0; i < S; ++i) {
-                    const int d = (int)((F >> (B * (S - 1 - i))) & ((1u << B) - 1));
-                    dig[i][u] = oz_bf16(neg ? -d : d, -B * (i + 1 - 3));      // 2^{-b (i - 3)}, i from 1
-                }
+        asm volatile("cp.async.wait_group 0;");
+        if (pending) {                                          // the previous batch still reads the slices
+            if (!mbar_wait_bounded(bar, phase, 1 << 24)) {
+                ok = false;
+                if (tid == 0) atomicOr(status, 4);
+                mbar_wait_bounded(bar, phase, 1 << 24);
             }
-            // core matrix (8-row group r / 8, K group q): offset ((r / 8) * (KC / 8) + q) * 128 + (r % 8) * 16
-            const int off = ((r >> 3) * (KC / 8) + q) * 128 + (r & 7) * 16;
-#pragma unroll
-            for (int i = 0; i < S; ++i) {
-                uint4 w;
-                w.x = dig[i][0] | ((uint32_t)dig[i][1] << 16);
-                w.y = dig[i][2] | ((uint32_t)dig[i][3] << 16);
-                w.z = dig[i][4] | ((uint32_t)dig[i][5] << 16);
-                w.w = dig[i][6] | ((uint32_t)dig[i][7] << 16);
-                *reinterpret_cast<uint4*>(As + i * O::A_SLICE + off) = w;
-            }
+            phase ^= 1;
+            pending = false;
         }
-        // B: item = (column n, 8-wide K group q)
-        for (int it = tid; it < NTN * (KC / 8); it += 128) {
+        // raw tiles of this chunk visible, slices free; a timed-out wait stops every thread
+        if (__syncthreads_or(ok ? 0 : 1)) {
+            ok = false;
+            break;
+        }
+        // A: item = (row r, 8-wide K group q), rows fastest
+        for (int it = tid; it < MT * (KC / 8); it += OZ_THREADS) {
+            const int r = it % MT, q = it / MT;
+            unsigned long long u[8];
+            const ulonglong2* src = reinterpret_cast<const ulonglong2*>(Wr + r * WRS + q * 8);
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const ulonglong2 x = src[v];
+                u[2 * v] = x.x;
+                u[2 * v + 1] = x.y;
+            }
+#pragma unroll
+            for (int v = 0; v < 8; ++v) if (k0 + q * 8 + v >= NU) u[v] = 0ull;   // trace columns: not W
+            const int off = ((r >> 3) * (KC / 8) + q) * 128 + (r & 7) * 16;
+            oz_store_digits<S, B, 3>(u, er[r], As + off, O::A_SLICE);
+        }
+        // B: item = (column n, 8-wide K group q), columns fastest
+        for (int it = tid; it < NTN * (KC / 8); it += OZ_THREADS) {
             const int n = it % NTN, q = it / NTN;
-            const int col = n0 + n;
-            uint16_t dig[S][8];
+            unsigned long long u[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int k = k0 + q * 8 + u;
-                const double v = (col < NT && k < NU) ? Z[(size_t)k * LD + col] : 0.0;
-                const unsigned long long F = oz_fixed(v, fc[n], BS);
-                const bool neg = v < 0.0;
-#pragma unroll
-                for (int j = 0; j < S; ++j) {
-                    const int d = (int)((F >> (B * (S - 1 - j))) & ((1u << B) - 1));
-                    dig[j][u] = oz_bf16(neg ? -d : d, -B * (j + 1 - 4));      // 2^{-b (j - 4)}
-                }
-            }
+            for (int v = 0; v < 8; ++v) u[v] = Zr[(q * 8 + v) * NTN + n];
             const int off = ((n >> 3) * (KC / 8) + q) * 128 + (n & 7) * 16;
-#pragma unroll
-            for (int j = 0; j < S; ++j) {
-                uint4 w;
-                w.x = dig[j][0] | ((uint32_t)dig[j][1] << 16);
-                w.y = dig[j][2] | ((uint32_t)dig[j][3] << 16);
-                w.z = dig[j][4] | ((uint32_t)dig[j][5] << 16);
-                w.w = dig[j][6] | ((uint32_t)dig[j][7] << 16);
-                *reinterpret_cast<uint4*>(Bs + j * O::B_SLICE + off) = w;
-            }
+            oz_store_digits<S, B, 4>(u, fc[n], Bs + off, O::B_SLICE);
         }
         asm volatile("fence.proxy.async.shared::cta;");
-        __syncthreads();
+        __syncthreads();                                        // slices written, raw tiles consumed
+        if (k0 + KC < NU) prefetch(k0 + KC);                    // next chunk's tiles under this chunk's MMAs
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
             const int nsteps = (min(KC, NU - k0) + 15) / 16;
@@ -221,49 +298,57 @@ __global__ void __launch_bounds__(128) k_schur_ozaki(double* top, double* bot, i
                 }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar));
         }
+        pending = true;
+    }
+    asm volatile("cp.async.wait_group 0;");
+    if (pending && ok) {
         if (!mbar_wait_bounded(bar, phase, 1 << 24)) {
             ok = false;
             if (tid == 0) atomicOr(status, 4);
             mbar_wait_bounded(bar, phase, 1 << 24);
         }
         phase ^= 1;
-        __syncthreads();
-        if (!ok) break;
     }
+    ok = !__syncthreads_or(ok ? 0 : 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok) {
-        // row r of the tile is tensor-memory lane r: warp w reads lanes 32 w .. 32 w + 31
-        const int r = warp * 32 + lane, row = m0 + r;
-        const int escale = er[r] - 7 * B;
-#pragma unroll 1
-        for (int c0 = 0; c0 < NTN; c0 += 16) {
-            double sum[16];
+        // warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (tile rows) and the 16-column
+        // quarter w / 4 of the tile; the six accumulators are combined exactly as integers in
+        // units of 2^{5b - 38} (the leading group needs at most 62 bits), converted once to FP64,
+        // scaled by 2^{e_r + f_c - 2b - 38} and subtracted from Dt
+        const int lg = warp & 3, c0 = (warp >> 2) * 16;
+        const int r = lg * 32 + lane, row = m0 + r;
+        long long tot[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) sum[j] = 0.0;
+        for (int j = 0; j < 16; ++j) tot[j] = 0ll;
 #pragma unroll 1
-            for (int g = 0; g < O::NACC; ++g) {
-                uint32_t v[16];
-                const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(g * NTN + c0);
-                asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                               "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                               "=r"(v[14]), "=r"(v[15])
-                             : "r"(addr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;");
-                // accumulator g holds a group only if some kept digit pair falls in it
-                if (g < 5 ? (g + 2 <= S + 1) : (S + 1 >= 7)) {
+        for (int g = 0; g < O::NACC; ++g) {
+            uint32_t v[16];
+            const uint32_t addr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)(g * NTN + c0);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                         : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                           "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                           "=r"(v[14]), "=r"(v[15])
+                         : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            // accumulator g holds a group only if some kept digit pair falls in it
+            if (g < 5 ? (g + 2 <= S + 1) : (S + 1 >= 7)) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) sum[j] += (double)__uint_as_float(v[j]);
-                }
+                for (int j = 0; j < 16; ++j) tot[j] += oz_acc_fixed(v[j], 38 - 5 * B);
             }
-            if (row < NT) {
+        }
+        if (row < NT) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int c = n0 + c0 + j;
-                    if (c0 + j < NTN && c < NT) {
-                        double* s = Bm + (size_t)row * LD + NU + c;
-                        *s -= ldexp(sum[j], escale + fc[c0 + j]);
-                    }
+            for (int j = 0; j < 16; ++j) {
+                const int c = n0 + c0 + j;
+                if (c < NT) {
+                    const int sc = er[r] + fc[c0 + j] - 2 * B - 38;
+                    const double x = __ll2double_rn(tot[j]);
+                    double* sp = Bm + (size_t)row * LD + NU + c;
+                    if (sc > -1023 && sc < 1024)               // 2^sc as a normal double, from its bits
+                        *sp -= x * __longlong_as_double((long long)(1023 + sc) << 52);
+                    else
+                        *sp -= ldexp(x, sc);
                 }
             }
         }

@@ -865,6 +865,22 @@ __global__ void __launch_bounds__(RMV_THREADS, 4) k_tet_rowmv(const T* __restric
 }
 
 // A7: dU = -U^{-1} (z + Z dUhat_K), dQ = dq0 - G dU - H dUhat_K
+// element Schur complement S^K (rows and columns NU .. NU + t of the condensed
+// element matrix, local trace order) to out at skoff[e], one CTA per element
+template <class TO>
+__global__ void k_tet_copy_sk(const TetElem* el, const double* mat, const int64_t* skoff, int64_t E, TO* out) {
+    const int64_t e = blockIdx.x;
+    if (e >= E) return;
+    const TetElem& d = el[e];
+    const int t = d.t, NU = d.NU, LD = d.LD;
+    const double* Mx = mat + d.moff;
+    TO* o = out + skoff[e];
+    for (int idx = threadIdx.x; idx < t * t; idx += blockDim.x) {
+        const int r = idx / t, c = idx - r * t;
+        o[idx] = (TO)Mx[(int64_t)(NU + r) * LD + NU + c];
+    }
+}
+
 constexpr int REC_THREADS = 128;
 
 // Interior recovery dW_K = -y_K - X_K dUhat_K (eq. local-elimination), one CTA
@@ -1305,6 +1321,14 @@ int linearize(hdg_ctx* h, const double* U, const double* Q, const double* UH, co
     }
     prof_end(h);
     TET_CK(cudaGetLastError());
+    if (h->d_skout) {
+        if (h->precision == HDG_PREC_FP64)
+            k_tet_copy_sk<double><<<(unsigned)c->E, 256, 0, st>>>(c->d_el, c->d_mat, c->d_skoff, c->E,
+                                                                  static_cast<double*>(h->d_skout));
+        else
+            k_tet_copy_sk<float><<<(unsigned)c->E, 256, 0, st>>>(c->d_el, c->d_mat, c->d_skoff, c->E,
+                                                                 static_cast<float*>(h->d_skout));
+    }
     prof_begin(h, HDG_K_ASSEMBLE);
     const unsigned gb = (unsigned)std::min<int64_t>(65535, (c->nnzb + 7) / 8);
     if (h->precision == HDG_PREC_FP64) {
@@ -1323,6 +1347,19 @@ int linearize(hdg_ctx* h, const double* U, const double* Q, const double* UH, co
     h->have_system = true;
     c->bj_ready = false;       // the diagonal blocks changed
     c->asm_ready = false;      // and so did the patches
+    return HDG_OK;
+}
+
+int set_element_block_output(hdg_ctx* h, void* SK) {
+    Ctx* c = h->tet;
+    if (SK && !c->d_skoff) {
+        std::vector<int64_t> off(c->E + 1, 0);
+        for (int64_t e = 0; e < c->E; ++e) off[e + 1] = off[e] + (int64_t)c->el[e].t * c->el[e].t;
+        std::string err;
+        const int rc = tet_upload(h, &c->d_skoff, off, err);
+        if (rc) { h->err = err; return rc; }
+    }
+    h->d_skout = SK;
     return HDG_OK;
 }
 

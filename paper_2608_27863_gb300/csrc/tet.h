@@ -119,6 +119,7 @@ struct Ctx {
     double* d_asmz = nullptr;              // [sum t] patch corrections
     int32_t* d_asmnext = nullptr;          // work counter of the set-up
     int64_t n_asm = 0, n_patch = 0;
+    int64_t* d_skoff = nullptr;            // [E + 1] offsets of the element Schur complements (t^2 each)
     int asm_prec = -1;                     // precision of the stored factors
     bool asm_ready = false;
 };
@@ -139,6 +140,8 @@ int residual(hdg_ctx* h, const double* U, const double* Q, const double* UH, con
              double a_ii, double* Rq, double* Ru, double* Ruh, double* norms);
 int bj_setup(hdg_ctx* h);
 int bj_apply(hdg_ctx* h, const double* x, double* y);
+// element Schur complements to the caller's buffer (packed [t_e][t_e] at offsets sum t^2)
+int set_element_block_output(hdg_ctx* h, void* SK);
 // additive Schwarz on element face patches (tet_schwarz.cu)
 int asm_setup(hdg_ctx* h);
 int asm_apply(hdg_ctx* h, const double* x, double* y);

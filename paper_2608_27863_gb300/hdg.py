@@ -41,7 +41,7 @@ EXPORTS = [
     "hdg_schwarz_apply", "hdg_rb_setup", "hdg_rb_push", "hdg_rb_guess", "hdg_av_field", "hdg_tgv_diagnostics",
     "hdg_autotune", "hdg_set_tuning", "hdg_set_bc_field", "hdg_reserve", "hdg_create_tet", "hdg_create_tet_host",
     "hdg_tet_query", "hdg_tet_layout", "hdg_tet_ref_tables", "hdg_tri_ref_tables", "hdg_partition",
-    "hdg_part_layout", "hdg_sdirk3_tableau", "hdg_measure_peaks",
+    "hdg_part_layout", "hdg_sdirk3_tableau", "hdg_measure_peaks", "hdg_set_element_block_output",
 ]
 KERNEL_CLASSES = ["point", "blocks", "elim", "assemble", "matvec", "recover", "schur"]
 
@@ -139,6 +139,7 @@ def lib():
         "hdg_dirk_step": [vp, vp, vp, vp, vp, dbl, i32, vp, vp, i32, i32, i32, vp],
         "hdg_sdirk3_tableau": [vp, vp],
         "hdg_measure_peaks": [vp, vp],
+        "hdg_set_element_block_output": [vp, vp],
         "hdg_create_tet": [ctypes.POINTER(vp), ctypes.POINTER(hdg_tet_mesh), dbl, dbl, dbl, dbl],
         "hdg_create_tet_host": [ctypes.POINTER(vp), ctypes.POINTER(hdg_tet_mesh), dbl, dbl, dbl, dbl],
         "hdg_tet_query": [vp, ctypes.POINTER(hdg_tet_sizes)],
@@ -272,6 +273,11 @@ def hdg_recover_interior(h, dUH, dQ, dU):
 
 def hdg_get_blocks(h, vals):
     _check(h, lib().hdg_get_blocks(h, _ptr(vals)))
+
+
+def hdg_set_element_block_output(h, SK):
+    """Later linearizations also write every element's S^K to SK (device tensor), or None to stop."""
+    _check(h, lib().hdg_set_element_block_output(h, _ptr(SK)))
 
 
 def hdg_status(h):
