@@ -24,6 +24,8 @@
 
 #include "common.h"
 #include "physics.cuh"
+#include "tc_util.cuh"
+#include "tma.h"
 
 namespace hdg {
 
@@ -1006,8 +1008,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_elim(double* top, double* bot, in
                 rowp(r)[NC - 1] = s;
             }
             __syncthreads();
-            continue;
-        }
+        } else {
 #pragma unroll 1
         for (int ct = c0; ct < NC; ct += TCW) {
             for (int idx = tid; idx < kb * TCW; idx += NTH) {
@@ -1032,6 +1033,7 @@ __global__ void __launch_bounds__(NTH, MINB) k_elim(double* top, double* bot, in
                 }
             }
             __syncthreads();
+        }
         }
     }
     if (tid == 0 && sflag) atomicOr(status, sflag);
@@ -1268,14 +1270,12 @@ __global__ void k_copy_sk(const TS* src, int64_t src_es, int64_t rs, int64_t col
     }
 }
 
-// FP64 Schur product on the tensor cores (ozaki.cuh)
-constexpr int OZ_THREADS = 512;
-template <class C>
-struct OzakiCfg;
-template <class C>
-__global__ void k_oz_scales(const double* top, const double* bot, int64_t e0, int32_t* ex);
-template <class C>
-__global__ void k_schur_ozaki(double* top, double* bot, int64_t e0, const int32_t* ex, int32_t* status);
+}  // namespace hdg
+
+// FP64 Schur product on the tensor cores (defined before its launch below)
+#include "ozaki.cuh"
+
+namespace hdg {
 
 template <int D, int P>
 int run_linearize(hdg_ctx* h, const LinArgs& la) {
@@ -1357,8 +1357,17 @@ int run_linearize(hdg_ctx* h, const LinArgs& la) {
             prof_end(h);
             prof_begin(h, HDG_K_SCHUR);
             k_oz_scales<C><<<(unsigned)ne, 256, 0, st>>>(h->d_top, h->d_bot, e0, h->d_ozexp);
+            CUtensorMap tmW, tmZ;                 // trace rows of this chunk, interior rows of every element
+            std::string terr;
+            if (make_tmap_f64_3d(&tmW, h->d_bot, C::LD, C::NT, (uint64_t)ne, 8ull * C::LD, 8ull * C::LD * C::NT,
+                                 OzakiCfg<C>::WRS, OzakiCfg<C>::MT, terr) ||
+                make_tmap_f64_3d(&tmZ, h->d_top, C::LD, C::NU, (uint64_t)h->E, 8ull * C::LD, 8ull * C::LD * C::NU,
+                                 OzakiCfg<C>::ZRS, OzakiCfg<C>::KC, terr)) {
+                h->err = terr;
+                return HDG_ECUDA;
+            }
             k_schur_ozaki<C><<<(unsigned)(ne * OzakiCfg<C>::NMT * OzakiCfg<C>::NNT), OZ_THREADS, OzakiCfg<C>::SMEM, st>>>(
-                h->d_top, h->d_bot, e0, h->d_ozexp, h->d_status);
+                h->d_top, h->d_bot, e0, h->d_ozexp, h->d_status, tmW, tmZ);
         } else if (h->elim_nb == 8) {
             if (h->elim_minb == 1)
                 k_elim<C, 8, 256, 1><<<(unsigned)ne, 256, sm_elim8, st>>>(h->d_top, h->d_bot, e0, h->d_status);

@@ -25,8 +25,9 @@
 //
 // k_oz_scales first computes every row's and column's exponent once per element.
 // Then one CTA (16 warps) per (element, 128-row tile, 64-column tile) walks K in
-// 32-wide chunks: the raw FP64 tiles of the next chunk are copied into shared
-// memory by cp.async while the tensor cores run the current one; the threads cut
+// 32-wide chunks: the raw FP64 tiles of the next chunk are loaded into shared
+// memory by TMA (cp.async.bulk.tensor, completing on an mbarrier) while the
+// tensor cores run the current one; the threads cut
 // the current raw tiles into the s digit slices of its W rows and Z columns, in
 // the canonical K-major layout without swizzle (8-row x 16-byte core matrices,
 // K-adjacent cores 128 B apart, 8-row groups 512 B apart), and one thread
@@ -37,11 +38,17 @@
 // and frees its tensor memory.
 #pragma once
 
-#include <cuda_bf16.h>
+#include <climits>
+#include <cstdint>
 
-#include "mixed.cuh"
+#include <cuda.h>
+
+#include "common.h"
+#include "tc_util.cuh"
 
 namespace hdg {
+
+constexpr int OZ_THREADS = 512;
 
 template <class C>
 struct OzakiCfg {
@@ -54,9 +61,13 @@ struct OzakiCfg {
     static constexpr int NMT = (NT + MT - 1) / MT, NNT = (NT + NTN - 1) / NTN;
     static constexpr int TCOLS = 512;                     // NACC * NTN = 384 columns allocated as 512
     static constexpr int A_SLICE = MT * KC * 2, B_SLICE = NTN * KC * 2;   // bytes of one digit slice
-    static constexpr int WRS = KC + 2;                    // raw W tile row stride (doubles): conflict-free rows
-    static constexpr int RAW = (MT * WRS + KC * NTN) * 8; // raw FP64 tiles of the next chunk
-    static constexpr int SMEM = S * (A_SLICE + B_SLICE) + RAW + (MT + NTN) * 4 + 64;
+    static constexpr int WRS = KC + 2;                    // raw W tile row (doubles): the TMA box is 2 wider than
+                                                          // the chunk, which also makes the rows conflict-free
+    static constexpr int ZRS = NTN + 2;                   // raw Z tile row: the box starts at an even column
+    static constexpr int RAW = (MT * WRS + KC * ZRS) * 8; // raw FP64 tiles of the next chunk
+    static constexpr int LOAD_BYTES = RAW;                // bytes one chunk's two TMA loads deliver
+    static constexpr int SMEM = S * (A_SLICE + B_SLICE) + RAW + (MT + NTN) * 4 + 64 + 16;
+    static_assert((S * (A_SLICE + B_SLICE)) % 128 == 0 && (MT * WRS * 8) % 128 == 0, "TMA destinations 128-B aligned");
     static_assert(S <= 9 && B * S >= 54 && B * S <= 56, "digit layout");
     static_assert(NACC * NTN <= TCOLS, "tensor-memory columns");
     static_assert((5LL * K * ((1 << B) - 1) * ((1 << B) - 1)) < (1LL << 24), "exact FP32 group accumulation");
@@ -132,13 +143,6 @@ __device__ __forceinline__ long long oz_acc_fixed(uint32_t bits, int c) {
     return (bits >> 31) ? -v : v;
 }
 
-__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" :: "r"(smem_u32(dst)), "l"(src), "r"(src_bytes));
-}
-__device__ __forceinline__ void cp_async8(void* dst, const void* src, int src_bytes) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" :: "r"(smem_u32(dst)), "l"(src), "r"(src_bytes));
-}
-
 // Scale exponents of one element, written to ex[el][0..NT) (rows of W, one warp per
 // row with lanes along the row) and ex[el][NT..2NT) (columns of Z, one thread per
 // column, coalesced over the columns): e with every |value| < 2^e, 0 for zero rows.
@@ -165,49 +169,58 @@ __global__ void __launch_bounds__(256) k_oz_scales(const double* top, const doub
     }
 }
 
+// W tiles: tmW over the chunk's trace rows [chunk][NT][LD] (box 34 x 128); Z tiles: tmZ
+// over the interior rows [E][NU][LD] (box 66 x 32, starting at the even column at or
+// below NU + n0); rows past NT (W) or NU (Z) and columns past LD arrive as zeros.
 template <class C>
 __global__ void __launch_bounds__(OZ_THREADS, 1) k_schur_ozaki(double* top, double* bot, int64_t e0, const int32_t* ex,
-                                                               int32_t* status) {
+                                                               int32_t* status, const __grid_constant__ CUtensorMap tmW,
+                                                               const __grid_constant__ CUtensorMap tmZ) {
     using O = OzakiCfg<C>;
     constexpr int NU = C::NU, NT = C::NT, LD = C::LD;
-    constexpr int MT = O::MT, NTN = O::NTN, KC = O::KC, S = O::S, B = O::B, WRS = O::WRS;
-    constexpr int NW = OZ_THREADS / 32;
+    constexpr int MT = O::MT, NTN = O::NTN, KC = O::KC, S = O::S, B = O::B, WRS = O::WRS, ZRS = O::ZRS;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t bid = blockIdx.x;
     const int nt = (int)(bid % O::NNT), mt = (int)((bid / O::NNT) % O::NMT);
     const int64_t el = bid / (O::NNT * O::NMT), e = e0 + el;
     const int m0 = mt * MT, n0 = nt * NTN;
-    const double* Z = top + e * (size_t)NU * LD + NU;          // Z_kc at Z[k * LD + c]
-    double* Bm = bot + el * (size_t)NT * LD;                    // W_rk at Bm[r * LD + k], S_rc at Bm[r * LD + NU + c]
-    const unsigned long long* Zb = reinterpret_cast<const unsigned long long*>(Z);
-    const unsigned long long* Wb = reinterpret_cast<const unsigned long long*>(Bm);
+    double* Bm = bot + el * (size_t)NT * LD;                    // S_rc at Bm[r * LD + NU + c]
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char* As = smraw;                                  // S slices [MT rows][KC] BF16, core layout
     unsigned char* Bs = As + S * O::A_SLICE;                    // S slices [NTN cols][KC]
     unsigned long long* Wr = reinterpret_cast<unsigned long long*>(Bs + S * O::B_SLICE);   // [MT][WRS] raw W
-    unsigned long long* Zr = Wr + MT * WRS;                     // [KC][NTN] raw Z
-    int* er = reinterpret_cast<int*>(Zr + KC * NTN);            // [MT] row exponents
+    unsigned long long* Zr = Wr + MT * WRS;                     // [KC][ZRS] raw Z
+    int* er = reinterpret_cast<int*>(Zr + KC * ZRS);            // [MT] row exponents
     int* fc = er + MT;                                          // [NTN] column exponents
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(fc + NTN);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(fc + NTN);    // [0] MMA completion, [1] TMA loads
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
 
-    // raw FP64 tiles of the chunk starting at k0, copied asynchronously; rows past the tile
-    // (W rows >= NT, Z rows >= NU, Z columns >= NT) are zero-filled without reading
+    // raw FP64 tiles of the chunk starting at k0, loaded by the tensor memory accelerator
+    const int zx = (NU + n0) & ~1, zoff = (NU + n0) & 1;        // Z box column start (even) and the offset in it
+    const uint32_t bar_ld = smem_u32(mbar + 1);
+    uint32_t ld_phase = 0;
+    bool ld_pending = false;                                    // a load is in flight (all threads track it)
     auto prefetch = [&](int k0) {
-        for (int it = tid; it < MT * (KC / 2); it += OZ_THREADS) {      // W: 16-byte pieces
-            const int r = it / (KC / 2), pz = it - r * (KC / 2);
-            const bool in = m0 + r < NT;                                 // columns k0 .. k0 + 31 < LD
-            cp_async16(Wr + r * WRS + 2 * pz, in ? (const void*)(Wb + (size_t)(m0 + r) * LD + k0 + 2 * pz) : (const void*)Wb,
-                       in ? 16 : 0);
+        ld_pending = true;
+        if (tid == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" :: "r"(bar_ld), "r"(O::LOAD_BYTES)
+                         : "memory");
+            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                         "[%0], [%1, {%2, %3, %4}], [%5];"
+                         :: "r"(smem_u32(Wr)), "l"(reinterpret_cast<uint64_t>(&tmW)), "r"(k0), "r"(m0), "r"((int)el),
+                            "r"(bar_ld) : "memory");
+            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+                         "[%0], [%1, {%2, %3, %4}], [%5];"
+                         :: "r"(smem_u32(Zr)), "l"(reinterpret_cast<uint64_t>(&tmZ)), "r"(zx), "r"(k0), "r"((int)e),
+                            "r"(bar_ld) : "memory");
         }
-        for (int it = tid; it < KC * NTN; it += OZ_THREADS) {            // Z: 8-byte words (row offset NU may be odd)
-            const int k = it / NTN, n = it - k * NTN;
-            const bool in = k0 + k < NU && n0 + n < NT;
-            cp_async8(Zr + k * NTN + n, in ? (const void*)(Zb + (size_t)(k0 + k) * LD + n0 + n) : (const void*)Zb,
-                      in ? 8 : 0);
-        }
-        asm volatile("cp.async.commit_group;");
     };
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(bar_ld), "r"(1));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    __syncthreads();
     prefetch(0);
 
     // row and column scales of this tile (k_oz_scales)
@@ -217,10 +230,6 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_schur_ozaki(double* top, doub
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(tslot)),
                      "r"(O::TCOLS));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(1));
-        asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -234,7 +243,13 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_schur_ozaki(double* top, doub
     bool ok = true, pending = false;                            // an MMA batch reads the digit slices
     unsigned used = 0;                                          // accumulators written so far (thread 0)
     for (int k0 = 0; k0 < NU; k0 += KC) {
-        asm volatile("cp.async.wait_group 0;");
+        if (!mbar_wait_bounded(bar_ld, ld_phase, 1 << 24)) {   // this chunk's tiles have landed
+            ok = false;
+            if (tid == 0) atomicOr(status, 4);
+            mbar_wait_bounded(bar_ld, ld_phase, 1 << 24);
+        }
+        ld_phase ^= 1;
+        ld_pending = false;
         if (pending) {                                          // the previous batch still reads the slices
             if (!mbar_wait_bounded(bar, phase, 1 << 24)) {
                 ok = false;
@@ -270,13 +285,14 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_schur_ozaki(double* top, doub
             const int n = it % NTN, q = it / NTN;
             unsigned long long u[8];
 #pragma unroll
-            for (int v = 0; v < 8; ++v) u[v] = Zr[(q * 8 + v) * NTN + n];
+            for (int v = 0; v < 8; ++v) u[v] = n0 + n < NT ? Zr[(q * 8 + v) * ZRS + zoff + n] : 0ull;
             const int off = ((n >> 3) * (KC / 8) + q) * 128 + (n & 7) * 16;
             oz_store_digits<S, B, 4>(u, fc[n], Bs + off, O::B_SLICE);
         }
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();                                        // slices written, raw tiles consumed
         if (k0 + KC < NU) prefetch(k0 + KC);                    // next chunk's tiles under this chunk's MMAs
+        // (the fence.proxy.async above orders this CTA's reads of the raw tiles before the loads)
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
             const int nsteps = (min(KC, NU - k0) + 15) / 16;
@@ -300,7 +316,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_schur_ozaki(double* top, doub
         }
         pending = true;
     }
-    asm volatile("cp.async.wait_group 0;");
+    if (ld_pending) mbar_wait_bounded(bar_ld, ld_phase, 1 << 24);   // after an early stop: no copy outlives the CTA
     if (pending && ok) {
         if (!mbar_wait_bounded(bar, phase, 1 << 24)) {
             ok = false;

@@ -7,7 +7,6 @@
 #pragma once
 
 #include "mixed.cuh"
-#include "ozaki.cuh"
 #include "schwarz.cuh"
 #include "av.cuh"
 
