@@ -284,12 +284,35 @@ def run_tet(args, rank, world, local_rank):
         e2e_ms += s.elapsed_time(e)
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
     cpu = None
+    check_ids, check_refs = None, None
     if pool is not None:
         rate, n_done, secs = oracle_rate(pool, ncores, m.n_elem, args.cpu_seconds, 100)
+        check_ids = oracle_check_elements(elem_p=m.elem_p)
+        check_refs = pool.map(_worker_schur, check_ids)
         pool.close()
         cpu = {"value": rate, "unit": "elements/s", "cores": ncores, "cpu_model": cpu_model(), "kind": "oracle",
                "sample": "%d seeded elements of the workload in %.1f s: per-element residual, complex-step "
                          "Jacobian, dense FP64 LU of the (q,u) block and Schur complement" % (n_done, secs)}
+    oracle_check = None
+    if check_ids is not None:
+        # per-element S^K of both forms against the oracle's condensation of the same elements (untimed)
+        ts = np.diff(layout["hoff"])[layout["e2f"]].sum(1).astype(np.int64)
+        offs = np.concatenate([[0], np.cumsum(ts ** 2)])
+
+        def tet_prec(prec):
+            H.hdg_set_params(h, tau=P.tau, precision=prec)
+            H.hdg_set_tuning(h, elim_nb=tuning["mixed" if prec != H.HDG_PREC_FP64 else "fp64"]["elim_nb"])
+
+        run1 = lambda: H.hdg_linearize_condense(h, U, Q, UH, Us, None, P.dt, P.a_ii)
+        precs = {"fp64": (H.HDG_PREC_FP64, tet_prec, run1)}
+        if not args.no_mixed:
+            precs["mixed"] = (H.HDG_PREC_MIXED, tet_prec, run1)
+        oracle_check = element_block_errors(H, h, torch, check_ids, offs, ts, check_refs, precs)
+        oracle_check = {"what": "relative Frobenius error of the per-element Schur complement S^K against the "
+                                "FP64 CPU oracle's condensation of the same element",
+                        "elements": check_ids, "degrees": [int(m.elem_p[e]) for e in check_ids], **oracle_check}
+        H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_FP64)
+        H.hdg_set_tuning(h, elim_nb=tuning["fp64"]["elim_nb"])
     E = m.n_elem
     fl = tet_flops(layout, m.elem_p.astype(np.int64))
     kern = {k: {"ms_per_step": v[0] / args.steps, "launches_per_step": v[1] / args.steps}
@@ -307,6 +330,8 @@ def run_tet(args, rank, world, local_rank):
              "dtype": "fp64 pointwise terms, lifting operators, elimination and residual; fp32 Jacobian "
                       "coefficients, column variations and contraction",
              "clocks": clocks_m}
+    if mixed is not None and oracle_check is not None:
+        mixed["block_err_vs_oracle"] = oracle_check["mixed"]["max_rel_err"]
     if not args.no_newton and mixed is not None:
         newton = {}
         H.hdg_set_preconditioner(h, H.HDG_PC_SCHWARZ if args.precond == "schwarz" else H.HDG_PC_BLOCKJACOBI)
@@ -383,6 +408,8 @@ def run_tet(args, rank, world, local_rank):
         "tuning": tuning,
         "peaks_measured_tflops": peaks,
     }
+    if oracle_check is not None:
+        out["oracle_check"] = oracle_check
     if cpu is not None:
         out["cpu_baseline"] = cpu
     H.hdg_destroy(h)
@@ -527,6 +554,11 @@ def _worker_condense(e):
     return 1
 
 
+def _worker_schur(e):
+    """The oracle's condensed element matrix S^K of element e (FP64)."""
+    return _W["pb"].condense(int(e))["S"]
+
+
 def oracle_pool(name, cores):
     import multiprocessing as mp
     saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
@@ -541,6 +573,44 @@ def oracle_pool(name, cores):
             os.environ[k] = v
     pool.map(_worker_condense, [0] * cores)  # warm every worker
     return pool
+
+
+def oracle_check_elements(elem_p=None, n_elem=0):
+    """Elements whose S^K the oracle leg also returns: for a mixed-degree mesh the
+    first and last element of every degree, else four spread over the mesh."""
+    if elem_p is not None:
+        import numpy as np
+        ids = []
+        for p in range(1, int(elem_p.max()) + 1):
+            w = np.flatnonzero(elem_p == p)
+            if len(w):
+                ids += [int(w[0]), int(w[-1])]
+        return sorted(set(ids))
+    return sorted({0, n_elem // 3, (2 * n_elem) // 3, n_elem - 1})
+
+
+def element_block_errors(H, h, torch, ids, offs, sizes, refs, precisions):
+    """Relative Frobenius error of the library's per-element S^K against the oracle's,
+    per precision (one linearization each through hdg_set_element_block_output)."""
+    total = int(offs[-1])
+    buf = torch.empty(total, dtype=torch.float64, device="cuda")
+    out = {}
+    for name, (prec, set_prec, run) in precisions.items():
+        set_prec(prec)
+        sk = buf if prec == H.HDG_PREC_FP64 else buf.view(torch.float32)[:total]
+        H.hdg_set_element_block_output(h, sk)
+        run()
+        torch.cuda.synchronize()
+        H.hdg_set_element_block_output(h, None)
+        errs = []
+        for e, ref in zip(ids, refs):
+            t = int(sizes[e])
+            got = sk[int(offs[e]):int(offs[e]) + t * t].double().cpu().numpy().reshape(t, t)
+            errs.append(float(((got - ref) ** 2).sum() ** 0.5 / max((ref ** 2).sum() ** 0.5, 1e-300)))
+        out[name] = {"max_rel_err": max(errs), "per_element": errs}
+    del buf
+    torch.cuda.empty_cache()
+    return out
 
 
 def oracle_rate(pool, cores, n_elem, seconds, seed):
@@ -757,15 +827,43 @@ def run_ours(args, rank, world, local_rank):
         e2e_ms += s.elapsed_time(e)
     e2e_ms = max_over_ranks(e2e_ms, world, dev)
 
+    check_ids, check_refs = None, None
     if pool is not None:
         n_sample = make_problem(args.workload, cpu_sample=True).mesh.n_elem if "cpu" in wl else m.n_elem
         rate, n_done, secs = oracle_rate(pool, ncores, n_sample, args.cpu_seconds, 100)
+        if "cpu" not in wl and not ("av" in wl and P.nu is None):
+            # the oracle's elements are this workload's (same mesh, state and viscosity field)
+            check_ids = oracle_check_elements(n_elem=m.n_elem)
+            check_refs = pool.map(_worker_schur, check_ids)
         pool.close()
         cpu = {"value": rate, "unit": "elements/s", "cores": ncores, "cpu_model": cpu_model(), "kind": "oracle",
                "sample": "%d seeded elements of %s in %.1f s: per-element residual, complex-step "
                          "Jacobian, dense FP64 LU of the (q,u) block and Schur complement (assembly, matvec "
                          "and recovery not included)" % (n_done, "a %d-element mesh of the same elements and physics"
                                                          % n_sample if "cpu" in wl else "the same workload", secs)}
+
+    oracle_check = None
+    if check_ids is not None:
+        # per-element S^K of both forms against the oracle's condensation of the same elements (untimed)
+        t_el = H.hdg_query_sizes(h)["t"]
+        ts = np.full(m.n_elem, t_el, dtype=np.int64)
+        offs = np.arange(m.n_elem + 1, dtype=np.int64) * t_el * t_el
+
+        def hex_prec(prec):
+            set_prec(prec)
+            tn = tuning.get("fp64" if prec == H.HDG_PREC_FP64 else "mixed")
+            if tn:
+                H.hdg_set_tuning(h, **{k: v for k, v in tn.items() if k != "fixed"})
+
+        run1 = lambda: H.hdg_linearize_condense(h, U, Q, UH, Us, nu, P.dt, P.a_ii)
+        precs = {"mixed": (mixed_prec, hex_prec, run1)}
+        if not mixed_only:
+            precs["fp64"] = (H.HDG_PREC_FP64, hex_prec, run1)
+        oracle_check = element_block_errors(H, h, torch, check_ids, offs, ts, check_refs, precs)
+        oracle_check = {"what": "relative Frobenius error of the per-element Schur complement S^K against the "
+                                "FP64 CPU oracle's condensation of the same element",
+                        "elements": check_ids, **oracle_check}
+        set_prec(H.HDG_PREC_FP64)
 
     # mixed vs FP64 at tolerance: Newton on the stage equations to ||F||_2 <= 1e-8 (FP64 residual)
     newton = {}
@@ -866,6 +964,9 @@ def run_ours(args, rank, world, local_rank):
         "tuning": tuning,
         "peaks_measured_tflops": peaks,
     }
+    if oracle_check is not None:
+        out["oracle_check"] = oracle_check
+        mixed["block_err_vs_oracle"] = oracle_check["mixed"]["max_rel_err"]
     if cpu is not None:
         out["cpu_baseline"] = cpu
     H.hdg_destroy(h)

@@ -902,7 +902,7 @@ int run_linearize_mixed(hdg_ctx* h, const LinArgs& la) {
         if (h->blocks_mode == 1 && C::D == 3) {
             // volume contraction on tensor cores (3xTF32), face terms added by the SIMT kernel
             using BT = BlkTC<C>;
-            k_blocks_tc<C><<<(unsigned)(ne * BT::NMT), 128, BT::smem_bytes(), st>>>(ba, h->d_status);
+            k_blocks_tc<C><<<(unsigned)(ne * BT::NMT), BT::THREADS, BT::smem_bytes(), st>>>(ba, h->d_status);
             kface<<<(unsigned)(ne * C::M * C::M), BC::TY * BC::TX, sm_blk, st>>>(ba);
         } else if (h->blocks_mode == 2) {
             // volume contraction by FP32 sum factorisation, then the face terms
@@ -1223,15 +1223,22 @@ struct BlkTC {
     static constexpr int K = C::D * C::NQ;
     static constexpr int NTN = (C::NP + 15) / 16 * 16;
     static constexpr int TCOLS = NTN <= 32 ? 32 : NTN <= 64 ? 64 : 128;
+    static constexpr int THREADS = 256;
+    static constexpr int STAGE = 2 * (MT * KC + NTN * KC);                // floats of one stage (hi and lo)
     static_assert(NTN <= 128, "N tile too wide");
-    __host__ __device__ static constexpr int smem_bytes() { return 2 * (MT * KC + NTN * KC) * 4 + 64; }
+    __host__ __device__ static constexpr int smem_bytes() { return 2 * STAGE * 4 + 64; }
 };
 
+// Volume contraction of the mixed form on the tensor cores: Out[(a, b, c)][i] =
+// sum_k G_ab[k][c] dphi[k][i] per element, 3xTF32 with FP32 accumulation in TMEM.
+// 8 warps per (element, 128-row tile); the operand tiles are double-buffered so that
+// the threads generate chunk c + 1 (rows fastest: a quarter warp's 16-byte stores are
+// contiguous) while the tensor cores run chunk c.
 template <class C>
-__global__ void __launch_bounds__(128) k_blocks_tc(BlkArgs<float> A, int32_t* status) {
+__global__ void __launch_bounds__(BlkTC<C>::THREADS) k_blocks_tc(BlkArgs<float> A, int32_t* status) {
     using S = BlkTC<C>;
     constexpr int D = C::D, M = C::M, NP = C::NP, NQ = C::NQ, NFP = C::NFP, NCOEF = C::NCOEF;
-    constexpr int NCB = S::NCB, MR = S::MR, MT = S::MT, KC = S::KC, K = S::K, NTN = S::NTN;
+    constexpr int NCB = S::NCB, MR = S::MR, MT = S::MT, KC = S::KC, K = S::K, NTN = S::NTN, TH = S::THREADS;
     constexpr int GEO = Geo<D>::N;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t bid = blockIdx.x;
@@ -1241,12 +1248,60 @@ __global__ void __launch_bounds__(128) k_blocks_tc(BlkArgs<float> A, int32_t* st
     const DeviceTables& T = A.tab;
     const float* cfe = reinterpret_cast<const float*>(A.vcoef) + (size_t)el * M * M * D * NCOEF * NQ;
     extern __shared__ __align__(1024) unsigned char smraw[];
-    float* Ah = reinterpret_cast<float*>(smraw);
-    float* Bh = Ah + MT * KC;
-    float* Al = Bh + NTN * KC;
-    float* Bl = Al + MT * KC;
+    float* stage0 = reinterpret_cast<float*>(smraw);
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smraw + S::smem_bytes() - 64);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+
+    // operand tiles of the chunk at k0 into stage buffer sb (Ah | Bh | Al | Bl)
+    auto generate = [&](int k0, float* sb) {
+        float* Ah = sb;
+        float* Bh = Ah + MT * KC;
+        float* Al = Bh + NTN * KC;
+        float* Bl = Al + MT * KC;
+        for (int it = tid; it < MT * (KC / 4); it += TH) {
+            const int rl = it % MT, q = it / MT, r = m0 + rl;
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            if (r < MR) {
+                const int ab = r / NCB, c = r - ab * NCB;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int k = k0 + q * 4 + u;
+                    if (k >= K) continue;
+                    const int dir = k / NQ, g = k - dir * NQ;
+                    const float* cc = cfe + ((size_t)ab * D + dir) * NCOEF * NQ + g;
+                    float x;
+                    if (c < NP) {
+                        x = cc[0] * T.fphi[g * NP + c];
+                        for (int r2 = 0; r2 < D; ++r2) x -= cc[(1 + r2) * NQ] * T.fpsi[((size_t)r2 * NQ + g) * NP + c];
+                    } else {
+                        const int c2 = c - NP, f = c2 / NFP, l = c2 - f * NFP;
+                        x = cc[(1 + D + f) * NQ] * T.ftheta[((size_t)f * NQ + g) * NFP + l];
+                    }
+                    v[u] = x;
+                }
+            }
+            const int off = ((rl >> 3) * (KC / 4) + q) * 32 + (rl & 7) * 4;
+            const float4 hi = make_float4(tf32_round(v[0]), tf32_round(v[1]), tf32_round(v[2]), tf32_round(v[3]));
+            *reinterpret_cast<float4*>(Ah + off) = hi;
+            *reinterpret_cast<float4*>(Al + off) = make_float4(tf32_round(v[0] - hi.x), tf32_round(v[1] - hi.y),
+                                                               tf32_round(v[2] - hi.z), tf32_round(v[3] - hi.w));
+        }
+        for (int it = tid; it < NTN * (KC / 4); it += TH) {
+            const int n = it % NTN, q = it / NTN;
+            float v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int k = k0 + q * 4 + u;
+                v[u] = (n < NP && k < K) ? T.fdphi[(size_t)k * NP + n] : 0.f;
+            }
+            const int off = ((n >> 3) * (KC / 4) + q) * 32 + (n & 7) * 4;
+            const float4 hi = make_float4(tf32_round(v[0]), tf32_round(v[1]), tf32_round(v[2]), tf32_round(v[3]));
+            *reinterpret_cast<float4*>(Bh + off) = hi;
+            *reinterpret_cast<float4*>(Bl + off) = make_float4(tf32_round(v[0] - hi.x), tf32_round(v[1] - hi.y),
+                                                               tf32_round(v[2] - hi.z), tf32_round(v[3] - hi.w));
+        }
+        asm volatile("fence.proxy.async.shared::cta;");
+    };
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(tslot)),
@@ -1255,48 +1310,38 @@ __global__ void __launch_bounds__(128) k_blocks_tc(BlkArgs<float> A, int32_t* st
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar)), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(mbar + 1)), "r"(1));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
+    generate(0, stage0);
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = *tslot;
     const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NTN >> 3) << 17) | ((uint32_t)(MT >> 4) << 24);
-    const uint32_t bar = smem_u32(mbar);
-    uint32_t phase = 0;
+    // one barrier per stage buffer: the batch that reads buffer s commits to barrier s, and
+    // is waited for before buffer s is written again, so no barrier runs two phases ahead
+    uint32_t phase = 0u, pending = 0u;                          // bit s: barrier s
     bool ok = true;
-    const int rr = lane >> 2, kq = lane & 3;          // position inside an 8 x 4 core matrix
-    for (int k0 = 0; k0 < K; k0 += KC) {
-        // generated operand: 128 rows x KC, one core matrix (8 rows x 4 k) per warp step
-        for (int core = warp; core < (MT / 8) * (KC / 4); core += 4) {
-            const int r = m0 + (core / (KC / 4)) * 8 + rr, k = k0 + (core % (KC / 4)) * 4 + kq;
-            float v = 0.f;
-            if (r < MR && k < K) {
-                const int ab = r / NCB, c = r - ab * NCB, dir = k / NQ, g = k - dir * NQ;
-                const float* cc = cfe + ((size_t)ab * D + dir) * NCOEF * NQ + g;
-                if (c < NP) {
-                    v = cc[0] * T.fphi[g * NP + c];
-                    for (int r2 = 0; r2 < D; ++r2) v -= cc[(1 + r2) * NQ] * T.fpsi[((size_t)r2 * NQ + g) * NP + c];
-                } else {
-                    const int c2 = c - NP, f = c2 / NFP, l = c2 - f * NFP;
-                    v = cc[(1 + D + f) * NQ] * T.ftheta[((size_t)f * NQ + g) * NFP + l];
-                }
-            }
-            const float hi = tf32_round(v);
-            Ah[core * 32 + lane] = hi;
-            Al[core * 32 + lane] = tf32_round(v - hi);
+    auto wait_stage = [&](int sb) {
+        if (!((pending >> sb) & 1u)) return;
+        const uint32_t bar = smem_u32(mbar + sb), par = (phase >> sb) & 1u;
+        if (!mbar_wait_bounded(bar, par, 1 << 24)) {
+            ok = false;
+            if (tid == 0) atomicOr(status, 4);
+            mbar_wait_bounded(bar, par, 1 << 24);
         }
-        for (int core = warp; core < (NTN / 8) * (KC / 4); core += 4) {
-            const int n = (core / (KC / 4)) * 8 + rr, k = k0 + (core % (KC / 4)) * 4 + kq;
-            const float v = (n < NP && k < K) ? T.fdphi[(size_t)k * NP + n] : 0.f;
-            const float hi = tf32_round(v);
-            Bh[core * 32 + lane] = hi;
-            Bl[core * 32 + lane] = tf32_round(v - hi);
-        }
-        asm volatile("fence.proxy.async.shared::cta;");
-        __syncthreads();
+        phase ^= 1u << sb;
+        pending &= ~(1u << sb);
+    };
+    for (int k0 = 0, ci = 0; k0 < K; k0 += KC, ++ci) {
+        const int sbi = ci & 1;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
+            const float* Ah = stage0 + sbi * S::STAGE;
+            const float* Bh = Ah + MT * KC;
+            const float* Al = Bh + NTN * KC;
+            const float* Bl = Al + MT * KC;
             const int nsteps = (min(KC, K - k0) + 7) / 8;
             for (int s = 0; s < nsteps; ++s) {
                 const uint32_t off = s * 256;
@@ -1313,28 +1358,37 @@ __global__ void __launch_bounds__(128) k_blocks_tc(BlkArgs<float> A, int32_t* st
                 asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
                              :: "r"(tmem), "l"(al), "l"(bh), "r"(idesc));
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(bar));
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(smem_u32(mbar + sbi)));
         }
-        if (!mbar_wait_bounded(bar, phase, 1 << 24)) {
-            ok = false;
-            if (tid == 0) atomicOr(status, 4);
-            mbar_wait_bounded(bar, phase, 1 << 24);
+        pending |= 1u << sbi;
+        if (k0 + KC < K) {
+            wait_stage(sbi ^ 1);                                 // the batch before this one read the other buffer
+            if (__syncthreads_or(ok ? 0 : 1)) {
+                ok = false;
+                break;
+            }
+            generate(k0 + KC, stage0 + (sbi ^ 1) * S::STAGE);
+            __syncthreads();
         }
-        phase ^= 1;
-        __syncthreads();
-        if (!ok) break;
     }
+    wait_stage(0);                                               // every batch completes before the epilogue
+    wait_stage(1);
+    ok = !__syncthreads_or(ok ? 0 : 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok) {
-        const int r = m0 + warp * 32 + lane;
+        // warp w reads lanes 32 (w % 4) .. + 31; warps 4..7 take the second half of the columns
+        const int lg = warp & 3, half = warp >> 2;
+        const int r = m0 + lg * 32 + lane;
         const int ab = r / NCB, c = r - ab * NCB, a = ab / M, b = ab - a * M;
         const double detJ = A.geo[e * GEO];
         double* A11 = A.R.a11 + e * A.R.a11_es;
         float* A12 = A.R.a12 + e * A.R.a12_es;
+        constexpr int HC = ((NTN / 2) + 15) / 16 * 16;
 #pragma unroll 1
-        for (int c0 = 0; c0 < NTN; c0 += 16) {
+        for (int c0 = half * HC; c0 < min(NTN, (half + 1) * HC); c0 += 16) {
             uint32_t v[16];
-            const uint32_t addr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            const uint32_t addr = tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)c0;
             asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
                          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
                            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])

@@ -42,3 +42,14 @@ def test_default_workload_is_the_tetrahedral_mesh():
     assert bench.TET_DRAM_BYTES_PER_ELEMENT > 1e6
     peak, src = bench.hbm_peak_gbs()
     assert peak > 1000 and isinstance(src, str)
+
+
+def test_oracle_check_elements_cover_every_degree():
+    """The bench's oracle check takes the first and last element of every degree of a
+    mixed-degree mesh, and four spread elements (ends included) of a uniform one."""
+    elem_p = np.array([2, 1, 1, 4, 2, 3, 4, 1])
+    ids = bench.oracle_check_elements(elem_p=elem_p)
+    assert ids == [0, 1, 3, 4, 5, 6, 7]
+    assert {int(elem_p[e]) for e in ids} == {1, 2, 3, 4}
+    assert bench.oracle_check_elements(n_elem=4096) == [0, 1365, 2730, 4095]
+    assert bench.oracle_check_elements(n_elem=1) == [0]
