@@ -41,7 +41,10 @@ METRIC = "HDG linearize+condense elements/s & % of FP64/TC peak; mixed vs FP64 a
 # L2); every CTA works on its own element, so traffic scales with the element
 # count of a launch.
 # Keyed by (kernel, d, p, elimination panel width).
-DRAM_BYTES_PER_ELEMENT = {("elim", 3, 2, 16): 16.45e6, ("elim", 3, 2, 8): 30.84e6}
+DRAM_BYTES_PER_ELEMENT = {("elim", 3, 2, 16): 16.45e6, ("elim", 3, 2, 8): 30.84e6,
+                          # FP64 element blocks, sum-factorised: k_blocks_sf (0.377 GB) + the face-term
+                          # pass k_blocks (0.936 GB) on the 512-element 8^3 launch
+                          ("blocks_sf", 3, 2, 0): (0.3775e9 + 0.9359e9) / 512}
 # The persistent tetrahedral kernel k_tet_linearize<double>: 86.5 GB (read + write) in one
 # ncu-captured launch over the 3,600 elements of the 10 x 20 x 3 mesh, whose degree mix and
 # curved fraction come from the same seeded generator as the 100,800-element mesh; the
@@ -914,7 +917,10 @@ def run_ours(args, rank, world, local_rank):
         kern["schur"]["bf16_tflops_executed"] = fl["schur_bf16"] * E / (prof["schur"][0] / args.steps) / 1e9
         kern["schur"]["bf16_frac_of_probe"] = kern["schur"]["bf16_tflops_executed"] / peaks["bf16_tcgen05"]
     dom = max(("elim", "blocks"), key=lambda k: prof[k][0])
-    traffic_key = (dom, m.dim, P.p, nb_used if dom == "elim" and not oz else 0)
+    sf64 = t64.get("blocks64_mode", 1) == 1
+    dom_name = dom + ("_sf" if dom == "blocks" and sf64 else "")
+    traffic_key = (dom_name, m.dim, P.p, nb_used if dom == "elim" and not oz else 0)
+    dom_kernels = {"elim": "k_elim", "blocks_sf": "k_blocks_sf + k_blocks (face terms)", "blocks": "k_blocks"}
     avg_launch_ms = prof[dom][0] / max(prof[dom][1], 1)
     per_launch_elems = E / max(prof[dom][1] / args.steps, 1)
     achieved = fl[dom] * per_launch_elems / (avg_launch_ms * 1e-3) / 1e12
@@ -942,12 +948,12 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": args.workload, "elements_per_gpu": E, "degree": P.p, "dim": m.dim,
                    "faces": H.hdg_query_sizes(h)["n_faces"], "parallelism": "replicas" if world > 1 else "single",
                    "precision": "fp64", "l2": "flushed between timed steps (256 MiB write)"},
-        "roofline": {"bound": "alu", "kernel": "k_" + dom, "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "alu", "kernel": dom_kernels[dom_name], "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak,
                      "traffic": (DRAM_BYTES_PER_ELEMENT[traffic_key] * per_launch_elems
                                  if traffic_key in DRAM_BYTES_PER_ELEMENT else None),
-                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one k_%s launch on the "
-                                       "8^3 case, per element, times the elements of one launch" % dom,
+                     "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one %s launch on the "
+                                       "8^3 case, per element, times the elements of one launch" % dom_kernels[dom_name],
                      "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz (derived); cuBLAS DGEMM "
                                     "measured in this run: %.3f TFLOP/s" % (smmax, dgemm),
                      "peak_measured": peaks["fp64_fma"], "frac_of_measured": achieved / peaks["fp64_fma"],

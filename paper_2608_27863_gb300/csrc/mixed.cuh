@@ -1218,7 +1218,7 @@ template <class C>
 struct BlkTC {
     static constexpr int NCB = C::NP + C::NF * C::NFP;
     static constexpr int MR = C::M * C::M * NCB;
-    static constexpr int MT = 128, KC = 32;
+    static constexpr int MT = 128, KC = 16;   // 16-wide chunks keep 4-5 CTAs (32-40 warps) per SM
     static constexpr int NMT = (MR + MT - 1) / MT;
     static constexpr int K = C::D * C::NQ;
     static constexpr int NTN = (C::NP + 15) / 16 * 16;

@@ -233,11 +233,291 @@ __device__ void load_geometry(const KArgs& A, const TetElem& d, double* gv, doub
     }
 }
 
+// ---------------------------------------------------------------------------
+// Mixed form: the contraction A2 on the tensor cores.
+//
+// The column operand of a component pair, T_ab[k][c] = sum_j s_j o_ab[k][j]
+// B_j[k][c], is linear in the point coefficients o_ab, so the element rows
+// C_ab[i][c] = sum_k R[k][i] T_ab[k][c] are also the product
+//   C[(ab, i)][c] = sum_{(j, k)} (s_j R[k][i] o_ab[k][j]) B[(j, k)][c]
+// whose column operand B is the same for all 25 pairs: the pairs stack along M
+// (25 Np rows) and B is formed once per chunk for all of them.  At a volume
+// point g the three directions of R (dphi_r[g][i]) fold into the row operand
+// too, since B depends on g only: 4 Nq terms (j = basis, psi/chi 1..3), then
+// 5 terms per face point (basis, face trace basis, psi/chi 1..3).  The trace
+// rows of face f are the same product with R = mu_f and the trace-row
+// coefficients over the points of f.  The products are 3xTF32 (hi hi + hi lo +
+// lo hi) accumulated in FP32 in tensor memory; 8 warps form the operands of
+// chunk c + 1 while the tensor cores run chunk c.
+constexpr int TKC = 16;                       // K per staged chunk
+constexpr int TMT = 128;                      // rows per tile (tensor-memory lanes)
+constexpr int TNP = 96;                       // columns: Nc <= 95, padded to a multiple of 16
+constexpr int TSTAGE = 2 * (TMT + TNP) * TKC; // floats per stage: A hi | B hi | A lo | B lo
+constexpr int TTCOLS = 128;                   // tensor-memory columns per CTA
+static_assert(2 * TSTAGE * (int)sizeof(float) <= (S_GEMM > S_ELIM ? S_GEMM : S_ELIM) * (int)sizeof(double),
+              "two operand stages fit the phase scratch");
+static_assert((S_DYN * sizeof(double)) % 16 == 0, "operand stages 16-byte aligned");
+
+struct TcState {        // per CTA, kept over the elements of the persistent loop
+    uint32_t tmem;      // accumulator (TTCOLS columns)
+    uint32_t bar;       // shared address of two mbarriers, one per operand stage
+    uint32_t phase;     // bit s: parity of the next phase of barrier s
+};
+
+// four consecutive K entries of one operand row, TF32 hi and lo parts, at the
+// row's position in the K-major core-matrix layout (8 rows x 16 bytes)
+__device__ __forceinline__ void tc_put4(float* hi, float* lo, int row, int kq, const float v[4]) {
+    const int off = ((row >> 3) * (TKC / 4) + kq) * 32 + (row & 7) * 4;
+    const float4 h = make_float4(tf32_round(v[0]), tf32_round(v[1]), tf32_round(v[2]), tf32_round(v[3]));
+    *reinterpret_cast<float4*>(hi + off) = h;
+    *reinterpret_cast<float4*>(lo + off) =
+        make_float4(tf32_round(v[0] - h.x), tf32_round(v[1] - h.y), tf32_round(v[2] - h.z), tf32_round(v[3] - h.w));
+}
+
+// one segment of the stacked product: the element rows (f = -1) or the trace
+// rows of face f.  Its K runs over blocks of one j each (volume j = 0..3 over
+// the Nq points, then face j = 0..4 over the sum_f Nfq face points; trace rows:
+// j = 0..4 over the Nfq points of face f), every block padded to whole chunks
+// so that a chunk has one j and consecutive points.
+struct TcSeg {
+    int f, rows, rdiv;      // rdiv: rows per pair (Np, or Nfp of face f)
+    int cv, cf, nch;        // chunks per volume block, per face block; chunks in all
+};
+
+struct TcChunk {
+    bool vol;
+    int j, p0, np;          // points p0 .. np - 1 of the block (face points: index into sum_f Nfq)
+};
+
+__device__ __forceinline__ TcChunk tc_chunk(const TetElem& d, const TcSeg& sg, int ci) {
+    TcChunk k;
+    if (sg.f < 0 && ci < 4 * sg.cv) {
+        k.vol = true; k.j = ci / sg.cv; k.p0 = (ci - k.j * sg.cv) * TKC; k.np = d.Nq;
+        return k;
+    }
+    const int c2 = sg.f < 0 ? ci - 4 * sg.cv : ci;
+    k.vol = false; k.j = c2 / sg.cf;
+    const int base = sg.f < 0 ? 0 : d.soff[sg.f];
+    k.p0 = base + (c2 - k.j * sg.cf) * TKC;
+    k.np = base + (sg.f < 0 ? d.sfq : d.nfq[sg.f]);
+    return k;
+}
+
+// B[(j, p)][c]
+__device__ __forceinline__ float tc_bval(const TetElem& d, const float* tabJ, const float* vq, const int* fpo,
+                                         const TcChunk& k, int p, int c) {
+    const int Np = d.Np;
+    if (k.vol) {
+        if (k.j == 0) return c < Np ? tabJ[d.vtab + (size_t)p * Np + c] : 0.f;
+        return vq[((size_t)(k.j - 1) * NPT + p) * NCM + c];
+    }
+    if (k.j == 0) return c < Np ? basis_row_t(tabJ, d, d.Nq + p)[c] : 0.f;
+    if (k.j == 1) {
+        const int f = face_of_point(d, p), l = c - Np - fpo[f];
+        return (l >= 0 && l < d.nfp[f]) ? tabJ[d.ttab[f] + (size_t)(p - d.soff[f]) * d.nfp[f] + l] : 0.f;
+    }
+    return vq[((size_t)(k.j - 2) * NPT + d.Nq + p) * NCM + c];
+}
+
+// the row of the tile this thread forms: (pair, i), fixed over the chunks of a tile
+struct TcRow {
+    bool live;
+    int i, cvo, cfo;        // basis index; coefficient offsets of the pair in cv and in cf / cb
+};
+
+// operands of chunk k of the row tile at m0 into stage sb (A hi | B hi | A lo | B lo);
+// thread tid forms row tid % 128 for the K quads tid / 128 and tid / 128 + 2, and
+// column operand entries tid and tid + 256
+__device__ void tc_form(const TetElem& d, const TcSeg& sg, const TcRow& rw, const TcChunk& k, int ncp,
+                        const float* tabJ, const float* cv, const float* cfb, const float* vq, const int* fpo,
+                        float* sb) {
+    const int tid = threadIdx.x, Np = d.Np, Nq = d.Nq;
+    float* Ah = sb;
+    float* Bh = Ah + TMT * TKC;
+    float* Al = Bh + TNP * TKC;
+    float* Bl = Al + TMT * TKC;
+    const int rl = tid & (TMT - 1);
+    const float sgn = k.vol ? (k.j > 0 ? -1.f : 1.f) : (k.j > 1 ? -1.f : 1.f);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int q = (tid >> 7) + 2 * h;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (rw.live) {
+            if (k.vol) {
+                const float* dphi = tabJ + d.vtab + (size_t)Nq * Np + rw.i;
+                const float* o = cv + rw.cvo + k.j;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int p = k.p0 + 4 * q + u;
+                    if (p < k.np) {
+                        const float* op = o + (size_t)p * 300;
+                        float x = dphi[(size_t)p * Np] * op[0];
+                        x = fmaf(dphi[((size_t)Nq + p) * Np], op[M * 4], x);
+                        x = fmaf(dphi[((size_t)2 * Nq + p) * Np], op[2 * M * 4], x);
+                        v[u] = sgn * x;
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int p = k.p0 + 4 * q + u;
+                    if (p < k.np) {
+                        const float r = sg.f < 0
+                                            ? basis_row_t(tabJ, d, Nq + p)[rw.i]
+                                            : tabJ[d.ttab[sg.f] + (size_t)(p - d.soff[sg.f]) * sg.rdiv + rw.i];
+                        v[u] = sgn * r * cfb[(size_t)p * 125 + rw.cfo + k.j];
+                    }
+                }
+            }
+        }
+        tc_put4(Ah, Al, rl, q, v);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int it = tid + h * NTH;
+        if (it < ncp * (TKC / 4)) {
+            const int n = it % ncp, q = it / ncp;
+            float v[4] = {0.f, 0.f, 0.f, 0.f};
+            if (n < Np + d.t / M) {
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int p = k.p0 + 4 * q + u;
+                    if (p < k.np) v[u] = tc_bval(d, tabJ, vq, fpo, k, p, n);
+                }
+            }
+            tc_put4(Bh, Bl, n, q, v);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+}
+
+// wait for the batch committed to stage sb (if any); on a timeout the status
+// records it and the tile's results are not stored
+__device__ __forceinline__ void tc_wait(TcState& ts, uint32_t& pending, int sb, bool& ok, int* sflag) {
+    if (!((pending >> sb) & 1u)) return;
+    const uint32_t bar = ts.bar + 8u * sb, par = (ts.phase >> sb) & 1u;
+    if (!mbar_wait_bounded(bar, par, 1 << 24)) {
+        ok = false;
+        if (threadIdx.x == 0) atomicOr(sflag, 4);
+        mbar_wait_bounded(bar, par, 1 << 24);
+    }
+    ts.phase ^= 1u << sb;
+    pending &= ~(1u << sb);
+}
+
+// the whole contraction of one element (element rows, then the trace rows of
+// each face) into the bordered matrix Mx, FP64 storage
+__device__ void contract_tc(const TetElem& d, const float* tabJ, const float* cv, const float* cf, const float* cb,
+                            const float* vq, const int* fpo, double* Mx, float* st0, TcState& ts, int* sflag) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int Np = d.Np, LD = d.LD, NU = d.NU, Nc = Np + d.t / M;
+    const int ncp = (Nc + 15) / 16 * 16;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(ncp >> 3) << 17) |
+                           ((uint32_t)(TMT >> 4) << 24);
+    for (int sgi = -1; sgi < 4; ++sgi) {
+        TcSeg sg;
+        sg.f = sgi;
+        sg.rdiv = sgi < 0 ? Np : d.nfp[sgi];
+        sg.rows = M * M * sg.rdiv;
+        sg.cv = (d.Nq + TKC - 1) / TKC;
+        sg.cf = ((sgi < 0 ? d.sfq : d.nfq[sgi]) + TKC - 1) / TKC;
+        sg.nch = (sgi < 0 ? 4 * sg.cv : 0) + 5 * sg.cf;
+        const float* cfb = sgi < 0 ? cf : cb;
+        for (int m0 = 0; m0 < sg.rows; m0 += TMT) {
+            uint32_t pending = 0;
+            bool ok = true;
+            TcRow rw;
+            {
+                const int r = m0 + (tid & (TMT - 1));
+                const int ab = r / sg.rdiv, a = ab / M, b = ab - a * M;
+                rw.live = r < sg.rows;
+                rw.i = r - ab * sg.rdiv;
+                rw.cvo = (a * 3 * M + b) * 4;
+                rw.cfo = (a * M + b) * 5;
+            }
+            tc_form(d, sg, rw, tc_chunk(d, sg, 0), ncp, tabJ, cv, cfb, vq, fpo, st0);
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            for (int ci = 0; ci < sg.nch; ++ci) {
+                const int sbi = ci & 1;
+                if (tid == 0) {
+                    const float* Ah = st0 + sbi * TSTAGE;
+                    const float* Bh = Ah + TMT * TKC;
+                    const float* Al = Bh + TNP * TKC;
+                    const float* Bl = Al + TMT * TKC;
+                    for (int s = 0; s < TKC / 8; ++s) {
+                        const uint32_t off = s * 256;
+                        const uint64_t ah = umma_desc(smem_u32(Ah) + off, 128, (TKC / 4) * 128);
+                        const uint64_t bh = umma_desc(smem_u32(Bh) + off, 128, (TKC / 4) * 128);
+                        const uint64_t al = umma_desc(smem_u32(Al) + off, 128, (TKC / 4) * 128);
+                        const uint64_t bl = umma_desc(smem_u32(Bl) + off, 128, (TKC / 4) * 128);
+                        const uint32_t acc = (ci > 0 || s > 0) ? 1u : 0u;
+                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                                     :: "r"(ts.tmem), "l"(ah), "l"(bh), "r"(idesc), "r"(acc));
+                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
+                                     :: "r"(ts.tmem), "l"(ah), "l"(bl), "r"(idesc));
+                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
+                                     :: "r"(ts.tmem), "l"(al), "l"(bh), "r"(idesc));
+                    }
+                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                                 :: "r"(ts.bar + 8u * sbi));
+                }
+                pending |= 1u << sbi;
+                if (ci + 1 < sg.nch) {
+                    tc_wait(ts, pending, sbi ^ 1, ok, sflag);       // the previous batch read the other stage
+                    if (__syncthreads_or(ok ? 0 : 1)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_form(d, sg, rw, tc_chunk(d, sg, ci + 1), ncp, tabJ, cv, cfb, vq, fpo,
+                            st0 + (sbi ^ 1) * TSTAGE);
+                    asm volatile("tcgen05.fence::before_thread_sync;");
+                    __syncthreads();
+                    asm volatile("tcgen05.fence::after_thread_sync;");
+                }
+            }
+            tc_wait(ts, pending, 0, ok, sflag);
+            tc_wait(ts, pending, 1, ok, sflag);
+            ok = !__syncthreads_or(ok ? 0 : 1);
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (ok) {
+                // warp w reads lanes 32 (w % 4) .. + 31; warps 4..7 take the second half of the columns
+                const int lg = warp & 3, half = warp >> 2;
+                const int r = m0 + lg * 32 + lane;
+                const int ab = r / sg.rdiv, i = r - ab * sg.rdiv, a = ab / M, b = ab - a * M;
+                const int64_t row = sgi < 0 ? (int64_t)a * Np + i : (int64_t)NU + d.toff[sgi] + a * sg.rdiv + i;
+                const int hc = ((ncp / 2) + 15) / 16 * 16;
+                for (int c0 = half * hc; c0 < min(ncp, (half + 1) * hc); c0 += 16) {
+                    uint32_t v[16];
+                    const uint32_t addr = ts.tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)c0;
+                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                                   "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                                   "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                                 : "r"(addr));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+                    if (r < sg.rows) {
+#pragma unroll
+                        for (int jj = 0; jj < 16; ++jj) {
+                            const int c = c0 + jj;
+                            if (c < Nc) Mx[row * LD + bcol(d, b, c)] = (double)__uint_as_float(v[jj]);
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+        }
+    }
+}
+
 // TJ: type of the Jacobian coefficients, the column variations and the
 // contraction (double: FP64 form; float: mixed form).  Pointwise terms, lifting
 // operators, mass term, right-hand side and the elimination are FP64 in both.
 template <class TJ, int NBE>
-__device__ void process_element(const KArgs& A, const TetElem& d, double* W, double* sm, int* sflag) {
+__device__ void process_element(const KArgs& A, const TetElem& d, double* W, double* sm, int* sflag, TcState* ts) {
     const int tid = threadIdx.x;
     const int Np = d.Np, Nq = d.Nq, NU = d.NU, t = d.t, LD = d.LD, sfq = d.sfq;
     const int sfp = t / M, Nc = Np + sfp, npt = Nq + sfq;
@@ -525,129 +805,135 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
         }
     }
     __syncthreads();
-    // A2: contraction into the bordered matrix, one (a, b) component pair at a time
-    TJ* sR = reinterpret_cast<TJ*>(sD);  // [KC][SRP] row basis
-    TJ* sT = sR + KC * SRP;              // [KC][STP] column variations times coefficients
-    const TJ* dphiJ = tabJ + d.vtab + (size_t)Nq * Np;
-    const TJ* phiJ = tabJ + d.vtab;
-    const int nrt = (Np + 3) / 4, nct = (Nc + 3) / 4;
-    const int ti = tid / nct, tc = tid - ti * nct;
-    const bool act = tid < nrt * nct;
-    const int K1 = 3 * Nq + sfq;         // element rows: volume (g, r) then face points
-    for (int ab = 0; ab < M * M; ++ab) {
-        const int a = ab / M, b = ab - a * M;
-        TJ acc[4][4] = {};
-        for (int k0 = 0; k0 < K1; k0 += KC) {
-            const int kc = min(KC, K1 - k0);
-            // operands of the chunk; four entries per thread per pass, their loads
-            // issued before any store so that they are in flight together
-            for (int base = tid; base < kc * SRP; base += 4 * NTH) {
-                TJ vv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int idx = base + u * NTH;
-                    const int kk = idx / SRP, i = idx - kk * SRP, K = k0 + kk;
-                    TJ v = 0;
-                    if (idx < kc * SRP && i < Np) {
-                        if (K < 3 * Nq) v = dphiJ[((size_t)(K % 3) * Nq + K / 3) * Np + i];
-                        else v = basis_row_t(tabJ, d, Nq + K - 3 * Nq)[i];
+    if constexpr (sizeof(TJ) == sizeof(float)) {
+        // A2 on the tensor cores (pairs stacked, coefficients folded into the row operand)
+        contract_tc(d, tabJ, cv, cf, cb, vq, fpo, Mx, reinterpret_cast<float*>(sD), *ts, sflag);
+        __syncthreads();
+    } else {
+        // A2: contraction into the bordered matrix, one (a, b) component pair at a time
+        TJ* sR = reinterpret_cast<TJ*>(sD);  // [KC][SRP] row basis
+        TJ* sT = sR + KC * SRP;              // [KC][STP] column variations times coefficients
+        const TJ* dphiJ = tabJ + d.vtab + (size_t)Nq * Np;
+        const TJ* phiJ = tabJ + d.vtab;
+        const int nrt = (Np + 3) / 4, nct = (Nc + 3) / 4;
+        const int ti = tid / nct, tc = tid - ti * nct;
+        const bool act = tid < nrt * nct;
+        const int K1 = 3 * Nq + sfq;         // element rows: volume (g, r) then face points
+        for (int ab = 0; ab < M * M; ++ab) {
+            const int a = ab / M, b = ab - a * M;
+            TJ acc[4][4] = {};
+            for (int k0 = 0; k0 < K1; k0 += KC) {
+                const int kc = min(KC, K1 - k0);
+                // operands of the chunk; four entries per thread per pass, their loads
+                // issued before any store so that they are in flight together
+                for (int base = tid; base < kc * SRP; base += 4 * NTH) {
+                    TJ vv[4];
+    #pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int idx = base + u * NTH;
+                        const int kk = idx / SRP, i = idx - kk * SRP, K = k0 + kk;
+                        TJ v = 0;
+                        if (idx < kc * SRP && i < Np) {
+                            if (K < 3 * Nq) v = dphiJ[((size_t)(K % 3) * Nq + K / 3) * Np + i];
+                            else v = basis_row_t(tabJ, d, Nq + K - 3 * Nq)[i];
+                        }
+                        vv[u] = v;
                     }
-                    vv[u] = v;
+    #pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (base + u * NTH < kc * SRP) sR[base + u * NTH] = vv[u];
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (base + u * NTH < kc * SRP) sR[base + u * NTH] = vv[u];
-            }
-            for (int base = tid; base < kc * STP; base += 4 * NTH) {
-                TJ vv[4];
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int idx = base + u * NTH;
-                    const int kk = idx / STP, c = idx - kk * STP, K = k0 + kk;
-                    TJ v = 0;
-                    if (idx < kc * STP && c < Nc) {
-                        if (K < 3 * Nq) {
-                            const int g = K / 3, r = K - 3 * g;
-                            const TJ* o = cv + (size_t)g * 300 + ((a * 3 + r) * M + b) * 4;
-                            if (c < Np) v = o[0] * phiJ[(size_t)g * Np + c];
-                            for (int l = 0; l < 3; ++l) v -= o[1 + l] * vq[((size_t)l * NPT + g) * NCM + c];
-                        } else {
-                            const int rr = K - 3 * Nq, x = Nq + rr;
-                            const TJ* o = cf + (size_t)rr * 125 + (a * M + b) * 5;
-                            if (c < Np) {
-                                v = o[0] * basis_row_t(tabJ, d, x)[c];
+                for (int base = tid; base < kc * STP; base += 4 * NTH) {
+                    TJ vv[4];
+    #pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int idx = base + u * NTH;
+                        const int kk = idx / STP, c = idx - kk * STP, K = k0 + kk;
+                        TJ v = 0;
+                        if (idx < kc * STP && c < Nc) {
+                            if (K < 3 * Nq) {
+                                const int g = K / 3, r = K - 3 * g;
+                                const TJ* o = cv + (size_t)g * 300 + ((a * 3 + r) * M + b) * 4;
+                                if (c < Np) v = o[0] * phiJ[(size_t)g * Np + c];
+                                for (int l = 0; l < 3; ++l) v -= o[1 + l] * vq[((size_t)l * NPT + g) * NCM + c];
                             } else {
-                                const int f = face_of_point(d, rr);
-                                const int l = c - Np - fpo[f];
-                                if (l >= 0 && l < d.nfp[f])
-                                    v = o[1] * tabJ[d.ttab[f] + (size_t)(rr - d.soff[f]) * d.nfp[f] + l];
+                                const int rr = K - 3 * Nq, x = Nq + rr;
+                                const TJ* o = cf + (size_t)rr * 125 + (a * M + b) * 5;
+                                if (c < Np) {
+                                    v = o[0] * basis_row_t(tabJ, d, x)[c];
+                                } else {
+                                    const int f = face_of_point(d, rr);
+                                    const int l = c - Np - fpo[f];
+                                    if (l >= 0 && l < d.nfp[f])
+                                        v = o[1] * tabJ[d.ttab[f] + (size_t)(rr - d.soff[f]) * d.nfp[f] + l];
+                                }
+                                for (int l = 0; l < 3; ++l) v -= o[2 + l] * vq[((size_t)l * NPT + x) * NCM + c];
                             }
-                            for (int l = 0; l < 3; ++l) v -= o[2 + l] * vq[((size_t)l * NPT + x) * NCM + c];
+                        }
+                        vv[u] = v;
+                    }
+    #pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (base + u * NTH < kc * STP) sT[base + u * NTH] = vv[u];
+                }
+                __syncthreads();
+                if (act) gemm_chunk(sR, sT, kc, ti, tc, acc);
+                __syncthreads();
+            }
+            if (act)
+                for (int u = 0; u < 4; ++u) {
+                    const int i = 4 * ti + u;
+                    if (i >= Np) continue;
+                    for (int v = 0; v < 4; ++v) {
+                        const int c = 4 * tc + v;
+                        if (c >= Nc) continue;
+                        Mx[(size_t)(a * Np + i) * LD + bcol(d, b, c)] = (double)acc[u][v];   // mass term added below
+                    }
+                }
+            // trace rows (f', a, l'): K = the points of face f'
+            for (int f2 = 0; f2 < 4; ++f2) {
+                const int nfq = d.nfq[f2], nfp = d.nfp[f2];
+                const TJ* mu = tabJ + d.ttab[f2];
+                for (int idx = tid; idx < nfq * SRP; idx += NTH) {
+                    const int kk = idx / SRP, l = idx - kk * SRP;
+                    sR[idx] = l < nfp ? mu[(size_t)kk * nfp + l] : TJ(0);
+                }
+                for (int idx = tid; idx < nfq * STP; idx += NTH) {
+                    const int kk = idx / STP, c = idx - kk * STP, rr = d.soff[f2] + kk, x = Nq + rr;
+                    TJ v = 0;
+                    if (c < Nc) {
+                        const TJ* o = cb + (size_t)rr * 125 + (a * M + b) * 5;
+                        if (c < Np) {
+                            v = o[0] * basis_row_t(tabJ, d, x)[c];
+                        } else {
+                            const int l = c - Np - fpo[f2];
+                            if (l >= 0 && l < nfp) v = o[1] * mu[(size_t)kk * nfp + l];
+                        }
+                        for (int l = 0; l < 3; ++l) v -= o[2 + l] * vq[((size_t)l * NPT + x) * NCM + c];
+                    }
+                    sT[idx] = v;
+                }
+                __syncthreads();
+                const int nrt2 = (nfp + 3) / 4;
+                const int ti2 = tid / nct, tc2 = tid - ti2 * nct;
+                if (tid < nrt2 * nct) {
+                    TJ acc2[4][4] = {};
+                    gemm_chunk(sR, sT, nfq, ti2, tc2, acc2);
+                    for (int u = 0; u < 4; ++u) {
+                        const int l = 4 * ti2 + u;
+                        if (l >= nfp) continue;
+                        for (int v = 0; v < 4; ++v) {
+                            const int c = 4 * tc2 + v;
+                            if (c >= Nc) continue;
+                            Mx[(size_t)(NU + d.toff[f2] + a * nfp + l) * LD + bcol(d, b, c)] = (double)acc2[u][v];
                         }
                     }
-                    vv[u] = v;
                 }
-#pragma unroll
-                for (int u = 0; u < 4; ++u)
-                    if (base + u * NTH < kc * STP) sT[base + u * NTH] = vv[u];
+                __syncthreads();
             }
-            __syncthreads();
-            if (act) gemm_chunk(sR, sT, kc, ti, tc, acc);
-            __syncthreads();
         }
-        if (act)
-            for (int u = 0; u < 4; ++u) {
-                const int i = 4 * ti + u;
-                if (i >= Np) continue;
-                for (int v = 0; v < 4; ++v) {
-                    const int c = 4 * tc + v;
-                    if (c >= Nc) continue;
-                    Mx[(size_t)(a * Np + i) * LD + bcol(d, b, c)] = (double)acc[u][v];   // mass term added below
-                }
-            }
-        // trace rows (f', a, l'): K = the points of face f'
-        for (int f2 = 0; f2 < 4; ++f2) {
-            const int nfq = d.nfq[f2], nfp = d.nfp[f2];
-            const TJ* mu = tabJ + d.ttab[f2];
-            for (int idx = tid; idx < nfq * SRP; idx += NTH) {
-                const int kk = idx / SRP, l = idx - kk * SRP;
-                sR[idx] = l < nfp ? mu[(size_t)kk * nfp + l] : TJ(0);
-            }
-            for (int idx = tid; idx < nfq * STP; idx += NTH) {
-                const int kk = idx / STP, c = idx - kk * STP, rr = d.soff[f2] + kk, x = Nq + rr;
-                TJ v = 0;
-                if (c < Nc) {
-                    const TJ* o = cb + (size_t)rr * 125 + (a * M + b) * 5;
-                    if (c < Np) {
-                        v = o[0] * basis_row_t(tabJ, d, x)[c];
-                    } else {
-                        const int l = c - Np - fpo[f2];
-                        if (l >= 0 && l < nfp) v = o[1] * mu[(size_t)kk * nfp + l];
-                    }
-                    for (int l = 0; l < 3; ++l) v -= o[2 + l] * vq[((size_t)l * NPT + x) * NCM + c];
-                }
-                sT[idx] = v;
-            }
-            __syncthreads();
-            const int nrt2 = (nfp + 3) / 4;
-            const int ti2 = tid / nct, tc2 = tid - ti2 * nct;
-            if (tid < nrt2 * nct) {
-                TJ acc2[4][4] = {};
-                gemm_chunk(sR, sT, nfq, ti2, tc2, acc2);
-                for (int u = 0; u < 4; ++u) {
-                    const int l = 4 * ti2 + u;
-                    if (l >= nfp) continue;
-                    for (int v = 0; v < 4; ++v) {
-                        const int c = 4 * tc2 + v;
-                        if (c >= Nc) continue;
-                        Mx[(size_t)(NU + d.toff[f2] + a * nfp + l) * LD + bcol(d, b, c)] = (double)acc2[u][v];
-                    }
-                }
-            }
-            __syncthreads();
-        }
+        __syncthreads();
     }
-    __syncthreads();
     // mass term (1/a_ii) M_ij on the diagonal component blocks: M = L L^T from the factor
     for (int idx = tid; idx < Np * Np; idx += NTH) {
         const int i = idx / Np, j = idx - i * Np;
@@ -700,9 +986,30 @@ __global__ void __launch_bounds__(NTH, 2) k_tet_linearize(KArgs A) {
     extern __shared__ double sm[];
     __shared__ TetElem d;
     __shared__ int s_idx, sflag;
+    __shared__ __align__(8) uint64_t tbar[2];
+    __shared__ uint32_t tslot;
     const int tid = threadIdx.x;
     double* W = A.work + (int64_t)blockIdx.x * A.wstride;
     if (tid == 0) sflag = 0;
+    TcState ts{0u, 0u, 0u};
+    if constexpr (sizeof(TJ) == sizeof(float)) {
+        // tensor memory and the two stage barriers of the contraction, held for the whole launch
+        if ((tid >> 5) == 0) {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&tslot)),
+                         "r"(TTCOLS));
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        }
+        if (tid == 0) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&tbar[0])), "r"(1));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(&tbar[1])), "r"(1));
+            asm volatile("fence.mbarrier_init.release.cluster;");
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        ts.tmem = tslot;
+        ts.bar = smem_u32(&tbar[0]);
+    }
     for (;;) {
         if (tid == 0) s_idx = atomicAdd(A.next, 1);
         __syncthreads();
@@ -713,8 +1020,14 @@ __global__ void __launch_bounds__(NTH, 2) k_tet_linearize(KArgs A) {
         for (int i = tid; i < NW; i += NTH)
             reinterpret_cast<int64_t*>(&d)[i] = reinterpret_cast<const int64_t*>(A.el + e)[i];
         __syncthreads();
-        process_element<TJ, NBE>(A, d, W, sm, &sflag);
+        process_element<TJ, NBE>(A, d, W, sm, &sflag, &ts);
         __syncthreads();
+    }
+    if constexpr (sizeof(TJ) == sizeof(float)) {
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        if ((tid >> 5) == 0)
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(ts.tmem), "r"(TTCOLS));
     }
     if (tid == 0 && sflag) atomicOr(A.status, sflag);
 }
