@@ -361,7 +361,7 @@ def run_tet(args, rank, world, local_rank):
         mixed["newton"] = newton
         H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_FP64)
     if args.dirk and mixed is not None:
-        # one SDIRK3 step, 3 stages x 4 Newton iterations (GMRES(30) each) captured as one CUDA graph,
+        # one SDIRK3 step, 3 stages x n Newton iterations (GMRES(m) each) captured as one CUDA graph,
         # mixed form; the first call captures (after one eager linearization), the second replays
         H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_MIXED)
         H.hdg_set_tuning(h, elim_nb=tuning["mixed"]["elim_nb"])
@@ -369,12 +369,14 @@ def run_tet(args, rank, world, local_rank):
         U2, Q2, UH2 = U.clone(), Q.clone(), UH.clone()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        H.hdg_dirk_step(h, U2, Q2, UH2, None, P.dt, A3, b3, n_newton=4, m=30, use_graph=True)
+        H.hdg_dirk_step(h, U2, Q2, UH2, None, P.dt, A3, b3, n_newton=args.dirk_newton, m=args.dirk_m,
+                        use_graph=True)
         t_first = time.perf_counter() - t0
         t0 = time.perf_counter()
-        hist = H.hdg_dirk_step(h, U2, Q2, UH2, None, P.dt, A3, b3, n_newton=4, m=30, use_graph=True)
+        hist = H.hdg_dirk_step(h, U2, Q2, UH2, None, P.dt, A3, b3, n_newton=args.dirk_newton, m=args.dirk_m,
+                               use_graph=True)
         t_replay = time.perf_counter() - t0
-        mixed["dirk_step"] = {"stages": 3, "newton_per_stage": 4, "gmres_m": 30, "graph": True,
+        mixed["dirk_step"] = {"stages": 3, "newton_per_stage": args.dirk_newton, "gmres_m": args.dirk_m, "graph": True,
                               "seconds_capture_and_run": t_first, "seconds_replay": t_replay,
                               "residual_history": [[float(v) for v in row] for row in hist]}
         H.hdg_set_params(h, tau=P.tau, precision=H.HDG_PREC_FP64)
@@ -1072,6 +1074,8 @@ def main():
     ap.add_argument("--precond", choices=["schwarz", "bj"], default="schwarz",
                     help="tetrahedral workloads: preconditioner of the Newton comparison's GMRES")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--dirk-newton", type=int, default=5, help="Newton iterations per stage of the --dirk step")
+    ap.add_argument("--dirk-m", type=int, default=100, help="GMRES iterations per Newton step of the --dirk step")
     ap.add_argument("--elim-nb", type=int, choices=[8, 16], default=None,
                     help="fix the FP64 elimination panel width instead of autotuning (profiling runs)")
     ap.add_argument("--tuning", default=None,

@@ -92,12 +92,20 @@ template <class T> __device__ __forceinline__ const T* jtab(const KArgs& A);
 template <> __device__ __forceinline__ const double* jtab<double>(const KArgs& A) { return A.tab; }
 template <> __device__ __forceinline__ const float* jtab<float>(const KArgs& A) { return A.tabf; }
 
-// Trace rows of the mixed form, after the FP64 elimination of the top rows
-// (LU of At with pivoting, Z = L^{-1} P Bt, z = L^{-1} P Rt): W = Ct U^{-1} in
-// FP32 (left-looking, one column of U at a time, W kept transposed so that
-// threads over trace rows read consecutive words), S = Dt - W Z in FP32 with
-// 8 x 8 register tiles, and the right-hand side Rh - W z in FP64.
-__device__ void trace_schur_f32(double* Mx, int NU, int t, int LD, float* Wt, float* Zf, float* smf) {
+// Trace rows of the mixed form, after the FP64 LU of the interior block At
+// (partial pivoting, panels of NB columns; the interchanges of a panel are
+// recorded in gpiv and applied only to the columns right of it inside At, so
+// the L of each panel is stored at that panel's row order):
+//  * z = L^{-1} P Rt in FP64 and Z = L^{-1} P Bt in FP32, panel by panel: the
+//    panel's interchanges, then its unit-lower block and the update of the rows
+//    below, one thread per column with the panel's values in registers;
+//  * W = Ct U^{-1} in FP32, panel by panel over the columns of U (W kept
+//    transposed so that threads over trace rows read consecutive words);
+//  * Z back into the bordered matrix (the recovery reads it), the right-hand
+//    side Rh - W z in FP64 and S = Dt - W Z in FP32 with 8 x 8 register tiles.
+template <int NB>
+__device__ void trace_schur_f32(double* Mx, int NU, int t, int LD, const int* gpiv, float* Wt, float* Zf,
+                                float* smf) {
     const int tid = threadIdx.x, NR = NU + t;
     for (int idx = tid; idx < NU * t; idx += NTH) {
         const int i = idx / t, r = idx - i * t;
@@ -105,17 +113,129 @@ __device__ void trace_schur_f32(double* Mx, int NU, int t, int LD, float* Wt, fl
         Zf[idx] = (float)Mx[(size_t)i * LD + NU + r];
     }
     __syncthreads();
-    float* ucol = smf;                                  // [NU] column j of U
-    for (int j = 0; j < NU; ++j) {
-        for (int i = tid; i <= j; i += NTH) ucol[i] = (float)Mx[(size_t)i * LD + j];
-        __syncthreads();
-        const float inv = ucol[j] != 0.0f ? 1.0f / ucol[j] : 1.0f;
-        for (int r = tid; r < t; r += NTH) {
-            float s2 = Wt[(size_t)j * t + r];
-            for (int i = 0; i < j; ++i) s2 = fmaf(-Wt[(size_t)i * t + r], ucol[i], s2);
-            Wt[(size_t)j * t + r] = s2 * inv;
+    // Z = L^{-1} P Bt (FP32, one thread per column) and z = L^{-1} P Rt (FP64:
+    // interchanges and the panel's block by one thread, the rows below by all)
+    float* sL = smf;                                    // [NU - k0][NB] panel of L
+    __shared__ double zp[NB];
+    double* zc = Mx + NR;                               // column NR, stride LD
+    for (int k0 = 0; k0 < NU; k0 += NB) {
+        const int kb = min(NB, NU - k0);
+        for (int idx = tid; idx < (NU - k0) * NB; idx += NTH) {
+            const int i = idx / NB, j = idx - i * NB;
+            sL[idx] = j < kb ? (float)Mx[(size_t)(k0 + i) * LD + k0 + j] : 0.0f;
         }
         __syncthreads();
+        for (int r = tid; r < t; r += NTH) {
+            float* zf = Zf + r;
+            for (int j = 0; j < kb; ++j) {
+                const int pr = gpiv[k0 + j];
+                if (pr != k0 + j) {
+                    const float x = zf[(size_t)(k0 + j) * t];
+                    zf[(size_t)(k0 + j) * t] = zf[(size_t)pr * t];
+                    zf[(size_t)pr * t] = x;
+                }
+            }
+            float zv[NB];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) zv[j] = j < kb ? zf[(size_t)(k0 + j) * t] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < NB; ++j)
+#pragma unroll
+                for (int jj = j + 1; jj < NB; ++jj)
+                    if (jj < kb) zv[jj] = fmaf(-sL[jj * NB + j], zv[j], zv[jj]);
+#pragma unroll
+            for (int j = 0; j < NB; ++j)
+                if (j < kb) zf[(size_t)(k0 + j) * t] = zv[j];
+            // rows below the panel, 8 at a time: their loads are in flight together
+            for (int i0 = k0 + kb; i0 < NU; i0 += 8) {
+                float s2[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s2[u] = zf[(size_t)min(i0 + u, NU - 1) * t];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float* l = sL + (size_t)(min(i0 + u, NU - 1) - k0) * NB;
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) s2[u] = fmaf(-l[j], zv[j], s2[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i0 + u < NU) zf[(size_t)(i0 + u) * t] = s2[u];
+            }
+        }
+        if (tid == NTH - 1) {
+            for (int j = 0; j < kb; ++j) {
+                const int pr = gpiv[k0 + j];
+                if (pr != k0 + j) {
+                    const double x = zc[(size_t)(k0 + j) * LD];
+                    zc[(size_t)(k0 + j) * LD] = zc[(size_t)pr * LD];
+                    zc[(size_t)pr * LD] = x;
+                }
+            }
+            for (int j = 0; j < kb; ++j) {
+                double zj = zc[(size_t)(k0 + j) * LD];
+                for (int i = 0; i < j; ++i) zj -= Mx[(size_t)(k0 + j) * LD + k0 + i] * zp[i];
+                zp[j] = zj;
+                zc[(size_t)(k0 + j) * LD] = zj;
+            }
+        }
+        __syncthreads();
+        for (int i = k0 + kb + tid; i < NU; i += NTH) {
+            double s2 = zc[(size_t)i * LD];
+            for (int j = 0; j < kb; ++j) s2 -= Mx[(size_t)i * LD + k0 + j] * zp[j];
+            zc[(size_t)i * LD] = s2;
+        }
+        __syncthreads();
+    }
+    // W = Ct U^{-1}: W U = Ct, panel by panel over the columns of U
+    float* sUp = smf;                                   // [NB][NU - k0] panel rows of U
+    float* sDi = smf + NB * NU;                         // [NB] reciprocal diagonal
+    for (int k0 = 0; k0 < NU; k0 += NB) {
+        const int kb = min(NB, NU - k0), w = NU - k0;
+        for (int idx = tid; idx < NB * w; idx += NTH) {
+            const int j = idx / w, c = idx - j * w;
+            sUp[idx] = (j < kb && c >= j) ? (float)Mx[(size_t)(k0 + j) * LD + k0 + c] : 0.0f;
+        }
+        if (tid < NB) {
+            const float u = tid < kb ? (float)Mx[(size_t)(k0 + tid) * LD + k0 + tid] : 1.0f;
+            sDi[tid] = u != 0.0f ? 1.0f / u : 1.0f;
+        }
+        __syncthreads();
+        for (int r = tid; r < t; r += NTH) {
+            float* wc = Wt + r;
+            float wv[NB];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) wv[j] = j < kb ? wc[(size_t)(k0 + j) * t] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                if (j >= kb) continue;
+#pragma unroll
+                for (int i = 0; i < j; ++i) wv[j] = fmaf(-wv[i], sUp[i * w + j], wv[j]);
+                wv[j] *= sDi[j];
+            }
+#pragma unroll
+            for (int j = 0; j < NB; ++j)
+                if (j < kb) wc[(size_t)(k0 + j) * t] = wv[j];
+            for (int c0 = kb; c0 < w; c0 += 8) {        // 8 columns at a time, loads in flight together
+                float s2[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s2[u] = wc[(size_t)(k0 + min(c0 + u, w - 1)) * t];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int c = min(c0 + u, w - 1);
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) s2[u] = fmaf(-wv[j], sUp[j * w + c], s2[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (c0 + u < w) wc[(size_t)(k0 + c0 + u) * t] = s2[u];
+            }
+        }
+        __syncthreads();
+    }
+    // Z to the bordered matrix (FP32 values in FP64 storage)
+    for (int idx = tid; idx < NU * t; idx += NTH) {
+        const int i = idx / t, r = idx - i * t;
+        Mx[(size_t)i * LD + NU + r] = (double)Zf[idx];
     }
     // right-hand side of the trace rows: Rh - W z (FP64)
     for (int r = tid; r < t; r += NTH) {
@@ -303,22 +423,6 @@ __device__ __forceinline__ TcChunk tc_chunk(const TetElem& d, const TcSeg& sg, i
     return k;
 }
 
-// B[(j, p)][c]
-__device__ __forceinline__ float tc_bval(const TetElem& d, const float* tabJ, const float* vq, const int* fpo,
-                                         const TcChunk& k, int p, int c) {
-    const int Np = d.Np;
-    if (k.vol) {
-        if (k.j == 0) return c < Np ? tabJ[d.vtab + (size_t)p * Np + c] : 0.f;
-        return vq[((size_t)(k.j - 1) * NPT + p) * NCM + c];
-    }
-    if (k.j == 0) return c < Np ? basis_row_t(tabJ, d, d.Nq + p)[c] : 0.f;
-    if (k.j == 1) {
-        const int f = face_of_point(d, p), l = c - Np - fpo[f];
-        return (l >= 0 && l < d.nfp[f]) ? tabJ[d.ttab[f] + (size_t)(p - d.soff[f]) * d.nfp[f] + l] : 0.f;
-    }
-    return vq[((size_t)(k.j - 2) * NPT + d.Nq + p) * NCM + c];
-}
-
 // the row of the tile this thread forms: (pair, i), fixed over the chunks of a tile
 struct TcRow {
     bool live;
@@ -327,66 +431,109 @@ struct TcRow {
 
 // operands of chunk k of the row tile at m0 into stage sb (A hi | B hi | A lo | B lo);
 // thread tid forms row tid % 128 for the K quads tid / 128 and tid / 128 + 2, and
-// column operand entries tid and tid + 256
+// column operand entries tid and tid + 256.  Every load of a thread's entries
+// goes out before the first is used (indices clamped into range, padding masked
+// afterwards), so that they are in flight together.
 __device__ void tc_form(const TetElem& d, const TcSeg& sg, const TcRow& rw, const TcChunk& k, int ncp,
                         const float* tabJ, const float* cv, const float* cfb, const float* vq, const int* fpo,
                         float* sb) {
-    const int tid = threadIdx.x, Np = d.Np, Nq = d.Nq;
+    const int tid = threadIdx.x, Np = d.Np, Nq = d.Nq, Nc = Np + d.t / M;
     float* Ah = sb;
     float* Bh = Ah + TMT * TKC;
     float* Al = Bh + TNP * TKC;
     float* Bl = Al + TMT * TKC;
     const int rl = tid & (TMT - 1);
     const float sgn = k.vol ? (k.j > 0 ? -1.f : 1.f) : (k.j > 1 ? -1.f : 1.f);
+    float va[2][4], vb[2][4];
+    // row operand
+    if (k.vol) {
+        const float* dphi = tabJ + d.vtab + (size_t)Nq * Np + rw.i;
+        const float* o = cv + rw.cvo + k.j;
+        float g0[2][4], g1[2][4], g2[2][4], c0[2][4], c1[2][4], c2[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = min(k.p0 + 4 * ((tid >> 7) + 2 * h) + u, k.np - 1);
+                g0[h][u] = dphi[(size_t)p * Np];
+                g1[h][u] = dphi[((size_t)Nq + p) * Np];
+                g2[h][u] = dphi[((size_t)2 * Nq + p) * Np];
+                const float* op = o + (size_t)p * 300;
+                c0[h][u] = op[0];
+                c1[h][u] = op[M * 4];
+                c2[h][u] = op[2 * M * 4];
+            }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                va[h][u] = sgn * fmaf(g2[h][u], c2[h][u], fmaf(g1[h][u], c1[h][u], g0[h][u] * c0[h][u]));
+    } else {
+        float rb[2][4], cb4[2][4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int p = min(k.p0 + 4 * ((tid >> 7) + 2 * h) + u, k.np - 1);
+                rb[h][u] = sg.f < 0 ? basis_row_t(tabJ, d, Nq + p)[rw.i]
+                                    : tabJ[d.ttab[sg.f] + (size_t)(p - d.soff[sg.f]) * sg.rdiv + rw.i];
+                cb4[h][u] = cfb[(size_t)p * 125 + rw.cfo + k.j];
+            }
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) va[h][u] = sgn * rb[h][u] * cb4[h][u];
+    }
+    // column operand
+    int nn[2], qq[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int it = min(tid + h * NTH, ncp * (TKC / 4) - 1);
+        nn[h] = it % ncp;
+        qq[h] = it / ncp;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int p = min(k.p0 + 4 * qq[h] + u, k.np - 1), c = min(nn[h], Nc - 1);
+            float x;
+            if (k.vol) {
+                x = k.j == 0 ? tabJ[d.vtab + (size_t)p * Np + min(c, Np - 1)]
+                             : vq[((size_t)(k.j - 1) * NPT + p) * NCM + c];
+            } else if (k.j == 0) {
+                x = basis_row_t(tabJ, d, Nq + p)[min(c, Np - 1)];
+            } else if (k.j == 1) {
+                const int f = face_of_point(d, p), nf = d.nfp[f];
+                const int l = min(max(c - Np - fpo[f], 0), nf - 1);
+                x = tabJ[d.ttab[f] + (size_t)(p - d.soff[f]) * nf + l];
+            } else {
+                x = vq[((size_t)(k.j - 2) * NPT + Nq + p) * NCM + c];
+            }
+            vb[h][u] = x;
+        }
+    }
+    // masks and stores
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const int q = (tid >> 7) + 2 * h;
-        float v[4] = {0.f, 0.f, 0.f, 0.f};
-        if (rw.live) {
-            if (k.vol) {
-                const float* dphi = tabJ + d.vtab + (size_t)Nq * Np + rw.i;
-                const float* o = cv + rw.cvo + k.j;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int p = k.p0 + 4 * q + u;
-                    if (p < k.np) {
-                        const float* op = o + (size_t)p * 300;
-                        float x = dphi[(size_t)p * Np] * op[0];
-                        x = fmaf(dphi[((size_t)Nq + p) * Np], op[M * 4], x);
-                        x = fmaf(dphi[((size_t)2 * Nq + p) * Np], op[2 * M * 4], x);
-                        v[u] = sgn * x;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int p = k.p0 + 4 * q + u;
-                    if (p < k.np) {
-                        const float r = sg.f < 0
-                                            ? basis_row_t(tabJ, d, Nq + p)[rw.i]
-                                            : tabJ[d.ttab[sg.f] + (size_t)(p - d.soff[sg.f]) * sg.rdiv + rw.i];
-                        v[u] = sgn * r * cfb[(size_t)p * 125 + rw.cfo + k.j];
-                    }
-                }
-            }
-        }
-        tc_put4(Ah, Al, rl, q, v);
+        for (int u = 0; u < 4; ++u)
+            if (!rw.live || k.p0 + 4 * q + u >= k.np) va[h][u] = 0.f;
+        tc_put4(Ah, Al, rl, q, va[h]);
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const int it = tid + h * NTH;
-        if (it < ncp * (TKC / 4)) {
-            const int n = it % ncp, q = it / ncp;
-            float v[4] = {0.f, 0.f, 0.f, 0.f};
-            if (n < Np + d.t / M) {
+        if (tid + h * NTH >= ncp * (TKC / 4)) continue;
+        const int n = nn[h], q = qq[h];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    const int p = k.p0 + 4 * q + u;
-                    if (p < k.np) v[u] = tc_bval(d, tabJ, vq, fpo, k, p, n);
-                }
+        for (int u = 0; u < 4; ++u) {
+            bool ok = n < Nc && k.p0 + 4 * q + u < k.np;
+            if (ok && k.j == 0) ok = n < Np;
+            if (ok && !k.vol && k.j == 1) {
+                const int p = k.p0 + 4 * q + u, f = face_of_point(d, p), l = n - Np - fpo[f];
+                ok = l >= 0 && l < d.nfp[f];
             }
-            tc_put4(Bh, Bl, n, q, v);
+            if (!ok) vb[h][u] = 0.f;
         }
+        tc_put4(Bh, Bl, n, q, vb[h]);
     }
     asm volatile("fence.proxy.async.shared::cta;");
 }
@@ -431,9 +578,9 @@ __device__ void contract_tc(const TetElem& d, const float* tabJ, const float* cv
                 const int r = m0 + (tid & (TMT - 1));
                 const int ab = r / sg.rdiv, a = ab / M, b = ab - a * M;
                 rw.live = r < sg.rows;
-                rw.i = r - ab * sg.rdiv;
-                rw.cvo = (a * 3 * M + b) * 4;
-                rw.cfo = (a * M + b) * 5;
+                rw.i = rw.live ? r - ab * sg.rdiv : 0;
+                rw.cvo = rw.live ? (a * 3 * M + b) * 4 : 0;
+                rw.cfo = rw.live ? (a * M + b) * 5 : 0;
             }
             tc_form(d, sg, rw, tc_chunk(d, sg, 0), ncp, tabJ, cv, cfb, vq, fpo, st0);
             asm volatile("tcgen05.fence::before_thread_sync;");
@@ -973,11 +1120,13 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
     if constexpr (sizeof(TJ) == sizeof(double)) {
         bordered_elim<NBE>(Mx, NU, NR, NR + 1, LD, sD, sD + NRMAX * NB, piv, sflag);
     } else {
-        // FP64 LU of At with its right-hand sides (top rows only), then the trace rows in FP32
-        bordered_elim<NBE>(Mx, NU, NU, NR + 1, LD, sD, sD + NRMAX * NB, piv, sflag);
+        // FP64 LU of At (interior columns only, interchanges recorded), then the
+        // right-hand sides and the trace rows in FP32 (z in FP64)
+        __shared__ int gpiv[M * NPMAX];
+        bordered_elim<NBE>(Mx, NU, NU, NU, LD, sD, sD + NRMAX * NB, piv, sflag, gpiv);
         __syncthreads();
-        trace_schur_f32(Mx, NU, t, LD, reinterpret_cast<float*>(W + W_VQ), reinterpret_cast<float*>(W + W_CV),
-                        reinterpret_cast<float*>(sD));
+        trace_schur_f32<NBE>(Mx, NU, t, LD, gpiv, reinterpret_cast<float*>(W + W_VQ),
+                             reinterpret_cast<float*>(W + W_CV), reinterpret_cast<float*>(sD));
     }
 }
 
