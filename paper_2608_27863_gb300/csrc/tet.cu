@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstring>
+#include <type_traits>
 
 #include "kernels.cuh"
 #include "solve.cuh"
@@ -64,7 +65,8 @@ struct KArgs {
     const double* tab; const float* tabf; const double* gvol; const double* gface;
     const double* U; const double* Q; const double* UH; const double* Ustar;
     double* mat; double* rec; double* work; int64_t wstride;
-    PhysT<double> ph; double dt, a_ii, tau; const double* ub; double ew;
+    PhysT<double> ph; PhysT<float> phf;                  // phf: Jacobian terms of the mixed form
+    double dt, a_ii, tau; const double* ub; double ew;
     int tau_mode;                                         // 0 constant tau, 1 state-dependent (stab_tau)
     int32_t* status;
     double* Rq; double* Ru; double* rk; double* part;     // residual evaluation outputs
@@ -86,6 +88,11 @@ __device__ __forceinline__ const T* basis_row_t(const T* tab, const TetElem& d, 
 __device__ __forceinline__ const double* basis_row(const KArgs& A, const TetElem& d, int x) {
     return basis_row_t(A.tab, d, x);
 }
+
+// physical constants in the evaluation type of the Jacobian terms
+template <class S> __device__ __forceinline__ const PhysT<S>& jphys(const KArgs& A);
+template <> __device__ __forceinline__ const PhysT<double>& jphys<double>(const KArgs& A) { return A.ph; }
+template <> __device__ __forceinline__ const PhysT<float>& jphys<float>(const KArgs& A) { return A.phf; }
 
 // tables in the contraction type: FP64, or their FP32 copy in the mixed form
 template <class T> __device__ __forceinline__ const T* jtab(const KArgs& A);
@@ -838,6 +845,7 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
     __syncthreads();
     // A1: fluxes and their Jacobians at the points
     const PhysT<double>& P = A.ph;
+    using SJ = std::conditional_t<sizeof(TJ) == sizeof(float), float, double>;   // Jacobian terms' type
     TJ* cv = reinterpret_cast<TJ*>(W + W_CV);
     TJ* cf = reinterpret_cast<TJ*>(W + W_CF);
     TJ* cb = reinterpret_cast<TJ*>(W + W_CB);
@@ -863,30 +871,65 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
                     for (int k = 0; k < 3; ++k) s += Ji[r * 3 + k] * (Fc[a][k] - Fv[a][k]);
                     rv[(x * M + a) * 3 + r] = wJ * s;
                 }
-            TJ* o = cv + (size_t)x * 300;
-            for (int b = 0; b < M; ++b) {
-                Dir ud[M];
-                for (int a = 0; a < M; ++a) ud[a] = {u[a], a == b ? 1.0 : 0.0};
-                Dir Fcd[M][3], Fvd[M][3];
-                conv_flux<3, Dir, double>(ud, P, Fcd);
-                visc_flux<3, Dir, double>(ud, q, 0.0, P, Fvd);
-                for (int a = 0; a < M; ++a)
-                    for (int r = 0; r < 3; ++r) {
-                        double s = 0.0;
-                        for (int k = 0; k < 3; ++k) s += Ji[r * 3 + k] * (Fcd[a][k].t - Fvd[a][k].t);
-                        o[((a * 3 + r) * M + b) * 4 + 0] = (TJ)(wJ * s);
+            if constexpr (sizeof(TJ) == sizeof(float)) {
+                // Jacobian coefficients in the contraction's precision (FP32 in the mixed form)
+                TJ* o = cv + (size_t)x * 300;
+                const PhysT<SJ>& PJ = jphys<SJ>(A);
+                SJ us[M], qs[M][3], Js[9];
+                for (int a = 0; a < M; ++a) { us[a] = (SJ)u[a]; for (int k = 0; k < 3; ++k) qs[a][k] = (SJ)q[a][k]; }
+                for (int k = 0; k < 9; ++k) Js[k] = (SJ)Ji[k];
+                const SJ wJs = (SJ)wJ;
+                for (int b = 0; b < M; ++b) {
+                    DirT<SJ> ud[M];
+                    for (int a = 0; a < M; ++a) ud[a] = {us[a], a == b ? SJ(1) : SJ(0)};
+                    DirT<SJ> Fcd[M][3], Fvd[M][3];
+                    conv_flux<3, DirT<SJ>, SJ>(ud, PJ, Fcd);
+                    visc_flux<3, DirT<SJ>, SJ>(ud, qs, SJ(0), PJ, Fvd);
+                    for (int a = 0; a < M; ++a)
+                        for (int r = 0; r < 3; ++r) {
+                            SJ s = SJ(0);
+                            for (int k = 0; k < 3; ++k) s += Js[r * 3 + k] * (Fcd[a][k].t - Fvd[a][k].t);
+                            o[((a * 3 + r) * M + b) * 4 + 0] = (TJ)(wJs * s);
+                        }
+                    for (int l = 0; l < 3; ++l) {
+                        SJ qe[M][3];
+                        for (int a = 0; a < M; ++a) for (int k = 0; k < 3; ++k) qe[a][k] = (a == b && k == l) ? SJ(1) : SJ(0);
+                        SJ Fq[M][3];
+                        visc_flux<3, SJ, SJ>(us, qe, SJ(0), PJ, Fq);
+                        for (int a = 0; a < M; ++a)
+                            for (int r = 0; r < 3; ++r) {
+                                SJ s = SJ(0);
+                                for (int k = 0; k < 3; ++k) s += Js[r * 3 + k] * Fq[a][k];
+                                o[((a * 3 + r) * M + b) * 4 + 1 + l] = (TJ)(-wJs * s);
+                            }
                     }
-                for (int l = 0; l < 3; ++l) {
-                    double qe[M][3];
-                    for (int a = 0; a < M; ++a) for (int k = 0; k < 3; ++k) qe[a][k] = (a == b && k == l) ? 1.0 : 0.0;
-                    double Fq[M][3];
-                    visc_flux<3, double, double>(u, qe, 0.0, P, Fq);
+                }
+            } else {
+                TJ* o = cv + (size_t)x * 300;
+                for (int b = 0; b < M; ++b) {
+                    Dir ud[M];
+                    for (int a = 0; a < M; ++a) ud[a] = {u[a], a == b ? 1.0 : 0.0};
+                    Dir Fcd[M][3], Fvd[M][3];
+                    conv_flux<3, Dir, double>(ud, P, Fcd);
+                    visc_flux<3, Dir, double>(ud, q, 0.0, P, Fvd);
                     for (int a = 0; a < M; ++a)
                         for (int r = 0; r < 3; ++r) {
                             double s = 0.0;
-                            for (int k = 0; k < 3; ++k) s += Ji[r * 3 + k] * Fq[a][k];
-                            o[((a * 3 + r) * M + b) * 4 + 1 + l] = (TJ)(-wJ * s);
+                            for (int k = 0; k < 3; ++k) s += Ji[r * 3 + k] * (Fcd[a][k].t - Fvd[a][k].t);
+                            o[((a * 3 + r) * M + b) * 4 + 0] = (TJ)(wJ * s);
                         }
+                    for (int l = 0; l < 3; ++l) {
+                        double qe[M][3];
+                        for (int a = 0; a < M; ++a) for (int k = 0; k < 3; ++k) qe[a][k] = (a == b && k == l) ? 1.0 : 0.0;
+                        double Fq[M][3];
+                        visc_flux<3, double, double>(u, qe, 0.0, P, Fq);
+                        for (int a = 0; a < M; ++a)
+                            for (int r = 0; r < 3; ++r) {
+                                double s = 0.0;
+                                for (int k = 0; k < 3; ++k) s += Ji[r * 3 + k] * Fq[a][k];
+                                o[((a * 3 + r) * M + b) * 4 + 1 + l] = (TJ)(-wJ * s);
+                            }
+                    }
                 }
             }
         } else {
@@ -924,28 +967,61 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
                 }
                 ob[(a * M + b) * 5 + kind] = (TJ)w;
             };
-            for (int b = 0; b < M; ++b) {
-                Dir ud[M];
-                for (int a = 0; a < M; ++a) ud[a] = {uh[a], a == b ? 1.0 : 0.0};
-                Dir Fcd[M][3], Fvd[M][3];
-                conv_flux<3, Dir, double>(ud, P, Fcd);
-                visc_flux<3, Dir, double>(ud, q, 0.0, P, Fvd);
-                const double dtau = A.tau_mode ? nrm * stab_tau<3, Dir, double>(ud, nh, d.hinv, P).t : 0.0;
-                for (int a = 0; a < M; ++a) {
-                    double fn = 0.0;
-                    for (int k = 0; k < 3; ++k) fn += (Fcd[a][k].t - Fvd[a][k].t) * nw[k];
-                    put(a, b, 0, a == b ? taun : 0.0);
-                    put(a, b, 1, fn - (a == b ? taun : 0.0) + (u[a] - uh[a]) * dtau);
+            if constexpr (sizeof(TJ) == sizeof(float)) {
+                const PhysT<SJ>& PJ = jphys<SJ>(A);
+                SJ uhs[M], qs[M][3], nws[3], nhs[3];
+                for (int a = 0; a < M; ++a) { uhs[a] = (SJ)uh[a]; for (int k = 0; k < 3; ++k) qs[a][k] = (SJ)q[a][k]; }
+                for (int k = 0; k < 3; ++k) { nws[k] = (SJ)nw[k]; nhs[k] = (SJ)nh[k]; }
+                for (int b = 0; b < M; ++b) {
+                    DirT<SJ> ud[M];
+                    for (int a = 0; a < M; ++a) ud[a] = {uhs[a], a == b ? SJ(1) : SJ(0)};
+                    DirT<SJ> Fcd[M][3], Fvd[M][3];
+                    conv_flux<3, DirT<SJ>, SJ>(ud, PJ, Fcd);
+                    visc_flux<3, DirT<SJ>, SJ>(ud, qs, SJ(0), PJ, Fvd);
+                    const double dtau =
+                        A.tau_mode ? nrm * (double)stab_tau<3, DirT<SJ>, SJ>(ud, nhs, (SJ)d.hinv, PJ).t : 0.0;
+                    for (int a = 0; a < M; ++a) {
+                        SJ fn = SJ(0);
+                        for (int k = 0; k < 3; ++k) fn += (Fcd[a][k].t - Fvd[a][k].t) * nws[k];
+                        put(a, b, 0, a == b ? taun : 0.0);
+                        put(a, b, 1, (double)fn - (a == b ? taun : 0.0) + (u[a] - uh[a]) * dtau);
+                    }
+                    for (int l = 0; l < 3; ++l) {
+                        SJ qe[M][3];
+                        for (int a = 0; a < M; ++a) for (int k = 0; k < 3; ++k) qe[a][k] = (a == b && k == l) ? SJ(1) : SJ(0);
+                        SJ Fq[M][3];
+                        visc_flux<3, SJ, SJ>(uhs, qe, SJ(0), PJ, Fq);
+                        for (int a = 0; a < M; ++a) {
+                            SJ fn = SJ(0);
+                            for (int k = 0; k < 3; ++k) fn += Fq[a][k] * nws[k];
+                            put(a, b, 2 + l, -(double)fn);
+                        }
+                    }
                 }
-                for (int l = 0; l < 3; ++l) {
-                    double qe[M][3];
-                    for (int a = 0; a < M; ++a) for (int k = 0; k < 3; ++k) qe[a][k] = (a == b && k == l) ? 1.0 : 0.0;
-                    double Fq[M][3];
-                    visc_flux<3, double, double>(uh, qe, 0.0, P, Fq);
+            } else {
+                for (int b = 0; b < M; ++b) {
+                    Dir ud[M];
+                    for (int a = 0; a < M; ++a) ud[a] = {uh[a], a == b ? 1.0 : 0.0};
+                    Dir Fcd[M][3], Fvd[M][3];
+                    conv_flux<3, Dir, double>(ud, P, Fcd);
+                    visc_flux<3, Dir, double>(ud, q, 0.0, P, Fvd);
+                    const double dtau = A.tau_mode ? nrm * stab_tau<3, Dir, double>(ud, nh, d.hinv, P).t : 0.0;
                     for (int a = 0; a < M; ++a) {
                         double fn = 0.0;
-                        for (int k = 0; k < 3; ++k) fn += Fq[a][k] * nw[k];
-                        put(a, b, 2 + l, -fn);
+                        for (int k = 0; k < 3; ++k) fn += (Fcd[a][k].t - Fvd[a][k].t) * nw[k];
+                        put(a, b, 0, a == b ? taun : 0.0);
+                        put(a, b, 1, fn - (a == b ? taun : 0.0) + (u[a] - uh[a]) * dtau);
+                    }
+                    for (int l = 0; l < 3; ++l) {
+                        double qe[M][3];
+                        for (int a = 0; a < M; ++a) for (int k = 0; k < 3; ++k) qe[a][k] = (a == b && k == l) ? 1.0 : 0.0;
+                        double Fq[M][3];
+                        visc_flux<3, double, double>(uh, qe, 0.0, P, Fq);
+                        for (int a = 0; a < M; ++a) {
+                            double fn = 0.0;
+                            for (int k = 0; k < 3; ++k) fn += Fq[a][k] * nw[k];
+                            put(a, b, 2 + l, -fn);
+                        }
                     }
                 }
             }
@@ -1762,7 +1838,7 @@ int linearize(hdg_ctx* h, const double* U, const double* Q, const double* UH, co
     A.tab = c->d_tab; A.tabf = c->d_tabf; A.gvol = c->d_gvol; A.gface = c->d_gface;
     A.U = U; A.Q = Q; A.UH = UH; A.Ustar = Ustar;
     A.mat = c->d_mat; A.rec = c->d_rec; A.work = c->d_work; A.wstride = c->work_stride;
-    A.ph = phys_t<double>(h->phys); A.dt = dt; A.a_ii = a_ii; A.tau = h->phys.tau;
+    A.ph = phys_t<double>(h->phys); A.phf = phys_t<float>(h->phys); A.dt = dt; A.a_ii = a_ii; A.tau = h->phys.tau;
     A.ub = h->d_ub; A.ew = h->e_wall; A.status = h->d_status;
     A.tau_mode = h->phys.tau_mode;
     cudaStream_t st = h->stream;
@@ -1859,7 +1935,7 @@ KArgs base_args(hdg_ctx* h, const double* U, const double* Q, const double* UH, 
     A.tab = c->d_tab; A.tabf = c->d_tabf; A.gvol = c->d_gvol; A.gface = c->d_gface;
     A.U = U; A.Q = Q; A.UH = UH; A.Ustar = Ustar;
     A.mat = c->d_mat; A.rec = c->d_rec; A.work = c->d_work; A.wstride = c->work_stride;
-    A.ph = phys_t<double>(h->phys); A.dt = dt; A.a_ii = a_ii; A.tau = h->phys.tau;
+    A.ph = phys_t<double>(h->phys); A.phf = phys_t<float>(h->phys); A.dt = dt; A.a_ii = a_ii; A.tau = h->phys.tau;
     A.ub = h->d_ub; A.ew = h->e_wall; A.status = h->d_status;
     A.tau_mode = h->phys.tau_mode;
     return A;
