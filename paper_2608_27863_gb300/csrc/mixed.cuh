@@ -1221,10 +1221,14 @@ struct BlkTC {
     static constexpr int MT = 128, KC = 16;   // 16-wide chunks keep 4-5 CTAs (32-40 warps) per SM
     static constexpr int NMT = (MR + MT - 1) / MT;
     static constexpr int K = C::D * C::NQ;
+    static constexpr int CPD = (C::NQ + KC - 1) / KC;                     // chunks per direction
+    static constexpr int NCH = C::D * CPD;                                // chunks in all
     static constexpr int NTN = (C::NP + 15) / 16 * 16;
     static constexpr int TCOLS = NTN <= 32 ? 32 : NTN <= 64 ? 64 : 128;
     static constexpr int THREADS = 256;
+    static_assert(THREADS == 2 * MT, "a thread forms one row for two K quads");
     static constexpr int STAGE = 2 * (MT * KC + NTN * KC);                // floats of one stage (hi and lo)
+    static constexpr int MINB = NTN <= 32 ? 5 : 3;                        // resident CTAs (registers, stages)
     static_assert(NTN <= 128, "N tile too wide");
     __host__ __device__ static constexpr int smem_bytes() { return 2 * STAGE * 4 + 64; }
 };
@@ -1235,10 +1239,10 @@ struct BlkTC {
 // the threads generate chunk c + 1 (rows fastest: a quarter warp's 16-byte stores are
 // contiguous) while the tensor cores run chunk c.
 template <class C>
-__global__ void __launch_bounds__(BlkTC<C>::THREADS) k_blocks_tc(BlkArgs<float> A, int32_t* status) {
+__global__ void __launch_bounds__(BlkTC<C>::THREADS, BlkTC<C>::MINB) k_blocks_tc(BlkArgs<float> A, int32_t* status) {
     using S = BlkTC<C>;
     constexpr int D = C::D, M = C::M, NP = C::NP, NQ = C::NQ, NFP = C::NFP, NCOEF = C::NCOEF;
-    constexpr int NCB = S::NCB, MR = S::MR, MT = S::MT, KC = S::KC, K = S::K, NTN = S::NTN, TH = S::THREADS;
+    constexpr int NCB = S::NCB, MR = S::MR, MT = S::MT, KC = S::KC, NTN = S::NTN, TH = S::THREADS;
     constexpr int GEO = Geo<D>::N;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int64_t bid = blockIdx.x;
@@ -1252,34 +1256,63 @@ __global__ void __launch_bounds__(BlkTC<C>::THREADS) k_blocks_tc(BlkArgs<float> 
     uint64_t* mbar = reinterpret_cast<uint64_t*>(smraw + S::smem_bytes() - 64);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
 
-    // operand tiles of the chunk at k0 into stage buffer sb (Ah | Bh | Al | Bl)
-    auto generate = [&](int k0, float* sb) {
+    // Chunks run over one direction and 16 consecutive points each (every
+    // direction's points padded to whole chunks), so that a chunk needs no
+    // division per entry; thread tid forms row tid % 128 (decoded once) for the
+    // K quads tid / 128 and tid / 128 + 2, each quad's loads issued before they are used.
+    const int rl = tid & (MT - 1), r0 = m0 + rl;
+    const bool live = r0 < MR;
+    const int rab = live ? r0 / NCB : 0, rc = live ? r0 - rab * NCB : 0;
+    const bool vol = rc < NP;
+    const int rf = vol ? 0 : (rc - NP) / NFP, rlf = vol ? 0 : rc - NP - rf * NFP;
+    const float* rcf = cfe + (size_t)rab * D * NCOEF * NQ;
+
+    // operand tiles of chunk ci into stage buffer sb (Ah | Bh | Al | Bl)
+    auto generate = [&](int ci, float* sb) {
         float* Ah = sb;
         float* Bh = Ah + MT * KC;
         float* Al = Bh + NTN * KC;
         float* Bl = Al + MT * KC;
-        for (int it = tid; it < MT * (KC / 4); it += TH) {
-            const int rl = it % MT, q = it / MT, r = m0 + rl;
-            float v[4] = {0.f, 0.f, 0.f, 0.f};
-            if (r < MR) {
-                const int ab = r / NCB, c = r - ab * NCB;
+        const int dir = ci / S::CPD, g0 = (ci - dir * S::CPD) * KC;
+        const float* cc = rcf + (size_t)dir * NCOEF * NQ;
+#pragma unroll 1
+        for (int h = 0; h < 2; ++h) {                  // one K quad at a time: its loads in flight together
+            const int q = (tid >> 7) + 2 * h;
+            float v[4];
+            if (vol) {
+                float c0[4], t0[4], cr[4][D], tr[4][D];
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
-                    const int k = k0 + q * 4 + u;
-                    if (k >= K) continue;
-                    const int dir = k / NQ, g = k - dir * NQ;
-                    const float* cc = cfe + ((size_t)ab * D + dir) * NCOEF * NQ + g;
-                    float x;
-                    if (c < NP) {
-                        x = cc[0] * T.fphi[g * NP + c];
-                        for (int r2 = 0; r2 < D; ++r2) x -= cc[(1 + r2) * NQ] * T.fpsi[((size_t)r2 * NQ + g) * NP + c];
-                    } else {
-                        const int c2 = c - NP, f = c2 / NFP, l = c2 - f * NFP;
-                        x = cc[(1 + D + f) * NQ] * T.ftheta[((size_t)f * NQ + g) * NFP + l];
+                    const int g = min(g0 + 4 * q + u, NQ - 1);
+                    c0[u] = cc[g];
+                    t0[u] = T.fphi[g * NP + rc];
+#pragma unroll
+                    for (int r2 = 0; r2 < D; ++r2) {
+                        cr[u][r2] = cc[(1 + r2) * NQ + g];
+                        tr[u][r2] = T.fpsi[((size_t)r2 * NQ + g) * NP + rc];
                     }
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    float x = c0[u] * t0[u];
+#pragma unroll
+                    for (int r2 = 0; r2 < D; ++r2) x = fmaf(-cr[u][r2], tr[u][r2], x);
                     v[u] = x;
                 }
+            } else {
+                float c1[4], t1[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int g = min(g0 + 4 * q + u, NQ - 1);
+                    c1[u] = cc[(1 + D + rf) * NQ + g];
+                    t1[u] = T.ftheta[((size_t)rf * NQ + g) * NFP + rlf];
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) v[u] = c1[u] * t1[u];
             }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (!live || g0 + 4 * q + u >= NQ) v[u] = 0.f;
             const int off = ((rl >> 3) * (KC / 4) + q) * 32 + (rl & 7) * 4;
             const float4 hi = make_float4(tf32_round(v[0]), tf32_round(v[1]), tf32_round(v[2]), tf32_round(v[3]));
             *reinterpret_cast<float4*>(Ah + off) = hi;
@@ -1288,17 +1321,17 @@ __global__ void __launch_bounds__(BlkTC<C>::THREADS) k_blocks_tc(BlkArgs<float> 
         }
         for (int it = tid; it < NTN * (KC / 4); it += TH) {
             const int n = it % NTN, q = it / NTN;
-            float v[4];
+            float w[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const int k = k0 + q * 4 + u;
-                v[u] = (n < NP && k < K) ? T.fdphi[(size_t)k * NP + n] : 0.f;
+                const int g = g0 + q * 4 + u;
+                w[u] = (n < NP && g < NQ) ? T.fdphi[((size_t)dir * NQ + g) * NP + n] : 0.f;
             }
             const int off = ((n >> 3) * (KC / 4) + q) * 32 + (n & 7) * 4;
-            const float4 hi = make_float4(tf32_round(v[0]), tf32_round(v[1]), tf32_round(v[2]), tf32_round(v[3]));
+            const float4 hi = make_float4(tf32_round(w[0]), tf32_round(w[1]), tf32_round(w[2]), tf32_round(w[3]));
             *reinterpret_cast<float4*>(Bh + off) = hi;
-            *reinterpret_cast<float4*>(Bl + off) = make_float4(tf32_round(v[0] - hi.x), tf32_round(v[1] - hi.y),
-                                                               tf32_round(v[2] - hi.z), tf32_round(v[3] - hi.w));
+            *reinterpret_cast<float4*>(Bl + off) = make_float4(tf32_round(w[0] - hi.x), tf32_round(w[1] - hi.y),
+                                                               tf32_round(w[2] - hi.z), tf32_round(w[3] - hi.w));
         }
         asm volatile("fence.proxy.async.shared::cta;");
     };
@@ -1334,7 +1367,7 @@ __global__ void __launch_bounds__(BlkTC<C>::THREADS) k_blocks_tc(BlkArgs<float> 
         phase ^= 1u << sb;
         pending &= ~(1u << sb);
     };
-    for (int k0 = 0, ci = 0; k0 < K; k0 += KC, ++ci) {
+    for (int ci = 0; ci < S::NCH; ++ci) {
         const int sbi = ci & 1;
         if (tid == 0) {
             asm volatile("tcgen05.fence::after_thread_sync;");
@@ -1342,14 +1375,13 @@ __global__ void __launch_bounds__(BlkTC<C>::THREADS) k_blocks_tc(BlkArgs<float> 
             const float* Bh = Ah + MT * KC;
             const float* Al = Bh + NTN * KC;
             const float* Bl = Al + MT * KC;
-            const int nsteps = (min(KC, K - k0) + 7) / 8;
-            for (int s = 0; s < nsteps; ++s) {
+            for (int s = 0; s < KC / 8; ++s) {
                 const uint32_t off = s * 256;
                 const uint64_t ah = umma_desc(smem_u32(Ah) + off, 128, (KC / 4) * 128);
                 const uint64_t bh = umma_desc(smem_u32(Bh) + off, 128, (KC / 4) * 128);
                 const uint64_t al = umma_desc(smem_u32(Al) + off, 128, (KC / 4) * 128);
                 const uint64_t bl = umma_desc(smem_u32(Bl) + off, 128, (KC / 4) * 128);
-                uint32_t acc = (k0 > 0 || s > 0) ? 1u : 0u;
+                uint32_t acc = (ci > 0 || s > 0) ? 1u : 0u;
                 asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                              "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
                              :: "r"(tmem), "l"(ah), "l"(bh), "r"(idesc), "r"(acc));
@@ -1362,13 +1394,13 @@ __global__ void __launch_bounds__(BlkTC<C>::THREADS) k_blocks_tc(BlkArgs<float> 
                          :: "r"(smem_u32(mbar + sbi)));
         }
         pending |= 1u << sbi;
-        if (k0 + KC < K) {
+        if (ci + 1 < S::NCH) {
             wait_stage(sbi ^ 1);                                 // the batch before this one read the other buffer
             if (__syncthreads_or(ok ? 0 : 1)) {
                 ok = false;
                 break;
             }
-            generate(k0 + KC, stage0 + (sbi ^ 1) * S::STAGE);
+            generate(ci + 1, stage0 + (sbi ^ 1) * S::STAGE);
             __syncthreads();
         }
     }

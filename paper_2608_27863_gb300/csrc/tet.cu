@@ -99,202 +99,6 @@ template <class T> __device__ __forceinline__ const T* jtab(const KArgs& A);
 template <> __device__ __forceinline__ const double* jtab<double>(const KArgs& A) { return A.tab; }
 template <> __device__ __forceinline__ const float* jtab<float>(const KArgs& A) { return A.tabf; }
 
-// Trace rows of the mixed form, after the FP64 LU of the interior block At
-// (partial pivoting, panels of NB columns; the interchanges of a panel are
-// recorded in gpiv and applied only to the columns right of it inside At, so
-// the L of each panel is stored at that panel's row order):
-//  * z = L^{-1} P Rt in FP64 and Z = L^{-1} P Bt in FP32, panel by panel: the
-//    panel's interchanges, then its unit-lower block and the update of the rows
-//    below, one thread per column with the panel's values in registers;
-//  * W = Ct U^{-1} in FP32, panel by panel over the columns of U (W kept
-//    transposed so that threads over trace rows read consecutive words);
-//  * Z back into the bordered matrix (the recovery reads it), the right-hand
-//    side Rh - W z in FP64 and S = Dt - W Z in FP32 with 8 x 8 register tiles.
-template <int NB>
-__device__ void trace_schur_f32(double* Mx, int NU, int t, int LD, const int* gpiv, float* Wt, float* Zf,
-                                float* smf) {
-    const int tid = threadIdx.x, NR = NU + t;
-    for (int idx = tid; idx < NU * t; idx += NTH) {
-        const int i = idx / t, r = idx - i * t;
-        Wt[idx] = (float)Mx[(size_t)(NU + r) * LD + i];
-        Zf[idx] = (float)Mx[(size_t)i * LD + NU + r];
-    }
-    __syncthreads();
-    // Z = L^{-1} P Bt (FP32, one thread per column) and z = L^{-1} P Rt (FP64:
-    // interchanges and the panel's block by one thread, the rows below by all)
-    float* sL = smf;                                    // [NU - k0][NB] panel of L
-    __shared__ double zp[NB];
-    double* zc = Mx + NR;                               // column NR, stride LD
-    for (int k0 = 0; k0 < NU; k0 += NB) {
-        const int kb = min(NB, NU - k0);
-        for (int idx = tid; idx < (NU - k0) * NB; idx += NTH) {
-            const int i = idx / NB, j = idx - i * NB;
-            sL[idx] = j < kb ? (float)Mx[(size_t)(k0 + i) * LD + k0 + j] : 0.0f;
-        }
-        __syncthreads();
-        for (int r = tid; r < t; r += NTH) {
-            float* zf = Zf + r;
-            for (int j = 0; j < kb; ++j) {
-                const int pr = gpiv[k0 + j];
-                if (pr != k0 + j) {
-                    const float x = zf[(size_t)(k0 + j) * t];
-                    zf[(size_t)(k0 + j) * t] = zf[(size_t)pr * t];
-                    zf[(size_t)pr * t] = x;
-                }
-            }
-            float zv[NB];
-#pragma unroll
-            for (int j = 0; j < NB; ++j) zv[j] = j < kb ? zf[(size_t)(k0 + j) * t] : 0.0f;
-#pragma unroll
-            for (int j = 0; j < NB; ++j)
-#pragma unroll
-                for (int jj = j + 1; jj < NB; ++jj)
-                    if (jj < kb) zv[jj] = fmaf(-sL[jj * NB + j], zv[j], zv[jj]);
-#pragma unroll
-            for (int j = 0; j < NB; ++j)
-                if (j < kb) zf[(size_t)(k0 + j) * t] = zv[j];
-            // rows below the panel, 8 at a time: their loads are in flight together
-            for (int i0 = k0 + kb; i0 < NU; i0 += 8) {
-                float s2[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) s2[u] = zf[(size_t)min(i0 + u, NU - 1) * t];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float* l = sL + (size_t)(min(i0 + u, NU - 1) - k0) * NB;
-#pragma unroll
-                    for (int j = 0; j < NB; ++j) s2[u] = fmaf(-l[j], zv[j], s2[u]);
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (i0 + u < NU) zf[(size_t)(i0 + u) * t] = s2[u];
-            }
-        }
-        if (tid == NTH - 1) {
-            for (int j = 0; j < kb; ++j) {
-                const int pr = gpiv[k0 + j];
-                if (pr != k0 + j) {
-                    const double x = zc[(size_t)(k0 + j) * LD];
-                    zc[(size_t)(k0 + j) * LD] = zc[(size_t)pr * LD];
-                    zc[(size_t)pr * LD] = x;
-                }
-            }
-            for (int j = 0; j < kb; ++j) {
-                double zj = zc[(size_t)(k0 + j) * LD];
-                for (int i = 0; i < j; ++i) zj -= Mx[(size_t)(k0 + j) * LD + k0 + i] * zp[i];
-                zp[j] = zj;
-                zc[(size_t)(k0 + j) * LD] = zj;
-            }
-        }
-        __syncthreads();
-        for (int i = k0 + kb + tid; i < NU; i += NTH) {
-            double s2 = zc[(size_t)i * LD];
-            for (int j = 0; j < kb; ++j) s2 -= Mx[(size_t)i * LD + k0 + j] * zp[j];
-            zc[(size_t)i * LD] = s2;
-        }
-        __syncthreads();
-    }
-    // W = Ct U^{-1}: W U = Ct, panel by panel over the columns of U
-    float* sUp = smf;                                   // [NB][NU - k0] panel rows of U
-    float* sDi = smf + NB * NU;                         // [NB] reciprocal diagonal
-    for (int k0 = 0; k0 < NU; k0 += NB) {
-        const int kb = min(NB, NU - k0), w = NU - k0;
-        for (int idx = tid; idx < NB * w; idx += NTH) {
-            const int j = idx / w, c = idx - j * w;
-            sUp[idx] = (j < kb && c >= j) ? (float)Mx[(size_t)(k0 + j) * LD + k0 + c] : 0.0f;
-        }
-        if (tid < NB) {
-            const float u = tid < kb ? (float)Mx[(size_t)(k0 + tid) * LD + k0 + tid] : 1.0f;
-            sDi[tid] = u != 0.0f ? 1.0f / u : 1.0f;
-        }
-        __syncthreads();
-        for (int r = tid; r < t; r += NTH) {
-            float* wc = Wt + r;
-            float wv[NB];
-#pragma unroll
-            for (int j = 0; j < NB; ++j) wv[j] = j < kb ? wc[(size_t)(k0 + j) * t] : 0.0f;
-#pragma unroll
-            for (int j = 0; j < NB; ++j) {
-                if (j >= kb) continue;
-#pragma unroll
-                for (int i = 0; i < j; ++i) wv[j] = fmaf(-wv[i], sUp[i * w + j], wv[j]);
-                wv[j] *= sDi[j];
-            }
-#pragma unroll
-            for (int j = 0; j < NB; ++j)
-                if (j < kb) wc[(size_t)(k0 + j) * t] = wv[j];
-            for (int c0 = kb; c0 < w; c0 += 8) {        // 8 columns at a time, loads in flight together
-                float s2[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) s2[u] = wc[(size_t)(k0 + min(c0 + u, w - 1)) * t];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int c = min(c0 + u, w - 1);
-#pragma unroll
-                    for (int j = 0; j < NB; ++j) s2[u] = fmaf(-wv[j], sUp[j * w + c], s2[u]);
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (c0 + u < w) wc[(size_t)(k0 + c0 + u) * t] = s2[u];
-            }
-        }
-        __syncthreads();
-    }
-    // Z to the bordered matrix (FP32 values in FP64 storage)
-    for (int idx = tid; idx < NU * t; idx += NTH) {
-        const int i = idx / t, r = idx - i * t;
-        Mx[(size_t)i * LD + NU + r] = (double)Zf[idx];
-    }
-    // right-hand side of the trace rows: Rh - W z (FP64)
-    for (int r = tid; r < t; r += NTH) {
-        double s2 = Mx[(size_t)(NU + r) * LD + NR];
-        for (int i = 0; i < NU; ++i) s2 -= (double)Wt[(size_t)i * t + r] * Mx[(size_t)i * LD + NR];
-        Mx[(size_t)(NU + r) * LD + NR] = s2;
-    }
-    // S = Dt - W Z
-    constexpr int KS = 16, TP = 304;                    // K staged per step; row stride of the staged panels
-    float* sW = smf;                                    // [KS][TP]
-    float* sZ = smf + KS * TP;                          // [KS][TP]
-    const int n8 = (t + 7) / 8, ntiles = n8 * n8;
-    for (int tile0 = 0; tile0 < ntiles; tile0 += NTH) {
-        const int tile = tile0 + tid;
-        const bool act = tile < ntiles;
-        const int tr = act ? tile / n8 : 0, tc = act ? tile - tr * n8 : 0;
-        float acc[8][8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-#pragma unroll
-            for (int v = 0; v < 8; ++v) acc[u][v] = 0.0f;
-        for (int k0 = 0; k0 < NU; k0 += KS) {
-            const int kc = min(KS, NU - k0);
-            __syncthreads();
-            for (int idx = tid; idx < kc * TP; idx += NTH) {
-                const int kk = idx / TP, c = idx - kk * TP;
-                sW[idx] = c < t ? Wt[(size_t)(k0 + kk) * t + c] : 0.0f;
-                sZ[idx] = c < t ? Zf[(size_t)(k0 + kk) * t + c] : 0.0f;
-            }
-            __syncthreads();
-            if (act)
-                for (int kk = 0; kk < kc; ++kk) {
-                    float wv[8], zv[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) { wv[u] = sW[kk * TP + 8 * tr + u]; zv[u] = sZ[kk * TP + 8 * tc + u]; }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u)
-#pragma unroll
-                        for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(wv[u], zv[v], acc[u][v]);
-                }
-        }
-        if (act)
-            for (int u = 0; u < 8; ++u) {
-                const int r = 8 * tr + u;
-                if (r >= t) continue;
-                for (int v = 0; v < 8; ++v) {
-                    const int c = 8 * tc + v;
-                    if (c < t) Mx[(size_t)(NU + r) * LD + NU + c] -= (double)acc[u][v];
-                }
-            }
-    }
-}
 
 // column index in the bordered matrix of column c (of component b) of the contraction
 __device__ __forceinline__ int bcol(const TetElem& d, int b, int c) {
@@ -559,15 +363,100 @@ __device__ __forceinline__ void tc_wait(TcState& ts, uint32_t& pending, int sb, 
     pending &= ~(1u << sb);
 }
 
+// One 128-row tile of a 3xTF32 product into tensor memory: nch chunks, chunk ci
+// formed by form(ci, stage) into A hi | B hi | A lo | B lo (K-major core
+// matrices), N = ncp columns; the threads form chunk c + 1 while the tensor
+// cores run chunk c.  Returns false when a wait timed out (nothing to store).
+template <class Form>
+__device__ bool tc_tile(TcState& ts, float* st0, int nch, int ncp, Form&& form, int* sflag) {
+    const int tid = threadIdx.x;
+    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(ncp >> 3) << 17) |
+                           ((uint32_t)(TMT >> 4) << 24);
+    uint32_t pending = 0;
+    bool ok = true;
+    form(0, st0);
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    for (int ci = 0; ci < nch; ++ci) {
+        const int sbi = ci & 1;
+        if (tid == 0) {
+            const float* Ah = st0 + sbi * TSTAGE;
+            const float* Bh = Ah + TMT * TKC;
+            const float* Al = Bh + TNP * TKC;
+            const float* Bl = Al + TMT * TKC;
+            for (int s = 0; s < TKC / 8; ++s) {
+                const uint32_t off = s * 256;
+                const uint64_t ah = umma_desc(smem_u32(Ah) + off, 128, (TKC / 4) * 128);
+                const uint64_t bh = umma_desc(smem_u32(Bh) + off, 128, (TKC / 4) * 128);
+                const uint64_t al = umma_desc(smem_u32(Al) + off, 128, (TKC / 4) * 128);
+                const uint64_t bl = umma_desc(smem_u32(Bl) + off, 128, (TKC / 4) * 128);
+                const uint32_t acc = (ci > 0 || s > 0) ? 1u : 0u;
+                asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                             "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                             :: "r"(ts.tmem), "l"(ah), "l"(bh), "r"(idesc), "r"(acc));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
+                             :: "r"(ts.tmem), "l"(ah), "l"(bl), "r"(idesc));
+                asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
+                             :: "r"(ts.tmem), "l"(al), "l"(bh), "r"(idesc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         :: "r"(ts.bar + 8u * sbi));
+        }
+        pending |= 1u << sbi;
+        if (ci + 1 < nch) {
+            tc_wait(ts, pending, sbi ^ 1, ok, sflag);               // the previous batch read the other stage
+            if (__syncthreads_or(ok ? 0 : 1)) {
+                ok = false;
+                break;
+            }
+            form(ci + 1, st0 + (sbi ^ 1) * TSTAGE);
+            asm volatile("tcgen05.fence::before_thread_sync;");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;");
+        }
+    }
+    tc_wait(ts, pending, 0, ok, sflag);
+    tc_wait(ts, pending, 1, ok, sflag);
+    ok = !__syncthreads_or(ok ? 0 : 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    return ok;
+}
+
+// Read a finished tile from tensor memory: store(row of the tile, first column,
+// 16 values) for every 16 columns below ncp; warp w reads lanes 32 (w % 4) ..
+// + 31, warps 4..7 the second half of the columns.  Ends with the barrier after
+// which the next tile may overwrite the accumulator.
+template <class Store>
+__device__ void tc_tile_store(const TcState& ts, int ncp, Store&& store) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int lg = warp & 3, half = warp >> 2;
+    const int hc = ((ncp / 2) + 15) / 16 * 16;
+    for (int c0 = half * hc; c0 < min(ncp, (half + 1) * hc); c0 += 16) {
+        uint32_t v[16];
+        const uint32_t addr = ts.tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)c0;
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                       "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+                       "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                     : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        store(lg * 32 + lane, c0, v);
+    }
+}
+
+__device__ __forceinline__ void tc_tile_done() {
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+}
+
 // the whole contraction of one element (element rows, then the trace rows of
 // each face) into the bordered matrix Mx, FP64 storage
 __device__ void contract_tc(const TetElem& d, const float* tabJ, const float* cv, const float* cf, const float* cb,
                             const float* vq, const int* fpo, double* Mx, float* st0, TcState& ts, int* sflag) {
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
     const int Np = d.Np, LD = d.LD, NU = d.NU, Nc = Np + d.t / M;
     const int ncp = (Nc + 15) / 16 * 16;
-    const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(ncp >> 3) << 17) |
-                           ((uint32_t)(TMT >> 4) << 24);
     for (int sgi = -1; sgi < 4; ++sgi) {
         TcSeg sg;
         sg.f = sgi;
@@ -578,8 +467,6 @@ __device__ void contract_tc(const TetElem& d, const float* tabJ, const float* cv
         sg.nch = (sgi < 0 ? 4 * sg.cv : 0) + 5 * sg.cf;
         const float* cfb = sgi < 0 ? cf : cb;
         for (int m0 = 0; m0 < sg.rows; m0 += TMT) {
-            uint32_t pending = 0;
-            bool ok = true;
             TcRow rw;
             {
                 const int r = m0 + (tid & (TMT - 1));
@@ -589,82 +476,238 @@ __device__ void contract_tc(const TetElem& d, const float* tabJ, const float* cv
                 rw.cvo = rw.live ? (a * 3 * M + b) * 4 : 0;
                 rw.cfo = rw.live ? (a * M + b) * 5 : 0;
             }
-            tc_form(d, sg, rw, tc_chunk(d, sg, 0), ncp, tabJ, cv, cfb, vq, fpo, st0);
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            for (int ci = 0; ci < sg.nch; ++ci) {
-                const int sbi = ci & 1;
-                if (tid == 0) {
-                    const float* Ah = st0 + sbi * TSTAGE;
-                    const float* Bh = Ah + TMT * TKC;
-                    const float* Al = Bh + TNP * TKC;
-                    const float* Bl = Al + TMT * TKC;
-                    for (int s = 0; s < TKC / 8; ++s) {
-                        const uint32_t off = s * 256;
-                        const uint64_t ah = umma_desc(smem_u32(Ah) + off, 128, (TKC / 4) * 128);
-                        const uint64_t bh = umma_desc(smem_u32(Bh) + off, 128, (TKC / 4) * 128);
-                        const uint64_t al = umma_desc(smem_u32(Al) + off, 128, (TKC / 4) * 128);
-                        const uint64_t bl = umma_desc(smem_u32(Bl) + off, 128, (TKC / 4) * 128);
-                        const uint32_t acc = (ci > 0 || s > 0) ? 1u : 0u;
-                        asm volatile("{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
-                                     :: "r"(ts.tmem), "l"(ah), "l"(bh), "r"(idesc), "r"(acc));
-                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
-                                     :: "r"(ts.tmem), "l"(ah), "l"(bl), "r"(idesc));
-                        asm volatile("tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, 1;"
-                                     :: "r"(ts.tmem), "l"(al), "l"(bh), "r"(idesc));
-                    }
-                    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                                 :: "r"(ts.bar + 8u * sbi));
-                }
-                pending |= 1u << sbi;
-                if (ci + 1 < sg.nch) {
-                    tc_wait(ts, pending, sbi ^ 1, ok, sflag);       // the previous batch read the other stage
-                    if (__syncthreads_or(ok ? 0 : 1)) {
-                        ok = false;
-                        break;
-                    }
-                    tc_form(d, sg, rw, tc_chunk(d, sg, ci + 1), ncp, tabJ, cv, cfb, vq, fpo,
-                            st0 + (sbi ^ 1) * TSTAGE);
-                    asm volatile("tcgen05.fence::before_thread_sync;");
-                    __syncthreads();
-                    asm volatile("tcgen05.fence::after_thread_sync;");
-                }
-            }
-            tc_wait(ts, pending, 0, ok, sflag);
-            tc_wait(ts, pending, 1, ok, sflag);
-            ok = !__syncthreads_or(ok ? 0 : 1);
-            asm volatile("tcgen05.fence::after_thread_sync;");
-            if (ok) {
-                // warp w reads lanes 32 (w % 4) .. + 31; warps 4..7 take the second half of the columns
-                const int lg = warp & 3, half = warp >> 2;
-                const int r = m0 + lg * 32 + lane;
-                const int ab = r / sg.rdiv, i = r - ab * sg.rdiv, a = ab / M, b = ab - a * M;
-                const int64_t row = sgi < 0 ? (int64_t)a * Np + i : (int64_t)NU + d.toff[sgi] + a * sg.rdiv + i;
-                const int hc = ((ncp / 2) + 15) / 16 * 16;
-                for (int c0 = half * hc; c0 < min(ncp, (half + 1) * hc); c0 += 16) {
-                    uint32_t v[16];
-                    const uint32_t addr = ts.tmem + ((uint32_t)(lg * 32) << 16) + (uint32_t)c0;
-                    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                                   "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
-                                   "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-                                 : "r"(addr));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;");
-                    if (r < sg.rows) {
+            auto form = [&](int ci, float* sb) {
+                tc_form(d, sg, rw, tc_chunk(d, sg, ci), ncp, tabJ, cv, cfb, vq, fpo, sb);
+            };
+            if (tc_tile(ts, st0, sg.nch, ncp, form, sflag)) {
+                tc_tile_store(ts, ncp, [&](int rl, int c0, const uint32_t* v) {
+                    const int r = m0 + rl;
+                    if (r >= sg.rows) return;
+                    const int ab = r / sg.rdiv, i = r - ab * sg.rdiv, a = ab / M, b = ab - a * M;
+                    const int64_t row = sgi < 0 ? (int64_t)a * Np + i : (int64_t)NU + d.toff[sgi] + a * sg.rdiv + i;
 #pragma unroll
-                        for (int jj = 0; jj < 16; ++jj) {
-                            const int c = c0 + jj;
-                            if (c < Nc) Mx[row * LD + bcol(d, b, c)] = (double)__uint_as_float(v[jj]);
-                        }
+                    for (int jj = 0; jj < 16; ++jj) {
+                        const int c = c0 + jj;
+                        if (c < Nc) Mx[row * LD + bcol(d, b, c)] = (double)__uint_as_float(v[jj]);
                     }
-                }
+                });
             }
-            asm volatile("tcgen05.fence::before_thread_sync;");
-            __syncthreads();
+            tc_tile_done();
         }
     }
+}
+
+// The trace rows' Schur product of the mixed form on the tensor cores:
+// S = Dt - W Z with W = Wt^T ([n_u][t], trace rows contiguous) and Z ([n_u][t]),
+// 3xTF32 as the contraction; tiles of 128 trace rows x 96 trace columns.
+__device__ void schur_tc(double* Mx, int NU, int t, int LD, const float* Wt, const float* Zf, float* st0,
+                         TcState& ts, int* sflag) {
+    const int tid = threadIdx.x;
+    const int nch = (NU + TKC - 1) / TKC;
+    for (int m0 = 0; m0 < t; m0 += TMT)
+        for (int n0 = 0; n0 < t; n0 += TNP) {
+            const int nc = min(TNP, t - n0), ncp = (nc + 15) / 16 * 16;
+            auto form = [&](int ci, float* sb) {
+                float* Ah = sb;
+                float* Bh = Ah + TMT * TKC;
+                float* Al = Bh + TNP * TKC;
+                float* Bl = Al + TMT * TKC;
+                const int k0 = ci * TKC, rl = tid & (TMT - 1), r = min(m0 + rl, t - 1);
+                const bool live = m0 + rl < t;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int q = (tid >> 7) + 2 * h;
+                    float v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v[u] = Wt[(size_t)min(k0 + 4 * q + u, NU - 1) * t + r];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (!live || k0 + 4 * q + u >= NU) v[u] = 0.f;
+                    tc_put4(Ah, Al, rl, q, v);
+                }
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int it = tid + h * NTH;
+                    if (it >= ncp * (TKC / 4)) continue;
+                    const int n = it % ncp, q = it / ncp, c = n0 + min(n, nc - 1);
+                    float v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v[u] = Zf[(size_t)min(k0 + 4 * q + u, NU - 1) * t + c];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+                        if (n >= nc || k0 + 4 * q + u >= NU) v[u] = 0.f;
+                    tc_put4(Bh, Bl, n, q, v);
+                }
+                asm volatile("fence.proxy.async.shared::cta;");
+            };
+            if (tc_tile(ts, st0, nch, ncp, form, sflag)) {
+                tc_tile_store(ts, ncp, [&](int rl, int c0, const uint32_t* v) {
+                    const int r = m0 + rl;
+                    if (r >= t) return;
+                    double* row = Mx + (size_t)(NU + r) * LD + NU + n0;
+#pragma unroll
+                    for (int jj = 0; jj < 16; ++jj)
+                        if (c0 + jj < nc) row[c0 + jj] -= (double)__uint_as_float(v[jj]);
+                });
+            }
+            tc_tile_done();
+        }
+}
+
+// Trace rows of the mixed form, after the FP64 LU of the interior block At
+// (partial pivoting, panels of NB columns; the interchanges of a panel are
+// recorded in gpiv and applied only to the columns right of it inside At, so
+// the L of each panel is stored at that panel's row order):
+//  * z = L^{-1} P Rt in FP64 and Z = L^{-1} P Bt in FP32, panel by panel: the
+//    panel's interchanges, then its unit-lower block and the update of the rows
+//    below, one thread per column with the panel's values in registers;
+//  * W = Ct U^{-1} in FP32, panel by panel over the columns of U (W kept
+//    transposed so that threads over trace rows read consecutive words);
+//  * Z back into the bordered matrix (the recovery reads it), the right-hand
+//    side Rh - W z in FP64 and S = Dt - W Z on the tensor cores (3xTF32).
+template <int NB>
+__device__ void trace_schur_f32(double* Mx, int NU, int t, int LD, const int* gpiv, float* Wt, float* Zf,
+                                float* smf, TcState& ts, int* sflag) {
+    const int tid = threadIdx.x, NR = NU + t;
+    for (int idx = tid; idx < NU * t; idx += NTH) {
+        const int i = idx / t, r = idx - i * t;
+        Wt[idx] = (float)Mx[(size_t)(NU + r) * LD + i];
+        Zf[idx] = (float)Mx[(size_t)i * LD + NU + r];
+    }
+    __syncthreads();
+    // Z = L^{-1} P Bt (FP32, one thread per column) and z = L^{-1} P Rt (FP64:
+    // interchanges and the panel's block by one thread, the rows below by all)
+    float* sL = smf;                                    // [NU - k0][NB] panel of L
+    __shared__ double zp[NB];
+    double* zc = Mx + NR;                               // column NR, stride LD
+    for (int k0 = 0; k0 < NU; k0 += NB) {
+        const int kb = min(NB, NU - k0);
+        for (int idx = tid; idx < (NU - k0) * NB; idx += NTH) {
+            const int i = idx / NB, j = idx - i * NB;
+            sL[idx] = j < kb ? (float)Mx[(size_t)(k0 + i) * LD + k0 + j] : 0.0f;
+        }
+        __syncthreads();
+        for (int r = tid; r < t; r += NTH) {
+            float* zf = Zf + r;
+            for (int j = 0; j < kb; ++j) {
+                const int pr = gpiv[k0 + j];
+                if (pr != k0 + j) {
+                    const float x = zf[(size_t)(k0 + j) * t];
+                    zf[(size_t)(k0 + j) * t] = zf[(size_t)pr * t];
+                    zf[(size_t)pr * t] = x;
+                }
+            }
+            float zv[NB];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) zv[j] = j < kb ? zf[(size_t)(k0 + j) * t] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < NB; ++j)
+#pragma unroll
+                for (int jj = j + 1; jj < NB; ++jj)
+                    if (jj < kb) zv[jj] = fmaf(-sL[jj * NB + j], zv[j], zv[jj]);
+#pragma unroll
+            for (int j = 0; j < NB; ++j)
+                if (j < kb) zf[(size_t)(k0 + j) * t] = zv[j];
+            // rows below the panel, 8 at a time: their loads are in flight together
+            for (int i0 = k0 + kb; i0 < NU; i0 += 8) {
+                float s2[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s2[u] = zf[(size_t)min(i0 + u, NU - 1) * t];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const float* l = sL + (size_t)(min(i0 + u, NU - 1) - k0) * NB;
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) s2[u] = fmaf(-l[j], zv[j], s2[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i0 + u < NU) zf[(size_t)(i0 + u) * t] = s2[u];
+            }
+        }
+        if (tid == NTH - 1) {
+            for (int j = 0; j < kb; ++j) {
+                const int pr = gpiv[k0 + j];
+                if (pr != k0 + j) {
+                    const double x = zc[(size_t)(k0 + j) * LD];
+                    zc[(size_t)(k0 + j) * LD] = zc[(size_t)pr * LD];
+                    zc[(size_t)pr * LD] = x;
+                }
+            }
+            for (int j = 0; j < kb; ++j) {
+                double zj = zc[(size_t)(k0 + j) * LD];
+                for (int i = 0; i < j; ++i) zj -= Mx[(size_t)(k0 + j) * LD + k0 + i] * zp[i];
+                zp[j] = zj;
+                zc[(size_t)(k0 + j) * LD] = zj;
+            }
+        }
+        __syncthreads();
+        for (int i = k0 + kb + tid; i < NU; i += NTH) {
+            double s2 = zc[(size_t)i * LD];
+            for (int j = 0; j < kb; ++j) s2 -= Mx[(size_t)i * LD + k0 + j] * zp[j];
+            zc[(size_t)i * LD] = s2;
+        }
+        __syncthreads();
+    }
+    // W = Ct U^{-1}: W U = Ct, panel by panel over the columns of U
+    float* sUp = smf;                                   // [NB][NU - k0] panel rows of U
+    float* sDi = smf + NB * NU;                         // [NB] reciprocal diagonal
+    for (int k0 = 0; k0 < NU; k0 += NB) {
+        const int kb = min(NB, NU - k0), w = NU - k0;
+        for (int idx = tid; idx < NB * w; idx += NTH) {
+            const int j = idx / w, c = idx - j * w;
+            sUp[idx] = (j < kb && c >= j) ? (float)Mx[(size_t)(k0 + j) * LD + k0 + c] : 0.0f;
+        }
+        if (tid < NB) {
+            const float u = tid < kb ? (float)Mx[(size_t)(k0 + tid) * LD + k0 + tid] : 1.0f;
+            sDi[tid] = u != 0.0f ? 1.0f / u : 1.0f;
+        }
+        __syncthreads();
+        for (int r = tid; r < t; r += NTH) {
+            float* wc = Wt + r;
+            float wv[NB];
+#pragma unroll
+            for (int j = 0; j < NB; ++j) wv[j] = j < kb ? wc[(size_t)(k0 + j) * t] : 0.0f;
+#pragma unroll
+            for (int j = 0; j < NB; ++j) {
+                if (j >= kb) continue;
+#pragma unroll
+                for (int i = 0; i < j; ++i) wv[j] = fmaf(-wv[i], sUp[i * w + j], wv[j]);
+                wv[j] *= sDi[j];
+            }
+#pragma unroll
+            for (int j = 0; j < NB; ++j)
+                if (j < kb) wc[(size_t)(k0 + j) * t] = wv[j];
+            for (int c0 = kb; c0 < w; c0 += 8) {        // 8 columns at a time, loads in flight together
+                float s2[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) s2[u] = wc[(size_t)(k0 + min(c0 + u, w - 1)) * t];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int c = min(c0 + u, w - 1);
+#pragma unroll
+                    for (int j = 0; j < NB; ++j) s2[u] = fmaf(-wv[j], sUp[j * w + c], s2[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (c0 + u < w) wc[(size_t)(k0 + c0 + u) * t] = s2[u];
+            }
+        }
+        __syncthreads();
+    }
+    // Z to the bordered matrix (FP32 values in FP64 storage)
+    for (int idx = tid; idx < NU * t; idx += NTH) {
+        const int i = idx / t, r = idx - i * t;
+        Mx[(size_t)i * LD + NU + r] = (double)Zf[idx];
+    }
+    // right-hand side of the trace rows: Rh - W z (FP64)
+    for (int r = tid; r < t; r += NTH) {
+        double s2 = Mx[(size_t)(NU + r) * LD + NR];
+        for (int i = 0; i < NU; ++i) s2 -= (double)Wt[(size_t)i * t + r] * Mx[(size_t)i * LD + NR];
+        Mx[(size_t)(NU + r) * LD + NR] = s2;
+    }
+    // S = Dt - W Z on the tensor cores
+    __syncthreads();
+    schur_tc(Mx, NU, t, LD, Wt, Zf, smf, ts, sflag);
 }
 
 // TJ: type of the Jacobian coefficients, the column variations and the
@@ -696,28 +739,32 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
     gather_element(A, d, sm);
     load_geometry(A, d, gv, gf);
     __syncthreads();
-    // physical gradients at the volume points, mass matrix
-    double* dp = W + W_DP;
+    // physical gradients at the volume points and the basis values, both times the
+    // point weight w|J| (so that E and M take one multiply-add per point), mass matrix
+    double* dp = W + W_DP;                               // [Nq][3][NPMAX] w|J| grad phi_i
+    double* wphi = W + W_VQ;                             // [Nq][NPMAX] w|J| phi_i (free until psi/chi)
     for (int idx = tid; idx < Nq * Np; idx += NTH) {
         const int g = idx / Np, i = idx - g * Np;
         const double* Ji = gv + g * 10 + 1;
         const double d0 = dphi[(size_t)g * Np + i], d1 = dphi[((size_t)Nq + g) * Np + i],
                      d2 = dphi[((size_t)2 * Nq + g) * Np + i];
-        for (int k = 0; k < 3; ++k) dp[(g * 3 + k) * NPMAX + i] = Ji[0 * 3 + k] * d0 + Ji[1 * 3 + k] * d1 + Ji[2 * 3 + k] * d2;
+        for (int k = 0; k < 3; ++k)
+            dp[(g * 3 + k) * NPMAX + i] = gv[g * 10] * (Ji[0 * 3 + k] * d0 + Ji[1 * 3 + k] * d1 + Ji[2 * 3 + k] * d2);
+        wphi[g * NPMAX + i] = gv[g * 10] * phi[(size_t)g * Np + i];
     }
+    __syncthreads();
     double* Mm = W + W_MM;
     for (int idx = tid; idx < Np * Np; idx += NTH) {
         const int i = idx / Np, j = idx - i * Np;
         double s = 0.0;
-        for (int g = 0; g < Nq; ++g) s += gv[g * 10] * phi[(size_t)g * Np + i] * phi[(size_t)g * Np + j];
+        for (int g = 0; g < Nq; ++g) s += wphi[g * NPMAX + i] * phi[(size_t)g * Np + j];
         Mm[i * NPMAX + j] = s;
     }
-    __syncthreads();
     // E_k = (phi_j, d_k phi_i) into G; B_q,k = -<phi_i mu_l n_k> into H
     for (int idx = tid; idx < 3 * Np * Np; idx += NTH) {
         const int k = idx / (Np * Np), rem = idx - k * Np * Np, i = rem / Np, j = rem - i * Np;
         double s = 0.0;
-        for (int g = 0; g < Nq; ++g) s += gv[g * 10] * dp[(g * 3 + k) * NPMAX + i] * phi[(size_t)g * Np + j];
+        for (int g = 0; g < Nq; ++g) s += dp[(g * 3 + k) * NPMAX + i] * phi[(size_t)g * Np + j];
         Gk[idx] = s;
     }
     for (int idx = tid; idx < 3 * Np * sfp; idx += NTH) {
@@ -731,6 +778,7 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
             s += gf[(d.soff[f] + q) * 3 + k] * phf[(size_t)q * Np + i] * mu[(size_t)q * d.nfp[f] + l];
         Hk[idx] = -s;
     }
+    __syncthreads();
     // Cholesky factor of the mass matrix (one warp)
     if (tid < 32) {
         for (int j = 0; j < Np; ++j) {
@@ -829,18 +877,27 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
         __syncthreads();
     }
     TJ* vq = reinterpret_cast<TJ*>(W + W_VQ);
-    for (int idx = tid; idx < 3 * npt * Nc; idx += NTH) {
-        const int k = idx / (npt * Nc), rem = idx - k * npt * Nc, x = rem / Nc, c = rem - x * Nc;
+    const int nc4 = (Nc + 3) / 4;                       // four columns per thread: one basis load per 4 FMAs
+    for (int idx = tid; idx < 3 * npt * nc4; idx += NTH) {
+        const int k = idx / (npt * nc4), rem = idx - k * npt * nc4, x = rem / nc4, c0 = 4 * (rem - x * nc4);
         const TJ* br = basis_row_t(tabJ, d, x);
-        TJ s = 0;
-        if (c < Np) {
-            const TJ* G = GJ + (size_t)k * Np * Np + c;
-            for (int j = 0; j < Np; ++j) s += br[j] * G[j * Np];
-        } else {
-            const TJ* H = HJ + (size_t)k * Np * sfp + (c - Np);
-            for (int j = 0; j < Np; ++j) s += br[j] * H[j * sfp];
+        const TJ* gp[4];
+        int st[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int c = min(c0 + u, Nc - 1);
+            if (c < Np) { gp[u] = GJ + (size_t)k * Np * Np + c; st[u] = Np; }
+            else { gp[u] = HJ + (size_t)k * Np * sfp + (c - Np); st[u] = sfp; }
         }
-        vq[((size_t)k * NPT + x) * NCM + c] = s;
+        TJ s[4] = {0, 0, 0, 0};
+        for (int j = 0; j < Np; ++j) {
+            const TJ b = br[j];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) s[u] += b * gp[u][j * st[u]];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (c0 + u < Nc) vq[((size_t)k * NPT + x) * NCM + c0 + u] = s[u];
     }
     __syncthreads();
     // A1: fluxes and their Jacobians at the points
@@ -1202,7 +1259,7 @@ __device__ void process_element(const KArgs& A, const TetElem& d, double* W, dou
         bordered_elim<NBE>(Mx, NU, NU, NU, LD, sD, sD + NRMAX * NB, piv, sflag, gpiv);
         __syncthreads();
         trace_schur_f32<NBE>(Mx, NU, t, LD, gpiv, reinterpret_cast<float*>(W + W_VQ),
-                             reinterpret_cast<float*>(W + W_CV), reinterpret_cast<float*>(sD));
+                             reinterpret_cast<float*>(W + W_CV), reinterpret_cast<float*>(sD), *ts, sflag);
     }
 }
 
