@@ -499,9 +499,10 @@ typedef struct {
  * boundary faces, tagged interior faces, a non-positive Jacobian at a
  * quadrature point).  Supported calls on the handle: hdg_set_params (tau,
  * viscosity law, precision: any HDG_PREC_MIXED* selects the tetrahedral mixed
- * form, FP32 Jacobian coefficients, contraction, trace rows of the elimination
- * and trace blocks with FP64 pointwise terms, interior LU and right-hand
- * sides), hdg_set_bc_state, hdg_set_stream, hdg_linearize_condense (packed
+ * form: FP32 Jacobian terms and column variations, the contraction and the
+ * Schur product S = Dt - W Z on the tensor cores in 3xTF32, FP32 triangular
+ * solves for W and Z and FP32 trace blocks, with FP64 fluxes, lifting
+ * operators, interior LU (pivoting) and right-hand sides), hdg_set_bc_state, hdg_set_stream, hdg_linearize_condense (packed
  * layouts; nu must be NULL), hdg_trace_matvec, hdg_trace_rhs,
  * hdg_recover_interior, hdg_get_blocks (FP32 values after a mixed
  * linearization), hdg_status, hdg_residual, hdg_update_state,
