@@ -76,3 +76,30 @@ def test_tet_element_blocks_match_oracle(H):
             assert np.linalg.norm(blk - ref) <= 1e-11 * np.linalg.norm(ref), e
     finally:
         H.hdg_destroy(h)
+
+
+def test_tet_mixed_element_blocks_match_oracle(H):
+    """The tetrahedral mixed form (tensor-core contraction and Schur product, FP32
+    triangular solves, FP64 interior LU) against the oracle's FP64 condensation of
+    every other element: 1e-4 relative per element in the Frobenius norm."""
+    from tests.test_gpu_tet import mesh_case, setup
+    prob, pb, h, dev = setup(H, mesh_case(1))
+    try:
+        H.hdg_set_params(h, tau=prob.tau, precision=H.HDG_PREC_MIXED)
+        L = H.hdg_tet_layout(h)
+        ts = np.diff(L["hoff"])[L["e2f"]].sum(1)
+        off = np.concatenate([[0], np.cumsum(ts.astype(np.int64) ** 2)])
+        SK = torch.zeros(int(off[-1]), dtype=torch.float32, device="cuda")
+        H.hdg_set_element_block_output(h, SK)
+        H.hdg_linearize_condense(h, dev["U"], dev["Q"], dev["UH"], dev["Ustar"], None, prob.dt, prob.a_ii)
+        assert H.hdg_status(h) == H.HDG_OK
+        got = SK.double().cpu().numpy()
+        errs = []
+        for e in range(0, len(ts), 2):                # every other element: all degrees, curved and affine
+            ref = pb.condense(e)["S"]
+            blk = got[off[e]:off[e + 1]].reshape(ts[e], ts[e])
+            errs.append(np.linalg.norm(blk - ref) / np.linalg.norm(ref))
+        assert max(errs) < 1e-4, max(errs)
+        assert max(errs) > 0.0                      # FP32 arithmetic is visible: not an FP64 copy
+    finally:
+        H.hdg_destroy(h)
