@@ -217,7 +217,8 @@ struct TcSeg {
 
 struct TcChunk {
     bool vol;
-    int j, p0, np;          // points p0 .. np - 1 of the block (face points: index into sum_f Nfq)
+    int j, p0, np;          // the chunk's points p0 .. p0 + 15 below the block's end np (face points:
+                            // an index into the sum_f Nfq face points)
 };
 
 __device__ __forceinline__ TcChunk tc_chunk(const TetElem& d, const TcSeg& sg, int ci) {
