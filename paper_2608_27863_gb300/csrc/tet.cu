@@ -578,7 +578,9 @@ __device__ void trace_schur_f32(double* Mx, int NU, int t, int LD, const int* gp
     __syncthreads();
     // Z = L^{-1} P Bt (FP32, one thread per column) and z = L^{-1} P Rt (FP64:
     // interchanges and the panel's block by one thread, the rows below by all)
+    constexpr int TPS = 304;                            // row stride of a staged panel (t <= 300)
     float* sL = smf;                                    // [NU - k0][NB] panel of L
+    float* sZp = smf + M * NPMAX * NB;                  // [NB][TPS] the panel's rows of Z
     __shared__ double zp[NB];
     double* zc = Mx + NR;                               // column NR, stride LD
     for (int k0 = 0; k0 < NU; k0 += NB) {
@@ -609,21 +611,6 @@ __device__ void trace_schur_f32(double* Mx, int NU, int t, int LD, const int* gp
 #pragma unroll
             for (int j = 0; j < NB; ++j)
                 if (j < kb) zf[(size_t)(k0 + j) * t] = zv[j];
-            // rows below the panel, 8 at a time: their loads are in flight together
-            for (int i0 = k0 + kb; i0 < NU; i0 += 8) {
-                float s2[8];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) s2[u] = zf[(size_t)min(i0 + u, NU - 1) * t];
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const float* l = sL + (size_t)(min(i0 + u, NU - 1) - k0) * NB;
-#pragma unroll
-                    for (int j = 0; j < NB; ++j) s2[u] = fmaf(-l[j], zv[j], s2[u]);
-                }
-#pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (i0 + u < NU) zf[(size_t)(i0 + u) * t] = s2[u];
-            }
         }
         if (tid == NTH - 1) {
             for (int j = 0; j < kb; ++j) {
@@ -642,16 +629,51 @@ __device__ void trace_schur_f32(double* Mx, int NU, int t, int LD, const int* gp
             }
         }
         __syncthreads();
+        for (int idx = tid; idx < kb * t; idx += NTH) {          // the panel's rows of Z, for the update
+            const int j = idx / t, r = idx - j * t;
+            sZp[j * TPS + r] = Zf[(size_t)(k0 + j) * t + r];
+        }
         for (int i = k0 + kb + tid; i < NU; i += NTH) {
             double s2 = zc[(size_t)i * LD];
             for (int j = 0; j < kb; ++j) s2 -= Mx[(size_t)i * LD + k0 + j] * zp[j];
             zc[(size_t)i * LD] = s2;
         }
         __syncthreads();
+        // rows below the panel: Z_below -= L_panel Z_panel in 4 x 4 register tiles
+        {
+            const int i0 = k0 + kb, nr = NU - i0, nrt = (nr + 3) / 4, nct = (t + 3) / 4;
+            for (int tile = tid; tile < nrt * nct; tile += NTH) {
+                const int ti = tile / nct, tc = tile - ti * nct, ib = i0 + 4 * ti, cb = 4 * tc;
+                float acc[4][4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        acc[u][v] = Zf[(size_t)min(ib + u, NU - 1) * t + min(cb + v, t - 1)];
+                for (int j = 0; j < kb; ++j) {
+                    float l[4], z[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) l[u] = sL[(size_t)(min(ib + u, NU - 1) - k0) * NB + j];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) z[v] = sZp[j * TPS + min(cb + v, t - 1)];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(-l[u], z[v], acc[u][v]);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        if (ib + u < NU && cb + v < t) Zf[(size_t)(ib + u) * t + cb + v] = acc[u][v];
+            }
+        }
+        __syncthreads();
     }
     // W = Ct U^{-1}: W U = Ct, panel by panel over the columns of U
     float* sUp = smf;                                   // [NB][NU - k0] panel rows of U
     float* sDi = smf + NB * NU;                         // [NB] reciprocal diagonal
+    float* sWp = smf + M * NPMAX * NB + NB;             // [NB][TPS] the panel's columns of W
     for (int k0 = 0; k0 < NU; k0 += NB) {
         const int kb = min(NB, NU - k0), w = NU - k0;
         for (int idx = tid; idx < NB * w; idx += NTH) {
@@ -677,20 +699,40 @@ __device__ void trace_schur_f32(double* Mx, int NU, int t, int LD, const int* gp
             }
 #pragma unroll
             for (int j = 0; j < NB; ++j)
-                if (j < kb) wc[(size_t)(k0 + j) * t] = wv[j];
-            for (int c0 = kb; c0 < w; c0 += 8) {        // 8 columns at a time, loads in flight together
-                float s2[8];
+                if (j < kb) {
+                    wc[(size_t)(k0 + j) * t] = wv[j];
+                    sWp[j * TPS + r] = wv[j];
+                }
+        }
+        __syncthreads();
+        // columns right of the panel: W_right -= W_panel U_panel,right in 4 x 4 register tiles
+        // (W kept transposed: row c of Wt is column c of W)
+        {
+            const int c0 = kb, nw = w - kb, nrt = (nw + 3) / 4, nct = (t + 3) / 4;
+            for (int tile = tid; tile < nrt * nct; tile += NTH) {
+                const int ti = tile / nct, tc = tile - ti * nct, cc = c0 + 4 * ti, rb = 4 * tc;
+                float acc[4][4];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) s2[u] = wc[(size_t)(k0 + min(c0 + u, w - 1)) * t];
+                for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int c = min(c0 + u, w - 1);
+                    for (int v = 0; v < 4; ++v)
+                        acc[u][v] = Wt[(size_t)(k0 + min(cc + u, w - 1)) * t + min(rb + v, t - 1)];
+                for (int j = 0; j < kb; ++j) {
+                    float uu[4], wr[4];
 #pragma unroll
-                    for (int j = 0; j < NB; ++j) s2[u] = fmaf(-wv[j], sUp[j * w + c], s2[u]);
+                    for (int u = 0; u < 4; ++u) uu[u] = sUp[j * w + min(cc + u, w - 1)];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) wr[v] = sWp[j * TPS + min(rb + v, t - 1)];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(-uu[u], wr[v], acc[u][v]);
                 }
 #pragma unroll
-                for (int u = 0; u < 8; ++u)
-                    if (c0 + u < w) wc[(size_t)(k0 + c0 + u) * t] = s2[u];
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+                        if (cc + u < w && rb + v < t) Wt[(size_t)(k0 + cc + u) * t + rb + v] = acc[u][v];
             }
         }
         __syncthreads();
