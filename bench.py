@@ -1069,7 +1069,8 @@ def main():
     ap.add_argument("--no-newton", action="store_true")
     ap.add_argument("--no-mixed", action="store_true", help="tetrahedral workloads: time the FP64 form only")
     ap.add_argument("--dirk", action="store_true",
-                    help="tetrahedral workloads: also time one graph-captured SDIRK3 step (3 stages x 4 Newton)")
+                    help="tetrahedral workloads: also time one graph-captured SDIRK3 step (3 stages x "
+                         "--dirk-newton Newton iterations x GMRES(--dirk-m))")
     ap.add_argument("--mixed-prec", choices=["fp32", "tf32", "3xtf32"], default="3xtf32")
     ap.add_argument("--precond", choices=["schwarz", "bj"], default="schwarz",
                     help="tetrahedral workloads: preconditioner of the Newton comparison's GMRES")

@@ -53,3 +53,14 @@ def test_oracle_check_elements_cover_every_degree():
     assert {int(elem_p[e]) for e in ids} == {1, 2, 3, 4}
     assert bench.oracle_check_elements(n_elem=4096) == [0, 1365, 2730, 4095]
     assert bench.oracle_check_elements(n_elem=1) == [0]
+
+
+def test_hex_traffic_table_covers_the_autotuned_dominant_kernels():
+    """The hex line's roofline traffic comes from ncu captures per (kernel, dim, p,
+    panel width): the FP64 element-block pair (sum-factorised volume + face terms)
+    and k_elim at both panel widths of hex p = 2; per-element bytes of the right
+    order (the 1.32 MB bordered matrix is read and written at least once)."""
+    t = bench.DRAM_BYTES_PER_ELEMENT
+    for key in (("elim", 3, 2, 16), ("elim", 3, 2, 8), ("blocks_sf", 3, 2, 0)):
+        assert key in t and 1e6 < t[key] < 1e8, key
+    assert t[("elim", 3, 2, 8)] > t[("elim", 3, 2, 16)]      # narrower panels re-read the trailing matrix more
